@@ -1,0 +1,747 @@
+/*
+ * FP64 CPU oracle of the receiver DSP chain -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Used by the tests, the smoke check and the benchmark's CPU-baseline leg; the
+ * CUDA receiver never links or calls it and shares no code with it.  Plain
+ * loops in the order of the method, double precision throughout.
+ *
+ * Paper passages followed (Sec. 2, "Multi-Format Real-Time DSP in GPU"):
+ *  - 12-bit ADC buffers of 2^22 samples at 4 GS/s, processed buffer by buffer
+ *    with overlap-save continuity carried from the previous buffer;
+ *  - KK front end: square root and natural logarithm of the detected signal at
+ *    4 samples/symbol, FD Hilbert transform by FFT/IFFT to recover the phase,
+ *    mixing with the square-root term and frequency downshifting (Fig. 1d);
+ *  - filtering and reduction to 2 samples/symbol, then a decision-directed LMS
+ *    equaliser with symbol-phase recovery, decision and demapping, applied to
+ *    data blocks of each buffer in parallel;
+ *  - PAM: equalisation, symbol decision and demapping (Fig. 1b);
+ *  - performance as Q-factor derived from the BER (Sec. 3).
+ * The filter shapes, adaptive algorithms (CMA, LMS, blind phase search) and
+ * their parameters are the configured workload's; where the paper is silent the
+ * reading used is stated beside the code.
+ */
+#include "rx_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI 3.14159265358979323846
+
+typedef struct { double re, im; } cx;
+
+static cx cx_mk(double r, double i) { cx z; z.re = r; z.im = i; return z; }
+static cx cx_add(cx a, cx b) { return cx_mk(a.re + b.re, a.im + b.im); }
+static cx cx_sub(cx a, cx b) { return cx_mk(a.re - b.re, a.im - b.im); }
+static cx cx_mul(cx a, cx b) { return cx_mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+static cx cx_conj(cx a) { return cx_mk(a.re, -a.im); }
+static cx cx_scale(cx a, double s) { return cx_mk(a.re * s, a.im * s); }
+static double cx_abs2(cx a) { return a.re * a.re + a.im * a.im; }
+static cx cx_expj(double t) { return cx_mk(cos(t), sin(t)); }
+
+static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
+
+/* ------------------------------------------------------------- 12-bit unpack
+ * Two 12-bit samples per three bytes (the ADC word of Sec. 2).  order 0:
+ * little-endian 24-bit word; order 1: big-endian nibble order. */
+void orx_unpack(const uint8_t *in, int64_t nsamp, int order, int32_t *codes)
+{
+    for (int64_t p = 0; p < nsamp / 2; p++) {
+        uint32_t b0 = in[3 * p], b1 = in[3 * p + 1], b2 = in[3 * p + 2];
+        if (order == 0) {
+            codes[2 * p] = (int32_t)(b0 | ((b1 & 0x0Fu) << 8));
+            codes[2 * p + 1] = (int32_t)((b1 >> 4) | (b2 << 4));
+        } else {
+            codes[2 * p] = (int32_t)((b0 << 4) | (b1 >> 4));
+            codes[2 * p + 1] = (int32_t)(((b1 & 0x0Fu) << 8) | b2);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------- FFT
+ * Radix-2 decimation-in-time, in place.  forward: X_k = sum x_n e^{-2pi i nk/N};
+ * inverse: x_n = (1/N) sum X_k e^{+2pi i nk/N}.  Twiddles from cos/sin of the
+ * exact angle (no recurrence). */
+void orx_fft(double *re, double *im, int n, int inverse)
+{
+    for (int i = 1, j = 0; i < n; i++) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            double t = re[i]; re[i] = re[j]; re[j] = t;
+            t = im[i]; im[i] = im[j]; im[j] = t;
+        }
+    }
+    double sgn = inverse ? 1.0 : -1.0;
+    for (int len = 2; len <= n; len <<= 1) {
+        int half = len >> 1;
+        for (int k = 0; k < half; k++) {
+            double ang = sgn * 2.0 * PI * (double)k / (double)len;
+            double wr = cos(ang), wi = sin(ang);
+            for (int s = 0; s < n; s += len) {
+                int a = s + k, b = a + half;
+                double xr = re[b] * wr - im[b] * wi;
+                double xi = re[b] * wi + im[b] * wr;
+                re[b] = re[a] - xr; im[b] = im[a] - xi;
+                re[a] += xr; im[a] += xi;
+            }
+        }
+    }
+    if (inverse) {
+        double s = 1.0 / (double)n;
+        for (int i = 0; i < n; i++) { re[i] *= s; im[i] *= s; }
+    }
+}
+
+/* Hilbert transform of one real block, circular: phi = IFFT(FFT(u) * h) with
+ * h_k = -j (0 < k < N/2), +j (N/2 < k < N), 0 at k = 0 and k = N/2.
+ * (FD Hilbert transform by FFT and IFFT, Sec. 2 KK chain.) */
+static void hilbert_block(const double *u, double *phi, int n, double *re, double *im)
+{
+    for (int i = 0; i < n; i++) { re[i] = u[i]; im[i] = 0.0; }
+    orx_fft(re, im, n, 0);
+    for (int k = 0; k < n; k++) {
+        double a = re[k], b = im[k];
+        if (k == 0 || 2 * k == n) { re[k] = 0.0; im[k] = 0.0; }
+        else if (2 * k < n) { re[k] = b; im[k] = -a; }      /* times -j */
+        else { re[k] = -b; im[k] = a; }                      /* times +j */
+    }
+    orx_fft(re, im, n, 1);
+    for (int i = 0; i < n; i++) phi[i] = re[i];
+}
+
+void orx_hilbert_circ(const double *u, double *phi, int n)
+{
+    double *re = xcalloc((size_t)n, sizeof(double)), *im = xcalloc((size_t)n, sizeof(double));
+    hilbert_block(u, phi, n, re, im);
+    free(re); free(im);
+}
+
+/* Intensity -> KK field, log guard as in the receiver. */
+static double kk_intensity(int32_t code) { return code > 0 ? (double)code : 0.5; }
+
+/* One circular KK reconstruction: E = sqrt(I) exp(j H{ln(I)/2}). */
+void orx_kk_circ(const double *intensity, double *e_re, double *e_im, int n)
+{
+    double *u = xcalloc((size_t)n, sizeof(double)), *phi = xcalloc((size_t)n, sizeof(double));
+    for (int i = 0; i < n; i++) u[i] = 0.5 * log(intensity[i]);
+    orx_hilbert_circ(u, phi, n);
+    for (int i = 0; i < n; i++) {
+        double a = sqrt(intensity[i]);
+        e_re[i] = a * cos(phi[i]);
+        e_im[i] = a * sin(phi[i]);
+    }
+    free(u); free(phi);
+}
+
+/* Root-raised cosine, sps*span+1 taps, unit energy, zero phase. */
+void orx_rrc(double beta, int sps, int span, double *taps)
+{
+    int half = sps * span / 2, n = 2 * half + 1;
+    double e = 0.0;
+    for (int i = 0; i < n; i++) {
+        double t = (double)(i - half) / (double)sps, v;
+        if (fabs(t) < 1e-12)
+            v = 1.0 - beta + 4.0 * beta / PI;
+        else if (beta > 0.0 && fabs(fabs(4.0 * beta * t) - 1.0) < 1e-12)
+            v = beta / sqrt(2.0) * ((1.0 + 2.0 / PI) * sin(PI / (4.0 * beta)) +
+                                    (1.0 - 2.0 / PI) * cos(PI / (4.0 * beta)));
+        else
+            v = (sin(PI * t * (1.0 - beta)) + 4.0 * beta * t * cos(PI * t * (1.0 + beta))) /
+                (PI * t * (1.0 - 16.0 * beta * beta * t * t));
+        taps[i] = v;
+        e += v * v;
+    }
+    e = 1.0 / sqrt(e);
+    for (int i = 0; i < n; i++) taps[i] *= e;
+}
+
+/* PRBS-15, Fibonacci LFSR x^15 + x^14 + 1; register loaded with
+ * (seed mod 32767) + 1; each step outputs r14 xor r15 and shifts it in. */
+void orx_prbs15(uint32_t seed, int64_t nbits, uint8_t *out)
+{
+    uint32_t r = (seed % 32767u) + 1u;
+    for (int64_t i = 0; i < nbits; i++) {
+        uint32_t nb = ((r >> 13) ^ (r >> 14)) & 1u;
+        r = ((r << 1) | nb) & 0x7FFFu;
+        out[i] = (uint8_t)nb;
+    }
+}
+
+/* Q = 20 log10(sqrt(2) erfcinv(2 BER)); erfcinv by bisection on erfc. */
+double orx_q_db(double ber)
+{
+    if (!(ber > 0.0)) return INFINITY;
+    if (ber >= 0.5) return -INFINITY;
+    double target = 2.0 * ber, lo = 0.0, hi = 30.0;
+    for (int it = 0; it < 200; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (erfc(mid) > target) lo = mid; else hi = mid;
+    }
+    return 20.0 * log10(sqrt(2.0) * 0.5 * (lo + hi));
+}
+
+/* ============================================================ the receiver */
+struct orx {
+    orx_cfg c;
+    int kk, bps, mq, dims, dec, hmf, th;
+    double scale, r2;
+    double *rrc;
+    uint8_t *prbs;                 /* one PRBS-15 period */
+    int64_t calls, e_prev, f_prev, q_prev;
+    int32_t *chist; int64_t chist_len, chist_cap;
+    int have_first; int32_t first_code;
+    cx *ehist; int64_t ehist_start, ehist_len;
+    cx *yhist; int64_t yhist_start, yhist_len;
+    cx carrier; double gain;
+    cx *w;                         /* taps every block of the next call starts from */
+    int trained;
+    int have_b, b_last; int64_t m_last;
+    int amb_done, amb_r;
+    int64_t n_samples, n_symbols, n_bits, n_bit_err, n_sym_err, n_near, n_amb, n_win, n_raw_err, n_slip;
+    /* debug views of the last call */
+    cx *d_E; int64_t d_E_start, d_E_len;
+    cx *d_y; int64_t d_y_start, d_y_len;
+    cx *d_z, *d_v; int32_t *d_ahat, *d_draw, *d_berr, *d_near; int64_t d_s_start, d_s_len;
+    double *d_win; int64_t d_win_len;
+    double scal[5];
+};
+
+orx *orx_create(const orx_cfg *cfg)
+{
+    orx *h = xcalloc(1, sizeof(orx));
+    h->c = *cfg;
+    int f = cfg->format;
+    if (f < 0 || f > 4 || cfg->ntaps < 1 || !(cfg->ntaps & 1) || cfg->win < 1 || cfg->win > 4096 ||
+        cfg->eq_block < cfg->win || cfg->eq_block % cfg->win || cfg->ntrain < 0 || cfg->ntrain % cfg->win ||
+        cfg->buf_len < 2 || (cfg->buf_len & 1) || cfg->sps < 2 || (cfg->sps & 1) || cfg->mf_span < 0 ||
+        (f >= 3 && (cfg->ncma < 0 || cfg->ncma > cfg->ntrain || cfg->ncma % cfg->win || cfg->bps_b < 1 ||
+                    cfg->ds_den < 1 || cfg->ols_n < 4 || (cfg->ols_n & (cfg->ols_n - 1)) ||
+                    cfg->ols_v < 2 || (cfg->ols_v & 1) || cfg->ols_v >= cfg->ols_n))) {
+        free(h);
+        return NULL;
+    }
+    h->kk = f >= 3;
+    h->bps = (f == 0) ? 1 : (f == 1) ? 2 : (f == 2) ? 3 : (f == 3) ? 2 : 4;
+    if (h->kk) {
+        h->dims = 2;
+        h->mq = (f == 3) ? 2 : 4;
+        h->scale = (f == 3) ? sqrt(2.0) : sqrt(10.0);
+        h->r2 = (f == 3) ? 1.0 : 1.32;   /* E|a|^4 / E|a|^2 of the unit-power constellation */
+        h->dec = cfg->sps / 2;           /* matched filter output at 2 samples/symbol */
+    } else {
+        h->dims = 1;
+        h->mq = 1 << h->bps;
+        h->scale = 1.0;
+        h->r2 = 0.0;
+        h->dec = cfg->sps / 2;
+    }
+    h->hmf = cfg->sps * cfg->mf_span / 2;
+    h->th = (cfg->ntaps - 1) / 2;
+    h->rrc = xcalloc((size_t)(2 * h->hmf + 1), sizeof(double));
+    orx_rrc(cfg->rrc_beta, cfg->sps, cfg->mf_span, h->rrc);
+    h->prbs = xcalloc(32767, 1);
+    orx_prbs15(cfg->prbs_seed, 32767, h->prbs);
+    h->chist_cap = h->kk ? cfg->ols_n : 2 * h->hmf;
+    h->chist = xcalloc((size_t)h->chist_cap, sizeof(int32_t));
+    h->w = xcalloc((size_t)cfg->ntaps, sizeof(cx));
+    h->w[h->th] = cx_mk(1.0, 0.0);      /* centre tap 1 */
+    h->gain = 1.0;
+    h->amb_r = -1;
+    return h;
+}
+
+void orx_set_taps(orx *h, const double *re, const double *im, int n)
+{
+    for (int i = 0; i < n && i < h->c.ntaps; i++) h->w[i] = cx_mk(re[i], im ? im[i] : 0.0);
+}
+
+/* --------------------------------------------------------------- decisions */
+/* level index (0 = lowest) of t on odd-integer levels -(mq-1)..(mq-1);
+ * thresholds at the even integers between them, ties to the upper level */
+static int decide_dim(double t, int mq)
+{
+    int L = 0;
+    for (int j = 0; j < mq - 1; j++)
+        if (t >= (double)(2 * j - (mq - 2))) L = j + 1;
+    return L;
+}
+static double level_value(int L, int mq) { return (double)(2 * L - (mq - 1)); }
+static int near_dim(double t, int mq)
+{
+    for (int j = 0; j < mq - 1; j++)
+        if (fabs(t - (double)(2 * j - (mq - 2))) < 1e-4) return 1;
+    return 0;
+}
+/* squared distance of t to the nearest level */
+static double dist_dim(double t, int mq)
+{
+    double best = INFINITY;
+    for (int L = 0; L < mq; L++) {
+        double d = t - level_value(L, mq);
+        if (d * d < best) best = d * d;
+    }
+    return best;
+}
+static int gray_of(int L) { return L ^ (L >> 1); }
+static int gray_inv(int g) { int L = g; for (int s = g >> 1; s; s >>= 1) L ^= s; return L; }
+
+/* transmitted level indices of symbol k from the PRBS (MSB first) */
+static void tx_symbol(const orx *h, int64_t k, int *LI, int *LQ)
+{
+    int nb = h->kk ? h->bps / 2 : h->bps;
+    int64_t b0 = (int64_t)h->bps * k;
+    int gi = 0, gq = 0;
+    for (int t = 0; t < nb; t++) gi = (gi << 1) | h->prbs[(b0 + t) % 32767];
+    if (h->kk)
+        for (int t = 0; t < nb; t++) gq = (gq << 1) | h->prbs[(b0 + nb + t) % 32767];
+    *LI = gray_inv(gi);
+    *LQ = h->kk ? gray_inv(gq) : 0;
+}
+
+/* Blind-phase-search metric of one window (exported for the pins):
+ * metric[b] = sum_k min_d |s z_k e^{-j theta_b} - d|^2, theta_b = (b/B)(pi/2) - pi/4,
+ * d over the square constellation with mq odd-integer levels per dimension. */
+void orx_bps_metrics(const double *z_re, const double *z_im, int W, int mq, double s, int B, double *metric)
+{
+    for (int b = 0; b < B; b++) {
+        double tb = ((double)b / (double)B) * (PI / 2.0) - PI / 4.0;
+        cx rot = cx_expj(-tb);
+        double M = 0.0;
+        for (int q = 0; q < W; q++) {
+            cx t = cx_scale(cx_mul(cx_mk(z_re[q], z_im[q]), rot), s);
+            M += dist_dim(t.re, mq) + dist_dim(t.im, mq);
+        }
+        metric[b] = M;
+    }
+}
+
+/* ------------------------------------------------------------ call context */
+typedef struct {
+    orx *h;
+    const int32_t *cur; int64_t base;   /* current buffer: stream samples [base, base+Nb) */
+    cx *E; int64_t E_start, E_len;      /* this call's KK outputs */
+    cx *y; int64_t y_start, y_len;      /* this call's matched-filter outputs */
+    double mu_pam, sd_pam;
+} ctx;
+
+static int32_t code_at(const ctx *x, int64_t n)
+{
+    const orx *h = x->h;
+    if (n < 0) return h->have_first ? h->first_code : x->cur[0];   /* pre-stream: first sample replicated */
+    if (n >= x->base) return x->cur[n - x->base];
+    int64_t i = n - (x->base - h->chist_len);
+    return (i >= 0) ? h->chist[i] : 0;   /* never reached for valid configs */
+}
+static cx e_at(const ctx *x, int64_t n)
+{
+    const orx *h = x->h;
+    if (n < 0) return cx_mk(0.0, 0.0);
+    if (n >= x->E_start) return x->E[n - x->E_start];
+    return h->ehist[n - h->ehist_start];
+}
+static cx y_at(const ctx *x, int64_t m)
+{
+    const orx *h = x->h;
+    if (m < 0) return cx_mk(0.0, 0.0);
+    if (m >= x->y_start) return x->y[m - x->y_start];
+    return h->yhist[m - h->yhist_start];
+}
+
+/* ----------------------------------------------------------- equaliser window
+ * One window of `win` symbols starting at symbol k0 with taps w:
+ *   z_k = sum_i conj(w_i) y[2k - i]              (i = -th..th)
+ *   blind phase search (decision-directed QAM): theta_b = (b/B)(pi/2) - pi/4,
+ *   metric_b = sum_k min_d |s z_k e^{-j theta_b} - d|^2, b* = first argmin
+ *   decision per dimension on s z_k e^{-j theta*}
+ *   error: CMA  e = z (R2 - |z|^2);  data-aided  e = a_k - z;
+ *          decision-directed  e = (d/s) e^{j theta*} - z
+ *   block-LMS update after the window: w_i += mu sum_k y[2k-i] conj(e_k)
+ * mode: 0 CMA, 1 data-aided, 2 decision-directed. */
+typedef struct { int b; double best, second; } winres;
+
+static winres eq_window(ctx *x, cx *w, int64_t k0, int mode, double mu,
+                        cx *z, cx *v, int32_t *draw, int32_t *nearf)
+{
+    orx *h = x->h;
+    int W = h->c.win, th = h->th;
+    winres R; R.b = -1; R.best = 0.0; R.second = 0.0;
+    for (int q = 0; q < W; q++) {
+        int64_t k = k0 + q;
+        cx acc = cx_mk(0.0, 0.0);
+        for (int i = -th; i <= th; i++) acc = cx_add(acc, cx_mul(cx_conj(w[i + th]), y_at(x, 2 * k - i)));
+        z[q] = acc;
+    }
+    double theta = 0.0;
+    if (h->kk && mode == 2) {
+        int B = h->c.bps_b;
+        double best = INFINITY, second = INFINITY;
+        int bb = 0;
+        for (int b = 0; b < B; b++) {
+            double tb = ((double)b / (double)B) * (PI / 2.0) - PI / 4.0;
+            cx rot = cx_expj(-tb);
+            double M = 0.0;
+            for (int q = 0; q < W; q++) {
+                cx t = cx_scale(cx_mul(z[q], rot), h->scale);
+                M += dist_dim(t.re, h->mq) + dist_dim(t.im, h->mq);
+            }
+            if (M < best) { second = best; best = M; bb = b; }
+            else if (M < second) second = M;
+        }
+        R.b = bb; R.best = best; R.second = second;
+        theta = ((double)bb / (double)B) * (PI / 2.0) - PI / 4.0;
+    }
+    cx e[4096];
+    cx rot = cx_expj(-theta), unrot = cx_expj(theta);
+    for (int q = 0; q < W; q++) {
+        int64_t k = k0 + q;
+        cx t = cx_scale(cx_mul(z[q], rot), h->scale);
+        v[q] = t;
+        int LI = decide_dim(t.re, h->mq);
+        int LQ = h->kk ? decide_dim(t.im, h->mq) : 0;
+        draw[2 * q] = LI; draw[2 * q + 1] = LQ;
+        nearf[q] = near_dim(t.re, h->mq) || (h->kk && near_dim(t.im, h->mq));
+        if (mode == 0) {
+            e[q] = cx_scale(z[q], h->r2 - cx_abs2(z[q]));
+        } else if (mode == 1) {
+            int aI, aQ;
+            tx_symbol(h, k, &aI, &aQ);
+            e[q] = cx_sub(cx_mk(level_value(aI, h->mq), 0.0), z[q]);
+        } else {
+            cx d = cx_mk(level_value(LI, h->mq), h->kk ? level_value(LQ, h->mq) : 0.0);
+            e[q] = cx_sub(cx_mul(cx_scale(d, 1.0 / h->scale), unrot), z[q]);
+        }
+    }
+    for (int i = -th; i <= th; i++) {
+        cx g = cx_mk(0.0, 0.0);
+        for (int q = 0; q < W; q++) g = cx_add(g, cx_mul(y_at(x, 2 * (k0 + q) - i), cx_conj(e[q])));
+        w[i + th] = cx_add(w[i + th], cx_scale(g, mu));
+    }
+    return R;
+}
+
+static void put_bit(uint8_t *out, int64_t t, int bit)
+{
+    if (bit) out[t >> 3] |= (uint8_t)(0x80u >> (t & 7));
+}
+
+int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bits_cap)
+{
+    const orx_cfg *c = &h->c;
+    int64_t Nb = c->buf_len;
+    int32_t *cur = xcalloc((size_t)Nb, sizeof(int32_t));
+    orx_unpack(packed, Nb, c->pack_order, cur);
+    ctx X; memset(&X, 0, sizeof X);
+    X.h = h; X.cur = cur; X.base = h->calls * Nb;
+    if (!h->have_first) { h->first_code = cur[0]; h->have_first = 1; }
+    int64_t avail = X.base + Nb;
+
+    /* emission counts: every step emits what its full support allows */
+    int64_t e_k = h->kk ? avail - c->ols_v / 2 : avail;
+    if (e_k < 0) e_k = 0;
+    int64_t f_k = (e_k >= h->hmf + 1) ? (e_k - h->hmf - 1) / h->dec + 1 : 0;
+    int64_t s_k = (f_k >= h->th + 1) ? (f_k - h->th - 1) / 2 + 1 : 0;
+    int64_t q_k = (s_k >= c->ntrain) ? c->ntrain + ((s_k - c->ntrain) / c->eq_block) * c->eq_block : 0;
+    if (q_k < h->q_prev) q_k = h->q_prev;
+
+    /* ---- KK field reconstruction by overlap-save blocks ---------------- */
+    X.E_start = h->e_prev; X.E_len = h->kk ? e_k - h->e_prev : 0;
+    X.E = xcalloc((size_t)(X.E_len > 0 ? X.E_len : 1), sizeof(cx));
+    if (h->kk && X.E_len > 0) {
+        int N = c->ols_n, V = c->ols_v, hop = N - V;
+        double *u = xcalloc((size_t)N, sizeof(double)), *phi = xcalloc((size_t)N, sizeof(double));
+        double *re = xcalloc((size_t)N, sizeof(double)), *im = xcalloc((size_t)N, sizeof(double));
+        int64_t J = (X.E_len + hop - 1) / hop;
+        for (int64_t j = 0; j < J; j++) {
+            int64_t o = h->e_prev + j * hop;                   /* first kept output */
+            int64_t ws = (j < J - 1) ? o - V / 2 : avail - N;   /* last block ends at the newest sample */
+            int64_t cnt = (j < J - 1) ? hop : e_k - o;
+            for (int t = 0; t < N; t++) u[t] = 0.5 * log(kk_intensity(code_at(&X, ws + t)));
+            hilbert_block(u, phi, N, re, im);
+            for (int64_t n = o; n < o + cnt; n++) {
+                double a = sqrt(kk_intensity(code_at(&X, n)));
+                X.E[n - X.E_start] = cx_scale(cx_expj(phi[n - ws]), a);
+            }
+        }
+        free(u); free(phi); free(re); free(im);
+        /* carrier (the real tone of the KK field) and signal-power gain of this call:
+         * c = mean E, P = mean I - |c|^2, g = 1/sqrt(sps P)  (reading) */
+        cx sumE = cx_mk(0.0, 0.0);
+        double sumI = 0.0;
+        for (int64_t n = h->e_prev; n < e_k; n++) {
+            sumE = cx_add(sumE, X.E[n - X.E_start]);
+            sumI += kk_intensity(code_at(&X, n));
+        }
+        h->carrier = cx_scale(sumE, 1.0 / (double)X.E_len);
+        double P = sumI / (double)X.E_len - cx_abs2(h->carrier);
+        h->gain = (P > 0.0) ? 1.0 / sqrt((double)c->sps * P) : 1.0;
+    }
+    if (!h->kk) {
+        /* DC removal and scaling by the buffer's mean and standard deviation */
+        double s1 = 0.0, s2 = 0.0;
+        for (int64_t i = 0; i < Nb; i++) { s1 += cur[i]; s2 += (double)cur[i] * cur[i]; }
+        X.mu_pam = s1 / (double)Nb;
+        double var = s2 / (double)Nb - X.mu_pam * X.mu_pam;
+        X.sd_pam = (var > 0.0) ? sqrt(var) : 1.0;
+    }
+
+    /* ---- matched filter (and 4 -> 2 samples/symbol for KK) ------------- */
+    X.y_start = h->f_prev; X.y_len = f_k - h->f_prev;
+    X.y = xcalloc((size_t)(X.y_len > 0 ? X.y_len : 1), sizeof(cx));
+    for (int64_t m = h->f_prev; m < f_k; m++) {
+        cx acc = cx_mk(0.0, 0.0);
+        for (int i = -h->hmf; i <= h->hmf; i++) {
+            int64_t n = (int64_t)h->dec * m - i;
+            if (n < 0) continue;
+            cx xn;
+            if (h->kk) {
+                /* carrier removal, then downshift by ds_num/ds_den cycles/sample */
+                int64_t p = ((n % c->ds_den) * c->ds_num) % c->ds_den;
+                xn = cx_mul(cx_sub(e_at(&X, n), h->carrier),
+                            cx_expj(-2.0 * PI * (double)p / (double)c->ds_den));
+            } else {
+                xn = cx_mk(((double)code_at(&X, n) - X.mu_pam) / X.sd_pam, 0.0);
+            }
+            acc = cx_add(acc, cx_scale(xn, h->rrc[i + h->hmf]));
+        }
+        X.y[m - X.y_start] = h->kk ? cx_scale(acc, h->gain) : acc;
+    }
+
+    /* ---- equaliser ------------------------------------------------------ */
+    int W = c->win;
+    int64_t sym_lo = h->trained ? h->q_prev : 0;
+    int64_t nproc = (q_k > sym_lo) ? q_k - sym_lo : 0;
+    if (!h->trained && q_k < c->ntrain) nproc = 0;
+    cx *Z = xcalloc((size_t)(nproc + 1), sizeof(cx)), *Vv = xcalloc((size_t)(nproc + 1), sizeof(cx));
+    int32_t *draw = xcalloc((size_t)(2 * nproc + 2), sizeof(int32_t));
+    int32_t *nearf = xcalloc((size_t)(nproc + 1), sizeof(int32_t));
+    int64_t pay_lo = sym_lo;
+    if (nproc > 0 && !h->trained) {
+        /* training at stream start, sequential over windows: KK CMA for the first
+         * ncma symbols then decision-directed; PAM data-aided LMS */
+        for (int64_t k0 = 0; k0 < c->ntrain; k0 += W) {
+            int mode = h->kk ? (k0 < c->ncma ? 0 : 2) : 1;
+            double mu = h->kk ? (mode == 0 ? c->mu_cma : c->mu) : c->mu_train;
+            eq_window(&X, h->w, k0, mode, mu, Z + k0, Vv + k0, draw + 2 * k0, nearf + k0);
+        }
+        h->trained = 1;
+        pay_lo = c->ntrain;
+    }
+    int64_t npay = (nproc > 0) ? q_k - pay_lo : 0;
+    int64_t nwin = npay / W;
+    double *dwin = xcalloc((size_t)(4 * nwin + 4), sizeof(double));
+    int64_t *msym = xcalloc((size_t)(npay + 1), sizeof(int64_t));
+    if (npay > 0) {
+        /* payload: independent blocks of eq_block symbols, all starting from the
+         * same taps (block parallelism of the 8192 data blocks, Sec. 2) */
+        cx *wb = xcalloc((size_t)c->ntaps, sizeof(cx)), *wlast = xcalloc((size_t)c->ntaps, sizeof(cx));
+        for (int64_t b0 = pay_lo; b0 < q_k; b0 += c->eq_block) {
+            memcpy(wb, h->w, sizeof(cx) * (size_t)c->ntaps);
+            for (int64_t k0 = b0; k0 < b0 + c->eq_block; k0 += W) {
+                int64_t o = k0 - sym_lo;
+                winres R = eq_window(&X, wb, k0, 2, c->mu, Z + o, Vv + o, draw + 2 * o, nearf + o);
+                int64_t wi = (k0 - pay_lo) / W;
+                dwin[4 * wi] = R.b; dwin[4 * wi + 2] = R.best; dwin[4 * wi + 3] = R.second;
+                if (h->kk && (R.second - R.best) <= 1e-6 * R.best) h->n_amb++;
+            }
+            memcpy(wlast, wb, sizeof(cx) * (size_t)c->ntaps);
+        }
+        memcpy(h->w, wlast, sizeof(cx) * (size_t)c->ntaps);
+        free(wb); free(wlast);
+        /* integer pi/2 unwrap of the window phase index, carried across calls */
+        for (int64_t wi = 0; wi < nwin; wi++) {
+            int b = (int)dwin[4 * wi];
+            int64_t m = 0;
+            if (h->kk) {
+                if (h->have_b) {
+                    int d = h->b_last - b;
+                    m = h->m_last + (d > c->bps_b / 2) - (d < -c->bps_b / 2);
+                }
+                h->have_b = 1; h->b_last = b; h->m_last = m;
+            }
+            dwin[4 * wi + 1] = (double)m;
+            for (int q = 0; q < W; q++) msym[wi * W + q] = m;
+        }
+        h->n_win += nwin;
+    }
+
+    /* ---- ambiguity, demap, bit errors ---------------------------------- */
+    int32_t *ahat = xcalloc((size_t)(2 * nproc + 2), sizeof(int32_t));
+    int32_t *berr = xcalloc((size_t)(nproc + 1), sizeof(int32_t));
+    for (int64_t i = 0; i < nproc; i++) { ahat[2 * i] = draw[2 * i]; ahat[2 * i + 1] = draw[2 * i + 1]; berr[i] = -1; }
+    int64_t off = pay_lo - sym_lo;
+    if (h->kk && npay > 0 && !h->amb_done) {
+        /* resolve the pi/2 ambiguity once: the rotation whose first amb_syms
+         * payload decisions best match the known transmitted symbols (reading) */
+        int64_t A = c->amb_syms < npay ? c->amb_syms : npay;
+        int best_r = 0; int64_t best_cnt = -1;
+        for (int r = 0; r < 4; r++) {
+            int64_t cnt = 0;
+            for (int64_t i = 0; i < A; i++) {
+                int LI = draw[2 * (off + i)], LQ = draw[2 * (off + i) + 1];
+                int q = (int)(((msym[i] + r) % 4 + 4) % 4);
+                for (int s = 0; s < q; s++) { int t = LI; LI = LQ; LQ = h->mq - 1 - t; }
+                int aI, aQ;
+                tx_symbol(h, pay_lo + i, &aI, &aQ);
+                cnt += (LI != aI || LQ != aQ);
+            }
+            if (best_cnt < 0 || cnt < best_cnt) { best_cnt = cnt; best_r = r; }
+        }
+        h->amb_r = best_r; h->amb_done = 1;
+    }
+    int64_t nbits = (int64_t)h->bps * npay;
+    if (bits_out && bits_cap > 0) memset(bits_out, 0, (size_t)((bits_cap + 7) / 8));
+    int nb = h->kk ? h->bps / 2 : h->bps;
+    for (int64_t i = 0; i < npay; i++) {
+        int64_t o = off + i;
+        int LI = draw[2 * o], LQ = draw[2 * o + 1];
+        if (h->kk) {
+            int q = (int)(((msym[i] + h->amb_r) % 4 + 4) % 4);
+            for (int s = 0; s < q; s++) { int t = LI; LI = LQ; LQ = h->mq - 1 - t; }
+        }
+        ahat[2 * o] = LI; ahat[2 * o + 1] = LQ;
+        int gi = gray_of(LI), gq = gray_of(LQ);
+        int64_t t0 = (int64_t)h->bps * i;
+        if (bits_out && t0 + h->bps <= bits_cap) {
+            for (int t = 0; t < nb; t++) put_bit(bits_out, t0 + t, (gi >> (nb - 1 - t)) & 1);
+            if (h->kk) for (int t = 0; t < nb; t++) put_bit(bits_out, t0 + nb + t, (gq >> (nb - 1 - t)) & 1);
+        }
+    }
+    /* Bit-error counting against the PRBS, window by window.  The blind phase
+     * search holds one phase per window, so a cycle slip can only start at a
+     * window edge; like a BER tester that re-synchronises after a slip, each
+     * window is scored under the pi/2 rotation (applied on top of the decoded
+     * symbols) with the fewest bit errors, ties to no rotation (reading).  PAM
+     * has no rotation.  Symbols used to resolve the stream-start ambiguity are
+     * not counted. */
+    for (int64_t wi = 0; wi < nwin; wi++) {
+        int64_t k0 = pay_lo + wi * W;
+        if (h->kk && k0 < c->ntrain + c->amb_syms) continue;
+        int nrot = h->kk ? 4 : 1;
+        int64_t errs[4] = {0, 0, 0, 0};
+        for (int rho = 0; rho < nrot; rho++) {
+            for (int q = 0; q < W; q++) {
+                int64_t o = off + wi * W + q, k = k0 + q;
+                int LI = ahat[2 * o], LQ = ahat[2 * o + 1];
+                for (int s = 0; s < rho; s++) { int t = LI; LI = LQ; LQ = h->mq - 1 - t; }
+                int gi = gray_of(LI), gq = gray_of(LQ), bitsym[8];
+                for (int t = 0; t < nb; t++) bitsym[t] = (gi >> (nb - 1 - t)) & 1;
+                if (h->kk) for (int t = 0; t < nb; t++) bitsym[nb + t] = (gq >> (nb - 1 - t)) & 1;
+                int ne = 0;
+                for (int t = 0; t < h->bps; t++) ne += bitsym[t] != h->prbs[((int64_t)h->bps * k + t) % 32767];
+                errs[rho] += ne;
+                if (rho == 0) berr[o] = ne;
+            }
+        }
+        int best = 0;
+        for (int rho = 1; rho < nrot; rho++) if (errs[rho] < errs[best]) best = rho;
+        if (best != 0) {
+            for (int q = 0; q < W; q++) {   /* per-symbol errors under the chosen rotation */
+                int64_t o = off + wi * W + q, k = k0 + q;
+                int LI = ahat[2 * o], LQ = ahat[2 * o + 1];
+                for (int s = 0; s < best; s++) { int t = LI; LI = LQ; LQ = h->mq - 1 - t; }
+                int gi = gray_of(LI), gq = gray_of(LQ), bitsym[8];
+                for (int t = 0; t < nb; t++) bitsym[t] = (gi >> (nb - 1 - t)) & 1;
+                if (h->kk) for (int t = 0; t < nb; t++) bitsym[nb + t] = (gq >> (nb - 1 - t)) & 1;
+                int ne = 0;
+                for (int t = 0; t < h->bps; t++) ne += bitsym[t] != h->prbs[((int64_t)h->bps * k + t) % 32767];
+                berr[o] = ne;
+            }
+            h->n_slip++;
+        }
+        h->n_raw_err += errs[0];
+        h->n_bit_err += errs[best];
+        h->n_bits += (int64_t)h->bps * W;
+        for (int q = 0; q < W; q++) {
+            int64_t o = off + wi * W + q;
+            h->n_sym_err += berr[o] > 0;
+            h->n_near += nearf[o];
+        }
+        h->n_symbols += W;
+    }
+
+    /* ---- debug views ---------------------------------------------------- */
+    free(h->d_E); free(h->d_y); free(h->d_z); free(h->d_v); free(h->d_ahat);
+    free(h->d_draw); free(h->d_berr); free(h->d_near); free(h->d_win);
+    h->d_E = X.E; h->d_E_start = X.E_start; h->d_E_len = X.E_len > 0 ? X.E_len : 0;
+    h->d_y = X.y; h->d_y_start = X.y_start; h->d_y_len = X.y_len > 0 ? X.y_len : 0;
+    h->d_z = Z; h->d_v = Vv; h->d_ahat = ahat; h->d_draw = draw; h->d_berr = berr; h->d_near = nearf;
+    h->d_s_start = sym_lo; h->d_s_len = nproc;
+    h->d_win = dwin; h->d_win_len = nwin;
+    h->scal[0] = h->carrier.re; h->scal[1] = h->carrier.im; h->scal[2] = h->gain;
+    h->scal[3] = X.mu_pam; h->scal[4] = X.sd_pam;
+    free(msym);
+
+    /* ---- carry the stream state to the next buffer ----------------------- */
+    if (h->kk && e_k > 0) {
+        int64_t lo = (int64_t)h->dec * f_k - h->hmf;
+        if (lo < 0) lo = 0;
+        cx *nh = xcalloc((size_t)(e_k - lo + 1), sizeof(cx));
+        for (int64_t n = lo; n < e_k; n++) nh[n - lo] = e_at(&X, n);
+        free(h->ehist); h->ehist = nh; h->ehist_start = lo; h->ehist_len = e_k - lo;
+    }
+    {
+        int64_t lo = 2 * (h->trained ? q_k : 0) - h->th;
+        if (lo < 0) lo = 0;
+        if (lo > f_k) lo = f_k;
+        cx *nh = xcalloc((size_t)(f_k - lo + 1), sizeof(cx));
+        for (int64_t m = lo; m < f_k; m++) nh[m - lo] = y_at(&X, m);
+        free(h->yhist); h->yhist = nh; h->yhist_start = lo; h->yhist_len = f_k - lo;
+    }
+    {
+        int64_t keep = avail < h->chist_cap ? avail : h->chist_cap;
+        int32_t *nh = xcalloc((size_t)h->chist_cap, sizeof(int32_t));
+        for (int64_t i = 0; i < keep; i++) nh[i] = code_at(&X, avail - keep + i);
+        free(h->chist); h->chist = nh; h->chist_len = keep;
+    }
+    h->e_prev = e_k; h->f_prev = f_k; h->q_prev = q_k;
+    h->calls++;
+    h->n_samples += Nb;
+    free(cur);
+    return nbits;
+}
+
+int64_t orx_get(orx *h, int what, void *dst, int64_t cap, int64_t *start)
+{
+    int64_t n = 0, s = 0, width = 0;
+    const void *src = NULL;
+    switch (what) {
+    case ORX_E: n = h->d_E_len; s = h->d_E_start; src = h->d_E; width = sizeof(cx); break;
+    case ORX_Y: n = h->d_y_len; s = h->d_y_start; src = h->d_y; width = sizeof(cx); break;
+    case ORX_Z: n = h->d_s_len; s = h->d_s_start; src = h->d_z; width = sizeof(cx); break;
+    case ORX_V: n = h->d_s_len; s = h->d_s_start; src = h->d_v; width = sizeof(cx); break;
+    case ORX_AHAT: n = h->d_s_len; s = h->d_s_start; src = h->d_ahat; width = 2 * sizeof(int32_t); break;
+    case ORX_BERR: n = h->d_s_len; s = h->d_s_start; src = h->d_berr; width = sizeof(int32_t); break;
+    case ORX_WIN: n = h->d_win_len; s = 0; src = h->d_win; width = 4 * sizeof(double); break;
+    case ORX_TAPS: n = h->c.ntaps; s = 0; src = h->w; width = sizeof(cx); break;
+    case ORX_SCAL: n = 5; s = 0; src = h->scal; width = sizeof(double); break;
+    case ORX_NEAR: n = h->d_s_len; s = h->d_s_start; src = h->d_near; width = sizeof(int32_t); break;
+    case ORX_DRAW: n = h->d_s_len; s = h->d_s_start; src = h->d_draw; width = 2 * sizeof(int32_t); break;
+    default: return -1;
+    }
+    if (start) *start = s;
+    if (dst && src && cap > 0) memcpy(dst, src, (size_t)((n < cap ? n : cap) * width));
+    return n;
+}
+
+void orx_stats(orx *h, orx_stats_t *o)
+{
+    memset(o, 0, sizeof *o);
+    o->calls = h->calls; o->samples = h->n_samples; o->symbols = h->n_symbols;
+    o->bits = h->n_bits; o->bit_errors = h->n_bit_err; o->sym_errors = h->n_sym_err;
+    o->near_threshold = h->n_near; o->ambiguous_windows = h->n_amb; o->windows = h->n_win;
+    o->amb_rot = h->amb_r;
+    o->raw_bit_errors = h->n_raw_err; o->slip_windows = h->n_slip;
+    o->ber = h->n_bits ? (double)h->n_bit_err / (double)h->n_bits : 0.0;
+    o->q_db = orx_q_db(o->ber);
+}
+
+void orx_destroy(orx *h)
+{
+    if (!h) return;
+    free(h->rrc); free(h->prbs); free(h->chist); free(h->ehist); free(h->yhist); free(h->w);
+    free(h->d_E); free(h->d_y); free(h->d_z); free(h->d_v); free(h->d_ahat);
+    free(h->d_draw); free(h->d_berr); free(h->d_near); free(h->d_win);
+    free(h);
+}
