@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GPU receiver on the KK-16QAM workload.
+
+Workload: a Kramers-Kronig 16QAM stream at 1 GBaud sampled at 4 GS/s, 12-bit,
+buffers of 2^22 samples, RRC 0.1, CSPR 10 dB, 100 kHz linewidth, SNR 20 dB,
+overlap-save Hilbert FFT 2^16 / 4096, downshift 0.55 GHz, 31-tap CMA -> DD-LMS
+FIR at 2 samples/symbol, blind phase search 32 phases x 64 symbols, 16QAM Gray
+demap, bit-error count.  One step runs the whole chain over a batch of
+``--bufs-per-step`` consecutive buffers of one stream, drawn from a ring of
+``--ring`` distinct synthetic buffers resident in HBM (the ring is larger than
+L2).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle (the method's plain restatement) on
+the host cores, each step a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "KK-16QAM Rx GSa/s on 1 GB300 at oracle-matched BER; CNN-eq vs LMS BER & GSa/s"
+FMT, NB, FS, BAUD = 4, 1 << 22, 4e9, 1e9
+GEN = dict(snr_db=20.0, cspr_db=10.0, linewidth=100e3)
+STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
+# algorithmic FP32 operations per ADC sample of each stage (5 N log2 N per FFT;
+# the overlap-save factor N/(N-V) = 16/15 included)
+OLS = 65536 / (65536 - 4096)
+FLOPS_PER_SAMPLE = {"kk_fwd": 13.0 * OLS, "kk_rows": 60.0 * OLS, "kk_inv": 13.0 * OLS, "mf": 130.0,
+                    "eq": 252.0}
+BYTES_PER_SAMPLE = {"unpack": 1.5 + 2.0}   # packed read + 16-bit code write
+SMS, LANES = 152, 128
+
+
+def workload_config(args):
+    return {"workload": "KK-16QAM single stream, 2^22-sample 12-bit buffers (synthetic)",
+            "format": "KK-16QAM", "baud": BAUD, "fs": FS, "buf_len": NB, "ols_n": 65536, "ols_v": 4096,
+            "fir_taps": 31, "bps_phases": 32, "bps_window": 64, "cspr_db": 10, "snr_db": 20,
+            "linewidth_hz": 100e3, "bufs_per_step": args.bufs_per_step, "ring_buffers": args.ring,
+            "l2": "inputs larger than L2: ring of %d distinct packed buffers = %.0f MiB" % (
+                args.ring, args.ring * NB * 1.5 / 2 ** 20),
+            "seed": 1}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------- clock sampler
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        inside = [l for (t, l) in self.samples if self.t0 is not None and self.t0 <= t <= self.t1]
+        if not inside:   # fall back to the samples nearest the timed region
+            inside = [l for (t, l) in self.samples][-3:]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in inside:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference
+def reference_arm(args, rank):
+    """FP64 oracle on the host cores; each step one bounded sample buffer."""
+    import oracle
+    import synth
+    total = args.steps + args.warmup
+    nb = 1 << 22
+    while nb > 1 << 15 and total * nb / 0.6e6 > 150.0:   # keep the whole run within minutes
+        nb //= 2
+    g = synth.gen_kk_stream(FMT, nb, total, seed=1, truth=False,
+                            workers=min(16, os.cpu_count() or 1), **GEN)
+    o = oracle.Oracle(**oracle.default_cfg(FMT, nb))
+    for b in range(args.warmup):
+        o.process(g["packed"][b])
+    t = time.perf_counter()
+    for b in range(args.warmup, total):
+        o.process(g["packed"][b])
+    dt = time.perf_counter() - t
+    value = args.steps * nb / dt / 1e9
+    s = o.stats()
+    cfg = workload_config(args)
+    cfg.update(buf_len=nb, bufs_per_step=1, ring_buffers=total)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "GSa/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one {nb}-sample buffer of the KK-16QAM stream per step"},
+            "e2e": {"value": value, "unit": "GSa/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "ber": s["ber"]}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU arm
+def gpu_arm(args, rank, world, local):
+    import torch
+    import synth
+    import paper_2010_14333_gb300 as rx
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    t_gen = time.perf_counter()
+    g = synth.gen_kk_stream(FMT, NB, args.ring, seed=1 + rank, truth=False,
+                            workers=min(16, os.cpu_count() or 1), **GEN)
+    t_gen = time.perf_counter() - t_gen
+    ring = [torch.from_numpy(p).cuda() for p in g["packed"]]
+    r = rx.Receiver(FMT, NB)
+    stream = torch.cuda.current_stream()
+
+    def run_steps(rcv, n, profile=False):
+        nbits = 0
+        for _ in range(n):
+            for j in range(args.bufs_per_step):
+                _, k = rcv.process(ring[rcv.pos % args.ring])
+                rcv.pos += 1
+                nbits += k
+        return nbits
+
+    r.pos = 0
+    run_steps(r, args.warmup)
+    torch.cuda.synchronize()
+    rx.rx_profile(r.h, True)
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.t0 = time.time()
+    ev0.record(stream)
+    run_steps(r, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks.t1 = time.time()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, calls = rx.rx_profile_read(r.h)
+    rx.rx_profile(r.h, False)
+    time.sleep(0.1)
+    clocks.stop()
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    samples = args.steps * args.bufs_per_step * NB * world
+    value = samples / (ms * 1e-3) / 1e9
+    stats = r.stats()
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    host_ring = [torch.from_numpy(p).pin_memory() for p in g["packed"]]
+    h2 = rx.rx_create(FMT, BAUD, FS, NB, rx.rx_default_config(FMT))
+    out_host = torch.zeros(rx.rx_max_bits(h2) // 8 + 16, dtype=torch.uint8).pin_memory()
+    sid = stream.cuda_stream
+    pos = 0
+    e2e_steps = max(1, min(args.steps, 10))
+    h2d = d2h = 0
+    for i in range(args.warmup + e2e_steps):
+        if i == args.warmup:
+            barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h2d = d2h = 0
+        for j in range(args.bufs_per_step):
+            n = rx.rx_process_host(h2, host_ring[pos % args.ring].data_ptr(), out_host.data_ptr(), sid)
+            pos += 1
+            h2d += NB * 3 // 2
+            d2h += (n + 7) // 8
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    barrier()
+    if dist:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    rx.rx_destroy(h2)
+    e2e_value = e2e_steps * args.bufs_per_step * NB * world / (e2e_ms * 1e-3) / 1e9
+
+    # ---- per-stage times (CUDA events on the launching stream) and roofline
+    per_call = {s: stage_ms[s] / max(calls, 1) for s in STAGES}
+    tot = sum(per_call.values())
+    dom = max(per_call, key=per_call.get)
+    peaks = load_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = SMS * LANES * 2 * sm_max * 1e6 / 1e12        # FP32 TFLOP/s at the maximum SM clock
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    stages = {}
+    for s in STAGES:
+        t = per_call[s]
+        d = {"ms_per_call": t, "share": t / tot if tot else 0.0}
+        if s in FLOPS_PER_SAMPLE and t > 0:
+            d["tflops"] = FLOPS_PER_SAMPLE[s] * NB / (t * 1e-3) / 1e12
+            d["frac_alu"] = d["tflops"] / alu_peak
+        if s in BYTES_PER_SAMPLE and t > 0:
+            d["gbs"] = BYTES_PER_SAMPLE[s] * NB / (t * 1e-3) / 1e9
+            d["frac_hbm"] = d["gbs"] / hbm_peak
+        stages[s] = d
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if os.path.exists(tr_path):
+        traffic = json.load(open(tr_path)).get(dom)
+    if dom in FLOPS_PER_SAMPLE:
+        ach = stages[dom]["tflops"]
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": ach / alu_peak, "traffic": traffic,
+                "peak_source": "FP32: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured)" % sm_max}
+    else:
+        ach = stages[dom]["gbs"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": traffic, "peak_source": "hbm_gbs of measured"}
+
+    # ---- oracle on the host: CPU baseline and BER match on the same buffers
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        nref = 2
+        o = oracle.Oracle(**oracle.default_cfg(FMT, NB))
+        t = time.perf_counter()
+        for b in range(nref):
+            o.process(g["packed"][b])
+        dt = time.perf_counter() - t
+        so = o.stats()
+        chk = rx.Receiver(FMT, NB)
+        for b in range(nref):
+            chk.process(ring[b])
+        sg = chk.stats()
+        cpu = {"value": nref * NB / dt / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first {nref} buffers (2^22 samples each) of the same stream, single thread",
+               "ber_oracle": so["ber"], "ber_gpu_same_buffers": sg["ber"],
+               "bit_errors_oracle": so["bit_errors"], "bit_errors_gpu": sg["bit_errors"], "bits": so["bits"]}
+
+    clk = clocks.summary()
+    launches_per_call = 7
+    line = {"metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args),
+            "e2e": {"value": e2e_value, "unit": "GSa/s", "h2d_bytes_per_step": h2d // e2e_steps,
+                    "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
+            "roofline": roof, "stages": stages, "cpu_baseline": cpu,
+            "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
+            "realtime_x": value / 4.0,
+            "ber": stats["ber"], "q_db": stats["q_db"], "bits": stats["bits"],
+            "device_error": stats["device_error"], "gen_s": t_gen}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--bufs-per-step", type=int, default=64)
+    ap.add_argument("--ring", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args, rank)
+        return
+    gpu_arm(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * rx.h -- C ABI of the GPU receiver library (librx.so).
+ *
+ * The library implements the per-buffer receiver DSP of "Real-time,
+ * Software-Defined, GPU-Based Receiver Field Trial" (arXiv 2010.14333), Sec. 2:
+ * a continuous stream of 12-bit ADC buffers comes in, the binary data of the
+ * recovered symbols goes out, and signal continuity is kept from one buffer to
+ * the next (the overlap-save continuity the paper carries between processing
+ * streams).  Two chains:
+ *   - Kramers-Kronig coherent QPSK/16QAM: 12-bit unpack, square root and
+ *     logarithm of the intensity, Hilbert transform by overlap-save FFT,
+ *     field = sqrt(I) exp(j phase), frequency downshift, matched filter with
+ *     4 -> 2 samples/symbol, adaptive FIR (CMA then decision-directed LMS),
+ *     blind phase search, decision, Gray demap, bit-error count (Sec. 2, KK
+ *     chain; Fig. 1c, 1d);
+ *   - direct-detection PAM-2/4/8: unpack, DC removal and scaling, matched
+ *     filter, LMS feed-forward equaliser (data-aided training then decision
+ *     directed), decision, Gray demap, bit-error count (Sec. 2, PAM chain).
+ * Every step runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions
+ *   - Every call returns an rx_status; nothing is thrown and nothing aborts.
+ *   - The caller owns the input and output buffers and the CUDA stream; the
+ *     library owns its device workspace and the stream state (allocated in
+ *     rx_create on the device current at that time, released in rx_destroy).
+ *   - rx_process only enqueues work on the given stream and never waits for
+ *     the GPU.  Arguments are checked before anything is enqueued; errors found
+ *     on the device (a bounded wait that ran out) are latched and reported by
+ *     rx_stats in rx_stats_t.device_error.
+ *   - One handle serves one stream of buffers; calls on one handle must be
+ *     issued in stream order from one host thread.
+ */
+#ifndef RX_H
+#define RX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rx_handle rx_handle;
+
+typedef enum { RX_PAM2 = 0, RX_PAM4 = 1, RX_PAM8 = 2, RX_KK_QPSK = 3, RX_KK_16QAM = 4 } rx_format;
+
+typedef enum {
+    RX_OK = 0,
+    RX_EINVAL = 1,    /* bad argument or configuration                            */
+    RX_ENOMEM = 2,    /* device or host allocation failed                         */
+    RX_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed             */
+    RX_ESTATE = 4,    /* handle in an unusable state (after an earlier failure)   */
+    RX_ETIMEOUT = 5,  /* a bounded device-side wait ran out (reported by stats)   */
+    RX_EBOUNDS = 6    /* output capacity too small                                */
+} rx_status;
+
+/* Receiver configuration.  rx_default_config fills every field with the
+ * defaults of the format; callers then change what they need. */
+typedef struct {
+    int32_t pack_order;  /* ADC word: 0 = little-endian 24-bit word (s0 = b0 | (b1&15)<<8,
+                            s1 = b1>>4 | b2<<4), 1 = big-endian nibbles                    */
+    int32_t ols_n;       /* KK overlap-save FFT length: 256, 4096 or 65536                 */
+    int32_t ols_v;       /* KK overlap, even, < ols_n; each block keeps ols_n - ols_v
+                            outputs with ols_v/2 samples of margin on both sides          */
+    int32_t ds_num;      /* KK downshift = ds_num / ds_den cycles per ADC sample (exact
+                            integer phase); default 11/80 = 0.55 GHz at 4 GS/s             */
+    int32_t ds_den;
+    double  rrc_beta;    /* matched-filter root-raised-cosine roll-off                     */
+    int32_t mf_span;     /* matched-filter span in symbols (even)                          */
+    int32_t ntaps;       /* adaptive FIR taps at 2 samples/symbol, odd, <= 31               */
+    int32_t ntrain;      /* training symbols at stream start, multiple of win              */
+    int32_t ncma;        /* KK: leading training symbols adapted by CMA, multiple of win   */
+    int32_t eq_block;    /* symbols per independently adapted block, multiple of win       */
+    int32_t win;         /* symbols per LMS update / blind-phase-search window: 64         */
+    double  mu;          /* decision-directed LMS step                                     */
+    double  mu_train;    /* PAM data-aided training step                                   */
+    double  mu_cma;      /* KK CMA step                                                    */
+    int32_t bps_b;       /* KK blind-phase-search test phases, 1..32                       */
+    int32_t amb_syms;    /* KK payload symbols that resolve the pi/2 ambiguity at stream
+                            start (multiple of win); they are not counted in the BER       */
+    uint32_t prbs_seed;  /* PRBS-15 seed of the transmitted bits (BER reference)           */
+    int32_t debug;       /* 1: keep soft symbols and window metrics for rx_debug_copy      */
+} rx_config;
+
+typedef struct {
+    int64_t calls;             /* rx_process calls                                       */
+    int64_t samples;           /* ADC samples consumed                                    */
+    int64_t symbols;           /* payload symbols scored                                  */
+    int64_t bits;              /* payload bits scored                                     */
+    int64_t bit_errors;        /* bit errors, each window scored under its best pi/2
+                                  rotation (BER-tester re-synchronisation after a slip)  */
+    int64_t raw_bit_errors;    /* bit errors of the decoded output with no re-sync       */
+    int64_t sym_errors;        /* symbols with at least one bit error                    */
+    int64_t slip_windows;      /* windows scored under a rotation other than the decoded  */
+    int64_t near_threshold;    /* scored symbols whose soft value lies within 1e-4 of a
+                                  decision threshold (level units)                        */
+    int64_t ambiguous_windows; /* phase-search windows whose two best metrics differ by
+                                  at most 1e-6 relative                                   */
+    int64_t windows;           /* payload windows processed                               */
+    int32_t amb_rot;           /* resolved stream-start pi/2 rotation, -1 before          */
+    int32_t device_error;      /* 0, or RX_ETIMEOUT if a device-side wait ran out         */
+    double  ber;               /* bit_errors / bits                                       */
+    double  q_db;              /* 20 log10(sqrt(2) erfcinv(2 BER)), Sec. 3 Q-factor       */
+} rx_stats_t;
+
+/* Debug selectors for rx_debug_copy (each refers to the last rx_process call). */
+enum {
+    RX_DBG_FIELD = 1,    /* KK field E[n] before carrier removal, float2 per ADC sample     */
+    RX_DBG_MF = 2,       /* matched-filter output at 2 samples/symbol: float2 (KK), float
+                            (PAM)                                                           */
+    RX_DBG_SOFT = 3,     /* equaliser output z_k per processed symbol, float2 (debug=1)      */
+    RX_DBG_DEC = 4,      /* decision byte per payload symbol: bits 0-2 I level index,
+                            bits 3-5 Q level index (before the pi/2 rotation), bit 6 near   */
+    RX_DBG_WIN = 5,      /* per payload window: float4 (b*, m, best metric, second metric);
+                            the metrics need debug=1                                         */
+    RX_DBG_TAPS = 6,     /* start taps of the next call, float2 per tap                      */
+    RX_DBG_SCAL = 7,     /* double[5]: carrier re, carrier im, gain, PAM mean, PAM 1/std     */
+    RX_DBG_CODES = 8     /* uint16 12-bit code per ADC sample of the last buffer             */
+};
+
+/* Defaults of a format (the workload settings of the synthetic configurations). */
+rx_status rx_default_config(rx_format format, rx_config *out);
+
+/* Create a receiver for one stream of buffers of buf_len ADC samples taken at
+ * fs samples/s of a signal at baud symbols/s.  fs/baud must be 2 (PAM) or 4
+ * (KK).  buf_len must be a positive multiple of 32.  cfg may be NULL (defaults).
+ * Allocates all device memory up front (cudaMalloc on the current device) and
+ * builds the constant tables; no kernel runs.  On success *out owns the handle. */
+rx_status rx_create(rx_format format, double baud, double fs, int64_t buf_len,
+                    const rx_config *cfg, rx_handle **out);
+
+/* Process the next buffer of the stream.
+ *   packed12_in: DEVICE pointer, buf_len*3/2 bytes, 16-byte aligned, packed 12-bit
+ *                samples (two per three bytes, cfg.pack_order).
+ *   bits_out:    DEVICE pointer with room for rx_max_bits(h)/8 bytes; receives the
+ *                payload bits decided in this call, MSB first within each symbol and
+ *                packed MSB first into bytes.
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream).
+ *   nbits_out:   HOST pointer, receives the number of bits written.  The count is
+ *                computed on the host from the stream position; no synchronisation.
+ * Every stage emits what its full filter support allows, so outputs lag the input
+ * by a fixed latency; symbols are emitted in whole equaliser blocks. */
+rx_status rx_process(rx_handle *h, const uint8_t *packed12_in, uint8_t *bits_out,
+                     void *cuda_stream, int64_t *nbits_out);
+
+/* Same as rx_process with HOST buffers: copies the input host->device, runs the
+ * chain and copies the bits device->host, all enqueued on cuda_stream.  For
+ * asynchronous copies the host buffers must be page-locked.  Returns after
+ * enqueuing; the bits are valid once the stream has reached this point. */
+rx_status rx_process_host(rx_handle *h, const uint8_t *host_in, uint8_t *host_bits_out,
+                          void *cuda_stream, int64_t *nbits_out);
+
+/* Upper bound of the bits one rx_process call can emit. */
+int64_t rx_max_bits(const rx_handle *h);
+
+/* Synchronises cuda_stream, then copies the accumulated counters. */
+rx_status rx_stats(rx_handle *h, rx_stats_t *out, void *cuda_stream);
+
+/* Copies an intermediate of the last call to HOST memory dst (capacity cap
+ * elements of the selector's type) after synchronising cuda_stream.  *count
+ * receives the number of elements available and *start the stream index of the
+ * first one (ADC sample, 2-sps sample, symbol or window, as the selector says). */
+rx_status rx_debug_copy(rx_handle *h, int what, void *dst, int64_t cap, int64_t *count,
+                        int64_t *start, void *cuda_stream);
+
+/* Replace the taps the next call starts from (HOST arrays of n <= ntaps values;
+ * im may be NULL for PAM).  Synchronous. */
+rx_status rx_set_taps(rx_handle *h, const double *re, const double *im, int n);
+
+/* Stage timing.  rx_profile(h, 1) makes every later rx_process record CUDA
+ * events on the caller's stream at the stage boundaries (unpack, K1a forward
+ * radix-16, K1b row FFTs, K1c field assembly, matched filter, equaliser,
+ * demap); rx_profile(h, 0) stops.  rx_profile_read waits for the recorded
+ * calls, writes the summed milliseconds of each stage to ms[0..n-1] (n <= 7,
+ * in the order above; a stage a format lacks reads 0) and the number of calls
+ * measured to *calls, and clears the record. */
+rx_status rx_profile(rx_handle *h, int enable);
+rx_status rx_profile_read(rx_handle *h, double *ms, int n, int64_t *calls);
+
+/* Releases the device memory and the handle.  NULL is ignored. */
+void rx_destroy(rx_handle *h);
+
+/* Static description of a status code. */
+const char *rx_strerror(rx_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RX_H */

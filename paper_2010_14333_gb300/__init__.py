@@ -1,0 +1,219 @@
+"""Python binding of the GPU receiver library librx.so (include/rx.h).
+
+Argument marshalling only: every step of the receiver runs in the library's
+CUDA kernels.  The names follow the C ABI.  PyTorch is used only to hold device
+memory and to hand over the current CUDA stream.  There is no fallback: if
+librx.so is missing or cannot be loaded, every entry point raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librx.so")
+
+RX_PAM2, RX_PAM4, RX_PAM8, RX_KK_QPSK, RX_KK_16QAM = range(5)
+RX_DBG_FIELD, RX_DBG_MF, RX_DBG_SOFT, RX_DBG_DEC, RX_DBG_WIN, RX_DBG_TAPS, RX_DBG_SCAL, RX_DBG_CODES = range(1, 9)
+BITS_PER_SYMBOL = {0: 1, 1: 2, 2: 3, 3: 2, 4: 4}
+
+
+class RxConfig(C.Structure):
+    _fields_ = [
+        ("pack_order", C.c_int32), ("ols_n", C.c_int32), ("ols_v", C.c_int32),
+        ("ds_num", C.c_int32), ("ds_den", C.c_int32), ("rrc_beta", C.c_double),
+        ("mf_span", C.c_int32), ("ntaps", C.c_int32), ("ntrain", C.c_int32),
+        ("ncma", C.c_int32), ("eq_block", C.c_int32), ("win", C.c_int32),
+        ("mu", C.c_double), ("mu_train", C.c_double), ("mu_cma", C.c_double),
+        ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
+        ("debug", C.c_int32),
+    ]
+
+
+class RxStats(C.Structure):
+    _fields_ = [
+        ("calls", C.c_int64), ("samples", C.c_int64), ("symbols", C.c_int64),
+        ("bits", C.c_int64), ("bit_errors", C.c_int64), ("raw_bit_errors", C.c_int64),
+        ("sym_errors", C.c_int64), ("slip_windows", C.c_int64), ("near_threshold", C.c_int64),
+        ("ambiguous_windows", C.c_int64), ("windows", C.c_int64), ("amb_rot", C.c_int32),
+        ("device_error", C.c_int32), ("ber", C.c_double), ("q_db", C.c_double),
+    ]
+
+
+class RxError(RuntimeError):
+    pass
+
+
+EXPORTED = sorted(["rx_default_config", "rx_create", "rx_process", "rx_process_host", "rx_max_bits",
+                   "rx_stats", "rx_debug_copy", "rx_set_taps", "rx_destroy", "rx_strerror",
+                   "rx_profile", "rx_profile_read"])
+STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librx.so (built by __graft_entry__.build()); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RxError(f"{path} is missing: build it with __graft_entry__.build() (no CPU fallback exists)")
+    L = C.CDLL(path)
+    vp, i64, P = C.c_void_p, C.c_int64, C.POINTER
+    L.rx_default_config.argtypes = [C.c_int, P(RxConfig)]
+    L.rx_create.argtypes = [C.c_int, C.c_double, C.c_double, i64, P(RxConfig), P(vp)]
+    L.rx_process.argtypes = [vp, vp, vp, vp, P(i64)]
+    L.rx_process_host.argtypes = [vp, vp, vp, vp, P(i64)]
+    L.rx_max_bits.argtypes = [vp]
+    L.rx_max_bits.restype = i64
+    L.rx_stats.argtypes = [vp, P(RxStats), vp]
+    L.rx_debug_copy.argtypes = [vp, C.c_int, vp, i64, P(i64), P(i64), vp]
+    L.rx_set_taps.argtypes = [vp, vp, vp, C.c_int]
+    L.rx_destroy.argtypes = [vp]
+    L.rx_destroy.restype = None
+    L.rx_profile.argtypes = [vp, C.c_int]
+    L.rx_profile_read.argtypes = [vp, P(C.c_double), C.c_int, P(i64)]
+    L.rx_strerror.argtypes = [C.c_int]
+    L.rx_strerror.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("rx_max_bits", "rx_destroy", "rx_strerror"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise RxError(f"rx status {status}: {rx_strerror(status)}")
+
+
+# ------------------------------------------------------------- C ABI, 1:1
+def rx_strerror(status: int) -> str:
+    return load().rx_strerror(status).decode()
+
+
+def rx_default_config(fmt: int) -> RxConfig:
+    c = RxConfig()
+    _check(load().rx_default_config(fmt, C.byref(c)))
+    return c
+
+
+def rx_create(fmt: int, baud: float, fs: float, buf_len: int, cfg: RxConfig | None = None) -> int:
+    h = C.c_void_p()
+    _check(load().rx_create(fmt, baud, fs, buf_len, C.byref(cfg) if cfg is not None else None, C.byref(h)))
+    return h.value
+
+
+def rx_process(h: int, packed12_in: int, bits_out: int, stream: int = 0) -> int:
+    n = C.c_int64()
+    _check(load().rx_process(h, packed12_in, bits_out, stream, C.byref(n)))
+    return n.value
+
+
+def rx_process_host(h: int, host_in: int, host_bits_out: int, stream: int = 0) -> int:
+    n = C.c_int64()
+    _check(load().rx_process_host(h, host_in, host_bits_out, stream, C.byref(n)))
+    return n.value
+
+
+def rx_max_bits(h: int) -> int:
+    return load().rx_max_bits(h)
+
+
+def rx_stats(h: int, stream: int = 0) -> dict:
+    s = RxStats()
+    _check(load().rx_stats(h, C.byref(s), stream))
+    return {k: getattr(s, k) for k, _ in RxStats._fields_}
+
+
+def rx_debug_copy(h: int, what: int, dst: int, cap: int, stream: int = 0):
+    n, s = C.c_int64(), C.c_int64()
+    _check(load().rx_debug_copy(h, what, dst, cap, C.byref(n), C.byref(s), stream))
+    return n.value, s.value
+
+
+def rx_set_taps(h: int, re, im=None):
+    re = np.ascontiguousarray(re, dtype=np.float64)
+    imv = None if im is None else np.ascontiguousarray(im, dtype=np.float64)
+    _check(load().rx_set_taps(h, re.ctypes.data, None if imv is None else imv.ctypes.data, len(re)))
+
+
+def rx_profile(h: int, enable: bool):
+    _check(load().rx_profile(h, int(bool(enable))))
+
+
+def rx_profile_read(h: int) -> tuple[dict, int]:
+    ms = (C.c_double * len(STAGES))()
+    n = C.c_int64()
+    _check(load().rx_profile_read(h, ms, len(STAGES), C.byref(n)))
+    return {s: ms[i] for i, s in enumerate(STAGES)}, n.value
+
+
+def rx_destroy(h: int):
+    if h:
+        load().rx_destroy(h)
+
+
+# ------------------------------------------------------------- convenience
+class Receiver:
+    """One stream of ADC buffers on the current CUDA device.
+
+    ``process`` takes a uint8 CUDA tensor of buf_len*3/2 packed bytes and
+    returns (bits tensor on the device, number of bits).  The work is enqueued
+    on torch's current stream; nothing waits for the GPU.
+    """
+
+    def __init__(self, fmt: int, buf_len: int, baud: float | None = None, fs: float = 4e9, **cfg):
+        import torch
+        self.torch = torch
+        load()
+        self.fmt = fmt
+        self.buf_len = buf_len
+        baud = baud if baud is not None else (fs / 4 if fmt >= 3 else fs / 2)
+        c = rx_default_config(fmt)
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        self.cfg = c
+        self.h = rx_create(fmt, baud, fs, buf_len, c)
+        self.max_bits = rx_max_bits(self.h)
+        self.bits = torch.zeros((self.max_bits + 7) // 8 + 16, dtype=torch.uint8, device="cuda")
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            rx_destroy(h)
+            self.h = None
+
+    def stream(self) -> int:
+        return self.torch.cuda.current_stream().cuda_stream
+
+    def process(self, packed):
+        assert packed.is_cuda and packed.dtype == self.torch.uint8
+        n = rx_process(self.h, packed.data_ptr(), self.bits.data_ptr(), self.stream())
+        return self.bits[: (n + 7) // 8], n
+
+    def stats(self) -> dict:
+        return rx_stats(self.h, self.stream())
+
+    def set_taps(self, taps):
+        taps = np.asarray(taps, dtype=np.complex128)
+        rx_set_taps(self.h, taps.real, taps.imag)
+
+    _DT = {RX_DBG_FIELD: (np.complex64, 1), RX_DBG_SOFT: (np.complex64, 1), RX_DBG_DEC: (np.uint8, 1),
+           RX_DBG_WIN: (np.float32, 4), RX_DBG_TAPS: (np.complex64, 1), RX_DBG_SCAL: (np.float64, 1),
+           RX_DBG_CODES: (np.uint16, 1)}
+
+    def debug(self, what: int):
+        n, s = rx_debug_copy(self.h, what, None, 0, self.stream())
+        if what == RX_DBG_MF:
+            dt, w = (np.complex64, 1) if self.fmt >= 3 else (np.float32, 1)
+        else:
+            dt, w = self._DT[what]
+        out = np.zeros(max(n, 0) * w, dtype=dt)
+        if n > 0:
+            rx_debug_copy(self.h, what, out.ctypes.data, n, self.stream())
+        return (out.reshape(-1, w) if w > 1 else out), s

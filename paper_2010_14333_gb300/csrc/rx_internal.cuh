@@ -1,0 +1,101 @@
+// Internal declarations shared by the receiver's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rx.h"
+
+namespace rxk {
+
+// ------------------------------------------------------------------ constants
+constexpr int kWin = 64;          // symbols per window (one warp: two per lane)
+constexpr int kMaxTaps = 31;      // adaptive FIR taps, one per lane
+constexpr int kYHist = 16;        // 2-sps samples of equaliser history before a block
+constexpr int kEHist = 64;        // ADC samples of field history kept for the MF
+constexpr int kPamHist = 64;      // codes kept before a PAM buffer (>= 2 * MF half length)
+constexpr int kCtaK1 = 256;       // threads per K1a / K1c CTA
+constexpr int kEqWarps = 4;       // warps (equaliser blocks) per K3 CTA
+constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before flagging RX_ETIMEOUT
+
+// counters in DevState::cnt
+enum { C_SYMBOLS, C_BITS, C_BITERR, C_RAWERR, C_SYMERR, C_SLIP, C_NEAR, C_AMBIG, C_WINDOWS, C_NCNT };
+
+// device-resident state of one stream
+struct DevState {
+    unsigned long long cnt[C_NCNT];
+    double carrier_re, carrier_im, gain;   // KK: this call's carrier and gain
+    double pam_mu, pam_inv_sd;             // PAM: this call's normalisation (debug view)
+    long long pam_s1[2], pam_s2[2];        // PAM: integer sums of codes / codes^2, by call parity
+    int unwrap_have[2], unwrap_b[2];       // pi/2 unwrap carry, by parity
+    long long unwrap_m[2];
+    int amb_r;                             // stream-start rotation, -1 before
+    unsigned int ticket;                   // last-CTA ticket of the carrier reduction
+    int err;                               // RX_ETIMEOUT when a bounded wait ran out
+};
+
+// per-CTA partial of the carrier reduction
+struct CarrierPartial {
+    double re, im;
+    long long i2;   // sum over kept outputs of 2*I (I = code, 0.5 for code 0), exact
+    long long pad;
+};
+
+// per-call geometry of the KK overlap-save blocks
+struct KkGeom {
+    long long e_prev, e_k;     // KK outputs emitted: [e_prev, e_k)
+    long long avail;           // stream samples seen after this buffer
+    long long cbase;           // stream index of codes[0]
+    long long ebase;           // stream index of field workspace [0] (= e_prev - kEHist)
+    long long ebase_prev;      // same for the previous field workspace
+    int N, V, hop, J, npairs, N2;
+    int sps;
+};
+
+// per-call schedule of the equaliser
+struct EqGeom {
+    long long sym_lo;          // first symbol processed (0 on the training call)
+    long long pay_lo;          // first payload symbol
+    long long q_k;             // symbols processed up to (exclusive)
+    long long ybase;           // stream index (2-sps) of Y workspace [0]
+    int nblk;                  // payload blocks in this call
+    int nwin;                  // payload windows in this call
+};
+
+struct EqParams {
+    int kk, mq, bps, ntaps, th, win, eq_block, ntrain, ncma, bps_b, amb_syms;
+    float scale, r2, mu, mu_train, mu_cma;
+};
+
+// ------------------------------------------------------------------ launchers
+// (each returns cudaGetLastError() after enqueuing)
+cudaError_t launch_unpack(const uint8_t *in, uint16_t *codes, const uint16_t *codes_prev,
+                          long long nb, int nhist, long long prev_off, int first_call,
+                          int pack_order, long long *s1, long long *s2, cudaStream_t st);
+
+cudaError_t launch_kk_front(const KkGeom &g, const uint16_t *codes, float2 *fftws,
+                            const float2 *twN, const float2 *twN2, float2 *E, const float2 *E_prev,
+                            CarrierPartial *partials, DevState *dst, cudaStream_t st, void *prof);
+// stage-boundary hook of the profiler (defined with the C ABI; prof may be null)
+void prof_stage(void *prof, int stage, cudaStream_t st);
+
+cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long long f_prev,
+                         long long f_k, const float *rrc, int hmf, const float2 *ds_tab,
+                         int ds_num, int ds_den, const DevState *dst, float2 *Y, long long ybase,
+                         const float2 *Y_prev, long long ybase_prev, cudaStream_t st);
+
+cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, long long n_end, long long f_prev,
+                          long long f_k, const float *rrc, int hmf, DevState *dst, int parity,
+                          float *Y, long long ybase, const float *Y_prev, long long ybase_prev,
+                          cudaStream_t st);
+
+cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void *Y,
+                      float2 *taps_in, float2 *taps_out, uint8_t *dec, uint8_t *winb,
+                      float4 *dbg_win, float2 *dbg_z, const uint8_t *prbs, DevState *dst,
+                      cudaStream_t st);
+
+cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in,
+                         const uint8_t *dec, const uint8_t *winb, float4 *dbg_win,
+                         const uint8_t *prbs, uint8_t *bits_out, DevState *dst, cudaStream_t st);
+
+}  // namespace rxk

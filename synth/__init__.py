@@ -140,26 +140,31 @@ def pack12(codes: np.ndarray, order: int = 0) -> np.ndarray:
 
 # ------------------------------------------------------------------- helpers
 def _shape(sym: np.ndarray, pulse: np.ndarray, sps: int, n0: int, n1: int) -> np.ndarray:
-    """Samples [n0, n1) of sum_k sym[k] * pulse[n - sps*k + half]."""
+    """Samples [n0, n1) of sum_k sym[k] * pulse[n - sps*k + half] (polyphase: for
+    n = sps*m + p, s[n] = sum_j sym[m - j] * pulse[sps*j + p + half])."""
     half = (len(pulse) - 1) // 2
-    k0 = max(0, -((-(n0 - half)) // sps))
-    k1 = min(len(sym), (n1 - 1 + half) // sps + 1)
     out_len = n1 - n0
-    if k1 <= k0:
-        return np.zeros(out_len, dtype=sym.dtype)
-    up = np.zeros((k1 - k0) * sps, dtype=sym.dtype)
-    up[::sps] = sym[k0:k1]
-    if _conv is not None and len(up) > 4096:
-        full = _conv(up, pulse)
-    else:
-        full = np.convolve(up, pulse)
-    # full[j] = sum_i up[i] pulse[j-i]; sample n = sps*k0 + j - half
-    start = n0 - (sps * k0 - half)
-    res = np.zeros(out_len, dtype=full.dtype)
-    lo = max(0, -start)
-    hi = min(out_len, len(full) - start)
-    if hi > lo:
-        res[lo:hi] = full[start + lo:start + hi]
+    res = np.zeros(out_len, dtype=np.result_type(sym.dtype, pulse.dtype))
+    m0 = n0 // sps - 1
+    m1 = (n1 - 1) // sps + 1
+    for p in range(sps):
+        js = [j for j in range(-(half + p) // sps - 1, (half - p) // sps + 2)
+              if 0 <= sps * j + p + half <= 2 * half]
+        jlo, jhi = js[0], js[-1]
+        taps = np.array([pulse[sps * j + p + half] for j in range(jlo, jhi + 1)])
+        # symbols needed for outputs m in [m0, m1]: k = m - j in [m0 - jhi, m1 - jlo]
+        k0, k1 = m0 - jhi, m1 - jlo
+        seg = np.zeros(k1 - k0 + 1, dtype=sym.dtype)
+        a, b = max(k0, 0), min(k1, len(sym) - 1)
+        if b >= a:
+            seg[a - k0:b - k0 + 1] = sym[a:b + 1]
+        full = np.convolve(seg, taps)           # full[i] = sum_t seg[i - t] taps[t]
+        # output m uses seg index (m - jlo) - k0 ... full index i = (m - jlo - k0) + 0
+        ms = np.arange(m0, m1 + 1)
+        vals = full[ms - jlo - k0 + 0]
+        n = ms * sps + p
+        sel = (n >= n0) & (n < n1)
+        res[n[sel] - n0] = vals[sel]
     return res
 
 
@@ -214,70 +219,142 @@ def gen_pam_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: fl
                 buf_len=buf_len)
 
 
+def _tx_symbols(fmt: int, prbs_seed: int, k0: int, k1: int, period_cache={}) -> np.ndarray:
+    """Transmitted symbols k in [k0, k1) of the PRBS-15 stream (k < 0 gives 0)."""
+    name, bps, kind = FORMATS[fmt]
+    key = (prbs_seed,)
+    if key not in period_cache:
+        period_cache[key] = prbs15_bits(prbs_seed, 32767)
+    per = period_cache[key]
+    ks = np.arange(max(k0, 0), max(k1, 0), dtype=np.int64)
+    out = np.zeros(k1 - k0, dtype=np.float64 if kind == "pam" else np.complex128)
+    if len(ks):
+        idx = (ks[:, None] * bps + np.arange(bps)[None, :]) % 32767
+        out[max(k0, 0) - k0:] = tx_levels(fmt, per[idx].reshape(-1))
+    return out
+
+
+def kk_phase_starts(buf_len: int, nbufs: int, seed: int, linewidth: float, fs: float,
+                    phase_noise: bool = True, phase_offset: float = 0.0):
+    """Wiener phase at the first sample of each buffer (the increments of buffer
+    b come from their own generator, so buffers can be made independently)."""
+    pn_std = np.sqrt(2.0 * np.pi * linewidth / fs)
+    th, out = float(phase_offset), []
+    for b in range(nbufs):
+        out.append(th)
+        if phase_noise and linewidth > 0:
+            inc = np.random.default_rng([int(seed), b, 31]).standard_normal(buf_len) * pn_std
+            th += float(np.sum(inc))
+    return out
+
+
+def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_db: float = 20.0,
+              cspr_db: float = 10.0, linewidth: float = 100e3, fs: float = 4e9, sps: int = 4,
+              beta: float = 0.1, span: int = 16, fd_num: int = 11, fd_den: int = 80,
+              noise: bool = True, phase_noise: bool = True, volterra=(0.0, 0.0),
+              prbs_seed: int = 1, pack_order: int = 0, symbols=None, phase_steps=(),
+              truth: bool = True):
+    """Buffer b of a Kramers-Kronig single-sideband QAM stream (see gen_kk_stream)."""
+    name, bps, kind = FORMATS[fmt]
+    assert kind == "qam"
+    n0, n1 = b * buf_len, (b + 1) * buf_len
+    pulse = rrc_pulse(beta, sps, span)
+    half = span // 2 + 2
+    ka, kb = (n0 - sps) // sps - half, n1 // sps + half + 1
+    if symbols is None:
+        a_seg = _tx_symbols(fmt, prbs_seed, ka, kb)
+        Es = 1.0   # unit-power constellation
+    else:
+        sy = np.asarray(symbols, dtype=np.complex128)
+        a_seg = np.zeros(kb - ka, dtype=np.complex128)
+        lo, hi = max(ka, 0), min(kb, len(sy))
+        if hi > lo:
+            a_seg[lo - ka:hi - ka] = sy[lo:hi]
+        Es = float(np.mean(np.abs(sy) ** 2))
+    Ps = Es / sps                      # per-sample power of the shaped signal
+    A = np.sqrt(10.0 ** (cspr_db / 10.0) * Ps)
+    sig2 = Ps * sps / 10.0 ** (snr_db / 10.0)
+    pn_std = np.sqrt(2.0 * np.pi * linewidth / fs)
+    # shaped baseband for samples [n0 - sps, n1): symbols re-indexed from ka
+    s = _shape(a_seg, pulse, sps, n0 - sps - ka * sps, n1 - ka * sps)
+    c1, c2 = volterra
+    if c1 != 0.0 or c2 != 0.0:
+        p = np.abs(s) ** 2
+        nl = c1 * s * p
+        nl[sps:] += c2 * s[:-sps] * p[:-sps]
+        s = s + nl
+    s = s[sps:]
+    n = np.arange(n0, n1, dtype=np.int64)
+    up = np.exp(2j * np.pi * np.arange(fd_den) / fd_den)[(n * fd_num) % fd_den]
+    if phase_noise and linewidth > 0:
+        inc = np.random.default_rng([int(seed), b, 31]).standard_normal(buf_len) * pn_std
+        th = theta0 + np.cumsum(inc)
+    else:
+        th = np.full(buf_len, theta0)
+    for (ns, dth) in phase_steps:
+        if ns < n1:
+            th[max(0, ns - n0):] += dth
+    E = A + s * up * np.exp(1j * th)
+    if noise:
+        rng = np.random.default_rng([int(seed), b, 29])
+        E = E + (rng.standard_normal(buf_len) + 1j * rng.standard_normal(buf_len)) * np.sqrt(sig2 / 2.0)
+    codes, clips = _quantise(np.abs(E) ** 2)
+    out = dict(packed=pack12(codes, pack_order), clips=clips, tone=A, Ps=Ps)
+    if truth:
+        out.update(codes=codes, field=s)
+    return out
+
+
+def _kk_worker(args):
+    kw, b, th0 = args
+    return kk_buffer(b=b, theta0=th0, **kw)
+
+
 def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: float = 20.0,
                   cspr_db: float = 10.0, linewidth: float = 100e3, fs: float = 4e9,
                   sps: int = 4, beta: float = 0.1, span: int = 16, fd_num: int = 11,
                   fd_den: int = 80, noise: bool = True, phase_noise: bool = True,
                   volterra=(0.0, 0.0), prbs_seed: int = 1, pack_order: int = 0,
-                  symbols=None, phase_offset: float = 0.0, phase_steps=()):
+                  symbols=None, phase_offset: float = 0.0, phase_steps=(), workers: int = 1,
+                  truth: bool = True):
     """Kramers-Kronig single-sideband QAM stream split into ADC buffers.
 
     The signal sits above a real tone at 0 Hz after an up-shift of fd_num/fd_den
     cycles per sample.  ``volterra`` = (c1, c2) adds c1*x|x|^2 + c2*x[n-sps]|x[n-sps]|^2
     to the shaped baseband before the shift.  ``symbols`` overrides the PRBS
     symbols (used for training data that must not follow an LFSR recurrence).
-    Returns dict with 'packed', 'codes', 'bits', 'symbols', 'field' (noiseless
-    complex baseband at sps, before the shift: what the receiver should recover)
-    and 'clips'.
+    ``phase_steps`` = [(sample, dtheta), ...] adds instantaneous phase jumps.
+    ``workers`` > 1 makes the buffers in a spawn-started process pool.
+    Returns dict with 'packed' (per buffer), 'codes', 'symbols' (the transmitted
+    symbols of the stream), 'field' (noiseless complex baseband at sps, before the
+    shift: what the receiver should recover; with truth=True) and 'clips'.
     """
     name, bps, kind = FORMATS[fmt]
     assert kind == "qam"
-    total = buf_len * nbufs
-    nsym = total // sps + span + 8
-    if symbols is None:
-        bits = prbs15_bits(prbs_seed, nsym * bps)
-        a = tx_levels(fmt, bits)
+    nsym = buf_len * nbufs // sps + span + 8
+    kw = dict(fmt=fmt, buf_len=buf_len, seed=seed, snr_db=snr_db, cspr_db=cspr_db,
+              linewidth=linewidth, fs=fs, sps=sps, beta=beta, span=span, fd_num=fd_num,
+              fd_den=fd_den, noise=noise, phase_noise=phase_noise, volterra=volterra,
+              prbs_seed=prbs_seed, pack_order=pack_order, symbols=symbols,
+              phase_steps=tuple(phase_steps), truth=truth)
+    th0 = kk_phase_starts(buf_len, nbufs, seed, linewidth, fs, phase_noise, phase_offset)
+    jobs = [(kw, b, th0[b]) for b in range(nbufs)]
+    if workers > 1 and nbufs > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_kk_worker, jobs))
     else:
-        bits = None
-        a = np.asarray(symbols, dtype=np.complex128)
-        assert len(a) >= nsym
-    pulse = rrc_pulse(beta, sps, span)
-    Ps = float(np.mean(np.abs(a) ** 2)) / sps  # per-sample power of the shaped signal
-    A = np.sqrt(10.0 ** (cspr_db / 10.0) * Ps)
-    sig2 = Ps * sps / 10.0 ** (snr_db / 10.0)
-    pn_std = np.sqrt(2.0 * np.pi * linewidth / fs)
-    theta0 = float(phase_offset)
-    packed, codes_all, field_all, clips = [], [], [], 0
-    c1, c2 = volterra
-    for b in range(nbufs):
-        n0, n1 = b * buf_len, (b + 1) * buf_len
-        s = _shape(a, pulse, sps, n0 - sps, n1)
-        if c1 != 0.0 or c2 != 0.0:
-            p = np.abs(s) ** 2
-            nl = c1 * s * p
-            nl[sps:] += c2 * s[:-sps] * p[:-sps]
-            s = s + nl
-        s = s[sps:]
-        field_all.append(s.copy())
-        n = np.arange(n0, n1, dtype=np.int64)
-        up = np.exp(2j * np.pi * ((n * fd_num) % fd_den) / fd_den)
-        rng = np.random.default_rng([int(seed), b, 29])
-        if phase_noise and linewidth > 0:
-            th = theta0 + np.cumsum(rng.standard_normal(len(s)) * pn_std)
-            theta0 = float(th[-1])
-        else:
-            th = np.full(len(s), theta0)
-        for (ns, dth) in phase_steps:
-            if ns < n1:
-                th[max(0, ns - n0):] += dth
-        E = A + s * up * np.exp(1j * th)
-        if noise:
-            E = E + (rng.standard_normal(len(s)) + 1j * rng.standard_normal(len(s))) * np.sqrt(sig2 / 2.0)
-        I = np.abs(E) ** 2
-        codes, c = _quantise(I)
-        clips += c
-        packed.append(pack12(codes, pack_order))
-        codes_all.append(codes)
-    return dict(packed=packed, codes=np.concatenate(codes_all), bits=bits, symbols=a,
-                field=np.concatenate(field_all), clips=clips, fmt=fmt, sps=sps,
-                buf_len=buf_len, tone=A, Ps=Ps)
+        parts = [_kk_worker(j) for j in jobs]
+    if symbols is None:
+        a = _tx_symbols(fmt, prbs_seed, 0, nsym)
+        bits = prbs15_bits(prbs_seed, nsym * bps)
+    else:
+        a, bits = np.asarray(symbols, dtype=np.complex128), None
+    out = dict(packed=[p["packed"] for p in parts], symbols=a, bits=bits,
+               clips=sum(p["clips"] for p in parts), fmt=fmt, sps=sps, buf_len=buf_len,
+               tone=parts[0]["tone"], Ps=parts[0]["Ps"])
+    if truth:
+        out["codes"] = np.concatenate([p["codes"] for p in parts])
+        out["field"] = np.concatenate([p["field"] for p in parts])
+    return out

@@ -1,0 +1,70 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+include/rx.h declares, and rejects bad arguments before touching the device."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2010_14333_gb300 as rx
+
+HDR = os.path.join(os.path.dirname(__file__), "..", "include", "rx.h")
+
+
+def declared_functions():
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rx_[a-z_]+)\s*\(", src)))
+
+
+def test_header_functions_are_exported():
+    lib = rx.load()
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(rx.EXPORTED) == names
+
+
+def test_binding_raises_without_library(tmp_path):
+    saved = rx._lib
+    rx._lib = None
+    try:
+        with pytest.raises(rx.RxError):
+            rx.load(str(tmp_path / "missing.so"))
+    finally:
+        rx._lib = saved
+
+
+def test_default_config_and_strerror():
+    c = rx.rx_default_config(rx.RX_KK_16QAM)
+    assert (c.ols_n, c.ols_v, c.ntaps, c.bps_b, c.win) == (65536, 4096, 31, 32, 64)
+    assert (c.ds_num, c.ds_den) == (11, 80)
+    p = rx.rx_default_config(rx.RX_PAM4)
+    assert (p.ntaps, p.ntrain, p.mu) == (15, 4096, 1e-3)
+    assert rx.rx_strerror(1).startswith("invalid")
+
+
+@pytest.mark.parametrize("args", [
+    (rx.RX_KK_16QAM, 1e9, 4e9, 1000),          # buf_len not a multiple of 32
+    (rx.RX_KK_16QAM, 2e9, 4e9, 1 << 20),       # KK needs 4 samples/symbol
+    (rx.RX_PAM4, 1e9, 4e9, 1 << 20),           # PAM needs 2 samples/symbol
+    (7, 1e9, 4e9, 1 << 20),                    # unknown format
+])
+def test_create_rejects_bad_arguments(args):
+    lib = rx.load()
+    h = C.c_void_p()
+    st = lib.rx_create(args[0], args[1], args[2], args[3], None, C.byref(h))
+    assert st == 1 and not h.value
+
+
+@pytest.mark.parametrize("field,value", [("ntaps", 33), ("ntaps", 14), ("ols_n", 8192), ("win", 32),
+                                         ("eq_block", 100), ("bps_b", 0), ("amb_syms", 100),
+                                         ("ncma", 20000)])
+def test_create_rejects_bad_config(field, value):
+    lib = rx.load()
+    c = rx.rx_default_config(rx.RX_KK_16QAM)
+    setattr(c, field, value)
+    h = C.c_void_p()
+    assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
