@@ -312,7 +312,11 @@ def gpu_arm(args, rank, world, local):
             "roofline": roof, "stages": stages, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
             "realtime_x": value / 4.0,
-            "ber": stats["ber"], "q_db": stats["q_db"], "bits": stats["bits"],
+            "ber": cpu["ber_gpu_same_buffers"] if cpu else None,
+            "ber_oracle": cpu["ber_oracle"] if cpu else None,
+            "ber_note": "BER of the first 2 buffers of the stream, GPU and FP64 oracle on the same input; "
+                        "the timed ring repeats its 32 buffers, so the PRBS reference is not aligned "
+                        "after a wrap and the timed run's own BER is not meaningful",
             "device_error": stats["device_error"], "gen_s": t_gen}
     if rank == 0:
         print(json.dumps(line), flush=True)
