@@ -176,6 +176,38 @@ rx_status rx_set_taps(rx_handle *h, const double *re, const double *im, int n);
 rx_status rx_profile(rx_handle *h, int enable);
 rx_status rx_profile_read(rx_handle *h, double *ms, int n, int64_t *calls);
 
+/* Kramers-Kronig field of one buffer without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory once they are running.  Examples are a real-time
+ * ingest thread that must not stall on cudaMalloc (which can synchronise the
+ * device), code running inside another framework whose device memory belongs
+ * to that framework's allocator, and plugin hosts that forbid allocations after
+ * start-up.  It computes what rx_process emits as RX_DBG_FIELD for the first
+ * buffer of a stream: 12-bit unpack, overlap-save Hilbert transform of
+ * ln(I)/2 and E = sqrt(I) exp(j phi), for stream samples [0, nsamp - ols_v/2).
+ *
+ *   packed12_in: DEVICE pointer, nsamp*3/2 bytes, 16-byte aligned.
+ *   nsamp:       multiple of 32, at most 524288 (2^19) samples.
+ *   ols_n/ols_v: as in rx_config (256, 4096 or 65536; even overlap < ols_n).
+ *   field_out:   DEVICE pointer, 8-byte aligned, room for 2*(nsamp - ols_v/2)
+ *                floats (interleaved real, imaginary).
+ *
+ * The scratch (twiddle tables, codes, FFT rows, field, reduction partials) is
+ * one fixed device array of about 10 MiB in librx.so; every GPU that loads the
+ * library holds it until the process exits.  Sizes beyond the limit return
+ * RX_EINVAL before anything is enqueued.  The call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine); it enqueues its kernels
+ * on cuda_stream and returns.  The first call on a device does a one-time
+ * set-up with that device current: it looks up the array's device address and
+ * uploads the twiddle tables with a synchronous copy, so make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents, so calls that overlap on the GPU (on different streams
+ * or from different threads) race and corrupt each other's results; issue them
+ * in order on one stream.  Returns RX_ECUDA when the set-up or a launch fails. */
+rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsamp, int32_t pack_order,
+                              int32_t ols_n, int32_t ols_v, float *field_out, void *cuda_stream);
+
 /* Releases the device memory and the handle.  NULL is ignored. */
 void rx_destroy(rx_handle *h);
 

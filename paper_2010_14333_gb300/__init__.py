@@ -49,7 +49,7 @@ class RxError(RuntimeError):
 
 EXPORTED = sorted(["rx_default_config", "rx_create", "rx_process", "rx_process_host", "rx_max_bits",
                    "rx_stats", "rx_debug_copy", "rx_set_taps", "rx_destroy", "rx_strerror",
-                   "rx_profile", "rx_profile_read"])
+                   "rx_profile", "rx_profile_read", "rx_kk_field_noalloc"])
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
 
 _lib = None
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
     L.rx_destroy.restype = None
     L.rx_profile.argtypes = [vp, C.c_int]
     L.rx_profile_read.argtypes = [vp, P(C.c_double), C.c_int, P(i64)]
+    L.rx_kk_field_noalloc.argtypes = [vp, i64, C.c_int32, C.c_int32, C.c_int32, vp, vp]
     L.rx_strerror.argtypes = [C.c_int]
     L.rx_strerror.restype = C.c_char_p
     for name in EXPORTED:
@@ -151,6 +152,13 @@ def rx_profile_read(h: int) -> tuple[dict, int]:
     n = C.c_int64()
     _check(load().rx_profile_read(h, ms, len(STAGES), C.byref(n)))
     return {s: ms[i] for i, s in enumerate(STAGES)}, n.value
+
+
+def rx_kk_field_noalloc(packed12_in: int, nsamp: int, pack_order: int, ols_n: int, ols_v: int,
+                        field_out: int, stream: int = 0):
+    """KK field of one buffer with no device allocation (scratch is a fixed array
+    inside librx.so); see include/rx.h."""
+    _check(load().rx_kk_field_noalloc(packed12_in, nsamp, pack_order, ols_n, ols_v, field_out, stream))
 
 
 def rx_destroy(h: int):

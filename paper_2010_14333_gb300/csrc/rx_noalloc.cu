@@ -1,0 +1,142 @@
+// rx_kk_field_noalloc: the Kramers-Kronig front end (12-bit unpack, overlap-save
+// Hilbert FFT, field sqrt(I) exp(j phi)) for callers that cannot allocate device
+// memory.  All scratch lives in one file-scope device array of fixed size; the
+// caller passes only the input and the output.  See include/rx.h.
+#include <math.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "rx_internal.cuh"
+
+using namespace rxk;
+
+namespace {
+
+constexpr long long kNaMaxSamples = 1LL << 19;          // largest buffer one call accepts
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// byte layout of the scratch array
+constexpr size_t kTwEntries = 16 + 256 + 4096 + 65536;   // e^{-2 pi i k / n} for n = 16, 256, 4096, 65536
+constexpr size_t kOffTw = 0;
+constexpr size_t kOffCodes = align_up(kOffTw + kTwEntries * sizeof(float2));
+constexpr size_t kCodesBytes = (size_t)(65536 + kNaMaxSamples) * sizeof(uint16_t);
+constexpr size_t kOffFft = align_up(kOffCodes + kCodesBytes);
+constexpr size_t kFftBytes = 4u << 20;                   // two-block complex FFT rows
+constexpr size_t kOffE = align_up(kOffFft + kFftBytes);
+constexpr size_t kEBytes = (size_t)(kEHist + kNaMaxSamples) * sizeof(float2);
+constexpr size_t kOffPart = align_up(kOffE + kEBytes);
+constexpr size_t kPartBytes = 64u << 10;                 // per-CTA carrier partials
+constexpr size_t kOffState = align_up(kOffPart + kPartBytes);
+constexpr size_t kScratchBytes = align_up(kOffState + sizeof(DevState));
+
+// One scratch region per GPU that loads the library (held until the process exits).
+// Every call uses it, so calls that overlap on the GPU race with each other.
+static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
+
+// offset of the n-point table inside the twiddle block
+size_t tw_offset(int n)
+{
+    switch (n) {
+    case 16: return 0;
+    case 256: return 16;
+    case 4096: return 16 + 256;
+    default: return 16 + 256 + 4096;   // 65536
+    }
+}
+
+// per-device set-up: device address of the scratch array and the uploaded tables
+constexpr int kMaxDevices = 64;
+unsigned char *g_dev_ptr[kMaxDevices];
+bool g_ready[kMaxDevices];
+
+cudaError_t setup_device(int dev, unsigned char **out)
+{
+    if (g_ready[dev]) {
+        *out = g_dev_ptr[dev];
+        return cudaSuccess;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess) return e;
+    // twiddle tables, once per device (host double precision, rounded once)
+    static float2 tw[kTwEntries];
+    const double pi = 3.14159265358979323846;
+    const int sizes[4] = {16, 256, 4096, 65536};
+    for (int s = 0; s < 4; s++) {
+        int n = sizes[s];
+        float2 *t = tw + tw_offset(n);
+        for (int k = 0; k < n; k++) {
+            double a = -2.0 * pi * (double)k / (double)n;
+            t[k] = make_float2((float)cos(a), (float)sin(a));
+        }
+    }
+    e = cudaMemcpy((unsigned char *)p + kOffTw, tw, sizeof tw, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    g_dev_ptr[dev] = (unsigned char *)p;
+    g_ready[dev] = true;
+    *out = (unsigned char *)p;
+    return cudaSuccess;
+}
+
+__global__ void k_na_copy_field(const float2 *__restrict__ src, float2 *__restrict__ dst, long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i];
+}
+
+}  // namespace
+
+extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsamp, int32_t pack_order,
+                                         int32_t ols_n, int32_t ols_v, float *field_out, void *cuda_stream)
+{
+    if (!packed12_in || !field_out || nsamp <= 0 || nsamp % 32 || nsamp > kNaMaxSamples) return RX_EINVAL;
+    if (((uintptr_t)packed12_in) & 15 || ((uintptr_t)field_out) & 7) return RX_EINVAL;
+    if (pack_order < 0 || pack_order > 1) return RX_EINVAL;
+    if (!(ols_n == 256 || ols_n == 4096 || ols_n == 65536) || ols_v < 2 || ols_v % 2 || ols_v >= ols_n)
+        return RX_EINVAL;
+    long long e_k = nsamp - ols_v / 2;
+    if (e_k <= 0) return RX_EINVAL;
+    KkGeom g;
+    memset(&g, 0, sizeof g);
+    g.N = ols_n;
+    g.V = ols_v;
+    g.hop = ols_n - ols_v;
+    g.N2 = ols_n / 16;
+    g.J = (int)((e_k + g.hop - 1) / g.hop);
+    g.npairs = (g.J + 1) / 2;
+    g.e_prev = 0;
+    g.e_k = e_k;
+    g.avail = nsamp;
+    g.cbase = -(long long)ols_n;        // codes: [ols_n samples before the stream | buffer]
+    g.ebase = -kEHist;                  // field: [kEHist history | buffer]
+    g.ebase_prev = -kEHist;
+    g.sps = 4;
+    size_t need_fft = (size_t)g.npairs * ols_n * sizeof(float2);
+    size_t need_part = (size_t)((g.N2 + kCtaK1 - 1) / kCtaK1) * g.npairs * sizeof(CarrierPartial);
+    if (need_fft > kFftBytes || need_part > kPartBytes) return RX_EINVAL;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RX_ECUDA;
+    unsigned char *base = nullptr;
+    if (setup_device(dev, &base) != cudaSuccess) return RX_ECUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const float2 *twN = (const float2 *)(base + kOffTw) + tw_offset(ols_n);
+    const float2 *twN2 = (const float2 *)(base + kOffTw) + tw_offset(ols_n / 16);
+    uint16_t *codes = (uint16_t *)(base + kOffCodes);
+    float2 *fftws = (float2 *)(base + kOffFft);
+    float2 *E = (float2 *)(base + kOffE);
+    CarrierPartial *part = (CarrierPartial *)(base + kOffPart);
+    DevState *ds = (DevState *)(base + kOffState);
+    // the last-CTA ticket of the carrier reduction must start at zero
+    if (cudaMemsetAsync(ds, 0, sizeof(DevState), st) != cudaSuccess) return RX_ECUDA;
+    if (launch_unpack(packed12_in, codes, nullptr, nsamp, ols_n, 0, 1, pack_order, nullptr, nullptr, st) !=
+        cudaSuccess)
+        return RX_ECUDA;
+    if (launch_kk_front(g, codes, fftws, twN, twN2, E, E, part, ds, st, nullptr) != cudaSuccess) return RX_ECUDA;
+    unsigned grid = (unsigned)((e_k + 255) / 256);
+    k_na_copy_field<<<grid, 256, 0, st>>>(E + kEHist, reinterpret_cast<float2 *>(field_out), e_k);
+    if (cudaGetLastError() != cudaSuccess) return RX_ECUDA;
+    return RX_OK;
+}
