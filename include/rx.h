@@ -58,9 +58,9 @@ typedef enum {
 typedef struct {
     int32_t pack_order;  /* ADC word: 0 = little-endian 24-bit word (s0 = b0 | (b1&15)<<8,
                             s1 = b1>>4 | b2<<4), 1 = big-endian nibbles                    */
-    int32_t ols_n;       /* KK overlap-save FFT length: 256, 4096 or 65536                 */
-    int32_t ols_v;       /* KK overlap, even, < ols_n; each block keeps ols_n - ols_v
-                            outputs with ols_v/2 samples of margin on both sides          */
+    int32_t ols_n;       /* KK overlap-save FFT length: 4096 or 65536                      */
+    int32_t ols_v;       /* KK overlap, multiple of 64, < ols_n; each block keeps
+                            ols_n - ols_v outputs with ols_v/2 samples of margin each side */
     int32_t ds_num;      /* KK downshift = ds_num / ds_den cycles per ADC sample (exact
                             integer phase); default 11/80 = 0.55 GHz at 4 GS/s             */
     int32_t ds_den;
@@ -189,7 +189,7 @@ rx_status rx_profile_read(rx_handle *h, double *ms, int n, int64_t *calls);
  *
  *   packed12_in: DEVICE pointer, nsamp*3/2 bytes, 16-byte aligned.
  *   nsamp:       multiple of 32, at most 524288 (2^19) samples.
- *   ols_n/ols_v: as in rx_config (256, 4096 or 65536; even overlap < ols_n).
+ *   ols_n/ols_v: as in rx_config (4096 or 65536; overlap a multiple of 64, < ols_n).
  *   field_out:   DEVICE pointer, 8-byte aligned, room for 2*(nsamp - ols_v/2)
  *                floats (interleaved real, imaginary).
  *

@@ -29,12 +29,18 @@ struct rx_handle {
     int broken;
     // device memory
     uint16_t *codes[2];
+    uint8_t *phist[2];              // KK: packed history, ping-pong
+    int hw;
     float2 *fftws, *E[2];
     void *Y[2];
     CarrierPartial *partials;
     uint8_t *dec, *winb, *prbs;
+    uint32_t *prbs_bits;            // the PRBS period bit-packed MSB first, first 256 bits repeated
+    uint4 *winrec;                  // per payload window: errors under the four rotations, near count
     float2 *taps[2], *twN, *twN2, *ds_tab;
+    float *lnt, *sqt;
     float *rrc;
+    float rrc_host[2 * 64 + 1];     // host copy of the matched-filter taps
     float4 *dbg_win;
     float2 *dbg_z;
     DevState *st;
@@ -201,7 +207,8 @@ void rx_destroy(rx_handle *h)
     if (!h) return;
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->E[0], h->E[1], h->Y[0], h->Y[1], h->partials,
                     h->dec, h->winb, h->prbs, h->taps[0], h->taps[1], h->twN, h->twN2, h->ds_tab,
-                    h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage, h->bits_stage};
+                    h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage, h->bits_stage, h->lnt, h->sqt,
+                    h->prbs_bits, h->winrec, h->phist[0], h->phist[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->prof_ev) {
@@ -245,8 +252,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         return RX_EINVAL;
     if (kk && (c.ncma < 0 || c.ncma > c.ntrain || c.ncma % kWin || c.bps_b < 1 || c.bps_b > 32 ||
                c.ds_den < 1 || c.ds_num < 0 || c.amb_syms < 0 || c.amb_syms % kWin || c.amb_syms > 4096 ||
-               !(c.ols_n == 256 || c.ols_n == 4096 || c.ols_n == 65536) || c.ols_v < 2 || c.ols_v % 2 ||
-               c.ols_v >= c.ols_n))
+               !(c.ols_n == 4096 || c.ols_n == 65536) || c.ols_v < 64 || c.ols_v % 64 || c.ols_v >= c.ols_n))
         return RX_EINVAL;
     rx_handle *h = (rx_handle *)calloc(1, sizeof(rx_handle));
     if (!h) return RX_ENOMEM;
@@ -313,16 +319,21 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     }
     if (kk) {
         for (int i = 0; i < 2; i++) RX_ALLOC(h->E[i], (kEHist + nb) * sizeof(float2));
+        for (int i = 0; i < 2; i++) RX_ALLOC(h->phist[i], (size_t)h->nhist * 3 / 2 + 16);
         RX_ALLOC(h->fftws, (size_t)h->npairs_max * h->N * sizeof(float2));
         int gx = (h->N2 + kCtaK1 - 1) / kCtaK1;
         RX_ALLOC(h->partials, (size_t)gx * h->npairs_max * sizeof(CarrierPartial));
-        RX_ALLOC(h->twN, h->N * sizeof(float2));
-        RX_ALLOC(h->twN2, h->N2 * sizeof(float2));
+        RX_ALLOC(h->twN, kk_tw_entries(h->N) * sizeof(float2));
+        RX_ALLOC(h->twN2, kk_tw_entries(h->N2) * sizeof(float2));
+        RX_ALLOC(h->lnt, kLutCodes * sizeof(float));
+        RX_ALLOC(h->sqt, kLutCodes * sizeof(float));
         RX_ALLOC(h->ds_tab, c.ds_den * sizeof(float2));
     }
     RX_ALLOC(h->dec, h->dec_cap);
     RX_ALLOC(h->winb, h->win_cap);
-    RX_ALLOC(h->prbs, 32767);
+    RX_ALLOC(h->prbs, 32767 + 256);
+    RX_ALLOC(h->prbs_bits, 1040 * sizeof(uint32_t));
+    RX_ALLOC(h->winrec, h->win_cap * sizeof(uint4));
     RX_ALLOC(h->rrc, (2 * h->hmf + 1) * sizeof(float));
     RX_ALLOC(h->st, sizeof(DevState));
     RX_ALLOC(h->in_stage, nb * 3 / 2 + 16);
@@ -338,24 +349,37 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     float *hf = (float *)malloc(sizeof(float) * nt);
     rrc_taps(c.rrc_beta, sps, c.mf_span, hd);
     for (int i = 0; i < nt; i++) hf[i] = (float)hd[i];
+    for (int i = 0; i < nt && i < (int)(sizeof h->rrc_host / sizeof(float)); i++) h->rrc_host[i] = hf[i];
     cudaError_t e = cudaMemcpy(h->rrc, hf, sizeof(float) * nt, cudaMemcpyHostToDevice);
     free(hd);
     free(hf);
-    uint8_t *pb = (uint8_t *)malloc(32767);
+    uint8_t *pb = (uint8_t *)malloc(32767 + 256);
     prbs15_period(c.prbs_seed, pb);
-    if (e == cudaSuccess) e = cudaMemcpy(h->prbs, pb, 32767, cudaMemcpyHostToDevice);
+    for (int i = 0; i < 256; i++) pb[32767 + i] = pb[i];   // one period plus its first 256 bits again
+    if (e == cudaSuccess) e = cudaMemcpy(h->prbs, pb, 32767 + 256, cudaMemcpyHostToDevice);
+    uint32_t pw[1040];
+    memset(pw, 0, sizeof pw);
+    for (int i = 0; i < 32767 + 256; i++)
+        if (pb[i]) pw[i >> 5] |= 0x80000000u >> (i & 31);
+    if (e == cudaSuccess) e = cudaMemcpy(h->prbs_bits, pw, sizeof pw, cudaMemcpyHostToDevice);
     free(pb);
     float2 t0[32];
     memset(t0, 0, sizeof t0);
     t0[h->th] = make_float2(1.f, 0.f);   // centre tap 1
     if (e == cudaSuccess) e = cudaMemcpy(h->taps[0], t0, sizeof t0, cudaMemcpyHostToDevice);
     if (kk && e == cudaSuccess) {
-        float2 *tw = (float2 *)malloc(sizeof(float2) * h->N);
-        twiddles(h->N, tw);
-        e = cudaMemcpy(h->twN, tw, sizeof(float2) * h->N, cudaMemcpyHostToDevice);
-        twiddles(h->N2, tw);
-        if (e == cudaSuccess) e = cudaMemcpy(h->twN2, tw, sizeof(float2) * h->N2, cudaMemcpyHostToDevice);
-        free(tw);
+        int n1 = kk_tw_entries(h->N), n2 = kk_tw_entries(h->N2);
+        float2 *t1 = (float2 *)malloc(sizeof(float2) * n1), *t2 = (float2 *)malloc(sizeof(float2) * n2);
+        float *ln = (float *)malloc(sizeof(float) * kLutCodes), *sq = (float *)malloc(sizeof(float) * kLutCodes);
+        kk_host_tables(h->N, ln, sq, t1, t2);
+        e = cudaMemcpy(h->twN, t1, sizeof(float2) * n1, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->twN2, t2, sizeof(float2) * n2, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->lnt, ln, sizeof(float) * kLutCodes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->sqt, sq, sizeof(float) * kLutCodes, cudaMemcpyHostToDevice);
+        free(t1);
+        free(t2);
+        free(ln);
+        free(sq);
         float2 *ds = (float2 *)malloc(sizeof(float2) * c.ds_den);
         twiddles(c.ds_den, ds);      // e^{-2 pi i p / den}
         if (e == cudaSuccess) e = cudaMemcpy(h->ds_tab, ds, sizeof(float2) * c.ds_den, cudaMemcpyHostToDevice);
@@ -396,12 +420,25 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
 
     if (h->prof_on && h->prof_head - h->prof_tail >= kProfRing) prof_harvest_one(h);
     prof_mark(h, 0, st);
-    // 12-bit unpack into [history | buffer]
-    int cw_new = h->cw ^ 1;
-    e = launch_unpack(in, h->codes[cw_new], h->codes[h->cw], h->nb, h->nhist, h->nb, h->calls == 0,
-                      c.pack_order, h->kk ? nullptr : &h->st->pam_s1[par], h->kk ? nullptr : &h->st->pam_s2[par],
-                      st);
-    h->cw = cw_new;
+    // 12-bit unpack into [history | buffer]: the PAM chain's input; the KK kernels
+    // read the packed bytes themselves, so there it only feeds the debug view
+    if (!h->kk || c.debug) {
+        int cw_new = h->cw ^ 1;
+        e = launch_unpack(in, h->codes[cw_new], h->codes[h->cw], h->nb, h->nhist, h->nb, h->calls == 0,
+                          c.pack_order, h->kk ? nullptr : &h->st->pam_s1[par],
+                          h->kk ? nullptr : &h->st->pam_s2[par], st);
+        h->cw = cw_new;
+    }
+    KkInput kin;
+    if (h->kk) {
+        kin.hist = h->phist[h->hw];
+        kin.in = in;
+        kin.hist_next = h->phist[h->hw ^ 1];
+        kin.hist_bytes = (long long)h->nhist * 3 / 2;
+        kin.in_bytes = h->nb * 3 / 2;
+        kin.order = c.pack_order;
+        kin.first_call = h->calls == 0;
+    }
     long long cbase = base - h->nhist;
 
     // KK field reconstruction
@@ -421,11 +458,15 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
         g.N2 = h->N2;
         g.sps = h->sps;
         int ew_new = h->ew ^ 1;
-        e = launch_kk_front(g, h->codes[h->cw], h->fftws, h->twN, h->twN2, h->E[ew_new], h->E[h->ew],
-                            h->partials, h->st, st, h->prof_on ? h : nullptr);
+        KkTables tb = {h->lnt, h->sqt, h->twN, h->twN2};
+        e = launch_kk_front(g, kin, h->fftws, tb, h->E[ew_new], h->E[h->ew], h->partials, h->st, st,
+                            h->prof_on ? h : nullptr);
         h->ew = ew_new;
         h->ebase_cur = g.ebase;
+    } else if (e == cudaSuccess && h->kk) {
+        e = launch_kk_hist(kin, st);
     }
+    if (h->kk) h->hw ^= 1;
     // matched filter
     prof_mark(h, 4, st);
     if (e == cudaSuccess && s.f_k > h->f_prev) {
@@ -434,7 +475,7 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
         if (h->kk)
             e = launch_kk_mf(h->E[h->ew], h->ebase_cur, s.e_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
                              c.ds_den, h->st, (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw], h->ybase_cur,
-                             st);
+                             st, h->rrc_host);
         else
             e = launch_pam_mf(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->rrc, h->hmf, h->st, par,
                               (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, st);
@@ -452,18 +493,18 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
     g.nwin = npay > 0 ? (int)(npay / kWin) : 0;
     prof_mark(h, 5, st);
     if (e == cudaSuccess && do_train) {
-        e = launch_eq(h->ep, g, 1, h->Y[h->yw], h->taps[h->tw], nullptr, h->dec, h->winb, nullptr, h->dbg_z,
-                      h->prbs, h->st, st);
+        e = launch_eq(h->ep, g, 1, h->Y[h->yw], h->taps[h->tw], nullptr, h->dec, h->winb, h->winrec, nullptr,
+                      h->dbg_z, h->prbs, h->prbs_bits, h->st, st);
         h->trained = 1;
     }
     if (e == cudaSuccess && g.nblk > 0) {
-        e = launch_eq(h->ep, g, 0, h->Y[h->yw], h->taps[h->tw], h->taps[h->tw ^ 1], h->dec, h->winb, h->dbg_win,
-                      h->dbg_z, h->prbs, h->st, st);
+        e = launch_eq(h->ep, g, 0, h->Y[h->yw], h->taps[h->tw], h->taps[h->tw ^ 1], h->dec, h->winb, h->winrec,
+                      h->dbg_win, h->dbg_z, h->prbs, h->prbs_bits, h->st, st);
         h->tw ^= 1;
         prof_mark(h, 6, st);
         if (e == cudaSuccess) {
             int resolve = h->kk && !h->amb_done;
-            e = launch_demap(h->ep, g, resolve, h->uw, h->dec, h->winb, h->dbg_win, h->prbs, bits_out, h->st, st);
+            e = launch_demap(h->ep, g, resolve, h->uw, h->dec, h->winb, h->winrec, h->dbg_win, bits_out, h->st, st);
             if (h->kk) h->uw ^= 1;
             h->amb_done = 1;
         }

@@ -59,28 +59,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
 }
 
 // ------------------------------------------------------------- symbol helpers
-__device__ __forceinline__ int decide(float t, int mq)
-{
-    int L = 0;
-    for (int j = 0; j < mq - 1; j++) L += (t >= (float)(2 * j - (mq - 2)));
-    return L;
-}
-__device__ __forceinline__ bool near_thr(float t, int mq)
-{
-    bool n = false;
-    for (int j = 0; j < mq - 1; j++) n |= fabsf(t - (float)(2 * j - (mq - 2))) < 1e-4f;
-    return n;
-}
-__device__ __forceinline__ float level(int L, int mq) { return (float)(2 * L - (mq - 1)); }
-// squared distance to the nearest odd-integer level by folding: for 4 levels
-// (||t| - 2| - 1)^2, for 2 levels (|t| - 1)^2
-__device__ __forceinline__ float dist_fold(float t, int mq)
-{
-    float a = fabsf(t);
-    for (int h = mq >> 1; h > 1; h >>= 1) a = fabsf(a - (float)h);
-    a -= 1.f;
-    return a * a;
-}
 __device__ __forceinline__ int gray(int L) { return L ^ (L >> 1); }
 __device__ __forceinline__ int gray_inv(int g)
 {
@@ -88,52 +66,103 @@ __device__ __forceinline__ int gray_inv(int g)
     for (int s = g >> 1; s; s >>= 1) L ^= s;
     return L;
 }
-// transmitted level indices of symbol k from the PRBS-15 table (MSB first)
-__device__ __forceinline__ void tx_sym(const uint8_t *prbs, long long k, int bps, bool qam, int &LI, int &LQ)
-{
-    int nb = qam ? bps / 2 : bps;
-    long long b0 = (long long)bps * k;
-    int gi = 0, gq = 0;
-    for (int t = 0; t < nb; t++) gi = (gi << 1) | prbs[(b0 + t) % 32767];
-    if (qam)
-        for (int t = 0; t < nb; t++) gq = (gq << 1) | prbs[(b0 + nb + t) % 32767];
-    LI = gray_inv(gi);
-    LQ = qam ? gray_inv(gq) : 0;
-}
-// rotate a level-index pair by -j (multiply the symbol by -j) q times
-__device__ __forceinline__ void rot_levels(int &LI, int &LQ, int q, int mq)
-{
-    for (int s = 0; s < (q & 3); s++) {
-        int t = LI;
-        LI = LQ;
-        LQ = mq - 1 - t;
-    }
-}
-
 // ---------------------------------------------------------------- one window
-// ys: 2-sps input with ys[i] = y[ym0 + i]; the window's first symbol is k0.
-// mode: 0 CMA, 1 data-aided (PAM training), 2 decision directed.
-// Returns the window's b* (QAM DD) or -1.
+// ys: 2-sps input in shared memory (16-byte aligned); c0: local index of y[2 k0]
+// (even); the window's 64 symbols are k0..k0+63.  mode: 0 CMA, 1 data-aided (PAM
+// training), 2 decision directed.  NT taps, TH = (NT-1)/2 odd, MQ levels per
+// dimension: compile-time so that every loop unrolls.
 struct WinOut {
     int b;
     float best, second;
+    unsigned errA, errB;   // bit errors of the window under absolute rotations 0,1 | 2,3 (16 bits each)
+    unsigned serr;         // symbol errors under rotations 0..3 (8 bits each)
+    unsigned nnear;        // symbols within 1e-4 of a threshold
 };
 
-__device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys, long long ym0,
-                                             long long k0, float2 *zs, float2 *es, float2 *ws, int mode,
-                                             float mu, int lane, uint8_t *dec_out, float2 *dbg_z)
+// reference bit group of BPS bits, MSB first, at PRBS position pos of the
+// bit-packed table (bit j at word j>>5, bit 31-(j&31)); the table repeats the
+// first 256 bits after the period, so pos + BPS never wraps
+template <int BPS>
+__device__ __forceinline__ int ref_bits(const uint32_t *__restrict__ tab, int pos)
 {
-    const int th = p.th;
-    // filter: z_k = sum_i conj(w_i) y[2k - i]
+    uint32_t w0 = __ldg(tab + (pos >> 5)), w1 = __ldg(tab + (pos >> 5) + 1);
+    return (int)(__funnelshift_l(w1, w0, pos & 31) >> (32 - BPS));
+}
+
+// rotate a level-index pair by -j, q times (q in 0..3)
+template <int MQ>
+__device__ __forceinline__ void rot_t(int &LI, int &LQ, int q)
+{
+    int a = LI, b = LQ;
+    if (q & 2) { a = MQ - 1 - a; b = MQ - 1 - b; }   // times -1
+    if (q & 1) { int t = a; a = b; b = MQ - 1 - t; } // times -j
+    LI = a;
+    LQ = b;
+}
+
+template <int MQ>
+__device__ __forceinline__ int decide_t(float t)
+{
+    int L = 0;
+#pragma unroll
+    for (int j = 0; j < MQ - 1; j++) L += (t >= (float)(2 * j - (MQ - 2)));
+    return L;
+}
+template <int MQ>
+__device__ __forceinline__ bool near_t(float t)
+{
+    bool n = false;
+#pragma unroll
+    for (int j = 0; j < MQ - 1; j++) n |= fabsf(t - (float)(2 * j - (MQ - 2))) < 1e-4f;
+    return n;
+}
+// squared distance to the nearest odd-integer level: fold |t| about the level
+// mid-points (4 levels: (||t| - 2| - 1)^2; 2 levels: (|t| - 1)^2)
+template <int MQ>
+__device__ __forceinline__ float dist_t(float t, float acc)
+{
+    float a = fabsf(t);
+#pragma unroll
+    for (int h = MQ >> 1; h > 1; h >>= 1) a = fabsf(a - (float)h);
+    a -= 1.f;
+    return fmaf(a, a, acc);
+}
+
+template <int NT, int MQ>
+__device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys, int c0, float2 *zs, float2 *es,
+                                             float2 *ws, int mode, float mu, int lane, uint8_t *dec_out,
+                                             float2 *dbg_z, const uint32_t *prbs_bits, int pwin)
+{
+    constexpr int TH = (NT - 1) / 2;
+    constexpr int NP = (NT + 1) / 2;              // y pairs per symbol
+    static_assert(TH % 2 == 1, "tap half-length must be odd");
+    // taps to registers (ws holds NT+1 entries, the last one zero)
+    float2 w[2 * NP];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+        float4 t = reinterpret_cast<const float4 *>(ws)[i];
+        w[2 * i] = make_float2(t.x, t.y);
+        w[2 * i + 1] = make_float2(t.z, t.w);
+    }
+    // filter: z_k = sum_i conj(w_i) y[2k + TH - i]; pairs start at the even index 2k - TH - 1
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         int q = lane + 32 * h;
-        const float2 *yc = ys + (2 * (k0 + q) - ym0);
+        const float4 *yp = reinterpret_cast<const float4 *>(ys + c0 + 2 * q - TH - 1);
         float ar = 0.f, ai = 0.f;
-        for (int i = 0; i < p.ntaps; i++) {
-            float2 w = ws[i], y = yc[th - i];
-            ar = fmaf(w.x, y.x, fmaf(w.y, y.y, ar));
-            ai = fmaf(w.x, y.y, fmaf(-w.y, y.x, ai));
+#pragma unroll
+        for (int v = 0; v < NP; v++) {
+            float4 Y = yp[v];
+            {   // offset 2v+1 -> tap NT-1-2v
+                const float2 wv = w[NT - 1 - 2 * v];
+                ar = fmaf(wv.x, Y.z, fmaf(wv.y, Y.w, ar));
+                ai = fmaf(wv.x, Y.w, fmaf(-wv.y, Y.z, ai));
+            }
+            if (v >= 1) {   // offset 2v -> tap NT-2v
+                const float2 wv = w[NT - 2 * v];
+                ar = fmaf(wv.x, Y.x, fmaf(wv.y, Y.y, ar));
+                ai = fmaf(wv.x, Y.y, fmaf(-wv.y, Y.x, ai));
+            }
         }
         zs[q] = make_float2(ar, ai);
         if (dbg_z) dbg_z[q] = make_float2(ar, ai);
@@ -145,16 +174,19 @@ __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys
     R.second = 0.f;
     float cs = 1.f, sn = 0.f;   // cos / sin of the chosen phase
     if (mode == 2) {
-        // blind phase search, lane b tests theta_b = (b/B)(pi/2) - pi/4
+        // blind phase search: lane b tests theta_b = (b/B)(pi/2) - pi/4
         float tsn, tcs;
         sincospif((float)lane / (float)(2 * p.bps_b) - 0.25f, &tsn, &tcs);
-        float sc = p.scale * tcs, ss = p.scale * tsn;
+        const float sc = p.scale * tcs, ss = p.scale * tsn;
         float M = 0.f;
-        for (int q = 0; q < kWin; q++) {
-            float2 z = zs[q];
-            float vr = fmaf(z.x, sc, z.y * ss);
-            float vi = fmaf(z.y, sc, -z.x * ss);
-            M += dist_fold(vr, p.mq) + dist_fold(vi, p.mq);
+        const float4 *z4 = reinterpret_cast<const float4 *>(zs);
+#pragma unroll 8
+        for (int q2 = 0; q2 < kWin / 2; q2++) {
+            float4 Z = z4[q2];
+            M = dist_t<MQ>(fmaf(Z.x, sc, Z.y * ss), M);
+            M = dist_t<MQ>(fmaf(Z.y, sc, -Z.x * ss), M);
+            M = dist_t<MQ>(fmaf(Z.z, sc, Z.w * ss), M);
+            M = dist_t<MQ>(fmaf(Z.w, sc, -Z.z * ss), M);
         }
         if (lane >= p.bps_b) M = __int_as_float(0x7f800000);
         float m1 = M, m2 = __int_as_float(0x7f800000);
@@ -180,89 +212,153 @@ __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys
     }
     // decisions and errors
     const float inv_s = 1.0f / p.scale;
+    constexpr int NB = MQ == 2 ? 1 : 2, BPS = 2 * NB;
+    unsigned eA = 0, eB = 0, se = 0, nn = 0;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         int q = lane + 32 * h;
         float2 z = zs[q];
         float vr = p.scale * fmaf(z.x, cs, z.y * sn);
         float vi = p.scale * fmaf(z.y, cs, -z.x * sn);
-        int LI = decide(vr, p.mq), LQ = decide(vi, p.mq);
-        bool nr = near_thr(vr, p.mq) || near_thr(vi, p.mq);
+        int LI = decide_t<MQ>(vr), LQ = decide_t<MQ>(vi);
+        bool nr = near_t<MQ>(vr) || near_t<MQ>(vi);
         if (dec_out) dec_out[q] = (uint8_t)(LI | (LQ << 3) | (nr ? 64 : 0));
+        if (prbs_bits) {
+            // bit errors of this symbol under each absolute pi/2 rotation of the decision
+            int ref = ref_bits<BPS>(prbs_bits, pwin + BPS * q);
+#pragma unroll
+            for (int rq = 0; rq < 4; rq++) {
+                int a = LI, b = LQ;
+                rot_t<MQ>(a, b, rq);
+                unsigned ne = __popc(((gray(a) << NB) | gray(b)) ^ ref);
+                if (rq < 2) eA += ne << (16 * rq);
+                else eB += ne << (16 * (rq - 2));
+                se += (ne > 0) << (8 * rq);
+            }
+            nn += nr;
+        }
         float2 e;
         if (mode == 0) {
             float f = p.r2 - (z.x * z.x + z.y * z.y);
             e = make_float2(z.x * f, z.y * f);
         } else {
-            float dI = level(LI, p.mq) * inv_s, dQ = level(LQ, p.mq) * inv_s;
+            float dI = (float)(2 * LI - (MQ - 1)) * inv_s, dQ = (float)(2 * LQ - (MQ - 1)) * inv_s;
             e = make_float2(fmaf(dI, cs, -dQ * sn) - z.x, fmaf(dI, sn, dQ * cs) - z.y);
         }
         es[q] = e;
     }
     __syncwarp();
-    // block-LMS update after the window: w_i += mu sum_k y[2k - i] conj(e_k)
-    if (lane < p.ntaps) {
-        int off = lane - th;
+    if (prbs_bits) {
+        R.errA = warp_sum_i(eA);
+        R.errB = warp_sum_i(eB);
+        R.serr = warp_sum_i(se);
+        R.nnear = warp_sum_i(nn);
+    }
+    // block-LMS update after the window: w_i += mu sum_k y[2k + TH - i] conj(e_k)
+    if (lane < NT) {
         float gr = 0.f, gi = 0.f;
-        const float2 *yb = ys + (2 * k0 - ym0 - off);
-        for (int q = 0; q < kWin; q++) {
-            float2 y = yb[2 * q], e = es[q];
-            gr = fmaf(y.x, e.x, fmaf(y.y, e.y, gr));
-            gi = fmaf(y.y, e.x, fmaf(-y.x, e.y, gi));
+        const float2 *yb = ys + (c0 + TH - lane);
+        const float4 *e4 = reinterpret_cast<const float4 *>(es);
+#pragma unroll 8
+        for (int q2 = 0; q2 < kWin / 2; q2++) {
+            float4 E = e4[q2];
+            float2 y0 = yb[4 * q2], y1 = yb[4 * q2 + 2];
+            gr = fmaf(y0.x, E.x, fmaf(y0.y, E.y, gr));
+            gi = fmaf(y0.y, E.x, fmaf(-y0.x, E.y, gi));
+            gr = fmaf(y1.x, E.z, fmaf(y1.y, E.w, gr));
+            gi = fmaf(y1.y, E.z, fmaf(-y1.x, E.w, gi));
         }
-        float2 w = ws[lane];
-        ws[lane] = make_float2(fmaf(mu, gr, w.x), fmaf(mu, gi, w.y));
+        float2 wl = ws[lane];
+        ws[lane] = make_float2(fmaf(mu, gr, wl.x), fmaf(mu, gi, wl.y));
     }
     __syncwarp();
     return R;
 }
 
-__device__ __forceinline__ void pam_window(const EqParams &p, const float *ys, long long ym0, long long k0,
-                                           float *zs, float *es, float *ws, int mode, float mu, int lane,
-                                           uint8_t *dec_out, float2 *dbg_z, const uint8_t *prbs)
+template <int NT, int MQ>
+__device__ __forceinline__ WinOut pam_window(const EqParams &p, const float *ys, int c0, long long k0, float *zs,
+                                             float *es, float *ws, int mode, float mu, int lane, uint8_t *dec_out,
+                                             float2 *dbg_z, const uint8_t *prbs_ext, const uint32_t *prbs_bits,
+                                             int pwin)
 {
-    const int th = p.th;
+    WinOut R;
+    R.b = 0;
+    R.best = R.second = 0.f;
+    R.errA = R.errB = R.serr = R.nnear = 0;
+    unsigned e0 = 0, s0 = 0, nn = 0;
+    constexpr int TH = (NT - 1) / 2;
+    constexpr int NP = (NT + 1) / 2;
+    static_assert(TH % 2 == 1, "tap half-length must be odd");
+    float w[2 * NP];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+        float2 t = reinterpret_cast<const float2 *>(ws)[i];
+        w[2 * i] = t.x;
+        w[2 * i + 1] = t.y;
+    }
+    constexpr int nb = MQ == 2 ? 1 : (MQ == 4 ? 2 : 3);
+    long long pb = (mode == 1) ? (long long)(((long long)nb * k0) % 32767) : 0;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         int q = lane + 32 * h;
-        const float *yc = ys + (2 * (k0 + q) - ym0);
+        const float2 *yp = reinterpret_cast<const float2 *>(ys + c0 + 2 * q - TH - 1);
         float a = 0.f;
-        for (int i = 0; i < p.ntaps; i++) a = fmaf(ws[i], yc[th - i], a);
+#pragma unroll
+        for (int v = 0; v < NP; v++) {
+            float2 Y = yp[v];
+            a = fmaf(w[NT - 1 - 2 * v], Y.y, a);
+            if (v >= 1) a = fmaf(w[NT - 2 * v], Y.x, a);
+        }
         zs[q] = a;
         if (dbg_z) dbg_z[q] = make_float2(a, 0.f);
-        int L = decide(a, p.mq);
-        bool nr = near_thr(a, p.mq);
+        int L = decide_t<MQ>(a);
+        bool nr = near_t<MQ>(a);
         if (dec_out) dec_out[q] = (uint8_t)(L | (nr ? 64 : 0));
+        if (prbs_bits) {
+            unsigned ne = __popc(gray(L) ^ ref_bits<nb>(prbs_bits, pwin + nb * q));
+            e0 += ne;
+            s0 += ne > 0;
+            nn += nr;
+        }
         float d;
-        if (mode == 1) {
-            int aI, aQ;
-            tx_sym(prbs, k0 + q, p.bps, false, aI, aQ);
-            d = level(aI, p.mq);
+        if (mode == 1) {   // data aided: the transmitted level from the PRBS
+            int pos = (int)(pb + nb * q);
+            pos = pos >= 32767 ? pos - 32767 : pos;
+            int gi = 0;
+            for (int t = 0; t < nb; t++) gi = (gi << 1) | prbs_ext[pos + t];
+            d = (float)(2 * gray_inv(gi) - (MQ - 1));
         } else {
-            d = level(L, p.mq);
+            d = (float)(2 * L - (MQ - 1));
         }
         es[q] = d - a;
     }
     __syncwarp();
-    if (lane < p.ntaps) {
-        int off = lane - th;
-        const float *yb = ys + (2 * k0 - ym0 - off);
+    if (prbs_bits) {
+        R.errA = warp_sum_i(e0);
+        R.serr = warp_sum_i(s0);
+        R.nnear = warp_sum_i(nn);
+    }
+    if (lane < NT) {
+        const float *yb = ys + (c0 + TH - lane);
         float g = 0.f;
+#pragma unroll 16
         for (int q = 0; q < kWin; q++) g = fmaf(yb[2 * q], es[q], g);
         ws[lane] = fmaf(mu, g, ws[lane]);
     }
     __syncwarp();
+    return R;
 }
 
 // -------------------------------------------------------------- equaliser kernel
 // Payload: one warp per block of eq_block symbols, input staged by one bulk copy.
 // Training (train=1): one warp runs the training windows sequentially, staging
 // each window's input with plain loads.
-template <bool QAM>
-__global__ void k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Yv, float2 *taps_in,
-                     float2 *taps_out, uint8_t *__restrict__ dec, uint8_t *__restrict__ winb,
-                     float4 *__restrict__ dbg_win, float2 *__restrict__ dbg_z, const uint8_t *__restrict__ prbs,
-                     DevState *dst)
+template <bool QAM, int NT, int MQ>
+__global__ void __launch_bounds__(32 * kEqWarps)
+    k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Yv, float2 *taps_in, float2 *taps_out,
+         uint8_t *__restrict__ dec, uint8_t *__restrict__ winb, uint4 *__restrict__ winrec,
+         float4 *__restrict__ dbg_win, float2 *__restrict__ dbg_z, const uint8_t *__restrict__ prbs_ext,
+         const uint32_t *__restrict__ prbs_bits, DevState *dst)
 {
     typedef typename std::conditional<QAM, float2, float>::type T;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -281,11 +377,10 @@ __global__ void k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Y
     T *ws = es + kWin;
     long long blk = (long long)blockIdx.x * kEqWarps + wid;
     if (!train && blk >= g.nblk) return;
-    // start taps
-    if (lane < p.ntaps) {
-        if (QAM) reinterpret_cast<float2 *>(ws)[lane] = taps_in[lane];
-        else reinterpret_cast<float *>(ws)[lane] = taps_in[lane].x;
-    }
+    // start taps; the slot past the last tap stays zero for the paired loads
+    if (QAM) reinterpret_cast<float2 *>(ws)[lane] = lane < NT ? taps_in[lane] : make_float2(0.f, 0.f);
+    else reinterpret_cast<float *>(ws)[lane] = lane < NT ? taps_in[lane].x : 0.f;
+    __syncwarp();
     unsigned ambig = 0;
     if (train) {
         for (long long k0 = 0; k0 < p.ntrain; k0 += kWin) {
@@ -296,16 +391,16 @@ __global__ void k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Y
             if (QAM) {
                 int mode = (k0 < p.ncma) ? 0 : 2;
                 float mu = mode == 0 ? p.mu_cma : p.mu;
-                qam_window(p, reinterpret_cast<float2 *>(ys), ym0, k0, reinterpret_cast<float2 *>(zs),
-                           reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), mode, mu, lane,
-                           nullptr, dz);
+                qam_window<NT, MQ>(p, reinterpret_cast<float2 *>(ys), kYHist, reinterpret_cast<float2 *>(zs),
+                                   reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), mode, mu, lane,
+                                   nullptr, dz, nullptr, 0);
             } else {
-                pam_window(p, reinterpret_cast<float *>(ys), ym0, k0, reinterpret_cast<float *>(zs),
-                           reinterpret_cast<float *>(es), reinterpret_cast<float *>(ws), 1, p.mu_train, lane,
-                           nullptr, dz, prbs);
+                pam_window<NT, MQ>(p, reinterpret_cast<float *>(ys), kYHist, k0, reinterpret_cast<float *>(zs),
+                                   reinterpret_cast<float *>(es), reinterpret_cast<float *>(ws), 1, p.mu_train, lane,
+                                   nullptr, dz, prbs_ext, nullptr, 0);
             }
         }
-        if (lane < p.ntaps)
+        if (lane < NT)
             taps_in[lane] = QAM ? reinterpret_cast<float2 *>(ws)[lane]
                                 : make_float2(reinterpret_cast<float *>(ws)[lane], 0.f);
         return;
@@ -324,27 +419,37 @@ __global__ void k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Y
         mbar_wait(bar, 0);
         return;
     }
+    const int bpsv = p.bps;
+    int pwin = (int)(((long long)bpsv * kb) % 32767);   // PRBS position of the window's first bit
     for (int w = 0; w < B / kWin; w++) {
         long long k0 = kb + (long long)w * kWin;
+        int c0 = kYHist + 2 * w * kWin;
         uint8_t *dq = dec + (k0 - g.pay_lo);
         float2 *dz = dbg_z ? dbg_z + (k0 - g.sym_lo) : nullptr;
         long long wi = (k0 - g.pay_lo) / kWin;
         if (QAM) {
-            WinOut R = qam_window(p, reinterpret_cast<float2 *>(ys), ym0, k0, reinterpret_cast<float2 *>(zs),
-                                  reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), 2, p.mu, lane,
-                                  dq, dz);
+            WinOut R = qam_window<NT, MQ>(p, reinterpret_cast<float2 *>(ys), c0, reinterpret_cast<float2 *>(zs),
+                                          reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), 2, p.mu,
+                                          lane, dq, dz, prbs_bits, pwin);
             if (lane == 0) {
                 winb[wi] = (uint8_t)R.b;
+                winrec[wi] = make_uint4(R.errA, R.errB, R.serr, (unsigned)R.b | (R.nnear << 8));
                 if (dbg_win) dbg_win[wi] = make_float4((float)R.b, 0.f, R.best, R.second);
                 ambig += (R.second - R.best) <= 1e-6f * R.best;
             }
         } else {
-            pam_window(p, reinterpret_cast<float *>(ys), ym0, k0, reinterpret_cast<float *>(zs),
-                       reinterpret_cast<float *>(es), reinterpret_cast<float *>(ws), 2, p.mu, lane, dq, dz, prbs);
-            if (lane == 0) winb[wi] = 0;
+            WinOut R = pam_window<NT, MQ>(p, reinterpret_cast<float *>(ys), c0, k0, reinterpret_cast<float *>(zs),
+                                          reinterpret_cast<float *>(es), reinterpret_cast<float *>(ws), 2, p.mu, lane,
+                                          dq, dz, prbs_ext, prbs_bits, pwin);
+            if (lane == 0) {
+                winb[wi] = 0;
+                winrec[wi] = make_uint4(R.errA, 0u, R.serr, R.nnear << 8);
+            }
         }
+        pwin += bpsv * kWin;
+        pwin = pwin >= 32767 ? pwin - 32767 : pwin;
     }
-    if (blk == g.nblk - 1 && lane < p.ntaps)
+    if (blk == g.nblk - 1 && lane < NT)
         taps_out[lane] = QAM ? reinterpret_cast<float2 *>(ws)[lane]
                              : make_float2(reinterpret_cast<float *>(ws)[lane], 0.f);
     if (lane == 0 && ambig) atomicAdd(&dst->cnt[C_AMBIG], (unsigned long long)ambig);
@@ -357,147 +462,166 @@ static size_t eq_smem_per_warp(bool qam, int B)
     return (w + 15) & ~(size_t)15;
 }
 
-cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void *Y, float2 *taps_in,
-                      float2 *taps_out, uint8_t *dec, uint8_t *winb, float4 *dbg_win, float2 *dbg_z,
-                      const uint8_t *prbs, DevState *dst, cudaStream_t st)
+template <bool QAM, int NT, int MQ>
+static cudaError_t launch_eq_t(const EqParams &p, const EqGeom &g, int train, const void *Y, float2 *taps_in,
+                               float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec, float4 *dbg_win,
+                               float2 *dbg_z, const uint8_t *prbs, const uint32_t *prbs_bits, DevState *dst,
+                               cudaStream_t st)
 {
-    bool qam = p.kk != 0;
     if (train) {
-        size_t smem = eq_smem_per_warp(qam, kWin);
-        if (qam) k_eq<true><<<1, 32, smem, st>>>(p, g, 1, Y, taps_in, taps_out, dec, winb, dbg_win, dbg_z, prbs, dst);
-        else k_eq<false><<<1, 32, smem, st>>>(p, g, 1, Y, taps_in, taps_out, dec, winb, dbg_win, dbg_z, prbs, dst);
+        size_t smem = eq_smem_per_warp(QAM, kWin);
+        k_eq<QAM, NT, MQ><<<1, 32, smem, st>>>(p, g, 1, Y, taps_in, taps_out, dec, winb, winrec, dbg_win, dbg_z, prbs,
+                                               prbs_bits, dst);
         return cudaGetLastError();
     }
-    size_t smem = eq_smem_per_warp(qam, p.eq_block) * kEqWarps;
+    size_t smem = eq_smem_per_warp(QAM, p.eq_block) * kEqWarps;
     unsigned grid = (unsigned)((g.nblk + kEqWarps - 1) / kEqWarps);
-    if (qam) {
-        cudaFuncSetAttribute(k_eq<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_eq<true><<<grid, 32 * kEqWarps, smem, st>>>(p, g, 0, Y, taps_in, taps_out, dec, winb, dbg_win, dbg_z,
-                                                      prbs, dst);
-    } else {
-        cudaFuncSetAttribute(k_eq<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_eq<false><<<grid, 32 * kEqWarps, smem, st>>>(p, g, 0, Y, taps_in, taps_out, dec, winb, dbg_win, dbg_z,
-                                                       prbs, dst);
-    }
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_eq<QAM, NT, MQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_eq<QAM, NT, MQ><<<grid, 32 * kEqWarps, smem, st>>>(p, g, 0, Y, taps_in, taps_out, dec, winb, winrec, dbg_win,
+                                                          dbg_z, prbs, prbs_bits, dst);
     return cudaGetLastError();
 }
 
+// tap counts with a compiled kernel (odd, half-length odd)
+#define RX_EQ_TAPS(X) X(3) X(7) X(11) X(15) X(19) X(23) X(27) X(31)
+
+cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void *Y, float2 *taps_in,
+                      float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec, float4 *dbg_win, float2 *dbg_z,
+                      const uint8_t *prbs, const uint32_t *prbs_bits, DevState *dst, cudaStream_t st)
+{
+#define RX_CASE(NTV)                                                                                           \
+    if (p.ntaps == NTV) {                                                                                      \
+        if (p.kk && p.mq == 2) return launch_eq_t<true, NTV, 2>(p, g, train, Y, taps_in, taps_out, dec, winb,  \
+                                                                winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);                \
+        if (p.kk && p.mq == 4) return launch_eq_t<true, NTV, 4>(p, g, train, Y, taps_in, taps_out, dec, winb,  \
+                                                                winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);                \
+        if (!p.kk && p.mq == 2) return launch_eq_t<false, NTV, 2>(p, g, train, Y, taps_in, taps_out, dec,      \
+                                                                  winb, winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);        \
+        if (!p.kk && p.mq == 4) return launch_eq_t<false, NTV, 4>(p, g, train, Y, taps_in, taps_out, dec,      \
+                                                                  winb, winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);        \
+        if (!p.kk && p.mq == 8) return launch_eq_t<false, NTV, 8>(p, g, train, Y, taps_in, taps_out, dec,      \
+                                                                  winb, winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);        \
+    }
+    RX_EQ_TAPS(RX_CASE)
+#undef RX_CASE
+    return cudaErrorInvalidValue;
+}
+
 // ------------------------------------------------------------------ demap / BER
-// R windows per CTA.  The pi/2 unwrap counter of window w is the carried value
-// plus a prefix sum of integer increments; each CTA sums the increments of all
-// earlier windows itself (a few KB of window indices), then scans its own.
-constexpr int kDemapWin = 64;
-constexpr int kDemapThreads = 256;
+// kDemapWin windows per CTA, one warp per window at a time.  The pi/2 unwrap
+// counter of window w is the carried value plus a prefix sum of integer
+// increments; each CTA sums the increments of all earlier windows itself
+// (16-byte loads of the window phase indices), then scans its own.  The
+// equaliser has already scored every window against the PRBS under the four
+// absolute rotations of its decisions (window records), so the bit-error
+// statistics here are selections: the decoded rotation q = m + r gives the raw
+// count, and the slip-tolerant count takes the best rotation, ties to q.
+constexpr int kDemapWin = 16;
+constexpr int kDemapThreads = 128;
 
 __device__ __forceinline__ int unwrap_inc(int b_prev, int b, int B)
 {
     int d = b_prev - b;
     return (d > B / 2) - (d < -B / 2);
 }
+__device__ __forceinline__ unsigned rec_err(const uint4 &r, int q)
+{
+    unsigned v = (q < 2) ? r.x : r.y;
+    return (v >> (16 * (q & 1))) & 0xFFFFu;
+}
+__device__ __forceinline__ unsigned rec_serr(const uint4 &r, int q) { return (r.z >> (8 * q)) & 0xFFu; }
 
-template <bool QAM>
+template <bool QAM, int BPS, int MQ>
 __global__ void __launch_bounds__(kDemapThreads)
     k_demap(EqParams p, EqGeom g, int resolve_amb, int uw_in, const uint8_t *__restrict__ dec,
-            const uint8_t *__restrict__ winb, float4 *__restrict__ dbg_win, const uint8_t *__restrict__ prbs,
+            const uint8_t *__restrict__ winb, const uint4 *__restrict__ winrec, float4 *__restrict__ dbg_win,
             uint8_t *__restrict__ bits_out, DevState *dst)
 {
+    constexpr int NW = kDemapThreads / 32;
+    constexpr int NB = QAM ? BPS / 2 : BPS;
     __shared__ long long s_m[kDemapWin];
-    __shared__ int s_red[kDemapThreads / 32][4];
+    __shared__ int s_red[NW];
     __shared__ int s_r;
-    __shared__ uint32_t s_bits[kDemapThreads / 32][8];
+    __shared__ uint8_t s_grp[NW][kWin];
     __shared__ unsigned long long s_cnt[C_NCNT];
     int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int w0 = blockIdx.x * kDemapWin;
     int wend = min(w0 + kDemapWin, g.nwin);
     if (tid < C_NCNT) s_cnt[tid] = 0;
-    int have = 0, blast = 0;
-    long long mstart = 0;
     if (QAM) {
-        have = dst->unwrap_have[uw_in];
-        blast = dst->unwrap_b[uw_in];
-        mstart = have ? dst->unwrap_m[uw_in] : 0;
-        // prefix of increments over windows [0, w0)
+        int have = dst->unwrap_have[uw_in];
+        int blast = dst->unwrap_b[uw_in];
+        long long mstart = have ? dst->unwrap_m[uw_in] : 0;
+        // prefix of increments over windows [0, w0), 16 windows per load
         int part = 0;
-        for (int w = tid; w < w0; w += kDemapThreads) {
-            int bp = (w == 0) ? blast : winb[w - 1];
-            if (w > 0 || have) part += unwrap_inc(bp, winb[w], p.bps_b);
+        for (int c = tid; c < w0 / 16; c += kDemapThreads) {
+            uint4 v = *reinterpret_cast<const uint4 *>(winb + 16 * c);
+            uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+            int prev = (c == 0) ? blast : winb[16 * c - 1];
+            bool use_first = (c > 0) || have;
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                int b = (wd[i >> 2] >> (8 * (i & 3))) & 0xFF;
+                if (i > 0 || use_first) part += unwrap_inc(prev, b, p.bps_b);
+                prev = b;
+            }
         }
         part = warp_sum_i(part);
-        if (lane == 0) s_red[wid][0] = part;
+        if (lane == 0) s_red[wid] = part;
         __syncthreads();
         long long pre = 0;
-        for (int i = 0; i < kDemapThreads / 32; i++) pre += s_red[i][0];
-        // inclusive scan of this CTA's increments (64 windows, two warps)
-        int inc = 0;
-        if (tid < kDemapWin && w0 + tid < wend) {
-            int w = w0 + tid;
-            int bp = (w == 0) ? blast : winb[w - 1];
-            if (w > 0 || have) inc = unwrap_inc(bp, winb[w], p.bps_b);
-        }
-        int sc = inc;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int v = __shfl_up_sync(0xffffffffu, sc, o);
-            if (lane >= o) sc += v;
+        for (int i = 0; i < NW; i++) pre += s_red[i];
+        if (tid < 32) {   // inclusive scan of this CTA's increments
+            int inc = 0;
+            if (tid < kDemapWin && w0 + tid < wend) {
+                int w = w0 + tid;
+                int bp = (w == 0) ? blast : winb[w - 1];
+                if (w > 0 || have) inc = unwrap_inc(bp, winb[w], p.bps_b);
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            if (tid < kDemapWin) s_m[tid] = mstart + pre + inc;
         }
-        __syncthreads();
-        if (tid == 31) s_red[0][1] = sc;
-        __syncthreads();
-        if (tid < kDemapWin) {
-            long long tot = sc + ((tid >= 32) ? s_red[0][1] : 0);
-            s_m[tid] = mstart + pre + tot;
-        }
-        // stream-start pi/2 ambiguity: every CTA resolves it identically
         if (resolve_amb) {
-            __syncthreads();
-            int nw = p.amb_syms / kWin;    // windows 0..nw-1 of this call
-            __shared__ long long s_ma[64];
+            // stream-start pi/2 ambiguity from the first amb_syms payload symbols:
+            // the rotation r whose decoded symbols (rotation m_w + r) match the
+            // transmitted ones best, ties to the lowest r; every CTA finds it alike
             if (tid < 32) {
+                int nw = p.amb_syms / kWin;   // windows 0..nw-1 of this call (first payload call)
                 int acc = 0;
-                long long mw[2];
+                unsigned cnt[4] = {0, 0, 0, 0};
                 for (int h = 0; h < 2; h++) {
                     int w = lane + 32 * h;
-                    int v = 0;
-                    if (w < nw && w > 0) v = unwrap_inc(winb[w - 1], winb[w], p.bps_b);
-                    // inclusive scan per half
-                    int s2 = v;
+                    int v = (w < nw && w > 0) ? unwrap_inc(winb[w - 1], winb[w], p.bps_b) : 0;
+#pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
-                        int t = __shfl_up_sync(0xffffffffu, s2, o);
-                        if (lane >= o) s2 += t;
+                        int t = __shfl_up_sync(0xffffffffu, v, o);
+                        if (lane >= o) v += t;
                     }
-                    mw[h] = acc + s2;
-                    acc += __shfl_sync(0xffffffffu, s2, 31);
+                    int m = acc + v;
+                    acc += __shfl_sync(0xffffffffu, v, 31);
+                    if (w < nw) {
+                        uint4 rc = winrec[w];
+#pragma unroll
+                        for (int r = 0; r < 4; r++) cnt[r] += rec_serr(rc, (m + r) & 3);
+                    }
                 }
-                s_ma[lane] = mw[0];
-                s_ma[lane + 32] = mw[1];
-            }
-            __syncthreads();
-            int cnt[4] = {0, 0, 0, 0};
-            for (int s = tid; s < p.amb_syms; s += kDemapThreads) {
-                uint8_t dv = dec[s];
-                int aI, aQ;
-                tx_sym(prbs, g.pay_lo + s, p.bps, true, aI, aQ);
-                for (int r = 0; r < 4; r++) {
-                    int LI = dv & 7, LQ = (dv >> 3) & 7;
-                    rot_levels(LI, LQ, (int)((s_ma[s / kWin] + r) & 3), p.mq);
-                    cnt[r] += (LI != aI) || (LQ != aQ);
-                }
-            }
-            for (int r = 0; r < 4; r++) {
-                int v = warp_sum_i(cnt[r]);
-                if (lane == 0) s_red[wid][r] = v;
-            }
-            __syncthreads();
-            if (tid == 0) {
                 int best = 0;
-                long long bc = -1;
+                unsigned bc = 0;
+#pragma unroll
                 for (int r = 0; r < 4; r++) {
-                    long long c = 0;
-                    for (int i = 0; i < kDemapThreads / 32; i++) c += s_red[i][r];
-                    if (bc < 0 || c < bc) { bc = c; best = r; }
+                    unsigned c = warp_sum_i(cnt[r]);
+                    if (r == 0 || c < bc) { bc = c; best = r; }
                 }
-                s_r = best;
-                if (blockIdx.x == 0) dst->amb_r = best;
+                if (tid == 0) {
+                    s_r = best;
+                    if (blockIdx.x == 0) dst->amb_r = best;
+                }
             }
         } else if (tid == 0) {
             s_r = dst->amb_r;
@@ -505,78 +629,54 @@ __global__ void __launch_bounds__(kDemapThreads)
     }
     __syncthreads();
     const int r = QAM ? s_r : 0;
-    const int nb = QAM ? p.bps / 2 : p.bps;
     const long long amb_end = QAM ? (long long)p.ntrain + p.amb_syms : 0;
-    // one warp per window, two symbols per lane
-    for (int wi = w0 + wid; wi < wend; wi += kDemapThreads / 32) {
+    constexpr int NBYTES = 8 * BPS;   // 64 symbols * BPS bits / 8
+    for (int wi = w0 + wid; wi < wend; wi += NW) {
         long long k0 = g.pay_lo + (long long)wi * kWin;
         long long mw = QAM ? s_m[wi - w0] : 0;
+        int qd = (int)((mw + r) & 3);
         if (dbg_win && lane == 0 && QAM) dbg_win[wi].y = (float)mw;
-        if (lane < 8) s_bits[wid][lane] = 0u;
-        __syncwarp();
-        int ah[2][2], ref[2], nr = 0;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             int q = lane + 32 * h;
             uint8_t dv = dec[(k0 - g.pay_lo) + q];
             int LI = dv & 7, LQ = QAM ? ((dv >> 3) & 7) : 0;
-            nr += (dv >> 6) & 1;
-            if (QAM) rot_levels(LI, LQ, (int)((mw + r) & 3), p.mq);
-            ah[h][0] = LI;
-            ah[h][1] = LQ;
-            int grp = QAM ? ((gray(LI) << nb) | gray(LQ)) : gray(LI);
-            // output bits, MSB first, at bit offset q * bps of the window
-            int bo = q * p.bps;
-            for (int t = 0; t < p.bps; t++) {
-                int bit = (grp >> (p.bps - 1 - t)) & 1;
-                int pos = bo + t;
-                if (bit) atomicOr(&s_bits[wid][pos >> 5], 1u << (31 - (pos & 31)));
-            }
-            long long kk = k0 + q, b0 = (long long)p.bps * kk;
-            int rg = 0;
-            for (int t = 0; t < p.bps; t++) rg = (rg << 1) | prbs[(b0 + t) % 32767];
-            ref[h] = rg;
+            if (QAM) rot_t<MQ>(LI, LQ, qd);
+            s_grp[wid][q] = (uint8_t)(QAM ? ((gray(LI) << NB) | gray(LQ)) : gray(LI));
         }
         __syncwarp();
-        int nbytes = 8 * p.bps;   // 64 symbols * bps bits / 8
-        if (lane < nbytes) {
-            uint32_t wv = s_bits[wid][lane >> 2];
-            bits_out[(long long)wi * nbytes + lane] = (uint8_t)(wv >> (24 - 8 * (lane & 3)));
-        }
-        bool counted = !(QAM && k0 < amb_end);
-        if (counted) {
-            int nrot = QAM ? 4 : 1;
-            int errs[4] = {0, 0, 0, 0}, serr[4] = {0, 0, 0, 0};
-            for (int rho = 0; rho < nrot; rho++) {
+        // output bytes, MSB first: byte b holds bits [8b, 8b+8) of the window
+        if (lane < NBYTES) {
+            int byte = 0;
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    int LI = ah[h][0], LQ = ah[h][1];
-                    if (QAM) rot_levels(LI, LQ, rho, p.mq);
-                    int grp = QAM ? ((gray(LI) << nb) | gray(LQ)) : gray(LI);
-                    int ne = __popc(grp ^ ref[h]);
-                    errs[rho] += ne;
-                    serr[rho] += ne > 0;
-                }
+            for (int t = 0; t < 8; t++) {
+                int bit = 8 * lane + t, q = bit / BPS, o = bit - q * BPS;
+                byte = (byte << 1) | ((s_grp[wid][q] >> (BPS - 1 - o)) & 1);
             }
-            for (int rho = 0; rho < nrot; rho++) {
-                errs[rho] = warp_sum_i(errs[rho]);
-                serr[rho] = warp_sum_i(serr[rho]);
-            }
-            nr = warp_sum_i(nr);
-            if (lane == 0) {
+            bits_out[(long long)wi * NBYTES + lane] = (uint8_t)byte;
+        }
+        if (lane == 0) {
+            uint4 rc = winrec[wi];
+            if (!(QAM && k0 < amb_end)) {
                 int best = 0;
-                for (int rho = 1; rho < nrot; rho++)
-                    if (errs[rho] < errs[best]) best = rho;
-                atomicAdd(&s_cnt[C_BITERR], (unsigned long long)errs[best]);
-                atomicAdd(&s_cnt[C_RAWERR], (unsigned long long)errs[0]);
-                atomicAdd(&s_cnt[C_SYMERR], (unsigned long long)serr[best]);
+                unsigned be = rec_err(rc, qd);
+#pragma unroll
+                for (int rho = 1; rho < (QAM ? 4 : 1); rho++) {
+                    unsigned e = rec_err(rc, (qd + rho) & 3);
+                    if (e < be) { be = e; best = rho; }
+                }
+                int qb = (qd + best) & 3;
+                atomicAdd(&s_cnt[C_BITERR], (unsigned long long)be);
+                atomicAdd(&s_cnt[C_RAWERR], (unsigned long long)rec_err(rc, qd));
+                atomicAdd(&s_cnt[C_SYMERR], (unsigned long long)rec_serr(rc, qb));
                 atomicAdd(&s_cnt[C_SLIP], (unsigned long long)(best != 0));
-                atomicAdd(&s_cnt[C_NEAR], (unsigned long long)nr);
-                atomicAdd(&s_cnt[C_BITS], (unsigned long long)(p.bps * kWin));
+                atomicAdd(&s_cnt[C_NEAR], (unsigned long long)(rc.w >> 8));
+                atomicAdd(&s_cnt[C_BITS], (unsigned long long)(BPS * kWin));
                 atomicAdd(&s_cnt[C_SYMBOLS], (unsigned long long)kWin);
             }
+            atomicAdd(&s_cnt[C_WINDOWS], 1ull);
         }
-        if (lane == 0) atomicAdd(&s_cnt[C_WINDOWS], 1ull);
+        __syncwarp();
     }
     __syncthreads();
     if (tid < C_NCNT && s_cnt[tid]) atomicAdd(&dst->cnt[tid], s_cnt[tid]);
@@ -590,16 +690,19 @@ __global__ void __launch_bounds__(kDemapThreads)
 }
 
 cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in, const uint8_t *dec,
-                         const uint8_t *winb, float4 *dbg_win, const uint8_t *prbs, uint8_t *bits_out,
+                         const uint8_t *winb, const uint4 *winrec, float4 *dbg_win, uint8_t *bits_out,
                          DevState *dst, cudaStream_t st)
 {
     unsigned grid = (unsigned)((g.nwin + kDemapWin - 1) / kDemapWin);
-    if (p.kk)
-        k_demap<true><<<grid, kDemapThreads, 0, st>>>(p, g, resolve_amb, uw_in, dec, winb, dbg_win, prbs,
-                                                      bits_out, dst);
-    else
-        k_demap<false><<<grid, kDemapThreads, 0, st>>>(p, g, resolve_amb, uw_in, dec, winb, dbg_win, prbs,
-                                                       bits_out, dst);
+#define RX_DEMAP(Q, B, M)                                                                                   \
+    k_demap<Q, B, M><<<grid, kDemapThreads, 0, st>>>(p, g, resolve_amb, uw_in, dec, winb, winrec, dbg_win,  \
+                                                     bits_out, dst)
+    if (p.kk && p.mq == 4) RX_DEMAP(true, 4, 4);
+    else if (p.kk) RX_DEMAP(true, 2, 2);
+    else if (p.mq == 2) RX_DEMAP(false, 1, 2);
+    else if (p.mq == 4) RX_DEMAP(false, 2, 4);
+    else RX_DEMAP(false, 3, 8);
+#undef RX_DEMAP
     return cudaGetLastError();
 }
 

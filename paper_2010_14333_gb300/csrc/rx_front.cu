@@ -128,39 +128,153 @@ __device__ __forceinline__ void ols_kept(const KkGeom &g, int j, int &t_lo, int 
 }
 
 // u = ln(I)/2 - ln(2048)/2 (the constant is annihilated by the Hilbert transform
-// and only keeps the FP32 FFT well scaled); I = code, 0.5 for code 0
-__device__ __forceinline__ float kk_u(uint16_t code)
+// and only keeps the FP32 FFT well scaled) and sqrt(I), I = code (0.5 for code 0):
+// the codes are 12-bit, so both are exact lookup tables computed in double.
+static int tw_split(int M)
 {
-    float I = code ? (float)code : 0.5f;
-    return 0.5f * logf(I * (1.0f / 2048.0f));
+    int m = 0;
+    while ((1 << m) < M) m++;
+    return (m + 1) / 2;
+}
+int kk_tw_entries(int M) { return (1 << tw_split(M)) + M / (1 << tw_split(M)); }
+
+static void factored_twiddles(int M, float2 *out)
+{
+    const double pi = 3.14159265358979323846;
+    int s = tw_split(M), lo = 1 << s, hi = M / lo;
+    for (int a = 0; a < lo; a++) {
+        double t = -2.0 * pi * (double)a / (double)M;
+        out[a] = make_float2((float)cos(t), (float)sin(t));
+    }
+    for (int a = 0; a < hi; a++) {
+        double t = -2.0 * pi * (double)a * (double)lo / (double)M;
+        out[lo + a] = make_float2((float)cos(t), (float)sin(t));
+    }
 }
 
-// K1a: radix-16 pass over the stride-N2 index of two packed blocks, then twiddle.
-__global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, const uint16_t *__restrict__ codes,
-                                                  float2 *__restrict__ fftws, const float2 *__restrict__ twN)
+void kk_host_tables(int N, float *lnt, float *sqt, float2 *twN, float2 *twN2)
 {
+    for (int c = 0; c < kLutCodes; c++) {
+        double I = c ? (double)c : 0.5;
+        lnt[c] = (float)(0.5 * log(I / 2048.0));
+        sqt[c] = (float)sqrt(I);
+    }
+    factored_twiddles(N, twN);
+    factored_twiddles(N / 16, twN2);
+}
+
+// factored twiddle table staged in shared memory
+struct TwSmem {
+    const float2 *lo, *hi;
+    int s, mask;
+    __device__ __forceinline__ float2 operator()(int a) const { return cmul(hi[a >> s], lo[a & mask]); }
+};
+__device__ __forceinline__ TwSmem stage_tw(const float2 *__restrict__ gtab, int M, float2 *sm)
+{
+    int m = 31 - __clz(M);
+    int s = (m + 1) / 2, lo = 1 << s, n = lo + (M >> s);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = __ldg(gtab + i);
+    TwSmem t;
+    t.lo = sm;
+    t.hi = sm + lo;
+    t.s = s;
+    t.mask = lo - 1;
+    return t;
+}
+
+// Packed 12-bit input of the KK front end, read directly (the unpack is fused):
+// stream sample n lives at byte 1.5 (n - cbase) of the virtual buffer
+// [history (the nhist samples before this buffer) | this buffer].  A CTA covers
+// 256 columns of a block pair; its 32 rows (2 blocks x 16 radix-16 rows) are 256
+// consecutive samples each, whose 384 bytes start on a 48-byte boundary and are
+// staged into shared memory with 16-byte loads.
+struct KkPacked {
+    const uint8_t *hist;   // packed history (nhist samples)
+    const uint8_t *in;     // this buffer
+    uint8_t *hist_next;    // history of the next call, or null
+    long long hist_bytes;  // nhist * 3 / 2
+    long long in_bytes;    // buf_len * 3 / 2
+    int order, first_call;
+};
+constexpr int kRawWords = 100;   // 384 bytes of a row + spare word, 16-byte multiple
+
+__device__ __forceinline__ void stage_rows(const KkGeom &g, const KkPacked &pk, int pair, int c0,
+                                           uint32_t (*raw)[kRawWords], bool hb)
+{
+    for (int i = threadIdx.x; i < 32 * 24; i += blockDim.x) {
+        int row = i / 24, ch = i - 24 * (i / 24), blk = row >> 4, q = row & 15;
+        if (blk && !hb) continue;
+        long long n = ols_ws(g, 2 * pair + blk) + c0 + (long long)g.N2 * q;
+        long long vb = (n - g.cbase) * 3 / 2 + 16 * ch;   // >= 0 for every window of the call
+        const uint8_t *src = vb < pk.hist_bytes ? pk.hist + vb : pk.in + (vb - pk.hist_bytes);
+        *reinterpret_cast<uint4 *>(&raw[row][4 * ch]) = __ldg(reinterpret_cast<const uint4 *>(src));
+    }
+}
+
+// 12-bit code of column t of a staged row (two samples per three bytes)
+__device__ __forceinline__ uint32_t decode_col(const uint32_t *rw, int t, int order)
+{
+    int b = (3 * t) >> 1;
+    uint32_t v = __funnelshift_r(rw[b >> 2], rw[(b >> 2) + 1], 8 * (b & 3));
+    uint32_t lo = v & 0xFFu, hi = (v >> 8) & 0xFFu;
+    if (order == 0) return (t & 1) ? ((lo >> 4) | (hi << 4)) : (lo | ((hi & 0xFu) << 8));
+    return (t & 1) ? (((lo & 0xFu) << 8) | hi) : ((lo << 4) | (hi >> 4));
+}
+
+__device__ __forceinline__ uint32_t first_code(const KkPacked &pk, const DevState *dst)
+{
+    if (!pk.first_call) return (uint32_t)dst->first_code;
+    uint32_t a, b;
+    decode_pair(pk.in[0], pk.in[1], pk.in[2], pk.order, a, b);
+    return a;
+}
+
+// K1a: unpack, u = ln(I)/2 by table, radix-16 pass over the stride-N2 index of two
+// packed blocks, twiddle.  CTAs with blockIdx.y == npairs copy the next history.
+__global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2 *__restrict__ fftws,
+                                                  const KkTables tb, DevState *dst)
+{
+    __shared__ float2 s_tw[512];
+    __shared__ __align__(16) uint32_t raw[32][kRawWords];
     int pair = blockIdx.y;
-    int n1 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n1 >= g.N2) return;
-    int ja = 2 * pair, jb = 2 * pair + 1;
-    long long oa = ols_ws(g, ja) - g.cbase;
-    bool hb = jb < g.J;
-    long long ob = hb ? ols_ws(g, jb) - g.cbase : 0;
+    if (pair == g.npairs) {
+        // history of the next call: samples [avail - nhist, avail) = virtual bytes
+        // [in_bytes, in_bytes + hist_bytes)
+        long long nch = pk.hist_bytes / 16;
+        for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += (long long)gridDim.x * blockDim.x) {
+            long long vb = pk.in_bytes + 16 * c;
+            const uint8_t *src = vb < pk.hist_bytes ? pk.hist + vb : pk.in + (vb - pk.hist_bytes);
+            reinterpret_cast<uint4 *>(pk.hist_next)[c] = __ldg(reinterpret_cast<const uint4 *>(src));
+        }
+        return;
+    }
+    const TwSmem tw = stage_tw(tb.twN, g.N, s_tw);
+    const int c0 = blockIdx.x * blockDim.x;
+    const int jb = 2 * pair + 1;
+    const bool hb = jb < g.J;
+    stage_rows(g, pk, pair, c0, raw, hb);
+    const uint32_t c_first = first_code(pk, dst);
+    if (pk.first_call && blockIdx.x == 0 && pair == 0 && threadIdx.x == 0) dst->first_code = (int)c_first;
+    __syncthreads();
+    const int t = threadIdx.x, n1 = c0 + t;
+    const long long wa = ols_ws(g, 2 * pair) + c0 + t, wb = hb ? ols_ws(g, jb) + c0 + t : 0;
     float2 x[16];
 #pragma unroll
     for (int q = 0; q < 16; q++) {
-        long long t = n1 + (long long)g.N2 * q;
-        float ua = kk_u(__ldg(codes + oa + t));
-        float ub = hb ? kk_u(__ldg(codes + ob + t)) : 0.f;
+        long long na = wa + (long long)g.N2 * q;
+        uint32_t ca = na < 0 ? c_first : decode_col(raw[q], t, pk.order);
+        float ua = __ldg(tb.lnt + ca), ub = 0.f;
+        if (hb) {
+            long long nb2 = wb + (long long)g.N2 * q;
+            uint32_t cb = nb2 < 0 ? c_first : decode_col(raw[16 + q], t, pk.order);
+            ub = __ldg(tb.lnt + cb);
+        }
         x[q] = make_float2(ua, ub);
     }
     dft16<false>(x);
     float2 *out = fftws + (size_t)pair * g.N + n1;
 #pragma unroll
-    for (int k2 = 0; k2 < 16; k2++) {
-        float2 w = __ldg(twN + n1 * k2);
-        out[(size_t)k2 * g.N2] = cmul(x[k2], w);
-    }
+    for (int k2 = 0; k2 < 16; k2++) out[(size_t)k2 * g.N2] = k2 ? cmul(x[k2], tw(n1 * k2)) : x[0];
 }
 
 // digit reversal of a P-digit base-16 index
@@ -184,14 +298,17 @@ __device__ __forceinline__ float2 hilbert_mul(float2 v, int k, int N)
 // frequency, digit-reversed output), Hilbert multiplier on the bins k = k2 + 16 k1,
 // inverse FFT (radix-16 decimation in time back to natural order).  In place.
 template <int P>
-__global__ void __launch_bounds__(256) k_kk_rows(KkGeom g, float2 *__restrict__ fftws,
-                                                const float2 *__restrict__ twN2)
+__global__ void __launch_bounds__(256, 3) k_kk_rows(KkGeom g, float2 *__restrict__ fftws,
+                                                   const float2 *__restrict__ twN2g)
 {
     constexpr int N2 = 1 << (4 * P);
     constexpr int TPR = N2 / 16;                  // threads per row
     constexpr int RPC = 256 / TPR;                // rows per CTA
     constexpr int SROW = N2 + N2 / 16;            // padded row in shared memory
     extern __shared__ float2 sm[];
+    __shared__ float2 s_tw[128];
+    const TwSmem tw2 = stage_tw(twN2g, N2, s_tw);
+    __syncthreads();
     int lr = threadIdx.x / TPR, t = threadIdx.x % TPR;
     int row = blockIdx.x * RPC + lr;
     bool active = row < g.npairs * 16;
@@ -204,7 +321,7 @@ __global__ void __launch_bounds__(256) k_kk_rows(KkGeom g, float2 *__restrict__ 
     for (int r = 0; r < 16; r++) x[r] = active ? d[t + r * TPR] : make_float2(0.f, 0.f);
     dft16<false>(x);
 #pragma unroll
-    for (int r = 1; r < 16; r++) x[r] = cmul(x[r], __ldg(twN2 + ((t * r) & (N2 - 1))));
+    for (int r = 1; r < 16; r++) x[r] = cmul(x[r], tw2(t * r));
     if (P == 1) {
 #pragma unroll
         for (int r = 0; r < 16; r++) x[r] = hilbert_mul(x[r], k2 + 16 * drev16<P>(r), g.N);
@@ -228,7 +345,7 @@ __global__ void __launch_bounds__(256) k_kk_rows(KkGeom g, float2 *__restrict__ 
         dft16<false>(x);
         if (p < P - 1) {
 #pragma unroll
-            for (int r = 1; r < 16; r++) x[r] = cmul(x[r], __ldg(twN2 + ((j * r * (N2 / M)) & (N2 - 1))));
+            for (int r = 1; r < 16; r++) x[r] = cmul(x[r], tw2(j * r * (N2 / M)));
 #pragma unroll
             for (int r = 0; r < 16; r++) s[pad16(o + j + r * sub)] = x[r];
             __syncthreads();
@@ -250,7 +367,7 @@ __global__ void __launch_bounds__(256) k_kk_rows(KkGeom g, float2 *__restrict__ 
 #pragma unroll
         for (int r = 0; r < 16; r++) {
             x[r] = s[pad16(o + j + r * sub)];
-            if (r) x[r] = cmulc(x[r], __ldg(twN2 + ((j * r * (N2 / M)) & (N2 - 1))));
+            if (r) x[r] = cmulc(x[r], tw2(j * r * (N2 / M)));
         }
         dft16<true>(x);
 #pragma unroll
@@ -261,7 +378,7 @@ __global__ void __launch_bounds__(256) k_kk_rows(KkGeom g, float2 *__restrict__ 
 #pragma unroll
     for (int r = 0; r < 16; r++) {
         x[r] = s[pad16(t + r * TPR)];
-        if (r) x[r] = cmulc(x[r], __ldg(twN2 + ((t * r) & (N2 - 1))));
+        if (r) x[r] = cmulc(x[r], tw2(t * r));
     }
     dft16<true>(x);
     if (active)
@@ -272,15 +389,20 @@ __global__ void __launch_bounds__(256) k_kk_rows(KkGeom g, float2 *__restrict__ 
 // K1c: inverse radix-16 pass, then for every kept output
 // E = sqrt(I) * exp(j phi) (Fig. 1d), written at its stream position, and the
 // per-call carrier / intensity sums (deterministic: fixed-order trees, last-CTA
-// finalisation in FP64).
-__global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, const uint16_t *__restrict__ codes,
-                                                  const float2 *__restrict__ fftws,
-                                                  const float2 *__restrict__ twN, float2 *__restrict__ E,
+// finalisation in FP64).  The codes for sqrt(I) come from the same staged rows.
+__global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const float2 *__restrict__ fftws,
+                                                  const KkTables tb, float2 *__restrict__ E,
                                                   const float2 *__restrict__ E_prev,
                                                   CarrierPartial *__restrict__ partials, DevState *dst)
 {
+    __shared__ float2 s_tw[512];
+    __shared__ __align__(16) uint32_t raw[32][kRawWords];
+    const TwSmem tw = stage_tw(tb.twN, g.N, s_tw);
     int pair = blockIdx.y;
-    int n1 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c0 = blockIdx.x * blockDim.x;
+    const bool hb = 2 * pair + 1 < g.J;
+    stage_rows(g, pk, pair, c0, raw, hb);
+    const uint32_t c_first = first_code(pk, dst);
     float sre = 0.f, sim = 0.f;
     int si2 = 0;
     if (blockIdx.x == 0 && blockIdx.y == 0) {
@@ -290,37 +412,38 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, const uint16_t *__r
             E[i] = (n < 0) ? make_float2(0.f, 0.f) : E_prev[n - g.ebase_prev];
         }
     }
-    if (n1 < g.N2) {
-        float2 x[16];
-        const float2 *in = fftws + (size_t)pair * g.N + n1;
+    const int t = threadIdx.x, n1 = c0 + t;
+    float2 x[16];
+    const float2 *in = fftws + (size_t)pair * g.N + n1;
 #pragma unroll
-        for (int k2 = 0; k2 < 16; k2++) x[k2] = cmulc(in[(size_t)k2 * g.N2], __ldg(twN + n1 * k2));
-        dft16<true>(x);
-        const float invN = 1.0f / (float)g.N;
+    for (int k2 = 0; k2 < 16; k2++) x[k2] = in[(size_t)k2 * g.N2];
+    __syncthreads();   // staged twiddles and rows
 #pragma unroll
-        for (int half = 0; half < 2; half++) {
-            int j = 2 * pair + half;
-            if (j >= g.J) break;
-            long long ws = ols_ws(g, j);
-            int tlo, thi;
-            ols_kept(g, j, tlo, thi);
+    for (int k2 = 1; k2 < 16; k2++) x[k2] = cmulc(x[k2], tw(n1 * k2));
+    dft16<true>(x);
+    const float invN = 1.0f / (float)g.N;
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-                int t = n1 + g.N2 * q;
-                if (t < tlo || t >= thi) continue;
-                long long n = ws + t;
-                uint16_t code = __ldg(codes + (n - g.cbase));
-                float I = code ? (float)code : 0.5f;
-                float phi = (half ? x[q].y : x[q].x) * invN;
-                float sn, cs;
-                sincosf(phi, &sn, &cs);
-                float A = sqrtf(I);
-                float2 e = make_float2(A * cs, A * sn);
-                E[n - g.ebase] = e;
-                sre += e.x;
-                sim += e.y;
-                si2 += code ? 2 * (int)code : 1;
-            }
+    for (int half = 0; half < 2; half++) {
+        int j = 2 * pair + half;
+        if (j >= g.J) break;
+        long long ws = ols_ws(g, j);
+        int tlo, thi;
+        ols_kept(g, j, tlo, thi);
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            int tt = n1 + g.N2 * q;
+            if (tt < tlo || tt >= thi) continue;
+            long long n = ws + tt;
+            uint32_t code = n < 0 ? c_first : decode_col(raw[16 * half + q], t, pk.order);
+            float phi = (half ? x[q].y : x[q].x) * invN;
+            float sn, cs;
+            __sincosf(phi, &sn, &cs);   // |phi| < pi: absolute error <= 2^-21.41
+            float A = __ldg(tb.sqt + code);
+            float2 e = make_float2(A * cs, A * sn);
+            E[n - g.ebase] = e;
+            sre += e.x;
+            sim += e.y;
+            si2 += code ? 2 * (int)code : 1;
         }
     }
     // CTA partial (fixed-order tree)
@@ -384,26 +507,59 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, const uint16_t *__r
     }
 }
 
-cudaError_t launch_kk_front(const KkGeom &g, const uint16_t *codes, float2 *fftws,
-                            const float2 *twN, const float2 *twN2, float2 *E, const float2 *E_prev,
-                            CarrierPartial *partials, DevState *dst, cudaStream_t st, void *prof)
+__global__ void k_kk_hist(KkPacked pk)
 {
-    dim3 grid((g.N2 + kCtaK1 - 1) / kCtaK1, g.npairs);
+    long long nch = pk.hist_bytes / 16;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += (long long)gridDim.x * blockDim.x) {
+        long long vb = pk.in_bytes + 16 * c;
+        const uint8_t *src = vb < pk.hist_bytes ? pk.hist + vb : pk.in + (vb - pk.hist_bytes);
+        reinterpret_cast<uint4 *>(pk.hist_next)[c] = __ldg(reinterpret_cast<const uint4 *>(src));
+    }
+}
+
+cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st)
+{
+    KkPacked pk;
+    pk.hist = inp.hist;
+    pk.in = inp.in;
+    pk.hist_next = inp.hist_next;
+    pk.hist_bytes = inp.hist_bytes;
+    pk.in_bytes = inp.in_bytes;
+    pk.order = inp.order;
+    pk.first_call = inp.first_call;
+    k_kk_hist<<<32, 256, 0, st>>>(pk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, const KkTables &tb,
+                            float2 *E, const float2 *E_prev, CarrierPartial *partials, DevState *dst,
+                            cudaStream_t st, void *prof)
+{
+    KkPacked pk;
+    pk.hist = inp.hist;
+    pk.in = inp.in;
+    pk.hist_next = inp.hist_next;
+    pk.hist_bytes = inp.hist_bytes;
+    pk.in_bytes = inp.in_bytes;
+    pk.order = inp.order;
+    pk.first_call = inp.first_call;
+    dim3 grid(g.N2 / kCtaK1, g.npairs);
+    dim3 grid_a(g.N2 / kCtaK1, g.npairs + (inp.hist_next ? 1 : 0));
     prof_stage(prof, 1, st);
-    k_kk_fwd<<<grid, kCtaK1, 0, st>>>(g, codes, fftws, twN);
+    k_kk_fwd<<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
     prof_stage(prof, 2, st);
     int rows = g.npairs * 16;
     if (g.N2 == 4096) {
         size_t smem = (size_t)(4096 + 256) * sizeof(float2);
-        k_kk_rows<3><<<rows, 256, smem, st>>>(g, fftws, twN2);
+        k_kk_rows<3><<<rows, 256, smem, st>>>(g, fftws, tb.twN2);
     } else if (g.N2 == 256) {
         size_t smem = (size_t)16 * (256 + 16) * sizeof(float2);
-        k_kk_rows<2><<<(rows + 15) / 16, 256, smem, st>>>(g, fftws, twN2);
+        k_kk_rows<2><<<(rows + 15) / 16, 256, smem, st>>>(g, fftws, tb.twN2);
     } else {
-        k_kk_rows<1><<<(rows + 255) / 256, 256, 0, st>>>(g, fftws, twN2);
+        k_kk_rows<1><<<(rows + 255) / 256, 256, 0, st>>>(g, fftws, tb.twN2);
     }
     prof_stage(prof, 3, st);
-    k_kk_inv<<<grid, kCtaK1, 0, st>>>(g, codes, fftws, twN, E, E_prev, partials, dst);
+    k_kk_inv<<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, partials, dst);
     return cudaGetLastError();
 }
 
@@ -453,12 +609,120 @@ __global__ void __launch_bounds__(kMfOut) k_kk_mf(const float2 *__restrict__ E, 
     Y[m - ybase] = make_float2(gn * ar, gn * ai);
 }
 
+// Register-tiled form for a compile-time half length HMF (even).  With the tile
+// starting at n0 = 2 m0 - HMF, the pairs P[p] = (x[n0 + 2p], x[n0 + 2p + 1])
+// turn the decimating filter into two plain FIRs over the pair index:
+//   y[m0 + j] = g * sum_{u=0..HMF} (ge[u] P[j+u].first + go[u] P[j+u].second)
+// with ge[u] = h[HMF - 2u], go[u] = h[HMF - 2u - 1].  Each thread computes 8
+// consecutive outputs from a sliding window of 8 pairs held in registers (one
+// 16-byte shared load per tap); the pair layout keeps one spare slot per 8 pairs,
+// which makes the stride-8-pair loads of a warp free of bank conflicts.
+template <int HMF>
+struct MfTaps {
+    float ge[HMF + 1];
+    float go[HMF];
+};
+
+constexpr int kMfThreads = 128, kMfR = 8, kMfTileOut = kMfThreads * kMfR;
+__host__ __device__ __forceinline__ int pad8(int p) { return p + (p >> 3); }
+
+template <int HMF>
+__global__ void __launch_bounds__(kMfThreads) k_kk_mf_t(const float2 *__restrict__ E, long long ebase,
+                                                       long long e_k, long long f_prev, long long f_k,
+                                                       const MfTaps<HMF> taps, const float2 *__restrict__ ds_tab,
+                                                       int ds_num, int ds_den, const DevState *__restrict__ dst,
+                                                       float2 *__restrict__ Y, long long ybase,
+                                                       const float2 *__restrict__ Y_prev, long long ybase_prev)
+{
+    constexpr int NPAIR = kMfTileOut + HMF + kMfR;
+    extern __shared__ float4 pr[];     // padded pair tile
+    long long m0 = f_prev + (long long)blockIdx.x * kMfTileOut;
+    long long n0 = 2 * m0 - HMF;
+    const float2 c = make_float2((float)dst->carrier_re, (float)dst->carrier_im);
+    const float gn = (float)dst->gain;
+    // integer phase index of the downshift, advanced incrementally
+    int idx = (int)((((n0 % ds_den) + ds_den) % ds_den + 2LL * threadIdx.x) % ds_den);
+    idx = (int)(((long long)idx * ds_num) % ds_den);
+    const int step = (int)((2LL * kMfThreads * ds_num) % ds_den), odd = ds_num % ds_den;
+    for (int pp = threadIdx.x; pp < NPAIR; pp += kMfThreads) {
+        long long n = n0 + 2 * pp;
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (n >= 0 && n < e_k) a = cmul(csub(E[n - ebase], c), __ldg(ds_tab + idx));
+        int idx1 = idx + odd;
+        idx1 = idx1 >= ds_den ? idx1 - ds_den : idx1;
+        if (n + 1 >= 0 && n + 1 < e_k) b = cmul(csub(E[n + 1 - ebase], c), __ldg(ds_tab + idx1));
+        pr[pad8(pp)] = make_float4(a.x, a.y, b.x, b.y);
+        idx += step;
+        idx = idx >= ds_den ? idx - ds_den : idx;
+    }
+    if (blockIdx.x == 0) {
+        for (long long m = ybase + threadIdx.x; m < f_prev; m += blockDim.x)
+            Y[m - ybase] = (m < 0) ? make_float2(0.f, 0.f) : Y_prev[m - ybase_prev];
+    }
+    __syncthreads();
+    const int j0 = kMfR * threadIdx.x;
+    float4 win[kMfR];
+#pragma unroll
+    for (int r = 0; r < kMfR; r++) win[r] = pr[pad8(j0 + r)];
+    float ar[kMfR], ai[kMfR];
+#pragma unroll
+    for (int r = 0; r < kMfR; r++) ar[r] = ai[r] = 0.f;
+#pragma unroll
+    for (int u = 0; u <= HMF; u++) {
+        const float he = taps.ge[u];
+#pragma unroll
+        for (int r = 0; r < kMfR; r++) {
+            ar[r] = fmaf(he, win[r].x, ar[r]);
+            ai[r] = fmaf(he, win[r].y, ai[r]);
+        }
+        if (u < HMF) {
+            const float ho = taps.go[u];
+#pragma unroll
+            for (int r = 0; r < kMfR; r++) {
+                ar[r] = fmaf(ho, win[r].z, ar[r]);
+                ai[r] = fmaf(ho, win[r].w, ai[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < kMfR - 1; r++) win[r] = win[r + 1];
+            win[kMfR - 1] = pr[pad8(j0 + u + kMfR)];
+        }
+    }
+    long long mb = m0 + j0;
+    if (mb + kMfR <= f_k) {
+        float4 *o = reinterpret_cast<float4 *>(Y + (mb - ybase));
+        bool al = (((uintptr_t)o) & 15) == 0;
+        if (al) {
+#pragma unroll
+            for (int r = 0; r < kMfR; r += 2)
+                o[r / 2] = make_float4(gn * ar[r], gn * ai[r], gn * ar[r + 1], gn * ai[r + 1]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < kMfR; r++) Y[mb + r - ybase] = make_float2(gn * ar[r], gn * ai[r]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < kMfR; r++)
+            if (mb + r < f_k) Y[mb + r - ybase] = make_float2(gn * ar[r], gn * ai[r]);
+    }
+}
+
 cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long long f_prev,
                          long long f_k, const float *rrc, int hmf, const float2 *ds_tab,
                          int ds_num, int ds_den, const DevState *dst, float2 *Y, long long ybase,
-                         const float2 *Y_prev, long long ybase_prev, cudaStream_t st)
+                         const float2 *Y_prev, long long ybase_prev, cudaStream_t st,
+                         const float *rrc_host)
 {
     long long n = f_k - f_prev;
+    if (hmf == 32 && rrc_host) {
+        MfTaps<32> t;
+        for (int u = 0; u <= 32; u++) t.ge[u] = rrc_host[32 + (32 - 2 * u)];
+        for (int u = 0; u < 32; u++) t.go[u] = rrc_host[32 + (32 - 2 * u - 1)];
+        unsigned grid = (unsigned)((n + kMfTileOut - 1) / kMfTileOut);
+        size_t smem = (size_t)pad8(kMfTileOut + 32 + kMfR) * sizeof(float4) + 16;
+        k_kk_mf_t<32><<<grid, kMfThreads, smem, st>>>(E, ebase, e_k, f_prev, f_k, t, ds_tab, ds_num, ds_den, dst,
+                                                      Y, ybase, Y_prev, ybase_prev);
+        return cudaGetLastError();
+    }
     unsigned grid = (unsigned)((n + kMfOut - 1) / kMfOut);
     size_t smem = (size_t)(2 * kMfOut + 2 * hmf) * sizeof(float2);
     k_kk_mf<<<grid, kMfOut, smem, st>>>(E, ebase, e_k, f_prev, f_k, rrc, hmf, ds_tab, ds_num,

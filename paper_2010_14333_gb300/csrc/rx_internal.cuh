@@ -30,6 +30,7 @@ struct DevState {
     int unwrap_have[2], unwrap_b[2];       // pi/2 unwrap carry, by parity
     long long unwrap_m[2];
     int amb_r;                             // stream-start rotation, -1 before
+    int first_code;                        // 12-bit code of the stream's first sample
     unsigned int ticket;                   // last-CTA ticket of the carrier reduction
     int err;                               // RX_ETIMEOUT when a bounded wait ran out
 };
@@ -50,6 +51,30 @@ struct KkGeom {
     long long ebase_prev;      // same for the previous field workspace
     int N, V, hop, J, npairs, N2;
     int sps;
+};
+
+// constant tables of the KK front end (device pointers).  Twiddles of an M-point
+// transform are factored W_M^a = hi[a >> s] * lo[a & (2^s - 1)], s = ceil(log2(M)/2),
+// stored as [lo (2^s) | hi (M / 2^s)].
+struct KkTables {
+    const float *lnt;      // 4096: ln(I)/2 - ln(2048)/2, I = code (0.5 for code 0)
+    const float *sqt;      // 4096: sqrt(I)
+    const float2 *twN;     // factored W_N
+    const float2 *twN2;    // factored W_{N/16}
+};
+constexpr int kLutCodes = 4096;
+// number of float2 entries of the factored table of an M-point transform
+int kk_tw_entries(int M);
+// host: fill the tables of a KK front end with FFT length N
+void kk_host_tables(int N, float *lnt, float *sqt, float2 *twN, float2 *twN2);
+
+// packed input of one KK call
+struct KkInput {
+    const uint8_t *hist;     // packed samples [base - nhist, base)
+    const uint8_t *in;       // packed buffer
+    uint8_t *hist_next;      // receives packed samples [avail - nhist, avail), or null
+    long long hist_bytes, in_bytes;
+    int order, first_call;
 };
 
 // per-call schedule of the equaliser
@@ -73,16 +98,20 @@ cudaError_t launch_unpack(const uint8_t *in, uint16_t *codes, const uint16_t *co
                           long long nb, int nhist, long long prev_off, int first_call,
                           int pack_order, long long *s1, long long *s2, cudaStream_t st);
 
-cudaError_t launch_kk_front(const KkGeom &g, const uint16_t *codes, float2 *fftws,
-                            const float2 *twN, const float2 *twN2, float2 *E, const float2 *E_prev,
-                            CarrierPartial *partials, DevState *dst, cudaStream_t st, void *prof);
+// copy of the next call's packed history only (calls that emit no field)
+cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st);
+
+cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, const KkTables &tb,
+                            float2 *E, const float2 *E_prev, CarrierPartial *partials, DevState *dst,
+                            cudaStream_t st, void *prof);
 // stage-boundary hook of the profiler (defined with the C ABI; prof may be null)
 void prof_stage(void *prof, int stage, cudaStream_t st);
 
 cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long long f_prev,
                          long long f_k, const float *rrc, int hmf, const float2 *ds_tab,
                          int ds_num, int ds_den, const DevState *dst, float2 *Y, long long ybase,
-                         const float2 *Y_prev, long long ybase_prev, cudaStream_t st);
+                         const float2 *Y_prev, long long ybase_prev, cudaStream_t st,
+                         const float *rrc_host);
 
 cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, long long n_end, long long f_prev,
                           long long f_k, const float *rrc, int hmf, DevState *dst, int parity,
@@ -90,12 +119,12 @@ cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, 
                           cudaStream_t st);
 
 cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void *Y,
-                      float2 *taps_in, float2 *taps_out, uint8_t *dec, uint8_t *winb,
-                      float4 *dbg_win, float2 *dbg_z, const uint8_t *prbs, DevState *dst,
-                      cudaStream_t st);
+                      float2 *taps_in, float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec,
+                      float4 *dbg_win, float2 *dbg_z, const uint8_t *prbs, const uint32_t *prbs_bits,
+                      DevState *dst, cudaStream_t st);
 
 cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in,
-                         const uint8_t *dec, const uint8_t *winb, float4 *dbg_win,
-                         const uint8_t *prbs, uint8_t *bits_out, DevState *dst, cudaStream_t st);
+                         const uint8_t *dec, const uint8_t *winb, const uint4 *winrec, float4 *dbg_win,
+                         uint8_t *bits_out, DevState *dst, cudaStream_t st);
 
 }  // namespace rxk

@@ -17,8 +17,10 @@ constexpr long long kNaMaxSamples = 1LL << 19;          // largest buffer one ca
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-// byte layout of the scratch array
-constexpr size_t kTwEntries = 16 + 256 + 4096 + 65536;   // e^{-2 pi i k / n} for n = 16, 256, 4096, 65536
+// byte layout of the scratch array: per FFT length (4096, 65536; the 256 slot is unused) a table
+// block [ln table | sqrt table | factored W_N | factored W_{N/16}]
+constexpr size_t kTabBytes = 2 * 4096 * sizeof(float) + 1024 * sizeof(float2);   // >= one block
+constexpr size_t kTwEntries = 3 * kTabBytes / sizeof(float2);
 constexpr size_t kOffTw = 0;
 constexpr size_t kOffCodes = align_up(kOffTw + kTwEntries * sizeof(float2));
 constexpr size_t kCodesBytes = (size_t)(65536 + kNaMaxSamples) * sizeof(uint16_t);
@@ -35,16 +37,8 @@ constexpr size_t kScratchBytes = align_up(kOffState + sizeof(DevState));
 // Every call uses it, so calls that overlap on the GPU race with each other.
 static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
 
-// offset of the n-point table inside the twiddle block
-size_t tw_offset(int n)
-{
-    switch (n) {
-    case 16: return 0;
-    case 256: return 16;
-    case 4096: return 16 + 256;
-    default: return 16 + 256 + 4096;   // 65536
-    }
-}
+// index of the table block of an FFT length
+int tab_index(int n) { return n == 256 ? 0 : (n == 4096 ? 1 : 2); }
 
 // per-device set-up: device address of the scratch array and the uploaded tables
 constexpr int kMaxDevices = 64;
@@ -60,19 +54,16 @@ cudaError_t setup_device(int dev, unsigned char **out)
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
     if (e != cudaSuccess) return e;
-    // twiddle tables, once per device (host double precision, rounded once)
-    static float2 tw[kTwEntries];
-    const double pi = 3.14159265358979323846;
-    const int sizes[4] = {16, 256, 4096, 65536};
-    for (int s = 0; s < 4; s++) {
-        int n = sizes[s];
-        float2 *t = tw + tw_offset(n);
-        for (int k = 0; k < n; k++) {
-            double a = -2.0 * pi * (double)k / (double)n;
-            t[k] = make_float2((float)cos(a), (float)sin(a));
-        }
+    // lookup and twiddle tables of the three FFT lengths, once per device
+    static unsigned char blk[3 * kTabBytes];
+    const int sizes[3] = {256, 4096, 65536};
+    for (int i = 0; i < 3; i++) {
+        unsigned char *b = blk + i * kTabBytes;
+        float *ln = (float *)b, *sq = ln + 4096;
+        float2 *t1 = (float2 *)(sq + 4096), *t2 = t1 + kk_tw_entries(sizes[i]);
+        kk_host_tables(sizes[i], ln, sq, t1, t2);
     }
-    e = cudaMemcpy((unsigned char *)p + kOffTw, tw, sizeof tw, cudaMemcpyHostToDevice);
+    e = cudaMemcpy((unsigned char *)p + kOffTw, blk, sizeof blk, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     g_dev_ptr[dev] = (unsigned char *)p;
     g_ready[dev] = true;
@@ -94,8 +85,7 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     if (!packed12_in || !field_out || nsamp <= 0 || nsamp % 32 || nsamp > kNaMaxSamples) return RX_EINVAL;
     if (((uintptr_t)packed12_in) & 15 || ((uintptr_t)field_out) & 7) return RX_EINVAL;
     if (pack_order < 0 || pack_order > 1) return RX_EINVAL;
-    if (!(ols_n == 256 || ols_n == 4096 || ols_n == 65536) || ols_v < 2 || ols_v % 2 || ols_v >= ols_n)
-        return RX_EINVAL;
+    if (!(ols_n == 4096 || ols_n == 65536) || ols_v < 64 || ols_v % 64 || ols_v >= ols_n) return RX_EINVAL;
     long long e_k = nsamp - ols_v / 2;
     if (e_k <= 0) return RX_EINVAL;
     KkGeom g;
@@ -122,8 +112,12 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     unsigned char *base = nullptr;
     if (setup_device(dev, &base) != cudaSuccess) return RX_ECUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const float2 *twN = (const float2 *)(base + kOffTw) + tw_offset(ols_n);
-    const float2 *twN2 = (const float2 *)(base + kOffTw) + tw_offset(ols_n / 16);
+    const unsigned char *tabb = base + kOffTw + tab_index(ols_n) * kTabBytes;
+    KkTables tb;
+    tb.lnt = (const float *)tabb;
+    tb.sqt = tb.lnt + 4096;
+    tb.twN = (const float2 *)(tb.sqt + 4096);
+    tb.twN2 = tb.twN + kk_tw_entries(ols_n);
     uint16_t *codes = (uint16_t *)(base + kOffCodes);
     float2 *fftws = (float2 *)(base + kOffFft);
     float2 *E = (float2 *)(base + kOffE);
@@ -131,10 +125,15 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     DevState *ds = (DevState *)(base + kOffState);
     // the last-CTA ticket of the carrier reduction must start at zero
     if (cudaMemsetAsync(ds, 0, sizeof(DevState), st) != cudaSuccess) return RX_ECUDA;
-    if (launch_unpack(packed12_in, codes, nullptr, nsamp, ols_n, 0, 1, pack_order, nullptr, nullptr, st) !=
-        cudaSuccess)
-        return RX_ECUDA;
-    if (launch_kk_front(g, codes, fftws, twN, twN2, E, E, part, ds, st, nullptr) != cudaSuccess) return RX_ECUDA;
+    KkInput kin;
+    kin.hist = (const uint8_t *)codes;      // never read for values: the first call fills the pre-stream
+    kin.in = packed12_in;
+    kin.hist_next = nullptr;
+    kin.hist_bytes = (long long)ols_n * 3 / 2;
+    kin.in_bytes = nsamp * 3 / 2;
+    kin.order = pack_order;
+    kin.first_call = 1;
+    if (launch_kk_front(g, kin, fftws, tb, E, E, part, ds, st, nullptr) != cudaSuccess) return RX_ECUDA;
     unsigned grid = (unsigned)((e_k + 255) / 256);
     k_na_copy_field<<<grid, 256, 0, st>>>(E + kEHist, reinterpret_cast<float2 *>(field_out), e_k);
     if (cudaGetLastError() != cudaSuccess) return RX_ECUDA;

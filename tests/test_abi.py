@@ -59,7 +59,8 @@ def test_create_rejects_bad_arguments(args):
     assert st == 1 and not h.value
 
 
-@pytest.mark.parametrize("field,value", [("ntaps", 33), ("ntaps", 14), ("ols_n", 8192), ("win", 32),
+@pytest.mark.parametrize("field,value", [("ntaps", 33), ("ntaps", 14), ("ols_n", 8192), ("ols_n", 256),
+                                         ("ols_v", 96), ("win", 32),
                                          ("eq_block", 100), ("bps_b", 0), ("amb_syms", 100),
                                          ("ncma", 20000)])
 def test_create_rejects_bad_config(field, value):

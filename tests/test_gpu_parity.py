@@ -34,8 +34,8 @@ def test_kk_qpsk_pack_orders(pack_order):
     assert s["bits"] > 0
 
 
-def test_kk_ols256_tiny_fft():
-    run(4, 1 << 16, 2, ols_n=256, ols_v=64, ntrain=2048, ncma=1024, amb_syms=1024)
+def test_kk_small_overlap_many_blocks():
+    run(4, 1 << 16, 2, ols_n=4096, ols_v=64, ntrain=2048, ncma=1024, amb_syms=1024)
 
 
 def test_kk16_full_size_buffer():
