@@ -71,6 +71,10 @@ def lib():
         L.orx_q_db.restype = C.c_double
         L.orx_bps_metrics.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
                                       C.c_int, C.c_void_p]
+        L.orx_cnn_nparams.restype = C.c_int
+        L.orx_cnn_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                        C.c_void_p]
+        L.orx_cnn_loss_grad.restype = C.c_double
         L.orx_create.argtypes = [P(OrxCfg)]
         L.orx_create.restype = C.c_void_p
         L.orx_process.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
@@ -138,6 +142,40 @@ def bps_metrics(z: np.ndarray, mq: int, scale: float, B: int) -> np.ndarray:
     im = np.ascontiguousarray(np.imag(z), dtype=np.float64)
     out = np.zeros(B)
     lib().orx_bps_metrics(_ptr(re), _ptr(im), len(re), mq, scale, B, _ptr(out))
+    return out
+
+
+# ------------------------------------------------------------------ CNN
+CNN_C, CNN_K, CNN_H = 32, 9, 64
+
+
+def cnn_nparams() -> int:
+    return lib().orx_cnn_nparams()
+
+
+def cnn_loss_grad(prm: np.ndarray, x: np.ndarray, tgt: np.ndarray, grad: bool = True):
+    """x: (nseg, 2S+24, 2) inputs, tgt: (nseg, S, 2) -> (loss, grad or None, out)."""
+    prm = np.ascontiguousarray(prm, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    tgt = np.ascontiguousarray(tgt, dtype=np.float64)
+    nseg, S = tgt.shape[0], tgt.shape[1]
+    assert x.shape == (nseg, 2 * S + 24, 2)
+    g = np.zeros(cnn_nparams()) if grad else None
+    out = np.zeros((nseg, S, 2))
+    loss = lib().orx_cnn_loss_grad(_ptr(prm), _ptr(x), _ptr(tgt), nseg, S, _ptr(g) if grad else None, _ptr(out))
+    return loss, g, out
+
+
+def cnn_param_slices():
+    """name -> (offset, shape) of the parameter vector."""
+    C, K, H = CNN_C, CNN_K, CNN_H
+    shapes = [("W1", (C, K, 2)), ("b1", (C,)), ("W2", (C, K, C)), ("b2", (C,)), ("W3", (C, K, C)), ("b3", (C,)),
+              ("M1", (H, C)), ("c1", (H,)), ("M2", (2, H)), ("c2", (2,))]
+    out, off = {}, 0
+    for n, sh in shapes:
+        out[n] = (off, sh)
+        off += int(np.prod(sh))
+    assert off == cnn_nparams()
     return out
 
 

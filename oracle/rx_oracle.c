@@ -745,3 +745,142 @@ void orx_destroy(orx *h)
     free(h->d_draw); free(h->d_berr); free(h->d_near); free(h->d_win);
     free(h);
 }
+
+/* =========================================================== CNN equaliser
+ * Learned equaliser (the configured workload's alternative to the adaptive FIR
+ * and phase search): input the 2-sps matched-filter output y as two channels
+ * (real, imaginary); three valid 1-D convolutions of 32 channels, kernel 9,
+ * each followed by GELU (exact erf form); at every symbol position an MLP
+ * 32 -> 64 (GELU) -> 2 gives the soft symbol (I, Q) in unit-power units.
+ * A segment of S symbols starting at symbol k0 reads y[2 k0 - 12, 2 k0 + 2 S + 12).
+ * Loss: mean over the symbols of |out - target|^2.
+ *
+ * Parameter vector (in this order):
+ *   W1[32][9][2] b1[32]  W2[32][9][32] b2[32]  W3[32][9][32] b3[32]
+ *   M1[64][32] c1[64]    M2[2][64] c2[2]
+ */
+#define CNN_C 32
+#define CNN_K 9
+#define CNN_H 64
+enum {
+    CNN_OW1 = 0,
+    CNN_OB1 = CNN_OW1 + CNN_C * CNN_K * 2,
+    CNN_OW2 = CNN_OB1 + CNN_C,
+    CNN_OB2 = CNN_OW2 + CNN_C * CNN_K * CNN_C,
+    CNN_OW3 = CNN_OB2 + CNN_C,
+    CNN_OB3 = CNN_OW3 + CNN_C * CNN_K * CNN_C,
+    CNN_OM1 = CNN_OB3 + CNN_C,
+    CNN_OC1 = CNN_OM1 + CNN_H * CNN_C,
+    CNN_OM2 = CNN_OC1 + CNN_H,
+    CNN_OC2 = CNN_OM2 + 2 * CNN_H,
+    CNN_NP = CNN_OC2 + 2
+};
+
+int orx_cnn_nparams(void) { return CNN_NP; }
+
+static double gelu(double u) { return 0.5 * u * (1.0 + erf(u / sqrt(2.0))); }
+static double gelu_d(double u)
+{
+    return 0.5 * (1.0 + erf(u / sqrt(2.0))) + u * exp(-0.5 * u * u) / sqrt(2.0 * PI);
+}
+
+/* valid convolution: out[p][o] = b[o] + sum_t sum_c W[o][t][c] in[p + t][c] */
+static void conv_fwd(const double *W, const double *b, const double *in, int Lin, int Cin, double *u)
+{
+    int Lout = Lin - CNN_K + 1;
+    for (int p = 0; p < Lout; p++)
+        for (int o = 0; o < CNN_C; o++) {
+            double a = b[o];
+            for (int t = 0; t < CNN_K; t++)
+                for (int c = 0; c < Cin; c++) a += W[(o * CNN_K + t) * Cin + c] * in[(p + t) * Cin + c];
+            u[p * CNN_C + o] = a;
+        }
+}
+
+/* Loss and (optionally) gradient and outputs over nseg segments of S symbols.
+ * x: nseg * (2S + 24) * 2 inputs, tgt: nseg * S * 2 targets. */
+double orx_cnn_loss_grad(const double *prm, const double *x, const double *tgt, int nseg, int S, double *grad,
+                         double *out)
+{
+    int L0 = 2 * S + 24, L1 = L0 - 8, L2 = L1 - 8, L3 = L2 - 8;
+    double *u1 = xcalloc((size_t)L1 * CNN_C, sizeof(double)), *h1 = xcalloc((size_t)L1 * CNN_C, sizeof(double));
+    double *u2 = xcalloc((size_t)L2 * CNN_C, sizeof(double)), *h2 = xcalloc((size_t)L2 * CNN_C, sizeof(double));
+    double *u3 = xcalloc((size_t)L3 * CNN_C, sizeof(double)), *h3 = xcalloc((size_t)L3 * CNN_C, sizeof(double));
+    double *dh1 = xcalloc((size_t)L1 * CNN_C, sizeof(double)), *dh2 = xcalloc((size_t)L2 * CNN_C, sizeof(double));
+    double *dh3 = xcalloc((size_t)L3 * CNN_C, sizeof(double));
+    double loss = 0.0;
+    double norm = 1.0 / ((double)nseg * (double)S);
+    if (grad) memset(grad, 0, sizeof(double) * CNN_NP);
+    const double *W1 = prm + CNN_OW1, *B1 = prm + CNN_OB1, *W2 = prm + CNN_OW2, *B2 = prm + CNN_OB2;
+    const double *W3 = prm + CNN_OW3, *B3 = prm + CNN_OB3, *M1 = prm + CNN_OM1, *C1 = prm + CNN_OC1;
+    const double *M2 = prm + CNN_OM2, *C2 = prm + CNN_OC2;
+    for (int sg = 0; sg < nseg; sg++) {
+        const double *xs = x + (size_t)sg * L0 * 2;
+        conv_fwd(W1, B1, xs, L0, 2, u1);
+        for (int i = 0; i < L1 * CNN_C; i++) h1[i] = gelu(u1[i]);
+        conv_fwd(W2, B2, h1, L1, CNN_C, u2);
+        for (int i = 0; i < L2 * CNN_C; i++) h2[i] = gelu(u2[i]);
+        conv_fwd(W3, B3, h2, L2, CNN_C, u3);
+        for (int i = 0; i < L3 * CNN_C; i++) h3[i] = gelu(u3[i]);
+        memset(dh3, 0, sizeof(double) * (size_t)L3 * CNN_C);
+        for (int j = 0; j < S; j++) {
+            const double *hv = h3 + (size_t)(2 * j) * CNN_C;
+            double v[CNN_H], z[CNN_H], o[2];
+            for (int m = 0; m < CNN_H; m++) {
+                double a = C1[m];
+                for (int c = 0; c < CNN_C; c++) a += M1[m * CNN_C + c] * hv[c];
+                v[m] = a;
+                z[m] = gelu(a);
+            }
+            for (int i = 0; i < 2; i++) {
+                double a = C2[i];
+                for (int m = 0; m < CNN_H; m++) a += M2[i * CNN_H + m] * z[m];
+                o[i] = a;
+            }
+            const double *tg = tgt + ((size_t)sg * S + j) * 2;
+            double e0 = o[0] - tg[0], e1 = o[1] - tg[1];
+            loss += (e0 * e0 + e1 * e1) * norm;
+            if (out) { out[((size_t)sg * S + j) * 2] = o[0]; out[((size_t)sg * S + j) * 2 + 1] = o[1]; }
+            if (!grad) continue;
+            double dout[2] = {2.0 * e0 * norm, 2.0 * e1 * norm}, dv[CNN_H];
+            for (int i = 0; i < 2; i++) {
+                grad[CNN_OC2 + i] += dout[i];
+                for (int m = 0; m < CNN_H; m++) grad[CNN_OM2 + i * CNN_H + m] += dout[i] * z[m];
+            }
+            for (int m = 0; m < CNN_H; m++) {
+                double dz = dout[0] * M2[m] + dout[1] * M2[CNN_H + m];
+                dv[m] = dz * gelu_d(v[m]);
+                grad[CNN_OC1 + m] += dv[m];
+                for (int c = 0; c < CNN_C; c++) grad[CNN_OM1 + m * CNN_C + c] += dv[m] * hv[c];
+            }
+            for (int c = 0; c < CNN_C; c++) {
+                double a = 0.0;
+                for (int m = 0; m < CNN_H; m++) a += M1[m * CNN_C + c] * dv[m];
+                dh3[(size_t)(2 * j) * CNN_C + c] = a;
+            }
+        }
+        if (!grad) continue;
+        /* backward through the three convolutions */
+        struct { const double *W; double *dW, *db; const double *u, *in; double *dh_in; int Lin, Cin; double *dh; int Lout; } L[3] = {
+            {W3, grad + CNN_OW3, grad + CNN_OB3, u3, h2, dh2, L2, CNN_C, dh3, L3},
+            {W2, grad + CNN_OW2, grad + CNN_OB2, u2, h1, dh1, L1, CNN_C, dh2, L2},
+            {W1, grad + CNN_OW1, grad + CNN_OB1, u1, xs, NULL, L0, 2, dh1, L1}};
+        for (int l = 0; l < 3; l++) {
+            int Cin = L[l].Cin;
+            if (L[l].dh_in) memset(L[l].dh_in, 0, sizeof(double) * (size_t)L[l].Lin * Cin);
+            for (int p = 0; p < L[l].Lout; p++)
+                for (int o = 0; o < CNN_C; o++) {
+                    double du = L[l].dh[p * CNN_C + o] * gelu_d(L[l].u[p * CNN_C + o]);
+                    if (du == 0.0) continue;
+                    L[l].db[o] += du;
+                    for (int t = 0; t < CNN_K; t++)
+                        for (int c = 0; c < Cin; c++) {
+                            L[l].dW[(o * CNN_K + t) * Cin + c] += du * L[l].in[(p + t) * Cin + c];
+                            if (L[l].dh_in) L[l].dh_in[(p + t) * Cin + c] += du * L[l].W[(o * CNN_K + t) * Cin + c];
+                        }
+                }
+        }
+    }
+    free(u1); free(h1); free(u2); free(h2); free(u3); free(h3); free(dh1); free(dh2); free(dh3);
+    return loss;
+}

@@ -67,6 +67,11 @@ double  orx_q_db(double ber);
 void    orx_bps_metrics(const double *z_re, const double *z_im, int W, int mq, double s, int B,
                         double *metric);
 
+/* CNN equaliser: parameter count, loss / gradient / outputs over segments */
+int     orx_cnn_nparams(void);
+double  orx_cnn_loss_grad(const double *prm, const double *x, const double *tgt, int nseg, int S,
+                          double *grad, double *out);
+
 /* streaming receiver */
 orx    *orx_create(const orx_cfg *cfg);
 int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bits_cap);
