@@ -208,6 +208,46 @@ rx_status rx_profile_read(rx_handle *h, double *ms, int n, int64_t *calls);
 rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsamp, int32_t pack_order,
                               int32_t ols_n, int32_t ols_v, float *field_out, void *cuda_stream);
 
+/* ------------------------------------------------------------------ CNN
+ * Learned equaliser (the configured workload's alternative to the adaptive FIR
+ * and blind phase search, trained on the GPU by the library's own kernels).
+ * Input: the 2-sps matched-filter output y (complex, as RX_DBG_MF).  Three valid
+ * convolutions of 32 channels, kernel 9, each followed by GELU (exact erf); at
+ * every symbol position an MLP 32 -> 64 (GELU) -> 2 gives the soft symbol in
+ * unit-power units.  A segment of 64 symbols starting at symbol k0 reads
+ * y[2 k0 - 12, 2 k0 + 140).  Parameters (rx_cnn_nparams() floats, in order):
+ *   W1[32][9][2] b1[32] W2[32][9][32] b2[32] W3[32][9][32] b3[32]
+ *   M1[64][32] c1[64] M2[2][64] c2[2].
+ * The forward convolutions run on the tensor cores with BF16 operands and FP32
+ * accumulation; gradients and Adam (beta 0.9 / 0.999, eps 1e-8) are FP32 on FP32
+ * master weights.  Loss: mean over symbols of |out - target|^2. */
+typedef struct rx_cnn rx_cnn;
+
+int       rx_cnn_nparams(void);
+/* Allocates parameters, Adam state and activation storage for up to max_seg
+ * segments per gradient call (device memory on the current device). */
+rx_status rx_cnn_create(int max_seg, rx_cnn **out);
+/* HOST float arrays of rx_cnn_nparams() values; set resets the Adam state.
+ * Both synchronise the device. */
+rx_status rx_cnn_set_params(rx_cnn *c, const float *params, int n);
+rx_status rx_cnn_get_params(rx_cnn *c, float *params, int n);
+/* DEVICE pointers: y complex float pairs; seg_start[s] = index in y of segment
+ * s's first input sample (2 k0 - 12); out receives nseg * 64 * 2 floats. */
+rx_status rx_cnn_forward(rx_cnn *c, const float *y, const int64_t *seg_start, int nseg, float *out,
+                         void *cuda_stream);
+/* Gradient of the loss over nseg <= max_seg segments with DEVICE targets
+ * tgt[nseg][64][2]; grad_out (DEVICE, rx_cnn_nparams() floats) and loss_out
+ * (DEVICE, one float) may be NULL.  The gradient is kept for rx_cnn_adam_step. */
+rx_status rx_cnn_grad(rx_cnn *c, const float *y, const int64_t *seg_start, const float *tgt, int nseg,
+                      float *grad_out, float *loss_out, void *cuda_stream);
+rx_status rx_cnn_adam_step(rx_cnn *c, float lr, void *cuda_stream);
+void      rx_cnn_destroy(rx_cnn *c);
+
+/* Use the CNN (NULL: back to the adaptive FIR) for the payload decisions of a KK
+ * receiver from its next call on.  The network is borrowed: keep it alive while
+ * the receiver uses it. */
+rx_status rx_set_cnn(rx_handle *h, const rx_cnn *cnn);
+
 /* Releases the device memory and the handle.  NULL is ignored. */
 void rx_destroy(rx_handle *h);
 

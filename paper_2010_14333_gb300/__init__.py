@@ -49,7 +49,9 @@ class RxError(RuntimeError):
 
 EXPORTED = sorted(["rx_default_config", "rx_create", "rx_process", "rx_process_host", "rx_max_bits",
                    "rx_stats", "rx_debug_copy", "rx_set_taps", "rx_destroy", "rx_strerror",
-                   "rx_profile", "rx_profile_read", "rx_kk_field_noalloc"])
+                   "rx_profile", "rx_profile_read", "rx_kk_field_noalloc", "rx_cnn_nparams", "rx_cnn_create",
+                   "rx_cnn_set_params", "rx_cnn_get_params", "rx_cnn_forward", "rx_cnn_grad",
+                   "rx_cnn_adam_step", "rx_cnn_destroy", "rx_set_cnn"])
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
 
 _lib = None
@@ -78,10 +80,20 @@ def load(path: str = LIB_PATH):
     L.rx_profile.argtypes = [vp, C.c_int]
     L.rx_profile_read.argtypes = [vp, P(C.c_double), C.c_int, P(i64)]
     L.rx_kk_field_noalloc.argtypes = [vp, i64, C.c_int32, C.c_int32, C.c_int32, vp, vp]
+    L.rx_cnn_nparams.restype = C.c_int
+    L.rx_cnn_create.argtypes = [C.c_int, P(vp)]
+    L.rx_cnn_set_params.argtypes = [vp, vp, C.c_int]
+    L.rx_cnn_get_params.argtypes = [vp, vp, C.c_int]
+    L.rx_cnn_forward.argtypes = [vp, vp, vp, C.c_int, vp, vp]
+    L.rx_cnn_grad.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp, vp]
+    L.rx_cnn_adam_step.argtypes = [vp, C.c_float, vp]
+    L.rx_cnn_destroy.argtypes = [vp]
+    L.rx_cnn_destroy.restype = None
+    L.rx_set_cnn.argtypes = [vp, vp]
     L.rx_strerror.argtypes = [C.c_int]
     L.rx_strerror.restype = C.c_char_p
     for name in EXPORTED:
-        if name not in ("rx_max_bits", "rx_destroy", "rx_strerror"):
+        if name not in ("rx_max_bits", "rx_destroy", "rx_strerror", "rx_cnn_nparams", "rx_cnn_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -159,6 +171,49 @@ def rx_kk_field_noalloc(packed12_in: int, nsamp: int, pack_order: int, ols_n: in
     """KK field of one buffer with no device allocation (scratch is a fixed array
     inside librx.so); see include/rx.h."""
     _check(load().rx_kk_field_noalloc(packed12_in, nsamp, pack_order, ols_n, ols_v, field_out, stream))
+
+
+def rx_cnn_nparams() -> int:
+    return load().rx_cnn_nparams()
+
+
+def rx_cnn_create(max_seg: int) -> int:
+    h = C.c_void_p()
+    _check(load().rx_cnn_create(max_seg, C.byref(h)))
+    return h.value
+
+
+def rx_cnn_set_params(c: int, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().rx_cnn_set_params(c, p.ctypes.data, len(p)))
+
+
+def rx_cnn_get_params(c: int) -> np.ndarray:
+    p = np.zeros(rx_cnn_nparams(), dtype=np.float32)
+    _check(load().rx_cnn_get_params(c, p.ctypes.data, len(p)))
+    return p
+
+
+def rx_cnn_forward(c: int, y: int, seg_start: int, nseg: int, out: int, stream: int = 0):
+    _check(load().rx_cnn_forward(c, y, seg_start, nseg, out, stream))
+
+
+def rx_cnn_grad(c: int, y: int, seg_start: int, tgt: int, nseg: int, grad_out: int | None, loss_out: int | None,
+                stream: int = 0):
+    _check(load().rx_cnn_grad(c, y, seg_start, tgt, nseg, grad_out, loss_out, stream))
+
+
+def rx_cnn_adam_step(c: int, lr: float, stream: int = 0):
+    _check(load().rx_cnn_adam_step(c, lr, stream))
+
+
+def rx_cnn_destroy(c: int):
+    if c:
+        load().rx_cnn_destroy(c)
+
+
+def rx_set_cnn(h: int, c: int | None):
+    _check(load().rx_set_cnn(h, c))
 
 
 def rx_destroy(h: int):

@@ -47,6 +47,7 @@ struct rx_handle {
     uint8_t *in_stage, *bits_stage;
     long long dec_cap, win_cap, y_cap;
     // stage timing: a ring of event sets, one per profiled call
+    const rx_cnn *cnn;              // learned equaliser for the payload, or null
     int prof_on;
     cudaEvent_t *prof_ev;      // kProfRing * kStages1 events
     int *prof_used;            // stages recorded in each ring slot (bitmask of boundaries)
@@ -498,9 +499,17 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
         h->trained = 1;
     }
     if (e == cudaSuccess && g.nblk > 0) {
-        e = launch_eq(h->ep, g, 0, h->Y[h->yw], h->taps[h->tw], h->taps[h->tw ^ 1], h->dec, h->winb, h->winrec,
-                      h->dbg_win, h->dbg_z, h->prbs, h->prbs_bits, h->st, st);
-        h->tw ^= 1;
+        if (h->cnn) {
+            // learned equaliser: one segment per payload window
+            long long seg_base = 2 * pay_lo - 12 - h->ybase_cur;
+            e = launch_cnn_decide(rx_cnn_dev_params(h->cnn), rx_cnn_dev_params_bf16(h->cnn),
+                                  (const float2 *)h->Y[h->yw], seg_base, g.nwin, h->dec, h->winb, h->winrec,
+                                  h->prbs_bits, pay_lo, h->ep.scale, h->mq, st);
+        } else {
+            e = launch_eq(h->ep, g, 0, h->Y[h->yw], h->taps[h->tw], h->taps[h->tw ^ 1], h->dec, h->winb, h->winrec,
+                          h->dbg_win, h->dbg_z, h->prbs, h->prbs_bits, h->st, st);
+            h->tw ^= 1;
+        }
         prof_mark(h, 6, st);
         if (e == cudaSuccess) {
             int resolve = h->kk && !h->amb_done;
@@ -685,6 +694,13 @@ rx_status rx_profile_read(rx_handle *h, double *ms, int n, int64_t *calls)
     *calls = h->prof_calls;
     memset(h->prof_ms, 0, sizeof h->prof_ms);
     h->prof_calls = 0;
+    return RX_OK;
+}
+
+rx_status rx_set_cnn(rx_handle *h, const rx_cnn *cnn)
+{
+    if (!h || (cnn && !h->kk)) return RX_EINVAL;
+    h->cnn = cnn;
     return RX_OK;
 }
 

@@ -1,0 +1,602 @@
+// Learned equaliser: a 1-D CNN over the 2-sps matched-filter output, trained on
+// the GPU by its own forward and backward kernels (BF16 operands on the tensor
+// cores for the forward convolutions, FP32 accumulation, FP32 master weights and
+// Adam).
+//
+// Network (the configured workload's learned equaliser): input y as two channels
+// (real, imaginary); three valid convolutions of 32 channels, kernel 9, each
+// followed by GELU (exact erf form); at every symbol position an MLP
+// 32 -> 64 (GELU) -> 2 gives the soft symbol in unit-power units.  A segment of
+// S = 64 symbols starting at symbol k0 reads y[2 k0 - 12, 2 k0 + 140).
+// Parameter vector: W1[32][9][2] b1[32] W2[32][9][32] b2[32] W3[32][9][32] b3[32]
+//                   M1[64][32] c1[64] M2[2][64] c2[2].
+// Activations are channel-last, so the im2col row of output position p of a
+// 32-channel layer is the contiguous slice act[32 p, 32 p + 288): the
+// convolution is a plain GEMM A[p][k] = act[32 p + k], k = 9 x 32, against
+// W[o][k], computed with mma.sync m16n8k16 (BF16 in, FP32 accumulate).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "rx_common.cuh"
+#include "rx_internal.cuh"
+
+namespace rxk {
+
+constexpr int CC = 32, CK = 9, CH = 64, CS = 64;          // channels, kernel, hidden, symbols per segment
+constexpr int L0 = 2 * CS + 24, L1 = L0 - 8, L2 = L1 - 8, L3 = L2 - 8;
+constexpr int KW = CK * CC;                               // 288
+constexpr int OW1 = 0, OB1 = OW1 + CC * CK * 2, OW2 = OB1 + CC, OB2 = OW2 + CC * KW, OW3 = OB2 + CC,
+              OB3 = OW3 + CC * KW, OM1 = OB3 + CC, OC1 = OM1 + CH * CC, OM2 = OC1 + CH, OC2 = OM2 + 2 * CH,
+              NPRM = OC2 + 2;
+constexpr int kCnnThreads = 128;
+
+__device__ __forceinline__ float gelu_f(float u) { return 0.5f * u * (1.0f + erff(u * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_df(float u)
+{
+    return 0.5f * (1.0f + erff(u * 0.70710678118654752f)) + u * 0.3989422804014327f * __expf(-0.5f * u * u);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// saved forward state of one segment (training)
+struct CnnSave {
+    float *u1, *u2, *u3;          // pre-activations, [seg][L][32]
+    __nv_bfloat16 *h1, *h2, *h3;  // activations, [seg][L][32]
+    float *v;                     // MLP pre-activation, [seg][S][64]
+    float *out;                   // outputs, [seg][S][2]
+};
+
+// 32-channel valid convolution layer on the tensor cores:
+// dst[p][o] = GELU(b[o] + sum_k src[32 p + k] W[o][k]) for p < Lout; src has at
+// least 16 * ceil(Lout / 16) + 8 rows (extra rows zero).
+template <int LOUT>
+__device__ __forceinline__ void conv32_mma(const __nv_bfloat16 *src, const __nv_bfloat16 *W, const float *b,
+                                           __nv_bfloat16 *dst, float *u_save, int warp, int lane)
+{
+    constexpr int TILES = (LOUT + 15) / 16;
+    const int g = lane >> 2, tq = lane & 3;
+    for (int tile = warp; tile < TILES; tile += kCnnThreads / 32) {
+        const int r0 = 16 * tile;
+        float acc[4][4];
+#pragma unroll
+        for (int n = 0; n < 4; n++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) acc[n][i] = 0.f;
+#pragma unroll 2
+        for (int k0 = 0; k0 < KW; k0 += 16) {
+            uint32_t a[4];
+            const __nv_bfloat16 *ar = src + 32 * (r0 + g) + k0 + 2 * tq;
+            a[0] = *reinterpret_cast<const uint32_t *>(ar);
+            a[1] = *reinterpret_cast<const uint32_t *>(ar + 32 * 8);
+            a[2] = *reinterpret_cast<const uint32_t *>(ar + 8);
+            a[3] = *reinterpret_cast<const uint32_t *>(ar + 32 * 8 + 8);
+#pragma unroll
+            for (int n = 0; n < 4; n++) {
+                const __nv_bfloat16 *br = W + KW * (8 * n + g) + k0 + 2 * tq;
+                mma_bf16(acc[n], a, *reinterpret_cast<const uint32_t *>(br),
+                         *reinterpret_cast<const uint32_t *>(br + 8));
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < 4; n++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                int r = r0 + g + 8 * (i >> 1), o = 8 * n + 2 * tq + (i & 1);
+                if (r < LOUT) {
+                    float u = acc[n][i] + b[o];
+                    dst[32 * r + o] = __float2bfloat16(gelu_f(u));
+                    if (u_save) u_save[32 * r + o] = u;
+                }
+            }
+    }
+}
+
+// shared-memory layout of the forward kernel (bytes)
+struct FwdSmem {
+    static constexpr int X = 0;                                     // float [L0][2]
+    static constexpr int W1 = X + L0 * 2 * 4;                       // float [32][18]
+    static constexpr int B = W1 + CC * 18 * 4;                      // float b1, b2, b3 [96]
+    static constexpr int M1 = B + 3 * CC * 4;                       // float [64][32]
+    static constexpr int C1 = M1 + CH * CC * 4;                     // float [64]
+    static constexpr int M2 = C1 + CH * 4;                          // float [2][64] + c2 [2]
+    static constexpr int WB2 = ((M2 + (2 * CH + 2) * 4) + 15) & ~15; // bf16 [32][288]
+    static constexpr int WB3 = WB2 + CC * KW * 2;
+    static constexpr int H1 = WB3 + CC * KW * 2;                    // bf16 [L1 + 16][32]
+    static constexpr int H2 = H1 + (L1 + 16) * CC * 2;              // bf16 [L2 + 16][32]
+    static constexpr int H3 = H2 + (L2 + 16) * CC * 2;              // bf16 [L3][32]
+    static constexpr int OUT = H3 + L3 * CC * 2;                    // float [S][2]
+    static constexpr int TOTAL = OUT + CS * 2 * 4;
+};
+
+// Forward pass of nseg segments, one CTA each.  y: complex 2-sps input; seg_start[s]:
+// index in y of the segment's first input sample (2 k0 - 12).  Writes out[s][j][2]
+// and, when sv.u1 is set, the activations for the backward pass.  In receiver mode
+// (dec non-null) it decides the symbols instead and scores them (window records).
+__global__ void __launch_bounds__(kCnnThreads)
+    k_cnn_fwd(const float *__restrict__ prm, const __nv_bfloat16 *__restrict__ prm_bf, const float2 *__restrict__ y,
+              const long long *__restrict__ seg_start, long long seg_base, long long seg_step, float *__restrict__ out,
+              CnnSave sv, uint8_t *__restrict__ dec, uint8_t *__restrict__ winb, uint4 *__restrict__ winrec,
+              const uint32_t *__restrict__ prbs_bits, long long k_first, float scale, int mq)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    float *xs = reinterpret_cast<float *>(sm + FwdSmem::X);
+    float *w1 = reinterpret_cast<float *>(sm + FwdSmem::W1);
+    float *bb = reinterpret_cast<float *>(sm + FwdSmem::B);
+    float *m1 = reinterpret_cast<float *>(sm + FwdSmem::M1);
+    float *c1 = reinterpret_cast<float *>(sm + FwdSmem::C1);
+    float *m2 = reinterpret_cast<float *>(sm + FwdSmem::M2);
+    __nv_bfloat16 *wb2 = reinterpret_cast<__nv_bfloat16 *>(sm + FwdSmem::WB2);
+    __nv_bfloat16 *wb3 = reinterpret_cast<__nv_bfloat16 *>(sm + FwdSmem::WB3);
+    __nv_bfloat16 *h1 = reinterpret_cast<__nv_bfloat16 *>(sm + FwdSmem::H1);
+    __nv_bfloat16 *h2 = reinterpret_cast<__nv_bfloat16 *>(sm + FwdSmem::H2);
+    __nv_bfloat16 *h3 = reinterpret_cast<__nv_bfloat16 *>(sm + FwdSmem::H3);
+    float *os = reinterpret_cast<float *>(sm + FwdSmem::OUT);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = blockIdx.x;
+    const long long st = seg_start ? seg_start[s] : seg_base + seg_step * s;
+    // stage inputs and parameters
+    for (int i = tid; i < L0; i += kCnnThreads) {
+        float2 v = y[st + i];
+        xs[2 * i] = v.x;
+        xs[2 * i + 1] = v.y;
+    }
+    for (int i = tid; i < CC * 18; i += kCnnThreads) w1[i] = prm[OW1 + i];
+    for (int i = tid; i < CC; i += kCnnThreads) {
+        bb[i] = prm[OB1 + i];
+        bb[CC + i] = prm[OB2 + i];
+        bb[2 * CC + i] = prm[OB3 + i];
+    }
+    for (int i = tid; i < CH * CC; i += kCnnThreads) m1[i] = prm[OM1 + i];
+    for (int i = tid; i < CH; i += kCnnThreads) c1[i] = prm[OC1 + i];
+    for (int i = tid; i < 2 * CH + 2; i += kCnnThreads) m2[i] = prm[OM2 + i];
+    for (int i = tid; i < CC * KW / 8; i += kCnnThreads) {
+        reinterpret_cast<uint4 *>(wb2)[i] = reinterpret_cast<const uint4 *>(prm_bf + OW2)[i];
+        reinterpret_cast<uint4 *>(wb3)[i] = reinterpret_cast<const uint4 *>(prm_bf + OW3)[i];
+    }
+    // zero the padding rows read by the last (partial) row tiles
+    for (int i = tid; i < 16 * CC; i += kCnnThreads) {
+        h1[L1 * CC + i] = __float2bfloat16(0.f);
+        h2[L2 * CC + i] = __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    // layer 1 (2 input channels, K = 18) on the CUDA cores
+    float *u1s = sv.u1 ? sv.u1 + (size_t)s * L1 * CC : nullptr;
+    for (int i = tid; i < L1 * CC; i += kCnnThreads) {
+        int p = i >> 5, o = i & 31;
+        float a = bb[o];
+#pragma unroll
+        for (int k = 0; k < 18; k++) a = fmaf(w1[o * 18 + k], xs[2 * p + k], a);
+        h1[i] = __float2bfloat16(gelu_f(a));
+        if (u1s) u1s[i] = a;
+    }
+    __syncthreads();
+    conv32_mma<L2>(h1, wb2, bb + CC, h2, sv.u2 ? sv.u2 + (size_t)s * L2 * CC : nullptr, warp, lane);
+    __syncthreads();
+    conv32_mma<L3>(h2, wb3, bb + 2 * CC, h3, sv.u3 ? sv.u3 + (size_t)s * L3 * CC : nullptr, warp, lane);
+    __syncthreads();
+    if (sv.h1) {
+        for (int i = tid; i < L1 * CC / 8; i += kCnnThreads)
+            reinterpret_cast<uint4 *>(sv.h1 + (size_t)s * L1 * CC)[i] = reinterpret_cast<const uint4 *>(h1)[i];
+        for (int i = tid; i < L2 * CC / 8; i += kCnnThreads)
+            reinterpret_cast<uint4 *>(sv.h2 + (size_t)s * L2 * CC)[i] = reinterpret_cast<const uint4 *>(h2)[i];
+        for (int i = tid; i < L3 * CC / 8; i += kCnnThreads)
+            reinterpret_cast<uint4 *>(sv.h3 + (size_t)s * L3 * CC)[i] = reinterpret_cast<const uint4 *>(h3)[i];
+    }
+    // MLP head at the symbol positions: two threads per symbol, 32 hidden units each
+    {
+        int j = tid >> 1, half = tid & 1;
+        float hv[CC];
+#pragma unroll
+        for (int c = 0; c < CC; c++) hv[c] = __bfloat162float(h3[(2 * j) * CC + c]);
+        float o0 = 0.f, o1 = 0.f;
+        for (int mm = 0; mm < CH / 2; mm++) {
+            int m = half * (CH / 2) + mm;
+            float a = c1[m];
+#pragma unroll
+            for (int c = 0; c < CC; c++) a = fmaf(m1[m * CC + c], hv[c], a);
+            if (sv.v) sv.v[((size_t)s * CS + j) * CH + m] = a;
+            float z = gelu_f(a);
+            o0 = fmaf(m2[m], z, o0);
+            o1 = fmaf(m2[CH + m], z, o1);
+        }
+        o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
+        o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+        if (!half) {
+            o0 += m2[2 * CH];
+            o1 += m2[2 * CH + 1];
+            os[2 * j] = o0;
+            os[2 * j + 1] = o1;
+            if (out) {
+                out[((size_t)s * CS + j) * 2] = o0;
+                out[((size_t)s * CS + j) * 2 + 1] = o1;
+            }
+            if (sv.out) {
+                sv.out[((size_t)s * CS + j) * 2] = o0;
+                sv.out[((size_t)s * CS + j) * 2 + 1] = o1;
+            }
+        }
+    }
+    if (!dec) return;
+    __syncthreads();
+    // receiver mode: decisions, decision bytes and the window record (one warp)
+    if (warp == 0) {
+        const int NB = mq == 2 ? 1 : 2, BPS = 2 * NB;
+        long long k0 = k_first + (long long)s * CS;
+        int pwin = (int)(((long long)BPS * k0) % 32767);
+        unsigned eA = 0, eB = 0, se = 0, nn = 0;
+        for (int h = 0; h < 2; h++) {
+            int q = lane + 32 * h;
+            float vr = scale * os[2 * q], vi = scale * os[2 * q + 1];
+            int LI = 0, LQ = 0;
+            bool nr = false;
+            for (int jj = 0; jj < mq - 1; jj++) {
+                float th = (float)(2 * jj - (mq - 2));
+                LI += vr >= th;
+                LQ += vi >= th;
+                nr |= fabsf(vr - th) < 1e-4f || fabsf(vi - th) < 1e-4f;
+            }
+            dec[(size_t)s * CS + q] = (uint8_t)(LI | (LQ << 3) | (nr ? 64 : 0));
+            int pos = pwin + BPS * q;
+            uint32_t w0 = prbs_bits[pos >> 5], w1 = prbs_bits[(pos >> 5) + 1];
+            int ref = (int)(__funnelshift_l(w1, w0, pos & 31) >> (32 - BPS));
+            for (int rq = 0; rq < 4; rq++) {
+                int a = LI, bq = LQ;
+                if (rq & 2) { a = mq - 1 - a; bq = mq - 1 - bq; }
+                if (rq & 1) { int t = a; a = bq; bq = mq - 1 - t; }
+                unsigned ne = __popc((((a ^ (a >> 1)) << NB) | (bq ^ (bq >> 1))) ^ ref);
+                if (rq < 2) eA += ne << (16 * rq);
+                else eB += ne << (16 * (rq - 2));
+                se += (ne > 0) << (8 * rq);
+            }
+            nn += nr;
+        }
+        eA = warp_sum_i(eA);
+        eB = warp_sum_i(eB);
+        se = warp_sum_i(se);
+        nn = warp_sum_i(nn);
+        if (lane == 0) {
+            winb[s] = 0;
+            winrec[s] = make_uint4(eA, eB, se, nn << 8);
+        }
+    }
+}
+
+// shared-memory layout of the backward kernel (bytes)
+struct BwdSmem {
+    static constexpr int X = 0;                                  // float [L0][2]
+    static constexpr int HIN = X + L0 * 2 * 4;                   // bf16 layer input [L1][32]
+    static constexpr int WB = HIN + L1 * CC * 2;                 // bf16 weights [32][288]
+    static constexpr int DU = WB + CC * KW * 2;                  // float [L1][32]
+    static constexpr int DH = DU + L1 * CC * 4;                  // float [L1][32]
+    static constexpr int DV = DH + L1 * CC * 4;                  // float [S][64]
+    static constexpr int TOTAL = DV + CS * CH * 4;
+};
+
+// Backward pass of one segment per CTA: per-segment partial gradient gpart[s][NPRM].
+__global__ void __launch_bounds__(256)
+    k_cnn_bwd(const float *__restrict__ prm, const __nv_bfloat16 *__restrict__ prm_bf, const float2 *__restrict__ y,
+              const long long *__restrict__ seg_start, const float *__restrict__ tgt, CnnSave sv, float norm,
+              float *__restrict__ gpart)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    float *xs = reinterpret_cast<float *>(sm + BwdSmem::X);
+    __nv_bfloat16 *hin = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::HIN);
+    __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::WB);
+    float *du = reinterpret_cast<float *>(sm + BwdSmem::DU);
+    float *dh = reinterpret_cast<float *>(sm + BwdSmem::DH);
+    float *dv = reinterpret_cast<float *>(sm + BwdSmem::DV);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int s = blockIdx.x;
+    float *G = gpart + (size_t)s * NPRM;
+    const long long st = seg_start[s];
+    for (int i = tid; i < L0; i += nth) {
+        float2 v = y[st + i];
+        xs[2 * i] = v.x;
+        xs[2 * i + 1] = v.y;
+    }
+    const __nv_bfloat16 *h3 = sv.h3 + (size_t)s * L3 * CC;
+    // ---- MLP head
+    for (int i = tid; i < CS * CH; i += nth) {
+        int j = i / CH, m = i - CH * j;
+        float o0 = sv.out[((size_t)s * CS + j) * 2], o1 = sv.out[((size_t)s * CS + j) * 2 + 1];
+        float d0 = 2.f * (o0 - tgt[((size_t)s * CS + j) * 2]) * norm;
+        float d1 = 2.f * (o1 - tgt[((size_t)s * CS + j) * 2 + 1]) * norm;
+        float vv = sv.v[((size_t)s * CS + j) * CH + m];
+        float dz = d0 * prm[OM2 + m] + d1 * prm[OM2 + CH + m];
+        dv[i] = dz * gelu_df(vv);
+    }
+    __syncthreads();
+    // dM2, dc2 (z recomputed from v), dM1, dc1
+    for (int i = tid; i < 2 * CH + 2; i += nth) {
+        float a = 0.f;
+        for (int j = 0; j < CS; j++) {
+            float o = sv.out[((size_t)s * CS + j) * 2 + (i < 2 * CH ? i / CH : i - 2 * CH)];
+            float d = 2.f * (o - tgt[((size_t)s * CS + j) * 2 + (i < 2 * CH ? i / CH : i - 2 * CH)]) * norm;
+            a += (i < 2 * CH) ? d * gelu_f(sv.v[((size_t)s * CS + j) * CH + (i % CH)]) : d;
+        }
+        G[OM2 + i] = a;   // OC2 follows OM2 contiguously
+    }
+    for (int i = tid; i < CH * CC + CH; i += nth) {
+        float a = 0.f;
+        if (i < CH * CC) {
+            int m = i / CC, c = i - CC * m;
+            for (int j = 0; j < CS; j++) a += dv[j * CH + m] * __bfloat162float(h3[(2 * j) * CC + c]);
+            G[OM1 + i] = a;
+        } else {
+            int m = i - CH * CC;
+            for (int j = 0; j < CS; j++) a += dv[j * CH + m];
+            G[OC1 + m] = a;
+        }
+    }
+    // dh3 at the symbol positions (zero elsewhere)
+    for (int i = tid; i < L3 * CC; i += nth) {
+        int p = i >> 5, c = i & 31;
+        float a = 0.f;
+        if (!(p & 1)) {
+            int j = p >> 1;
+            for (int m = 0; m < CH; m++) a += prm[OM1 + m * CC + c] * dv[j * CH + m];
+        }
+        dh[i] = a;
+    }
+    __syncthreads();
+    // ---- conv layers 3, 2, 1
+    for (int l = 3; l >= 1; l--) {
+        const int Lout = (l == 3) ? L3 : (l == 2) ? L2 : L1;
+        const int Lin = Lout + 8;
+        const int Cin = (l == 1) ? 2 : CC;
+        const float *U = (l == 3) ? sv.u3 + (size_t)s * L3 * CC : (l == 2) ? sv.u2 + (size_t)s * L2 * CC
+                                                                          : sv.u1 + (size_t)s * L1 * CC;
+        const int OW = (l == 3) ? OW3 : (l == 2) ? OW2 : OW1, OB = (l == 3) ? OB3 : (l == 2) ? OB2 : OB1;
+        // layer input (bf16) and weights
+        if (l > 1) {
+            const __nv_bfloat16 *src = (l == 3) ? sv.h2 + (size_t)s * L2 * CC : sv.h1 + (size_t)s * L1 * CC;
+            for (int i = tid; i < Lin * CC / 8; i += nth)
+                reinterpret_cast<uint4 *>(hin)[i] = reinterpret_cast<const uint4 *>(src)[i];
+            for (int i = tid; i < CC * KW / 8; i += nth)
+                reinterpret_cast<uint4 *>(wb)[i] = reinterpret_cast<const uint4 *>(prm_bf + OW)[i];
+        }
+        for (int i = tid; i < Lout * CC; i += nth) du[i] = dh[i] * gelu_df(U[i]);
+        __syncthreads();
+        // dW[o][t][c] = sum_p du[p][o] in[p + t][c];  db[o] = sum_p du[p][o]
+        const int nw = CC * CK * Cin;
+        for (int i = tid; i < nw + CC; i += nth) {
+            float a = 0.f;
+            if (i < nw) {
+                int o = i / (CK * Cin), r = i - o * CK * Cin, t = r / Cin, c = r - t * Cin;
+                if (l > 1)
+                    for (int p = 0; p < Lout; p++) a = fmaf(du[p * CC + o], __bfloat162float(hin[(p + t) * CC + c]), a);
+                else
+                    for (int p = 0; p < Lout; p++) a = fmaf(du[p * CC + o], xs[(p + t) * 2 + c], a);
+                G[OW + i] = a;
+            } else {
+                int o = i - nw;
+                for (int p = 0; p < Lout; p++) a += du[p * CC + o];
+                G[OB + o] = a;
+            }
+        }
+        // gradient of the layer input: dh_in[q][c] = sum_t sum_o W[o][t][c] du[q - t][o]
+        if (l > 1) {
+            __syncthreads();
+            for (int i = tid; i < Lin * CC; i += nth) {
+                int q = i >> 5, c = i & 31;
+                float a = 0.f;
+                for (int t = 0; t < CK; t++) {
+                    int p = q - t;
+                    if (p < 0 || p >= Lout) continue;
+#pragma unroll 8
+                    for (int o = 0; o < CC; o++) a = fmaf(__bfloat162float(wb[o * KW + t * CC + c]), du[p * CC + o], a);
+                }
+                dh[i] = a;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// grad[i] = sum_s gpart[s][i] (fixed order)
+__global__ void k_cnn_reduce(const float *__restrict__ gpart, int nseg, float *__restrict__ grad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPRM) return;
+    float a = 0.f;
+    for (int s = 0; s < nseg; s++) a += gpart[(size_t)s * NPRM + i];
+    grad[i] = a;
+}
+
+// sum of the per-symbol squared errors (loss), fixed order within one CTA
+__global__ void k_cnn_loss(const float *__restrict__ out, const float *__restrict__ tgt, long long n, float norm,
+                           float *__restrict__ loss)
+{
+    __shared__ float red[256];
+    float a = 0.f;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        float d = out[i] - tgt[i];
+        a = fmaf(d, d, a);
+    }
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int s2 = 128; s2 > 0; s2 >>= 1) {
+        if ((int)threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0] * norm;
+}
+
+// Adam on the FP32 master weights; refreshes the BF16 copy
+__global__ void k_cnn_adam(float *__restrict__ prm, __nv_bfloat16 *__restrict__ prm_bf, float *__restrict__ m,
+                           float *__restrict__ v, const float *__restrict__ grad, float lr, float b1t, float b2t)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPRM) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    float g = grad[i];
+    float mi = b1 * m[i] + (1.f - b1) * g, vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    float mh = mi / (1.f - b1t), vh = vi / (1.f - b2t);
+    float w = prm[i] - lr * mh / (sqrtf(vh) + eps);
+    prm[i] = w;
+    prm_bf[i] = __float2bfloat16(w);
+}
+
+__global__ void k_cnn_tobf(const float *__restrict__ prm, __nv_bfloat16 *__restrict__ prm_bf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NPRM) prm_bf[i] = __float2bfloat16(prm[i]);
+}
+
+cudaError_t launch_cnn_decide(const float *prm, const void *prm_bf, const float2 *y, long long seg_base, int nseg,
+                              uint8_t *dec, uint8_t *winb, uint4 *winrec, const uint32_t *prbs_bits,
+                              long long k_first, float scale, int mq, cudaStream_t st)
+{
+    CnnSave sv;
+    memset(&sv, 0, sizeof sv);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_cnn_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, FwdSmem::TOTAL);
+        attr = true;
+    }
+    k_cnn_fwd<<<nseg, kCnnThreads, FwdSmem::TOTAL, st>>>(prm, (const __nv_bfloat16 *)prm_bf, y, nullptr, seg_base,
+                                                        2 * CS, nullptr, sv, dec, winb, winrec, prbs_bits, k_first,
+                                                        scale, mq);
+    return cudaGetLastError();
+}
+
+}  // namespace rxk
+
+using namespace rxk;
+
+struct rx_cnn {
+    int max_seg;
+    float *prm, *grad, *m, *v, *gpart, *loss;
+    __nv_bfloat16 *prm_bf;
+    CnnSave sv;
+    long long step;
+};
+
+extern "C" {
+
+int rx_cnn_nparams(void) { return NPRM; }
+
+void rx_cnn_destroy(rx_cnn *c)
+{
+    if (!c) return;
+    void *p[] = {c->prm, c->grad, c->m, c->v, c->gpart, c->loss, c->prm_bf, c->sv.u1, c->sv.u2, c->sv.u3,
+                 c->sv.h1, c->sv.h2, c->sv.h3, c->sv.v, c->sv.out};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    free(c);
+}
+
+rx_status rx_cnn_create(int max_seg, rx_cnn **out)
+{
+    if (!out || max_seg <= 0) return RX_EINVAL;
+    *out = nullptr;
+    rx_cnn *c = (rx_cnn *)calloc(1, sizeof(rx_cnn));
+    if (!c) return RX_ENOMEM;
+    c->max_seg = max_seg;
+    size_t S = (size_t)max_seg;
+    struct {
+        void **p;
+        size_t b;
+    } al[] = {{(void **)&c->prm, NPRM * 4},
+              {(void **)&c->grad, NPRM * 4},
+              {(void **)&c->m, NPRM * 4},
+              {(void **)&c->v, NPRM * 4},
+              {(void **)&c->gpart, S * NPRM * 4},
+              {(void **)&c->loss, 16},
+              {(void **)&c->prm_bf, NPRM * 2 + 64},
+              {(void **)&c->sv.u1, S * L1 * CC * 4},
+              {(void **)&c->sv.u2, S * L2 * CC * 4},
+              {(void **)&c->sv.u3, S * L3 * CC * 4},
+              {(void **)&c->sv.h1, S * L1 * CC * 2},
+              {(void **)&c->sv.h2, S * L2 * CC * 2},
+              {(void **)&c->sv.h3, S * L3 * CC * 2},
+              {(void **)&c->sv.v, S * CS * CH * 4},
+              {(void **)&c->sv.out, S * CS * 2 * 4}};
+    for (auto &a : al) {
+        if (cudaMalloc(a.p, a.b) != cudaSuccess || cudaMemset(*a.p, 0, a.b) != cudaSuccess) {
+            cudaGetLastError();
+            rx_cnn_destroy(c);
+            return RX_ENOMEM;
+        }
+    }
+    cudaFuncSetAttribute(k_cnn_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, FwdSmem::TOTAL);
+    cudaFuncSetAttribute(k_cnn_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, BwdSmem::TOTAL);
+    *out = c;
+    return RX_OK;
+}
+
+rx_status rx_cnn_set_params(rx_cnn *c, const float *host, int n)
+{
+    if (!c || !host || n != NPRM) return RX_EINVAL;
+    if (cudaMemcpy(c->prm, host, NPRM * 4, cudaMemcpyHostToDevice) != cudaSuccess) return RX_ECUDA;
+    cudaMemset(c->m, 0, NPRM * 4);
+    cudaMemset(c->v, 0, NPRM * 4);
+    c->step = 0;
+    k_cnn_tobf<<<(NPRM + 255) / 256, 256>>>(c->prm, c->prm_bf);
+    if (cudaDeviceSynchronize() != cudaSuccess) return RX_ECUDA;
+    return RX_OK;
+}
+
+rx_status rx_cnn_get_params(rx_cnn *c, float *host, int n)
+{
+    if (!c || !host || n != NPRM) return RX_EINVAL;
+    if (cudaMemcpy(host, c->prm, NPRM * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return RX_ECUDA;
+    return RX_OK;
+}
+
+rx_status rx_cnn_forward(rx_cnn *c, const float *y, const int64_t *seg_start, int nseg, float *out, void *stream)
+{
+    if (!c || !y || !seg_start || !out || nseg <= 0) return RX_EINVAL;
+    CnnSave sv;
+    memset(&sv, 0, sizeof sv);
+    k_cnn_fwd<<<nseg, kCnnThreads, FwdSmem::TOTAL, (cudaStream_t)stream>>>(
+        c->prm, c->prm_bf, (const float2 *)y, (const long long *)seg_start, 0, 0, out, sv, nullptr, nullptr, nullptr,
+        nullptr, 0, 1.f, 4);
+    return cudaGetLastError() == cudaSuccess ? RX_OK : RX_ECUDA;
+}
+
+rx_status rx_cnn_grad(rx_cnn *c, const float *y, const int64_t *seg_start, const float *tgt, int nseg, float *grad_out,
+                      float *loss_out, void *stream)
+{
+    if (!c || !y || !seg_start || !tgt || nseg <= 0 || nseg > c->max_seg) return RX_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    float norm = 1.f / ((float)nseg * CS);
+    k_cnn_fwd<<<nseg, kCnnThreads, FwdSmem::TOTAL, st>>>(c->prm, c->prm_bf, (const float2 *)y,
+                                                         (const long long *)seg_start, 0, 0, nullptr, c->sv, nullptr,
+                                                         nullptr, nullptr, nullptr, 0, 1.f, 4);
+    k_cnn_bwd<<<nseg, 256, BwdSmem::TOTAL, st>>>(c->prm, c->prm_bf, (const float2 *)y, (const long long *)seg_start,
+                                                 tgt, c->sv, norm, c->gpart);
+    k_cnn_reduce<<<(NPRM + 255) / 256, 256, 0, st>>>(c->gpart, nseg, c->grad);
+    k_cnn_loss<<<1, 256, 0, st>>>(c->sv.out, tgt, (long long)nseg * CS * 2, norm, c->loss);
+    if (grad_out) cudaMemcpyAsync(grad_out, c->grad, NPRM * 4, cudaMemcpyDeviceToDevice, st);
+    if (loss_out) cudaMemcpyAsync(loss_out, c->loss, 4, cudaMemcpyDeviceToDevice, st);
+    return cudaGetLastError() == cudaSuccess ? RX_OK : RX_ECUDA;
+}
+
+rx_status rx_cnn_adam_step(rx_cnn *c, float lr, void *stream)
+{
+    if (!c || !(lr > 0)) return RX_EINVAL;
+    c->step++;
+    float b1t = powf(0.9f, (float)c->step), b2t = powf(0.999f, (float)c->step);
+    k_cnn_adam<<<(NPRM + 255) / 256, 256, 0, (cudaStream_t)stream>>>(c->prm, c->prm_bf, c->m, c->v, c->grad, lr, b1t,
+                                                                     b2t);
+    return cudaGetLastError() == cudaSuccess ? RX_OK : RX_ECUDA;
+}
+
+// device pointers of the parameters (for the receiver's CNN path)
+const float *rx_cnn_dev_params(const rx_cnn *c) { return c ? c->prm : nullptr; }
+const void *rx_cnn_dev_params_bf16(const rx_cnn *c) { return c ? (const void *)c->prm_bf : nullptr; }
+
+}  // extern "C"

@@ -127,4 +127,14 @@ cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, in
                          const uint8_t *dec, const uint8_t *winb, const uint4 *winrec, float4 *dbg_win,
                          uint8_t *bits_out, DevState *dst, cudaStream_t st);
 
+// CNN decisions for nseg consecutive payload windows (receiver mode)
+cudaError_t launch_cnn_decide(const float *prm, const void *prm_bf, const float2 *y, long long seg_base, int nseg,
+                              uint8_t *dec, uint8_t *winb, uint4 *winrec, const uint32_t *prbs_bits,
+                              long long k_first, float scale, int mq, cudaStream_t st);
+
 }  // namespace rxk
+
+extern "C" {
+const float *rx_cnn_dev_params(const rx_cnn *c);
+const void *rx_cnn_dev_params_bf16(const rx_cnn *c);
+}

@@ -37,7 +37,7 @@ except Exception:  # pragma: no cover - scipy is present on both machines
 
 __all__ = [
     "FORMATS", "prbs15_bits", "gray_index", "tx_levels", "rrc_pulse",
-    "pack12", "gen_pam_stream", "gen_kk_stream",
+    "pack12", "gen_pam_stream", "gen_kk_stream", "splitmix64_bits", "random_symbols",
 ]
 
 # format id -> (name, bits per symbol, kind)
@@ -66,6 +66,25 @@ def prbs15_bits(seed: int, nbits: int) -> np.ndarray:
         period[i] = new
     reps = nbits // 32767 + 1
     return np.tile(period, reps)[:nbits].copy()
+
+
+def splitmix64_bits(seed: int, nbits: int) -> np.ndarray:
+    """Bits from the counter-based splitmix64 generator (Steele, Lea, Flood 2014):
+    word i = mix(seed + (i+1) * 0x9E3779B97F4A7C15), 64 bits per word, MSB first.
+    Used for learned-equaliser data, which must not follow an LFSR recurrence."""
+    nw = (nbits + 63) // 64
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (np.arange(1, nw + 1, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15))
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    bits = np.unpackbits(z.astype(">u8").view(np.uint8))
+    return bits[:nbits].copy()
+
+
+def random_symbols(fmt: int, n: int, seed: int) -> np.ndarray:
+    """n symbols of the format from splitmix64 bits (Gray mapped like the PRBS data)."""
+    return tx_levels(fmt, splitmix64_bits(seed, n * FORMATS[fmt][1]))
 
 
 def gray_index(bits: np.ndarray, nb: int) -> np.ndarray:
