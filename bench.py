@@ -35,6 +35,7 @@ if ROOT not in sys.path:
 
 METRIC = "KK-16QAM Rx GSa/s on 1 GB300 at oracle-matched BER; CNN-eq vs LMS BER & GSa/s"
 FMT, NB, FS, BAUD = 4, 1 << 22, 4e9, 1e9
+PROFILE_EVERY = 16          # stage events on one call in 16 of the timed run
 GEN = dict(snr_db=20.0, cspr_db=10.0, linewidth=100e3)
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
 # algorithmic FP32 operations per ADC sample of each stage (5 N log2 N per FFT;
@@ -177,19 +178,24 @@ def gpu_arm(args, rank, world, local):
     r = rx.Receiver(FMT, NB)
     stream = torch.cuda.current_stream()
 
-    def run_steps(rcv, n, profile=False):
+    # one step = one pipelined call over bufs_per_step consecutive buffers of the ring
+    bits_out = [torch.zeros(r.max_bits // 8 + 16, dtype=torch.uint8, device="cuda")
+                for _ in range(args.bufs_per_step)]
+    out_ptrs = [b.data_ptr() for b in bits_out]
+    sid = stream.cuda_stream
+
+    def run_steps(rcv, n):
         nbits = 0
         for _ in range(n):
-            for j in range(args.bufs_per_step):
-                _, k = rcv.process(ring[rcv.pos % args.ring])
-                rcv.pos += 1
-                nbits += k
+            ins = [ring[(rcv.pos + j) % args.ring].data_ptr() for j in range(args.bufs_per_step)]
+            nbits += sum(rx.rx_process_batch(rcv.h, ins, out_ptrs, sid))
+            rcv.pos += args.bufs_per_step
         return nbits
 
     r.pos = 0
     run_steps(r, args.warmup)
     torch.cuda.synchronize()
-    rx.rx_profile(r.h, True)
+    rx.rx_profile(r.h, PROFILE_EVERY)
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
@@ -219,8 +225,9 @@ def gpu_arm(args, rank, world, local):
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     host_ring = [torch.from_numpy(p).pin_memory() for p in g["packed"]]
     h2 = rx.rx_create(FMT, BAUD, FS, NB, rx.rx_default_config(FMT))
-    out_host = torch.zeros(rx.rx_max_bits(h2) // 8 + 16, dtype=torch.uint8).pin_memory()
-    sid = stream.cuda_stream
+    out_host = [torch.zeros(rx.rx_max_bits(h2) // 8 + 16, dtype=torch.uint8).pin_memory()
+                for _ in range(args.bufs_per_step)]
+    hout_ptrs = [t.data_ptr() for t in out_host]
     pos = 0
     e2e_steps = max(1, min(args.steps, 10))
     h2d = d2h = 0
@@ -232,11 +239,11 @@ def gpu_arm(args, rank, world, local):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             h2d = d2h = 0
-        for j in range(args.bufs_per_step):
-            n = rx.rx_process_host(h2, host_ring[pos % args.ring].data_ptr(), out_host.data_ptr(), sid)
-            pos += 1
-            h2d += NB * 3 // 2
-            d2h += (n + 7) // 8
+        hin = [host_ring[(pos + j) % args.ring].data_ptr() for j in range(args.bufs_per_step)]
+        ns = rx.rx_process_host_batch(h2, hin, hout_ptrs, sid)
+        pos += args.bufs_per_step
+        h2d += args.bufs_per_step * NB * 3 // 2
+        d2h += sum((n + 7) // 8 for n in ns)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -247,6 +254,34 @@ def gpu_arm(args, rank, world, local):
         e2e_ms = float(tt.item())
     rx.rx_destroy(h2)
     e2e_value = e2e_steps * args.bufs_per_step * NB * world / (e2e_ms * 1e-3) / 1e9
+
+    # ---- per-buffer latency, one buffer in flight at a time (the paper's budget:
+    # five streams of 2^22 samples within 5 * 2^22 / 4 GS/s = 5.243 ms; one buffer
+    # arrives every 1.049 ms)
+    lat_dev, lat_host = [], []
+    h3 = rx.rx_create(FMT, BAUD, FS, NB, rx.rx_default_config(FMT))
+    try:
+        for i in range(args.latency_reps + 5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rx.rx_process(r.h, ring[r.pos % args.ring].data_ptr(), out_ptrs[0], sid)
+            b.record(stream)
+            r.pos += 1
+            c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c.record(stream)
+            rx.rx_process_host(h3, host_ring[i % args.ring].data_ptr(), hout_ptrs[0], sid)
+            d.record(stream)
+            torch.cuda.synchronize()
+            if i >= 5:
+                lat_dev.append(a.elapsed_time(b))
+                lat_host.append(c.elapsed_time(d))
+    finally:
+        rx.rx_destroy(h3)
+    pct = lambda v, q: float(np.percentile(np.asarray(v), q))
+    latency = {"reps": args.latency_reps, "budget_ms": 5.243, "arrival_interval_ms": NB / FS * 1e3,
+               "device_p50_ms": pct(lat_dev, 50), "device_p99_ms": pct(lat_dev, 99),
+               "host_p50_ms": pct(lat_host, 50), "host_p99_ms": pct(lat_host, 99),
+               "note": "one buffer at a time; device = input resident in HBM, host = pinned H2D + chain + D2H"}
 
     # ---- per-stage times (CUDA events on the launching stream) and roofline
     per_call = {s: stage_ms[s] / max(calls, 1) for s in STAGES}
@@ -301,15 +336,19 @@ def gpu_arm(args, rank, world, local):
                "ber_oracle": so["ber"], "ber_gpu_same_buffers": sg["ber"],
                "bit_errors_oracle": so["bit_errors"], "bit_errors_gpu": sg["bit_errors"], "bits": so["bits"]}
 
+    cnn_line = None
+    if rank == 0 and not args.no_cnn:
+        cnn_line = cnn_leg(args, ring)
+
     clk = clocks.summary()
-    launches_per_call = 7
+    launches_per_call = 6
     line = {"metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args),
             "e2e": {"value": e2e_value, "unit": "GSa/s", "h2d_bytes_per_step": h2d // e2e_steps,
                     "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
-            "roofline": roof, "stages": stages, "cpu_baseline": cpu,
+            "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line,
             "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
             "realtime_x": value / 4.0,
             "ber": cpu["ber_gpu_same_buffers"] if cpu else None,
@@ -324,6 +363,69 @@ def gpu_arm(args, rank, world, local):
         dist.destroy_process_group()
 
 
+VOLT = dict(volterra=(0.05, 0.02), cspr_db=6.0, linewidth=0.0, phase_noise=False)
+
+
+def cnn_leg(args, ring):
+    """Learned equaliser against the adaptive FIR on the Volterra + SSBI channel
+    (CSPR 6 dB, SNR 16..22 dB): train on 2^24 counter-based symbols, judge BER on a
+    fresh PRBS stream, and time the CNN receiver on the 2^22-sample buffers."""
+    import torch
+    import synth
+    import paper_2010_14333_gb300 as rx
+    from paper_2010_14333_gb300 import cnn
+    t0 = time.perf_counter()
+    nb, per_snr = NB, 4
+    ys, syms, off = [], [], 0
+    for i, snr in enumerate((16.0, 18.0, 20.0, 22.0)):
+        sym = synth.random_symbols(FMT, per_snr * nb // 4 + 64, seed=1000 + i)
+        g = synth.gen_kk_stream(FMT, nb, per_snr, seed=500 + i, symbols=sym, truth=False, snr_db=snr,
+                                workers=min(16, os.cpu_count() or 1), **VOLT)
+        ys.append(cnn.mf_output(g["packed"], nb))
+        syms.append(sym[: len(ys[-1]) // 2])
+    # one training set: the streams side by side (segments never cross a seam: a
+    # 64-symbol gap of zeros is left between them and excluded)
+    gap = 256
+    y_all = np.concatenate([np.concatenate([y[: 2 * len(s)], np.zeros(2 * gap, np.complex64)]) for y, s in zip(ys, syms)])
+    s_all = np.concatenate([np.concatenate([s, np.zeros(gap, np.complex64)]) for s in syms])
+    n_train = sum(len(s) for s in syms)
+    tr = cnn.CnnTrainer(batch=64, seed=7)
+    tr.set_data(y_all, s_all, k_lo=64)
+    steps = int(os.environ.get("RX_CNN_STEPS", "6000"))
+    tr.train(steps - steps // 4, lr=1e-3)
+    tr.train(steps // 4, lr=2e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    # judge: fresh PRBS stream at 19 dB through both receivers
+    gev = synth.gen_kk_stream(FMT, nb, 4, seed=777, truth=False, snr_db=19.0,
+                              workers=min(16, os.cpu_count() or 1), **VOLT)
+    lms, net = rx.Receiver(FMT, nb), rx.Receiver(FMT, nb)
+    rx.rx_set_cnn(net.h, tr.h)
+    for p in gev["packed"]:
+        d = torch.from_numpy(p).cuda()
+        lms.process(d)
+        net.process(d)
+    sl, sn = lms.stats(), net.stats()
+    # throughput of the CNN receiver on the benchmark buffers
+    r = rx.Receiver(FMT, nb)
+    rx.rx_set_cnn(r.h, tr.h)
+    r.process_batch(ring[:3])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nrun = 2 * len(ring)
+    e0.record()
+    r.process_batch(ring)
+    r.process_batch(ring)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"gsa_s": nrun * nb / (ms * 1e-3) / 1e9, "ber_cnn": sn["ber"], "ber_lms": sl["ber"],
+            "bits": sn["bits"], "train_symbols": int(n_train), "train_steps": steps, "batch_symbols": 64 * 64,
+            "train_s": t_train,
+            "channel": "KK-16QAM, Volterra (0.05, 0.02), CSPR 6 dB, no laser phase noise; train SNR 16/18/20/22 dB "
+                       "(counter-based symbols), judge SNR 19 dB (PRBS-15)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,6 +435,8 @@ def main():
     ap.add_argument("--bufs-per-step", type=int, default=64)
     ap.add_argument("--ring", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cnn", action="store_true")
+    ap.add_argument("--latency-reps", type=int, default=300)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -142,12 +142,32 @@ rx_status rx_create(rx_format format, double baud, double fs, int64_t buf_len,
 rx_status rx_process(rx_handle *h, const uint8_t *packed12_in, uint8_t *bits_out,
                      void *cuda_stream, int64_t *nbits_out);
 
+/* Process n consecutive buffers of the stream (ins[i], outs[i] as in rx_process;
+ * nbits_out[i] per buffer).  The results are those of n rx_process calls.  The
+ * front end of buffer i+1 (field reconstruction, matched filter) runs on
+ * cuda_stream concurrently with the back end of buffer i (equaliser, decisions,
+ * bits) on a stream the handle owns, as the paper overlaps consecutive buffers in
+ * parallel processing streams chained by events (Sec. 2); cuda_stream waits for
+ * the last back end before the call returns its work.  With cfg.debug = 1 the
+ * buffers run one at a time on cuda_stream. */
+rx_status rx_process_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *const *outs, int n,
+                           void *cuda_stream, int64_t *nbits_out);
+
 /* Same as rx_process with HOST buffers: copies the input host->device, runs the
  * chain and copies the bits device->host, all enqueued on cuda_stream.  For
  * asynchronous copies the host buffers must be page-locked.  Returns after
  * enqueuing; the bits are valid once the stream has reached this point. */
 rx_status rx_process_host(rx_handle *h, const uint8_t *host_in, uint8_t *host_bits_out,
                           void *cuda_stream, int64_t *nbits_out);
+
+/* rx_process_batch with HOST buffers (page-locked for the copies to overlap):
+ * host_ins[i] holds buffer i as packed 12-bit bytes, host_outs[i] receives its
+ * bits (capacity rx_max_bits / 8 + 1 bytes).  The copy of buffer i+1 to the
+ * device runs on a stream the handle owns, concurrently with the front end of
+ * buffer i; each buffer's bits are copied back after its demap.  The outputs are
+ * valid once cuda_stream has reached the end of the call. */
+rx_status rx_process_host_batch(rx_handle *h, const uint8_t *const *host_ins, uint8_t *const *host_outs, int n,
+                                void *cuda_stream, int64_t *nbits_out);
 
 /* Upper bound of the bits one rx_process call can emit. */
 int64_t rx_max_bits(const rx_handle *h);
@@ -166,10 +186,12 @@ rx_status rx_debug_copy(rx_handle *h, int what, void *dst, int64_t cap, int64_t 
  * im may be NULL for PAM).  Synchronous. */
 rx_status rx_set_taps(rx_handle *h, const double *re, const double *im, int n);
 
-/* Stage timing.  rx_profile(h, 1) makes every later rx_process record CUDA
- * events on the caller's stream at the stage boundaries (unpack, K1a forward
+/* Stage timing.  rx_profile(h, n) with n >= 1 makes every n-th later call
+ * (those whose call index is a multiple of n) record a CUDA event before and
+ * after each stage, on the stream that runs the stage (unpack, K1a forward
  * radix-16, K1b row FFTs, K1c field assembly, matched filter, equaliser,
- * demap); rx_profile(h, 0) stops.  rx_profile_read waits for the recorded
+ * demap); rx_profile(h, 0) stops.  Sampling keeps the cost of the events off
+ * most calls of a long run.  rx_profile_read waits for the recorded
  * calls, writes the summed milliseconds of each stage to ms[0..n-1] (n <= 7,
  * in the order above; a stage a format lacks reads 0) and the number of calls
  * measured to *calls, and clears the record. */

@@ -51,7 +51,8 @@ EXPORTED = sorted(["rx_default_config", "rx_create", "rx_process", "rx_process_h
                    "rx_stats", "rx_debug_copy", "rx_set_taps", "rx_destroy", "rx_strerror",
                    "rx_profile", "rx_profile_read", "rx_kk_field_noalloc", "rx_cnn_nparams", "rx_cnn_create",
                    "rx_cnn_set_params", "rx_cnn_get_params", "rx_cnn_forward", "rx_cnn_grad",
-                   "rx_cnn_adam_step", "rx_cnn_destroy", "rx_set_cnn"])
+                   "rx_cnn_adam_step", "rx_cnn_destroy", "rx_set_cnn", "rx_process_batch",
+                   "rx_process_host_batch"])
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
 
 _lib = None
@@ -70,6 +71,8 @@ def load(path: str = LIB_PATH):
     L.rx_create.argtypes = [C.c_int, C.c_double, C.c_double, i64, P(RxConfig), P(vp)]
     L.rx_process.argtypes = [vp, vp, vp, vp, P(i64)]
     L.rx_process_host.argtypes = [vp, vp, vp, vp, P(i64)]
+    L.rx_process_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
+    L.rx_process_host_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.rx_max_bits.argtypes = [vp]
     L.rx_max_bits.restype = i64
     L.rx_stats.argtypes = [vp, P(RxStats), vp]
@@ -127,6 +130,26 @@ def rx_process(h: int, packed12_in: int, bits_out: int, stream: int = 0) -> int:
     return n.value
 
 
+def rx_process_batch(h: int, ins, outs, stream: int = 0):
+    """ins, outs: sequences of device pointers; returns the bit count per buffer."""
+    n = len(ins)
+    ia = (C.c_void_p * n)(*ins)
+    oa = (C.c_void_p * n)(*outs)
+    nb = (C.c_int64 * n)()
+    _check(load().rx_process_batch(h, ia, oa, n, stream, nb))
+    return list(nb)
+
+
+def rx_process_host_batch(h: int, host_ins, host_outs, stream: int = 0):
+    """host_ins, host_outs: sequences of (page-locked) host pointers; bit count per buffer."""
+    n = len(host_ins)
+    ia = (C.c_void_p * n)(*host_ins)
+    oa = (C.c_void_p * n)(*host_outs)
+    nb = (C.c_int64 * n)()
+    _check(load().rx_process_host_batch(h, ia, oa, n, stream, nb))
+    return list(nb)
+
+
 def rx_process_host(h: int, host_in: int, host_bits_out: int, stream: int = 0) -> int:
     n = C.c_int64()
     _check(load().rx_process_host(h, host_in, host_bits_out, stream, C.byref(n)))
@@ -155,8 +178,9 @@ def rx_set_taps(h: int, re, im=None):
     _check(load().rx_set_taps(h, re.ctypes.data, None if imv is None else imv.ctypes.data, len(re)))
 
 
-def rx_profile(h: int, enable: bool):
-    _check(load().rx_profile(h, int(bool(enable))))
+def rx_profile(h: int, every: int):
+    """Record stage events on every `every`-th call (0 stops; True means every call)."""
+    _check(load().rx_profile(h, int(every)))
 
 
 def rx_profile_read(h: int) -> tuple[dict, int]:
@@ -258,6 +282,17 @@ class Receiver:
         assert packed.is_cuda and packed.dtype == self.torch.uint8
         n = rx_process(self.h, packed.data_ptr(), self.bits.data_ptr(), self.stream())
         return self.bits[: (n + 7) // 8], n
+
+    def process_batch(self, packed_list):
+        """Consecutive buffers in one pipelined call; returns [(bits tensor, nbits)]."""
+        t = self.torch
+        if not hasattr(self, "_bbufs") or len(self._bbufs) < len(packed_list):
+            self._bbufs = [t.zeros((self.max_bits + 7) // 8 + 16, dtype=t.uint8, device="cuda")
+                           for _ in range(len(packed_list))]
+        outs = self._bbufs[: len(packed_list)]
+        n = rx_process_batch(self.h, [p.data_ptr() for p in packed_list], [o.data_ptr() for o in outs],
+                             self.stream())
+        return [(o[: (k + 7) // 8], k) for o, k in zip(outs, n)]
 
     def stats(self) -> dict:
         return rx_stats(self.h, self.stream())

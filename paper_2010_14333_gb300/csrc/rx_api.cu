@@ -31,12 +31,18 @@ struct rx_handle {
     uint16_t *codes[2];
     uint8_t *phist[2];              // KK: packed history, ping-pong
     int hw;
-    float2 *fftws, *E[2];
-    void *Y[2];
+    float2 *fftws, *E[kSlots];
+    void *Y[kSlots];
     CarrierPartial *partials;
-    uint8_t *dec, *winb, *prbs;
+    uint8_t *dec[kSlots], *winb[kSlots], *prbs;
     uint32_t *prbs_bits;            // the PRBS period bit-packed MSB first, first 256 bits repeated
-    uint4 *winrec;                  // per payload window: errors under the four rotations, near count
+    uint4 *winrec[kSlots];          // per payload window: errors under the four rotations, near count
+    int l_ds;                       // decision slot of the last call
+    // two-stream pipeline of rx_process_batch: the front end (field, matched
+    // filter) of buffer i+1 runs on the caller's stream while the back end
+    // (equaliser, demap) of buffer i runs on `back`
+    cudaStream_t back, copy;
+    cudaEvent_t ev_front, ev_join, ev_yfree[kSlots], ev_inready[2], ev_infree[2];
     float2 *taps[2], *twN, *twN2, *ds_tab;
     float *lnt, *sqt;
     float *rrc;
@@ -44,13 +50,14 @@ struct rx_handle {
     float4 *dbg_win;
     float2 *dbg_z;
     DevState *st;
-    uint8_t *in_stage, *bits_stage;
+    uint8_t *in_stage[2], *bits_stage;   // device staging of the host-buffer entry points
     long long dec_cap, win_cap, y_cap;
     // stage timing: a ring of event sets, one per profiled call
     const rx_cnn *cnn;              // learned equaliser for the payload, or null
-    int prof_on;
-    cudaEvent_t *prof_ev;      // kProfRing * kStages1 events
-    int *prof_used;            // stages recorded in each ring slot (bitmask of boundaries)
+    int prof_on;               // sampling period in calls (0: off)
+    int prof_cur;              // the call being enqueued is sampled
+    cudaEvent_t *prof_ev;      // kProfRing * 2 * kStages events (begin, end of every stage)
+    int *prof_used;            // stages recorded in each ring slot (bitmask)
     long long prof_head, prof_tail;
     double prof_ms[8];
     long long prof_calls;
@@ -58,35 +65,48 @@ struct rx_handle {
 
 static const int kProfRing = 1024;
 static const int kStages = 7;        // unpack, kk_fwd, kk_rows, kk_inv, mf, eq, demap
-static const int kStages1 = kStages + 1;
+static const int kEvPerCall = 2 * kStages;
 
-// record the boundary before stage `stage` (kStages = end of call)
-static void prof_mark(rx_handle *h, int stage, cudaStream_t st)
+// begin / end event of a stage, on the stream that runs it
+static void prof_begin(rx_handle *h, int stage, cudaStream_t st)
 {
-    if (!h->prof_on) return;
+    if (!h->prof_cur) return;
     long long slot = h->prof_head % kProfRing;
-    cudaEventRecord(h->prof_ev[slot * kStages1 + stage], st);
+    cudaEventRecord(h->prof_ev[slot * kEvPerCall + 2 * stage], st);
     h->prof_used[slot] |= 1 << stage;
 }
-
-void rxk::prof_stage(void *prof, int stage, cudaStream_t st)
+static void prof_end(rx_handle *h, int stage, cudaStream_t st)
 {
-    if (prof) prof_mark((rx_handle *)prof, stage, st);
+    if (!h->prof_cur) return;
+    long long slot = h->prof_head % kProfRing;
+    cudaEventRecord(h->prof_ev[slot * kEvPerCall + 2 * stage + 1], st);
 }
 
-// harvest the oldest recorded call (blocking on its last event)
+// hook of the K1 launcher: s > 0 begins stage s; s < 0 ends stage -s-1 and, up to
+// stage 3, begins stage -s
+void rxk::prof_stage(void *prof, int stage, cudaStream_t st)
+{
+    if (!prof) return;
+    rx_handle *h = (rx_handle *)prof;
+    if (stage > 0) {
+        prof_begin(h, stage, st);
+    } else {
+        prof_end(h, -stage - 1, st);
+        if (-stage <= 3) prof_begin(h, -stage, st);
+    }
+}
+
+// harvest the oldest recorded call (blocking on its events)
 static void prof_harvest_one(rx_handle *h)
 {
     long long slot = h->prof_tail % kProfRing;
     int used = h->prof_used[slot];
-    cudaEvent_t *ev = h->prof_ev + slot * kStages1;
-    cudaEventSynchronize(ev[kStages]);
+    cudaEvent_t *ev = h->prof_ev + slot * kEvPerCall;
     for (int s = 0; s < kStages; s++) {
         if (!(used & (1 << s))) continue;
-        int e = s + 1;
-        while (e < kStages && !(used & (1 << e))) e++;   // next recorded boundary
+        cudaEventSynchronize(ev[2 * s + 1]);
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ev[s], ev[e]) == cudaSuccess) h->prof_ms[s] += ms;
+        if (cudaEventElapsedTime(&ms, ev[2 * s], ev[2 * s + 1]) == cudaSuccess) h->prof_ms[s] += ms;
     }
     h->prof_used[slot] = 0;
     h->prof_tail++;
@@ -206,16 +226,28 @@ int64_t rx_max_bits(const rx_handle *h)
 void rx_destroy(rx_handle *h)
 {
     if (!h) return;
-    void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->E[0], h->E[1], h->Y[0], h->Y[1], h->partials,
-                    h->dec, h->winb, h->prbs, h->taps[0], h->taps[1], h->twN, h->twN2, h->ds_tab,
-                    h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage, h->bits_stage, h->lnt, h->sqt,
-                    h->prbs_bits, h->winrec, h->phist[0], h->phist[1]};
+    // work still queued on the pipeline's own streams finishes before the memory goes
+    if (h->back) cudaStreamSynchronize(h->back);
+    if (h->copy) cudaStreamSynchronize(h->copy);
+    void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->E[0], h->E[1], h->E[2], h->Y[0], h->Y[1], h->Y[2],
+                    h->partials, h->dec[0], h->dec[1], h->dec[2], h->winb[0], h->winb[1], h->winb[2],
+                    h->winrec[0], h->winrec[1], h->winrec[2], h->prbs, h->taps[0], h->taps[1], h->twN, h->twN2,
+                    h->ds_tab,
+                    h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1], h->bits_stage, h->lnt, h->sqt,
+                    h->prbs_bits, h->phist[0], h->phist[1]};
+    static_assert(kSlots == 3, "slot arrays listed above");
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->prof_ev) {
-        for (int i = 0; i < kProfRing * kStages1; i++) cudaEventDestroy(h->prof_ev[i]);
+        for (int i = 0; i < kProfRing * kEvPerCall; i++) cudaEventDestroy(h->prof_ev[i]);
         free(h->prof_ev);
     }
+    if (h->back) cudaStreamDestroy(h->back);
+    if (h->copy) cudaStreamDestroy(h->copy);
+    cudaEvent_t *evs[] = {&h->ev_front, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1], &h->ev_yfree[2],
+                          &h->ev_inready[0], &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
+    for (cudaEvent_t *ev : evs)
+        if (*ev) cudaEventDestroy(*ev);
     free(h->prof_used);
     free(h);
 }
@@ -315,11 +347,16 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     size_t yel = kk ? sizeof(float2) : sizeof(float);
     for (int i = 0; i < 2; i++) {
         RX_ALLOC(h->codes[i], (h->nhist + nb) * sizeof(uint16_t));
-        RX_ALLOC(h->Y[i], h->y_cap * yel);
         RX_ALLOC(h->taps[i], 32 * sizeof(float2));
     }
+    for (int i = 0; i < kSlots; i++) {
+        RX_ALLOC(h->Y[i], h->y_cap * yel);
+        RX_ALLOC(h->dec[i], h->dec_cap);
+        RX_ALLOC(h->winb[i], h->win_cap);
+        RX_ALLOC(h->winrec[i], h->win_cap * sizeof(uint4));
+    }
     if (kk) {
-        for (int i = 0; i < 2; i++) RX_ALLOC(h->E[i], (kEHist + nb) * sizeof(float2));
+        for (int i = 0; i < kSlots; i++) RX_ALLOC(h->E[i], (kEHist + nb) * sizeof(float2));
         for (int i = 0; i < 2; i++) RX_ALLOC(h->phist[i], (size_t)h->nhist * 3 / 2 + 16);
         RX_ALLOC(h->fftws, (size_t)h->npairs_max * h->N * sizeof(float2));
         int gx = (h->N2 + kCtaK1 - 1) / kCtaK1;
@@ -330,14 +367,11 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         RX_ALLOC(h->sqt, kLutCodes * sizeof(float));
         RX_ALLOC(h->ds_tab, c.ds_den * sizeof(float2));
     }
-    RX_ALLOC(h->dec, h->dec_cap);
-    RX_ALLOC(h->winb, h->win_cap);
     RX_ALLOC(h->prbs, 32767 + 256);
     RX_ALLOC(h->prbs_bits, 1040 * sizeof(uint32_t));
-    RX_ALLOC(h->winrec, h->win_cap * sizeof(uint4));
     RX_ALLOC(h->rrc, (2 * h->hmf + 1) * sizeof(float));
     RX_ALLOC(h->st, sizeof(DevState));
-    RX_ALLOC(h->in_stage, nb * 3 / 2 + 16);
+    for (int i = 0; i < 2; i++) RX_ALLOC(h->in_stage[i], nb * 3 / 2 + 16);
     RX_ALLOC(h->bits_stage, rx_max_bits(h) / 8 + 16);
     if (c.debug) {
         RX_ALLOC(h->dbg_win, h->win_cap * sizeof(float4));
@@ -388,7 +422,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     }
     DevState s0;
     memset(&s0, 0, sizeof s0);
-    s0.gain = 1.0;
+    for (int i = 0; i < kSlots; i++) s0.cg[i][2] = 1.0;
     s0.amb_r = -1;
     if (e == cudaSuccess) e = cudaMemcpy(h->st, &s0, sizeof s0, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -398,16 +432,34 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     }
     h->ebase_cur = -kEHist;
     h->ybase_cur = -kYHist;
+    {
+        bool ok = cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
+        cudaEvent_t *evs[] = {&h->ev_front, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1], &h->ev_yfree[2],
+                              &h->ev_inready[0], &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
+        for (cudaEvent_t *ev : evs)
+            ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            rx_destroy(h);
+            return RX_ECUDA;
+        }
+    }
     *out = h;
     return RX_OK;
 }
 
-rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *stream, int64_t *nbits_out)
+// Enqueue one buffer: field reconstruction and matched filter on `sf`, equaliser,
+// decisions and bits on `sb` (the same stream for rx_process).  With two streams
+// the back end of this call waits for its front end, and the front end of a later
+// call that reuses a matched-filter slot waits for the back end that read it.
+// With host buffers (host_in / host_out non-null) the input is copied into one of
+// two staging buffers on `sc`, overlapping the previous front end, and the bits
+// are copied back on `sb` after the demap.
+static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out, const uint8_t *host_in,
+                              uint8_t *host_out, cudaStream_t sf, cudaStream_t sb, cudaStream_t sc,
+                              int64_t *nbits_out)
 {
-    if (!h || !in || !nbits_out) return RX_EINVAL;
-    if (h->broken) return RX_ESTATE;
-    if (((uintptr_t)in) & 15) return RX_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
     const rx_config &c = h->cfg;
     Sched s = schedule(h, h->calls, h->q_prev);
     long long base = h->calls * h->nb;
@@ -415,21 +467,35 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
     bool do_train = !h->trained && s.q_k >= c.ntrain && s.q_k > 0;
     long long pay_lo = do_train ? c.ntrain : h->q_prev;
     long long npay = (h->trained || do_train) ? s.q_k - pay_lo : 0;
-    if (npay > 0 && !bits_out) return RX_EINVAL;
+    if (npay > 0 && !bits_out && !host_out) return RX_EINVAL;
+    const bool two = sf != sb;
     cudaError_t e = cudaSuccess;
     int par = (int)(h->calls & 1);
+    int ds = (int)(h->calls % kSlots);   // decision slot of this call
+    if (host_in) {
+        in = h->in_stage[par];
+        if (sc != sf) cudaStreamWaitEvent(sc, h->ev_infree[par], 0);   // the front end two calls back is done
+        e = cudaMemcpyAsync(h->in_stage[par], host_in, (size_t)(h->nb * 3 / 2), cudaMemcpyHostToDevice, sc);
+        if (sc != sf) {
+            cudaEventRecord(h->ev_inready[par], sc);
+            cudaStreamWaitEvent(sf, h->ev_inready[par], 0);
+        }
+    }
+    if (host_out) bits_out = h->bits_stage;
 
-    if (h->prof_on && h->prof_head - h->prof_tail >= kProfRing) prof_harvest_one(h);
-    prof_mark(h, 0, st);
+    h->prof_cur = h->prof_on > 0 && h->calls % h->prof_on == 0;
+    if (h->prof_cur && h->prof_head - h->prof_tail >= kProfRing) prof_harvest_one(h);
+    prof_begin(h, 0, sf);
     // 12-bit unpack into [history | buffer]: the PAM chain's input; the KK kernels
     // read the packed bytes themselves, so there it only feeds the debug view
     if (!h->kk || c.debug) {
         int cw_new = h->cw ^ 1;
         e = launch_unpack(in, h->codes[cw_new], h->codes[h->cw], h->nb, h->nhist, h->nb, h->calls == 0,
                           c.pack_order, h->kk ? nullptr : &h->st->pam_s1[par],
-                          h->kk ? nullptr : &h->st->pam_s2[par], st);
+                          h->kk ? nullptr : &h->st->pam_s2[par], sf);
         h->cw = cw_new;
     }
+    prof_end(h, 0, sf);
     KkInput kin;
     if (h->kk) {
         kin.hist = h->phist[h->hw];
@@ -458,30 +524,38 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
         g.npairs = (g.J + 1) / 2;
         g.N2 = h->N2;
         g.sps = h->sps;
-        int ew_new = h->ew ^ 1;
+        int ew_new = (h->ew + 1) % kSlots;
+        g.slot = ew_new;
         KkTables tb = {h->lnt, h->sqt, h->twN, h->twN2};
-        e = launch_kk_front(g, kin, h->fftws, tb, h->E[ew_new], h->E[h->ew], h->partials, h->st, st,
-                            h->prof_on ? h : nullptr);
+        e = launch_kk_front(g, kin, h->fftws, tb, h->E[ew_new], h->E[h->ew], h->partials, h->st, sf,
+                            h->prof_cur ? h : nullptr);
         h->ew = ew_new;
         h->ebase_cur = g.ebase;
     } else if (e == cudaSuccess && h->kk) {
-        e = launch_kk_hist(kin, st);
+        e = launch_kk_hist(kin, sf);
     }
     if (h->kk) h->hw ^= 1;
     // matched filter
-    prof_mark(h, 4, st);
+    prof_begin(h, 4, sf);
     if (e == cudaSuccess && s.f_k > h->f_prev) {
         long long yb = 2 * h->q_prev - kYHist;
-        int yw_new = h->yw ^ 1;
+        int yw_new = (h->yw + 1) % kSlots;
+        if (two) cudaStreamWaitEvent(sf, h->ev_yfree[yw_new], 0);   // the back end is done with this slot
         if (h->kk)
             e = launch_kk_mf(h->E[h->ew], h->ebase_cur, s.e_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
-                             c.ds_den, h->st, (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw], h->ybase_cur,
-                             st, h->rrc_host);
+                             c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw],
+                             h->ybase_cur, sf, h->rrc_host);
         else
             e = launch_pam_mf(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->rrc, h->hmf, h->st, par,
-                              (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, st);
+                              (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf);
         h->yw = yw_new;
         h->ybase_cur = yb;
+    }
+    prof_end(h, 4, sf);
+    if (host_in && sc != sf) cudaEventRecord(h->ev_infree[par], sf);
+    if (two) {
+        cudaEventRecord(h->ev_front, sf);
+        cudaStreamWaitEvent(sb, h->ev_front, 0);
     }
     // equaliser, decisions, bits
     EqGeom g;
@@ -492,10 +566,10 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
     g.ybase = h->ybase_cur;
     g.nblk = npay > 0 ? (int)(npay / c.eq_block) : 0;
     g.nwin = npay > 0 ? (int)(npay / kWin) : 0;
-    prof_mark(h, 5, st);
+    prof_begin(h, 5, sb);
     if (e == cudaSuccess && do_train) {
-        e = launch_eq(h->ep, g, 1, h->Y[h->yw], h->taps[h->tw], nullptr, h->dec, h->winb, h->winrec, nullptr,
-                      h->dbg_z, h->prbs, h->prbs_bits, h->st, st);
+        e = launch_eq(h->ep, g, 1, h->Y[h->yw], h->taps[h->tw], nullptr, h->dec[ds], h->winb[ds], h->winrec[ds],
+                      nullptr, h->dbg_z, h->prbs, h->prbs_bits, h->st, sb);
         h->trained = 1;
     }
     if (e == cudaSuccess && g.nblk > 0) {
@@ -503,25 +577,30 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
             // learned equaliser: one segment per payload window
             long long seg_base = 2 * pay_lo - 12 - h->ybase_cur;
             e = launch_cnn_decide(rx_cnn_dev_params(h->cnn), rx_cnn_dev_params_bf16(h->cnn),
-                                  (const float2 *)h->Y[h->yw], seg_base, g.nwin, h->dec, h->winb, h->winrec,
-                                  h->prbs_bits, pay_lo, h->ep.scale, h->mq, st);
+                                  (const float2 *)h->Y[h->yw], seg_base, g.nwin, h->dec[ds], h->winb[ds],
+                                  h->winrec[ds], h->prbs_bits, pay_lo, h->ep.scale, h->mq, sb);
         } else {
-            e = launch_eq(h->ep, g, 0, h->Y[h->yw], h->taps[h->tw], h->taps[h->tw ^ 1], h->dec, h->winb, h->winrec,
-                          h->dbg_win, h->dbg_z, h->prbs, h->prbs_bits, h->st, st);
+            e = launch_eq(h->ep, g, 0, h->Y[h->yw], h->taps[h->tw], h->taps[h->tw ^ 1], h->dec[ds], h->winb[ds],
+                          h->winrec[ds], h->dbg_win, h->dbg_z, h->prbs, h->prbs_bits, h->st, sb);
             h->tw ^= 1;
         }
-        prof_mark(h, 6, st);
-        if (e == cudaSuccess) {
-            int resolve = h->kk && !h->amb_done;
-            e = launch_demap(h->ep, g, resolve, h->uw, h->dec, h->winb, h->winrec, h->dbg_win, bits_out, h->st, st);
-            if (h->kk) h->uw ^= 1;
-            h->amb_done = 1;
-        }
     }
-    if (h->prof_on) {
-        prof_mark(h, kStages, st);
-        h->prof_head++;
+    prof_end(h, 5, sb);
+    if (two) cudaEventRecord(h->ev_yfree[h->yw], sb);
+    if (e == cudaSuccess && g.nblk > 0) {
+        prof_begin(h, 6, sb);
+        int resolve = h->kk && !h->amb_done;
+        e = launch_demap(h->ep, g, resolve, h->uw, h->dec[ds], h->winb[ds], h->winrec[ds], h->dbg_win, bits_out,
+                         h->st, sb);
+        if (h->kk) h->uw ^= 1;
+        h->amb_done = 1;
+        prof_end(h, 6, sb);
+        if (e == cudaSuccess && host_out)
+            e = cudaMemcpyAsync(host_out, h->bits_stage, (size_t)((h->bps * npay + 7) / 8), cudaMemcpyDeviceToHost,
+                                sb);
     }
+    if (h->prof_cur) h->prof_head++;
+    h->prof_cur = 0;
     if (e != cudaSuccess) {
         h->broken = 1;
         return RX_ECUDA;
@@ -534,6 +613,7 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
     h->l_pay_lo = pay_lo;
     h->l_q_k = s.q_k;
     h->l_nwin = g.nwin;
+    h->l_ds = ds;
     h->e_prev = s.e_k;
     h->f_prev = s.f_k;
     h->q_prev = s.q_k;
@@ -542,21 +622,67 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
     return RX_OK;
 }
 
+rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *stream, int64_t *nbits_out)
+{
+    if (!h || !in || !nbits_out) return RX_EINVAL;
+    if (h->broken) return RX_ESTATE;
+    if (((uintptr_t)in) & 15) return RX_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    return enqueue_call(h, in, bits_out, nullptr, nullptr, st, st, st, nbits_out);
+}
+
+// n calls of enqueue_call on the pipeline's streams, joined onto the caller's stream
+static rx_status run_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *const *outs, bool host, int n,
+                           void *stream, int64_t *nbits_out)
+{
+    cudaStream_t sf = (cudaStream_t)stream;
+    const bool one = h->cfg.debug != 0;             // debug views want one call at a time
+    cudaStream_t sb = one ? sf : h->back;
+    cudaStream_t sc = one ? sf : h->copy;
+    if (!one && host) {
+        // the copy stream must not overwrite a staging buffer before earlier work on the caller's stream
+        if (cudaEventRecord(h->ev_join, sf) != cudaSuccess || cudaStreamWaitEvent(sc, h->ev_join, 0) != cudaSuccess)
+            return RX_ECUDA;
+    }
+    for (int i = 0; i < n; i++) {
+        rx_status r = host ? enqueue_call(h, nullptr, nullptr, ins[i], outs[i], sf, sb, sc, &nbits_out[i])
+                           : enqueue_call(h, ins[i], outs[i], nullptr, nullptr, sf, sb, sc, &nbits_out[i]);
+        if (r != RX_OK) return r;
+    }
+    if (!one) {
+        if (cudaEventRecord(h->ev_join, sb) != cudaSuccess || cudaStreamWaitEvent(sf, h->ev_join, 0) != cudaSuccess)
+            return RX_ECUDA;
+    }
+    return RX_OK;
+}
+
+rx_status rx_process_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *const *outs, int n, void *stream,
+                           int64_t *nbits_out)
+{
+    if (!h || !ins || !outs || !nbits_out || n <= 0) return RX_EINVAL;
+    if (h->broken) return RX_ESTATE;
+    for (int i = 0; i < n; i++)
+        if (!ins[i] || (((uintptr_t)ins[i]) & 15)) return RX_EINVAL;
+    return run_batch(h, ins, outs, false, n, stream, nbits_out);
+}
+
+rx_status rx_process_host_batch(rx_handle *h, const uint8_t *const *host_ins, uint8_t *const *host_outs, int n,
+                                void *stream, int64_t *nbits_out)
+{
+    if (!h || !host_ins || !host_outs || !nbits_out || n <= 0) return RX_EINVAL;
+    if (h->broken) return RX_ESTATE;
+    for (int i = 0; i < n; i++)
+        if (!host_ins[i] || !host_outs[i]) return RX_EINVAL;
+    return run_batch(h, host_ins, host_outs, true, n, stream, nbits_out);
+}
+
 rx_status rx_process_host(rx_handle *h, const uint8_t *host_in, uint8_t *host_bits_out, void *stream,
                           int64_t *nbits_out)
 {
     if (!h || !host_in || !host_bits_out || !nbits_out) return RX_EINVAL;
     if (h->broken) return RX_ESTATE;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(h->in_stage, host_in, (size_t)(h->nb * 3 / 2), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return RX_ECUDA;
-    rx_status r = rx_process(h, h->in_stage, h->bits_stage, stream, nbits_out);
-    if (r != RX_OK) return r;
-    if (*nbits_out > 0 &&
-        cudaMemcpyAsync(host_bits_out, h->bits_stage, (size_t)((*nbits_out + 7) / 8), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess)
-        return RX_ECUDA;
-    return RX_OK;
+    return enqueue_call(h, nullptr, nullptr, host_in, host_bits_out, st, st, st, nbits_out);
 }
 
 static double q_from_ber(double ber)
@@ -629,7 +755,7 @@ rx_status rx_debug_copy(rx_handle *h, int what, void *dst, int64_t cap, int64_t 
         n = h->l_q_k - h->l_pay_lo;
         if (n < 0) n = 0;
         s0 = h->l_pay_lo;
-        src = h->dec;
+        src = h->dec[h->l_ds];
         el = 1;
         break;
     case RX_DBG_WIN:
@@ -654,7 +780,7 @@ rx_status rx_debug_copy(rx_handle *h, int what, void *dst, int64_t cap, int64_t 
     case RX_DBG_SCAL: {
         DevState s;
         if (cudaMemcpy(&s, h->st, sizeof s, cudaMemcpyDeviceToHost) != cudaSuccess) return RX_ECUDA;
-        double v[5] = {s.carrier_re, s.carrier_im, s.gain, s.pam_mu, s.pam_inv_sd};
+        double v[5] = {s.cg[h->ew][0], s.cg[h->ew][1], s.cg[h->ew][2], s.pam_mu, s.pam_inv_sd};
         *count = 5;
         *start = 0;
         if (dst) memcpy(dst, v, sizeof(double) * (size_t)(cap < 5 ? cap : 5));
@@ -674,15 +800,15 @@ rx_status rx_debug_copy(rx_handle *h, int what, void *dst, int64_t cap, int64_t 
 
 rx_status rx_profile(rx_handle *h, int enable)
 {
-    if (!h) return RX_EINVAL;
+    if (!h || enable < 0) return RX_EINVAL;
     if (enable && !h->prof_ev) {
-        h->prof_ev = (cudaEvent_t *)calloc((size_t)kProfRing * kStages1, sizeof(cudaEvent_t));
+        h->prof_ev = (cudaEvent_t *)calloc((size_t)kProfRing * kEvPerCall, sizeof(cudaEvent_t));
         h->prof_used = (int *)calloc(kProfRing, sizeof(int));
         if (!h->prof_ev || !h->prof_used) return RX_ENOMEM;
-        for (int i = 0; i < kProfRing * kStages1; i++)
+        for (int i = 0; i < kProfRing * kEvPerCall; i++)
             if (cudaEventCreate(&h->prof_ev[i]) != cudaSuccess) return RX_ECUDA;
     }
-    h->prof_on = enable ? 1 : 0;
+    h->prof_on = enable;
     return RX_OK;
 }
 

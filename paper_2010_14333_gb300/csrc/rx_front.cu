@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
         partials[cta].im = b;
         partials[cta].i2 = c;
         __threadfence();
-        unsigned tk = atomicAdd(&dst->ticket, 1u);
+        unsigned tk = atomicAdd(&dst->ticket[g.slot], 1u);
         last = (tk == (unsigned)(ncta - 1));
     }
     __syncthreads();
@@ -500,10 +500,10 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
         double cr = dre[0] / cnt, ci = dim[0] / cnt;
         double ibar = (double)dii[0] / (2.0 * cnt);
         double P = ibar - (cr * cr + ci * ci);
-        dst->carrier_re = cr;
-        dst->carrier_im = ci;
-        dst->gain = (P > 0.0) ? 1.0 / sqrt((double)g.sps * P) : 1.0;
-        dst->ticket = 0u;
+        dst->cg[g.slot][0] = cr;
+        dst->cg[g.slot][1] = ci;
+        dst->cg[g.slot][2] = (P > 0.0) ? 1.0 / sqrt((double)g.sps * P) : 1.0;
+        dst->ticket[g.slot] = 0u;
     }
 }
 
@@ -547,7 +547,7 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     dim3 grid_a(g.N2 / kCtaK1, g.npairs + (inp.hist_next ? 1 : 0));
     prof_stage(prof, 1, st);
     k_kk_fwd<<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
-    prof_stage(prof, 2, st);
+    prof_stage(prof, -2, st);
     int rows = g.npairs * 16;
     if (g.N2 == 4096) {
         size_t smem = (size_t)(4096 + 256) * sizeof(float2);
@@ -558,8 +558,9 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     } else {
         k_kk_rows<1><<<(rows + 255) / 256, 256, 0, st>>>(g, fftws, tb.twN2);
     }
-    prof_stage(prof, 3, st);
+    prof_stage(prof, -3, st);
     k_kk_inv<<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, partials, dst);
+    prof_stage(prof, -4, st);
     return cudaGetLastError();
 }
 
@@ -572,15 +573,15 @@ constexpr int kMfOut = 256;
 __global__ void __launch_bounds__(kMfOut) k_kk_mf(const float2 *__restrict__ E, long long ebase, long long e_k,
                                                  long long f_prev, long long f_k, const float *__restrict__ rrc,
                                                  int hmf, const float2 *__restrict__ ds_tab, int ds_num,
-                                                 int ds_den, const DevState *__restrict__ dst,
+                                                 int ds_den, const double *__restrict__ cg,
                                                  float2 *__restrict__ Y, long long ybase,
                                                  const float2 *__restrict__ Y_prev, long long ybase_prev)
 {
     extern __shared__ float2 xs[];
     long long m0 = f_prev + (long long)blockIdx.x * kMfOut;
     int L = 2 * kMfOut + 2 * hmf;
-    float2 c = make_float2((float)dst->carrier_re, (float)dst->carrier_im);
-    float gn = (float)dst->gain;
+    float2 c = make_float2((float)cg[0], (float)cg[1]);
+    float gn = (float)cg[2];
     long long n0 = 2 * m0 - hmf;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         long long n = n0 + i;
@@ -630,7 +631,7 @@ template <int HMF>
 __global__ void __launch_bounds__(kMfThreads) k_kk_mf_t(const float2 *__restrict__ E, long long ebase,
                                                        long long e_k, long long f_prev, long long f_k,
                                                        const MfTaps<HMF> taps, const float2 *__restrict__ ds_tab,
-                                                       int ds_num, int ds_den, const DevState *__restrict__ dst,
+                                                       int ds_num, int ds_den, const double *__restrict__ cg,
                                                        float2 *__restrict__ Y, long long ybase,
                                                        const float2 *__restrict__ Y_prev, long long ybase_prev)
 {
@@ -638,8 +639,8 @@ __global__ void __launch_bounds__(kMfThreads) k_kk_mf_t(const float2 *__restrict
     extern __shared__ float4 pr[];     // padded pair tile
     long long m0 = f_prev + (long long)blockIdx.x * kMfTileOut;
     long long n0 = 2 * m0 - HMF;
-    const float2 c = make_float2((float)dst->carrier_re, (float)dst->carrier_im);
-    const float gn = (float)dst->gain;
+    const float2 c = make_float2((float)cg[0], (float)cg[1]);
+    const float gn = (float)cg[2];
     // integer phase index of the downshift, advanced incrementally
     int idx = (int)((((n0 % ds_den) + ds_den) % ds_den + 2LL * threadIdx.x) % ds_den);
     idx = (int)(((long long)idx * ds_num) % ds_den);
@@ -708,7 +709,7 @@ __global__ void __launch_bounds__(kMfThreads) k_kk_mf_t(const float2 *__restrict
 
 cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long long f_prev,
                          long long f_k, const float *rrc, int hmf, const float2 *ds_tab,
-                         int ds_num, int ds_den, const DevState *dst, float2 *Y, long long ybase,
+                         int ds_num, int ds_den, const double *cg, float2 *Y, long long ybase,
                          const float2 *Y_prev, long long ybase_prev, cudaStream_t st,
                          const float *rrc_host)
 {
@@ -719,14 +720,14 @@ cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long l
         for (int u = 0; u < 32; u++) t.go[u] = rrc_host[32 + (32 - 2 * u - 1)];
         unsigned grid = (unsigned)((n + kMfTileOut - 1) / kMfTileOut);
         size_t smem = (size_t)pad8(kMfTileOut + 32 + kMfR) * sizeof(float4) + 16;
-        k_kk_mf_t<32><<<grid, kMfThreads, smem, st>>>(E, ebase, e_k, f_prev, f_k, t, ds_tab, ds_num, ds_den, dst,
+        k_kk_mf_t<32><<<grid, kMfThreads, smem, st>>>(E, ebase, e_k, f_prev, f_k, t, ds_tab, ds_num, ds_den, cg,
                                                       Y, ybase, Y_prev, ybase_prev);
         return cudaGetLastError();
     }
     unsigned grid = (unsigned)((n + kMfOut - 1) / kMfOut);
     size_t smem = (size_t)(2 * kMfOut + 2 * hmf) * sizeof(float2);
     k_kk_mf<<<grid, kMfOut, smem, st>>>(E, ebase, e_k, f_prev, f_k, rrc, hmf, ds_tab, ds_num,
-                                        ds_den, dst, Y, ybase, Y_prev, ybase_prev);
+                                        ds_den, cg, Y, ybase, Y_prev, ybase_prev);
     return cudaGetLastError();
 }
 

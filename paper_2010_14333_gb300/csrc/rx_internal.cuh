@@ -17,6 +17,7 @@ constexpr int kPamHist = 64;      // codes kept before a PAM buffer (>= 2 * MF h
 constexpr int kCtaK1 = 256;       // threads per K1a / K1c CTA
 constexpr int kEqWarps = 4;       // warps (equaliser blocks) per K3 CTA
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before flagging RX_ETIMEOUT
+constexpr int kSlots = 3;         // per-call buffer ring (field, MF output, decisions, carrier/gain)
 
 // counters in DevState::cnt
 enum { C_SYMBOLS, C_BITS, C_BITERR, C_RAWERR, C_SYMERR, C_SLIP, C_NEAR, C_AMBIG, C_WINDOWS, C_NCNT };
@@ -24,14 +25,14 @@ enum { C_SYMBOLS, C_BITS, C_BITERR, C_RAWERR, C_SYMERR, C_SLIP, C_NEAR, C_AMBIG,
 // device-resident state of one stream
 struct DevState {
     unsigned long long cnt[C_NCNT];
-    double carrier_re, carrier_im, gain;   // KK: this call's carrier and gain
+    double cg[kSlots][4];                  // KK per slot: carrier re, carrier im, gain
     double pam_mu, pam_inv_sd;             // PAM: this call's normalisation (debug view)
     long long pam_s1[2], pam_s2[2];        // PAM: integer sums of codes / codes^2, by call parity
     int unwrap_have[2], unwrap_b[2];       // pi/2 unwrap carry, by parity
     long long unwrap_m[2];
     int amb_r;                             // stream-start rotation, -1 before
     int first_code;                        // 12-bit code of the stream's first sample
-    unsigned int ticket;                   // last-CTA ticket of the carrier reduction
+    unsigned int ticket[kSlots];           // last-CTA ticket of the carrier reduction, per slot
     int err;                               // RX_ETIMEOUT when a bounded wait ran out
 };
 
@@ -51,6 +52,7 @@ struct KkGeom {
     long long ebase_prev;      // same for the previous field workspace
     int N, V, hop, J, npairs, N2;
     int sps;
+    int slot;                  // carrier / gain slot written by this call
 };
 
 // constant tables of the KK front end (device pointers).  Twiddles of an M-point
@@ -109,7 +111,7 @@ void prof_stage(void *prof, int stage, cudaStream_t st);
 
 cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long long f_prev,
                          long long f_k, const float *rrc, int hmf, const float2 *ds_tab,
-                         int ds_num, int ds_den, const DevState *dst, float2 *Y, long long ybase,
+                         int ds_num, int ds_den, const double *cg, float2 *Y, long long ybase,
                          const float2 *Y_prev, long long ybase_prev, cudaStream_t st,
                          const float *rrc_host);
 

@@ -103,6 +103,7 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     g.ebase = -kEHist;                  // field: [kEHist history | buffer]
     g.ebase_prev = -kEHist;
     g.sps = 4;
+    g.slot = 0;
     size_t need_fft = (size_t)g.npairs * ols_n * sizeof(float2);
     size_t need_part = (size_t)((g.N2 + kCtaK1 - 1) / kCtaK1) * g.npairs * sizeof(CarrierPartial);
     if (need_fft > kFftBytes || need_part > kPartBytes) return RX_EINVAL;

@@ -69,3 +69,13 @@ def test_create_rejects_bad_config(field, value):
     setattr(c, field, value)
     h = C.c_void_p()
     assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
+
+
+def test_null_handle_calls_are_rejected():
+    lib = rx.load()
+    n = (C.c_int64 * 2)()
+    ptrs = (C.c_void_p * 2)(16, 32)
+    assert lib.rx_process(None, ptrs[0], ptrs[1], None, n) == 1
+    assert lib.rx_process_batch(None, ptrs, ptrs, 2, None, n) == 1
+    assert lib.rx_process_host_batch(None, ptrs, ptrs, 2, None, n) == 1
+    assert lib.rx_process_host(None, ptrs[0], ptrs[1], None, n) == 1
