@@ -29,6 +29,7 @@ class OrxCfg(C.Structure):
         ("ncma", C.c_int32), ("eq_block", C.c_int32), ("win", C.c_int32),
         ("mu", C.c_double), ("mu_train", C.c_double), ("mu_cma", C.c_double),
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
+        ("eq_frozen", C.c_int32),
     ]
 
 
@@ -183,10 +184,10 @@ def cnn_param_slices():
 KK_DEFAULTS = dict(sps=4, pack_order=0, ols_n=65536, ols_v=4096, ds_num=11, ds_den=80,
                    rrc_beta=0.1, mf_span=16, ntaps=31, ntrain=16384, ncma=8192, eq_block=256,
                    win=64, mu=1e-3, mu_train=1e-3, mu_cma=1e-3, bps_b=32, amb_syms=1024,
-                   prbs_seed=1)
+                   prbs_seed=1, eq_frozen=0)
 PAM_DEFAULTS = dict(sps=2, pack_order=0, ols_n=0, ols_v=0, ds_num=0, ds_den=1, rrc_beta=0.1,
                     mf_span=16, ntaps=15, ntrain=4096, ncma=0, eq_block=256, win=64, mu=1e-3,
-                    mu_train=1e-3, mu_cma=0.0, bps_b=1, amb_syms=0, prbs_seed=1)
+                    mu_train=1e-3, mu_cma=0.0, bps_b=1, amb_syms=0, prbs_seed=1, eq_frozen=0)
 
 
 def default_cfg(fmt: int, buf_len: int, **kw) -> dict:

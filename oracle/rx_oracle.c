@@ -362,7 +362,7 @@ static cx y_at(const ctx *x, int64_t m)
 typedef struct { int b; double best, second; } winres;
 
 static winres eq_window(ctx *x, cx *w, int64_t k0, int mode, double mu,
-                        cx *z, cx *v, int32_t *draw, int32_t *nearf)
+                        cx *z, cx *v, int32_t *draw, int32_t *nearf, cx *grad)
 {
     orx *h = x->h;
     int W = h->c.win, th = h->th;
@@ -416,7 +416,8 @@ static winres eq_window(ctx *x, cx *w, int64_t k0, int mode, double mu,
     for (int i = -th; i <= th; i++) {
         cx g = cx_mk(0.0, 0.0);
         for (int q = 0; q < W; q++) g = cx_add(g, cx_mul(y_at(x, 2 * (k0 + q) - i), cx_conj(e[q])));
-        w[i + th] = cx_add(w[i + th], cx_scale(g, mu));
+        if (grad) grad[i + th] = cx_add(grad[i + th], g);   /* frozen taps: gradient only */
+        else w[i + th] = cx_add(w[i + th], cx_scale(g, mu));
     }
     return R;
 }
@@ -523,7 +524,7 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
         for (int64_t k0 = 0; k0 < c->ntrain; k0 += W) {
             int mode = h->kk ? (k0 < c->ncma ? 0 : 2) : 1;
             double mu = h->kk ? (mode == 0 ? c->mu_cma : c->mu) : c->mu_train;
-            eq_window(&X, h->w, k0, mode, mu, Z + k0, Vv + k0, draw + 2 * k0, nearf + k0);
+            eq_window(&X, h->w, k0, mode, mu, Z + k0, Vv + k0, draw + 2 * k0, nearf + k0, NULL);
         }
         h->trained = 1;
         pay_lo = c->ntrain;
@@ -536,19 +537,34 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
         /* payload: independent blocks of eq_block symbols, all starting from the
          * same taps (block parallelism of the 8192 data blocks, Sec. 2) */
         cx *wb = xcalloc((size_t)c->ntaps, sizeof(cx)), *wlast = xcalloc((size_t)c->ntaps, sizeof(cx));
+        /* frozen taps (eq_frozen, KK, reading of the block-Toeplitz form): every
+         * symbol of a block is filtered with the taps the call started from, so
+         * the filter of the whole call is one fixed FIR; the gradient of the last
+         * block, sum_k y[2k-i] conj(e_k), is summed window by window, and the next
+         * call starts from w + mu (W / eq_block) times it, i.e. the mean of the
+         * block's per-window steps */
+        int frozen = h->kk && c->eq_frozen;
+        cx *gsum = xcalloc((size_t)c->ntaps, sizeof(cx)), *gdrop = xcalloc((size_t)c->ntaps, sizeof(cx));
         for (int64_t b0 = pay_lo; b0 < q_k; b0 += c->eq_block) {
             memcpy(wb, h->w, sizeof(cx) * (size_t)c->ntaps);
+            int last = b0 + c->eq_block >= q_k;
             for (int64_t k0 = b0; k0 < b0 + c->eq_block; k0 += W) {
                 int64_t o = k0 - sym_lo;
-                winres R = eq_window(&X, wb, k0, 2, c->mu, Z + o, Vv + o, draw + 2 * o, nearf + o);
+                winres R = eq_window(&X, wb, k0, 2, c->mu, Z + o, Vv + o, draw + 2 * o, nearf + o,
+                                     frozen ? (last ? gsum : gdrop) : NULL);
                 int64_t wi = (k0 - pay_lo) / W;
                 dwin[4 * wi] = R.b; dwin[4 * wi + 2] = R.best; dwin[4 * wi + 3] = R.second;
                 if (h->kk && (R.second - R.best) <= 1e-6 * R.best) h->n_amb++;
             }
-            memcpy(wlast, wb, sizeof(cx) * (size_t)c->ntaps);
+            if (!frozen) memcpy(wlast, wb, sizeof(cx) * (size_t)c->ntaps);
         }
-        memcpy(h->w, wlast, sizeof(cx) * (size_t)c->ntaps);
-        free(wb); free(wlast);
+        if (frozen) {
+            double step = c->mu * (double)W / (double)c->eq_block;
+            for (int i = 0; i < c->ntaps; i++) h->w[i] = cx_add(h->w[i], cx_scale(gsum[i], step));
+        } else {
+            memcpy(h->w, wlast, sizeof(cx) * (size_t)c->ntaps);
+        }
+        free(wb); free(wlast); free(gsum); free(gdrop);
         /* integer pi/2 unwrap of the window phase index, carried across calls */
         for (int64_t wi = 0; wi < nwin; wi++) {
             int b = (int)dwin[4 * wi];

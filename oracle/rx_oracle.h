@@ -43,6 +43,10 @@ typedef struct {
     int32_t bps_b;       /* blind phase search test phases                             */
     int32_t amb_syms;    /* KK: payload symbols used to resolve the pi/2 ambiguity     */
     uint32_t prbs_seed;  /* PRBS-15 seed of the transmitted bits                       */
+    int32_t eq_frozen;   /* KK payload: 0 taps adapt window by window inside a block;
+                            1 every block filters with the call's start taps (block-
+                            Toeplitz form) and one averaged step over the last block
+                            gives the next call's taps                                */
 } orx_cfg;
 
 typedef struct {
