@@ -79,7 +79,23 @@ typedef struct {
                             start (multiple of win); they are not counted in the BER       */
     uint32_t prbs_seed;  /* PRBS-15 seed of the transmitted bits (BER reference)           */
     int32_t debug;       /* 1: keep soft symbols and window metrics for rx_debug_copy      */
+    int32_t fir_prec;    /* KK equaliser form (rx_fir_prec): RX_FIR_ADAPTIVE adapts the taps
+                            window by window inside each block (default); the others
+                            filter every payload block with the call's start taps and
+                            take one averaged LMS step over the last block: FP32 on the
+                            CUDA cores, or a block-Toeplitz GEMM on the tensor cores in
+                            BF16, FP16 or FP8-E4M3 (per-block scaling) with FP32
+                            accumulation.  The tensor-core forms need 2048 % eq_block == 0. */
 } rx_config;
+
+/* Equaliser forms and precisions (rx_config.fir_prec). */
+typedef enum {
+    RX_FIR_ADAPTIVE = 0,
+    RX_FIR_FROZEN_F32 = 1,
+    RX_FIR_BF16 = 2,
+    RX_FIR_FP16 = 3,
+    RX_FIR_FP8 = 4
+} rx_fir_prec;
 
 typedef struct {
     int64_t calls;             /* rx_process calls                                       */
@@ -197,6 +213,24 @@ rx_status rx_set_taps(rx_handle *h, const double *re, const double *im, int n);
  * measured to *calls, and clears the record. */
 rx_status rx_profile(rx_handle *h, int enable);
 rx_status rx_profile_read(rx_handle *h, double *ms, int n, int64_t *calls);
+
+/* Block-Toeplitz FIR with fixed taps on the tensor cores: the equaliser's
+ * filter in its frozen form (Sec. 2 equaliser; precision forms of the FIR
+ * contraction), exposed on its own so that its rounding can be measured.
+ *   z[k] = sum_{i=0}^{ntaps-1} conj(w[i]) y[2k + ntaps - 1 - i],  k = 0 .. nsym-1
+ * y:      DEVICE, complex FP32 interleaved (re, im), ny samples at 2 samples per
+ *         symbol, 16-byte aligned; ny >= 2 nsym + ntaps + 1.
+ * w:      DEVICE, ntaps complex FP32 taps (odd ntaps <= 31).
+ * prec:   RX_FIR_BF16, RX_FIR_FP16 or RX_FIR_FP8 (operands rounded to that type,
+ *         FP32 accumulation; FP8 scales y by a power of two per block of
+ *         scale_block symbols and w by one power of two, both undone on output).
+ * nsym:   multiple of 16; scale_block: multiple of 16 dividing 2048 and nsym.
+ * z_out:  DEVICE, nsym complex FP32, 16-byte aligned.
+ * status: DEVICE int32 the caller zeroed; a device-side wait that ran out writes
+ *         RX_ETIMEOUT there.
+ * Enqueued on cuda_stream; returns RX_EINVAL for bad arguments before launching. */
+rx_status rx_fir_block(const float *y, int64_t ny, const float *w, int ntaps, int prec, int64_t nsym,
+                       int scale_block, float *z_out, int32_t *status, void *cuda_stream);
 
 /* Kramers-Kronig field of one buffer without any device allocation.
  *

@@ -17,6 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librx.so")
 
 RX_PAM2, RX_PAM4, RX_PAM8, RX_KK_QPSK, RX_KK_16QAM = range(5)
+RX_FIR_ADAPTIVE, RX_FIR_FROZEN_F32, RX_FIR_BF16, RX_FIR_FP16, RX_FIR_FP8 = range(5)
 RX_DBG_FIELD, RX_DBG_MF, RX_DBG_SOFT, RX_DBG_DEC, RX_DBG_WIN, RX_DBG_TAPS, RX_DBG_SCAL, RX_DBG_CODES = range(1, 9)
 BITS_PER_SYMBOL = {0: 1, 1: 2, 2: 3, 3: 2, 4: 4}
 
@@ -29,7 +30,7 @@ class RxConfig(C.Structure):
         ("ncma", C.c_int32), ("eq_block", C.c_int32), ("win", C.c_int32),
         ("mu", C.c_double), ("mu_train", C.c_double), ("mu_cma", C.c_double),
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
-        ("debug", C.c_int32),
+        ("debug", C.c_int32), ("fir_prec", C.c_int32),
     ]
 
 
@@ -52,7 +53,7 @@ EXPORTED = sorted(["rx_default_config", "rx_create", "rx_process", "rx_process_h
                    "rx_profile", "rx_profile_read", "rx_kk_field_noalloc", "rx_cnn_nparams", "rx_cnn_create",
                    "rx_cnn_set_params", "rx_cnn_get_params", "rx_cnn_forward", "rx_cnn_grad",
                    "rx_cnn_adam_step", "rx_cnn_destroy", "rx_set_cnn", "rx_process_batch",
-                   "rx_process_host_batch"])
+                   "rx_process_host_batch", "rx_fir_block"])
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
 
 _lib = None
@@ -73,6 +74,7 @@ def load(path: str = LIB_PATH):
     L.rx_process_host.argtypes = [vp, vp, vp, vp, P(i64)]
     L.rx_process_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.rx_process_host_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
+    L.rx_fir_block.argtypes = [vp, i64, vp, C.c_int, C.c_int, i64, C.c_int, vp, vp, vp]
     L.rx_max_bits.argtypes = [vp]
     L.rx_max_bits.restype = i64
     L.rx_stats.argtypes = [vp, P(RxStats), vp]
@@ -148,6 +150,12 @@ def rx_process_host_batch(h: int, host_ins, host_outs, stream: int = 0):
     nb = (C.c_int64 * n)()
     _check(load().rx_process_host_batch(h, ia, oa, n, stream, nb))
     return list(nb)
+
+
+def rx_fir_block(y: int, ny: int, w: int, ntaps: int, prec: int, nsym: int, scale_block: int, z: int,
+                 status: int, stream: int = 0):
+    """Tensor-core block-Toeplitz FIR (device pointers; see include/rx.h)."""
+    _check(load().rx_fir_block(y, ny, w, ntaps, prec, nsym, scale_block, z, status, stream))
 
 
 def rx_process_host(h: int, host_in: int, host_bits_out: int, stream: int = 0) -> int:
@@ -262,7 +270,10 @@ class Receiver:
         self.buf_len = buf_len
         baud = baud if baud is not None else (fs / 4 if fmt >= 3 else fs / 2)
         c = rx_default_config(fmt)
+        names = {f for f, _ in RxConfig._fields_}
         for k, v in cfg.items():
+            if k not in names:
+                raise TypeError(f"unknown receiver option {k!r}")
             setattr(c, k, v)
         self.cfg = c
         self.h = rx_create(fmt, baud, fs, buf_len, c)

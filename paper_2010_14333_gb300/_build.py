@@ -10,7 +10,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librx.so")
-SOURCES = ["rx_front.cu", "rx_eq.cu", "rx_api.cu", "rx_noalloc.cu", "rx_cnn.cu"]
+SOURCES = ["rx_front.cu", "rx_eq.cu", "rx_fir_tc.cu", "rx_api.cu", "rx_noalloc.cu", "rx_cnn.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

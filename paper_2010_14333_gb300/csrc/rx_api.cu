@@ -51,6 +51,7 @@ struct rx_handle {
     float2 *dbg_z;
     DevState *st;
     uint8_t *in_stage[2], *bits_stage;   // device staging of the host-buffer entry points
+    float2 *zbuf;                   // payload soft symbols of the tensor-core FIR forms
     long long dec_cap, win_cap, y_cap;
     // stage timing: a ring of event sets, one per profiled call
     const rx_cnn *cnn;              // learned equaliser for the payload, or null
@@ -234,7 +235,7 @@ void rx_destroy(rx_handle *h)
                     h->winrec[0], h->winrec[1], h->winrec[2], h->prbs, h->taps[0], h->taps[1], h->twN, h->twN2,
                     h->ds_tab,
                     h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1], h->bits_stage, h->lnt, h->sqt,
-                    h->prbs_bits, h->phist[0], h->phist[1]};
+                    h->prbs_bits, h->phist[0], h->phist[1], h->zbuf};
     static_assert(kSlots == 3, "slot arrays listed above");
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -283,6 +284,9 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         c.mf_span < 0 || c.mf_span % 2 || sps * c.mf_span / 2 > kEHist / 2 || !(c.rrc_beta >= 0) ||
         c.rrc_beta > 1 || c.eq_block > 4096)
         return RX_EINVAL;
+    if (c.fir_prec < RX_FIR_ADAPTIVE || c.fir_prec > RX_FIR_FP8 || (c.fir_prec != RX_FIR_ADAPTIVE && !kk) ||
+        (c.fir_prec >= RX_FIR_BF16 && 2048 % c.eq_block))
+        return RX_EINVAL;
     if (kk && (c.ncma < 0 || c.ncma > c.ntrain || c.ncma % kWin || c.bps_b < 1 || c.bps_b > 32 ||
                c.ds_den < 1 || c.ds_num < 0 || c.amb_syms < 0 || c.amb_syms % kWin || c.amb_syms > 4096 ||
                !(c.ols_n == 4096 || c.ols_n == 65536) || c.ols_v < 64 || c.ols_v % 64 || c.ols_v >= c.ols_n))
@@ -325,6 +329,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     p.mu = (float)c.mu;
     p.mu_train = (float)c.mu_train;
     p.mu_cma = (float)c.mu_cma;
+    p.frozen = c.fir_prec != RX_FIR_ADAPTIVE;
 
     // the first call that emits payload must carry the ambiguity-resolution symbols
     if (kk && c.amb_syms > 0) {
@@ -373,6 +378,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     RX_ALLOC(h->st, sizeof(DevState));
     for (int i = 0; i < 2; i++) RX_ALLOC(h->in_stage[i], nb * 3 / 2 + 16);
     RX_ALLOC(h->bits_stage, rx_max_bits(h) / 8 + 16);
+    if (c.fir_prec >= RX_FIR_BF16) RX_ALLOC(h->zbuf, symcap * sizeof(float2));
     if (c.debug) {
         RX_ALLOC(h->dbg_win, h->win_cap * sizeof(float4));
         RX_ALLOC(h->dbg_z, symcap * sizeof(float2));
@@ -568,7 +574,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     g.nwin = npay > 0 ? (int)(npay / kWin) : 0;
     prof_begin(h, 5, sb);
     if (e == cudaSuccess && do_train) {
-        e = launch_eq(h->ep, g, 1, h->Y[h->yw], h->taps[h->tw], nullptr, h->dec[ds], h->winb[ds], h->winrec[ds],
+        e = launch_eq(h->ep, g, 1, h->Y[h->yw], nullptr, h->taps[h->tw], nullptr, h->dec[ds], h->winb[ds], h->winrec[ds],
                       nullptr, h->dbg_z, h->prbs, h->prbs_bits, h->st, sb);
         h->trained = 1;
     }
@@ -580,8 +586,16 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
                                   (const float2 *)h->Y[h->yw], seg_base, g.nwin, h->dec[ds], h->winb[ds],
                                   h->winrec[ds], h->prbs_bits, pay_lo, h->ep.scale, h->mq, sb);
         } else {
-            e = launch_eq(h->ep, g, 0, h->Y[h->yw], h->taps[h->tw], h->taps[h->tw ^ 1], h->dec[ds], h->winb[ds],
-                          h->winrec[ds], h->dbg_win, h->dbg_z, h->prbs, h->prbs_bits, h->st, sb);
+            const float2 *zin = nullptr;
+            if (c.fir_prec >= RX_FIR_BF16) {
+                // frozen taps: the whole payload's filter as one tensor-core GEMM
+                e = launch_fir_tc(c.fir_prec, (const float2 *)h->Y[h->yw], h->ybase_cur, pay_lo, npay,
+                                  h->taps[h->tw], c.ntaps, c.eq_block, h->zbuf, &h->st->err, sb);
+                zin = h->zbuf;
+            }
+            if (e == cudaSuccess)
+                e = launch_eq(h->ep, g, 0, h->Y[h->yw], zin, h->taps[h->tw], h->taps[h->tw ^ 1], h->dec[ds],
+                              h->winb[ds], h->winrec[ds], h->dbg_win, h->dbg_z, h->prbs, h->prbs_bits, h->st, sb);
             h->tw ^= 1;
         }
     }
@@ -821,6 +835,21 @@ rx_status rx_profile_read(rx_handle *h, double *ms, int n, int64_t *calls)
     memset(h->prof_ms, 0, sizeof h->prof_ms);
     h->prof_calls = 0;
     return RX_OK;
+}
+
+rx_status rx_fir_block(const float *y, int64_t ny, const float *w, int ntaps, int prec, int64_t nsym,
+                       int scale_block, float *z_out, int32_t *status, void *stream)
+{
+    if (!y || !w || !z_out || !status || ntaps < 1 || ntaps > kMaxTaps || !(ntaps & 1) || nsym <= 0 ||
+        nsym % 16 || prec < RX_FIR_BF16 || prec > RX_FIR_FP8 || scale_block < 16 || scale_block % 16 ||
+        2048 % scale_block || nsym % scale_block || ny < 2 * nsym + ntaps + 1 || (((uintptr_t)y) & 15) ||
+        (((uintptr_t)z_out) & 15))
+        return RX_EINVAL;
+    // y[j] holds stream index j - TH, so z_k = sum_i conj(w_i) y[2k + TH - i] in stream terms
+    cudaError_t e = launch_fir_tc(prec, (const float2 *)y, -(long long)((ntaps - 1) / 2), 0, nsym,
+                                  (const float2 *)w, ntaps, scale_block, (float2 *)z_out, (int *)status,
+                                  (cudaStream_t)stream);
+    return e == cudaSuccess ? RX_OK : RX_ECUDA;
 }
 
 rx_status rx_set_cnn(rx_handle *h, const rx_cnn *cnn)

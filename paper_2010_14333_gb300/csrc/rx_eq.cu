@@ -15,48 +15,19 @@
 // shuffle), lanes hold two symbols each in the filter and one tap each in the
 // update.  A block's 2-sps input is staged into shared memory by one bulk
 // asynchronous copy (cp.async.bulk, completion on an mbarrier).
+//
+// Frozen form (QAM only): every window of a block filters with the call's start
+// taps, so the filter of the call is one fixed FIR (computed here in FP32, or
+// passed in as soft symbols by the tensor-core block-Toeplitz kernel); the warp
+// of the last block sums sum_k y[2k+TH-i] conj(e_k) over its windows and writes
+// start taps + mu (64 / eq_block) times that sum as the next call's taps.
 #include <type_traits>
 
+#include "rx_async.cuh"
 #include "rx_common.cuh"
 #include "rx_internal.cuh"
 
 namespace rxk {
-
-// ------------------------------------------------------------ bulk copy / mbarrier
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-// bounded wait on phase `parity`; false when the poll limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
-{
-    for (int it = 0; it < kWaitLimit; it++) {
-        uint32_t done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done)
-                     : "r"(smem_u32(bar)), "r"(parity)
-                     : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 
 // ------------------------------------------------------------- symbol helpers
 __device__ __forceinline__ int gray(int L) { return L ^ (L >> 1); }
@@ -128,10 +99,11 @@ __device__ __forceinline__ float dist_t(float t, float acc)
     return fmaf(a, a, acc);
 }
 
-template <int NT, int MQ>
+template <int NT, int MQ, bool FRZ = false>
 __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys, int c0, float2 *zs, float2 *es,
                                              float2 *ws, int mode, float mu, int lane, uint8_t *dec_out,
-                                             float2 *dbg_z, const uint32_t *prbs_bits, int pwin)
+                                             float2 *dbg_z, const uint32_t *prbs_bits, int pwin,
+                                             const float2 *zin = nullptr, float2 *G = nullptr)
 {
     constexpr int TH = (NT - 1) / 2;
     constexpr int NP = (NT + 1) / 2;              // y pairs per symbol
@@ -148,6 +120,12 @@ __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         int q = lane + 32 * h;
+        if (FRZ && zin) {   // soft symbols from the block-Toeplitz kernel
+            float2 zq = zin[q];
+            zs[q] = zq;
+            if (dbg_z) dbg_z[q] = zq;
+            continue;
+        }
         const float4 *yp = reinterpret_cast<const float4 *>(ys + c0 + 2 * q - TH - 1);
         float ar = 0.f, ai = 0.f;
 #pragma unroll
@@ -254,8 +232,9 @@ __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys
         R.serr = warp_sum_i(se);
         R.nnear = warp_sum_i(nn);
     }
-    // block-LMS update after the window: w_i += mu sum_k y[2k + TH - i] conj(e_k)
-    if (lane < NT) {
+    // block-LMS update after the window: w_i += mu sum_k y[2k + TH - i] conj(e_k);
+    // frozen form: the sum only, accumulated in G (last block), taps unchanged
+    if (lane < NT && (!FRZ || G)) {
         float gr = 0.f, gi = 0.f;
         const float2 *yb = ys + (c0 + TH - lane);
         const float4 *e4 = reinterpret_cast<const float4 *>(es);
@@ -268,8 +247,13 @@ __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys
             gr = fmaf(y1.x, E.z, fmaf(y1.y, E.w, gr));
             gi = fmaf(y1.y, E.z, fmaf(-y1.x, E.w, gi));
         }
-        float2 wl = ws[lane];
-        ws[lane] = make_float2(fmaf(mu, gr, wl.x), fmaf(mu, gi, wl.y));
+        if (FRZ) {
+            G->x += gr;
+            G->y += gi;
+        } else {
+            float2 wl = ws[lane];
+            ws[lane] = make_float2(fmaf(mu, gr, wl.x), fmaf(mu, gi, wl.y));
+        }
     }
     __syncwarp();
     return R;
@@ -353,9 +337,10 @@ __device__ __forceinline__ WinOut pam_window(const EqParams &p, const float *ys,
 // Payload: one warp per block of eq_block symbols, input staged by one bulk copy.
 // Training (train=1): one warp runs the training windows sequentially, staging
 // each window's input with plain loads.
-template <bool QAM, int NT, int MQ>
+template <bool QAM, int NT, int MQ, bool FRZ = false>
 __global__ void __launch_bounds__(32 * kEqWarps)
-    k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Yv, float2 *taps_in, float2 *taps_out,
+    k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Yv, const float2 *__restrict__ zin,
+         float2 *taps_in, float2 *taps_out,
          uint8_t *__restrict__ dec, uint8_t *__restrict__ winb, uint4 *__restrict__ winrec,
          float4 *__restrict__ dbg_win, float2 *__restrict__ dbg_z, const uint8_t *__restrict__ prbs_ext,
          const uint32_t *__restrict__ prbs_bits, DevState *dst)
@@ -407,18 +392,23 @@ __global__ void __launch_bounds__(32 * kEqWarps)
     }
     long long kb = g.pay_lo + blk * B;
     long long ym0 = 2 * kb - kYHist;
-    if (lane == 0) {
-        mbar_init(bar, 1);
-        unsigned bytes = (unsigned)(ylen * sizeof(T));
-        mbar_expect_tx(bar, bytes);
-        bulk_g2s(ys, Y + (ym0 - g.ybase), bytes, bar);
+    const bool last = blk == g.nblk - 1;
+    // with soft symbols given, only the last block (tap step) reads the input
+    if (!(FRZ && zin) || last) {
+        if (lane == 0) {
+            mbar_init(bar, 1);
+            unsigned bytes = (unsigned)(ylen * sizeof(T));
+            mbar_expect_tx(bar, bytes);
+            bulk_g2s(ys, Y + (ym0 - g.ybase), bytes, bar);
+        }
+        __syncwarp();
+        if (!mbar_wait(bar, 0)) {
+            if (lane == 0) atomicExch(&dst->err, (int)RX_ETIMEOUT);
+            mbar_wait(bar, 0);
+            return;
+        }
     }
-    __syncwarp();
-    if (!mbar_wait(bar, 0)) {
-        if (lane == 0) atomicExch(&dst->err, (int)RX_ETIMEOUT);
-        mbar_wait(bar, 0);
-        return;
-    }
+    float2 G = make_float2(0.f, 0.f);   // frozen form: tap gradient of the last block
     const int bpsv = p.bps;
     int pwin = (int)(((long long)bpsv * kb) % 32767);   // PRBS position of the window's first bit
     for (int w = 0; w < B / kWin; w++) {
@@ -428,9 +418,10 @@ __global__ void __launch_bounds__(32 * kEqWarps)
         float2 *dz = dbg_z ? dbg_z + (k0 - g.sym_lo) : nullptr;
         long long wi = (k0 - g.pay_lo) / kWin;
         if (QAM) {
-            WinOut R = qam_window<NT, MQ>(p, reinterpret_cast<float2 *>(ys), c0, reinterpret_cast<float2 *>(zs),
-                                          reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), 2, p.mu,
-                                          lane, dq, dz, prbs_bits, pwin);
+            WinOut R = qam_window<NT, MQ, FRZ>(p, reinterpret_cast<float2 *>(ys), c0, reinterpret_cast<float2 *>(zs),
+                                               reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), 2,
+                                               p.mu, lane, dq, dz, prbs_bits, pwin,
+                                               zin ? zin + (k0 - g.pay_lo) : nullptr, (FRZ && last) ? &G : nullptr);
             if (lane == 0) {
                 winb[wi] = (uint8_t)R.b;
                 winrec[wi] = make_uint4(R.errA, R.errB, R.serr, (unsigned)R.b | (R.nnear << 8));
@@ -449,9 +440,14 @@ __global__ void __launch_bounds__(32 * kEqWarps)
         pwin += bpsv * kWin;
         pwin = pwin >= 32767 ? pwin - 32767 : pwin;
     }
-    if (blk == g.nblk - 1 && lane < NT)
+    if (FRZ && last && lane < NT) {
+        const float step = p.mu * (float)kWin / (float)B;
+        float2 w0 = reinterpret_cast<float2 *>(ws)[lane];
+        taps_out[lane] = make_float2(fmaf(step, G.x, w0.x), fmaf(step, G.y, w0.y));
+    } else if (!FRZ && last && lane < NT) {
         taps_out[lane] = QAM ? reinterpret_cast<float2 *>(ws)[lane]
                              : make_float2(reinterpret_cast<float *>(ws)[lane], 0.f);
+    }
     if (lane == 0 && ambig) atomicAdd(&dst->cnt[C_AMBIG], (unsigned long long)ambig);
 }
 
@@ -463,44 +459,53 @@ static size_t eq_smem_per_warp(bool qam, int B)
 }
 
 template <bool QAM, int NT, int MQ>
-static cudaError_t launch_eq_t(const EqParams &p, const EqGeom &g, int train, const void *Y, float2 *taps_in,
-                               float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec, float4 *dbg_win,
-                               float2 *dbg_z, const uint8_t *prbs, const uint32_t *prbs_bits, DevState *dst,
-                               cudaStream_t st)
+static cudaError_t launch_eq_t(const EqParams &p, const EqGeom &g, int train, const void *Y, const float2 *zin,
+                               float2 *taps_in, float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec,
+                               float4 *dbg_win, float2 *dbg_z, const uint8_t *prbs, const uint32_t *prbs_bits,
+                               DevState *dst, cudaStream_t st)
 {
     if (train) {
         size_t smem = eq_smem_per_warp(QAM, kWin);
-        k_eq<QAM, NT, MQ><<<1, 32, smem, st>>>(p, g, 1, Y, taps_in, taps_out, dec, winb, winrec, dbg_win, dbg_z, prbs,
-                                               prbs_bits, dst);
+        k_eq<QAM, NT, MQ><<<1, 32, smem, st>>>(p, g, 1, Y, nullptr, taps_in, taps_out, dec, winb, winrec, dbg_win,
+                                               dbg_z, prbs, prbs_bits, dst);
         return cudaGetLastError();
     }
     size_t smem = eq_smem_per_warp(QAM, p.eq_block) * kEqWarps;
     unsigned grid = (unsigned)((g.nblk + kEqWarps - 1) / kEqWarps);
+    if constexpr (QAM) {
+        if (p.frozen) {
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(k_eq<QAM, NT, MQ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_eq<QAM, NT, MQ, true><<<grid, 32 * kEqWarps, smem, st>>>(p, g, 0, Y, zin, taps_in, taps_out, dec, winb,
+                                                                        winrec, dbg_win, dbg_z, prbs, prbs_bits, dst);
+            return cudaGetLastError();
+        }
+    }
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_eq<QAM, NT, MQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_eq<QAM, NT, MQ><<<grid, 32 * kEqWarps, smem, st>>>(p, g, 0, Y, taps_in, taps_out, dec, winb, winrec, dbg_win,
-                                                          dbg_z, prbs, prbs_bits, dst);
+    k_eq<QAM, NT, MQ><<<grid, 32 * kEqWarps, smem, st>>>(p, g, 0, Y, nullptr, taps_in, taps_out, dec, winb, winrec,
+                                                          dbg_win, dbg_z, prbs, prbs_bits, dst);
     return cudaGetLastError();
 }
 
 // tap counts with a compiled kernel (odd, half-length odd)
 #define RX_EQ_TAPS(X) X(3) X(7) X(11) X(15) X(19) X(23) X(27) X(31)
 
-cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void *Y, float2 *taps_in,
-                      float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec, float4 *dbg_win, float2 *dbg_z,
-                      const uint8_t *prbs, const uint32_t *prbs_bits, DevState *dst, cudaStream_t st)
+cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void *Y, const float2 *zin,
+                      float2 *taps_in, float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec, float4 *dbg_win,
+                      float2 *dbg_z, const uint8_t *prbs, const uint32_t *prbs_bits, DevState *dst, cudaStream_t st)
 {
 #define RX_CASE(NTV)                                                                                           \
     if (p.ntaps == NTV) {                                                                                      \
-        if (p.kk && p.mq == 2) return launch_eq_t<true, NTV, 2>(p, g, train, Y, taps_in, taps_out, dec, winb,  \
+        if (p.kk && p.mq == 2) return launch_eq_t<true, NTV, 2>(p, g, train, Y, zin, taps_in, taps_out, dec, winb,  \
                                                                 winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);                \
-        if (p.kk && p.mq == 4) return launch_eq_t<true, NTV, 4>(p, g, train, Y, taps_in, taps_out, dec, winb,  \
+        if (p.kk && p.mq == 4) return launch_eq_t<true, NTV, 4>(p, g, train, Y, zin, taps_in, taps_out, dec, winb,  \
                                                                 winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);                \
-        if (!p.kk && p.mq == 2) return launch_eq_t<false, NTV, 2>(p, g, train, Y, taps_in, taps_out, dec,      \
+        if (!p.kk && p.mq == 2) return launch_eq_t<false, NTV, 2>(p, g, train, Y, zin, taps_in, taps_out, dec,      \
                                                                   winb, winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);        \
-        if (!p.kk && p.mq == 4) return launch_eq_t<false, NTV, 4>(p, g, train, Y, taps_in, taps_out, dec,      \
+        if (!p.kk && p.mq == 4) return launch_eq_t<false, NTV, 4>(p, g, train, Y, zin, taps_in, taps_out, dec,      \
                                                                   winb, winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);        \
-        if (!p.kk && p.mq == 8) return launch_eq_t<false, NTV, 8>(p, g, train, Y, taps_in, taps_out, dec,      \
+        if (!p.kk && p.mq == 8) return launch_eq_t<false, NTV, 8>(p, g, train, Y, zin, taps_in, taps_out, dec,      \
                                                                   winb, winrec, dbg_win, dbg_z, prbs, prbs_bits, dst, st);        \
     }
     RX_EQ_TAPS(RX_CASE)

@@ -92,6 +92,7 @@ struct EqGeom {
 struct EqParams {
     int kk, mq, bps, ntaps, th, win, eq_block, ntrain, ncma, bps_b, amb_syms;
     float scale, r2, mu, mu_train, mu_cma;
+    int frozen;   // payload blocks filter with the call's start taps (block-Toeplitz form)
 };
 
 // ------------------------------------------------------------------ launchers
@@ -120,10 +121,17 @@ cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, 
                           float *Y, long long ybase, const float *Y_prev, long long ybase_prev,
                           cudaStream_t st);
 
-cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void *Y,
+// zin: soft symbols of the payload from the block-Toeplitz tensor-core FIR
+// (frozen form), or null to filter in FP32 inside the equaliser
+cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void *Y, const float2 *zin,
                       float2 *taps_in, float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec,
                       float4 *dbg_win, float2 *dbg_z, const uint8_t *prbs, const uint32_t *prbs_bits,
                       DevState *dst, cudaStream_t st);
+
+// block-Toeplitz FIR on the tensor cores (frozen taps): z[k - k_lo] for
+// k in [k_lo, k_lo + nsym), z_k = sum_i conj(w_i) Y[2k + TH - i - ybase]
+cudaError_t launch_fir_tc(int prec, const float2 *Y, long long ybase, long long k_lo, long long nsym,
+                          const float2 *taps, int ntaps, int scale_block, float2 *z, int *err, cudaStream_t st);
 
 cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in,
                          const uint8_t *dec, const uint8_t *winb, const uint4 *winrec, float4 *dbg_win,

@@ -45,7 +45,9 @@ class Pair:
         cfg = dict(cfg)
         cfg.setdefault("debug", 1)
         dbg = cfg.pop("debug")
-        self.o = oracle.Oracle(**oracle.default_cfg(fmt, nb, **cfg))
+        ocfg = dict(cfg)
+        ocfg["eq_frozen"] = int(ocfg.pop("fir_prec", 0) != 0)   # the oracle's frozen-tap form
+        self.o = oracle.Oracle(**oracle.default_cfg(fmt, nb, **ocfg))
         self.g = rx.Receiver(fmt, nb, debug=dbg, **cfg)
         self.report = dict(exempt=0, cascade=0, symbols=0, windows=0, ambiguous=0, calls=0)
         self.bad_blocks = set()     # cascaded blocks (carry their taps forward)

@@ -79,3 +79,34 @@ def test_null_handle_calls_are_rejected():
     assert lib.rx_process_batch(None, ptrs, ptrs, 2, None, n) == 1
     assert lib.rx_process_host_batch(None, ptrs, ptrs, 2, None, n) == 1
     assert lib.rx_process_host(None, ptrs[0], ptrs[1], None, n) == 1
+
+
+@pytest.mark.parametrize("args", [
+    (0, 1000, 16, 31, 2, 256, 256, 16, 16),         # null input
+    (16, 1000, 16, 31, 1, 256, 256, 16, 16),        # FP32 is not a tensor-core precision
+    (16, 1000, 16, 31, 2, 250, 256, 16, 16),        # nsym not a multiple of 16
+    (16, 1000, 16, 30, 2, 256, 256, 16, 16),        # even tap count
+    (16, 500, 16, 31, 2, 256, 256, 16, 16),         # input shorter than 2 nsym + ntaps + 1
+    (16, 1000, 16, 31, 4, 256, 96, 16, 16),         # FP8 scale block must divide 2048
+    (8, 1000, 16, 31, 2, 256, 256, 16, 16),         # input not 16-byte aligned
+])
+def test_fir_block_rejects_bad_arguments(args):
+    y, ny, w, nt, prec, nsym, sblk, z, st = args
+    assert rx.load().rx_fir_block(y, ny, w, nt, prec, nsym, sblk, z, st, None) == 1
+
+
+def test_receiver_rejects_unknown_option_and_bad_precision():
+    with pytest.raises(TypeError):
+        rx.Receiver(4, 1 << 20, eq_frozen=1)
+    lib = rx.load()
+    h = C.c_void_p()
+    c = rx.rx_default_config(rx.RX_PAM4)
+    c.fir_prec = rx.RX_FIR_BF16                       # the tensor-core forms are KK only
+    assert lib.rx_create(rx.RX_PAM4, 2e9, 4e9, 1 << 20, C.byref(c), C.byref(h)) == 1
+    c = rx.rx_default_config(rx.RX_KK_16QAM)
+    c.fir_prec = rx.RX_FIR_FP8
+    c.eq_block = 192 * 16                             # 2048 % eq_block != 0
+    assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
+    c.fir_prec = 5
+    c.eq_block = 1024
+    assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
