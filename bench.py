@@ -42,7 +42,7 @@ STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
 # the overlap-save factor N/(N-V) = 16/15 included)
 OLS = 65536 / (65536 - 4096)
 FLOPS_PER_SAMPLE = {"kk_fwd": 13.0 * OLS, "kk_rows": 60.0 * OLS, "kk_inv": 13.0 * OLS, "mf": 130.0,
-                    "eq": 252.0}
+                    "eq": 252.0, "kk_front": 86.0 * OLS}
 BYTES_PER_SAMPLE = {"unpack": 1.5 + 2.0}   # packed read + 16-bit code write
 SMS, LANES = 152, 128
 
@@ -195,7 +195,7 @@ def gpu_arm(args, rank, world, local):
     r.pos = 0
     run_steps(r, args.warmup)
     torch.cuda.synchronize()
-    rx.rx_profile(r.h, PROFILE_EVERY)
+    rx.rx_profile(r.h, max(1, min(PROFILE_EVERY, args.steps * args.bufs_per_step // 4)))
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
@@ -285,6 +285,12 @@ def gpu_arm(args, rank, world, local):
 
     # ---- per-stage times (CUDA events on the launching stream) and roofline
     per_call = {s: stage_ms[s] / max(calls, 1) for s in STAGES}
+    if per_call["kk_rows"] < 1e-4 and per_call["kk_inv"] < 1e-4:
+        # 2^16-point blocks run as one fused cluster kernel, profiled in the first slot
+        per_call["kk_front"] = per_call.pop("kk_fwd")
+        del per_call["kk_rows"], per_call["kk_inv"]
+    if per_call.get("unpack", 0.0) == 0.0:
+        per_call.pop("unpack", None)      # the KK kernels read the packed input themselves
     tot = sum(per_call.values())
     dom = max(per_call, key=per_call.get)
     peaks = load_peaks()
@@ -292,7 +298,7 @@ def gpu_arm(args, rank, world, local):
     alu_peak = SMS * LANES * 2 * sm_max * 1e6 / 1e12        # FP32 TFLOP/s at the maximum SM clock
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     stages = {}
-    for s in STAGES:
+    for s in per_call:
         t = per_call[s]
         d = {"ms_per_call": t, "share": t / tot if tot else 0.0}
         if s in FLOPS_PER_SAMPLE and t > 0:
@@ -306,7 +312,9 @@ def gpu_arm(args, rank, world, local):
     tr_path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if os.path.exists(tr_path):
         traffic = json.load(open(tr_path)).get(dom)
-    if dom in FLOPS_PER_SAMPLE:
+    if calls == 0 or tot == 0 or not ("tflops" in stages[dom] or "gbs" in stages[dom]):
+        roof = None
+    elif dom in FLOPS_PER_SAMPLE:
         ach = stages[dom]["tflops"]
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": ach / alu_peak, "traffic": traffic,
@@ -339,16 +347,23 @@ def gpu_arm(args, rank, world, local):
     cnn_line = None
     if rank == 0 and not args.no_cnn:
         cnn_line = cnn_leg(args, ring)
+    prec_line = None
+    if rank == 0 and not args.no_precision:
+        prec_line = precision_leg(args, g, ring)
+    batched_line = None
+    if rank == 0 and not args.no_batched:
+        batched_line = batched_leg(args)
 
     clk = clocks.summary()
-    launches_per_call = 6
+    launches_per_call = 6                 # KK front (three kernels), matched filter, equaliser, demap
     line = {"metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args),
             "e2e": {"value": e2e_value, "unit": "GSa/s", "h2d_bytes_per_step": h2d // e2e_steps,
                     "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
-            "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line,
+            "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line, "precision": prec_line,
+            "batched": batched_line,
             "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
             "realtime_x": value / 4.0,
             "ber": cpu["ber_gpu_same_buffers"] if cpu else None,
@@ -426,6 +441,198 @@ def cnn_leg(args, ring):
                        "(counter-based symbols), judge SNR 19 dB (PRBS-15)"}
 
 
+def precision_leg(args, g, ring):
+    """Precision forms of the equaliser on the KK-16QAM workload (eq_block 1024):
+    the adaptive FP32 chain, the frozen-tap form in FP32, and the block-Toeplitz
+    FIR on the tensor cores in BF16 / FP16 / FP8-E4M3.  Throughput over the ring;
+    soft-symbol relative RMS error and BER against the FP64 oracle on the first
+    two buffers of the stream; the tensor-core FIR kernel timed alone."""
+    import torch
+    import oracle
+    import paper_2010_14333_gb300 as rx
+    nref = 2
+    forms = [("adaptive_f32", rx.RX_FIR_ADAPTIVE), ("frozen_f32", rx.RX_FIR_FROZEN_F32),
+             ("bf16", rx.RX_FIR_BF16), ("fp16", rx.RX_FIR_FP16), ("fp8_e4m3", rx.RX_FIR_FP8)]
+    ref = {}
+    for frozen in (0, 1):
+        o = oracle.Oracle(**oracle.default_cfg(FMT, NB, eq_block=1024, eq_frozen=frozen))
+        zs = []
+        for b in range(nref):
+            o.process(g["packed"][b])
+            zs.append(o.get(oracle.ORX_Z))
+        ref[frozen] = (zs, o.stats())
+    res = {}
+    for name, prec in forms:
+        zs, so = ref[int(prec != rx.RX_FIR_ADAPTIVE)]
+        d = rx.Receiver(FMT, NB, fir_prec=prec, eq_block=1024, debug=1)
+        num = den = 0.0
+        for b in range(nref):
+            d.process(ring[b])
+            z, z0 = d.debug(rx.RX_DBG_SOFT)
+            zo, zo0 = zs[b]
+            if len(z):
+                zo = zo[z0 - zo0: z0 - zo0 + len(z)]
+                num += float(np.sum(np.abs(z - zo) ** 2))
+                den += float(np.sum(np.abs(zo) ** 2))
+        sd = d.stats()
+        del d
+        r = rx.Receiver(FMT, NB, fir_prec=prec, eq_block=1024)
+        r.process_batch(ring[:3])
+        torch.cuda.synchronize()
+        rx.rx_profile(r.h, 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            r.process_batch(ring)
+        e1.record()
+        torch.cuda.synchronize()
+        ms, calls = rx.rx_profile_read(r.h)
+        rx.rx_profile(r.h, 0)
+        res[name] = {"gsa_s": 2 * len(ring) * NB / (e0.elapsed_time(e1) * 1e-3) / 1e9,
+                     "eq_us_per_buffer": ms["eq"] / max(calls, 1) * 1e3,
+                     "soft_rel_rms_vs_oracle": (num / den) ** 0.5 if den else None,
+                     "ber": sd["ber"], "ber_oracle": so["ber"], "bits": sd["bits"],
+                     "oracle_form": "frozen" if prec != rx.RX_FIR_ADAPTIVE else "adaptive"}
+        del r
+    # the tensor-core FIR alone: 2^20 symbols (one buffer's payload), 31 taps
+    nsym, nt = 1 << 20, 31
+    rng = np.random.default_rng(3)
+    ny = 2 * nsym + nt + 1
+    yv = torch.from_numpy(rng.standard_normal(2 * ny).astype(np.float32)).cuda()
+    wv = torch.zeros(2 * nt, dtype=torch.float32, device="cuda")
+    wv[2 * (nt // 2)] = 1.0
+    zv = torch.zeros(2 * nsym, dtype=torch.float32, device="cuda")
+    stv = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sid = torch.cuda.current_stream().cuda_stream
+    kern = {}
+    for name, prec in forms[2:]:
+        for _ in range(3):
+            rx.rx_fir_block(yv.data_ptr(), ny, wv.data_ptr(), nt, prec, nsym, 1024, zv.data_ptr(), stv.data_ptr(), sid)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 50
+        e0.record()
+        for _ in range(reps):
+            rx.rx_fir_block(yv.data_ptr(), ny, wv.data_ptr(), nt, prec, nsym, 1024, zv.data_ptr(), stv.data_ptr(), sid)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / reps * 1e3
+        byt = nsym * (16 + 8)                    # 2 complex FP32 inputs + 1 complex output per symbol
+        kern[name] = {"us_per_2e20_symbols": us, "gbs": byt / (us * 1e-6) / 1e9,
+                      "algorithmic_tflops": 8 * nt * nsym / (us * 1e-6) / 1e12,
+                      "tensor_tflops_issued": 2 * 128 * 32 * 128 * (nsym // 2048) / (us * 1e-6) / 1e12}
+    return {"eq_block": 1024, "forms": res, "fir_kernel": kern,
+            "sample": f"soft symbols and BER on the first {nref} buffers; throughput over the {len(ring)}-buffer ring x 2"}
+
+
+def _gen_member(job):
+    """One member stream of the batched workload (runs in a spawned worker)."""
+    import synth
+    fmt, nb, nbufs, seed, snr = job
+    if fmt >= 3:
+        g = synth.gen_kk_stream(fmt, nb, nbufs, seed=seed, snr_db=snr, truth=False)
+    else:
+        g = synth.gen_pam_stream(fmt, nb, nbufs, seed=seed, snr_db=snr)
+    return g["packed"]
+
+
+def batched_leg(args):
+    """Many streams at once: 64 receivers with buffer lengths drawn from
+    {2^18 .. 2^22}, formats mixed (PAM-2/4/8 at 2 GBaud, KK-QPSK/16QAM at
+    1 GBaud), SNR 14..22 dB.  Aggregate GSa/s over rounds of one buffer per
+    stream: one stream after another on one CUDA stream, then as a group (worker
+    streams), as a group captured into an updated CUDA graph, and with the
+    autotuned implementation choices; per-round latency percentiles."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    import torch
+    import paper_2010_14333_gb300 as rx
+    rng = np.random.default_rng(2022)
+    nmem = args.batched_streams
+    fmts = rng.integers(0, 5, nmem)
+    lens = 1 << (18 + rng.integers(0, 5, nmem))
+    snrs = rng.uniform(14.0, 22.0, nmem)
+    nbufs = 2
+    t0 = time.perf_counter()
+    jobs = [(int(f), int(n), nbufs, 5000 + m, float(sn)) for m, (f, n, sn) in enumerate(zip(fmts, lens, snrs))]
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        packed = list(ex.map(_gen_member, jobs))
+    t_gen = time.perf_counter() - t0
+    dev = [[torch.from_numpy(p).cuda() for p in pk] for pk in packed]
+    samples_round = int(np.sum(lens))
+    st = torch.cuda.Stream()
+    sid = st.cuda_stream
+
+    def make():
+        rs = [rx.Receiver(int(f), int(n)) for f, n in zip(fmts, lens)]
+        outs = [torch.zeros(r.max_bits // 8 + 16, dtype=torch.uint8, device="cuda") for r in rs]
+        return rs, outs
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    res = {}
+    for mode in ("serial", "group", "group_graph", "group_graph_tuned"):
+        rs, outs = make()
+        g = None
+        if mode != "serial":
+            flags = {"group": 0, "group_graph": rx.RX_GROUP_GRAPH,
+                     "group_graph_tuned": rx.RX_GROUP_GRAPH | rx.RX_GROUP_TUNE}[mode]
+            tt = time.perf_counter()
+            g = rx.rx_group_create([r.h for r in rs], flags)
+            t_create = time.perf_counter() - tt
+        optr = [o.data_ptr() for o in outs]
+
+        def round_(k):
+            ins = [dev[m][k % nbufs].data_ptr() for m in range(nmem)]
+            if g is None:
+                for m in range(nmem):
+                    rx.rx_process(rs[m].h, ins[m], optr[m], sid)
+            else:
+                rx.rx_group_process(g, ins, optr, sid)
+
+        with torch.cuda.stream(st):
+            for k in range(3):
+                round_(k)
+            st.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(st)
+            for k in range(args.batched_rounds):
+                round_(k)
+            e1.record(st)
+            st.synchronize()
+            ms = e0.elapsed_time(e1)
+            lat = []
+            for k in range(args.batched_rounds):
+                a, b = ev(), ev()
+                a.record(st)
+                round_(k)
+                b.record(st)
+                st.synchronize()
+                lat.append(a.elapsed_time(b))
+        errs = sum(r.stats()["device_error"] != 0 for r in rs)
+        d = {"gsa_s": samples_round * args.batched_rounds / (ms * 1e-3) / 1e9,
+             "ms_per_round": ms / args.batched_rounds,
+             "round_latency_p50_ms": float(np.percentile(lat, 50)),
+             "round_latency_p99_ms": float(np.percentile(lat, 99)),
+             "members_with_device_error": int(errs)}
+        if g is not None:
+            d["create_s"] = t_create
+            if mode == "group_graph_tuned":
+                tun = [rx.rx_group_tuning(g, m) for m in range(nmem)]
+                d["tuned_kk_front_1"] = int(sum(1 for f, t in zip(fmts, tun) if f >= 3 and t[0] == 1))
+                d["tuned_eq_warps"] = {str(w): int(sum(1 for t in tun if t[1] == w)) for w in (2, 4, 8)}
+            rx.rx_group_destroy(g)
+        res[mode] = d
+        del rs, outs
+    names = ["PAM-2", "PAM-4", "PAM-8", "KK-QPSK", "KK-16QAM"]
+    return {"streams": nmem, "samples_per_round": samples_round, "rounds": args.batched_rounds,
+            "formats": {n: int(np.sum(fmts == i)) for i, n in enumerate(names)},
+            "lengths": {str(int(l)): int(np.sum(lens == l)) for l in sorted(set(lens.tolist()))},
+            "budget_ms": 5.243, "gen_s": t_gen, "modes": res,
+            "note": "each stream cycles 2 buffers of its own synthetic stream; latency = one round "
+                    "(one buffer of every stream) from an idle GPU"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,6 +643,10 @@ def main():
     ap.add_argument("--ring", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cnn", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-streams", type=int, default=64)
+    ap.add_argument("--batched-rounds", type=int, default=10)
     ap.add_argument("--latency-reps", type=int, default=300)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

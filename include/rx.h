@@ -86,6 +86,12 @@ typedef struct {
                             CUDA cores, or a block-Toeplitz GEMM on the tensor cores in
                             BF16, FP16 or FP8-E4M3 (per-block scaling) with FP32
                             accumulation.  The tensor-core forms need 2048 % eq_block == 0. */
+    int32_t kk_front;    /* implementation of the 2^16-point KK front end (same arithmetic;
+                            the carrier sums differ in rounding order only): 0 = three
+                            four-step kernels (column DFT, row FFTs, column DFT + field),
+                            1 = one thread-block-cluster kernel holding each block pair
+                            in distributed shared memory.  Ignored for ols_n = 4096.      */
+    int32_t eq_warps;    /* equaliser blocks (warps) per CTA: 0 = default (4), 2, 4 or 8   */
 } rx_config;
 
 /* Equaliser forms and precisions (rx_config.fir_prec). */
@@ -160,12 +166,13 @@ rx_status rx_process(rx_handle *h, const uint8_t *packed12_in, uint8_t *bits_out
 
 /* Process n consecutive buffers of the stream (ins[i], outs[i] as in rx_process;
  * nbits_out[i] per buffer).  The results are those of n rx_process calls.  The
- * front end of buffer i+1 (field reconstruction, matched filter) runs on
- * cuda_stream concurrently with the back end of buffer i (equaliser, decisions,
- * bits) on a stream the handle owns, as the paper overlaps consecutive buffers in
- * parallel processing streams chained by events (Sec. 2); cuda_stream waits for
- * the last back end before the call returns its work.  With cfg.debug = 1 the
- * buffers run one at a time on cuda_stream. */
+ * front end of buffer i+1 (field reconstruction, matched filter) runs
+ * concurrently with the back end of buffer i (equaliser, decisions, bits), on
+ * two streams the handle owns (the front one at the highest stream priority),
+ * as the paper overlaps consecutive buffers in parallel streams chained by
+ * events (Sec. 2).  The pipeline starts after the work already on cuda_stream,
+ * and cuda_stream waits for its last back end before anything enqueued later.
+ * With cfg.debug = 1 the buffers run one at a time on cuda_stream. */
 rx_status rx_process_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *const *outs, int n,
                            void *cuda_stream, int64_t *nbits_out);
 
@@ -231,6 +238,32 @@ rx_status rx_profile_read(rx_handle *h, double *ms, int n, int64_t *calls);
  * Enqueued on cuda_stream; returns RX_EINVAL for bad arguments before launching. */
 rx_status rx_fir_block(const float *y, int64_t ny, const float *w, int ntaps, int prec, int64_t nsym,
                        int scale_block, float *z_out, int32_t *status, void *cuda_stream);
+
+/* Groups: many independent streams per submission (the paper's receiver runs
+ * one stream per format; a group serves many at once, of any formats and buffer
+ * lengths).  A group holds n existing handles (not owned; each must be used
+ * only through the group while it exists) and processes one buffer of every
+ * member per rx_group_process call: ins[i], outs[i] and nbits_out[i] as in
+ * rx_process for member i.  Results equal those of n rx_process calls.
+ * Members run concurrently on up to 8 worker streams the group owns, forked
+ * from cuda_stream and joined back into it.
+ *   RX_GROUP_GRAPH: each round is captured into a CUDA graph, the executable
+ *     graph is updated in place and launched once (cuda_stream must not be the
+ *     legacy default stream).  A failed capture leaves the members in RX_ESTATE.
+ *   RX_GROUP_TUNE:  at creation, each distinct member shape (format, buffer
+ *     length, configuration) times its implementation choices on pseudo-random
+ *     input and keeps the fastest: the 2^16-point front-end structure
+ *     (kk_front 0 / 1) and the equaliser CTA shape (eq_warps 2 / 4 / 8).  The
+ *     choice of eq_warps leaves every output bit-identical; kk_front changes
+ *     only the summation order of the carrier estimate.  rx_group_tuning reports
+ *     the choice for member i. */
+typedef struct rx_group rx_group;
+enum { RX_GROUP_GRAPH = 1, RX_GROUP_TUNE = 2 };
+rx_status rx_group_create(rx_handle *const *members, int n, int flags, rx_group **out);
+rx_status rx_group_process(rx_group *g, const uint8_t *const *ins, uint8_t *const *outs, void *cuda_stream,
+                           int64_t *nbits_out);
+rx_status rx_group_tuning(const rx_group *g, int i, int32_t *kk_front, int32_t *eq_warps);
+rx_status rx_group_destroy(rx_group *g);
 
 /* Kramers-Kronig field of one buffer without any device allocation.
  *

@@ -30,7 +30,7 @@ class RxConfig(C.Structure):
         ("ncma", C.c_int32), ("eq_block", C.c_int32), ("win", C.c_int32),
         ("mu", C.c_double), ("mu_train", C.c_double), ("mu_cma", C.c_double),
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
-        ("debug", C.c_int32), ("fir_prec", C.c_int32),
+        ("debug", C.c_int32), ("fir_prec", C.c_int32), ("kk_front", C.c_int32), ("eq_warps", C.c_int32),
     ]
 
 
@@ -53,7 +53,9 @@ EXPORTED = sorted(["rx_default_config", "rx_create", "rx_process", "rx_process_h
                    "rx_profile", "rx_profile_read", "rx_kk_field_noalloc", "rx_cnn_nparams", "rx_cnn_create",
                    "rx_cnn_set_params", "rx_cnn_get_params", "rx_cnn_forward", "rx_cnn_grad",
                    "rx_cnn_adam_step", "rx_cnn_destroy", "rx_set_cnn", "rx_process_batch",
-                   "rx_process_host_batch", "rx_fir_block"])
+                   "rx_process_host_batch", "rx_fir_block", "rx_group_create", "rx_group_process",
+                   "rx_group_tuning", "rx_group_destroy"])
+RX_GROUP_GRAPH, RX_GROUP_TUNE = 1, 2
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
 
 _lib = None
@@ -75,6 +77,10 @@ def load(path: str = LIB_PATH):
     L.rx_process_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.rx_process_host_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.rx_fir_block.argtypes = [vp, i64, vp, C.c_int, C.c_int, i64, C.c_int, vp, vp, vp]
+    L.rx_group_create.argtypes = [vp, C.c_int, C.c_int, P(vp)]
+    L.rx_group_process.argtypes = [vp, vp, vp, vp, vp]
+    L.rx_group_tuning.argtypes = [vp, C.c_int, P(C.c_int32), P(C.c_int32)]
+    L.rx_group_destroy.argtypes = [vp]
     L.rx_max_bits.argtypes = [vp]
     L.rx_max_bits.restype = i64
     L.rx_stats.argtypes = [vp, P(RxStats), vp]
@@ -156,6 +162,34 @@ def rx_fir_block(y: int, ny: int, w: int, ntaps: int, prec: int, nsym: int, scal
                  status: int, stream: int = 0):
     """Tensor-core block-Toeplitz FIR (device pointers; see include/rx.h)."""
     _check(load().rx_fir_block(y, ny, w, ntaps, prec, nsym, scale_block, z, status, stream))
+
+
+def rx_group_create(handles, flags: int = 0) -> int:
+    """A group over existing receiver handles (see include/rx.h)."""
+    arr = (C.c_void_p * len(handles))(*handles)
+    g = C.c_void_p()
+    _check(load().rx_group_create(arr, len(handles), flags, C.byref(g)))
+    return g.value
+
+
+def rx_group_process(g: int, ins, outs, stream: int = 0):
+    """One buffer per member (device pointers); returns the bit count per member."""
+    n = len(ins)
+    ia = (C.c_void_p * n)(*ins)
+    oa = (C.c_void_p * n)(*outs)
+    nb = (C.c_int64 * n)()
+    _check(load().rx_group_process(g, ia, oa, stream, nb))
+    return list(nb)
+
+
+def rx_group_tuning(g: int, i: int):
+    f, w = C.c_int32(), C.c_int32()
+    _check(load().rx_group_tuning(g, i, C.byref(f), C.byref(w)))
+    return f.value, w.value
+
+
+def rx_group_destroy(g: int):
+    _check(load().rx_group_destroy(g))
 
 
 def rx_process_host(h: int, host_in: int, host_bits_out: int, stream: int = 0) -> int:

@@ -41,8 +41,10 @@ struct rx_handle {
     // two-stream pipeline of rx_process_batch: the front end (field, matched
     // filter) of buffer i+1 runs on the caller's stream while the back end
     // (equaliser, demap) of buffer i runs on `back`
-    cudaStream_t back, copy;
-    cudaEvent_t ev_front, ev_join, ev_yfree[kSlots], ev_inready[2], ev_infree[2];
+    // the front end runs on `front`, created at the highest priority so that its
+    // cluster launches are placed ahead of the back end's CTAs
+    cudaStream_t front, back, copy;
+    cudaEvent_t ev_fork, ev_front, ev_join, ev_yfree[kSlots], ev_inready[2], ev_infree[2];
     float2 *taps[2], *twN, *twN2, *ds_tab;
     float *lnt, *sqt;
     float *rrc;
@@ -53,6 +55,7 @@ struct rx_handle {
     uint8_t *in_stage[2], *bits_stage;   // device staging of the host-buffer entry points
     float2 *zbuf;                   // payload soft symbols of the tensor-core FIR forms
     long long dec_cap, win_cap, y_cap;
+    int nsm;                        // SMs of the handle's device
     // stage timing: a ring of event sets, one per profiled call
     const rx_cnn *cnn;              // learned equaliser for the payload, or null
     int prof_on;               // sampling period in calls (0: off)
@@ -228,6 +231,7 @@ void rx_destroy(rx_handle *h)
 {
     if (!h) return;
     // work still queued on the pipeline's own streams finishes before the memory goes
+    if (h->front) cudaStreamSynchronize(h->front);
     if (h->back) cudaStreamSynchronize(h->back);
     if (h->copy) cudaStreamSynchronize(h->copy);
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->E[0], h->E[1], h->E[2], h->Y[0], h->Y[1], h->Y[2],
@@ -243,9 +247,10 @@ void rx_destroy(rx_handle *h)
         for (int i = 0; i < kProfRing * kEvPerCall; i++) cudaEventDestroy(h->prof_ev[i]);
         free(h->prof_ev);
     }
+    if (h->front) cudaStreamDestroy(h->front);
     if (h->back) cudaStreamDestroy(h->back);
     if (h->copy) cudaStreamDestroy(h->copy);
-    cudaEvent_t *evs[] = {&h->ev_front, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1], &h->ev_yfree[2],
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1], &h->ev_yfree[2],
                           &h->ev_inready[0], &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
     for (cudaEvent_t *ev : evs)
         if (*ev) cudaEventDestroy(*ev);
@@ -286,6 +291,8 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         return RX_EINVAL;
     if (c.fir_prec < RX_FIR_ADAPTIVE || c.fir_prec > RX_FIR_FP8 || (c.fir_prec != RX_FIR_ADAPTIVE && !kk) ||
         (c.fir_prec >= RX_FIR_BF16 && 2048 % c.eq_block))
+        return RX_EINVAL;
+    if (c.kk_front < 0 || c.kk_front > 1 || !(c.eq_warps == 0 || c.eq_warps == 2 || c.eq_warps == 4 || c.eq_warps == 8))
         return RX_EINVAL;
     if (kk && (c.ncma < 0 || c.ncma > c.ntrain || c.ncma % kWin || c.bps_b < 1 || c.bps_b > 32 ||
                c.ds_den < 1 || c.ds_num < 0 || c.amb_syms < 0 || c.amb_syms % kWin || c.amb_syms > 4096 ||
@@ -330,6 +337,13 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     p.mu_train = (float)c.mu_train;
     p.mu_cma = (float)c.mu_cma;
     p.frozen = c.fir_prec != RX_FIR_ADAPTIVE;
+    if (c.eq_warps) {
+        p.warps = c.eq_warps;
+        if (eq_smem_bytes(p, p.warps) > kMaxSmemCta) { free(h); return RX_EINVAL; }
+    } else {   // default: 4 blocks per CTA, fewer when long blocks do not fit
+        p.warps = 4;
+        while (p.warps > 1 && eq_smem_bytes(p, p.warps) > kMaxSmemCta) p.warps /= 2;
+    }
 
     // the first call that emits payload must carry the ambiguity-resolution symbols
     if (kk && c.amb_syms > 0) {
@@ -439,12 +453,27 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     h->ebase_cur = -kEHist;
     h->ybase_cur = -kYHist;
     {
-        bool ok = cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        bool ok = cudaStreamCreateWithPriority(&h->front, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
-        cudaEvent_t *evs[] = {&h->ev_front, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1], &h->ev_yfree[2],
+        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1], &h->ev_yfree[2],
                               &h->ev_inready[0], &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
         for (cudaEvent_t *ev : evs)
             ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            rx_destroy(h);
+            return RX_ECUDA;
+        }
+    }
+    {
+        int dev = 0;
+        bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                  prepare_eq(h->ep) == cudaSuccess && (!kk || prepare_kk_front() == cudaSuccess) &&
+                  (c.fir_prec < RX_FIR_BF16 || prepare_fir_tc(c.fir_prec) == cudaSuccess);
         if (!ok) {
             cudaGetLastError();
             rx_destroy(h);
@@ -491,17 +520,17 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
 
     h->prof_cur = h->prof_on > 0 && h->calls % h->prof_on == 0;
     if (h->prof_cur && h->prof_head - h->prof_tail >= kProfRing) prof_harvest_one(h);
-    prof_begin(h, 0, sf);
     // 12-bit unpack into [history | buffer]: the PAM chain's input; the KK kernels
     // read the packed bytes themselves, so there it only feeds the debug view
     if (!h->kk || c.debug) {
+        prof_begin(h, 0, sf);
         int cw_new = h->cw ^ 1;
         e = launch_unpack(in, h->codes[cw_new], h->codes[h->cw], h->nb, h->nhist, h->nb, h->calls == 0,
                           c.pack_order, h->kk ? nullptr : &h->st->pam_s1[par],
                           h->kk ? nullptr : &h->st->pam_s2[par], sf);
         h->cw = cw_new;
+        prof_end(h, 0, sf);
     }
-    prof_end(h, 0, sf);
     KkInput kin;
     if (h->kk) {
         kin.hist = h->phist[h->hw];
@@ -532,6 +561,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         g.sps = h->sps;
         int ew_new = (h->ew + 1) % kSlots;
         g.slot = ew_new;
+        g.fused = c.kk_front;
         KkTables tb = {h->lnt, h->sqt, h->twN, h->twN2};
         e = launch_kk_front(g, kin, h->fftws, tb, h->E[ew_new], h->E[h->ew], h->partials, h->st, sf,
                             h->prof_cur ? h : nullptr);
@@ -590,7 +620,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
             if (c.fir_prec >= RX_FIR_BF16) {
                 // frozen taps: the whole payload's filter as one tensor-core GEMM
                 e = launch_fir_tc(c.fir_prec, (const float2 *)h->Y[h->yw], h->ybase_cur, pay_lo, npay,
-                                  h->taps[h->tw], c.ntaps, c.eq_block, h->zbuf, &h->st->err, sb);
+                                  h->taps[h->tw], c.ntaps, c.eq_block, h->zbuf, &h->st->err, h->nsm, sb);
                 zin = h->zbuf;
             }
             if (e == cudaSuccess)
@@ -649,13 +679,15 @@ rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *s
 static rx_status run_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *const *outs, bool host, int n,
                            void *stream, int64_t *nbits_out)
 {
-    cudaStream_t sf = (cudaStream_t)stream;
+    cudaStream_t caller = (cudaStream_t)stream;
     const bool one = h->cfg.debug != 0;             // debug views want one call at a time
-    cudaStream_t sb = one ? sf : h->back;
-    cudaStream_t sc = one ? sf : h->copy;
-    if (!one && host) {
-        // the copy stream must not overwrite a staging buffer before earlier work on the caller's stream
-        if (cudaEventRecord(h->ev_join, sf) != cudaSuccess || cudaStreamWaitEvent(sc, h->ev_join, 0) != cudaSuccess)
+    cudaStream_t sf = one ? caller : h->front;
+    cudaStream_t sb = one ? caller : h->back;
+    cudaStream_t sc = one ? caller : h->copy;
+    if (!one) {
+        // everything earlier on the caller's stream precedes the pipeline
+        if (cudaEventRecord(h->ev_fork, caller) != cudaSuccess || cudaStreamWaitEvent(sf, h->ev_fork, 0) != cudaSuccess ||
+            cudaStreamWaitEvent(sb, h->ev_fork, 0) != cudaSuccess || cudaStreamWaitEvent(sc, h->ev_fork, 0) != cudaSuccess)
             return RX_ECUDA;
     }
     for (int i = 0; i < n; i++) {
@@ -664,7 +696,8 @@ static rx_status run_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *con
         if (r != RX_OK) return r;
     }
     if (!one) {
-        if (cudaEventRecord(h->ev_join, sb) != cudaSuccess || cudaStreamWaitEvent(sf, h->ev_join, 0) != cudaSuccess)
+        // the back end of the last buffer waited for its front end: joining it joins all
+        if (cudaEventRecord(h->ev_join, sb) != cudaSuccess || cudaStreamWaitEvent(caller, h->ev_join, 0) != cudaSuccess)
             return RX_ECUDA;
     }
     return RX_OK;
@@ -846,10 +879,264 @@ rx_status rx_fir_block(const float *y, int64_t ny, const float *w, int ntaps, in
         (((uintptr_t)z_out) & 15))
         return RX_EINVAL;
     // y[j] holds stream index j - TH, so z_k = sum_i conj(w_i) y[2k + TH - i] in stream terms
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        prepare_fir_tc(prec) != cudaSuccess)
+        return RX_ECUDA;
     cudaError_t e = launch_fir_tc(prec, (const float2 *)y, -(long long)((ntaps - 1) / 2), 0, nsym,
-                                  (const float2 *)w, ntaps, scale_block, (float2 *)z_out, (int *)status,
+                                  (const float2 *)w, ntaps, scale_block, (float2 *)z_out, (int *)status, nsm,
                                   (cudaStream_t)stream);
     return e == cudaSuccess ? RX_OK : RX_ECUDA;
+}
+
+// ----------------------------------------------------------------- groups
+// Members run on worker streams forked from the caller's stream; member i goes
+// to worker i mod nw in order of decreasing buffer length.  With RX_GROUP_GRAPH
+// each round is captured into a CUDA graph whose executable instance is
+// updated in place (the topology repeats round to round; only kernel
+// parameters change) and launched once.
+struct rx_group {
+    int n, nw, flags;
+    rx_handle **m;
+    int *order;
+    cudaStream_t ws[8];
+    cudaEvent_t fork, done[8];
+    cudaGraphExec_t exec;
+    int *tuned;   // per member: kk_front | eq_warps << 4
+};
+
+__global__ void k_fill_bytes(uint8_t *p, long long n, unsigned seed)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        unsigned x = (unsigned)i * 2654435761u ^ seed;
+        x ^= x >> 15;
+        x *= 2246822519u;
+        x ^= x >> 13;
+        p[i] = (uint8_t)x;
+    }
+}
+
+// time `calls` calls of a fresh handle of this shape and implementation choice
+static float time_variant(int fmt, double baud, double fs, long long nb, rx_config c, const uint8_t *const *bufs,
+                          int nbuf, uint8_t *bits, cudaStream_t st)
+{
+    rx_handle *t = nullptr;
+    if (rx_create((rx_format)fmt, baud, fs, nb, &c, &t) != RX_OK) return -1.f;
+    float best = -1.f;
+    int64_t nbits;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    bool ok = true;
+    for (int i = 0; i < 4 && ok; i++) ok = rx_process(t, bufs[i % nbuf], bits, st, &nbits) == RX_OK;   // training
+    for (int rep = 0; rep < 3 && ok; rep++) {
+        cudaEventRecord(a, st);
+        for (int i = 0; i < 3 && ok; i++) ok = rx_process(t, bufs[i % nbuf], bits, st, &nbits) == RX_OK;
+        cudaEventRecord(b, st);
+        float ms = 0.f;
+        if (ok && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+            best = (best < 0.f || ms < best) ? ms : best;
+    }
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    rx_destroy(t);
+    return ok ? best : -1.f;
+}
+
+// pick the fastest implementation choice (front-end kernel structure, equaliser
+// CTA shape) for each distinct member shape, on pseudo-random input
+static rx_status tune_group(rx_group *g)
+{
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return RX_ECUDA;
+    rx_status r = RX_OK;
+    for (int i = 0; i < g->n && r == RX_OK; i++) {
+        rx_handle *h = g->m[i];
+        int j = 0;   // an earlier member of the same shape
+        for (; j < i; j++) {
+            rx_handle *o = g->m[j];
+            if (o->fmt == h->fmt && o->nb == h->nb && o->sps == h->sps && !memcmp(&o->cfg, &h->cfg, sizeof h->cfg))
+                break;
+        }
+        if (j < i) {
+            g->tuned[i] = g->tuned[j];
+        } else {
+            const int nbuf = 2;
+            uint8_t *bufs[nbuf] = {nullptr, nullptr}, *bits = nullptr;
+            size_t bytes = (size_t)(h->nb * 3 / 2);
+            bool ok = cudaMalloc(&bits, (size_t)(rx_max_bits(h) / 8 + 16)) == cudaSuccess;
+            for (int b = 0; b < nbuf && ok; b++) {
+                ok = cudaMalloc(&bufs[b], bytes + 16) == cudaSuccess;
+                if (ok) k_fill_bytes<<<(unsigned)((bytes + 255) / 256), 256, 0, st>>>(bufs[b], (long long)bytes, 977u * (b + 1));
+            }
+            float best = -1.f;
+            int pick = h->cfg.kk_front | (h->ep.warps << 4);
+            int fronts = (h->kk && h->N == 65536) ? 2 : 1;
+            const int warps[3] = {2, 4, 8};
+            double baud = 4e9 / h->sps;
+            for (int f = 0; f < fronts && ok; f++)
+                for (int w = 0; w < 3 && ok; w++) {
+                    rx_config c = h->cfg;
+                    c.kk_front = f;
+                    c.eq_warps = warps[w];
+                    c.debug = 0;
+                    float ms = time_variant(h->fmt, baud, 4e9, h->nb, c, bufs, nbuf, bits, st);
+                    if (ms > 0.f && (best < 0.f || ms < best)) {
+                        best = ms;
+                        pick = f | (warps[w] << 4);
+                    }
+                }
+            for (int b = 0; b < nbuf; b++) cudaFree(bufs[b]);
+            cudaFree(bits);
+            if (!ok) r = RX_ECUDA;
+            g->tuned[i] = pick;
+        }
+        // apply: neither choice changes the stream state
+        h->cfg.kk_front = g->tuned[i] & 15;
+        h->cfg.eq_warps = g->tuned[i] >> 4;
+        h->ep.warps = h->cfg.eq_warps;
+        if (prepare_eq(h->ep) != cudaSuccess) r = RX_ECUDA;
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return r;
+}
+
+rx_status rx_group_destroy(rx_group *g)
+{
+    if (!g) return RX_EINVAL;
+    for (int w = 0; w < g->nw; w++) {
+        if (g->ws[w]) {
+            cudaStreamSynchronize(g->ws[w]);
+            cudaStreamDestroy(g->ws[w]);
+        }
+        if (g->done[w]) cudaEventDestroy(g->done[w]);
+    }
+    if (g->fork) cudaEventDestroy(g->fork);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    free(g->m);
+    free(g->order);
+    free(g->tuned);
+    free(g);
+    return RX_OK;
+}
+
+rx_status rx_group_create(rx_handle *const *members, int n, int flags, rx_group **out)
+{
+    if (!members || !out || n < 1 || (flags & ~(RX_GROUP_GRAPH | RX_GROUP_TUNE))) return RX_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; i++) {
+        if (!members[i] || members[i]->broken) return RX_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (members[j] == members[i]) return RX_EINVAL;
+    }
+    rx_group *g = (rx_group *)calloc(1, sizeof(rx_group));
+    if (!g) return RX_ENOMEM;
+    g->n = n;
+    g->flags = flags;
+    g->nw = n < 8 ? n : 8;
+    g->m = (rx_handle **)malloc(sizeof(rx_handle *) * n);
+    g->order = (int *)malloc(sizeof(int) * n);
+    g->tuned = (int *)calloc(n, sizeof(int));
+    if (!g->m || !g->order || !g->tuned) {
+        rx_group_destroy(g);
+        return RX_ENOMEM;
+    }
+    for (int i = 0; i < n; i++) {
+        g->m[i] = members[i];
+        g->order[i] = i;
+        g->tuned[i] = members[i]->cfg.kk_front | (members[i]->ep.warps << 4);
+    }
+    // longest buffers first, dealt round-robin over the workers
+    for (int i = 1; i < n; i++)
+        for (int j = i; j > 0 && g->m[g->order[j]]->nb > g->m[g->order[j - 1]]->nb; j--) {
+            int t = g->order[j];
+            g->order[j] = g->order[j - 1];
+            g->order[j - 1] = t;
+        }
+    bool ok = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int w = 0; w < g->nw && ok; w++)
+        ok = cudaStreamCreateWithFlags(&g->ws[w], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&g->done[w], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        rx_group_destroy(g);
+        return RX_ECUDA;
+    }
+    if (flags & RX_GROUP_TUNE) {
+        rx_status r = tune_group(g);
+        if (r != RX_OK) {
+            rx_group_destroy(g);
+            return r;
+        }
+    }
+    *out = g;
+    return RX_OK;
+}
+
+rx_status rx_group_tuning(const rx_group *g, int i, int32_t *kk_front, int32_t *eq_warps)
+{
+    if (!g || i < 0 || i >= g->n || !kk_front || !eq_warps) return RX_EINVAL;
+    *kk_front = g->tuned[i] & 15;
+    *eq_warps = g->tuned[i] >> 4;
+    return RX_OK;
+}
+
+rx_status rx_group_process(rx_group *g, const uint8_t *const *ins, uint8_t *const *outs, void *stream,
+                           int64_t *nbits_out)
+{
+    if (!g || !ins || !outs || !nbits_out) return RX_EINVAL;
+    cudaStream_t caller = (cudaStream_t)stream;
+    const bool graph = (g->flags & RX_GROUP_GRAPH) != 0;
+    if (graph && !caller) return RX_EINVAL;   // the legacy default stream cannot be captured
+    for (int i = 0; i < g->n; i++) {
+        if (g->m[i]->broken) return RX_ESTATE;
+        if (!ins[i] || (((uintptr_t)ins[i]) & 15)) return RX_EINVAL;
+    }
+    if (graph && cudaStreamBeginCapture(caller, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return RX_ECUDA;
+    cudaError_t e = cudaEventRecord(g->fork, caller);
+    for (int w = 0; w < g->nw && e == cudaSuccess; w++) e = cudaStreamWaitEvent(g->ws[w], g->fork, 0);
+    rx_status r = e == cudaSuccess ? RX_OK : RX_ECUDA;
+    for (int k = 0; k < g->n && r == RX_OK; k++) {
+        int i = g->order[k];
+        rx_handle *h = g->m[i];
+        cudaStream_t ws = g->ws[k % g->nw];
+        int prof = h->prof_on;
+        h->prof_on = 0;   // no stage events inside a group round
+        r = enqueue_call(h, ins[i], outs[i], nullptr, nullptr, ws, ws, ws, &nbits_out[i]);
+        h->prof_on = prof;
+    }
+    for (int w = 0; w < g->nw && r == RX_OK; w++)
+        if (cudaEventRecord(g->done[w], g->ws[w]) != cudaSuccess || cudaStreamWaitEvent(caller, g->done[w], 0) != cudaSuccess)
+            r = RX_ECUDA;
+    if (!graph) return r;
+    cudaGraph_t gr = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(caller, &gr);
+    if (r != RX_OK || ec != cudaSuccess || !gr) {
+        // the members' stream positions advanced for work that never ran
+        for (int i = 0; i < g->n; i++) g->m[i]->broken = 1;
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        return r != RX_OK ? r : RX_ECUDA;
+    }
+    if (g->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(g->exec, gr, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(g->exec);
+            g->exec = nullptr;
+        }
+    }
+    if (!g->exec) ec = cudaGraphInstantiate(&g->exec, gr, 0);
+    if (ec == cudaSuccess) ec = cudaGraphLaunch(g->exec, caller);
+    cudaGraphDestroy(gr);
+    if (ec != cudaSuccess) {
+        for (int i = 0; i < g->n; i++) g->m[i]->broken = 1;
+        return RX_ECUDA;
+    }
+    return RX_OK;
 }
 
 rx_status rx_set_cnn(rx_handle *h, const rx_cnn *cnn)

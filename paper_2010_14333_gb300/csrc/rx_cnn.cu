@@ -461,11 +461,7 @@ cudaError_t launch_cnn_decide(const float *prm, const void *prm_bf, const float2
 {
     CnnSave sv;
     memset(&sv, 0, sizeof sv);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_cnn_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, FwdSmem::TOTAL);
-        attr = true;
-    }
+    // the shared-memory attribute of k_cnn_fwd was set by rx_cnn_create on this device
     k_cnn_fwd<<<nseg, kCnnThreads, FwdSmem::TOTAL, st>>>(prm, (const __nv_bfloat16 *)prm_bf, y, nullptr, seg_base,
                                                         2 * CS, nullptr, sv, dec, winb, winrec, prbs_bits, k_first,
                                                         scale, mq);

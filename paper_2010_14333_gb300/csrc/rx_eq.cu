@@ -338,7 +338,7 @@ __device__ __forceinline__ WinOut pam_window(const EqParams &p, const float *ys,
 // Training (train=1): one warp runs the training windows sequentially, staging
 // each window's input with plain loads.
 template <bool QAM, int NT, int MQ, bool FRZ = false>
-__global__ void __launch_bounds__(32 * kEqWarps)
+__global__ void __launch_bounds__(32 * kEqWarpsMax)
     k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Yv, const float2 *__restrict__ zin,
          float2 *taps_in, float2 *taps_out,
          uint8_t *__restrict__ dec, uint8_t *__restrict__ winb, uint4 *__restrict__ winrec,
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(32 * kEqWarps)
     T *zs = ys + ylen;
     T *es = zs + kWin;
     T *ws = es + kWin;
-    long long blk = (long long)blockIdx.x * kEqWarps + wid;
+    long long blk = (long long)blockIdx.x * (blockDim.x >> 5) + wid;
     if (!train && blk >= g.nblk) return;
     // start taps; the slot past the last tap stays zero for the paired loads
     if (QAM) reinterpret_cast<float2 *>(ws)[lane] = lane < NT ? taps_in[lane] : make_float2(0.f, 0.f);
@@ -470,26 +470,52 @@ static cudaError_t launch_eq_t(const EqParams &p, const EqGeom &g, int train, co
                                                dbg_z, prbs, prbs_bits, dst);
         return cudaGetLastError();
     }
-    size_t smem = eq_smem_per_warp(QAM, p.eq_block) * kEqWarps;
-    unsigned grid = (unsigned)((g.nblk + kEqWarps - 1) / kEqWarps);
+    size_t smem = eq_smem_per_warp(QAM, p.eq_block) * p.warps;
+    unsigned grid = (unsigned)((g.nblk + p.warps - 1) / p.warps);
     if constexpr (QAM) {
         if (p.frozen) {
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(k_eq<QAM, NT, MQ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_eq<QAM, NT, MQ, true><<<grid, 32 * kEqWarps, smem, st>>>(p, g, 0, Y, zin, taps_in, taps_out, dec, winb,
+            k_eq<QAM, NT, MQ, true><<<grid, 32 * p.warps, smem, st>>>(p, g, 0, Y, zin, taps_in, taps_out, dec, winb,
                                                                         winrec, dbg_win, dbg_z, prbs, prbs_bits, dst);
             return cudaGetLastError();
         }
     }
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_eq<QAM, NT, MQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_eq<QAM, NT, MQ><<<grid, 32 * kEqWarps, smem, st>>>(p, g, 0, Y, nullptr, taps_in, taps_out, dec, winb, winrec,
+    k_eq<QAM, NT, MQ><<<grid, 32 * p.warps, smem, st>>>(p, g, 0, Y, nullptr, taps_in, taps_out, dec, winb, winrec,
                                                           dbg_win, dbg_z, prbs, prbs_bits, dst);
     return cudaGetLastError();
 }
 
+// shared-memory attribute of the payload kernel for the handle's CTA shape; set
+// once per handle so that launches (and graph captures) make no attribute calls
+template <bool QAM, int NT, int MQ>
+static cudaError_t prepare_eq_t(const EqParams &p)
+{
+    int smem = (int)(eq_smem_per_warp(QAM, p.eq_block) * p.warps);
+    if constexpr (QAM) {
+        if (p.frozen)
+            return cudaFuncSetAttribute(k_eq<QAM, NT, MQ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+    return cudaFuncSetAttribute(k_eq<QAM, NT, MQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 // tap counts with a compiled kernel (odd, half-length odd)
 #define RX_EQ_TAPS(X) X(3) X(7) X(11) X(15) X(19) X(23) X(27) X(31)
+
+size_t eq_smem_bytes(const EqParams &p, int warps) { return eq_smem_per_warp(p.kk != 0, p.eq_block) * warps; }
+
+cudaError_t prepare_eq(const EqParams &p)
+{
+#define RX_PREP(NTV)                                                                                           \
+    if (p.ntaps == NTV) {                                                                                      \
+        if (p.kk && p.mq == 2) return prepare_eq_t<true, NTV, 2>(p);                                            \
+        if (p.kk && p.mq == 4) return prepare_eq_t<true, NTV, 4>(p);                                            \
+        if (!p.kk && p.mq == 2) return prepare_eq_t<false, NTV, 2>(p);                                          \
+        if (!p.kk && p.mq == 4) return prepare_eq_t<false, NTV, 4>(p);                                          \
+        if (!p.kk && p.mq == 8) return prepare_eq_t<false, NTV, 8>(p);                                          \
+    }
+    RX_EQ_TAPS(RX_PREP)
+#undef RX_PREP
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void *Y, const float2 *zin,
                       float2 *taps_in, float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec, float4 *dbg_win,

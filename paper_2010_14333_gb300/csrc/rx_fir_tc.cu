@@ -2,21 +2,27 @@
 //
 // The equaliser's filter z_k = sum_i conj(w_i) y[2k + TH - i] with taps that are
 // fixed for a whole call (the frozen form) is one dense contraction: rows of 16
-// consecutive symbols, each row an (M = 1) x (K = 2 * (30 + NT) real inputs,
-// padded to 128) slice of the 2-sps sequence (a Hankel matrix of y, complex
-// interleaved as stored), times a K x 32 real Toeplitz matrix built from the
-// taps (complex split to real:  [re; im] outputs of each symbol).  One CTA
-// computes 128 rows (2048 symbols) with M = 128, N = 32 tcgen05.mma in BF16,
-// FP16 or FP8-E4M3 with FP32 accumulation in tensor memory:
-//   - one bulk copy (cp.async.bulk) stages the tile's 4.1 k complex inputs in
-//     shared memory as FP32;
-//   - the threads convert them into the K-major operand layout (core matrices
-//     of 8 rows x 16 bytes; FP8 with a power-of-two scale per block of
-//     rows_per_scale rows, taken from the block's largest input);
+// consecutive symbols, each row a K = 2 (30 + NT) real slice (padded to 128) of
+// the 2-sps sequence as stored (complex interleaved; consecutive rows overlap,
+// a Hankel matrix), times a K x 32 real Toeplitz matrix of the taps (complex
+// split to real: re / im output of each symbol).  Tiles of 128 rows (2048
+// symbols) run through M = 128, N = 32 tcgen05.mma in BF16, FP16 or FP8-E4M3
+// with FP32 accumulation in tensor memory.  Persistent CTAs (two per SM), per
+// tile:
+//   - a bulk copy (cp.async.bulk) stages the next tile's 4.1 k complex FP32
+//     inputs while this tile is processed (two stage buffers, one mbarrier each);
+//   - the threads convert the staged inputs into the K-major no-swizzle operand
+//     layout (core matrices of 8 rows x 16 bytes), lanes spread over 8 rows x 4
+//     K-columns with a rotated read order so that neither the shared-memory reads
+//     nor the 16-byte stores conflict; FP8 first takes a power-of-two scale per
+//     block of rows_per_scale rows from the block's largest input;
 //   - one thread issues the MMAs and commits them to an mbarrier;
-//   - each warp reads its 32 accumulator lanes (tcgen05.ld), rescales, stores z.
-// Every wait is bounded: on time-out the kernel records RX_ETIMEOUT, waits
-// (bounded) for its own copies and MMAs, frees its tensor memory and returns.
+//   - each warp reads its 32 accumulator lanes (tcgen05.ld 32x32b), rescales,
+//     transposes through shared memory and stores 512 contiguous bytes per
+//     instruction.
+// The taps' Toeplitz operand is built once per CTA.  Every wait is bounded: on
+// time-out the kernel records RX_ETIMEOUT, waits (bounded) for its own copies and
+// MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -33,15 +39,20 @@ constexpr int kN = 2 * kRowSyms;                   // real outputs per row
 constexpr int kKP = 128;                           // padded K (2 * (30 + NT) <= 122)
 constexpr int kThreads = 128;
 constexpr int kStage = 2 * kRowSyms * kTileRows + 64;   // staged complex inputs per tile
+constexpr int kOutPitch = kN + 4;                  // floats per row of the output transpose
 constexpr uint32_t kTmemCols = 32;
-// dynamic shared memory: A | B | stage | barriers and scratch, padded so that a
-// tile's operand reads stay inside the allocation for any stride of the layout
+// dynamic shared memory: A | B | stage[2] | barriers and scratch
 constexpr int kOffA = 0;
-constexpr int kOffB = kOffA + kTileRows * kKP * 2;   // 32 KB (room for 16-bit A)
+constexpr int kOffB = kOffA + kTileRows * kKP * 2;   // 32 KB (16-bit A; FP8 uses half)
 constexpr int kOffStage = kOffB + kN * kKP * 2;      // + 8 KB
-constexpr int kOffMisc = kOffStage + kStage * 8;
-constexpr int kSmem = 112 * 1024;
-static_assert(kOffMisc + 1024 <= kSmem, "shared-memory plan");
+constexpr int kStageBytes = kStage * 8;
+constexpr int kOffMisc = kOffStage + 2 * kStageBytes;
+// misc: 3 mbarriers + TMEM slot (64 B) | per-row maxima (128 floats) | scale exponents (128 ints)
+constexpr int kOffRmax = kOffMisc + 64;
+constexpr int kOffExp = kOffRmax + kTileRows * 4;
+constexpr int kSmem = kOffExp + kTileRows * 4;
+static_assert(kTileRows * kOutPitch * 4 <= kStageBytes, "output transpose fits a stage buffer");
+static_assert(kSmem <= 113 * 1024, "two CTAs per SM");
 
 template <int PREC> struct Fmt;
 template <> struct Fmt<RX_FIR_BF16> {
@@ -106,41 +117,49 @@ __device__ __forceinline__ int fp8_exp(float m)
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
     k_fir_tc(const float2 *__restrict__ Y, long long ybase, long long k_lo, int nrows,
              const float2 *__restrict__ taps, int ntaps, int rows_per_scale, float2 *__restrict__ z, int *err)
 {
     constexpr int ES = Fmt<PREC>::esize;
     constexpr int EPP = 16 / ES;                    // K elements per 16-byte core row
-    constexpr int PLANES = kKP / EPP;               // K core-matrix columns
+    constexpr int PLANES = kKP / EPP;               // K core-matrix columns (16 or 8)
     constexpr int PLANE_A = kTileRows * 16, PLANE_B = kN * 16;
     constexpr int NMMA = PLANES / 2;                // each MMA consumes two K core matrices
+    constexpr int F2 = EPP / 2;                     // float2 reads per (row, plane)
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sA = sm + kOffA, *sB = sm + kOffB;
-    float2 *stage = reinterpret_cast<float2 *>(sm + kOffStage);
-    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sm + kOffMisc);
-    uint64_t *bar_mma = bar_ld + 1;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_ld + 2);
-    int *s_exp = reinterpret_cast<int *>(sm + kOffMisc + 64);      // per scale block of the tile (<= 128)
+    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sm + kOffMisc);   // [2]
+    uint64_t *bar_mma = bar_ld + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_ld + 3);
+    float *s_rmax = reinterpret_cast<float *>(sm + kOffRmax);          // [128]
+    int *s_exp = reinterpret_cast<int *>(sm + kOffExp);                // [<= 128]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int th = (ntaps - 1) / 2;
     const int ns = 2 * kRowSyms - 2 + ntaps;       // complex inputs per row
-    const int r0 = blockIdx.x * kTileRows;
-    const int rows = min(kTileRows, nrows - r0);
+    const int ntiles = (nrows + kTileRows - 1) / kTileRows;
 
-    // first input of the tile (stream index 2 k - TH of its first symbol), staged
-    // from an even element offset so that the bulk copy starts on 16 bytes
-    const long long m0 = 2 * (k_lo + (long long)r0 * kRowSyms) - th;
-    const long long e0 = m0 - ybase;
-    const long long es = e0 & ~1LL;
-    const int shift = (int)(e0 - es);
-    const int nst = ((shift + 2 * kRowSyms * (rows - 1) + ns) + 1) & ~1;   // complex inputs, even
-
+    // staged range of tile t: from an even element offset, so the copy starts on 16 bytes
+    auto tile_src = [&](int t, long long &es, int &shift, int &nst) {
+        int r0 = t * kTileRows, rows = min(kTileRows, nrows - r0);
+        long long e0 = 2 * (k_lo + (long long)r0 * kRowSyms) - th - ybase;
+        es = e0 & ~1LL;
+        shift = (int)(e0 - es);
+        nst = ((shift + 2 * kRowSyms * (rows - 1) + ns) + 1) & ~1;
+    };
+    auto issue = [&](int t, int buf) {
+        long long es;
+        int shift, nst;
+        tile_src(t, es, shift, nst);
+        fence_async_smem();   // earlier generic writes to this buffer precede the copy
+        mbar_expect_tx(bar_ld + buf, (unsigned)(nst * 8));
+        bulk_g2s(sm + kOffStage + buf * kStageBytes, Y + es, (unsigned)(nst * 8), bar_ld + buf);
+    };
     if (tid == 0) {
         mbar_init(bar_ld, 1);
+        mbar_init(bar_ld + 1, 1);
         mbar_init(bar_mma, 1);
-        mbar_expect_tx(bar_ld, (unsigned)(nst * 8));
-        bulk_g2s(stage, Y + es, (unsigned)(nst * 8), bar_ld);
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
     }
     __syncwarp();
     if (warp == 0) tmem_alloc(tslot, kTmemCols);
@@ -173,83 +192,144 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    const uint32_t idesc = umma_idesc(Fmt<PREC>::code, kTileRows, kN);
 
-    bool ok = mbar_wait(bar_ld, 0);
-    if (!ok) {
-        atomicExch(err, (int)RX_ETIMEOUT);
-        mbar_wait(bar_ld, 0);
-    }
-    ok = __syncthreads_and(ok) != 0;   // one decision for the whole CTA
-    // FP8: scale exponent of each block of rows_per_scale rows (the tile holds
-    // whole blocks), from the largest magnitude any of its rows reads
-    if (PREC == RX_FIR_FP8) {
-        float m = 0.f;
-        if (tid < rows) {
-            const float2 *x = stage + shift + 2 * kRowSyms * tid;
-            for (int s = 0; s < ns; s++) m = fmaxf(m, fmaxf(fabsf(x[s].x), fabsf(x[s].y)));
+    // lane -> (row r_lo, K column p_lo) of an 8 x 4 group; a warp's groups cover
+    // its own 32 rows (r_hi = 4 warp .. 4 warp + 3) and every K column
+    const int r_lo = lane & 7, p_lo = lane >> 3, rot = r_lo % F2;
+    bool ok = true;
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+        const int buf = it & 1;
+        const int r0 = t * kTileRows, rows = min(kTileRows, nrows - r0);
+        long long es;
+        int shift, nst;
+        tile_src(t, es, shift, nst);
+        if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x, buf ^ 1);   // prefetch
+        bool got = mbar_wait(bar_ld + buf, (unsigned)((it >> 1) & 1));
+        if (!got) {
+            atomicExch(err, (int)RX_ETIMEOUT);
+            mbar_wait(bar_ld + buf, (unsigned)((it >> 1) & 1));
         }
-        reinterpret_cast<float *>(s_exp)[tid] = m;
-        __syncthreads();
-        if (tid < kTileRows / rows_per_scale) {
-            float bm = 0.f;
-            for (int r = tid * rows_per_scale; r < (tid + 1) * rows_per_scale; r++)
-                bm = fmaxf(bm, reinterpret_cast<float *>(s_exp)[r]);
-            m = bm;
-        }
-        __syncthreads();
-        if (tid < kTileRows / rows_per_scale) s_exp[tid] = fp8_exp(m);
-        __syncthreads();
-    }
-    // A: row r, K index k -> staged float 2 (shift + 32 r) + k for k < 2 ns, else 0
-    for (int u = tid; u < kTileRows * PLANES; u += kThreads) {
-        int r = u % kTileRows, pl = u / kTileRows;
-        float v[16];
-        const float *src = reinterpret_cast<const float *>(stage + shift + 2 * kRowSyms * r) + pl * EPP;
-#pragma unroll
-        for (int t = 0; t < EPP; t++) v[t] = (r < rows && pl * EPP + t < 2 * ns) ? src[t] : 0.f;
-        float sAv = PREC == RX_FIR_FP8 ? ldexpf(1.f, s_exp[r / rows_per_scale]) : 1.f;
-        *reinterpret_cast<uint4 *>(sA + pl * PLANE_A + r * 16) = pack16<PREC>(v, sAv);
-    }
-    fence_async_smem();
-    __syncthreads();
+        ok = __syncthreads_and(got) != 0;
+        if (!ok) break;
+        const float *stf = reinterpret_cast<const float *>(sm + kOffStage + buf * kStageBytes) + 2 * shift;
 
-    if (tid == 0 && ok) {
-        tc_fence_after();
-        const uint32_t idesc = umma_idesc(Fmt<PREC>::code, kTileRows, kN);
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        // (row, K column) -> the 16 bytes of K elements it holds, read in a rotated
+        // order; returns the EPP floats in natural order
+        auto load_unit = [&](int r, int pl, float (&v)[16]) {
+            const float *base = stf + 4 * kRowSyms * r + pl * EPP;   // rows start 2 kRowSyms complex apart
+            float2 tmp[F2];
 #pragma unroll
-        for (int q = 0; q < NMMA; q++) {
-            uint64_t ad = umma_sdesc(a0 + q * 2 * PLANE_A, PLANE_A, 128);
-            uint64_t bd = umma_sdesc(b0 + q * 2 * PLANE_B, PLANE_B, 128);
-            if (PREC == RX_FIR_FP8) umma_f8(tmem, ad, bd, idesc, q > 0);
-            else umma_f16(tmem, ad, bd, idesc, q > 0);
+            for (int q = 0; q < F2; q++) {
+                int qq = (q + rot) % F2;
+                tmp[q] = *reinterpret_cast<const float2 *>(base + 2 * qq);
+            }
+#pragma unroll
+            for (int q = 0; q < F2; q++) {
+                // undo the rotation: element qq came in slot (qq - rot) mod F2
+                float2 e = tmp[0];
+#pragma unroll
+                for (int u = 1; u < F2; u++)
+                    if (((q - rot + F2) % F2) == u) e = tmp[u];
+                v[2 * q] = e.x;
+                v[2 * q + 1] = e.y;
+            }
+#pragma unroll
+            for (int u = 0; u < EPP; u++)
+                if (r >= rows || pl * EPP + u >= 2 * ns) v[u] = 0.f;
+        };
+
+        if (PREC == RX_FIR_FP8) {
+            // per-row largest input magnitude, then per scale block
+#pragma unroll 1
+            for (int rh = 0; rh < 4; rh++) {
+                int r = 32 * warp + 8 * rh + r_lo;
+                float m = 0.f;
+#pragma unroll 1
+                for (int ph = 0; ph < PLANES / 4; ph++) {
+                    float v[16];
+                    load_unit(r, 4 * ph + p_lo, v);
+#pragma unroll
+                    for (int u = 0; u < EPP; u++) m = fmaxf(m, fabsf(v[u]));
+                }
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+                if (p_lo == 0) s_rmax[r] = m;
+            }
+            __syncthreads();
+            if (tid < kTileRows / rows_per_scale) {
+                float bm = 0.f;
+                for (int r = tid * rows_per_scale; r < (tid + 1) * rows_per_scale; r++) bm = fmaxf(bm, s_rmax[r]);
+                s_exp[tid] = fp8_exp(bm);
+            }
+            __syncthreads();
         }
-        umma_commit(bar_mma);
-    }
-    if (ok) {
-        bool done = mbar_wait(bar_mma, 0);
+        // A: row r, K index k -> staged float 2 (shift + 32 r) + k for k < 2 ns, else 0
+#pragma unroll 1
+        for (int rh = 0; rh < 4; rh++) {
+            int r = 32 * warp + 8 * rh + r_lo;
+            float sAv = PREC == RX_FIR_FP8 ? ldexpf(1.f, s_exp[r / rows_per_scale]) : 1.f;
+#pragma unroll 2
+            for (int ph = 0; ph < PLANES / 4; ph++) {
+                int pl = 4 * ph + p_lo;
+                float v[16];
+                load_unit(r, pl, v);
+                *reinterpret_cast<uint4 *>(sA + pl * PLANE_A + r * 16) = pack16<PREC>(v, sAv);
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+            for (int q = 0; q < NMMA; q++) {
+                uint64_t ad = umma_sdesc(a0 + q * 2 * PLANE_A, PLANE_A, 128);
+                uint64_t bd = umma_sdesc(b0 + q * 2 * PLANE_B, PLANE_B, 128);
+                if (PREC == RX_FIR_FP8) umma_f8(tmem, ad, bd, idesc, q > 0);
+                else umma_f16(tmem, ad, bd, idesc, q > 0);
+            }
+            umma_commit(bar_mma);
+        }
+        bool done = mbar_wait(bar_mma, (unsigned)(it & 1));
         if (!done) {
             atomicExch(err, (int)RX_ETIMEOUT);
-            mbar_wait(bar_mma, 0);
+            mbar_wait(bar_mma, (unsigned)(it & 1));
         }
-        ok = done;
-    }
-    ok = __syncthreads_and(ok) != 0;
-    tc_fence_after();
-    if (ok) {
-        // epilogue: warp w owns accumulator lanes 32w..32w+31 (= rows)
-        uint32_t acc[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), acc);
-        int r = 32 * warp + lane;
-        if (r < rows) {
+        ok = __syncthreads_and(done) != 0;
+        if (!ok) break;
+        tc_fence_after();
+        // epilogue: warp w owns accumulator lanes (= rows) 32w .. 32w+31; rows go
+        // through the consumed stage buffer to leave as contiguous 512-byte stores
+        {
+            uint32_t acc[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), acc);
+            const int r = 32 * warp + lane;
             float inv = 1.f;
-            if (PREC == RX_FIR_FP8) inv = ldexpf(1.f, -(eB + s_exp[r / rows_per_scale]));
-            float4 *dst = reinterpret_cast<float4 *>(z + (long long)(r0 + r) * kRowSyms);
+            if (PREC == RX_FIR_FP8) inv = ldexpf(1.f, -(eB + s_exp[min(r, kTileRows - 1) / rows_per_scale]));
+            float *ot = reinterpret_cast<float *>(sm + kOffStage + buf * kStageBytes);
+            __syncwarp();
 #pragma unroll
-            for (int q = 0; q < kRowSyms / 2; q++)
-                dst[q] = make_float4(__uint_as_float(acc[4 * q]) * inv, __uint_as_float(acc[4 * q + 1]) * inv,
-                                     __uint_as_float(acc[4 * q + 2]) * inv, __uint_as_float(acc[4 * q + 3]) * inv);
+            for (int q = 0; q < kN / 4; q++)
+                *reinterpret_cast<float4 *>(ot + r * kOutPitch + 4 * q) =
+                    make_float4(__uint_as_float(acc[4 * q]) * inv, __uint_as_float(acc[4 * q + 1]) * inv,
+                                __uint_as_float(acc[4 * q + 2]) * inv, __uint_as_float(acc[4 * q + 3]) * inv);
+            __syncwarp();
+            float4 *zt = reinterpret_cast<float4 *>(z + (long long)r0 * kRowSyms);
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                int rr = 32 * warp + 4 * i + (lane >> 3), ch = lane & 7;
+                if (rr < rows)
+                    zt[rr * 8 + ch] = *reinterpret_cast<const float4 *>(ot + rr * kOutPitch + 4 * ch);
+            }
         }
+        tc_fence_before();
+        __syncthreads();   // A, the accumulator and this stage buffer are free again
+    }
+    if (!ok && tid == 0) {
+        // a prefetch may still be in flight: wait for it (bounded) before leaving
+        mbar_wait(bar_ld + ((it + 1) & 1), (unsigned)(((it + 1) >> 1) & 1));
     }
     tc_fence_before();
     __syncthreads();
@@ -258,8 +338,19 @@ __global__ void __launch_bounds__(kThreads)
 
 }  // namespace
 
+cudaError_t prepare_fir_tc(int prec)
+{
+    switch (prec) {
+    case RX_FIR_BF16: return cudaFuncSetAttribute(k_fir_tc<RX_FIR_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    case RX_FIR_FP16: return cudaFuncSetAttribute(k_fir_tc<RX_FIR_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    case RX_FIR_FP8: return cudaFuncSetAttribute(k_fir_tc<RX_FIR_FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_fir_tc(int prec, const float2 *Y, long long ybase, long long k_lo, long long nsym,
-                          const float2 *taps, int ntaps, int scale_block, float2 *z, int *err, cudaStream_t st)
+                          const float2 *taps, int ntaps, int scale_block, float2 *z, int *err, int nsm,
+                          cudaStream_t st)
 {
     if (nsym <= 0) return cudaSuccess;
     if (nsym % kRowSyms || ntaps < 1 || ntaps > 31 || !(ntaps & 1) || scale_block % kRowSyms ||
@@ -267,12 +358,9 @@ cudaError_t launch_fir_tc(int prec, const float2 *Y, long long ybase, long long 
         return cudaErrorInvalidValue;
     int nrows = (int)(nsym / kRowSyms);
     int rps = scale_block / kRowSyms;
-    unsigned grid = (unsigned)((nrows + kTileRows - 1) / kTileRows);
-#define RX_FIR_LAUNCH(P)                                                                                     \
-    do {                                                                                                     \
-        cudaFuncSetAttribute(k_fir_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);               \
-        k_fir_tc<P><<<grid, kThreads, kSmem, st>>>(Y, ybase, k_lo, nrows, taps, ntaps, rps, z, err);         \
-    } while (0)
+    int ntiles = (nrows + kTileRows - 1) / kTileRows;
+    unsigned grid = (unsigned)min(ntiles, 2 * nsm);   // two persistent CTAs per SM
+#define RX_FIR_LAUNCH(P) k_fir_tc<P><<<grid, kThreads, kSmem, st>>>(Y, ybase, k_lo, nrows, taps, ntaps, rps, z, err)
     switch (prec) {
     case RX_FIR_BF16: RX_FIR_LAUNCH(RX_FIR_BF16); break;
     case RX_FIR_FP16: RX_FIR_LAUNCH(RX_FIR_FP16); break;

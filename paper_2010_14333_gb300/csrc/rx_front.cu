@@ -14,6 +14,8 @@
 // style into a radix-16 pass over the stride-N2 index (K1a, registers only), an
 // N2-point FFT per row with the multiplier and the inverse in shared memory (K1b),
 // and the inverse radix-16 pass fused with sqrt/exp/field assembly (K1c).
+#include <cooperative_groups.h>
+
 #include "rx_common.cuh"
 #include "rx_internal.cuh"
 
@@ -507,6 +509,278 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
     }
 }
 
+// ====================================================== KK front end, fused
+// One thread-block cluster of kClC CTAs per block pair computes the whole
+// Hilbert transform of the pair in distributed shared memory (the 2^16-point
+// case, N2 = 4096): CTA c owns rows k2 = 2c, 2c+1 of the 16 x 4096 four-step
+// layout, padded as in K1b.
+//   A  columns:  CTA c takes columns n1 in [512 c, 512 c + 512): 12-bit codes
+//      straight from the packed input, u = ln(I)/2, radix-16 DFT over the
+//      stride-N2 index, twiddle, each result stored into the shared memory of
+//      the CTA that owns its row;
+//   B  rows:     forward 4096-point FFT, Hilbert multiplier, inverse FFT of the
+//      CTA's two rows in its own shared memory (the passes of K1b);
+//   C  columns:  the 16 values of each of its columns gathered back from the
+//      owners, inverse radix-16 DFT, E = sqrt(I) exp(j phi) for the kept
+//      outputs and the carrier sums (the reduction of K1c).
+// Cluster barriers separate the phases, so the 512 KB of a pair never leave the
+// chip; global traffic is the packed input and the field.
+constexpr int kClC = 8;
+constexpr int kClThreads = 256;
+constexpr int kClN2 = 4096;
+constexpr int kClRow = kClN2 + kClN2 / 16;   // padded row
+constexpr int kClCols = kClN2 / kClC;        // columns per CTA
+constexpr size_t kClSmem = (size_t)(2 * kClRow + 512 + 128) * sizeof(float2);
+
+// 12-bit codes of 32 consecutive stream samples (one per lane) starting at
+// virtual-buffer offset t0 (a multiple of 32, so its 48 bytes start on 16 bytes
+// and lie wholly in the history or in this buffer): lanes 0..11 load one word
+// each, every lane takes its two bytes from the owners by shuffle.
+__device__ __forceinline__ uint32_t warp_codes(const KkPacked &pk, long long t0, int lane)
+{
+    long long vb = (3 * t0) >> 1;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(vb < pk.hist_bytes ? pk.hist + vb
+                                                                                : pk.in + (vb - pk.hist_bytes));
+    uint32_t w = lane < 12 ? __ldg(src + lane) : 0u;
+    int b = (3 * lane) >> 1;
+    uint32_t w0 = __shfl_sync(0xffffffffu, w, b >> 2);
+    uint32_t w1 = __shfl_sync(0xffffffffu, w, min((b >> 2) + 1, 31));
+    uint32_t v = __funnelshift_r(w0, w1, 8 * (b & 3));
+    uint32_t lo = v & 0xFFu, hi = (v >> 8) & 0xFFu;
+    if (pk.order == 0) return (lane & 1) ? ((lo >> 4) | (hi << 4)) : (lo | ((hi & 0xFu) << 8));
+    return (lane & 1) ? (((lo & 0xFu) << 8) | hi) : ((lo << 4) | (hi >> 4));
+}
+
+__global__ void __cluster_dims__(kClC, 1, 1) __launch_bounds__(kClThreads, 3)
+    k_kk_cluster(KkGeom g, KkPacked pk, const KkTables tb, float2 *__restrict__ E,
+                 const float2 *__restrict__ E_prev, CarrierPartial *__restrict__ partials, DevState *dst)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ float2 smc[];
+    float2 *rows = smc;                         // [2][kClRow]
+    const TwSmem tw = stage_tw(tb.twN, g.N, smc + 2 * kClRow);
+    const TwSmem tw2 = stage_tw(tb.twN2, kClN2, smc + 2 * kClRow + 512);
+    const int c = (int)cl.block_rank();
+    const int pair = blockIdx.x / kClC;
+    const int t = threadIdx.x;
+    const bool hb = 2 * pair + 1 < g.J;
+    const uint32_t c_first = first_code(pk, dst);
+    if (pk.first_call && blockIdx.x == 0 && t == 0) dst->first_code = (int)c_first;
+    // history of the next call (packed bytes [in_bytes, in_bytes + hist_bytes) of
+    // the virtual buffer), spread over the grid
+    if (pk.hist_next) {
+        long long nch = pk.hist_bytes / 16;
+        for (long long ch = (long long)blockIdx.x * blockDim.x + t; ch < nch; ch += (long long)gridDim.x * blockDim.x) {
+            long long vb = pk.in_bytes + 16 * ch;
+            const uint8_t *src = vb < pk.hist_bytes ? pk.hist + vb : pk.in + (vb - pk.hist_bytes);
+            reinterpret_cast<uint4 *>(pk.hist_next)[ch] = __ldg(reinterpret_cast<const uint4 *>(src));
+        }
+    }
+    if (blockIdx.x == 0)   // field history for the matched filter
+        for (int i = t; i < kEHist; i += blockDim.x) {
+            long long n = g.e_prev - kEHist + i;
+            E[i] = (n < 0) ? make_float2(0.f, 0.f) : E_prev[n - g.ebase_prev];
+        }
+    __syncthreads();   // staged twiddles
+
+    // ---- A: forward column DFTs, scattered to the row owners
+    const long long wsa = ols_ws(g, 2 * pair), wsb = hb ? ols_ws(g, 2 * pair + 1) : 0;
+    cl.sync();         // every CTA of the cluster is running before remote stores
+#pragma unroll 1
+    for (int h = 0; h < kClCols / kClThreads; h++) {
+        const int n1 = c * kClCols + h * kClThreads + t;
+        float2 x[16];
+        const int lane = t & 31;
+        const int n1w = n1 - lane;                  // first column of the warp
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            long long na = wsa + n1w + (long long)kClN2 * q;   // warp-uniform, a multiple of 32
+            uint32_t ca = na < 0 ? c_first : warp_codes(pk, na - g.cbase, lane);
+            float ub = 0.f;
+            if (hb) {
+                long long nb2 = wsb + n1w + (long long)kClN2 * q;
+                ub = __ldg(tb.lnt + (nb2 < 0 ? c_first : warp_codes(pk, nb2 - g.cbase, lane)));
+            }
+            x[q] = make_float2(__ldg(tb.lnt + ca), ub);
+        }
+        dft16<false>(x);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; k2++) {
+            float2 *dstp = cl.map_shared_rank(rows + (k2 & 1) * kClRow, k2 >> 1);
+            dstp[pad16(n1)] = k2 ? cmul(x[k2], tw(n1 * k2)) : x[0];
+        }
+    }
+    cl.sync();
+
+    // ---- B: the CTA's two rows, FFT / Hilbert / inverse FFT (passes of K1b, P = 3)
+#pragma unroll 1
+    for (int lr = 0; lr < 2; lr++) {
+        const int k2 = 2 * c + lr;
+        float2 *s = rows + lr * kClRow;
+        float2 x[16];
+#pragma unroll
+        for (int r = 0; r < 16; r++) x[r] = s[pad16(t + r * 256)];
+        dft16<false>(x);
+#pragma unroll
+        for (int r = 1; r < 16; r++) x[r] = cmul(x[r], tw2(t * r));
+#pragma unroll
+        for (int r = 0; r < 16; r++) s[pad16(t + r * 256)] = x[r];
+        __syncthreads();
+        {   // pass 1 (M = 256)
+            int o = (t / 16) * 256, j = t % 16;
+#pragma unroll
+            for (int r = 0; r < 16; r++) x[r] = s[pad16(o + j + r * 16)];
+            dft16<false>(x);
+#pragma unroll
+            for (int r = 1; r < 16; r++) x[r] = cmul(x[r], tw2(j * r * 16));
+#pragma unroll
+            for (int r = 0; r < 16; r++) s[pad16(o + j + r * 16)] = x[r];
+        }
+        __syncthreads();
+        {   // pass 2 (M = 16), Hilbert multiplier on X[k2 + 16 drev(o + r)], first inverse pass
+            int o = t * 16;
+#pragma unroll
+            for (int r = 0; r < 16; r++) x[r] = s[pad16(o + r)];
+            dft16<false>(x);
+#pragma unroll
+            for (int r = 0; r < 16; r++) x[r] = hilbert_mul(x[r], k2 + 16 * drev16<3>(o + r), g.N);
+            dft16<true>(x);
+#pragma unroll
+            for (int r = 0; r < 16; r++) s[pad16(o + r)] = x[r];
+        }
+        __syncthreads();
+        {   // inverse pass 1
+            int o = (t / 16) * 256, j = t % 16;
+#pragma unroll
+            for (int r = 0; r < 16; r++) {
+                x[r] = s[pad16(o + j + r * 16)];
+                if (r) x[r] = cmulc(x[r], tw2(j * r * 16));
+            }
+            dft16<true>(x);
+#pragma unroll
+            for (int r = 0; r < 16; r++) s[pad16(o + j + r * 16)] = x[r];
+        }
+        __syncthreads();
+        // inverse pass 0, in place
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            x[r] = s[pad16(t + r * 256)];
+            if (r) x[r] = cmulc(x[r], tw2(t * r));
+        }
+        dft16<true>(x);
+#pragma unroll
+        for (int r = 0; r < 16; r++) s[pad16(t + r * 256)] = x[r];
+    }
+    cl.sync();
+
+    // ---- C: inverse column DFTs from the row owners, field and carrier sums
+    float sre = 0.f, sim = 0.f;
+    int si2 = 0;
+    const float invN = 1.0f / (float)g.N;
+#pragma unroll 1
+    for (int h = 0; h < kClCols / kClThreads; h++) {
+        const int n1 = c * kClCols + h * kClThreads + t;
+        float2 x[16];
+#pragma unroll
+        for (int k2 = 0; k2 < 16; k2++) {
+            const float2 *srcp = cl.map_shared_rank(rows + (k2 & 1) * kClRow, k2 >> 1);
+            x[k2] = srcp[pad16(n1)];
+        }
+#pragma unroll
+        for (int k2 = 1; k2 < 16; k2++) x[k2] = cmulc(x[k2], tw(n1 * k2));
+        dft16<true>(x);
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            int j = 2 * pair + half;
+            if (j >= g.J) break;
+            long long ws = half ? wsb : wsa;
+            int tlo, thi;
+            ols_kept(g, j, tlo, thi);
+            const int lane = t & 31;
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                int tt = n1 + kClN2 * q;
+                int tw0 = tt - lane;                    // warp-uniform
+                if (tw0 + 31 < tlo || tw0 >= thi) continue;
+                long long n = ws + tt;
+                long long nw = ws + tw0;
+                uint32_t code = nw < 0 ? c_first : warp_codes(pk, nw - g.cbase, lane);
+                if (tt < tlo || tt >= thi) continue;
+                float phi = (half ? x[q].y : x[q].x) * invN;
+                float sn, cs;
+                __sincosf(phi, &sn, &cs);   // |phi| < pi: absolute error <= 2^-21.41
+                float A = __ldg(tb.sqt + code);
+                float2 e = make_float2(A * cs, A * sn);
+                E[n - g.ebase] = e;
+                sre += e.x;
+                sim += e.y;
+                si2 += code ? 2 * (int)code : 1;
+            }
+        }
+    }
+    cl.sync();   // no CTA leaves while its rows may still be read
+
+    // CTA partial (fixed-order tree), then the last CTA of the grid reduces in FP64
+    __shared__ float rre[kClThreads / 32], rim[kClThreads / 32];
+    __shared__ int ri[kClThreads / 32];
+    __shared__ bool last;
+    sre = warp_sum_f(sre);
+    sim = warp_sum_f(sim);
+    si2 = warp_sum_i(si2);
+    int lane = t & 31, wid = t >> 5;
+    if (lane == 0) { rre[wid] = sre; rim[wid] = sim; ri[wid] = si2; }
+    __syncthreads();
+    const int ncta = gridDim.x;
+    if (t == 0) {
+        double a = 0, b = 0;
+        long long cc = 0;
+        for (int i = 0; i < kClThreads / 32; i++) { a += rre[i]; b += rim[i]; cc += ri[i]; }
+        partials[blockIdx.x].re = a;
+        partials[blockIdx.x].im = b;
+        partials[blockIdx.x].i2 = cc;
+        __threadfence();
+        unsigned tk = atomicAdd(&dst->ticket[g.slot], 1u);
+        last = (tk == (unsigned)(ncta - 1));
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // FP64 scratch in the row area: no CTA of the cluster reads it after the last barrier
+    double *dre = reinterpret_cast<double *>(rows), *dim = dre + kClThreads;
+    long long *dii = reinterpret_cast<long long *>(dim + kClThreads);
+    double a = 0, b = 0;
+    long long cc = 0;
+    for (int i = t; i < ncta; i += blockDim.x) {
+        volatile CarrierPartial *pp = partials + i;
+        a += pp->re;
+        b += pp->im;
+        cc += pp->i2;
+    }
+    dre[t] = a;
+    dim[t] = b;
+    dii[t] = cc;
+    __syncthreads();
+    for (int sft = blockDim.x / 2; sft > 0; sft >>= 1) {
+        if (t < sft) {
+            dre[t] += dre[t + sft];
+            dim[t] += dim[t + sft];
+            dii[t] += dii[t + sft];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double cnt = (double)(g.e_k - g.e_prev);
+        double cr = dre[0] / cnt, ci = dim[0] / cnt;
+        double ibar = (double)dii[0] / (2.0 * cnt);
+        double P = ibar - (cr * cr + ci * ci);
+        dst->cg[g.slot][0] = cr;
+        dst->cg[g.slot][1] = ci;
+        dst->cg[g.slot][2] = (P > 0.0) ? 1.0 / sqrt((double)g.sps * P) : 1.0;
+        dst->ticket[g.slot] = 0u;
+    }
+}
+
 __global__ void k_kk_hist(KkPacked pk)
 {
     long long nch = pk.hist_bytes / 16;
@@ -531,6 +805,11 @@ cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st)
     return cudaGetLastError();
 }
 
+cudaError_t prepare_kk_front()
+{
+    return cudaFuncSetAttribute(k_kk_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem);
+}
+
 cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, const KkTables &tb,
                             float2 *E, const float2 *E_prev, CarrierPartial *partials, DevState *dst,
                             cudaStream_t st, void *prof)
@@ -543,6 +822,15 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     pk.in_bytes = inp.in_bytes;
     pk.order = inp.order;
     pk.first_call = inp.first_call;
+    if (g.N2 == kClN2 && g.fused) {
+        // 2^16-point blocks: the fused cluster kernel (profiled as the K1a stage)
+        prof_stage(prof, 1, st);
+        k_kk_cluster<<<g.npairs * kClC, kClThreads, kClSmem, st>>>(g, pk, tb, E, E_prev, partials, dst);
+        prof_stage(prof, -2, st);
+        prof_stage(prof, -3, st);
+        prof_stage(prof, -4, st);
+        return cudaGetLastError();
+    }
     dim3 grid(g.N2 / kCtaK1, g.npairs);
     dim3 grid_a(g.N2 / kCtaK1, g.npairs + (inp.hist_next ? 1 : 0));
     prof_stage(prof, 1, st);

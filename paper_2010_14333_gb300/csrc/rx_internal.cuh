@@ -15,7 +15,7 @@ constexpr int kYHist = 16;        // 2-sps samples of equaliser history before a
 constexpr int kEHist = 64;        // ADC samples of field history kept for the MF
 constexpr int kPamHist = 64;      // codes kept before a PAM buffer (>= 2 * MF half length)
 constexpr int kCtaK1 = 256;       // threads per K1a / K1c CTA
-constexpr int kEqWarps = 4;       // warps (equaliser blocks) per K3 CTA
+constexpr int kEqWarpsMax = 8;    // most warps (equaliser blocks) per K3 CTA
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before flagging RX_ETIMEOUT
 constexpr int kSlots = 3;         // per-call buffer ring (field, MF output, decisions, carrier/gain)
 
@@ -53,6 +53,7 @@ struct KkGeom {
     int N, V, hop, J, npairs, N2;
     int sps;
     int slot;                  // carrier / gain slot written by this call
+    int fused;                 // 2^16-point blocks: one cluster kernel instead of three
 };
 
 // constant tables of the KK front end (device pointers).  Twiddles of an M-point
@@ -93,6 +94,7 @@ struct EqParams {
     int kk, mq, bps, ntaps, th, win, eq_block, ntrain, ncma, bps_b, amb_syms;
     float scale, r2, mu, mu_train, mu_cma;
     int frozen;   // payload blocks filter with the call's start taps (block-Toeplitz form)
+    int warps;    // equaliser blocks (warps) per CTA
 };
 
 // ------------------------------------------------------------------ launchers
@@ -131,7 +133,16 @@ cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void 
 // block-Toeplitz FIR on the tensor cores (frozen taps): z[k - k_lo] for
 // k in [k_lo, k_lo + nsym), z_k = sum_i conj(w_i) Y[2k + TH - i - ybase]
 cudaError_t launch_fir_tc(int prec, const float2 *Y, long long ybase, long long k_lo, long long nsym,
-                          const float2 *taps, int ntaps, int scale_block, float2 *z, int *err, cudaStream_t st);
+                          const float2 *taps, int ntaps, int scale_block, float2 *z, int *err, int nsm,
+                          cudaStream_t st);
+
+// one-time kernel attributes (dynamic shared memory above 48 KB) of what a handle
+// launches, set at creation so that launches and graph captures make no such calls
+cudaError_t prepare_eq(const EqParams &p);
+size_t eq_smem_bytes(const EqParams &p, int warps);   // dynamic shared memory of a payload CTA
+constexpr size_t kMaxSmemCta = 227 * 1024;
+cudaError_t prepare_fir_tc(int prec);
+cudaError_t prepare_kk_front();
 
 cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in,
                          const uint8_t *dec, const uint8_t *winb, const uint4 *winrec, float4 *dbg_win,

@@ -47,6 +47,8 @@ class Pair:
         dbg = cfg.pop("debug")
         ocfg = dict(cfg)
         ocfg["eq_frozen"] = int(ocfg.pop("fir_prec", 0) != 0)   # the oracle's frozen-tap form
+        for k in ("kk_front", "eq_warps"):                       # implementation choices only
+            ocfg.pop(k, None)
         self.o = oracle.Oracle(**oracle.default_cfg(fmt, nb, **ocfg))
         self.g = rx.Receiver(fmt, nb, debug=dbg, **cfg)
         self.report = dict(exempt=0, cascade=0, symbols=0, windows=0, ambiguous=0, calls=0)

@@ -110,3 +110,16 @@ def test_receiver_rejects_unknown_option_and_bad_precision():
     c.fir_prec = 5
     c.eq_block = 1024
     assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
+
+
+def test_group_rejects_bad_arguments():
+    lib = rx.load()
+    g = C.c_void_p()
+    arr = (C.c_void_p * 2)(None, None)
+    assert lib.rx_group_create(arr, 2, 0, C.byref(g)) == 1          # null members
+    assert lib.rx_group_create(arr, 0, 0, C.byref(g)) == 1          # empty group
+    assert lib.rx_group_create(None, 2, 0, C.byref(g)) == 1
+    assert lib.rx_group_process(None, None, None, None, None) == 1
+    f, w = C.c_int32(), C.c_int32()
+    assert lib.rx_group_tuning(None, 0, C.byref(f), C.byref(w)) == 1
+    assert lib.rx_group_destroy(None) == 1

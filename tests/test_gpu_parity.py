@@ -46,6 +46,12 @@ def test_kk16_full_size_buffer():
     assert 1e-4 < so["ber"] < 2e-2
 
 
+def test_kk16_full_size_cluster_front():
+    """The same two 2^22-sample buffers through the one-kernel cluster front end."""
+    p, s, so = run(4, 1 << 22, 2, kk_front=1)
+    assert s["bits"] == so["bits"] > 8_000_000
+
+
 @pytest.mark.parametrize("fmt", [0, 1, 2])
 def test_pam_chain(fmt):
     p, s, so = run(fmt, 1 << 20 if fmt == 1 else 1 << 18, 2)
