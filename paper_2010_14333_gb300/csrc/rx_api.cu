@@ -1,6 +1,7 @@
 // C ABI of the receiver library: handle lifetime, per-call scheduling of the
 // kernels, constant tables, statistics and debug copies.  See include/rx.h.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -9,6 +10,23 @@
 #include "rx_internal.cuh"
 
 using namespace rxk;
+
+// RX_TRACE=1 in the environment: report each failing CUDA call of the library on
+// stderr (name and place), for diagnosing a status of RX_ECUDA
+static bool trace_on()
+{
+    static int on = -1;
+    if (on < 0) {
+        const char *v = getenv("RX_TRACE");
+        on = (v && *v && *v != '0') ? 1 : 0;
+    }
+    return on == 1;
+}
+static cudaError_t traced(cudaError_t e, const char *where)
+{
+    if (e != cudaSuccess && trace_on()) fprintf(stderr, "rx: %s failed: %s\n", where, cudaGetErrorName(e));
+    return e;
+}
 
 struct rx_handle {
     int fmt, kk, bps, mq, sps, decim, hmf, th;
@@ -495,6 +513,10 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
                               uint8_t *host_out, cudaStream_t sf, cudaStream_t sb, cudaStream_t sc,
                               int64_t *nbits_out)
 {
+    // the launchers detect failures with cudaGetLastError: clear an error some
+    // earlier, unrelated call left behind (a sticky one makes the launches fail)
+    cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess) traced(stale, "an earlier CUDA call (cleared)");
     const rx_config &c = h->cfg;
     Sched s = schedule(h, h->calls, h->q_prev);
     long long base = h->calls * h->nb;
@@ -563,12 +585,12 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         g.slot = ew_new;
         g.fused = c.kk_front;
         KkTables tb = {h->lnt, h->sqt, h->twN, h->twN2};
-        e = launch_kk_front(g, kin, h->fftws, tb, h->E[ew_new], h->E[h->ew], h->partials, h->st, sf,
-                            h->prof_cur ? h : nullptr);
+        e = traced(launch_kk_front(g, kin, h->fftws, tb, h->E[ew_new], h->E[h->ew], h->partials, h->st, sf,
+                                   h->prof_cur ? h : nullptr), "KK front end");
         h->ew = ew_new;
         h->ebase_cur = g.ebase;
     } else if (e == cudaSuccess && h->kk) {
-        e = launch_kk_hist(kin, sf);
+        e = traced(launch_kk_hist(kin, sf), "KK history copy");
     }
     if (h->kk) h->hw ^= 1;
     // matched filter
@@ -646,6 +668,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     if (h->prof_cur) h->prof_head++;
     h->prof_cur = 0;
     if (e != cudaSuccess) {
+        traced(e, "rx_process enqueue");
         h->broken = 1;
         return RX_ECUDA;
     }
@@ -922,7 +945,12 @@ static float time_variant(int fmt, double baud, double fs, long long nb, rx_conf
                           int nbuf, uint8_t *bits, cudaStream_t st)
 {
     rx_handle *t = nullptr;
-    if (rx_create((rx_format)fmt, baud, fs, nb, &c, &t) != RX_OK) return -1.f;
+    rx_status cr = rx_create((rx_format)fmt, baud, fs, nb, &c, &t);
+    if (cr != RX_OK) {
+        if (trace_on()) fprintf(stderr, "rx: tuner candidate rejected by rx_create: %s\n", rx_strerror(cr));
+        cudaGetLastError();
+        return -1.f;
+    }
     float best = -1.f;
     int64_t nbits;
     cudaEvent_t a, b;
@@ -942,6 +970,8 @@ static float time_variant(int fmt, double baud, double fs, long long nb, rx_conf
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     rx_destroy(t);
+    cudaError_t e = cudaGetLastError();   // a failed candidate leaves nothing behind
+    if (!ok || e != cudaSuccess) traced(e != cudaSuccess ? e : cudaErrorUnknown, "tuner candidate");
     return ok ? best : -1.f;
 }
 

@@ -484,12 +484,14 @@ static cudaError_t launch_eq_t(const EqParams &p, const EqGeom &g, int train, co
     return cudaGetLastError();
 }
 
-// shared-memory attribute of the payload kernel for the handle's CTA shape; set
-// once per handle so that launches (and graph captures) make no attribute calls
+// shared-memory attribute of the payload kernel, set to the largest CTA any
+// handle may launch (the attribute belongs to the function, which handles with
+// different CTA shapes share); set at handle creation so that launches (and graph
+// captures) make no attribute calls
 template <bool QAM, int NT, int MQ>
 static cudaError_t prepare_eq_t(const EqParams &p)
 {
-    int smem = (int)(eq_smem_per_warp(QAM, p.eq_block) * p.warps);
+    const int smem = (int)kMaxSmemCta;
     if constexpr (QAM) {
         if (p.frozen)
             return cudaFuncSetAttribute(k_eq<QAM, NT, MQ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

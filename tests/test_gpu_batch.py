@@ -134,3 +134,19 @@ def test_eq_warps_do_not_change_results(warps):
     nb = 1 << 19
     g = make_stream(4, nb, 4, seed=17, workers=4)
     same(batched(4, nb, g["packed"], [4], eq_warps=warps), sequential(4, nb, g["packed"]))
+
+
+def test_handles_with_different_cta_shapes_coexist():
+    """A kernel's shared-memory limit belongs to the function: creating a handle
+    with small equaliser CTAs after one with large CTAs must not break the latter."""
+    nb = 1 << 19
+    g = make_stream(4, nb, 3, seed=18, workers=4)
+    r8 = rx.Receiver(4, nb, eq_warps=8)
+    r2 = rx.Receiver(4, nb, eq_warps=2)
+    for p in g["packed"]:
+        d = torch.from_numpy(p).cuda()
+        r8.process(d)
+        r2.process(d)
+    s8, s2 = r8.stats(), r2.stats()
+    assert s8["bits"] == s2["bits"] > 0 and s8["bit_errors"] == s2["bit_errors"]
+    assert s8["device_error"] == 0 and s2["device_error"] == 0
