@@ -635,8 +635,9 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
             // learned equaliser: one segment per payload window
             long long seg_base = 2 * pay_lo - 12 - h->ybase_cur;
             e = launch_cnn_decide(rx_cnn_dev_params(h->cnn), rx_cnn_dev_params_bf16(h->cnn),
-                                  (const float2 *)h->Y[h->yw], seg_base, g.nwin, h->dec[ds], h->winb[ds],
-                                  h->winrec[ds], h->prbs_bits, pay_lo, h->ep.scale, h->mq, sb);
+                                  (const float2 *)h->Y[h->yw], seg_base, s.f_k - h->ybase_cur, g.nwin, h->dec[ds],
+                                  h->winb[ds], h->winrec[ds], h->prbs_bits, pay_lo, h->ep.scale, h->mq,
+                                  h->dbg_z ? h->dbg_z + (pay_lo - sym_lo) : nullptr, &h->st->err, h->nsm, sb);
         } else {
             const float2 *zin = nullptr;
             if (c.fir_prec >= RX_FIR_BF16) {
@@ -1172,6 +1173,7 @@ rx_status rx_group_process(rx_group *g, const uint8_t *const *ins, uint8_t *cons
 rx_status rx_set_cnn(rx_handle *h, const rx_cnn *cnn)
 {
     if (!h || (cnn && !h->kk)) return RX_EINVAL;
+    if (cnn && prepare_cnn_rx() != cudaSuccess) return RX_ECUDA;
     h->cnn = cnn;
     return RX_OK;
 }

@@ -19,8 +19,10 @@
 #include <string.h>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "rx_async.cuh"
 #include "rx_common.cuh"
 #include "rx_internal.cuh"
 
@@ -455,16 +457,349 @@ __global__ void k_cnn_tobf(const float *__restrict__ prm, __nv_bfloat16 *__restr
     if (i < NPRM) prm_bf[i] = __float2bfloat16(prm[i]);
 }
 
-cudaError_t launch_cnn_decide(const float *prm, const void *prm_bf, const float2 *y, long long seg_base, int nseg,
-                              uint8_t *dec, uint8_t *winb, uint4 *winrec, const uint32_t *prbs_bits,
-                              long long k_first, float scale, int mq, cudaStream_t st)
+// ====================================================================
+// Receiver inference on the fifth-generation tensor cores (tcgen05).
+//
+// Tiles of kTS = 256 symbols (four 64-symbol windows) per iteration of a
+// persistent CTA (one per SM, 512 threads: four warps per tensor-memory lane
+// quarter, each taking a quarter of the accumulator columns).  Activations live in shared memory as
+// four "planes" of 8 channels, each position one 16-byte row: with this layout
+// the im2col operand of a 32-channel, 9-tap convolution at K-step ks (taps ks/2,
+// channel groups 2 (ks % 2) and +1) is the plane pair read from position
+// p + ks/2 onwards, i.e. a K-major no-swizzle matrix descriptor whose start
+// address moves by whole 16-byte rows; no im2col copy is made.
+//   layer 1 (2 -> 32, K = 18 padded to 32): an explicit FP16 im2col of the
+//      FP32 input (16-byte rows are 8 consecutive reals of y), FP16 weights,
+//      tcgen05.mma (M = 128, N = 32) and the same epilogue as the other layers;
+//   layers 2, 3 (32 -> 32): 18 tcgen05.mma (M = 128, N = 32, K = 16) per 128
+//      output positions into tensor memory; epilogue bias + GELU -> BF16 planes;
+//   MLP 32 -> 64: tcgen05.mma (M = 128, N = 64) over all positions; the epilogue
+//      keeps the symbol (even) positions, GELU, then 64 -> 2 on the CUDA cores;
+//   decisions and window records as the FIR receiver.
+// GELU uses erf from the Abramowitz-Stegun rational approximation 7.1.25
+// (|error| <= 2.5e-5), well below the BF16 rounding of the activations (2^-9).
+constexpr int kTS = 256;
+constexpr int kP0 = 2 * kTS + 24, kP1 = kP0 - 8, kP2 = kP1 - 8, kP3 = kP2 - 8;   // 536 528 520 512
+constexpr int kMT2 = (kP2 + 127) / 128, kMT3 = kP3 / 128;                     // 5, 4
+constexpr int kR1 = 128 * kMT2 + 8;          // rows of the h1 / h3 planes (rows >= kP1 stay zero)
+constexpr int kR2 = kP2 + 8;                 // rows of the h2 planes
+constexpr int kRxThreads = 512;
+constexpr uint32_t kRxTmem = 256;
+struct RxSmem {
+    static constexpr int W2 = 0;                          // bf16 planes [36][32 rows][16 B]
+    static constexpr int W3 = W2 + 36 * 512;
+    static constexpr int M1 = W3 + 36 * 512;              // bf16 planes [4][64 rows][16 B]
+    static constexpr int H1 = M1 + 4 * 1024;              // bf16 planes [4][kR1][16 B] (h1, then h3)
+    static constexpr int H2 = H1 + 4 * kR1 * 16;          // bf16 planes [4][kR2][16 B]
+    static constexpr int A1 = H2 + 4 * kR2 * 16;          // fp16 im2col planes [4][kRA][16 B]
+    static constexpr int B1 = A1 + 4 * 640 * 16;          // fp16 planes [4][32 rows][16 B]
+    static constexpr int X = B1 + 4 * 512;                // float2 [kP0]
+    static constexpr int PRM = X + ((kP0 * 8 + 127) & ~127);   // W1 [32][18] | b1 b2 b3 [96] | c1 [64] | M2 [128] | c2 [2]
+    static constexpr int PART = PRM + 4096;               // float [kTS][4 column quarters][2]
+    static constexpr int OS = PART + kTS * 32;            // float [kTS][2]
+    static constexpr int BAR = OS + kTS * 8;              // mbarrier, TMEM slot
+    static constexpr int TOTAL = BAR + 64;
+};
+static_assert(RxSmem::TOTAL <= 227 * 1024, "receiver CNN shared memory");
+
+__device__ __forceinline__ float erf_as(float x)
 {
-    CnnSave sv;
-    memset(&sv, 0, sizeof sv);
-    // the shared-memory attribute of k_cnn_fwd was set by rx_cnn_create on this device
-    k_cnn_fwd<<<nseg, kCnnThreads, FwdSmem::TOTAL, st>>>(prm, (const __nv_bfloat16 *)prm_bf, y, nullptr, seg_base,
-                                                        2 * CS, nullptr, sv, dec, winb, winrec, prbs_bits, k_first,
-                                                        scale, mq);
+    // Abramowitz & Stegun 7.1.25: erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3) exp(-x^2), t = 1 / (1 + p x), x >= 0
+    float ax = fabsf(x);
+    float t = __fdividef(1.0f, fmaf(0.47047f, ax, 1.0f));
+    float poly = fmaf(fmaf(0.7478556f, t, -0.0958798f), t, 0.3480242f) * t;
+    float r = 1.0f - poly * __expf(-ax * ax);
+    return copysignf(r, x);
+}
+__device__ __forceinline__ float gelu_rx(float u) { return 0.5f * u * (1.0f + erf_as(u * 0.70710678118654752f)); }
+
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__global__ void __launch_bounds__(kRxThreads, 1)
+    k_cnn_rx_tc(const float *__restrict__ prm, const __nv_bfloat16 *__restrict__ prm_bf, const float2 *__restrict__ y,
+                long long seg_base, long long y_end, int nwin, uint8_t *__restrict__ dec, uint8_t *__restrict__ winb,
+                uint4 *__restrict__ winrec, const uint32_t *__restrict__ prbs_bits, long long k_first, float scale,
+                int mq, float2 *__restrict__ soft, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sW2 = sm + RxSmem::W2, *sW3 = sm + RxSmem::W3, *sM1 = sm + RxSmem::M1;
+    unsigned char *sH1 = sm + RxSmem::H1, *sH2 = sm + RxSmem::H2, *sA1 = sm + RxSmem::A1, *sB1 = sm + RxSmem::B1;
+    float2 *xs = reinterpret_cast<float2 *>(sm + RxSmem::X);
+    float *w1 = reinterpret_cast<float *>(sm + RxSmem::PRM);
+    float *bb = w1 + CC * 18;
+    float *c1 = bb + 3 * CC;
+    float *m2 = c1 + CH;                         // [2][64] then c2 [2]
+    float *part = reinterpret_cast<float *>(sm + RxSmem::PART);
+    float *os = reinterpret_cast<float *>(sm + RxSmem::OS);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + RxSmem::BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quarter = warp & 3, cq = warp >> 2;
+    constexpr int PL1 = kR1 * 16, PL2 = kR2 * 16, PLA = 640 * 16;
+
+    if (tid == 0) mbar_init(bar, 1);
+    __syncwarp();
+    if (warp == 0) tmem_alloc(tslot, kRxTmem);
+    // weights: B operands as K-major planes (chunk (row n, K column kk) at kk * rows * 16 + n * 16)
+    for (int u = tid; u < 36 * 32; u += kRxThreads) {
+        int n = u & 31, kk = u >> 5;
+        *reinterpret_cast<uint4 *>(sW2 + kk * 512 + n * 16) =
+            *reinterpret_cast<const uint4 *>(prm_bf + OW2 + n * KW + 8 * kk);
+        *reinterpret_cast<uint4 *>(sW3 + kk * 512 + n * 16) =
+            *reinterpret_cast<const uint4 *>(prm_bf + OW3 + n * KW + 8 * kk);
+    }
+    for (int u = tid; u < 4 * CH; u += kRxThreads) {
+        int n = u & 63, kk = u >> 6;
+        *reinterpret_cast<uint4 *>(sM1 + kk * 1024 + n * 16) = *reinterpret_cast<const uint4 *>(prm_bf + OM1 + n * CC + 8 * kk);
+    }
+    for (int i = tid; i < CC * 18; i += kRxThreads) w1[i] = prm[OW1 + i];
+    for (int u = tid; u < 4 * 32; u += kRxThreads) {   // layer-1 weights, FP16, K padded to 32
+        int n = u & 31, kk = u >> 5;
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            int k0 = 8 * kk + 2 * i;
+            float a = k0 < 18 ? prm[OW1 + n * 18 + k0] : 0.f, b = k0 + 1 < 18 ? prm[OW1 + n * 18 + k0 + 1] : 0.f;
+            __half2 h = __floats2half2_rn(a, b);
+            w[i] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(sB1 + kk * 512 + n * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    for (int i = tid; i < CC; i += kRxThreads) {
+        bb[i] = prm[OB1 + i];
+        bb[CC + i] = prm[OB2 + i];
+        bb[2 * CC + i] = prm[OB3 + i];
+    }
+    for (int i = tid; i < CH; i += kRxThreads) c1[i] = prm[OC1 + i];
+    for (int i = tid; i < 2 * CH + 2; i += kRxThreads) m2[i] = prm[OM2 + i];
+    // rows past the computed positions are read by the last row tiles: zero once
+    for (int i = tid; i < 4 * kR1; i += kRxThreads)
+        *reinterpret_cast<uint4 *>(sH1 + (i / kR1) * PL1 + (i % kR1) * 16) = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 4 * kR2; i += kRxThreads)
+        *reinterpret_cast<uint4 *>(sH2 + (i / kR2) * PL2 + (i % kR2) * 16) = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t id32 = umma_idesc(1, 128, 32), id64 = umma_idesc(1, 128, 64), id16 = umma_idesc(0, 128, 32);
+    const uint32_t aA1 = smem_u32(sA1), aB1 = smem_u32(sB1);
+    const uint32_t aH1 = smem_u32(sH1), aH2 = smem_u32(sH2), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3),
+                   aM1 = smem_u32(sM1);
+    const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's lane quarter
+    unsigned phase = 0;
+    bool ok = true;
+    const int ntiles = (nwin + 3) / 4;
+
+    // one row tile group of a convolution: 18 K-steps of the taps x channel groups
+    auto conv_mma = [&](uint32_t aH, int PL, uint32_t aW, int mtiles) {
+        for (int m = 0; m < mtiles; m++)
+            for (int ks = 0; ks < 18; ks++) {
+                uint64_t ad = umma_sdesc(aH + (128 * m + ks / 2) * 16 + 2 * (ks & 1) * PL, PL, 128);
+                uint64_t bd = umma_sdesc(aW + 2 * ks * 512, 512, 128);
+                umma_f16(tmem + 32 * m, ad, bd, id32, ks > 0);
+            }
+    };
+    auto wait_mma = [&]() -> bool {
+        bool done = mbar_wait(bar, phase);
+        if (!done) {
+            atomicExch(err, (int)RX_ETIMEOUT);
+            mbar_wait(bar, phase);
+        }
+        phase ^= 1u;
+        return __syncthreads_and(done) != 0;
+    };
+    // conv epilogue: rows of this warp's lane quarter, channel group cq (8 channels)
+    auto conv_epi = [&](int mtiles, int valid, const float *bias, unsigned char *dstH, int PLd) {
+        for (int m = 0; m < mtiles; m++) {
+            uint32_t r[8];
+            tmem_ld8(tq + 32 * m + 8 * cq, r);
+            int row = 128 * m + 32 * quarter + lane;
+            if (row < valid) {
+                uint32_t w[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    int o = 8 * cq + 2 * i;
+                    w[i] = pack_bf2(gelu_rx(__uint_as_float(r[2 * i]) + bias[o]),
+                                    gelu_rx(__uint_as_float(r[2 * i + 1]) + bias[o + 1]));
+                }
+                *reinterpret_cast<uint4 *>(dstH + cq * PLd + row * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    };
+
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const long long ib = seg_base + 2LL * kTS * t;   // first input of the tile
+        for (int i = tid; i < kP0; i += kRxThreads)
+            xs[i] = (ib + i < y_end) ? y[ib + i] : make_float2(0.f, 0.f);
+        __syncthreads();
+        // layer 1: FP16 im2col (row p, K column kk: reals 2p + 8 kk .. + 8 of the input, zero past K = 18)
+        const float *xf = reinterpret_cast<const float *>(xs);
+        for (int u = tid; u < 640 * 4; u += kRxThreads) {
+            int p = u >> 2, kk = u & 3;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (p < kP1 && kk < 3) {
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    int k0 = 8 * kk + 2 * i;
+                    float a = k0 < 18 ? xf[2 * p + k0] : 0.f, b = k0 + 1 < 18 ? xf[2 * p + k0 + 1] : 0.f;
+                    __half2 h = __floats2half2_rn(a, b);
+                    w[i] = *reinterpret_cast<uint32_t *>(&h);
+                }
+            }
+            *reinterpret_cast<uint4 *>(sA1 + kk * PLA + p * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            for (int m = 0; m < kMT2; m++)
+                for (int ks = 0; ks < 2; ks++) {
+                    uint64_t ad = umma_sdesc(aA1 + 128 * m * 16 + 2 * ks * PLA, PLA, 128);
+                    uint64_t bd = umma_sdesc(aB1 + 2 * ks * 512, 512, 128);
+                    umma_f16(tmem + 32 * m, ad, bd, id16, ks > 0);
+                }
+            umma_commit(bar);
+        }
+        if (!(ok = wait_mma())) break;
+        tc_fence_after();
+        conv_epi(kMT2, kP1, bb, sH1, PL1);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // layer 2
+        if (tid == 0) {
+            tc_fence_after();
+            conv_mma(aH1, PL1, aW2, kMT2);
+            umma_commit(bar);
+        }
+        if (!(ok = wait_mma())) break;
+        tc_fence_after();
+        conv_epi(kMT2, kP2, bb + CC, sH2, PL2);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // layer 3 (h3 overwrites h1: layer 2's MMAs have completed)
+        if (tid == 0) {
+            tc_fence_after();
+            conv_mma(aH2, PL2, aW3, kMT3);
+            umma_commit(bar);
+        }
+        if (!(ok = wait_mma())) break;
+        tc_fence_after();
+        conv_epi(kMT3, kP3, bb + 2 * CC, sH1, PL1);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // MLP 32 -> 64 at every position (M = 128, N = 64, K = 32)
+        if (tid == 0) {
+            tc_fence_after();
+            for (int m = 0; m < kMT3; m++)
+                for (int ks = 0; ks < 2; ks++) {
+                    uint64_t ad = umma_sdesc(aH1 + 128 * m * 16 + 2 * ks * PL1, PL1, 128);
+                    uint64_t bd = umma_sdesc(aM1 + 2 * ks * 1024, 1024, 128);
+                    umma_f16(tmem + 64 * m, ad, bd, id64, ks > 0);
+                }
+            umma_commit(bar);
+        }
+        if (!(ok = wait_mma())) break;
+        tc_fence_after();
+        for (int m = 0; m < kMT3; m++) {
+            uint32_t r[16];
+            tmem_ld16(tq + 64 * m + 16 * cq, r);
+            int row = 128 * m + 32 * quarter + lane;
+            if (!(row & 1)) {
+                float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    int hu = 16 * cq + i;
+                    float z = gelu_rx(__uint_as_float(r[i]) + c1[hu]);
+                    o0 = fmaf(m2[hu], z, o0);
+                    o1 = fmaf(m2[CH + hu], z, o1);
+                }
+                part[(row >> 1) * 8 + 2 * cq] = o0;
+                part[(row >> 1) * 8 + 2 * cq + 1] = o1;
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        for (int j = tid; j < kTS; j += kRxThreads) {
+            const float *pj = part + 8 * j;
+            float o0 = ((pj[0] + pj[2]) + (pj[4] + pj[6])) + m2[2 * CH];
+            float o1 = ((pj[1] + pj[3]) + (pj[5] + pj[7])) + m2[2 * CH + 1];
+            os[2 * j] = o0;
+            os[2 * j + 1] = o1;
+            long long ks = (long long)kTS * t + j;
+            if (soft && ks < 64LL * nwin) soft[ks] = make_float2(o0, o1);
+        }
+        __syncthreads();
+        // decisions and window records: warp w < 4 takes window 4 t + w
+        if (warp < 4 && 4 * t + warp < nwin) {
+            const int s = 4 * t + warp;
+            const float *osw = os + 2 * 64 * warp;
+            const int NB = mq == 2 ? 1 : 2, BPS = 2 * NB;
+            long long k0 = k_first + (long long)s * CS;
+            int pwin = (int)(((long long)BPS * k0) % 32767);
+            unsigned eA = 0, eB = 0, se = 0, nn = 0;
+            for (int h = 0; h < 2; h++) {
+                int q = lane + 32 * h;
+                float vr = scale * osw[2 * q], vi = scale * osw[2 * q + 1];
+                int LI = 0, LQ = 0;
+                bool nr = false;
+                for (int jj = 0; jj < mq - 1; jj++) {
+                    float th = (float)(2 * jj - (mq - 2));
+                    LI += vr >= th;
+                    LQ += vi >= th;
+                    nr |= fabsf(vr - th) < 1e-4f || fabsf(vi - th) < 1e-4f;
+                }
+                dec[(size_t)s * CS + q] = (uint8_t)(LI | (LQ << 3) | (nr ? 64 : 0));
+                int pos = pwin + BPS * q;
+                uint32_t w0 = prbs_bits[pos >> 5], w1w = prbs_bits[(pos >> 5) + 1];
+                int ref = (int)(__funnelshift_l(w1w, w0, pos & 31) >> (32 - BPS));
+                for (int rq = 0; rq < 4; rq++) {
+                    int a = LI, bq = LQ;
+                    if (rq & 2) { a = mq - 1 - a; bq = mq - 1 - bq; }
+                    if (rq & 1) { int tt = a; a = bq; bq = mq - 1 - tt; }
+                    unsigned ne = __popc((((a ^ (a >> 1)) << NB) | (bq ^ (bq >> 1))) ^ ref);
+                    if (rq < 2) eA += ne << (16 * rq);
+                    else eB += ne << (16 * (rq - 2));
+                    se += (ne > 0) << (8 * rq);
+                }
+                nn += nr;
+            }
+            eA = warp_sum_i(eA);
+            eB = warp_sum_i(eB);
+            se = warp_sum_i(se);
+            nn = warp_sum_i(nn);
+            if (lane == 0) {
+                winb[s] = 0;
+                winrec[s] = make_uint4(eA, eB, se, nn << 8);
+            }
+        }
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kRxTmem);
+}
+
+cudaError_t prepare_cnn_rx()
+{
+    return cudaFuncSetAttribute(k_cnn_rx_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, RxSmem::TOTAL);
+}
+
+cudaError_t launch_cnn_decide(const float *prm, const void *prm_bf, const float2 *y, long long seg_base, long long y_end,
+                              int nwin, uint8_t *dec, uint8_t *winb, uint4 *winrec, const uint32_t *prbs_bits,
+                              long long k_first, float scale, int mq, float2 *soft, int *err, int nsm, cudaStream_t st)
+{
+    if (nwin <= 0) return cudaSuccess;
+    int ntiles = (nwin + 3) / 4;
+    unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
+    k_cnn_rx_tc<<<grid, kRxThreads, RxSmem::TOTAL, st>>>(prm, (const __nv_bfloat16 *)prm_bf, y, seg_base, y_end, nwin,
+                                                        dec, winb, winrec, prbs_bits, k_first, scale, mq, soft, err);
     return cudaGetLastError();
 }
 

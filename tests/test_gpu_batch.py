@@ -150,3 +150,11 @@ def test_handles_with_different_cta_shapes_coexist():
     s8, s2 = r8.stats(), r2.stats()
     assert s8["bits"] == s2["bits"] > 0 and s8["bit_errors"] == s2["bit_errors"]
     assert s8["device_error"] == 0 and s2["device_error"] == 0
+
+
+def test_full_size_batch_equals_sequential():
+    """The bench's launch configuration: 2^22-sample KK-16QAM buffers through the
+    two-stream pipeline, against one call per buffer."""
+    nb = 1 << 22
+    g = make_stream(4, nb, 4, seed=19, workers=8)
+    same(batched(4, nb, g["packed"], [4]), sequential(4, nb, g["packed"]))

@@ -103,3 +103,72 @@ def test_trained_cnn_beats_the_adaptive_fir():
     print("BER lms", sl["ber"], "cnn", sn["ber"], "losses", losses)
     assert sl["bits"] == sn["bits"] > 0
     assert sn["ber"] < sl["ber"], (sn["ber"], sl["ber"])
+
+
+def test_cnn_receiver_soft_matches_training_forward():
+    """The receiver's tensor-core inference (tcgen05, row-shifted activation
+    planes, 256-symbol tiles) against the training forward (mma.sync, 64-symbol
+    segments) on the same 2-sps samples, with random weights."""
+    nb = 1 << 19
+    g = synth.gen_kk_stream(4, nb, 2, seed=23, truth=False, **VOLT)
+    p = cnn.init_params(11).astype(np.float32)
+    p += np.random.default_rng(12).standard_normal(len(p)).astype(np.float32) * 0.02
+    c = rx.rx_cnn_create(64)
+    try:
+        rx.rx_cnn_set_params(c, p)
+        r = rx.Receiver(4, nb, debug=1)
+        rx.rx_set_cnn(r.h, c)
+        for b in range(2):
+            r.process(torch.from_numpy(g["packed"][b]).cuda())
+        soft, s0 = r.debug(rx.RX_DBG_SOFT)
+        y, y0 = r.debug(rx.RX_DBG_MF)
+        assert len(soft) > 0
+        # windows well inside the call, whose inputs lie in the MF view
+        ks = [k for k in range(s0 + 64 * 20, s0 + len(soft) - 64 * 20, 64 * 37)][:24]
+        seg = [2 * k - 12 - y0 for k in ks]
+        assert min(seg) >= 0 and max(seg) + L0 <= len(y)
+        yd = torch.view_as_real(torch.from_numpy(y.astype(np.complex64)).cuda()).contiguous()
+        sd = torch.from_numpy(np.asarray(seg, dtype=np.int64)).cuda()
+        out = torch.zeros(len(seg) * S * 2, dtype=torch.float32, device="cuda")
+        rx.rx_cnn_forward(c, yd.data_ptr(), sd.data_ptr(), len(seg), out.data_ptr())
+        torch.cuda.synchronize()
+        ref = out.cpu().numpy().reshape(len(seg), S, 2)
+        ref = ref[..., 0] + 1j * ref[..., 1]
+        got = np.stack([soft[k - s0: k - s0 + S] for k in ks])
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert rel < 1e-2, rel
+    finally:
+        rx.rx_cnn_destroy(c)
+
+
+def test_cnn_receiver_pass_through_closed_form():
+    """Identity-like weights: the receiver's soft symbol is GELU^4 of the 2-sps
+    sample at the symbol position (channel-wise), computed here from its MF view."""
+    nb = 1 << 19
+    g = synth.gen_kk_stream(4, nb, 2, seed=24, truth=False)
+    p = np.zeros(rx.rx_cnn_nparams(), dtype=np.float32)
+    sl = oracle.cnn_param_slices()
+    for name, cin in (("W1", 2), ("W2", 32), ("W3", 32)):
+        W = p[sl[name][0]:sl[name][0] + 32 * 9 * cin].reshape(32, 9, cin)
+        W[0, 4, 0] = W[1, 4, 1] = 1.0
+    p[sl["M1"][0] + 0 * 32 + 0] = p[sl["M1"][0] + 1 * 32 + 1] = 1.0
+    p[sl["M2"][0] + 0 * 64 + 0] = p[sl["M2"][0] + 1 * 64 + 1] = 1.0
+    c = rx.rx_cnn_create(8)
+    try:
+        rx.rx_cnn_set_params(c, p)
+        r = rx.Receiver(4, nb, debug=1)
+        rx.rx_set_cnn(r.h, c)
+        for b in range(2):
+            r.process(torch.from_numpy(g["packed"][b]).cuda())
+        soft, s0 = r.debug(rx.RX_DBG_SOFT)
+        y, y0 = r.debug(rx.RX_DBG_MF)
+        k = np.arange(s0 + 64, s0 + len(soft) - 64)
+        k = k[(2 * k - y0 >= 0) & (2 * k - y0 < len(y))]
+        gl = lambda u: 0.5 * u * (1 + erf(u / math.sqrt(2)))
+        v = y[2 * k - y0]
+        ref = gl(gl(gl(gl(v.real)))) + 1j * gl(gl(gl(gl(v.imag))))
+        got = soft[k - s0]
+        # BF16 activations: relative rounding 2^-9 per layer
+        assert np.max(np.abs(got - ref)) < 2e-2 * max(1.0, np.max(np.abs(ref)))
+    finally:
+        rx.rx_cnn_destroy(c)
