@@ -175,7 +175,7 @@ def gpu_arm(args, rank, world, local):
                             workers=min(16, os.cpu_count() or 1), **GEN)
     t_gen = time.perf_counter() - t_gen
     ring = [torch.from_numpy(p).cuda() for p in g["packed"]]
-    r = rx.Receiver(FMT, NB)
+    r = rx.Receiver(FMT, NB, eq_warps=args.eq_warps)
     stream = torch.cuda.current_stream()
 
     # one step = one pipelined call over bufs_per_step consecutive buffers of the ring
@@ -224,7 +224,9 @@ def gpu_arm(args, rank, world, local):
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     host_ring = [torch.from_numpy(p).pin_memory() for p in g["packed"]]
-    h2 = rx.rx_create(FMT, BAUD, FS, NB, rx.rx_default_config(FMT))
+    c2 = rx.rx_default_config(FMT)
+    c2.eq_warps = args.eq_warps
+    h2 = rx.rx_create(FMT, BAUD, FS, NB, c2)
     out_host = [torch.zeros(rx.rx_max_bits(h2) // 8 + 16, dtype=torch.uint8).pin_memory()
                 for _ in range(args.bufs_per_step)]
     hout_ptrs = [t.data_ptr() for t in out_host]
@@ -648,6 +650,7 @@ def main():
     ap.add_argument("--batched-streams", type=int, default=64)
     ap.add_argument("--batched-rounds", type=int, default=10)
     ap.add_argument("--latency-reps", type=int, default=300)
+    ap.add_argument("--eq-warps", type=int, default=0, help="equaliser blocks per CTA (0: library default)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

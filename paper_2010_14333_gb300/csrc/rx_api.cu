@@ -72,7 +72,6 @@ struct rx_handle {
     DevState *st;
     uint8_t *in_stage[2], *bits_stage;   // device staging of the host-buffer entry points
     float2 *zbuf;                   // payload soft symbols of the tensor-core FIR forms
-    long long *uprefix;             // unwrap counter per 16-window group of the demap
     long long dec_cap, win_cap, y_cap;
     int nsm;                        // SMs of the handle's device
     // stage timing: a ring of event sets, one per profiled call
@@ -258,7 +257,7 @@ void rx_destroy(rx_handle *h)
                     h->winrec[0], h->winrec[1], h->winrec[2], h->prbs, h->taps[0], h->taps[1], h->twN, h->twN2,
                     h->ds_tab,
                     h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1], h->bits_stage, h->lnt, h->sqt,
-                    h->prbs_bits, h->phist[0], h->phist[1], h->zbuf, h->uprefix};
+                    h->prbs_bits, h->phist[0], h->phist[1], h->zbuf};
     static_assert(kSlots == 3, "slot arrays listed above");
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -406,7 +405,6 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         RX_ALLOC(h->ds_tab, c.ds_den * sizeof(float2));
     }
     RX_ALLOC(h->prbs, 32767 + 256);
-    RX_ALLOC(h->uprefix, (h->win_cap / 16 + 16) * sizeof(long long));
     RX_ALLOC(h->prbs_bits, 1040 * sizeof(uint32_t));
     RX_ALLOC(h->rrc, (2 * h->hmf + 1) * sizeof(float));
     RX_ALLOC(h->st, sizeof(DevState));
@@ -659,7 +657,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     if (e == cudaSuccess && g.nblk > 0) {
         prof_begin(h, 6, sb);
         int resolve = h->kk && !h->amb_done;
-        e = launch_demap(h->ep, g, resolve, h->uw, h->dec[ds], h->winb[ds], h->winrec[ds], h->dbg_win, bits_out, h->uprefix,
+        e = launch_demap(h->ep, g, resolve, h->uw, h->dec[ds], h->winb[ds], h->winrec[ds], h->dbg_win, bits_out,
                          h->st, sb);
         if (h->kk) h->uw ^= 1;
         h->amb_done = 1;

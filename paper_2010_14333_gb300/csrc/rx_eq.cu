@@ -108,42 +108,44 @@ __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys
     constexpr int TH = (NT - 1) / 2;
     constexpr int NP = (NT + 1) / 2;              // y pairs per symbol
     static_assert(TH % 2 == 1, "tap half-length must be odd");
-    // taps to registers (ws holds NT+1 entries, the last one zero)
-    float2 w[2 * NP];
+    // filter: z_k = sum_i conj(w_i) y[2k + TH - i]; pairs start at the even index 2k - TH - 1.
+    // The tap pair (w[NT-1-2v], w[NT-2v]) is one 16-byte shared-memory broadcast
+    // (ws holds NT+1 entries, the last one zero), shared by the lane's two symbols.
+    if (FRZ && zin) {   // soft symbols from the block-Toeplitz kernel
 #pragma unroll
-    for (int i = 0; i < NP; i++) {
-        float4 t = reinterpret_cast<const float4 *>(ws)[i];
-        w[2 * i] = make_float2(t.x, t.y);
-        w[2 * i + 1] = make_float2(t.z, t.w);
-    }
-    // filter: z_k = sum_i conj(w_i) y[2k + TH - i]; pairs start at the even index 2k - TH - 1
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        int q = lane + 32 * h;
-        if (FRZ && zin) {   // soft symbols from the block-Toeplitz kernel
+        for (int h = 0; h < 2; h++) {
+            int q = lane + 32 * h;
             float2 zq = zin[q];
             zs[q] = zq;
             if (dbg_z) dbg_z[q] = zq;
-            continue;
         }
-        const float4 *yp = reinterpret_cast<const float4 *>(ys + c0 + 2 * q - TH - 1);
-        float ar = 0.f, ai = 0.f;
+    } else {
+        const float4 *yp0 = reinterpret_cast<const float4 *>(ys + c0 + 2 * lane - TH - 1);
+        const float4 *yp1 = reinterpret_cast<const float4 *>(ys + c0 + 2 * (lane + 32) - TH - 1);
+        const float4 *wp = reinterpret_cast<const float4 *>(ws);
+        float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
 #pragma unroll
         for (int v = 0; v < NP; v++) {
-            float4 Y = yp[v];
-            {   // offset 2v+1 -> tap NT-1-2v
-                const float2 wv = w[NT - 1 - 2 * v];
-                ar = fmaf(wv.x, Y.z, fmaf(wv.y, Y.w, ar));
-                ai = fmaf(wv.x, Y.w, fmaf(-wv.y, Y.z, ai));
-            }
+            const float4 W = wp[(NT - 1 - 2 * v) / 2];
+            const float4 Y0 = yp0[v], Y1 = yp1[v];
+            // offset 2v+1 -> tap NT-1-2v
+            ar0 = fmaf(W.x, Y0.z, fmaf(W.y, Y0.w, ar0));
+            ai0 = fmaf(W.x, Y0.w, fmaf(-W.y, Y0.z, ai0));
+            ar1 = fmaf(W.x, Y1.z, fmaf(W.y, Y1.w, ar1));
+            ai1 = fmaf(W.x, Y1.w, fmaf(-W.y, Y1.z, ai1));
             if (v >= 1) {   // offset 2v -> tap NT-2v
-                const float2 wv = w[NT - 2 * v];
-                ar = fmaf(wv.x, Y.x, fmaf(wv.y, Y.y, ar));
-                ai = fmaf(wv.x, Y.y, fmaf(-wv.y, Y.x, ai));
+                ar0 = fmaf(W.z, Y0.x, fmaf(W.w, Y0.y, ar0));
+                ai0 = fmaf(W.z, Y0.y, fmaf(-W.w, Y0.x, ai0));
+                ar1 = fmaf(W.z, Y1.x, fmaf(W.w, Y1.y, ar1));
+                ai1 = fmaf(W.z, Y1.y, fmaf(-W.w, Y1.x, ai1));
             }
         }
-        zs[q] = make_float2(ar, ai);
-        if (dbg_z) dbg_z[q] = make_float2(ar, ai);
+        zs[lane] = make_float2(ar0, ai0);
+        zs[lane + 32] = make_float2(ar1, ai1);
+        if (dbg_z) {
+            dbg_z[lane] = make_float2(ar0, ai0);
+            dbg_z[lane + 32] = make_float2(ar1, ai1);
+        }
     }
     __syncwarp();
     WinOut R;
@@ -569,7 +571,7 @@ template <bool QAM, int BPS, int MQ>
 __global__ void __launch_bounds__(kDemapThreads)
     k_demap(EqParams p, EqGeom g, int resolve_amb, int uw_in, const uint8_t *__restrict__ dec,
             const uint8_t *__restrict__ winb, const uint4 *__restrict__ winrec, float4 *__restrict__ dbg_win,
-            uint8_t *__restrict__ bits_out, const long long *__restrict__ prefix, DevState *dst)
+            uint8_t *__restrict__ bits_out, DevState *dst)
 {
     constexpr int NW = kDemapThreads / 32;
     constexpr int NB = QAM ? BPS / 2 : BPS;
@@ -585,8 +587,27 @@ __global__ void __launch_bounds__(kDemapThreads)
     if (QAM) {
         int have = dst->unwrap_have[uw_in];
         int blast = dst->unwrap_b[uw_in];
-        // unwrap counter before this CTA's first window (k_unwrap_scan)
-        const long long pre = prefix[blockIdx.x];
+        long long mstart = have ? dst->unwrap_m[uw_in] : 0;
+        // prefix of increments over windows [0, w0), 16 windows per load
+        int part = 0;
+        for (int c = tid; c < w0 / 16; c += kDemapThreads) {
+            uint4 v = *reinterpret_cast<const uint4 *>(winb + 16 * c);
+            uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+            int prev = (c == 0) ? blast : winb[16 * c - 1];
+            bool use_first = (c > 0) || have;
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                int b = (wd[i >> 2] >> (8 * (i & 3))) & 0xFF;
+                if (i > 0 || use_first) part += unwrap_inc(prev, b, p.bps_b);
+                prev = b;
+            }
+        }
+        part = warp_sum_i(part);
+        if (lane == 0) s_red[wid] = part;
+        __syncthreads();
+        long long pre = 0;
+#pragma unroll
+        for (int i = 0; i < NW; i++) pre += s_red[i];
         if (tid < 32) {   // inclusive scan of this CTA's increments
             int inc = 0;
             if (tid < kDemapWin && w0 + tid < wend) {
@@ -599,7 +620,7 @@ __global__ void __launch_bounds__(kDemapThreads)
                 int v = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += v;
             }
-            if (tid < kDemapWin) s_m[tid] = pre + inc;
+            if (tid < kDemapWin) s_m[tid] = mstart + pre + inc;
         }
         if (resolve_amb) {
             // stream-start pi/2 ambiguity from the first amb_syms payload symbols:
@@ -703,74 +724,14 @@ __global__ void __launch_bounds__(kDemapThreads)
     }
 }
 
-// Unwrap counter at the start of every k_demap CTA: the carried counter plus the
-// sum of the integer increments of all earlier windows of the call.  One CTA;
-// thread t sums the increments of its run of consecutive 16-window groups, a
-// block-wide exclusive scan of those sums gives each run's start, and the thread
-// writes the start of each of its groups.
-constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads)
-    k_unwrap_scan(int bps_b, int nwin, int uw_in, const uint8_t *__restrict__ winb, long long *__restrict__ prefix,
-                  const DevState *dst)
-{
-    __shared__ long long s_w[kScanThreads / 32];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int have = dst->unwrap_have[uw_in], blast = dst->unwrap_b[uw_in];
-    const long long mstart = have ? dst->unwrap_m[uw_in] : 0;
-    const int ngroups = (nwin + kDemapWin - 1) / kDemapWin;
-    const int per = (ngroups + kScanThreads - 1) / kScanThreads;
-    const int g0 = min(t * per, ngroups), g1 = min(g0 + per, ngroups);
-    auto group_sum = [&](int gi) {
-        int s = 0;
-        for (int i = 0; i < kDemapWin; i++) {
-            int w = gi * kDemapWin + i;
-            if (w >= nwin) break;
-            int bp = (w == 0) ? blast : winb[w - 1];
-            if (w > 0 || have) s += unwrap_inc(bp, winb[w], bps_b);
-        }
-        return s;
-    };
-    long long local = 0;
-    for (int gi = g0; gi < g1; gi++) local += group_sum(gi);
-    // exclusive block scan of the per-thread sums
-    long long v = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        long long u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    if (lane == 31) s_w[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        long long x = s_w[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            long long u = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += u;
-        }
-        s_w[lane] = x;   // inclusive over warps
-    }
-    __syncthreads();
-    long long run = mstart + (wid ? s_w[wid - 1] : 0) + (v - local);
-    for (int gi = g0; gi < g1; gi++) {
-        prefix[gi] = run;
-        run += group_sum(gi);
-    }
-}
-
 cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in, const uint8_t *dec,
                          const uint8_t *winb, const uint4 *winrec, float4 *dbg_win, uint8_t *bits_out,
-                         long long *prefix, DevState *dst, cudaStream_t st)
+                         DevState *dst, cudaStream_t st)
 {
     unsigned grid = (unsigned)((g.nwin + kDemapWin - 1) / kDemapWin);
-    if (p.kk) {
-        k_unwrap_scan<<<1, kScanThreads, 0, st>>>(p.bps_b, g.nwin, uw_in, winb, prefix, dst);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
 #define RX_DEMAP(Q, B, M)                                                                                   \
     k_demap<Q, B, M><<<grid, kDemapThreads, 0, st>>>(p, g, resolve_amb, uw_in, dec, winb, winrec, dbg_win,  \
-                                                     bits_out, prefix, dst)
+                                                     bits_out, dst)
     if (p.kk && p.mq == 4) RX_DEMAP(true, 4, 4);
     else if (p.kk) RX_DEMAP(true, 2, 2);
     else if (p.mq == 2) RX_DEMAP(false, 1, 2);

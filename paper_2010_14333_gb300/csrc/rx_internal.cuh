@@ -144,11 +144,9 @@ constexpr size_t kMaxSmemCta = 227 * 1024;
 cudaError_t prepare_fir_tc(int prec);
 cudaError_t prepare_kk_front();
 
-// prefix: scratch of (nwin + 15) / 16 counters (the unwrap counter at each
-// 16-window group), written by a one-CTA scan before the demap (KK)
 cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in,
                          const uint8_t *dec, const uint8_t *winb, const uint4 *winrec, float4 *dbg_win,
-                         uint8_t *bits_out, long long *prefix, DevState *dst, cudaStream_t st);
+                         uint8_t *bits_out, DevState *dst, cudaStream_t st);
 
 // CNN decisions for nseg consecutive payload windows (receiver mode)
 // CNN receiver on the tensor cores: soft symbols and decisions of nwin 64-symbol
