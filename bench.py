@@ -154,6 +154,20 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def replica_throughput(ms_local, units_per_rank, dist=None, device="cpu"):
+    """Replicas only: every rank runs its own stream; the job's time is the slowest
+    rank's and its throughput is all ranks' units over that time (units per s)."""
+    import torch
+    world = 1
+    ms = ms_local
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * world / (ms * 1e-3)
+
+
 # --------------------------------------------------------------------- GPU arm
 def gpu_arm(args, rank, world, local):
     import torch
@@ -214,12 +228,8 @@ def gpu_arm(args, rank, world, local):
     rx.rx_profile(r.h, False)
     time.sleep(0.1)
     clocks.stop()
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    samples = args.steps * args.bufs_per_step * NB * world
-    value = samples / (ms * 1e-3) / 1e9
+    ms, value = replica_throughput(ms, args.steps * args.bufs_per_step * NB, dist, "cuda")
+    value /= 1e9
     stats = r.stats()
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
@@ -250,12 +260,9 @@ def gpu_arm(args, rank, world, local):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     barrier()
-    if dist:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms, e2e_value = replica_throughput(e2e_ms, e2e_steps * args.bufs_per_step * NB, dist, "cuda")
+    e2e_value /= 1e9
     rx.rx_destroy(h2)
-    e2e_value = e2e_steps * args.bufs_per_step * NB * world / (e2e_ms * 1e-3) / 1e9
 
     # ---- per-buffer latency, one buffer in flight at a time (the paper's budget:
     # five streams of 2^22 samples within 5 * 2^22 / 4 GS/s = 5.243 ms; one buffer
