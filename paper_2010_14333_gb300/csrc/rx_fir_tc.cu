@@ -37,7 +37,7 @@ constexpr int kRowSyms = 16;                       // symbols per GEMM row
 constexpr int kTileRows = 128;                     // M of one MMA
 constexpr int kN = 2 * kRowSyms;                   // real outputs per row
 constexpr int kKP = 128;                           // padded K (2 * (30 + NT) <= 122)
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;            // 8 warps: (row quarter, K / column half)
 constexpr int kStage = 2 * kRowSyms * kTileRows + 64;   // staged complex inputs per tile
 constexpr int kOutPitch = kN + 4;                  // floats per row of the output transpose
 constexpr uint32_t kTmemCols = 32;
@@ -48,8 +48,8 @@ constexpr int kOffStage = kOffB + kN * kKP * 2;      // + 8 KB
 constexpr int kStageBytes = kStage * 8;
 constexpr int kOffMisc = kOffStage + 2 * kStageBytes;
 // misc: 3 mbarriers + TMEM slot (64 B) | per-row maxima (128 floats) | scale exponents (128 ints)
-constexpr int kOffRmax = kOffMisc + 64;
-constexpr int kOffExp = kOffRmax + kTileRows * 4;
+constexpr int kOffRmax = kOffMisc + 64;                 // float [2 halves][128 rows]
+constexpr int kOffExp = kOffRmax + 2 * kTileRows * 4;
 constexpr int kSmem = kOffExp + kTileRows * 4;
 static_assert(kTileRows * kOutPitch * 4 <= kStageBytes, "output transpose fits a stage buffer");
 static_assert(kSmem <= 113 * 1024, "two CTAs per SM");
@@ -132,9 +132,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sm + kOffMisc);   // [2]
     uint64_t *bar_mma = bar_ld + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_ld + 3);
-    float *s_rmax = reinterpret_cast<float *>(sm + kOffRmax);          // [128]
+    float *s_rmax = reinterpret_cast<float *>(sm + kOffRmax);          // [2][128]
     int *s_exp = reinterpret_cast<int *>(sm + kOffExp);                // [<= 128]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quarter = warp & 3, half = warp >> 2;
     const int th = (ntaps - 1) / 2;
     const int ns = 2 * kRowSyms - 2 + ntaps;       // complex inputs per row
     const int ntiles = (nrows + kTileRows - 1) / kTileRows;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const uint32_t idesc = umma_idesc(Fmt<PREC>::code, kTileRows, kN);
 
     // lane -> (row r_lo, K column p_lo) of an 8 x 4 group; a warp's groups cover
-    // its own 32 rows (r_hi = 4 warp .. 4 warp + 3) and every K column
+    // the 32 rows of its lane quarter and half of the K columns
     const int r_lo = lane & 7, p_lo = lane >> 3, rot = r_lo % F2;
     bool ok = true;
     int it = 0;
@@ -244,10 +244,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             // per-row largest input magnitude, then per scale block
 #pragma unroll 1
             for (int rh = 0; rh < 4; rh++) {
-                int r = 32 * warp + 8 * rh + r_lo;
+                int r = 32 * quarter + 8 * rh + r_lo;
                 float m = 0.f;
 #pragma unroll 1
-                for (int ph = 0; ph < PLANES / 4; ph++) {
+                for (int ph = half * (PLANES / 8); ph < (half + 1) * (PLANES / 8); ph++) {
                     float v[16];
                     load_unit(r, 4 * ph + p_lo, v);
 #pragma unroll
@@ -255,12 +255,13 @@ __global__ void __launch_bounds__(kThreads, 2)
                 }
                 m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
                 m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
-                if (p_lo == 0) s_rmax[r] = m;
+                if (p_lo == 0) s_rmax[half * kTileRows + r] = m;
             }
             __syncthreads();
             if (tid < kTileRows / rows_per_scale) {
                 float bm = 0.f;
-                for (int r = tid * rows_per_scale; r < (tid + 1) * rows_per_scale; r++) bm = fmaxf(bm, s_rmax[r]);
+                for (int r = tid * rows_per_scale; r < (tid + 1) * rows_per_scale; r++)
+                    bm = fmaxf(bm, fmaxf(s_rmax[r], s_rmax[kTileRows + r]));
                 s_exp[tid] = fp8_exp(bm);
             }
             __syncthreads();
@@ -268,10 +269,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         // A: row r, K index k -> staged float 2 (shift + 32 r) + k for k < 2 ns, else 0
 #pragma unroll 1
         for (int rh = 0; rh < 4; rh++) {
-            int r = 32 * warp + 8 * rh + r_lo;
+            int r = 32 * quarter + 8 * rh + r_lo;
             float sAv = PREC == RX_FIR_FP8 ? ldexpf(1.f, s_exp[r / rows_per_scale]) : 1.f;
 #pragma unroll 2
-            for (int ph = 0; ph < PLANES / 4; ph++) {
+            for (int ph = half * (PLANES / 8); ph < (half + 1) * (PLANES / 8); ph++) {
                 int pl = 4 * ph + p_lo;
                 float v[16];
                 load_unit(r, pl, v);
@@ -300,28 +301,26 @@ __global__ void __launch_bounds__(kThreads, 2)
         ok = __syncthreads_and(done) != 0;
         if (!ok) break;
         tc_fence_after();
-        // epilogue: warp w owns accumulator lanes (= rows) 32w .. 32w+31; rows go
-        // through the consumed stage buffer to leave as contiguous 512-byte stores
+        // epilogue: warp (quarter, half) owns accumulator lanes 32 quarter .. + 31 (rows)
+        // and columns 16 half .. + 15; rows go through the consumed stage buffer to
+        // leave as contiguous 512-byte stores
         {
-            uint32_t acc[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), acc);
-            const int r = 32 * warp + lane;
+            uint32_t acc[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * half, acc);
+            const int r = 32 * quarter + lane;
             float inv = 1.f;
-            if (PREC == RX_FIR_FP8) inv = ldexpf(1.f, -(eB + s_exp[min(r, kTileRows - 1) / rows_per_scale]));
+            if (PREC == RX_FIR_FP8) inv = ldexpf(1.f, -(eB + s_exp[r / rows_per_scale]));
             float *ot = reinterpret_cast<float *>(sm + kOffStage + buf * kStageBytes);
-            __syncwarp();
 #pragma unroll
-            for (int q = 0; q < kN / 4; q++)
-                *reinterpret_cast<float4 *>(ot + r * kOutPitch + 4 * q) =
+            for (int q = 0; q < 4; q++)
+                *reinterpret_cast<float4 *>(ot + r * kOutPitch + 16 * half + 4 * q) =
                     make_float4(__uint_as_float(acc[4 * q]) * inv, __uint_as_float(acc[4 * q + 1]) * inv,
                                 __uint_as_float(acc[4 * q + 2]) * inv, __uint_as_float(acc[4 * q + 3]) * inv);
-            __syncwarp();
+            __syncthreads();
             float4 *zt = reinterpret_cast<float4 *>(z + (long long)r0 * kRowSyms);
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                int rr = 32 * warp + 4 * i + (lane >> 3), ch = lane & 7;
-                if (rr < rows)
-                    zt[rr * 8 + ch] = *reinterpret_cast<const float4 *>(ot + rr * kOutPitch + 4 * ch);
+            for (int i = tid; i < kTileRows * 8; i += kThreads) {
+                int rr = i >> 3, ch = i & 7;
+                if (rr < rows) zt[rr * 8 + ch] = *reinterpret_cast<const float4 *>(ot + rr * kOutPitch + 4 * ch);
             }
         }
         tc_fence_before();
