@@ -61,8 +61,8 @@ struct rx_handle {
     // (equaliser, demap) of buffer i runs on `back`
     // the front end runs on `front`, created at the highest priority so that its
     // cluster launches are placed ahead of the back end's CTAs
-    cudaStream_t front, back, copy;
-    cudaEvent_t ev_fork, ev_front, ev_join, ev_yfree[kSlots], ev_inready[2], ev_infree[2];
+    cudaStream_t front, mid, back, copy;   // KK: field on front, matched filter on mid
+    cudaEvent_t ev_fork, ev_front, ev_mid, ev_join, ev_yfree[kSlots], ev_efree[kSlots], ev_inready[2], ev_infree[2];
     float2 *taps[2], *twN, *twN2, *ds_tab;
     float *lnt, *sqt;
     float *rrc;
@@ -250,6 +250,7 @@ void rx_destroy(rx_handle *h)
     if (!h) return;
     // work still queued on the pipeline's own streams finishes before the memory goes
     if (h->front) cudaStreamSynchronize(h->front);
+    if (h->mid) cudaStreamSynchronize(h->mid);
     if (h->back) cudaStreamSynchronize(h->back);
     if (h->copy) cudaStreamSynchronize(h->copy);
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->E[0], h->E[1], h->E[2], h->Y[0], h->Y[1], h->Y[2],
@@ -266,10 +267,12 @@ void rx_destroy(rx_handle *h)
         free(h->prof_ev);
     }
     if (h->front) cudaStreamDestroy(h->front);
+    if (h->mid) cudaStreamDestroy(h->mid);
     if (h->back) cudaStreamDestroy(h->back);
     if (h->copy) cudaStreamDestroy(h->copy);
-    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1], &h->ev_yfree[2],
-                          &h->ev_inready[0], &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1],
+                          &h->ev_yfree[2], &h->ev_efree[0], &h->ev_efree[1], &h->ev_efree[2], &h->ev_inready[0],
+                          &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
     for (cudaEvent_t *ev : evs)
         if (*ev) cudaEventDestroy(*ev);
     free(h->prof_used);
@@ -474,10 +477,12 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         int least = 0, greatest = 0;
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
         bool ok = cudaStreamCreateWithPriority(&h->front, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+                  cudaStreamCreateWithPriority(&h->mid, cudaStreamNonBlocking, greatest) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
-        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1], &h->ev_yfree[2],
-                              &h->ev_inready[0], &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
+        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1],
+                              &h->ev_yfree[2], &h->ev_efree[0], &h->ev_efree[1], &h->ev_efree[2], &h->ev_inready[0],
+                              &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
         for (cudaEvent_t *ev : evs)
             ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) {
@@ -511,7 +516,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
 // are copied back on `sb` after the demap.
 static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out, const uint8_t *host_in,
                               uint8_t *host_out, cudaStream_t sf, cudaStream_t sb, cudaStream_t sc,
-                              int64_t *nbits_out)
+                              int64_t *nbits_out, cudaStream_t smid = nullptr)
 {
     // the launchers detect failures with cudaGetLastError: clear an error some
     // earlier, unrelated call left behind (a sticky one makes the launches fail)
@@ -526,6 +531,10 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     long long npay = (h->trained || do_train) ? s.q_k - pay_lo : 0;
     if (npay > 0 && !bits_out && !host_out) return RX_EINVAL;
     const bool two = sf != sb;
+    // KK in the pipeline: the matched filter runs on a third stream between the
+    // field (front) and the equaliser (back); field slots wait for it to be done
+    const bool three = two && h->kk && smid;
+    cudaStream_t sm = three ? smid : sf;
     cudaError_t e = cudaSuccess;
     int par = (int)(h->calls & 1);
     int ds = (int)(h->calls % kSlots);   // decision slot of this call
@@ -584,6 +593,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         int ew_new = (h->ew + 1) % kSlots;
         g.slot = ew_new;
         g.fused = c.kk_front;
+        if (three) cudaStreamWaitEvent(sf, h->ev_efree[ew_new], 0);   // the matched filter is done with this slot
         KkTables tb = {h->lnt, h->sqt, h->twN, h->twN2};
         e = traced(launch_kk_front(g, kin, h->fftws, tb, h->E[ew_new], h->E[h->ew], h->partials, h->st, sf,
                                    h->prof_cur ? h : nullptr), "KK front end");
@@ -593,27 +603,38 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         e = traced(launch_kk_hist(kin, sf), "KK history copy");
     }
     if (h->kk) h->hw ^= 1;
+    if (three) {
+        if (host_in && sc != sf) cudaEventRecord(h->ev_infree[par], sf);   // the field has read the input
+        cudaEventRecord(h->ev_front, sf);
+        cudaStreamWaitEvent(sm, h->ev_front, 0);
+    }
     // matched filter
-    prof_begin(h, 4, sf);
+    prof_begin(h, 4, sm);
     if (e == cudaSuccess && s.f_k > h->f_prev) {
         long long yb = 2 * h->q_prev - kYHist;
         int yw_new = (h->yw + 1) % kSlots;
-        if (two) cudaStreamWaitEvent(sf, h->ev_yfree[yw_new], 0);   // the back end is done with this slot
+        if (two) cudaStreamWaitEvent(sm, h->ev_yfree[yw_new], 0);   // the back end is done with this slot
         if (h->kk)
             e = launch_kk_mf(h->E[h->ew], h->ebase_cur, s.e_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
                              c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw],
-                             h->ybase_cur, sf, h->rrc_host);
+                             h->ybase_cur, sm, h->rrc_host);
         else
             e = launch_pam_mf(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->rrc, h->hmf, h->st, par,
                               (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf);
         h->yw = yw_new;
         h->ybase_cur = yb;
     }
-    prof_end(h, 4, sf);
-    if (host_in && sc != sf) cudaEventRecord(h->ev_infree[par], sf);
-    if (two) {
-        cudaEventRecord(h->ev_front, sf);
-        cudaStreamWaitEvent(sb, h->ev_front, 0);
+    prof_end(h, 4, sm);
+    if (three) {
+        cudaEventRecord(h->ev_efree[h->ew], sm);
+        cudaEventRecord(h->ev_mid, sm);
+        cudaStreamWaitEvent(sb, h->ev_mid, 0);
+    } else {
+        if (host_in && sc != sf) cudaEventRecord(h->ev_infree[par], sf);
+        if (two) {
+            cudaEventRecord(h->ev_front, sf);
+            cudaStreamWaitEvent(sb, h->ev_front, 0);
+        }
     }
     // equaliser, decisions, bits
     EqGeom g;
@@ -711,12 +732,14 @@ static rx_status run_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *con
     if (!one) {
         // everything earlier on the caller's stream precedes the pipeline
         if (cudaEventRecord(h->ev_fork, caller) != cudaSuccess || cudaStreamWaitEvent(sf, h->ev_fork, 0) != cudaSuccess ||
+            cudaStreamWaitEvent(h->mid, h->ev_fork, 0) != cudaSuccess ||
             cudaStreamWaitEvent(sb, h->ev_fork, 0) != cudaSuccess || cudaStreamWaitEvent(sc, h->ev_fork, 0) != cudaSuccess)
             return RX_ECUDA;
     }
     for (int i = 0; i < n; i++) {
-        rx_status r = host ? enqueue_call(h, nullptr, nullptr, ins[i], outs[i], sf, sb, sc, &nbits_out[i])
-                           : enqueue_call(h, ins[i], outs[i], nullptr, nullptr, sf, sb, sc, &nbits_out[i]);
+        cudaStream_t sm = one ? nullptr : h->mid;
+        rx_status r = host ? enqueue_call(h, nullptr, nullptr, ins[i], outs[i], sf, sb, sc, &nbits_out[i], sm)
+                           : enqueue_call(h, ins[i], outs[i], nullptr, nullptr, sf, sb, sc, &nbits_out[i], sm);
         if (r != RX_OK) return r;
     }
     if (!one) {
