@@ -61,8 +61,9 @@ struct rx_handle {
     // (equaliser, demap) of buffer i runs on `back`
     // the front end runs on `front`, created at the highest priority so that its
     // cluster launches are placed ahead of the back end's CTAs
-    cudaStream_t front, mid, back, copy;   // KK: field on front, matched filter on mid
-    cudaEvent_t ev_fork, ev_front, ev_mid, ev_join, ev_yfree[kSlots], ev_efree[kSlots], ev_inready[2], ev_infree[2];
+    cudaStream_t front, mid, back, tail, copy;   // KK: field | matched filter | equaliser | demap
+    cudaEvent_t ev_fork, ev_front, ev_mid, ev_eq, ev_join, ev_yfree[kSlots], ev_efree[kSlots], ev_dfree[kSlots],
+        ev_inready[2], ev_infree[2];
     float2 *taps[2], *twN, *twN2, *ds_tab;
     float *lnt, *sqt;
     float *rrc;
@@ -252,6 +253,7 @@ void rx_destroy(rx_handle *h)
     if (h->front) cudaStreamSynchronize(h->front);
     if (h->mid) cudaStreamSynchronize(h->mid);
     if (h->back) cudaStreamSynchronize(h->back);
+    if (h->tail) cudaStreamSynchronize(h->tail);
     if (h->copy) cudaStreamSynchronize(h->copy);
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->E[0], h->E[1], h->E[2], h->Y[0], h->Y[1], h->Y[2],
                     h->partials, h->dec[0], h->dec[1], h->dec[2], h->winb[0], h->winb[1], h->winb[2],
@@ -269,10 +271,12 @@ void rx_destroy(rx_handle *h)
     if (h->front) cudaStreamDestroy(h->front);
     if (h->mid) cudaStreamDestroy(h->mid);
     if (h->back) cudaStreamDestroy(h->back);
+    if (h->tail) cudaStreamDestroy(h->tail);
     if (h->copy) cudaStreamDestroy(h->copy);
-    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1],
-                          &h->ev_yfree[2], &h->ev_efree[0], &h->ev_efree[1], &h->ev_efree[2], &h->ev_inready[0],
-                          &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_yfree[0],
+                          &h->ev_yfree[1], &h->ev_yfree[2], &h->ev_efree[0], &h->ev_efree[1], &h->ev_efree[2],
+                          &h->ev_dfree[0], &h->ev_dfree[1], &h->ev_dfree[2], &h->ev_inready[0], &h->ev_inready[1],
+                          &h->ev_infree[0], &h->ev_infree[1]};
     for (cudaEvent_t *ev : evs)
         if (*ev) cudaEventDestroy(*ev);
     free(h->prof_used);
@@ -479,10 +483,12 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         bool ok = cudaStreamCreateWithPriority(&h->front, cudaStreamNonBlocking, greatest) == cudaSuccess &&
                   cudaStreamCreateWithPriority(&h->mid, cudaStreamNonBlocking, greatest) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->tail, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
-        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_join, &h->ev_yfree[0], &h->ev_yfree[1],
-                              &h->ev_yfree[2], &h->ev_efree[0], &h->ev_efree[1], &h->ev_efree[2], &h->ev_inready[0],
-                              &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
+        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_yfree[0],
+                              &h->ev_yfree[1], &h->ev_yfree[2], &h->ev_efree[0], &h->ev_efree[1], &h->ev_efree[2],
+                              &h->ev_dfree[0], &h->ev_dfree[1], &h->ev_dfree[2], &h->ev_inready[0], &h->ev_inready[1],
+                              &h->ev_infree[0], &h->ev_infree[1]};
         for (cudaEvent_t *ev : evs)
             ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) {
@@ -516,7 +522,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
 // are copied back on `sb` after the demap.
 static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out, const uint8_t *host_in,
                               uint8_t *host_out, cudaStream_t sf, cudaStream_t sb, cudaStream_t sc,
-                              int64_t *nbits_out, cudaStream_t smid = nullptr)
+                              int64_t *nbits_out, cudaStream_t smid = nullptr, cudaStream_t stail = nullptr)
 {
     // the launchers detect failures with cudaGetLastError: clear an error some
     // earlier, unrelated call left behind (a sticky one makes the launches fail)
@@ -535,6 +541,9 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     // field (front) and the equaliser (back); field slots wait for it to be done
     const bool three = two && h->kk && smid;
     cudaStream_t sm = three ? smid : sf;
+    // the demap (and the copy of the bits) on a fourth stream, after its equaliser
+    const bool four = two && stail;
+    cudaStream_t st4 = four ? stail : sb;
     cudaError_t e = cudaSuccess;
     int par = (int)(h->calls & 1);
     int ds = (int)(h->calls % kSlots);   // decision slot of this call
@@ -645,6 +654,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     g.ybase = h->ybase_cur;
     g.nblk = npay > 0 ? (int)(npay / c.eq_block) : 0;
     g.nwin = npay > 0 ? (int)(npay / kWin) : 0;
+    if (four) cudaStreamWaitEvent(sb, h->ev_dfree[ds], 0);   // the demap is done with these decision slots
     prof_begin(h, 5, sb);
     if (e == cudaSuccess && do_train) {
         e = launch_eq(h->ep, g, 1, h->Y[h->yw], nullptr, h->taps[h->tw], nullptr, h->dec[ds], h->winb[ds], h->winrec[ds],
@@ -675,18 +685,23 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     }
     prof_end(h, 5, sb);
     if (two) cudaEventRecord(h->ev_yfree[h->yw], sb);
+    if (four) {
+        cudaEventRecord(h->ev_eq, sb);
+        cudaStreamWaitEvent(st4, h->ev_eq, 0);
+    }
     if (e == cudaSuccess && g.nblk > 0) {
-        prof_begin(h, 6, sb);
+        prof_begin(h, 6, st4);
         int resolve = h->kk && !h->amb_done;
         e = launch_demap(h->ep, g, resolve, h->uw, h->dec[ds], h->winb[ds], h->winrec[ds], h->dbg_win, bits_out,
-                         h->st, sb);
+                         h->st, st4);
         if (h->kk) h->uw ^= 1;
         h->amb_done = 1;
-        prof_end(h, 6, sb);
+        prof_end(h, 6, st4);
         if (e == cudaSuccess && host_out)
             e = cudaMemcpyAsync(host_out, h->bits_stage, (size_t)((h->bps * npay + 7) / 8), cudaMemcpyDeviceToHost,
-                                sb);
+                                st4);
     }
+    if (four) cudaEventRecord(h->ev_dfree[ds], st4);
     if (h->prof_cur) h->prof_head++;
     h->prof_cur = 0;
     if (e != cudaSuccess) {
@@ -733,18 +748,20 @@ static rx_status run_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *con
         // everything earlier on the caller's stream precedes the pipeline
         if (cudaEventRecord(h->ev_fork, caller) != cudaSuccess || cudaStreamWaitEvent(sf, h->ev_fork, 0) != cudaSuccess ||
             cudaStreamWaitEvent(h->mid, h->ev_fork, 0) != cudaSuccess ||
+            cudaStreamWaitEvent(h->tail, h->ev_fork, 0) != cudaSuccess ||
             cudaStreamWaitEvent(sb, h->ev_fork, 0) != cudaSuccess || cudaStreamWaitEvent(sc, h->ev_fork, 0) != cudaSuccess)
             return RX_ECUDA;
     }
     for (int i = 0; i < n; i++) {
-        cudaStream_t sm = one ? nullptr : h->mid;
-        rx_status r = host ? enqueue_call(h, nullptr, nullptr, ins[i], outs[i], sf, sb, sc, &nbits_out[i], sm)
-                           : enqueue_call(h, ins[i], outs[i], nullptr, nullptr, sf, sb, sc, &nbits_out[i], sm);
+        cudaStream_t sm = one ? nullptr : h->mid, s4 = one ? nullptr : h->tail;
+        rx_status r = host ? enqueue_call(h, nullptr, nullptr, ins[i], outs[i], sf, sb, sc, &nbits_out[i], sm, s4)
+                           : enqueue_call(h, ins[i], outs[i], nullptr, nullptr, sf, sb, sc, &nbits_out[i], sm, s4);
         if (r != RX_OK) return r;
     }
     if (!one) {
-        // the back end of the last buffer waited for its front end: joining it joins all
-        if (cudaEventRecord(h->ev_join, sb) != cudaSuccess || cudaStreamWaitEvent(caller, h->ev_join, 0) != cudaSuccess)
+        // the last demap waited for its equaliser, which waited for its matched filter
+        // and field: joining the tail joins all
+        if (cudaEventRecord(h->ev_join, h->tail) != cudaSuccess || cudaStreamWaitEvent(caller, h->ev_join, 0) != cudaSuccess)
             return RX_ECUDA;
     }
     return RX_OK;
