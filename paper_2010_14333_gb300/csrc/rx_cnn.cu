@@ -460,8 +460,8 @@ __global__ void k_cnn_tobf(const float *__restrict__ prm, __nv_bfloat16 *__restr
 // ====================================================================
 // Receiver inference on the fifth-generation tensor cores (tcgen05).
 //
-// Tiles of kTS = 256 symbols (four 64-symbol windows) per iteration of a
-// persistent CTA (one per SM, 512 threads: four warps per tensor-memory lane
+// Tiles of kTS = 128 symbols (two 64-symbol windows) per iteration of a
+// persistent CTA (two per SM, 512 threads each: four warps per tensor-memory lane
 // quarter, each taking a quarter of the accumulator columns).  Activations live in shared memory as
 // four "planes" of 8 channels, each position one 16-byte row: with this layout
 // the im2col operand of a 32-channel, 9-tap convolution at K-step ks (taps ks/2,
@@ -482,21 +482,23 @@ __global__ void k_cnn_tobf(const float *__restrict__ prm, __nv_bfloat16 *__restr
 // with the hardware tanh (tanh.approx.f16x2): its distance to the erf form
 // (< 2.2e-4 absolute) and the FP16 arithmetic (2^-11 relative) stay at the
 // resolution the activations are stored with.
-constexpr int kTS = 256;
-constexpr int kP0 = 2 * kTS + 24, kP1 = kP0 - 8, kP2 = kP1 - 8, kP3 = kP2 - 8;   // 536 528 520 512
-constexpr int kMT2 = (kP2 + 127) / 128, kMT3 = kP3 / 128;                     // 5, 4
+constexpr int kTS = 128;
+constexpr int kP0 = 2 * kTS + 24, kP1 = kP0 - 8, kP2 = kP1 - 8, kP3 = kP2 - 8;   // 280 272 264 256
+constexpr int kMT1 = (kP1 + 127) / 128, kMT2 = (kP2 + 127) / 128, kMT3 = kP3 / 128;   // 3, 3, 2
 constexpr int kR1 = 128 * kMT2 + 8;          // rows of the h1 / h3 planes (rows >= kP1 stay zero)
 constexpr int kR2 = kP2 + 8;                 // rows of the h2 planes
+constexpr int kRA = 128 * kMT1;              // rows of the layer-1 im2col planes
+constexpr int kWinT = kTS / 64;              // windows per tile
 constexpr int kRxThreads = 512;
-constexpr uint32_t kRxTmem = 256;
+constexpr uint32_t kRxTmem = 128;
 struct RxSmem {
     static constexpr int W2 = 0;                          // bf16 planes [36][32 rows][16 B]
     static constexpr int W3 = W2 + 36 * 512;
     static constexpr int M1 = W3 + 36 * 512;              // bf16 planes [4][64 rows][16 B]
-    static constexpr int H1 = M1 + 4 * 1024;              // bf16 planes [4][kR1][16 B] (h1, then h3)
-    static constexpr int H2 = H1 + 4 * kR1 * 16;          // bf16 planes [4][kR2][16 B]
-    static constexpr int A1 = H2 + 4 * kR2 * 16;          // fp16 im2col planes [4][kRA][16 B]
-    static constexpr int B1 = A1 + 4 * 640 * 16;          // fp16 planes [4][32 rows][16 B]
+    static constexpr int H1 = M1 + 4 * 1024;              // fp16 planes [4][kR1][16 B] (h1, then h3)
+    static constexpr int H2 = H1 + 4 * kR1 * 16;          // fp16 planes [4][kR2][16 B], and before
+    static constexpr int A1 = H2;                         // them the layer-1 im2col planes [4][kRA][16 B]
+    static constexpr int B1 = H2 + 16 * (4 * kR2 > 4 * kRA ? 4 * kR2 : 4 * kRA);   // fp16 planes [4][32][16 B]
     static constexpr int X = B1 + 4 * 512;                // float2 [kP0]
     static constexpr int PRM = X + ((kP0 * 8 + 127) & ~127);   // W1 [32][18] | b1 b2 b3 [96] | c1 [64] | M2 [128] | c2 [2]
     static constexpr int PART = PRM + 4096;               // float [kTS][4 column quarters][2]
@@ -504,7 +506,8 @@ struct RxSmem {
     static constexpr int BAR = OS + kTS * 8;              // mbarrier, TMEM slot
     static constexpr int TOTAL = BAR + 64;
 };
-static_assert(RxSmem::TOTAL <= 227 * 1024, "receiver CNN shared memory");
+static_assert(RxSmem::TOTAL <= 113 * 1024, "two receiver CNN CTAs per SM");
+static_assert(128 * kMT3 - 1 + 8 < kP2, "layer 3 reads only computed h2 rows");
 
 __device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
 
@@ -522,7 +525,7 @@ __device__ __forceinline__ __half2 gelu_h2(float a, float b)
     return __hmul2(__hmul2(half, u), __hadd2(one, t));
 }
 
-__global__ void __launch_bounds__(kRxThreads, 1)
+__global__ void __launch_bounds__(kRxThreads, 2)
     k_cnn_rx_tc(const float *__restrict__ prm, const __nv_bfloat16 *__restrict__ prm_bf, const float2 *__restrict__ y,
                 long long seg_base, long long y_end, int nwin, uint8_t *__restrict__ dec, uint8_t *__restrict__ winb,
                 uint4 *__restrict__ winrec, const uint32_t *__restrict__ prbs_bits, long long k_first, float scale,
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__(kRxThreads, 1)
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + RxSmem::BAR);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quarter = warp & 3, cq = warp >> 2;
-    constexpr int PL1 = kR1 * 16, PL2 = kR2 * 16, PLA = 640 * 16;
+    constexpr int PL1 = kR1 * 16, PL2 = kR2 * 16, PLA = kRA * 16;
 
     if (tid == 0) mbar_init(bar, 1);
     __syncwarp();
@@ -585,8 +588,6 @@ __global__ void __launch_bounds__(kRxThreads, 1)
     // rows past the computed positions are read by the last row tiles: zero once
     for (int i = tid; i < 4 * kR1; i += kRxThreads)
         *reinterpret_cast<uint4 *>(sH1 + (i / kR1) * PL1 + (i % kR1) * 16) = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < 4 * kR2; i += kRxThreads)
-        *reinterpret_cast<uint4 *>(sH2 + (i / kR2) * PL2 + (i % kR2) * 16) = make_uint4(0, 0, 0, 0);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(kRxThreads, 1)
     const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's lane quarter
     unsigned phase = 0;
     bool ok = true;
-    const int ntiles = (nwin + 3) / 4;
+    const int ntiles = (nwin + kWinT - 1) / kWinT;
 
     // one row tile group of a convolution: 18 K-steps of the taps x channel groups
     auto conv_mma = [&](uint32_t aH, int PL, uint32_t aW, int mtiles) {
@@ -645,7 +646,7 @@ __global__ void __launch_bounds__(kRxThreads, 1)
         __syncthreads();
         // layer 1: FP16 im2col (row p, K column kk: reals 2p + 8 kk .. + 8 of the input, zero past K = 18)
         const float *xf = reinterpret_cast<const float *>(xs);
-        for (int u = tid; u < 640 * 4; u += kRxThreads) {
+        for (int u = tid; u < kRA * 4; u += kRxThreads) {
             int p = u >> 2, kk = u & 3;
             uint32_t w[4] = {0u, 0u, 0u, 0u};
             if (p < kP1 && kk < 3) {
@@ -663,7 +664,7 @@ __global__ void __launch_bounds__(kRxThreads, 1)
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            for (int m = 0; m < kMT2; m++)
+            for (int m = 0; m < kMT1; m++)
                 for (int ks = 0; ks < 2; ks++) {
                     uint64_t ad = umma_sdesc(aA1 + 128 * m * 16 + 2 * ks * PLA, PLA, 128);
                     uint64_t bd = umma_sdesc(aB1 + 2 * ks * 512, 512, 128);
@@ -673,7 +674,7 @@ __global__ void __launch_bounds__(kRxThreads, 1)
         }
         if (!(ok = wait_mma())) break;
         tc_fence_after();
-        conv_epi(kMT2, kP1, bb, sH1, PL1);
+        conv_epi(kMT1, kP1, bb, sH1, PL1);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -743,9 +744,9 @@ __global__ void __launch_bounds__(kRxThreads, 1)
             if (soft && ks < 64LL * nwin) soft[ks] = make_float2(o0, o1);
         }
         __syncthreads();
-        // decisions and window records: warp w < 4 takes window 4 t + w
-        if (warp < 4 && 4 * t + warp < nwin) {
-            const int s = 4 * t + warp;
+        // decisions and window records: warp w < kWinT takes window kWinT t + w
+        if (warp < kWinT && kWinT * t + warp < nwin) {
+            const int s = kWinT * t + warp;
             const float *osw = os + 2 * 64 * warp;
             const int NB = mq == 2 ? 1 : 2, BPS = 2 * NB;
             long long k0 = k_first + (long long)s * CS;
@@ -803,8 +804,8 @@ cudaError_t launch_cnn_decide(const float *prm, const void *prm_bf, const float2
                               long long k_first, float scale, int mq, float2 *soft, int *err, int nsm, cudaStream_t st)
 {
     if (nwin <= 0) return cudaSuccess;
-    int ntiles = (nwin + 3) / 4;
-    unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
+    int ntiles = (nwin + kWinT - 1) / kWinT;
+    unsigned grid = (unsigned)(ntiles < 2 * nsm ? ntiles : 2 * nsm);   // two persistent CTAs per SM
     k_cnn_rx_tc<<<grid, kRxThreads, RxSmem::TOTAL, st>>>(prm, (const __nv_bfloat16 *)prm_bf, y, seg_base, y_end, nwin,
                                                         dec, winb, winrec, prbs_bits, k_first, scale, mq, soft, err);
     return cudaGetLastError();
