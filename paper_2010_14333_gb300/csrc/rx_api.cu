@@ -665,8 +665,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         if (h->cnn) {
             // learned equaliser: one segment per payload window
             long long seg_base = 2 * pay_lo - 12 - h->ybase_cur;
-            e = launch_cnn_decide(rx_cnn_dev_params(h->cnn), rx_cnn_dev_params_bf16(h->cnn),
-                                  (const float2 *)h->Y[h->yw], seg_base, s.f_k - h->ybase_cur, g.nwin, h->dec[ds],
+            e = launch_cnn_decide(rx_cnn_dev_params(h->cnn), (const float2 *)h->Y[h->yw], seg_base, s.f_k - h->ybase_cur, g.nwin, h->dec[ds],
                                   h->winb[ds], h->winrec[ds], h->prbs_bits, pay_lo, h->ep.scale, h->mq,
                                   h->dbg_z ? h->dbg_z + (pay_lo - sym_lo) : nullptr, &h->st->err, h->nsm, sb);
         } else {

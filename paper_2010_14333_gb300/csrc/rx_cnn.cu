@@ -526,7 +526,7 @@ __device__ __forceinline__ __half2 gelu_h2(float a, float b)
 }
 
 __global__ void __launch_bounds__(kRxThreads, 2)
-    k_cnn_rx_tc(const float *__restrict__ prm, const __nv_bfloat16 *__restrict__ prm_bf, const float2 *__restrict__ y,
+    k_cnn_rx_tc(const float *__restrict__ prm, const float2 *__restrict__ y,
                 long long seg_base, long long y_end, int nwin, uint8_t *__restrict__ dec, uint8_t *__restrict__ winb,
                 uint4 *__restrict__ winrec, const uint32_t *__restrict__ prbs_bits, long long k_first, float scale,
                 int mq, float2 *__restrict__ soft, int *err)
@@ -799,14 +799,14 @@ cudaError_t prepare_cnn_rx()
     return cudaFuncSetAttribute(k_cnn_rx_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, RxSmem::TOTAL);
 }
 
-cudaError_t launch_cnn_decide(const float *prm, const void *prm_bf, const float2 *y, long long seg_base, long long y_end,
+cudaError_t launch_cnn_decide(const float *prm, const float2 *y, long long seg_base, long long y_end,
                               int nwin, uint8_t *dec, uint8_t *winb, uint4 *winrec, const uint32_t *prbs_bits,
                               long long k_first, float scale, int mq, float2 *soft, int *err, int nsm, cudaStream_t st)
 {
     if (nwin <= 0) return cudaSuccess;
     int ntiles = (nwin + kWinT - 1) / kWinT;
     unsigned grid = (unsigned)(ntiles < 2 * nsm ? ntiles : 2 * nsm);   // two persistent CTAs per SM
-    k_cnn_rx_tc<<<grid, kRxThreads, RxSmem::TOTAL, st>>>(prm, (const __nv_bfloat16 *)prm_bf, y, seg_base, y_end, nwin,
+    k_cnn_rx_tc<<<grid, kRxThreads, RxSmem::TOTAL, st>>>(prm, y, seg_base, y_end, nwin,
                                                         dec, winb, winrec, prbs_bits, k_first, scale, mq, soft, err);
     return cudaGetLastError();
 }
@@ -936,6 +936,5 @@ rx_status rx_cnn_adam_step(rx_cnn *c, float lr, void *stream)
 
 // device pointers of the parameters (for the receiver's CNN path)
 const float *rx_cnn_dev_params(const rx_cnn *c) { return c ? c->prm : nullptr; }
-const void *rx_cnn_dev_params_bf16(const rx_cnn *c) { return c ? (const void *)c->prm_bf : nullptr; }
 
 }  // extern "C"

@@ -151,7 +151,7 @@ cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, in
 // CNN decisions for nseg consecutive payload windows (receiver mode)
 // CNN receiver on the tensor cores: soft symbols and decisions of nwin 64-symbol
 // windows; y[seg_base + 2 j - 12 ..] feeds symbol j, inputs at y_end and beyond read 0
-cudaError_t launch_cnn_decide(const float *prm, const void *prm_bf, const float2 *y, long long seg_base, long long y_end,
+cudaError_t launch_cnn_decide(const float *prm, const float2 *y, long long seg_base, long long y_end,
                               int nwin, uint8_t *dec, uint8_t *winb, uint4 *winrec, const uint32_t *prbs_bits,
                               long long k_first, float scale, int mq, float2 *soft, int *err, int nsm, cudaStream_t st);
 cudaError_t prepare_cnn_rx();
@@ -160,5 +160,4 @@ cudaError_t prepare_cnn_rx();
 
 extern "C" {
 const float *rx_cnn_dev_params(const rx_cnn *c);
-const void *rx_cnn_dev_params_bf16(const rx_cnn *c);
 }
