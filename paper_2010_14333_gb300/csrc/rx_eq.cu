@@ -552,8 +552,8 @@ cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void 
 // absolute rotations of its decisions (window records), so the bit-error
 // statistics here are selections: the decoded rotation q = m + r gives the raw
 // count, and the slip-tolerant count takes the best rotation, ties to q.
-constexpr int kDemapWin = 16;
-constexpr int kDemapThreads = 128;
+constexpr int kDemapWin = 32;
+constexpr int kDemapThreads = 256;
 
 __device__ __forceinline__ int unwrap_inc(int b_prev, int b, int B)
 {
