@@ -255,15 +255,19 @@ void rx_destroy(rx_handle *h)
     if (h->back) cudaStreamSynchronize(h->back);
     if (h->tail) cudaStreamSynchronize(h->tail);
     if (h->copy) cudaStreamSynchronize(h->copy);
-    void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->E[0], h->E[1], h->E[2], h->Y[0], h->Y[1], h->Y[2],
-                    h->partials, h->dec[0], h->dec[1], h->dec[2], h->winb[0], h->winb[1], h->winb[2],
-                    h->winrec[0], h->winrec[1], h->winrec[2], h->prbs, h->taps[0], h->taps[1], h->twN, h->twN2,
-                    h->ds_tab,
-                    h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1], h->bits_stage, h->lnt, h->sqt,
-                    h->prbs_bits, h->phist[0], h->phist[1], h->zbuf};
-    static_assert(kSlots == 3, "slot arrays listed above");
+    void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->partials, h->prbs, h->taps[0], h->taps[1], h->twN,
+                    h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
+                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->zbuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (int i = 0; i < kSlots; i++) {
+        void *sp[] = {h->E[i], h->Y[i], h->dec[i], h->winb[i], h->winrec[i]};
+        for (void *p : sp)
+            if (p) cudaFree(p);
+        cudaEvent_t ev[] = {h->ev_yfree[i], h->ev_efree[i], h->ev_dfree[i]};
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
     if (h->prof_ev) {
         for (int i = 0; i < kProfRing * kEvPerCall; i++) cudaEventDestroy(h->prof_ev[i]);
         free(h->prof_ev);
@@ -273,10 +277,8 @@ void rx_destroy(rx_handle *h)
     if (h->back) cudaStreamDestroy(h->back);
     if (h->tail) cudaStreamDestroy(h->tail);
     if (h->copy) cudaStreamDestroy(h->copy);
-    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_yfree[0],
-                          &h->ev_yfree[1], &h->ev_yfree[2], &h->ev_efree[0], &h->ev_efree[1], &h->ev_efree[2],
-                          &h->ev_dfree[0], &h->ev_dfree[1], &h->ev_dfree[2], &h->ev_inready[0], &h->ev_inready[1],
-                          &h->ev_infree[0], &h->ev_infree[1]};
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_inready[0],
+                          &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
     for (cudaEvent_t *ev : evs)
         if (*ev) cudaEventDestroy(*ev);
     free(h->prof_used);
@@ -485,12 +487,14 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
                   cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->tail, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
-        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_yfree[0],
-                              &h->ev_yfree[1], &h->ev_yfree[2], &h->ev_efree[0], &h->ev_efree[1], &h->ev_efree[2],
-                              &h->ev_dfree[0], &h->ev_dfree[1], &h->ev_dfree[2], &h->ev_inready[0], &h->ev_inready[1],
-                              &h->ev_infree[0], &h->ev_infree[1]};
+        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_inready[0],
+                              &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
         for (cudaEvent_t *ev : evs)
             ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < kSlots; i++)
+            ok = ok && cudaEventCreateWithFlags(&h->ev_yfree[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->ev_efree[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->ev_dfree[i], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             rx_destroy(h);
