@@ -73,6 +73,7 @@ struct rx_handle {
     DevState *st;
     uint8_t *in_stage[2], *bits_stage;   // device staging of the host-buffer entry points
     float2 *zbuf;                   // payload soft symbols of the tensor-core FIR forms
+    float2 *gpart;                  // frozen forms: tap-gradient partials, one row of 32 per window
     long long dec_cap, win_cap, y_cap;
     int nsm;                        // SMs of the handle's device
     // stage timing: a ring of event sets, one per profiled call
@@ -257,7 +258,7 @@ void rx_destroy(rx_handle *h)
     if (h->copy) cudaStreamSynchronize(h->copy);
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->partials, h->prbs, h->taps[0], h->taps[1], h->twN,
                     h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
-                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->zbuf};
+                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->zbuf, h->gpart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kSlots; i++) {
@@ -314,7 +315,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     if (c.pack_order < 0 || c.pack_order > 1 || c.ntaps < 1 || c.ntaps > kMaxTaps || !(c.ntaps & 1) ||
         c.win != kWin || c.eq_block < kWin || c.eq_block % kWin || c.ntrain < 0 || c.ntrain % kWin ||
         c.mf_span < 0 || c.mf_span % 2 || sps * c.mf_span / 2 > kEHist / 2 || !(c.rrc_beta >= 0) ||
-        c.rrc_beta > 1 || c.eq_block > 4096)
+        c.rrc_beta > 1 || c.eq_block > kMaxEqBlock)
         return RX_EINVAL;
     if (c.fir_prec < RX_FIR_ADAPTIVE || c.fir_prec > RX_FIR_FP8 || (c.fir_prec != RX_FIR_ADAPTIVE && !kk) ||
         (c.fir_prec >= RX_FIR_BF16 && 2048 % c.eq_block))
@@ -420,6 +421,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     for (int i = 0; i < 2; i++) RX_ALLOC(h->in_stage[i], nb * 3 / 2 + 16);
     RX_ALLOC(h->bits_stage, rx_max_bits(h) / 8 + 16);
     if (c.fir_prec >= RX_FIR_BF16) RX_ALLOC(h->zbuf, symcap * sizeof(float2));
+    if (c.fir_prec >= RX_FIR_FROZEN_F32) RX_ALLOC(h->gpart, (size_t)(kMaxEqBlock / kWin) * 32 * sizeof(float2));
     if (c.debug) {
         RX_ALLOC(h->dbg_win, h->win_cap * sizeof(float4));
         RX_ALLOC(h->dbg_z, symcap * sizeof(float2));
@@ -658,6 +660,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     g.ybase = h->ybase_cur;
     g.nblk = npay > 0 ? (int)(npay / c.eq_block) : 0;
     g.nwin = npay > 0 ? (int)(npay / kWin) : 0;
+    g.gpart = h->gpart;
     if (four) cudaStreamWaitEvent(sb, h->ev_dfree[ds], 0);   // the demap is done with these decision slots
     prof_begin(h, 5, sb);
     if (e == cudaSuccess && do_train) {

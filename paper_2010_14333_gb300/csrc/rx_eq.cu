@@ -339,10 +339,9 @@ __device__ __forceinline__ WinOut pam_window(const EqParams &p, const float *ys,
 // Payload: one warp per block of eq_block symbols, input staged by one bulk copy.
 // Training (train=1): one warp runs the training windows sequentially, staging
 // each window's input with plain loads.
-template <bool QAM, int NT, int MQ, bool FRZ = false>
+template <bool QAM, int NT, int MQ>
 __global__ void __launch_bounds__(32 * kEqWarpsMax)
-    k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Yv, const float2 *__restrict__ zin,
-         float2 *taps_in, float2 *taps_out,
+    k_eq(EqParams p, EqGeom g, int train, const void *__restrict__ Yv, float2 *taps_in, float2 *taps_out,
          uint8_t *__restrict__ dec, uint8_t *__restrict__ winb, uint4 *__restrict__ winrec,
          float4 *__restrict__ dbg_win, float2 *__restrict__ dbg_z, const uint8_t *__restrict__ prbs_ext,
          const uint32_t *__restrict__ prbs_bits, DevState *dst)
@@ -395,22 +394,18 @@ __global__ void __launch_bounds__(32 * kEqWarpsMax)
     long long kb = g.pay_lo + blk * B;
     long long ym0 = 2 * kb - kYHist;
     const bool last = blk == g.nblk - 1;
-    // with soft symbols given, only the last block (tap step) reads the input
-    if (!(FRZ && zin) || last) {
-        if (lane == 0) {
-            mbar_init(bar, 1);
-            unsigned bytes = (unsigned)(ylen * sizeof(T));
-            mbar_expect_tx(bar, bytes);
-            bulk_g2s(ys, Y + (ym0 - g.ybase), bytes, bar);
-        }
-        __syncwarp();
-        if (!mbar_wait(bar, 0)) {
-            if (lane == 0) atomicExch(&dst->err, (int)RX_ETIMEOUT);
-            mbar_wait(bar, 0);
-            return;
-        }
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        unsigned bytes = (unsigned)(ylen * sizeof(T));
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(ys, Y + (ym0 - g.ybase), bytes, bar);
     }
-    float2 G = make_float2(0.f, 0.f);   // frozen form: tap gradient of the last block
+    __syncwarp();
+    if (!mbar_wait(bar, 0)) {
+        if (lane == 0) atomicExch(&dst->err, (int)RX_ETIMEOUT);
+        mbar_wait(bar, 0);
+        return;
+    }
     const int bpsv = p.bps;
     int pwin = (int)(((long long)bpsv * kb) % 32767);   // PRBS position of the window's first bit
     for (int w = 0; w < B / kWin; w++) {
@@ -420,10 +415,9 @@ __global__ void __launch_bounds__(32 * kEqWarpsMax)
         float2 *dz = dbg_z ? dbg_z + (k0 - g.sym_lo) : nullptr;
         long long wi = (k0 - g.pay_lo) / kWin;
         if (QAM) {
-            WinOut R = qam_window<NT, MQ, FRZ>(p, reinterpret_cast<float2 *>(ys), c0, reinterpret_cast<float2 *>(zs),
-                                               reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), 2,
-                                               p.mu, lane, dq, dz, prbs_bits, pwin,
-                                               zin ? zin + (k0 - g.pay_lo) : nullptr, (FRZ && last) ? &G : nullptr);
+            WinOut R = qam_window<NT, MQ>(p, reinterpret_cast<float2 *>(ys), c0, reinterpret_cast<float2 *>(zs),
+                                          reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), 2, p.mu,
+                                          lane, dq, dz, prbs_bits, pwin);
             if (lane == 0) {
                 winb[wi] = (uint8_t)R.b;
                 winrec[wi] = make_uint4(R.errA, R.errB, R.serr, (unsigned)R.b | (R.nnear << 8));
@@ -442,15 +436,98 @@ __global__ void __launch_bounds__(32 * kEqWarpsMax)
         pwin += bpsv * kWin;
         pwin = pwin >= 32767 ? pwin - 32767 : pwin;
     }
-    if (FRZ && last && lane < NT) {
-        const float step = p.mu * (float)kWin / (float)B;
-        float2 w0 = reinterpret_cast<float2 *>(ws)[lane];
-        taps_out[lane] = make_float2(fmaf(step, G.x, w0.x), fmaf(step, G.y, w0.y));
-    } else if (!FRZ && last && lane < NT) {
+    if (last && lane < NT) {
         taps_out[lane] = QAM ? reinterpret_cast<float2 *>(ws)[lane]
                              : make_float2(reinterpret_cast<float *>(ws)[lane], 0.f);
     }
     if (lane == 0 && ambig) atomicAdd(&dst->cnt[C_AMBIG], (unsigned long long)ambig);
+}
+
+// ------------------------------------------------- frozen form, window-parallel
+// Every payload block filters with the call's start taps, so no window depends
+// on another: one warp per 64-symbol window.  With soft symbols from the
+// block-Toeplitz kernel (zin) only the windows of the last block read the
+// input, for the tap step; without, each window stages its input and filters
+// on the CUDA cores.  The last block's windows leave their partial sums of
+// y conj(e) in gpart; the warp that finishes last (ticket) adds them in window
+// order, so the next taps do not depend on the order the warps ran in.
+template <int NT, int MQ>
+__global__ void __launch_bounds__(32 * kEqWarpsMax)
+    k_eq_frozen(EqParams p, EqGeom g, const float2 *__restrict__ Y, const float2 *__restrict__ zin,
+                const float2 *__restrict__ taps_in, float2 *__restrict__ taps_out, uint8_t *__restrict__ dec,
+                uint8_t *__restrict__ winb, uint4 *__restrict__ winrec, float4 *__restrict__ dbg_win,
+                float2 *__restrict__ dbg_z, const uint32_t *__restrict__ prbs_bits, DevState *dst)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int ylen = 2 * kWin + 2 * kYHist;
+    constexpr size_t per_warp = (16 + (size_t)(ylen + 2 * kWin + 32) * sizeof(float2) + 15) & ~(size_t)15;
+    unsigned char *base = smraw + per_warp * wid;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base);
+    float2 *ys = reinterpret_cast<float2 *>(base + 16);
+    float2 *zs = ys + ylen;
+    float2 *es = zs + kWin;
+    float2 *ws = es + kWin;
+    const long long wi = (long long)blockIdx.x * (blockDim.x >> 5) + wid;
+    if (wi >= g.nwin) return;
+    const int nlast = p.eq_block / kWin;            // windows of the last block
+    const long long wl = (long long)g.nwin - nlast;  // its first window
+    const bool last = wi >= wl;
+    ws[lane] = lane < NT ? taps_in[lane] : make_float2(0.f, 0.f);
+    __syncwarp();
+    const long long k0 = g.pay_lo + wi * kWin;
+    if (!zin || last) {
+        if (lane == 0) {
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, (unsigned)(ylen * sizeof(float2)));
+            bulk_g2s(ys, Y + (2 * k0 - kYHist - g.ybase), (unsigned)(ylen * sizeof(float2)), bar);
+        }
+        __syncwarp();
+        if (!mbar_wait(bar, 0)) {
+            if (lane == 0) atomicExch(&dst->err, (int)RX_ETIMEOUT);
+            mbar_wait(bar, 0);
+            return;
+        }
+    }
+    const int pwin = (int)(((long long)p.bps * k0) % 32767);
+    float2 G = make_float2(0.f, 0.f);
+    WinOut R = qam_window<NT, MQ, true>(p, ys, kYHist, zs, es, ws, 2, p.mu, lane, dec + (k0 - g.pay_lo),
+                                        dbg_z ? dbg_z + (k0 - g.sym_lo) : nullptr, prbs_bits, pwin,
+                                        zin ? zin + (k0 - g.pay_lo) : nullptr, last ? &G : nullptr);
+    const long long wq = (k0 - g.pay_lo) / kWin;
+    if (lane == 0) {
+        winb[wq] = (uint8_t)R.b;
+        winrec[wq] = make_uint4(R.errA, R.errB, R.serr, (unsigned)R.b | (R.nnear << 8));
+        if (dbg_win) dbg_win[wq] = make_float4((float)R.b, 0.f, R.best, R.second);
+        if ((R.second - R.best) <= 1e-6f * R.best) atomicAdd(&dst->cnt[C_AMBIG], 1ull);
+    }
+    if (!last) return;
+    float2 *gp = g.gpart + (wi - wl) * 32;
+    if (lane < NT) gp[lane] = G;
+    __threadfence();
+    __syncwarp();
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(&dst->eq_ticket, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t != (unsigned)nlast - 1) return;
+    __threadfence();
+    if (lane < NT) {
+        float gr = 0.f, gi = 0.f;
+        for (int j = 0; j < nlast; j++) {
+            float2 v = __ldcg(g.gpart + j * 32 + lane);
+            gr += v.x;
+            gi += v.y;
+        }
+        const float step = p.mu * (float)kWin / (float)p.eq_block;
+        float2 w0 = ws[lane];
+        taps_out[lane] = make_float2(fmaf(step, gr, w0.x), fmaf(step, gi, w0.y));
+    }
+    if (lane == 0) dst->eq_ticket = 0;
+}
+
+static size_t eq_smem_frozen_per_warp()
+{
+    return (16 + (size_t)(2 * kWin + 2 * kYHist + 2 * kWin + 32) * sizeof(float2) + 15) & ~(size_t)15;
 }
 
 static size_t eq_smem_per_warp(bool qam, int B)
@@ -468,21 +545,23 @@ static cudaError_t launch_eq_t(const EqParams &p, const EqGeom &g, int train, co
 {
     if (train) {
         size_t smem = eq_smem_per_warp(QAM, kWin);
-        k_eq<QAM, NT, MQ><<<1, 32, smem, st>>>(p, g, 1, Y, nullptr, taps_in, taps_out, dec, winb, winrec, dbg_win,
-                                               dbg_z, prbs, prbs_bits, dst);
+        k_eq<QAM, NT, MQ><<<1, 32, smem, st>>>(p, g, 1, Y, taps_in, taps_out, dec, winb, winrec, dbg_win, dbg_z,
+                                               prbs, prbs_bits, dst);
         return cudaGetLastError();
     }
-    size_t smem = eq_smem_per_warp(QAM, p.eq_block) * p.warps;
-    unsigned grid = (unsigned)((g.nblk + p.warps - 1) / p.warps);
     if constexpr (QAM) {
         if (p.frozen) {
-            k_eq<QAM, NT, MQ, true><<<grid, 32 * p.warps, smem, st>>>(p, g, 0, Y, zin, taps_in, taps_out, dec, winb,
-                                                                        winrec, dbg_win, dbg_z, prbs, prbs_bits, dst);
+            if (g.nwin < p.eq_block / kWin) return cudaErrorInvalidValue;
+            unsigned grid = (unsigned)((g.nwin + p.warps - 1) / p.warps);
+            k_eq_frozen<NT, MQ><<<grid, 32 * p.warps, eq_smem_frozen_per_warp() * p.warps, st>>>(
+                p, g, (const float2 *)Y, zin, taps_in, taps_out, dec, winb, winrec, dbg_win, dbg_z, prbs_bits, dst);
             return cudaGetLastError();
         }
     }
-    k_eq<QAM, NT, MQ><<<grid, 32 * p.warps, smem, st>>>(p, g, 0, Y, nullptr, taps_in, taps_out, dec, winb, winrec,
-                                                          dbg_win, dbg_z, prbs, prbs_bits, dst);
+    size_t smem = eq_smem_per_warp(QAM, p.eq_block) * p.warps;
+    unsigned grid = (unsigned)((g.nblk + p.warps - 1) / p.warps);
+    k_eq<QAM, NT, MQ><<<grid, 32 * p.warps, smem, st>>>(p, g, 0, Y, taps_in, taps_out, dec, winb, winrec, dbg_win,
+                                                          dbg_z, prbs, prbs_bits, dst);
     return cudaGetLastError();
 }
 
@@ -496,7 +575,7 @@ static cudaError_t prepare_eq_t(const EqParams &p)
     const int smem = (int)kMaxSmemCta;
     if constexpr (QAM) {
         if (p.frozen)
-            return cudaFuncSetAttribute(k_eq<QAM, NT, MQ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            return cudaFuncSetAttribute(k_eq_frozen<NT, MQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     }
     return cudaFuncSetAttribute(k_eq<QAM, NT, MQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }

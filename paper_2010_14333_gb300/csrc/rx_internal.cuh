@@ -17,7 +17,8 @@ constexpr int kPamHist = 64;      // codes kept before a PAM buffer (>= 2 * MF h
 constexpr int kCtaK1 = 256;       // threads per K1a / K1c CTA
 constexpr int kEqWarpsMax = 8;    // most warps (equaliser blocks) per K3 CTA
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before flagging RX_ETIMEOUT
-constexpr int kSlots = 3;         // per-call buffer ring (field, MF output, decisions, carrier/gain)
+constexpr int kSlots = 3;
+constexpr int kMaxEqBlock = 4096;  // largest eq_block (symbols)         // per-call buffer ring (field, MF output, decisions, carrier/gain)
 
 // counters in DevState::cnt
 enum { C_SYMBOLS, C_BITS, C_BITERR, C_RAWERR, C_SYMERR, C_SLIP, C_NEAR, C_AMBIG, C_WINDOWS, C_NCNT };
@@ -33,6 +34,7 @@ struct DevState {
     int amb_r;                             // stream-start rotation, -1 before
     int first_code;                        // 12-bit code of the stream's first sample
     unsigned int ticket[kSlots];           // last-CTA ticket of the carrier reduction, per slot
+    unsigned int eq_ticket;                // last-warp ticket of the frozen form's tap step
     int err;                               // RX_ETIMEOUT when a bounded wait ran out
 };
 
@@ -88,6 +90,7 @@ struct EqGeom {
     long long ybase;           // stream index (2-sps) of Y workspace [0]
     int nblk;                  // payload blocks in this call
     int nwin;                  // payload windows in this call
+    float2 *gpart;             // frozen form: per-window tap-gradient partials of the last block
 };
 
 struct EqParams {
