@@ -462,67 +462,77 @@ __global__ void k_cnn_tobf(const float *__restrict__ prm, __nv_bfloat16 *__restr
 //
 // Tiles of kTS = 128 symbols (two 64-symbol windows) per iteration of a
 // persistent CTA (two per SM, 512 threads each: four warps per tensor-memory lane
-// quarter, each taking a quarter of the accumulator columns).  Activations live in shared memory as
-// four "planes" of 8 channels, each position one 16-byte row: with this layout
-// the im2col operand of a 32-channel, 9-tap convolution at K-step ks (taps ks/2,
-// channel groups 2 (ks % 2) and +1) is the plane pair read from position
-// p + ks/2 onwards, i.e. a K-major no-swizzle matrix descriptor whose start
-// address moves by whole 16-byte rows; no im2col copy is made.
-//   layer 1 (2 -> 32, K = 18 padded to 32): an explicit FP16 im2col of the
-//      FP32 input (16-byte rows are 8 consecutive reals of y), FP16 weights,
-//      tcgen05.mma (M = 128, N = 32) and the same epilogue as the other layers;
-//   layers 2, 3 (32 -> 32): 18 tcgen05.mma (M = 128, N = 32, K = 16) per 128
-//      output positions into tensor memory; epilogue bias + GELU -> FP16 planes;
-//   MLP 32 -> 64: tcgen05.mma (M = 128, N = 64) over all positions; the epilogue
-//      keeps the symbol (even) positions, GELU, then 64 -> 2 on the CUDA cores;
+// quarter, each taking a quarter of the accumulator columns).  Activations live
+// in shared memory as "planes" of 8 channels, each position one 16-byte row: with
+// this layout the im2col operand of a 32-channel, 9-tap convolution at K-step ks
+// (tap ks/2, channel groups 2 (ks % 2) and +1) is the plane pair read from
+// position p + ks/2 onwards, i.e. a K-major no-swizzle matrix descriptor whose
+// start address moves by whole 16-byte rows; no im2col copy is made.
+//   layer 1 (2 -> 32, K = 18 padded to 32): one FP16 plane whose row p holds the
+//      8 reals of positions p .. p+3; a descriptor whose two K core matrices sit
+//      4 rows apart (leading offset 64 bytes) reads rows p, p+4 (K 0..15) and,
+//      8 rows on, p+8, p+12 (K 16..31): the whole im2col row of position p;
+//   layer 2 (32 -> 32): 18 tcgen05.mma (M = 128, N = 32, K = 16) per 128
+//      positions; its epilogue stores the even and the odd positions in two
+//      separate plane sets;
+//   layer 3 (32 -> 32) only at the symbol (even) positions 2j: tap 2e reads the
+//      even set from row j + e, tap 2e + 1 the odd set from row j + e, so one
+//      M = 128 tile covers the tile's 128 symbols;
+//   MLP 32 -> 64 (M = 128, N = 64) on the symbols, bias + GELU into FP16
+//      planes, then 64 -> 2 as one more MMA (N = 16, two live columns);
 //   decisions and window records as the FIR receiver.
 // Inference precision: FP16 operands (activations and weights, converted from the
-// FP32 master weights), FP32 accumulation in tensor memory.  GELU is evaluated in
-// packed FP16 by its tanh form 0.5 u (1 + tanh(sqrt(2/pi) (u + 0.044715 u^3)))
+// FP32 master weights), FP32 accumulation in tensor memory; bias and GELU in
+// packed FP16, GELU by its tanh form 0.5 u (1 + tanh(sqrt(2/pi) (u + 0.044715 u^3)))
 // with the hardware tanh (tanh.approx.f16x2): its distance to the erf form
 // (< 2.2e-4 absolute) and the FP16 arithmetic (2^-11 relative) stay at the
 // resolution the activations are stored with.
 constexpr int kTS = 128;
-constexpr int kP0 = 2 * kTS + 24, kP1 = kP0 - 8, kP2 = kP1 - 8, kP3 = kP2 - 8;   // 280 272 264 256
-constexpr int kMT1 = (kP1 + 127) / 128, kMT2 = (kP2 + 127) / 128, kMT3 = kP3 / 128;   // 3, 3, 2
-constexpr int kR1 = 128 * kMT2 + 8;          // rows of the h1 / h3 planes (rows >= kP1 stay zero)
-constexpr int kR2 = kP2 + 8;                 // rows of the h2 planes
-constexpr int kRA = 128 * kMT1;              // rows of the layer-1 im2col planes
+constexpr int kP0 = 2 * kTS + 24, kP1 = kP0 - 8, kP2 = kP1 - 8;   // 280 272 264 input / layer-1 / layer-2 positions
+constexpr int kMT1 = (kP1 + 127) / 128, kMT2 = (kP2 + 127) / 128;  // 3, 3 row tiles
+constexpr int kRX = 128 * kMT1 + 12;         // rows of the layer-1 input plane (396)
+constexpr int kR1 = 128 * kMT2 + 8;          // rows of the h1 planes (rows >= kP1 stay zero); h3 reuses rows < 128
+constexpr int kRE = kP2 / 2 + 4;             // rows of each even / odd h2 plane (136; rows < 132 written)
 constexpr int kWinT = kTS / 64;              // windows per tile
 constexpr int kRxThreads = 512;
 constexpr uint32_t kRxTmem = 128;
+constexpr uint32_t kColOut = 96;             // accumulator columns of the 64 -> 2 projection
 struct RxSmem {
-    static constexpr int W2 = 0;                          // bf16 planes [36][32 rows][16 B]
+    static constexpr int W2 = 0;                          // fp16 planes [36][32 rows][16 B]
     static constexpr int W3 = W2 + 36 * 512;
-    static constexpr int M1 = W3 + 36 * 512;              // bf16 planes [4][64 rows][16 B]
-    static constexpr int H1 = M1 + 4 * 1024;              // fp16 planes [4][kR1][16 B] (h1, then h3)
-    static constexpr int H2 = H1 + 4 * kR1 * 16;          // fp16 planes [4][kR2][16 B], and before
-    static constexpr int A1 = H2;                         // them the layer-1 im2col planes [4][kRA][16 B]
-    static constexpr int B1 = H2 + 16 * (4 * kR2 > 4 * kRA ? 4 * kR2 : 4 * kRA);   // fp16 planes [4][32][16 B]
-    static constexpr int X = B1 + 4 * 512;                // float2 [kP0]
-    static constexpr int PRM = X + ((kP0 * 8 + 127) & ~127);   // W1 [32][18] | b1 b2 b3 [96] | c1 [64] | M2 [128] | c2 [2]
-    static constexpr int PART = PRM + 4096;               // float [kTS][4 column quarters][2]
-    static constexpr int OS = PART + kTS * 32;            // float [kTS][2]
+    static constexpr int M1 = W3 + 36 * 512;              // fp16 planes [4][64 rows][16 B]
+    static constexpr int M2 = M1 + 4 * 1024;              // fp16 planes [8][16 rows][16 B] (rows 0, 1 live)
+    static constexpr int B1 = M2 + 8 * 256;               // fp16 planes [4][32 rows][16 B]
+    static constexpr int H1 = B1 + 4 * 512;               // fp16 planes [4][kR1][16 B] (h1, then h3)
+    static constexpr int HX = H1 + 4 * kR1 * 16;          // the layer-1 input plane [kRX][16 B], then the
+                                                          // even/odd h2 planes [2][4][kRE][16 B], then the
+                                                          // hidden planes [8][128][16 B]
+    static constexpr int HXB = 2 * 4 * kRE * 16;
+    static constexpr int BH = HX + HXB;                   // half2 biases: layers 1..3 [3][16], MLP [32]
+    static constexpr int C2 = BH + 80 * 4;                // float [2]: output bias
+    static constexpr int OS = C2 + 16;                    // float [kTS][2]
     static constexpr int BAR = OS + kTS * 8;              // mbarrier, TMEM slot
     static constexpr int TOTAL = BAR + 64;
 };
+static_assert(kRX * 16 <= RxSmem::HXB && 8 * 128 * 16 <= RxSmem::HXB, "aliases of the HX region fit");
 static_assert(RxSmem::TOTAL <= 113 * 1024, "two receiver CNN CTAs per SM");
-static_assert(128 * kMT3 - 1 + 8 < kP2, "layer 3 reads only computed h2 rows");
+static_assert(2 * (kRE - 4) == kP2, "even / odd h2 rows cover the layer-2 positions");
 
 __device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
+__device__ __forceinline__ __half2 bits_h2(uint32_t u) { return *reinterpret_cast<__half2 *>(&u); }
 
-// GELU of two FP32 pre-activations in packed FP16 (tanh form, hardware tanh)
-__device__ __forceinline__ __half2 gelu_h2(float a, float b)
+// bias + GELU of two FP32 accumulators in packed FP16 (tanh form, hardware tanh):
+// u = acc + b; t = tanh(u (c0 + c1 u^2)); 0.5 u (1 + t) = h + h t with h = u / 2
+__device__ __forceinline__ uint32_t gelu_h2(uint32_t a, uint32_t b, uint32_t bias)
 {
-    const __half2 u = __floats2half2_rn(a, b);
-    const __half2 k0 = __float2half2_rn(0.7978845608028654f), k1 = __float2half2_rn(0.044715f);
-    const __half2 half = __float2half2_rn(0.5f), one = __float2half2_rn(1.0f);
-    __half2 u2 = __hmul2(u, u);
-    __half2 arg = __hmul2(__hmul2(k0, u), __hfma2(k1, u2, one));   // sqrt(2/pi) (u + 0.044715 u^3)
+    const __half2 c0 = __float2half2_rn(0.7978845608028654f), c1 = __float2half2_rn(0.7978845608028654f * 0.044715f);
+    const __half2 hf = __float2half2_rn(0.5f);
+    const __half2 u = __hadd2(__floats2half2_rn(__uint_as_float(a), __uint_as_float(b)), bits_h2(bias));
+    const __half2 arg = __hmul2(u, __hfma2(__hmul2(u, u), c1, c0));
     uint32_t th;
     asm("tanh.approx.f16x2 %0, %1;" : "=r"(th) : "r"(h2_bits(arg)));
-    __half2 t = *reinterpret_cast<__half2 *>(&th);
-    return __hmul2(__hmul2(half, u), __hadd2(one, t));
+    const __half2 h = __hmul2(u, hf);
+    return h2_bits(__hfma2(h, bits_h2(th), h));
 }
 
 __global__ void __launch_bounds__(kRxThreads, 2)
@@ -532,19 +542,15 @@ __global__ void __launch_bounds__(kRxThreads, 2)
                 int mq, float2 *__restrict__ soft, int *err)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *sW2 = sm + RxSmem::W2, *sW3 = sm + RxSmem::W3, *sM1 = sm + RxSmem::M1;
-    unsigned char *sH1 = sm + RxSmem::H1, *sH2 = sm + RxSmem::H2, *sA1 = sm + RxSmem::A1, *sB1 = sm + RxSmem::B1;
-    float2 *xs = reinterpret_cast<float2 *>(sm + RxSmem::X);
-    float *w1 = reinterpret_cast<float *>(sm + RxSmem::PRM);
-    float *bb = w1 + CC * 18;
-    float *c1 = bb + 3 * CC;
-    float *m2 = c1 + CH;                         // [2][64] then c2 [2]
-    float *part = reinterpret_cast<float *>(sm + RxSmem::PART);
+    unsigned char *sW2 = sm + RxSmem::W2, *sW3 = sm + RxSmem::W3, *sM1 = sm + RxSmem::M1, *sM2 = sm + RxSmem::M2;
+    unsigned char *sB1 = sm + RxSmem::B1, *sH1 = sm + RxSmem::H1, *sHX = sm + RxSmem::HX;
+    uint32_t *bh = reinterpret_cast<uint32_t *>(sm + RxSmem::BH);   // half2 bias pairs
+    float *c2 = reinterpret_cast<float *>(sm + RxSmem::C2);
     float *os = reinterpret_cast<float *>(sm + RxSmem::OS);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + RxSmem::BAR);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quarter = warp & 3, cq = warp >> 2;
-    constexpr int PL1 = kR1 * 16, PL2 = kR2 * 16, PLA = kRA * 16;
+    constexpr int PL1 = kR1 * 16, PLE = kRE * 16, EO = 4 * PLE;
 
     if (tid == 0) mbar_init(bar, 1);
     __syncwarp();
@@ -565,7 +571,11 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         int n = u & 63, kk = u >> 6;
         *reinterpret_cast<uint4 *>(sM1 + kk * 1024 + n * 16) = h8(prm + OM1 + n * CC + 8 * kk);
     }
-    for (int i = tid; i < CC * 18; i += kRxThreads) w1[i] = prm[OW1 + i];
+    for (int u = tid; u < 8 * 16; u += kRxThreads) {   // output projection: rows 0, 1 = the two outputs
+        int n = u & 15, kk = u >> 4;
+        *reinterpret_cast<uint4 *>(sM2 + kk * 256 + n * 16) =
+            n < 2 ? h8(prm + OM2 + n * CH + 8 * kk) : make_uint4(0, 0, 0, 0);
+    }
     for (int u = tid; u < 4 * 32; u += kRxThreads) {   // layer-1 weights, FP16, K padded to 32
         int n = u & 31, kk = u >> 5;
         uint32_t w[4];
@@ -573,18 +583,16 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         for (int i = 0; i < 4; i++) {
             int k0 = 8 * kk + 2 * i;
             float a = k0 < 18 ? prm[OW1 + n * 18 + k0] : 0.f, b = k0 + 1 < 18 ? prm[OW1 + n * 18 + k0 + 1] : 0.f;
-            __half2 h = __floats2half2_rn(a, b);
-            w[i] = *reinterpret_cast<uint32_t *>(&h);
+            w[i] = h2_bits(__floats2half2_rn(a, b));
         }
         *reinterpret_cast<uint4 *>(sB1 + kk * 512 + n * 16) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    for (int i = tid; i < CC; i += kRxThreads) {
-        bb[i] = prm[OB1 + i];
-        bb[CC + i] = prm[OB2 + i];
-        bb[2 * CC + i] = prm[OB3 + i];
+    for (int i = tid; i < 3 * 16; i += kRxThreads) {
+        const int off = (i < 16 ? OB1 : i < 32 ? OB2 : OB3) + 2 * (i & 15);
+        bh[i] = h2_bits(__floats2half2_rn(prm[off], prm[off + 1]));
     }
-    for (int i = tid; i < CH; i += kRxThreads) c1[i] = prm[OC1 + i];
-    for (int i = tid; i < 2 * CH + 2; i += kRxThreads) m2[i] = prm[OM2 + i];
+    for (int i = tid; i < 32; i += kRxThreads) bh[48 + i] = h2_bits(__floats2half2_rn(prm[OC1 + 2 * i], prm[OC1 + 2 * i + 1]));
+    if (tid < 2) c2[tid] = prm[OC2 + tid];
     // rows past the computed positions are read by the last row tiles: zero once
     for (int i = tid; i < 4 * kR1; i += kRxThreads)
         *reinterpret_cast<uint4 *>(sH1 + (i / kR1) * PL1 + (i % kR1) * 16) = make_uint4(0, 0, 0, 0);
@@ -593,25 +601,14 @@ __global__ void __launch_bounds__(kRxThreads, 2)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    // every inference layer: kind::f16 with FP16 operands
-    const uint32_t id32 = umma_idesc(0, 128, 32), id64 = umma_idesc(0, 128, 64), id16 = id32;
-    const uint32_t aA1 = smem_u32(sA1), aB1 = smem_u32(sB1);
-    const uint32_t aH1 = smem_u32(sH1), aH2 = smem_u32(sH2), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3),
-                   aM1 = smem_u32(sM1);
+    const uint32_t id16 = umma_idesc(0, 128, 16), id32 = umma_idesc(0, 128, 32), id64 = umma_idesc(0, 128, 64);
+    const uint32_t aB1 = smem_u32(sB1), aH1 = smem_u32(sH1), aHX = smem_u32(sHX), aW2 = smem_u32(sW2),
+                   aW3 = smem_u32(sW3), aM1 = smem_u32(sM1), aM2 = smem_u32(sM2);
     const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's lane quarter
     unsigned phase = 0;
     bool ok = true;
     const int ntiles = (nwin + kWinT - 1) / kWinT;
 
-    // one row tile group of a convolution: 18 K-steps of the taps x channel groups
-    auto conv_mma = [&](uint32_t aH, int PL, uint32_t aW, int mtiles) {
-        for (int m = 0; m < mtiles; m++)
-            for (int ks = 0; ks < 18; ks++) {
-                uint64_t ad = umma_sdesc(aH + (128 * m + ks / 2) * 16 + 2 * (ks & 1) * PL, PL, 128);
-                uint64_t bd = umma_sdesc(aW + 2 * ks * 512, 512, 128);
-                umma_f16(tmem + 32 * m, ad, bd, id32, ks > 0);
-            }
-    };
     auto wait_mma = [&]() -> bool {
         bool done = mbar_wait(bar, phase);
         if (!done) {
@@ -621,44 +618,32 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         phase ^= 1u;
         return __syncthreads_and(done) != 0;
     };
-    // conv epilogue: rows of this warp's lane quarter, channel group cq (8 channels)
-    auto conv_epi = [&](int mtiles, int valid, const float *bias, unsigned char *dstH, int PLd) {
-        for (int m = 0; m < mtiles; m++) {
-            uint32_t r[8];
-            tmem_ld8(tq + 32 * m + 8 * cq, r);
-            int row = 128 * m + 32 * quarter + lane;
-            if (row < valid) {
-                uint32_t w[4];
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    int o = 8 * cq + 2 * i;
-                    w[i] = h2_bits(gelu_h2(__uint_as_float(r[2 * i]) + bias[o], __uint_as_float(r[2 * i + 1]) + bias[o + 1]));
-                }
-                *reinterpret_cast<uint4 *>(dstH + cq * PLd + row * 16) = make_uint4(w[0], w[1], w[2], w[3]);
-            }
+    // conv epilogue of row tile m: rows of this warp's lane quarter, channel group
+    // cq (8 channels); row -> address of its 16-byte FP16 row in the destination
+    auto conv_epi = [&](int m, int valid, const uint32_t *bias, auto dst_row) {
+        uint32_t r[8];
+        tmem_ld8(tq + 32 * m + 8 * cq, r);
+        const int row = 128 * m + 32 * quarter + lane;
+        if (row < valid) {
+            const uint4 b = *reinterpret_cast<const uint4 *>(bias + 4 * cq);
+            *reinterpret_cast<uint4 *>(dst_row(row)) =
+                make_uint4(gelu_h2(r[0], r[1], b.x), gelu_h2(r[2], r[3], b.y), gelu_h2(r[4], r[5], b.z),
+                           gelu_h2(r[6], r[7], b.w));
         }
     };
 
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const long long ib = seg_base + 2LL * kTS * t;   // first input of the tile
-        for (int i = tid; i < kP0; i += kRxThreads)
-            xs[i] = (ib + i < y_end) ? y[ib + i] : make_float2(0.f, 0.f);
-        __syncthreads();
-        // layer 1: FP16 im2col (row p, K column kk: reals 2p + 8 kk .. + 8 of the input, zero past K = 18)
-        const float *xf = reinterpret_cast<const float *>(xs);
-        for (int u = tid; u < kRA * 4; u += kRxThreads) {
-            int p = u >> 2, kk = u & 3;
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-            if (p < kP1 && kk < 3) {
+        // layer-1 input plane: row p = positions p .. p+3 (8 reals) in FP16, zero past kP0
+        for (int p = tid; p < kRX; p += kRxThreads) {
+            uint32_t w[4];
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    int k0 = 8 * kk + 2 * i;
-                    float a = k0 < 18 ? xf[2 * p + k0] : 0.f, b = k0 + 1 < 18 ? xf[2 * p + k0 + 1] : 0.f;
-                    __half2 h = __floats2half2_rn(a, b);
-                    w[i] = *reinterpret_cast<uint32_t *>(&h);
-                }
+            for (int i = 0; i < 4; i++) {
+                const long long g = ib + p + i;
+                const float2 v = (p + i < kP0 && g < y_end) ? y[g] : make_float2(0.f, 0.f);
+                w[i] = h2_bits(__floats2half2_rn(v.x, v.y));
             }
-            *reinterpret_cast<uint4 *>(sA1 + kk * PLA + p * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(sHX + p * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         fence_async_smem();
         __syncthreads();
@@ -666,83 +651,105 @@ __global__ void __launch_bounds__(kRxThreads, 2)
             tc_fence_after();
             for (int m = 0; m < kMT1; m++)
                 for (int ks = 0; ks < 2; ks++) {
-                    uint64_t ad = umma_sdesc(aA1 + 128 * m * 16 + 2 * ks * PLA, PLA, 128);
+                    uint64_t ad = umma_sdesc(aHX + (128 * m + 8 * ks) * 16, 64, 128);
                     uint64_t bd = umma_sdesc(aB1 + 2 * ks * 512, 512, 128);
-                    umma_f16(tmem + 32 * m, ad, bd, id16, ks > 0);
+                    umma_f16(tmem + 32 * m, ad, bd, id32, ks > 0);
                 }
             umma_commit(bar);
         }
         if (!(ok = wait_mma())) break;
         tc_fence_after();
-        conv_epi(kMT1, kP1, bb, sH1, PL1);
+        for (int m = 0; m < kMT1; m++)
+            conv_epi(m, kP1, bh, [&](int row) { return sH1 + cq * PL1 + row * 16; });
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        // layer 2
+        // layer 2 (reads h1; the input plane is free)
         if (tid == 0) {
             tc_fence_after();
-            conv_mma(aH1, PL1, aW2, kMT2);
-            umma_commit(bar);
-        }
-        if (!(ok = wait_mma())) break;
-        tc_fence_after();
-        conv_epi(kMT2, kP2, bb + CC, sH2, PL2);
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        // layer 3 (h3 overwrites h1: layer 2's MMAs have completed)
-        if (tid == 0) {
-            tc_fence_after();
-            conv_mma(aH2, PL2, aW3, kMT3);
-            umma_commit(bar);
-        }
-        if (!(ok = wait_mma())) break;
-        tc_fence_after();
-        conv_epi(kMT3, kP3, bb + 2 * CC, sH1, PL1);
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        // MLP 32 -> 64 at every position (M = 128, N = 64, K = 32)
-        if (tid == 0) {
-            tc_fence_after();
-            for (int m = 0; m < kMT3; m++)
-                for (int ks = 0; ks < 2; ks++) {
-                    uint64_t ad = umma_sdesc(aH1 + 128 * m * 16 + 2 * ks * PL1, PL1, 128);
-                    uint64_t bd = umma_sdesc(aM1 + 2 * ks * 1024, 1024, 128);
-                    umma_f16(tmem + 64 * m, ad, bd, id64, ks > 0);
+            for (int m = 0; m < kMT2; m++)
+                for (int ks = 0; ks < 18; ks++) {
+                    uint64_t ad = umma_sdesc(aH1 + (128 * m + ks / 2) * 16 + 2 * (ks & 1) * PL1, PL1, 128);
+                    uint64_t bd = umma_sdesc(aW2 + 2 * ks * 512, 512, 128);
+                    umma_f16(tmem + 32 * m, ad, bd, id32, ks > 0);
                 }
             umma_commit(bar);
         }
         if (!(ok = wait_mma())) break;
         tc_fence_after();
-        for (int m = 0; m < kMT3; m++) {
-            uint32_t r[16];
-            tmem_ld16(tq + 64 * m + 16 * cq, r);
-            int row = 128 * m + 32 * quarter + lane;
-            if (!(row & 1)) {
-                float o0 = 0.f, o1 = 0.f;
-#pragma unroll
-                for (int i = 0; i < 16; i += 2) {
-                    int hu = 16 * cq + i;
-                    float2 z = __half22float2(gelu_h2(__uint_as_float(r[i]) + c1[hu], __uint_as_float(r[i + 1]) + c1[hu + 1]));
-                    o0 = fmaf(m2[hu], z.x, fmaf(m2[hu + 1], z.y, o0));
-                    o1 = fmaf(m2[CH + hu], z.x, fmaf(m2[CH + hu + 1], z.y, o1));
-                }
-                part[(row >> 1) * 8 + 2 * cq] = o0;
-                part[(row >> 1) * 8 + 2 * cq + 1] = o1;
+        for (int m = 0; m < kMT2; m++)
+            conv_epi(m, kP2, bh + 16, [&](int row) { return sHX + (row & 1) * EO + cq * PLE + (row >> 1) * 16; });
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // layer 3 at the symbol positions: tap d reads set d & 1 from row j + d / 2
+        if (tid == 0) {
+            tc_fence_after();
+            for (int ks = 0; ks < 18; ks++) {
+                const int d = ks >> 1;
+                uint64_t ad = umma_sdesc(aHX + (d & 1) * EO + (d >> 1) * 16 + 2 * (ks & 1) * PLE, PLE, 128);
+                uint64_t bd = umma_sdesc(aW3 + 2 * ks * 512, 512, 128);
+                umma_f16(tmem, ad, bd, id32, ks > 0);
             }
+            umma_commit(bar);
         }
+        if (!(ok = wait_mma())) break;
+        tc_fence_after();
+        conv_epi(0, kTS, bh + 32, [&](int row) { return sH1 + cq * PL1 + row * 16; });   // h3, row = symbol
+        fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        for (int j = tid; j < kTS; j += kRxThreads) {
-            const float *pj = part + 8 * j;
-            float o0 = ((pj[0] + pj[2]) + (pj[4] + pj[6])) + m2[2 * CH];
-            float o1 = ((pj[1] + pj[3]) + (pj[5] + pj[7])) + m2[2 * CH + 1];
+        // MLP 32 -> 64 on the symbols (M = 128, N = 64, K = 32)
+        if (tid == 0) {
+            tc_fence_after();
+            for (int ks = 0; ks < 2; ks++) {
+                uint64_t ad = umma_sdesc(aH1 + 2 * ks * PL1, PL1, 128);
+                uint64_t bd = umma_sdesc(aM1 + 2 * ks * 1024, 1024, 128);
+                umma_f16(tmem, ad, bd, id64, ks > 0);
+            }
+            umma_commit(bar);
+        }
+        if (!(ok = wait_mma())) break;
+        tc_fence_after();
+        {   // hidden units 16 cq .. + 15 of symbol row -> planes 2 cq, 2 cq + 1 (the h2 planes are free)
+            uint32_t r[16];
+            tmem_ld16(tq + 16 * cq, r);
+            const int row = 32 * quarter + lane;
+            const uint4 b0 = *reinterpret_cast<const uint4 *>(bh + 48 + 8 * cq);
+            const uint4 b1 = *reinterpret_cast<const uint4 *>(bh + 48 + 8 * cq + 4);
+            *reinterpret_cast<uint4 *>(sHX + (2 * cq) * 2048 + row * 16) =
+                make_uint4(gelu_h2(r[0], r[1], b0.x), gelu_h2(r[2], r[3], b0.y), gelu_h2(r[4], r[5], b0.z),
+                           gelu_h2(r[6], r[7], b0.w));
+            *reinterpret_cast<uint4 *>(sHX + (2 * cq + 1) * 2048 + row * 16) =
+                make_uint4(gelu_h2(r[8], r[9], b1.x), gelu_h2(r[10], r[11], b1.y), gelu_h2(r[12], r[13], b1.z),
+                           gelu_h2(r[14], r[15], b1.w));
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // 64 -> 2 (M = 128, N = 16 with rows 2..15 of B zero, K = 64)
+        if (tid == 0) {
+            tc_fence_after();
+            for (int ks = 0; ks < 4; ks++) {
+                uint64_t ad = umma_sdesc(aHX + 2 * ks * 2048, 2048, 128);
+                uint64_t bd = umma_sdesc(aM2 + 2 * ks * 256, 256, 128);
+                umma_f16(tmem + kColOut, ad, bd, id16, ks > 0);
+            }
+            umma_commit(bar);
+        }
+        if (!(ok = wait_mma())) break;
+        tc_fence_after();
+        if (cq == 0) {
+            uint32_t r[8];
+            tmem_ld8(tq + kColOut, r);
+            const int j = 32 * quarter + lane;
+            const float o0 = __uint_as_float(r[0]) + c2[0], o1 = __uint_as_float(r[1]) + c2[1];
             os[2 * j] = o0;
             os[2 * j + 1] = o1;
-            long long ks = (long long)kTS * t + j;
+            const long long ks = (long long)kTS * t + j;
             if (soft && ks < 64LL * nwin) soft[ks] = make_float2(o0, o1);
         }
+        tc_fence_before();
         __syncthreads();
         // decisions and window records: warp w < kWinT takes window kWinT t + w
         if (warp < kWinT && kWinT * t + warp < nwin) {
