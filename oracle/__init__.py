@@ -29,7 +29,7 @@ class OrxCfg(C.Structure):
         ("ncma", C.c_int32), ("eq_block", C.c_int32), ("win", C.c_int32),
         ("mu", C.c_double), ("mu_train", C.c_double), ("mu_cma", C.c_double),
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
-        ("eq_frozen", C.c_int32),
+        ("eq_frozen", C.c_int32), ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
     ]
 
 
@@ -67,6 +67,10 @@ def lib():
         L.orx_hilbert_circ.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
         L.orx_kk_circ.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         L.orx_rrc.argtypes = [C.c_double, C.c_int, C.c_int, C.c_void_p]
+        L.orx_rrc_half.argtypes = [C.c_double, C.c_int, C.c_int, C.c_void_p]
+        L.orx_fd_response.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+        L.orx_fd_block.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]
         L.orx_prbs15.argtypes = [C.c_uint32, C.c_int64, C.c_void_p]
         L.orx_q_db.argtypes = [C.c_double]
         L.orx_q_db.restype = C.c_double
@@ -128,6 +132,32 @@ def rrc(beta: float, sps: int, span: int) -> np.ndarray:
     return h
 
 
+def rrc_half(beta: float, sps: int, half: int) -> np.ndarray:
+    h = np.zeros(2 * half + 1)
+    lib().orx_rrc_half(beta, sps, half, _ptr(h))
+    return h
+
+
+def fd_response(h: np.ndarray, n: int) -> np.ndarray:
+    """H_k = sum_i h_i e^{-2 pi i k i / n}, taps i = -(L-1)/2 .. (L-1)/2."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    re, im = np.zeros(n), np.zeros(n)
+    lib().orx_fd_response(_ptr(h), len(h), n, _ptr(re), _ptr(im))
+    return re + 1j * im
+
+
+def fd_block(x: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """One frequency-domain block with bin-truncation downsampling: N inputs -> N/4 outputs."""
+    n = len(x)
+    xr = np.ascontiguousarray(np.real(x), dtype=np.float64)
+    xi = np.ascontiguousarray(np.imag(x), dtype=np.float64)
+    Hr = np.ascontiguousarray(np.real(H), dtype=np.float64)
+    Hi = np.ascontiguousarray(np.imag(H), dtype=np.float64)
+    yr, yi = np.zeros(n // 4), np.zeros(n // 4)
+    lib().orx_fd_block(_ptr(xr), _ptr(xi), n, _ptr(Hr), _ptr(Hi), _ptr(yr), _ptr(yi))
+    return yr + 1j * yi
+
+
 def prbs15(seed: int, nbits: int) -> np.ndarray:
     out = np.zeros(nbits, dtype=np.uint8)
     lib().orx_prbs15(seed, nbits, _ptr(out))
@@ -184,10 +214,11 @@ def cnn_param_slices():
 KK_DEFAULTS = dict(sps=4, pack_order=0, ols_n=65536, ols_v=4096, ds_num=11, ds_den=80,
                    rrc_beta=0.1, mf_span=16, ntaps=31, ntrain=16384, ncma=8192, eq_block=256,
                    win=64, mu=1e-3, mu_train=1e-3, mu_cma=1e-3, bps_b=32, amb_syms=1024,
-                   prbs_seed=1, eq_frozen=0)
+                   prbs_seed=1, eq_frozen=0, mf_mode=0, fd_n=1024, fd_taps=203)
 PAM_DEFAULTS = dict(sps=2, pack_order=0, ols_n=0, ols_v=0, ds_num=0, ds_den=1, rrc_beta=0.1,
                     mf_span=16, ntaps=15, ntrain=4096, ncma=0, eq_block=256, win=64, mu=1e-3,
-                    mu_train=1e-3, mu_cma=0.0, bps_b=1, amb_syms=0, prbs_seed=1, eq_frozen=0)
+                    mu_train=1e-3, mu_cma=0.0, bps_b=1, amb_syms=0, prbs_seed=1, eq_frozen=0, mf_mode=0,
+                    fd_n=1024, fd_taps=203)
 
 
 def default_cfg(fmt: int, buf_len: int, **kw) -> dict:

@@ -136,9 +136,12 @@ void orx_kk_circ(const double *intensity, double *e_re, double *e_im, int n)
 }
 
 /* Root-raised cosine, sps*span+1 taps, unit energy, zero phase. */
-void orx_rrc(double beta, int sps, int span, double *taps)
+void orx_rrc(double beta, int sps, int span, double *taps) { orx_rrc_half(beta, sps, sps * span / 2, taps); }
+
+/* The same pulse with 2*half+1 taps (any half-length). */
+void orx_rrc_half(double beta, int sps, int half, double *taps)
 {
-    int half = sps * span / 2, n = 2 * half + 1;
+    int n = 2 * half + 1;
     double e = 0.0;
     for (int i = 0; i < n; i++) {
         double t = (double)(i - half) / (double)sps, v;
@@ -155,6 +158,55 @@ void orx_rrc(double beta, int sps, int span, double *taps)
     }
     e = 1.0 / sqrt(e);
     for (int i = 0; i < n; i++) taps[i] *= e;
+}
+
+/* ------------------------------------------- frequency-domain filtering
+ * The paper's static equaliser runs in the frequency domain on overlap-save
+ * blocks of a 1024-point FFT, and a 512-point IFFT brings the signal to 2
+ * samples per symbol (Sec. 2, KK chain).  Readings: "100% overlap" is a hop of
+ * N/2 (8192 blocks per 2^22-sample buffer); the filter is zero-phase and its
+ * response is H_k = sum_i h_i e^{-2 pi i k i / N} over the taps i = -(L-1)/2 ..
+ * (L-1)/2; the downsampler keeps the bins -N/4 <= k < N/4 (bin k goes to
+ * position k mod N/2 of the half-length spectrum); block b takes the N inputs
+ * starting at stream index hop*b - N/4 and keeps its central half. */
+void orx_fd_response(const double *h, int ntaps, int n, double *H_re, double *H_im)
+{
+    int half = (ntaps - 1) / 2;
+    for (int k = 0; k < n; k++) {
+        double re = 0.0, im = 0.0;
+        for (int i = -half; i <= half; i++) {
+            double a = -2.0 * PI * (double)(((int64_t)k * i) % n) / (double)n;
+            re += h[i + half] * cos(a);
+            im += h[i + half] * sin(a);
+        }
+        H_re[k] = re;
+        H_im[k] = im;
+    }
+}
+
+/* One block: X = FFT_N(x); Z_{k mod N/2} = X_k H_k for -N/4 <= k < N/4;
+ * z_m = (1/N) sum_k' Z_k' e^{+2 pi i k' m / (N/2)}, which for a block with no
+ * energy outside those bins is the circular convolution of x with h at the even
+ * index 2m; y = z_m for m in [N/8, 3N/8) (N/4 outputs). */
+void orx_fd_block(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
+                  double *y_re, double *y_im)
+{
+    int m2 = n / 2;
+    double *re = xcalloc((size_t)n, sizeof(double)), *im = xcalloc((size_t)n, sizeof(double));
+    double *zr = xcalloc((size_t)m2, sizeof(double)), *zi = xcalloc((size_t)m2, sizeof(double));
+    for (int i = 0; i < n; i++) { re[i] = x_re[i]; im[i] = x_im[i]; }
+    orx_fft(re, im, n, 0);
+    for (int kp = 0; kp < m2; kp++) {
+        int k = kp < n / 4 ? kp : kp + m2;
+        zr[kp] = re[k] * H_re[k] - im[k] * H_im[k];
+        zi[kp] = re[k] * H_im[k] + im[k] * H_re[k];
+    }
+    orx_fft(zr, zi, m2, 1);          /* includes 1/(N/2) */
+    for (int m = n / 8; m < 3 * n / 8; m++) {
+        y_re[m - n / 8] = 0.5 * zr[m];
+        y_im[m - n / 8] = 0.5 * zi[m];
+    }
+    free(re); free(im); free(zr); free(zi);
 }
 
 /* PRBS-15, Fibonacci LFSR x^15 + x^14 + 1; register loaded with
@@ -196,6 +248,8 @@ struct orx {
     cx *yhist; int64_t yhist_start, yhist_len;
     cx carrier; double gain;
     cx *w;                         /* taps every block of the next call starts from */
+    int fd;                        /* frequency-domain reduction to 2 samples/symbol */
+    double *fd_Hr, *fd_Hi;         /* its filter response, fd_n bins */
     int trained;
     int have_b, b_last; int64_t m_last;
     int amb_done, amb_r;
@@ -218,7 +272,10 @@ orx *orx_create(const orx_cfg *cfg)
         cfg->buf_len < 2 || (cfg->buf_len & 1) || cfg->sps < 2 || (cfg->sps & 1) || cfg->mf_span < 0 ||
         (f >= 3 && (cfg->ncma < 0 || cfg->ncma > cfg->ntrain || cfg->ncma % cfg->win || cfg->bps_b < 1 ||
                     cfg->ds_den < 1 || cfg->ols_n < 4 || (cfg->ols_n & (cfg->ols_n - 1)) ||
-                    cfg->ols_v < 2 || (cfg->ols_v & 1) || cfg->ols_v >= cfg->ols_n))) {
+                    cfg->ols_v < 2 || (cfg->ols_v & 1) || cfg->ols_v >= cfg->ols_n)) ||
+        cfg->mf_mode < 0 || cfg->mf_mode > 1 ||
+        (cfg->mf_mode == 1 && (f < 3 || cfg->sps != 4 || cfg->fd_n < 16 || (cfg->fd_n & (cfg->fd_n - 1)) ||
+                               cfg->fd_taps < 1 || !(cfg->fd_taps & 1) || cfg->fd_taps > cfg->fd_n / 2 + 1))) {
         free(h);
         return NULL;
     }
@@ -241,6 +298,15 @@ orx *orx_create(const orx_cfg *cfg)
     h->th = (cfg->ntaps - 1) / 2;
     h->rrc = xcalloc((size_t)(2 * h->hmf + 1), sizeof(double));
     orx_rrc(cfg->rrc_beta, cfg->sps, cfg->mf_span, h->rrc);
+    h->fd = cfg->mf_mode == 1;
+    if (h->fd) {
+        double *hf = xcalloc((size_t)cfg->fd_taps, sizeof(double));
+        orx_rrc_half(cfg->rrc_beta, cfg->sps, (cfg->fd_taps - 1) / 2, hf);
+        h->fd_Hr = xcalloc((size_t)cfg->fd_n, sizeof(double));
+        h->fd_Hi = xcalloc((size_t)cfg->fd_n, sizeof(double));
+        orx_fd_response(hf, cfg->fd_taps, cfg->fd_n, h->fd_Hr, h->fd_Hi);
+        free(hf);
+    }
     h->prbs = xcalloc(32767, 1);
     orx_prbs15(cfg->prbs_seed, 32767, h->prbs);
     h->chist_cap = h->kk ? cfg->ols_n : 2 * h->hmf;
@@ -442,6 +508,11 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
     int64_t e_k = h->kk ? avail - c->ols_v / 2 : avail;
     if (e_k < 0) e_k = 0;
     int64_t f_k = (e_k >= h->hmf + 1) ? (e_k - h->hmf - 1) / h->dec + 1 : 0;
+    if (h->fd) {   /* whole blocks: block b needs the inputs up to hop*b + 3N/4 */
+        int64_t N = c->fd_n, hop = N / 2;
+        int64_t bk = (e_k >= 3 * N / 4) ? (e_k - 3 * N / 4) / hop + 1 : 0;
+        f_k = bk * (hop / 2);
+    }
     int64_t s_k = (f_k >= h->th + 1) ? (f_k - h->th - 1) / 2 + 1 : 0;
     int64_t q_k = (s_k >= c->ntrain) ? c->ntrain + ((s_k - c->ntrain) / c->eq_block) * c->eq_block : 0;
     if (q_k < h->q_prev) q_k = h->q_prev;
@@ -490,7 +561,29 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
     /* ---- matched filter (and 4 -> 2 samples/symbol for KK) ------------- */
     X.y_start = h->f_prev; X.y_len = f_k - h->f_prev;
     X.y = xcalloc((size_t)(X.y_len > 0 ? X.y_len : 1), sizeof(cx));
-    for (int64_t m = h->f_prev; m < f_k; m++) {
+    if (h->fd) {
+        /* static frequency-domain filter, N-point blocks with hop N/2, bin-truncation
+         * downsampling; the block input is the carrier-removed, downshifted field */
+        int N = c->fd_n, hop = N / 2;
+        double *xr = xcalloc((size_t)N, sizeof(double)), *xi = xcalloc((size_t)N, sizeof(double));
+        double *yr = xcalloc((size_t)(N / 4), sizeof(double)), *yi = xcalloc((size_t)(N / 4), sizeof(double));
+        for (int64_t b = h->f_prev / (hop / 2); b < f_k / (hop / 2); b++) {
+            for (int t = 0; t < N; t++) {
+                int64_t n = (int64_t)hop * b - N / 4 + t;
+                cx xn = cx_mk(0.0, 0.0);
+                if (n >= 0) {
+                    int64_t p = ((n % c->ds_den) * c->ds_num) % c->ds_den;
+                    xn = cx_mul(cx_sub(e_at(&X, n), h->carrier), cx_expj(-2.0 * PI * (double)p / (double)c->ds_den));
+                }
+                xr[t] = xn.re; xi[t] = xn.im;
+            }
+            orx_fd_block(xr, xi, N, h->fd_Hr, h->fd_Hi, yr, yi);
+            for (int m = 0; m < N / 4; m++)
+                X.y[(int64_t)(hop / 2) * b + m - X.y_start] = cx_scale(cx_mk(yr[m], yi[m]), h->gain);
+        }
+        free(xr); free(xi); free(yr); free(yi);
+    }
+    for (int64_t m = h->fd ? f_k : h->f_prev; m < f_k; m++) {
         cx acc = cx_mk(0.0, 0.0);
         for (int i = -h->hmf; i <= h->hmf; i++) {
             int64_t n = (int64_t)h->dec * m - i;
@@ -691,7 +784,7 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
 
     /* ---- carry the stream state to the next buffer ----------------------- */
     if (h->kk && e_k > 0) {
-        int64_t lo = (int64_t)h->dec * f_k - h->hmf;
+        int64_t lo = h->fd ? (int64_t)h->dec * f_k - c->fd_n / 4 : (int64_t)h->dec * f_k - h->hmf;
         if (lo < 0) lo = 0;
         cx *nh = xcalloc((size_t)(e_k - lo + 1), sizeof(cx));
         for (int64_t n = lo; n < e_k; n++) nh[n - lo] = e_at(&X, n);
@@ -757,6 +850,7 @@ void orx_destroy(orx *h)
 {
     if (!h) return;
     free(h->rrc); free(h->prbs); free(h->chist); free(h->ehist); free(h->yhist); free(h->w);
+    free(h->fd_Hr); free(h->fd_Hi);
     free(h->d_E); free(h->d_y); free(h->d_z); free(h->d_v); free(h->d_ahat);
     free(h->d_draw); free(h->d_berr); free(h->d_near); free(h->d_win);
     free(h);
