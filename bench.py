@@ -370,6 +370,9 @@ def gpu_arm(args, rank, world, local):
     prec_line = None
     if rank == 0 and not args.no_precision:
         prec_line = precision_leg(args, g, ring)
+    fd_line = None
+    if rank == 0 and not args.no_fd:
+        fd_line = fd_leg(args, g, ring)
     batched_line = None
     if rank == 0 and not args.no_batched:
         batched_line = batched_leg(args)
@@ -383,7 +386,7 @@ def gpu_arm(args, rank, world, local):
             "e2e": {"value": e2e_value, "unit": "GSa/s", "h2d_bytes_per_step": h2d // e2e_steps,
                     "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
             "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line, "precision": prec_line,
-            "batched": batched_line,
+            "fd_filter": fd_line, "batched": batched_line,
             "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
             "realtime_x": value / 4.0,
             "ber": cpu["ber_gpu_same_buffers"] if cpu else None,
@@ -544,6 +547,53 @@ def precision_leg(args, g, ring):
             "sample": f"soft symbols and BER on the first {nref} buffers; throughput over the {len(ring)}-buffer ring x 2"}
 
 
+def fd_leg(args, g, ring):
+    """The paper's form of the reduction to 2 samples/symbol (Sec. 2): a static
+    203-tap filter in the frequency domain on 1024-point overlap-save blocks (hop
+    512, 8192 blocks per buffer) with a 512-point bin-truncation inverse, in place
+    of the 65-tap time-domain matched filter.  Receiver throughput over the ring,
+    the filter stage time, and the 2-sps samples and BER against the FP64 oracle
+    in the same form on the first two buffers."""
+    import torch
+    import oracle
+    import paper_2010_14333_gb300 as rx
+    nref = 2
+    o = oracle.Oracle(**oracle.default_cfg(FMT, NB, mf_mode=1))
+    d = rx.Receiver(FMT, NB, mf_mode=1, debug=1)
+    num = den = 0.0
+    for b in range(nref):
+        o.process(g["packed"][b])
+        d.process(ring[b])
+        y, y0 = d.debug(rx.RX_DBG_MF)
+        yo, yo0 = o.get(oracle.ORX_Y)
+        if len(y) and (y0, len(y)) == (yo0, len(yo)):
+            num += float(np.sum(np.abs(y - yo) ** 2))
+            den += float(np.sum(np.abs(yo) ** 2))
+    sd, so = d.stats(), o.stats()
+    del d
+    out = {"fd_n": 1024, "fd_taps": 203, "y_rel_rms_vs_oracle": (num / den) ** 0.5 if den else None,
+           "ber": sd["ber"], "ber_oracle": so["ber"], "bits": sd["bits"]}
+    for mode in (1, 0):
+        r = rx.Receiver(FMT, NB, mf_mode=mode)
+        for _ in range(2):
+            r.process_batch(ring)
+        torch.cuda.synchronize()
+        rx.rx_profile(r.h, 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            r.process_batch(ring)
+        e1.record()
+        torch.cuda.synchronize()
+        ms, calls = rx.rx_profile_read(r.h)
+        rx.rx_profile(r.h, 0)
+        key = "frequency_domain" if mode else "time_domain_65_taps"
+        out[key] = {"gsa_s": 2 * len(ring) * NB / (e0.elapsed_time(e1) * 1e-3) / 1e9,
+                    "filter_us_per_buffer": ms["mf"] / max(calls, 1) * 1e3}
+        del r
+    return out
+
+
 def _gen_member(job):
     """One member stream of the batched workload (runs in a spawned worker)."""
     import synth
@@ -665,6 +715,7 @@ def main():
     ap.add_argument("--no-cnn", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-fd", action="store_true")
     ap.add_argument("--batched-streams", type=int, default=64)
     ap.add_argument("--batched-rounds", type=int, default=10)
     ap.add_argument("--latency-reps", type=int, default=300)

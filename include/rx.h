@@ -92,7 +92,19 @@ typedef struct {
                             1 = one thread-block-cluster kernel holding each block pair
                             in distributed shared memory.  Ignored for ols_n = 4096.      */
     int32_t eq_warps;    /* equaliser blocks (warps) per CTA: 0 = default (4), 2, 4 or 8   */
+    int32_t mf_mode;     /* KK reduction to 2 samples/symbol (rx_mf_mode): RX_MF_TIME = the
+                            time-domain matched filter of mf_span symbols (default);
+                            RX_MF_FD = the static filter applied in the frequency domain on
+                            overlap-save blocks of fd_n samples (hop fd_n/2) with an
+                            fd_n/2-point inverse of the bins |k| < fd_n/4 as downsampler
+                            (Sec. 2: FD equaliser on a 1024-point FFT, 512-point IFFT) */
+    int32_t fd_n;        /* RX_MF_FD block length: power of two, 16 .. 1024; default 1024  */
+    int32_t fd_taps;     /* RX_MF_FD filter taps (root-raised cosine, zero phase, unit
+                            energy): odd, <= fd_n/2 + 1; default 203                       */
 } rx_config;
+
+/* Reduction to 2 samples/symbol of the KK chain (rx_config.mf_mode). */
+typedef enum { RX_MF_TIME = 0, RX_MF_FD = 1 } rx_mf_mode;
 
 /* Equaliser forms and precisions (rx_config.fir_prec). */
 typedef enum {

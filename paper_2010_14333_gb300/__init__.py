@@ -31,6 +31,7 @@ class RxConfig(C.Structure):
         ("mu", C.c_double), ("mu_train", C.c_double), ("mu_cma", C.c_double),
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
         ("debug", C.c_int32), ("fir_prec", C.c_int32), ("kk_front", C.c_int32), ("eq_warps", C.c_int32),
+        ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
     ]
 
 
@@ -56,6 +57,7 @@ EXPORTED = sorted(["rx_default_config", "rx_create", "rx_process", "rx_process_h
                    "rx_process_host_batch", "rx_fir_block", "rx_group_create", "rx_group_process",
                    "rx_group_tuning", "rx_group_destroy"])
 RX_GROUP_GRAPH, RX_GROUP_TUNE = 1, 2
+RX_MF_TIME, RX_MF_FD = 0, 1
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
 
 _lib = None

@@ -74,6 +74,8 @@ struct rx_handle {
     uint8_t *in_stage[2], *bits_stage;   // device staging of the host-buffer entry points
     float2 *zbuf;                   // payload soft symbols of the tensor-core FIR forms
     float2 *gpart;                  // frozen forms: tap-gradient partials, one row of 32 per window
+    int fd;                         // frequency-domain reduction to 2 samples/symbol
+    float2 *fd_H, *fd_tw;           // its kept-bin response (times 1/N) and N-point twiddles
     long long dec_cap, win_cap, y_cap;
     int nsm;                        // SMs of the handle's device
     // stage timing: a ring of event sets, one per profiled call
@@ -139,10 +141,13 @@ static void prof_harvest_one(rx_handle *h)
 
 // ---------------------------------------------------------------- host tables
 // Root-raised cosine, sps*span+1 taps, unit energy, zero phase (textbook form).
-static void rrc_taps(double beta, int sps, int span, double *h)
+static void rrc_half(double beta, int sps, int half, double *h);
+static void rrc_taps(double beta, int sps, int span, double *h) { rrc_half(beta, sps, sps * span / 2, h); }
+// the same pulse with 2 half + 1 taps
+static void rrc_half(double beta, int sps, int half, double *h)
 {
     const double pi = 3.14159265358979323846;
-    int half = sps * span / 2, n = 2 * half + 1;
+    int n = 2 * half + 1;
     double e = 0;
     for (int i = 0; i < n; i++) {
         double t = (double)(i - half) / sps, v;
@@ -191,6 +196,10 @@ static Sched schedule(const rx_handle *h, long long calls, long long q_prev)
     s.e_k = h->kk ? s.avail - h->V / 2 : s.avail;
     if (s.e_k < 0) s.e_k = 0;
     s.f_k = (s.e_k >= h->hmf + 1) ? (s.e_k - h->hmf - 1) / h->decim + 1 : 0;
+    if (h->fd) {   // whole frequency-domain blocks: block b reads up to N/2 b + 3N/4
+        long long N = h->cfg.fd_n, bk = (s.e_k >= 3 * N / 4) ? (s.e_k - 3 * N / 4) / (N / 2) + 1 : 0;
+        s.f_k = bk * (N / 4);
+    }
     s.s_k = (s.f_k >= h->th + 1) ? (s.f_k - h->th - 1) / 2 + 1 : 0;
     long long nt = h->cfg.ntrain, B = h->cfg.eq_block;
     s.q_k = (s.s_k >= nt) ? nt + ((s.s_k - nt) / B) * B : 0;
@@ -238,6 +247,9 @@ rx_status rx_default_config(rx_format f, rx_config *c)
     c->amb_syms = kk ? 1024 : 0;
     c->prbs_seed = 1;
     c->debug = 0;
+    c->mf_mode = RX_MF_TIME;
+    c->fd_n = 1024;
+    c->fd_taps = 203;
     return RX_OK;
 }
 
@@ -258,7 +270,7 @@ void rx_destroy(rx_handle *h)
     if (h->copy) cudaStreamSynchronize(h->copy);
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->partials, h->prbs, h->taps[0], h->taps[1], h->twN,
                     h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
-                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->zbuf, h->gpart};
+                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->zbuf, h->gpart, h->fd_H, h->fd_tw};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kSlots; i++) {
@@ -322,6 +334,10 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         return RX_EINVAL;
     if (c.kk_front < 0 || c.kk_front > 1 || !(c.eq_warps == 0 || c.eq_warps == 2 || c.eq_warps == 4 || c.eq_warps == 8))
         return RX_EINVAL;
+    if (c.mf_mode < RX_MF_TIME || c.mf_mode > RX_MF_FD ||
+        (c.mf_mode == RX_MF_FD && (!kk || c.fd_n < 16 || c.fd_n > kEHist || (c.fd_n & (c.fd_n - 1)) ||
+                                   c.fd_taps < 1 || !(c.fd_taps & 1) || c.fd_taps > c.fd_n / 2 + 1)))
+        return RX_EINVAL;
     if (kk && (c.ncma < 0 || c.ncma > c.ntrain || c.ncma % kWin || c.bps_b < 1 || c.bps_b > 32 ||
                c.ds_den < 1 || c.ds_num < 0 || c.amb_syms < 0 || c.amb_syms % kWin || c.amb_syms > 4096 ||
                !(c.ols_n == 4096 || c.ols_n == 65536) || c.ols_v < 64 || c.ols_v % 64 || c.ols_v >= c.ols_n))
@@ -335,6 +351,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     h->sps = sps;
     h->decim = sps / 2;
     h->hmf = sps * c.mf_span / 2;
+    h->fd = c.mf_mode == RX_MF_FD;
     h->th = (c.ntaps - 1) / 2;
     h->nb = buf_len;
     h->cfg = c;
@@ -468,6 +485,33 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         twiddles(c.ds_den, ds);      // e^{-2 pi i p / den}
         if (e == cudaSuccess) e = cudaMemcpy(h->ds_tab, ds, sizeof(float2) * c.ds_den, cudaMemcpyHostToDevice);
         free(ds);
+    }
+    if (h->fd) {
+        // frequency-domain filter: response of the zero-phase taps at the kept bins
+        // (k' < N/4 -> k = k', else k = k' + N/2), times 1/N; N-point twiddles
+        const double pi = 3.14159265358979323846;
+        const int N = c.fd_n, half = (c.fd_taps - 1) / 2;
+        double *hf = (double *)malloc(sizeof(double) * c.fd_taps);
+        float2 *Hk = (float2 *)malloc(sizeof(float2) * N / 2), *tw = (float2 *)malloc(sizeof(float2) * N);
+        rrc_half(c.rrc_beta, sps, half, hf);
+        for (int kp = 0; kp < N / 2; kp++) {
+            int k = kp < N / 4 ? kp : kp + N / 2;
+            double re = 0, im = 0;
+            for (int i = -half; i <= half; i++) {
+                double a = -2.0 * pi * (double)(((long long)k * i) % N) / N;
+                re += hf[i + half] * cos(a);
+                im += hf[i + half] * sin(a);
+            }
+            Hk[kp] = make_float2((float)(re / N), (float)(im / N));
+        }
+        twiddles(N, tw);
+        if (e == cudaSuccess) e = cudaMalloc(&h->fd_H, sizeof(float2) * N / 2);
+        if (e == cudaSuccess) e = cudaMalloc(&h->fd_tw, sizeof(float2) * N);
+        if (e == cudaSuccess) e = cudaMemcpy(h->fd_H, Hk, sizeof(float2) * N / 2, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->fd_tw, tw, sizeof(float2) * N, cudaMemcpyHostToDevice);
+        free(hf);
+        free(Hk);
+        free(tw);
     }
     DevState s0;
     memset(&s0, 0, sizeof s0);
@@ -629,7 +673,11 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         long long yb = 2 * h->q_prev - kYHist;
         int yw_new = (h->yw + 1) % kSlots;
         if (two) cudaStreamWaitEvent(sm, h->ev_yfree[yw_new], 0);   // the back end is done with this slot
-        if (h->kk)
+        if (h->kk && h->fd)
+            e = launch_kk_fdmf(h->E[h->ew], h->ebase_cur, h->f_prev, s.f_k, c.fd_n, h->fd_H, h->fd_tw, h->ds_tab,
+                               c.ds_num, c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb,
+                               (const float2 *)h->Y[h->yw], h->ybase_cur, sm);
+        else if (h->kk)
             e = launch_kk_mf(h->E[h->ew], h->ebase_cur, s.e_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
                              c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw],
                              h->ybase_cur, sm, h->rrc_host);

@@ -1019,6 +1019,260 @@ cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long l
     return cudaGetLastError();
 }
 
+// ============================================ frequency-domain reduction (KK)
+// The paper's form of the filter before the equaliser (Sec. 2, KK chain): a
+// static filter applied in the frequency domain on overlap-save blocks of N =
+// fd_n samples with hop N/2, and an N/2-point inverse transform of the kept bins
+// -N/4 <= k < N/4 as the downsampler to 2 samples/symbol.  One CTA per block b:
+//   - the N inputs from stream index N/2 b - N/4 (carrier removed, downshifted by
+//     the exact integer phase; zero before the stream start) are staged in
+//     shared memory;
+//   - a radix-4 Stockham FFT (natural order in and out, two ping-pong buffers,
+//     a last radix-2 pass when log2 N is odd) transforms them;
+//   - the kept bins times the filter response (pre-scaled by 1/N) form the
+//     N/2-point spectrum, which the inverse Stockham FFT brings back;
+//   - the central half, N/4 outputs, leaves at 2 samples/symbol times the gain.
+constexpr int kFdThreads = 128;
+
+// Stockham passes of an n-point transform (n = N or N/2) on shared buffers a, b;
+// tw is the N-point table e^{-2 pi i t / N}; returns the buffer with the result
+template <bool INV>
+__device__ float2 *stockham(float2 *a, float2 *b, int n, int N, const float2 *__restrict__ tw)
+{
+    int ns = 1;
+    for (; ns * 4 <= n; ns *= 4) {
+        const int q4 = n >> 2, ts = N / (4 * ns);
+        for (int j = threadIdx.x; j < q4; j += blockDim.x) {
+            const int k = j & (ns - 1);
+            float2 v0 = a[j], v1 = a[j + q4], v2 = a[j + 2 * q4], v3 = a[j + 3 * q4];
+            if (ns > 1) {
+                float2 w1 = __ldg(tw + k * ts), w2 = __ldg(tw + 2 * k * ts), w3 = __ldg(tw + 3 * k * ts);
+                if (INV) {
+                    w1 = cconj(w1);
+                    w2 = cconj(w2);
+                    w3 = cconj(w3);
+                }
+                v1 = cmul(v1, w1);
+                v2 = cmul(v2, w2);
+                v3 = cmul(v3, w3);
+            }
+            dft4<INV>(v0, v1, v2, v3);
+            const int o = ((j - k) << 2) + k;
+            b[o] = v0;
+            b[o + ns] = v1;
+            b[o + 2 * ns] = v2;
+            b[o + 3 * ns] = v3;
+        }
+        __syncthreads();
+        float2 *t = a;
+        a = b;
+        b = t;
+    }
+    if (ns < n) {   // one radix-2 pass
+        const int h2 = n >> 1, ts = N / (2 * ns);
+        for (int j = threadIdx.x; j < h2; j += blockDim.x) {
+            const int k = j & (ns - 1);
+            float2 w = __ldg(tw + k * ts);
+            if (INV) w = cconj(w);
+            const float2 v0 = a[j], v1 = cmul(a[j + h2], w);
+            const int o = ((j - k) << 1) + k;
+            b[o] = cadd(v0, v1);
+            b[o + ns] = csub(v0, v1);
+        }
+        __syncthreads();
+        a = b;
+    }
+    return a;
+}
+
+__global__ void __launch_bounds__(kFdThreads) k_kk_fdmf(const float2 *__restrict__ E, long long ebase,
+                                                       long long b_first, int N, const float2 *__restrict__ H,
+                                                       const float2 *__restrict__ tw,
+                                                       const float2 *__restrict__ ds_tab, int ds_num, int ds_den,
+                                                       const double *__restrict__ cg, float2 *__restrict__ Y,
+                                                       long long ybase, long long f_prev,
+                                                       const float2 *__restrict__ Y_prev, long long ybase_prev)
+{
+    extern __shared__ float2 fbuf[];   // [2][N]
+    float2 *a = fbuf, *b = fbuf + N;
+    const long long blk = b_first + blockIdx.x;
+    const long long n0 = (N / 2) * blk - N / 4;   // stream index of the block's first input
+    const float2 c = make_float2((float)cg[0], (float)cg[1]);
+    const float gn = (float)cg[2];
+    // integer phase index of the downshift: p(n) = n ds_num mod ds_den, advanced by the thread stride
+    long long r0 = (n0 + threadIdx.x) % ds_den;
+    if (r0 < 0) r0 += ds_den;
+    int p = (int)((r0 * ds_num) % ds_den);
+    const int step = (int)(((long long)kFdThreads * ds_num) % ds_den);
+    for (int t = threadIdx.x; t < N; t += kFdThreads) {
+        const long long n = n0 + t;
+        a[t] = n < 0 ? make_float2(0.f, 0.f) : cmul(csub(E[n - ebase], c), __ldg(ds_tab + p));
+        p += step;
+        p = p >= ds_den ? p - ds_den : p;
+    }
+    if (blockIdx.x == 0)
+        for (long long m = ybase + threadIdx.x; m < f_prev; m += kFdThreads)
+            Y[m - ybase] = (m < 0) ? make_float2(0.f, 0.f) : Y_prev[m - ybase_prev];
+    __syncthreads();
+    float2 *X = stockham<false>(a, b, N, N, tw);
+    float2 *Z = X == a ? b : a;
+    const int half = N >> 1, q = N >> 2;
+    for (int kp = threadIdx.x; kp < half; kp += kFdThreads) Z[kp] = cmul(X[kp < q ? kp : kp + half], __ldg(H + kp));
+    __syncthreads();
+    float2 *z = stockham<true>(Z, X, half, N, tw);
+    const long long s0 = (long long)(N / 4) * blk - ybase;   // 2-sps index of the block's first output
+    for (int m = threadIdx.x; m < q; m += kFdThreads) Y[s0 + m] = cscale(z[m + N / 8], gn);
+}
+
+// W32^k = e^{-2 pi i k / 32} for k = 0..15 (cos and sin of pi k / 16)
+__device__ __forceinline__ float2 w32(int k)
+{
+    switch (k) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(0.98078528040323043f, -0.19509032201612825f);
+    case 2: return make_float2(0.92387953251128674f, -0.38268343236508978f);
+    case 3: return make_float2(0.83146961230254524f, -0.55557023301960218f);
+    case 4: return make_float2(0.70710678118654752f, -0.70710678118654752f);
+    case 5: return make_float2(0.55557023301960218f, -0.83146961230254524f);
+    case 6: return make_float2(0.38268343236508978f, -0.92387953251128674f);
+    case 7: return make_float2(0.19509032201612825f, -0.98078528040323043f);
+    case 8: return make_float2(0.f, -1.f);
+    case 9: return make_float2(-0.19509032201612825f, -0.98078528040323043f);
+    case 10: return make_float2(-0.38268343236508978f, -0.92387953251128674f);
+    case 11: return make_float2(-0.55557023301960218f, -0.83146961230254524f);
+    case 12: return make_float2(-0.70710678118654752f, -0.70710678118654752f);
+    case 13: return make_float2(-0.83146961230254524f, -0.55557023301960218f);
+    case 14: return make_float2(-0.92387953251128674f, -0.38268343236508978f);
+    default: return make_float2(-0.98078528040323043f, -0.19509032201612825f);   // k = 15
+    }
+}
+
+// 32-point DFT in registers, natural order in and out, unscaled: two 16-point
+// DFTs over the even and odd samples and one radix-2 combination
+template <bool INV>
+__device__ __forceinline__ void dft32(float2 (&x)[32])
+{
+    float2 e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        e[i] = x[2 * i];
+        o[i] = x[2 * i + 1];
+    }
+    dft16<INV>(e);
+    dft16<INV>(o);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        float2 w = w32(k);
+        if (INV) w.y = -w.y;
+        const float2 t = cmul(o[k], w);
+        x[k] = cadd(e[k], t);
+        x[k + 16] = csub(e[k], t);
+    }
+}
+
+// The 1024-point form, one warp per block, as a 32 x 32 four-step transform with
+// n = lane + 32 q and k = k2 + 32 k1:
+//   forward: 32-point DFTs over q in registers, twiddle W1024^(lane k2), a padded
+//     shared-memory transpose, 32-point DFTs over the former lane index: lane k2
+//     then holds the bins k2 + 32 k1;
+//   the kept bins (k1 < 8 or k1 >= 24) times the response give the 512-point
+//     spectrum at k' = lane + 32 j (j = k1, or k1 - 16);
+//   inverse with m = m_a + 16 m_b: 16-point inverse DFTs over j in registers,
+//     twiddle e^{+2 pi i lane m_a / 512}, a transpose, then per m_a the inverse
+//     32-point DFT over the lanes split between a lane pair (even / odd lanes,
+//     16 points each, halves exchanged by shuffles), evaluated only at the kept
+//     outputs m_b = 8 .. 23 (m = 128 .. 383).
+constexpr int kFdWarps = 4, kFdPitch = 33;
+
+__global__ void __launch_bounds__(32 * kFdWarps, 4)
+    k_kk_fd1024(const float2 *__restrict__ E, long long ebase, long long b_first, long long nblk,
+                const float2 *__restrict__ H, const float2 *__restrict__ tw, const float2 *__restrict__ ds_tab,
+                int ds_num, int ds_den, const double *__restrict__ cg, float2 *__restrict__ Y, long long ybase,
+                long long f_prev, const float2 *__restrict__ Y_prev, long long ybase_prev)
+{
+    __shared__ float2 s_tw[1024];
+    __shared__ float2 s_t[kFdWarps][32 * kFdPitch];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_tw[i] = tw[i];
+    if (blockIdx.x == 0)
+        for (long long m = ybase + threadIdx.x; m < f_prev; m += blockDim.x)
+            Y[m - ybase] = (m < 0) ? make_float2(0.f, 0.f) : Y_prev[m - ybase_prev];
+    __syncthreads();
+    const long long bi = (long long)blockIdx.x * kFdWarps + w;
+    if (bi >= nblk) return;
+    const long long blk = b_first + bi, n0 = 512 * blk - 256;
+    const float2 c = make_float2((float)cg[0], (float)cg[1]);
+    const float gn = (float)cg[2];
+    long long r0 = (n0 + lane) % ds_den;
+    if (r0 < 0) r0 += ds_den;
+    int p = (int)((r0 * ds_num) % ds_den);
+    const int step = (int)((32LL * ds_num) % ds_den);
+    float2 x[32];
+#pragma unroll
+    for (int q = 0; q < 32; q++) {
+        const long long n = n0 + lane + 32 * q;
+        x[q] = n < 0 ? make_float2(0.f, 0.f) : cmul(csub(E[n - ebase], c), __ldg(ds_tab + p));
+        p += step;
+        p = p >= ds_den ? p - ds_den : p;
+    }
+    dft32<false>(x);
+#pragma unroll
+    for (int k2 = 1; k2 < 32; k2++) x[k2] = cmul(x[k2], s_tw[lane * k2]);
+    float2 *T = s_t[w];
+#pragma unroll
+    for (int k2 = 0; k2 < 32; k2++) T[lane * kFdPitch + k2] = x[k2];
+    __syncwarp();
+#pragma unroll
+    for (int n1 = 0; n1 < 32; n1++) x[n1] = T[n1 * kFdPitch + lane];
+    __syncwarp();
+    dft32<false>(x);
+    float2 z[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) z[j] = cmul(x[j < 8 ? j : j + 16], __ldg(H + lane + 32 * j));
+    dft16<true>(z);
+#pragma unroll
+    for (int ma = 1; ma < 16; ma++) z[ma] = cmulc(z[ma], s_tw[2 * lane * ma]);
+#pragma unroll
+    for (int ma = 0; ma < 16; ma++) T[lane * 17 + ma] = z[ma];
+    __syncwarp();
+    const int ma = lane >> 1, h = lane & 1;
+#pragma unroll
+    for (int i = 0; i < 16; i++) z[i] = T[(2 * i + h) * 17 + ma];
+    dft16<true>(z);   // h = 0: even-lane half E[r]; h = 1: odd-lane half O[r]
+    const long long s0 = 256 * blk - ybase;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        // lane h = 0 emits m_b = 8 + i (r = 8 + i), lane h = 1 emits m_b = 16 + i (r = i)
+        const float2 send = h ? z[8 + i] : z[i];
+        const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 1),
+                                         __shfl_xor_sync(0xffffffffu, send.y, 1));
+        const float2 Ev = h ? other : z[8 + i], Ov = h ? z[i] : other;
+        float2 wv = h ? w32(i) : w32(8 + i);   // e^{+2 pi i m_b / 32} = conj(W32^r), negated for m_b >= 16
+        wv.y = -wv.y;
+        if (h) wv = make_float2(-wv.x, -wv.y);
+        Y[s0 + ma + 16 * (8 * h + i)] = cscale(cadd(Ev, cmul(wv, Ov)), gn);
+    }
+}
+
+cudaError_t launch_kk_fdmf(const float2 *E, long long ebase, long long f_prev, long long f_k, int N,
+                           const float2 *H, const float2 *tw, const float2 *ds_tab, int ds_num, int ds_den,
+                           const double *cg, float2 *Y, long long ybase, const float2 *Y_prev,
+                           long long ybase_prev, cudaStream_t st)
+{
+    const int per = N / 4;   // outputs per block
+    if (N < 16 || (N & (N - 1)) || f_prev % per || f_k % per) return cudaErrorInvalidValue;
+    const long long nblk = (f_k - f_prev) / per;
+    if (nblk <= 0) return cudaSuccess;
+    if (N == 1024) {
+        k_kk_fd1024<<<(unsigned)((nblk + kFdWarps - 1) / kFdWarps), 32 * kFdWarps, 0, st>>>(
+            E, ebase, f_prev / per, nblk, H, tw, ds_tab, ds_num, ds_den, cg, Y, ybase, f_prev, Y_prev, ybase_prev);
+        return cudaGetLastError();
+    }
+    k_kk_fdmf<<<(unsigned)nblk, kFdThreads, 2 * N * sizeof(float2), st>>>(
+        E, ebase, f_prev / per, N, H, tw, ds_tab, ds_num, ds_den, cg, Y, ybase, f_prev, Y_prev, ybase_prev);
+    return cudaGetLastError();
+}
+
 // =========================================================== PAM matched filter
 // x[n] = (code[n] - mu) / sd with the buffer's exact integer moments, x[n < 0] = 0;
 // y[m] = sum_i h_i x[m - i] at 2 samples/symbol.

@@ -12,7 +12,7 @@ namespace rxk {
 constexpr int kWin = 64;          // symbols per window (one warp: two per lane)
 constexpr int kMaxTaps = 31;      // adaptive FIR taps, one per lane
 constexpr int kYHist = 16;        // 2-sps samples of equaliser history before a block
-constexpr int kEHist = 64;        // ADC samples of field history kept for the MF
+constexpr int kEHist = 1024;      // ADC samples of field history kept for the MF (>= fd_n)
 constexpr int kPamHist = 64;      // codes kept before a PAM buffer (>= 2 * MF half length)
 constexpr int kCtaK1 = 256;       // threads per K1a / K1c CTA
 constexpr int kEqWarpsMax = 8;    // most warps (equaliser blocks) per K3 CTA
@@ -120,6 +120,13 @@ cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long l
                          int ds_num, int ds_den, const double *cg, float2 *Y, long long ybase,
                          const float2 *Y_prev, long long ybase_prev, cudaStream_t st,
                          const float *rrc_host);
+
+// frequency-domain form (static filter on N-point overlap-save blocks, hop N/2,
+// N/2-point bin-truncation inverse); f_prev and f_k are multiples of N/4
+cudaError_t launch_kk_fdmf(const float2 *E, long long ebase, long long f_prev, long long f_k, int N,
+                           const float2 *H, const float2 *tw, const float2 *ds_tab, int ds_num, int ds_den,
+                           const double *cg, float2 *Y, long long ybase, const float2 *Y_prev,
+                           long long ybase_prev, cudaStream_t st);
 
 cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, long long n_end, long long f_prev,
                           long long f_k, const float *rrc, int hmf, DevState *dst, int parity,

@@ -71,6 +71,21 @@ def test_create_rejects_bad_config(field, value):
     assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
 
 
+@pytest.mark.parametrize("kw", [dict(mf_mode=2), dict(mf_mode=1, fd_n=2048), dict(mf_mode=1, fd_n=1000),
+                                dict(mf_mode=1, fd_n=8), dict(mf_mode=1, fd_taps=202),
+                                dict(mf_mode=1, fd_n=256, fd_taps=131)])
+def test_create_rejects_bad_fd_config(kw):
+    lib = rx.load()
+    c = rx.rx_default_config(rx.RX_KK_16QAM)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    h = C.c_void_p()
+    assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
+    p = rx.rx_default_config(rx.RX_PAM4)   # the frequency-domain form is the KK chain's
+    p.mf_mode = 1
+    assert lib.rx_create(rx.RX_PAM4, 2e9, 4e9, 1 << 20, C.byref(p), C.byref(h)) == 1
+
+
 def test_null_handle_calls_are_rejected():
     lib = rx.load()
     n = (C.c_int64 * 2)()
