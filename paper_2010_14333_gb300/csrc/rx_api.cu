@@ -432,7 +432,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         RX_ALLOC(h->ds_tab, c.ds_den * sizeof(float2));
     }
     RX_ALLOC(h->prbs, 32767 + 256);
-    RX_ALLOC(h->prbs_bits, 1040 * sizeof(uint32_t));
+    RX_ALLOC(h->prbs_bits, kPrbsWords * sizeof(uint32_t));
     RX_ALLOC(h->rrc, (2 * h->hmf + 1) * sizeof(float));
     RX_ALLOC(h->st, sizeof(DevState));
     for (int i = 0; i < 2; i++) RX_ALLOC(h->in_stage[i], nb * 3 / 2 + 16);
@@ -458,7 +458,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     prbs15_period(c.prbs_seed, pb);
     for (int i = 0; i < 256; i++) pb[32767 + i] = pb[i];   // one period plus its first 256 bits again
     if (e == cudaSuccess) e = cudaMemcpy(h->prbs, pb, 32767 + 256, cudaMemcpyHostToDevice);
-    uint32_t pw[1040];
+    uint32_t pw[kPrbsWords];
     memset(pw, 0, sizeof pw);
     for (int i = 0; i < 32767 + 256; i++)
         if (pb[i]) pw[i >> 5] |= 0x80000000u >> (i & 31);

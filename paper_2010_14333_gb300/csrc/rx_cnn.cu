@@ -18,6 +18,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -511,7 +513,9 @@ struct RxSmem {
     static constexpr int BH = HX + HXB;                   // half2 biases: layers 1..3 [3][16], MLP [32]
     static constexpr int C2 = BH + 80 * 4;                // float [2]: output bias
     static constexpr int OS = C2 + 16;                    // float [kTS][2]
-    static constexpr int BAR = OS + kTS * 8;              // mbarrier, TMEM slot
+    static constexpr int XS = OS + kTS * 8;               // float2 [kP0]: the next tile's input (async copy)
+    static constexpr int PRB = XS + kP0 * 8;              // uint32 [kPrbsWords]: the PRBS reference bits
+    static constexpr int BAR = PRB + kPrbsWords * 4;      // mbarrier, TMEM slot
     static constexpr int TOTAL = BAR + 64;
 };
 static_assert(kRX * 16 <= RxSmem::HXB && 8 * 128 * 16 <= RxSmem::HXB, "aliases of the HX region fit");
@@ -547,6 +551,8 @@ __global__ void __launch_bounds__(kRxThreads, 2)
     uint32_t *bh = reinterpret_cast<uint32_t *>(sm + RxSmem::BH);   // half2 bias pairs
     float *c2 = reinterpret_cast<float *>(sm + RxSmem::C2);
     float *os = reinterpret_cast<float *>(sm + RxSmem::OS);
+    float2 *xs = reinterpret_cast<float2 *>(sm + RxSmem::XS);
+    uint32_t *s_prbs = reinterpret_cast<uint32_t *>(sm + RxSmem::PRB);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + RxSmem::BAR);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quarter = warp & 3, cq = warp >> 2;
@@ -593,6 +599,16 @@ __global__ void __launch_bounds__(kRxThreads, 2)
     }
     for (int i = tid; i < 32; i += kRxThreads) bh[48 + i] = h2_bits(__floats2half2_rn(prm[OC1 + 2 * i], prm[OC1 + 2 * i + 1]));
     if (tid < 2) c2[tid] = prm[OC2 + tid];
+    for (int i = tid; i < kPrbsWords; i += kRxThreads) s_prbs[i] = prbs_bits[i];
+    // the first tile's input, copied asynchronously (zero past the stream end)
+    auto prefetch = [&](int t) {
+        if (tid < kP0) {
+            const long long g = seg_base + 2LL * kTS * t + tid;
+            cp_async8(xs + tid, g < y_end ? y + g : y, g < y_end);
+        }
+        cp_async_commit();
+    };
+    if ((int)blockIdx.x < (nwin + kWinT - 1) / kWinT) prefetch(blockIdx.x);
     // rows past the computed positions are read by the last row tiles: zero once
     for (int i = tid; i < 4 * kR1; i += kRxThreads)
         *reinterpret_cast<uint4 *>(sH1 + (i / kR1) * PL1 + (i % kR1) * 16) = make_uint4(0, 0, 0, 0);
@@ -618,35 +634,43 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         phase ^= 1u;
         return __syncthreads_and(done) != 0;
     };
-    // conv epilogue of row tile m: rows of this warp's lane quarter, channel group
-    // cq (8 channels); row -> address of its 16-byte FP16 row in the destination
-    auto conv_epi = [&](int m, int valid, const uint32_t *bias, auto dst_row) {
-        uint32_t r[8];
-        tmem_ld8(tq + 32 * m + 8 * cq, r);
-        const int row = 128 * m + 32 * quarter + lane;
-        if (row < valid) {
-            const uint4 b = *reinterpret_cast<const uint4 *>(bias + 4 * cq);
-            *reinterpret_cast<uint4 *>(dst_row(row)) =
-                make_uint4(gelu_h2(r[0], r[1], b.x), gelu_h2(r[2], r[3], b.y), gelu_h2(r[4], r[5], b.z),
-                           gelu_h2(r[6], r[7], b.w));
+    // conv epilogue of MT row tiles: rows of this warp's lane quarter, channel group
+    // cq (8 channels); every tile's accumulator load in flight before one wait;
+    // row -> address of its 16-byte FP16 row in the destination
+    auto conv_epi = [&](auto mt, int valid, const uint32_t *bias, auto dst_row) {
+        constexpr int MT = decltype(mt)::value;
+        uint32_t r[8 * MT];
+#pragma unroll
+        for (int m = 0; m < MT; m++) tmem_ld8_nw(tq + 32 * m + 8 * cq, *reinterpret_cast<uint32_t(*)[8]>(r + 8 * m));
+        tmem_wait_ld(r);
+        const uint4 b = *reinterpret_cast<const uint4 *>(bias + 4 * cq);
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+            const int row = 128 * m + 32 * quarter + lane;
+            const uint32_t *q = r + 8 * m;
+            if (row < valid)
+                *reinterpret_cast<uint4 *>(dst_row(row)) =
+                    make_uint4(gelu_h2(q[0], q[1], b.x), gelu_h2(q[2], q[3], b.y), gelu_h2(q[4], q[5], b.z),
+                               gelu_h2(q[6], q[7], b.w));
         }
     };
 
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const long long ib = seg_base + 2LL * kTS * t;   // first input of the tile
         // layer-1 input plane: row p = positions p .. p+3 (8 reals) in FP16, zero past kP0
+        cp_async_wait_all();
+        __syncthreads();   // the tile's input is in xs
         for (int p = tid; p < kRX; p += kRxThreads) {
             uint32_t w[4];
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                const long long g = ib + p + i;
-                const float2 v = (p + i < kP0 && g < y_end) ? y[g] : make_float2(0.f, 0.f);
+                const float2 v = p + i < kP0 ? xs[p + i] : make_float2(0.f, 0.f);
                 w[i] = h2_bits(__floats2half2_rn(v.x, v.y));
             }
             *reinterpret_cast<uint4 *>(sHX + p * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         fence_async_smem();
         __syncthreads();
+        if (t + (int)gridDim.x < ntiles) prefetch(t + gridDim.x);   // lands while this tile computes
         if (tid == 0) {
             tc_fence_after();
             for (int m = 0; m < kMT1; m++)
@@ -659,8 +683,7 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         }
         if (!(ok = wait_mma())) break;
         tc_fence_after();
-        for (int m = 0; m < kMT1; m++)
-            conv_epi(m, kP1, bh, [&](int row) { return sH1 + cq * PL1 + row * 16; });
+        conv_epi(std::integral_constant<int, kMT1>(), kP1, bh, [&](int row) { return sH1 + cq * PL1 + row * 16; });
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -677,8 +700,8 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         }
         if (!(ok = wait_mma())) break;
         tc_fence_after();
-        for (int m = 0; m < kMT2; m++)
-            conv_epi(m, kP2, bh + 16, [&](int row) { return sHX + (row & 1) * EO + cq * PLE + (row >> 1) * 16; });
+        conv_epi(std::integral_constant<int, kMT2>(), kP2, bh + 16,
+                 [&](int row) { return sHX + (row & 1) * EO + cq * PLE + (row >> 1) * 16; });
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -695,7 +718,8 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         }
         if (!(ok = wait_mma())) break;
         tc_fence_after();
-        conv_epi(0, kTS, bh + 32, [&](int row) { return sH1 + cq * PL1 + row * 16; });   // h3, row = symbol
+        conv_epi(std::integral_constant<int, 1>(), kTS, bh + 32,
+                 [&](int row) { return sH1 + cq * PL1 + row * 16; });   // h3, row = symbol
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -772,7 +796,7 @@ __global__ void __launch_bounds__(kRxThreads, 2)
                 }
                 dec[(size_t)s * CS + q] = (uint8_t)(LI | (LQ << 3) | (nr ? 64 : 0));
                 int pos = pwin + BPS * q;
-                uint32_t w0 = prbs_bits[pos >> 5], w1w = prbs_bits[(pos >> 5) + 1];
+                uint32_t w0 = s_prbs[pos >> 5], w1w = s_prbs[(pos >> 5) + 1];
                 int ref = (int)(__funnelshift_l(w1w, w0, pos & 31) >> (32 - BPS));
                 for (int rq = 0; rq < 4; rq++) {
                     int a = LI, bq = LQ;
@@ -796,6 +820,7 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         }
         __syncthreads();
     }
+    cp_async_wait_all();   // a prefetch may still be in flight after an early exit
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, kRxTmem);
