@@ -103,7 +103,7 @@ template <int NT, int MQ, bool FRZ = false>
 __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys, int c0, float2 *zs, float2 *es,
                                              float2 *ws, int mode, float mu, int lane, uint8_t *dec_out,
                                              float2 *dbg_z, const uint32_t *prbs_bits, int pwin,
-                                             const float2 *zin = nullptr, float2 *G = nullptr)
+                                             float2 tph, const float2 *zin = nullptr, float2 *G = nullptr)
 {
     constexpr int TH = (NT - 1) / 2;
     constexpr int NP = (NT + 1) / 2;              // y pairs per symbol
@@ -154,9 +154,8 @@ __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys
     R.second = 0.f;
     float cs = 1.f, sn = 0.f;   // cos / sin of the chosen phase
     if (mode == 2) {
-        // blind phase search: lane b tests theta_b = (b/B)(pi/2) - pi/4
-        float tsn, tcs;
-        sincospif((float)lane / (float)(2 * p.bps_b) - 0.25f, &tsn, &tcs);
+        // blind phase search: lane b tests theta_b = (b/B)(pi/2) - pi/4 (tph = cos, sin)
+        const float tcs = tph.x, tsn = tph.y;
         const float sc = p.scale * tcs, ss = p.scale * tsn;
         float M = 0.f;
         const float4 *z4 = reinterpret_cast<const float4 *>(zs);
@@ -205,16 +204,18 @@ __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys
         if (dec_out) dec_out[q] = (uint8_t)(LI | (LQ << 3) | (nr ? 64 : 0));
         if (prbs_bits) {
             // bit errors of this symbol under each absolute pi/2 rotation of the decision
-            int ref = ref_bits<BPS>(prbs_bits, pwin + BPS * q);
-#pragma unroll
-            for (int rq = 0; rq < 4; rq++) {
-                int a = LI, b = LQ;
-                rot_t<MQ>(a, b, rq);
-                unsigned ne = __popc(((gray(a) << NB) | gray(b)) ^ ref);
-                if (rq < 2) eA += ne << (16 * rq);
-                else eB += ne << (16 * (rq - 2));
-                se += (ne > 0) << (8 * rq);
-            }
+            // with gray(MQ-1-L) = gray(L) ^ cm, rotation q of (LI, LQ) has the code
+            // q0: (gI, gQ), q1: (gQ, gI^cm), q2: (gI^cm, gQ^cm), q3: (gQ^cm, gI)
+            const int ref = ref_bits<BPS>(prbs_bits, pwin + BPS * q);
+            constexpr int cm = MQ == 2 ? 1 : 2;
+            const int gI = gray(LI), gQ = gray(LQ);
+            const int X = ((gI << NB) | gQ) ^ ref, Xs = ((gQ << NB) | gI) ^ ref;
+            const unsigned n0 = __popc(X), n1 = __popc(Xs ^ cm), n2 = __popc(X ^ ((cm << NB) | cm)),
+                           n3 = __popc(Xs ^ (cm << NB));
+            eA += n0 + (n1 << 16);
+            eB += n2 + (n3 << 16);
+            se += (unsigned)(n0 > 0) | ((unsigned)(n1 > 0) << 8) | ((unsigned)(n2 > 0) << 16) |
+                  ((unsigned)(n3 > 0) << 24);
             nn += nr;
         }
         float2 e;
@@ -335,6 +336,14 @@ __device__ __forceinline__ WinOut pam_window(const EqParams &p, const float *ys,
     return R;
 }
 
+// cos and sin of the test phase of this lane, theta_b = (b/B)(pi/2) - pi/4
+__device__ __forceinline__ float2 test_phase(const EqParams &p, int lane)
+{
+    float sn, cs;
+    sincospif((float)lane / (float)(2 * p.bps_b) - 0.25f, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
 // -------------------------------------------------------------- equaliser kernel
 // Payload: one warp per block of eq_block symbols, input staged by one bulk copy.
 // Training (train=1): one warp runs the training windows sequentially, staging
@@ -368,6 +377,7 @@ __global__ void __launch_bounds__(32 * kEqWarpsMax)
     else reinterpret_cast<float *>(ws)[lane] = lane < NT ? taps_in[lane].x : 0.f;
     __syncwarp();
     unsigned ambig = 0;
+    const float2 tph = test_phase(p, lane);
     if (train) {
         for (long long k0 = 0; k0 < p.ntrain; k0 += kWin) {
             long long ym0 = 2 * k0 - kYHist;
@@ -379,7 +389,7 @@ __global__ void __launch_bounds__(32 * kEqWarpsMax)
                 float mu = mode == 0 ? p.mu_cma : p.mu;
                 qam_window<NT, MQ>(p, reinterpret_cast<float2 *>(ys), kYHist, reinterpret_cast<float2 *>(zs),
                                    reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), mode, mu, lane,
-                                   nullptr, dz, nullptr, 0);
+                                   nullptr, dz, nullptr, 0, tph);
             } else {
                 pam_window<NT, MQ>(p, reinterpret_cast<float *>(ys), kYHist, k0, reinterpret_cast<float *>(zs),
                                    reinterpret_cast<float *>(es), reinterpret_cast<float *>(ws), 1, p.mu_train, lane,
@@ -417,7 +427,7 @@ __global__ void __launch_bounds__(32 * kEqWarpsMax)
         if (QAM) {
             WinOut R = qam_window<NT, MQ>(p, reinterpret_cast<float2 *>(ys), c0, reinterpret_cast<float2 *>(zs),
                                           reinterpret_cast<float2 *>(es), reinterpret_cast<float2 *>(ws), 2, p.mu,
-                                          lane, dq, dz, prbs_bits, pwin);
+                                          lane, dq, dz, prbs_bits, pwin, tph);
             if (lane == 0) {
                 winb[wi] = (uint8_t)R.b;
                 winrec[wi] = make_uint4(R.errA, R.errB, R.serr, (unsigned)R.b | (R.nnear << 8));
@@ -493,7 +503,8 @@ __global__ void __launch_bounds__(32 * kEqWarpsMax)
     float2 G = make_float2(0.f, 0.f);
     WinOut R = qam_window<NT, MQ, true>(p, ys, kYHist, zs, es, ws, 2, p.mu, lane, dec + (k0 - g.pay_lo),
                                         dbg_z ? dbg_z + (k0 - g.sym_lo) : nullptr, prbs_bits, pwin,
-                                        zin ? zin + (k0 - g.pay_lo) : nullptr, last ? &G : nullptr);
+                                        test_phase(p, lane), zin ? zin + (k0 - g.pay_lo) : nullptr,
+                                        last ? &G : nullptr);
     const long long wq = (k0 - g.pay_lo) / kWin;
     if (lane == 0) {
         winb[wq] = (uint8_t)R.b;
