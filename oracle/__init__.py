@@ -71,6 +71,8 @@ def lib():
         L.orx_fd_response.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
         L.orx_fd_block.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
+        L.orx_fd_block_full.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]
         L.orx_prbs15.argtypes = [C.c_uint32, C.c_int64, C.c_void_p]
         L.orx_q_db.argtypes = [C.c_double]
         L.orx_q_db.restype = C.c_double
@@ -158,6 +160,18 @@ def fd_block(x: np.ndarray, H: np.ndarray) -> np.ndarray:
     return yr + 1j * yi
 
 
+def fd_block_full(x: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """One frequency-domain block at the input rate: N inputs -> the N/2 central outputs."""
+    n = len(x)
+    xr = np.ascontiguousarray(np.real(x), dtype=np.float64)
+    xi = np.ascontiguousarray(np.imag(x), dtype=np.float64)
+    Hr = np.ascontiguousarray(np.real(H), dtype=np.float64)
+    Hi = np.ascontiguousarray(np.imag(H), dtype=np.float64)
+    yr, yi = np.zeros(n // 2), np.zeros(n // 2)
+    lib().orx_fd_block_full(_ptr(xr), _ptr(xi), n, _ptr(Hr), _ptr(Hi), _ptr(yr), _ptr(yi))
+    return yr + 1j * yi
+
+
 def prbs15(seed: int, nbits: int) -> np.ndarray:
     out = np.zeros(nbits, dtype=np.uint8)
     lib().orx_prbs15(seed, nbits, _ptr(out))
@@ -218,7 +232,7 @@ KK_DEFAULTS = dict(sps=4, pack_order=0, ols_n=65536, ols_v=4096, ds_num=11, ds_d
 PAM_DEFAULTS = dict(sps=2, pack_order=0, ols_n=0, ols_v=0, ds_num=0, ds_den=1, rrc_beta=0.1,
                     mf_span=16, ntaps=15, ntrain=4096, ncma=0, eq_block=256, win=64, mu=1e-3,
                     mu_train=1e-3, mu_cma=0.0, bps_b=1, amb_syms=0, prbs_seed=1, eq_frozen=0, mf_mode=0,
-                    fd_n=1024, fd_taps=203)
+                    fd_n=1024, fd_taps=503)
 
 
 def default_cfg(fmt: int, buf_len: int, **kw) -> dict:

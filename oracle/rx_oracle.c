@@ -209,6 +209,25 @@ void orx_fd_block(const double *x_re, const double *x_im, int n, const double *H
     free(re); free(im); free(zr); free(zi);
 }
 
+/* The same block without downsampling (the PAM chain, already at 2 samples per
+ * symbol): y = IFFT_N(X H) at the central indices N/4 .. 3N/4 - 1 (N/2 outputs),
+ * the circular convolution of x with h there, alias-free while the taps span at
+ * most N/2 + 1. */
+void orx_fd_block_full(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
+                       double *y_re, double *y_im)
+{
+    double *re = xcalloc((size_t)n, sizeof(double)), *im = xcalloc((size_t)n, sizeof(double));
+    for (int i = 0; i < n; i++) { re[i] = x_re[i]; im[i] = x_im[i]; }
+    orx_fft(re, im, n, 0);
+    for (int k = 0; k < n; k++) {
+        double a = re[k] * H_re[k] - im[k] * H_im[k], b = re[k] * H_im[k] + im[k] * H_re[k];
+        re[k] = a; im[k] = b;
+    }
+    orx_fft(re, im, n, 1);           /* includes 1/N */
+    for (int m = n / 4; m < 3 * n / 4; m++) { y_re[m - n / 4] = re[m]; y_im[m - n / 4] = im[m]; }
+    free(re); free(im);
+}
+
 /* PRBS-15, Fibonacci LFSR x^15 + x^14 + 1; register loaded with
  * (seed mod 32767) + 1; each step outputs r14 xor r15 and shifts it in. */
 void orx_prbs15(uint32_t seed, int64_t nbits, uint8_t *out)
@@ -274,7 +293,7 @@ orx *orx_create(const orx_cfg *cfg)
                     cfg->ds_den < 1 || cfg->ols_n < 4 || (cfg->ols_n & (cfg->ols_n - 1)) ||
                     cfg->ols_v < 2 || (cfg->ols_v & 1) || cfg->ols_v >= cfg->ols_n)) ||
         cfg->mf_mode < 0 || cfg->mf_mode > 1 ||
-        (cfg->mf_mode == 1 && (f < 3 || cfg->sps != 4 || cfg->fd_n < 16 || (cfg->fd_n & (cfg->fd_n - 1)) ||
+        (cfg->mf_mode == 1 && (cfg->sps != (f >= 3 ? 4 : 2) || cfg->fd_n < 16 || (cfg->fd_n & (cfg->fd_n - 1)) ||
                                cfg->fd_taps < 1 || !(cfg->fd_taps & 1) || cfg->fd_taps > cfg->fd_n / 2 + 1))) {
         free(h);
         return NULL;
@@ -310,6 +329,7 @@ orx *orx_create(const orx_cfg *cfg)
     h->prbs = xcalloc(32767, 1);
     orx_prbs15(cfg->prbs_seed, 32767, h->prbs);
     h->chist_cap = h->kk ? cfg->ols_n : 2 * h->hmf;
+    if (!h->kk && cfg->mf_mode == 1 && h->chist_cap < cfg->fd_n) h->chist_cap = cfg->fd_n;
     h->chist = xcalloc((size_t)h->chist_cap, sizeof(int32_t));
     h->w = xcalloc((size_t)cfg->ntaps, sizeof(cx));
     h->w[h->th] = cx_mk(1.0, 0.0);      /* centre tap 1 */
@@ -511,7 +531,7 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
     if (h->fd) {   /* whole blocks: block b needs the inputs up to hop*b + 3N/4 */
         int64_t N = c->fd_n, hop = N / 2;
         int64_t bk = (e_k >= 3 * N / 4) ? (e_k - 3 * N / 4) / hop + 1 : 0;
-        f_k = bk * (hop / 2);
+        f_k = bk * (hop / h->dec);
     }
     int64_t s_k = (f_k >= h->th + 1) ? (f_k - h->th - 1) / 2 + 1 : 0;
     int64_t q_k = (s_k >= c->ntrain) ? c->ntrain + ((s_k - c->ntrain) / c->eq_block) * c->eq_block : 0;
@@ -561,7 +581,23 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
     /* ---- matched filter (and 4 -> 2 samples/symbol for KK) ------------- */
     X.y_start = h->f_prev; X.y_len = f_k - h->f_prev;
     X.y = xcalloc((size_t)(X.y_len > 0 ? X.y_len : 1), sizeof(cx));
-    if (h->fd) {
+    if (h->fd && !h->kk) {
+        /* PAM: static frequency-domain filter on N-point blocks with hop N/2 at the
+         * input rate; the block input is the normalised code, zero before the stream */
+        int N = c->fd_n, hop = N / 2;
+        double *xr = xcalloc((size_t)N, sizeof(double)), *xi = xcalloc((size_t)N, sizeof(double));
+        double *yr = xcalloc((size_t)(N / 2), sizeof(double)), *yi = xcalloc((size_t)(N / 2), sizeof(double));
+        for (int64_t b = h->f_prev / hop; b < f_k / hop; b++) {
+            for (int t = 0; t < N; t++) {
+                int64_t n = (int64_t)hop * b - N / 4 + t;
+                xr[t] = n < 0 ? 0.0 : ((double)code_at(&X, n) - X.mu_pam) / X.sd_pam;
+                xi[t] = 0.0;
+            }
+            orx_fd_block_full(xr, xi, N, h->fd_Hr, h->fd_Hi, yr, yi);
+            for (int m = 0; m < N / 2; m++) X.y[(int64_t)hop * b + m - X.y_start] = cx_mk(yr[m], 0.0);
+        }
+        free(xr); free(xi); free(yr); free(yi);
+    } else if (h->fd) {
         /* static frequency-domain filter, N-point blocks with hop N/2, bin-truncation
          * downsampling; the block input is the carrier-removed, downshifted field */
         int N = c->fd_n, hop = N / 2;

@@ -47,10 +47,11 @@ typedef struct {
                             1 every block filters with the call's start taps (block-
                             Toeplitz form) and one averaged step over the last block
                             gives the next call's taps                                */
-    int32_t mf_mode;     /* KK reduction to 2 samples/symbol: 0 time-domain matched filter
-                            (mf_span), 1 static frequency-domain filter of fd_taps taps on
-                            fd_n-point overlap-save blocks with bin-truncation
-                            downsampling (fd_n/2-point inverse)                          */
+    int32_t mf_mode;     /* filter before the equaliser: 0 time-domain matched filter
+                            (mf_span); 1 static frequency-domain filter of fd_taps taps on
+                            fd_n-point overlap-save blocks (hop fd_n/2): KK with bin-
+                            truncation downsampling (fd_n/2-point inverse), PAM at the
+                            input rate (fd_n-point inverse)                              */
     int32_t fd_n;        /* frequency-domain block length (power of two, >= 16)           */
     int32_t fd_taps;     /* frequency-domain filter taps (odd, <= fd_n/2 + 1)             */
 } orx_cfg;
@@ -76,6 +77,8 @@ void    orx_rrc_half(double beta, int sps, int half, double *taps);
 void    orx_fd_response(const double *h, int ntaps, int n, double *H_re, double *H_im);
 void    orx_fd_block(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
                      double *y_re, double *y_im);
+void    orx_fd_block_full(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
+                          double *y_re, double *y_im);
 void    orx_prbs15(uint32_t seed, int64_t nbits, uint8_t *out);
 double  orx_q_db(double ber);
 void    orx_bps_metrics(const double *z_re, const double *z_im, int W, int mq, double s, int B,

@@ -1,10 +1,11 @@
-"""Pins of the oracle's frequency-domain reduction to 2 samples/symbol (the
-paper's static FD equaliser on overlap-save blocks of an N-point FFT, then an
-N/2-point IFFT as downsampler; Sec. 2, KK chain), against what the mathematics
-fixes independently of the oracle's FFT: closed-form filter responses, pure
-tones through the block (the response at the tone's bin, or nothing outside
-the kept band), brute-force double sums on a tiny block, the block grid of a
-stream, and a noiseless stream decoded without errors."""
+"""Pins of the oracle's frequency-domain filter forms (the paper's static FD
+equalisers on overlap-save blocks of an N-point FFT, Sec. 2: in the KK chain an
+N/2-point IFFT of the kept bins is the downsampler to 2 samples/symbol; the PAM
+chain stays at its input rate), against what the mathematics fixes
+independently of the oracle's FFT: closed-form filter responses, pure tones
+through the block (the response at the tone's bin, or nothing outside the kept
+band), brute-force double sums on a tiny block, the block grid of a stream, and
+noiseless streams decoded without errors."""
 
 import numpy as np
 import pytest
@@ -139,8 +140,73 @@ def test_fd_close_to_time_domain_filter():
 
 
 def test_fd_rejects_bad_configurations():
-    for kw in (dict(fd_n=1000), dict(fd_taps=202), dict(fd_taps=1024 // 2 + 3), dict(fd_n=8)):
-        with pytest.raises(ValueError):
-            oracle.Oracle(**oracle.default_cfg(4, 1 << 16, mf_mode=1, **kw))
-    with pytest.raises(ValueError):
-        oracle.Oracle(**oracle.default_cfg(1, 1 << 16, mf_mode=1))
+    for fmt in (4, 1):
+        for kw in (dict(fd_n=1000), dict(fd_taps=202), dict(fd_taps=1024 // 2 + 3), dict(fd_n=8)):
+            with pytest.raises(ValueError):
+                oracle.Oracle(**oracle.default_cfg(fmt, 1 << 16, mf_mode=1, **kw))
+
+
+@pytest.mark.parametrize("n", [64, 1024])
+def test_fd_block_full_tones(n):
+    """Without downsampling every bin passes: tones anywhere on the bin grid leave
+    as the tone times H at the bin, on the central half of the block."""
+    rng = np.random.default_rng(6)
+    ks = [0, 1, n // 4, n // 2, n // 2 + 3, n - 1, -(n // 8)]
+    amps = rng.standard_normal(len(ks)) + 1j * rng.standard_normal(len(ks))
+    t = np.arange(n)
+    x = sum(A * np.exp(2j * np.pi * k * t / n) for A, k in zip(amps, ks))
+    H = oracle.fd_response(rng.standard_normal(n // 2 + 1), n)
+    y = oracle.fd_block_full(x, H)
+    m = np.arange(n // 4, 3 * n // 4)
+    want = sum(A * H[k % n] * np.exp(2j * np.pi * k * m / n) for A, k in zip(amps, ks))
+    assert np.abs(y - want).max() < 1e-11 * max(1.0, np.abs(want).max())
+
+
+def test_fd_block_full_brute_force_tiny():
+    n = 16
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    H = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    want = []
+    for m in range(n // 4, 3 * n // 4):
+        acc = 0j
+        for k in range(n):
+            Xk = sum(x[t] * np.exp(-2j * np.pi * t * k / n) for t in range(n))
+            acc += Xk * H[k] * np.exp(2j * np.pi * k * m / n)
+        want.append(acc / n)
+    assert np.abs(oracle.fd_block_full(x, H) - np.array(want)).max() < 1e-12
+
+
+def test_fd_pam_stream_block_grid():
+    """PAM-4 in the frequency-domain form: the stream output of call 2 is the pinned
+    full-rate block on the stream grid over the normalised codes of calls 1 and 2."""
+    nb = 1 << 16
+    g = synth.gen_pam_stream(1, nb, 2, seed=3)
+    cfg = oracle.default_cfg(1, nb, mf_mode=1)
+    o = oracle.Oracle(**cfg)
+    N, hop = cfg["fd_n"], cfg["fd_n"] // 2
+    codes = np.concatenate([oracle.unpack(g["packed"][b], nb) for b in range(2)]).astype(np.float64)
+    for b in range(2):
+        o.process(g["packed"][b])
+    y, y0 = o.get(oracle.ORX_Y)
+    scal, _ = o.get(oracle.ORX_SCAL)
+    mu, sd = scal[3], scal[4]
+    assert len(y) > 0 and y0 % hop == 0 and len(y) % hop == 0
+    H = oracle.fd_response(oracle.rrc_half(cfg["rrc_beta"], 2, (cfg["fd_taps"] - 1) // 2), N)
+    for b in range(y0 // hop, (y0 + len(y)) // hop):
+        n = hop * b - N // 4 + np.arange(N)
+        x = np.where(n >= 0, (codes[np.clip(n, 0, None)] - mu) / sd, 0.0)
+        want = oracle.fd_block_full(x, H).real
+        got = np.real(y[hop * b - y0 + np.arange(N // 2)])
+        assert np.abs(got - want).max() < 1e-12 * np.abs(want).max(), b
+
+
+@pytest.mark.parametrize("fmt", [0, 1, 2])
+def test_fd_pam_noiseless_with_isi_zero_errors(fmt):
+    N = 1 << 19
+    g = synth.gen_pam_stream(fmt, N, 2, seed=3, noise=False)
+    o = oracle.Oracle(**oracle.default_cfg(fmt, N, mf_mode=1))
+    for b in range(2):
+        o.process(g["packed"][b])
+    s = o.stats()
+    assert s["bits"] > 400_000 and s["bit_errors"] == 0
