@@ -261,7 +261,8 @@ class Oracle:
 
     def process(self, packed: np.ndarray) -> np.ndarray:
         packed = np.ascontiguousarray(packed, dtype=np.uint8)
-        cap = self.bps * (self.cfg["buf_len"] // 2 + 64)
+        c = self.cfg   # a call can emit the symbols held back by the previous one: one block more
+        cap = self.bps * (c["buf_len"] // c["sps"] + c["eq_block"] + c["ntrain"] + 64)
         out = np.zeros((cap + 7) // 8, dtype=np.uint8)
         nbits = lib().orx_process(self._h, _ptr(packed), _ptr(out), cap)
         return out[: (nbits + 7) // 8].copy(), int(nbits)

@@ -198,7 +198,7 @@ static Sched schedule(const rx_handle *h, long long calls, long long q_prev)
     s.f_k = (s.e_k >= h->hmf + 1) ? (s.e_k - h->hmf - 1) / h->decim + 1 : 0;
     if (h->fd) {   // whole frequency-domain blocks: block b reads up to N/2 b + 3N/4
         long long N = h->cfg.fd_n, bk = (s.e_k >= 3 * N / 4) ? (s.e_k - 3 * N / 4) / (N / 2) + 1 : 0;
-        s.f_k = bk * (N / 4);
+        s.f_k = bk * (N / 2) / h->decim;
     }
     s.s_k = (s.f_k >= h->th + 1) ? (s.f_k - h->th - 1) / 2 + 1 : 0;
     long long nt = h->cfg.ntrain, B = h->cfg.eq_block;
@@ -249,7 +249,7 @@ rx_status rx_default_config(rx_format f, rx_config *c)
     c->debug = 0;
     c->mf_mode = RX_MF_TIME;
     c->fd_n = 1024;
-    c->fd_taps = 203;
+    c->fd_taps = kk ? 203 : 503;
     return RX_OK;
 }
 
@@ -335,8 +335,9 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     if (c.kk_front < 0 || c.kk_front > 1 || !(c.eq_warps == 0 || c.eq_warps == 2 || c.eq_warps == 4 || c.eq_warps == 8))
         return RX_EINVAL;
     if (c.mf_mode < RX_MF_TIME || c.mf_mode > RX_MF_FD ||
-        (c.mf_mode == RX_MF_FD && (!kk || c.fd_n < 16 || c.fd_n > kEHist || (c.fd_n & (c.fd_n - 1)) ||
-                                   c.fd_taps < 1 || !(c.fd_taps & 1) || c.fd_taps > c.fd_n / 2 + 1)))
+        (c.mf_mode == RX_MF_FD && (c.fd_n < 16 || c.fd_n > kEHist || (c.fd_n & (c.fd_n - 1)) ||
+                                   (!kk && c.fd_n != 1024) || c.fd_taps < 1 || !(c.fd_taps & 1) ||
+                                   c.fd_taps > c.fd_n / 2 + 1)))
         return RX_EINVAL;
     if (kk && (c.ncma < 0 || c.ncma > c.ntrain || c.ncma % kWin || c.bps_b < 1 || c.bps_b > 32 ||
                c.ds_den < 1 || c.ds_num < 0 || c.amb_syms < 0 || c.amb_syms % kWin || c.amb_syms > 4096 ||
@@ -355,7 +356,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     h->th = (c.ntaps - 1) / 2;
     h->nb = buf_len;
     h->cfg = c;
-    h->nhist = kk ? c.ols_n : kPamHist;
+    h->nhist = kk ? c.ols_n : (c.mf_mode == RX_MF_FD ? c.fd_n : kPamHist);
     if (kk) {
         h->N = c.ols_n;
         h->V = c.ols_v;
@@ -490,12 +491,13 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         // frequency-domain filter: response of the zero-phase taps at the kept bins
         // (k' < N/4 -> k = k', else k = k' + N/2), times 1/N; N-point twiddles
         const double pi = 3.14159265358979323846;
-        const int N = c.fd_n, half = (c.fd_taps - 1) / 2;
+        // (KK: the N/2 kept bins in downsampled order; PAM: all N bins)
+        const int N = c.fd_n, half = (c.fd_taps - 1) / 2, nbins = kk ? N / 2 : N;
         double *hf = (double *)malloc(sizeof(double) * c.fd_taps);
-        float2 *Hk = (float2 *)malloc(sizeof(float2) * N / 2), *tw = (float2 *)malloc(sizeof(float2) * N);
+        float2 *Hk = (float2 *)malloc(sizeof(float2) * nbins), *tw = (float2 *)malloc(sizeof(float2) * N);
         rrc_half(c.rrc_beta, sps, half, hf);
-        for (int kp = 0; kp < N / 2; kp++) {
-            int k = kp < N / 4 ? kp : kp + N / 2;
+        for (int kp = 0; kp < nbins; kp++) {
+            int k = (!kk || kp < N / 4) ? kp : kp + N / 2;
             double re = 0, im = 0;
             for (int i = -half; i <= half; i++) {
                 double a = -2.0 * pi * (double)(((long long)k * i) % N) / N;
@@ -505,9 +507,9 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
             Hk[kp] = make_float2((float)(re / N), (float)(im / N));
         }
         twiddles(N, tw);
-        if (e == cudaSuccess) e = cudaMalloc(&h->fd_H, sizeof(float2) * N / 2);
+        if (e == cudaSuccess) e = cudaMalloc(&h->fd_H, sizeof(float2) * nbins);
         if (e == cudaSuccess) e = cudaMalloc(&h->fd_tw, sizeof(float2) * N);
-        if (e == cudaSuccess) e = cudaMemcpy(h->fd_H, Hk, sizeof(float2) * N / 2, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->fd_H, Hk, sizeof(float2) * nbins, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(h->fd_tw, tw, sizeof(float2) * N, cudaMemcpyHostToDevice);
         free(hf);
         free(Hk);
@@ -681,6 +683,9 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
             e = launch_kk_mf(h->E[h->ew], h->ebase_cur, s.e_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
                              c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw],
                              h->ybase_cur, sm, h->rrc_host);
+        else if (h->fd)
+            e = launch_pam_fd1024(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->fd_H, h->fd_tw, h->st,
+                                  par, (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf);
         else
             e = launch_pam_mf(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->rrc, h->hmf, h->st, par,
                               (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf);

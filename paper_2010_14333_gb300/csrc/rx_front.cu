@@ -1322,6 +1322,97 @@ __global__ void __launch_bounds__(kMfOut) k_pam_mf(const uint16_t *__restrict__ 
     Y[m - ybase] = a;
 }
 
+// ===================================================== PAM frequency-domain filter
+// The paper's PAM form (Sec. 2): a static filter applied on 1024-point
+// overlap-save blocks (hop 512) at the input rate.  One warp per block: the
+// normalised codes x[n] = (code - mu) / sd of the N inputs from 512 b - 256 go
+// through the same 32 x 32 four-step forward transform as the KK form (lane k2
+// holds the bins k2 + 32 k1), every bin is multiplied by the response (times
+// 1/N), and the 1024-point inverse runs as a second four-step with m = m_a + 32
+// m_b: 32-point inverse DFTs over k1 in registers, twiddle e^{+2 pi i lane m_a /
+// 1024}, a transpose, 32-point inverse DFTs over the former lane index; lane m_a
+// keeps m_b = 8 .. 23 (m = 256 .. 767), whose real part is y.
+__global__ void __launch_bounds__(32 * kFdWarps, 4)
+    k_pam_fd1024(const uint16_t *__restrict__ codes, long long cbase, long long nb, long long n_end,
+                 long long b_first, long long nblk, const float2 *__restrict__ H, const float2 *__restrict__ tw,
+                 DevState *dst, int parity, float *__restrict__ Y, long long ybase, long long f_prev,
+                 const float *__restrict__ Y_prev, long long ybase_prev)
+{
+    __shared__ float2 s_tw[1024];
+    __shared__ float2 s_t[kFdWarps][32 * kFdPitch];
+    __shared__ float s_mu, s_inv;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_tw[i] = tw[i];
+    if (threadIdx.x == 0) {
+        double mu = (double)dst->pam_s1[parity] / (double)nb;
+        double var = (double)dst->pam_s2[parity] / (double)nb - mu * mu;
+        double inv = (var > 0.0) ? 1.0 / sqrt(var) : 1.0;
+        s_mu = (float)mu;
+        s_inv = (float)inv;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        for (long long m = ybase + threadIdx.x; m < f_prev; m += blockDim.x)
+            Y[m - ybase] = (m < 0) ? 0.f : Y_prev[m - ybase_prev];
+        if (threadIdx.x == 0) {   // debug view; the sums of the next call start from zero
+            double mu = (double)dst->pam_s1[parity] / (double)nb;
+            double var = (double)dst->pam_s2[parity] / (double)nb - mu * mu;
+            dst->pam_mu = mu;
+            dst->pam_inv_sd = (var > 0.0) ? 1.0 / sqrt(var) : 1.0;
+            dst->pam_s1[parity ^ 1] = 0;
+            dst->pam_s2[parity ^ 1] = 0;
+        }
+    }
+    const long long bi = (long long)blockIdx.x * kFdWarps + w;
+    if (bi >= nblk) return;
+    const long long blk = b_first + bi, n0 = 512 * blk - 256;
+    const float mu = s_mu, inv = s_inv;
+    float2 x[32];
+#pragma unroll
+    for (int q = 0; q < 32; q++) {
+        const long long n = n0 + lane + 32 * q;
+        x[q] = make_float2(n >= 0 && n < n_end ? ((float)codes[n - cbase] - mu) * inv : 0.f, 0.f);
+    }
+    dft32<false>(x);
+#pragma unroll
+    for (int k2 = 1; k2 < 32; k2++) x[k2] = cmul(x[k2], s_tw[lane * k2]);
+    float2 *T = s_t[w];
+#pragma unroll
+    for (int k2 = 0; k2 < 32; k2++) T[lane * kFdPitch + k2] = x[k2];
+    __syncwarp();
+#pragma unroll
+    for (int n1 = 0; n1 < 32; n1++) x[n1] = T[n1 * kFdPitch + lane];
+    __syncwarp();
+    dft32<false>(x);   // x[k1] = X[lane + 32 k1]
+#pragma unroll
+    for (int k1 = 0; k1 < 32; k1++) x[k1] = cmul(x[k1], __ldg(H + lane + 32 * k1));
+    dft32<true>(x);    // over k1 -> m_a
+#pragma unroll
+    for (int ma = 1; ma < 32; ma++) x[ma] = cmulc(x[ma], s_tw[lane * ma]);
+#pragma unroll
+    for (int ma = 0; ma < 32; ma++) T[lane * kFdPitch + ma] = x[ma];
+    __syncwarp();
+#pragma unroll
+    for (int l = 0; l < 32; l++) x[l] = T[l * kFdPitch + lane];
+    dft32<true>(x);    // lane m_a: x[m_b] = z[m_a + 32 m_b]
+    const long long s0 = 512 * blk - ybase;
+#pragma unroll
+    for (int mb = 8; mb < 24; mb++) Y[s0 + lane + 32 * (mb - 8)] = x[mb].x;
+}
+
+cudaError_t launch_pam_fd1024(const uint16_t *codes, long long cbase, long long nb, long long n_end,
+                              long long f_prev, long long f_k, const float2 *H, const float2 *tw, DevState *dst,
+                              int parity, float *Y, long long ybase, const float *Y_prev, long long ybase_prev,
+                              cudaStream_t st)
+{
+    if (f_prev % 512 || f_k % 512) return cudaErrorInvalidValue;
+    const long long nblk = (f_k - f_prev) / 512;
+    if (nblk <= 0) return cudaSuccess;
+    k_pam_fd1024<<<(unsigned)((nblk + kFdWarps - 1) / kFdWarps), 32 * kFdWarps, 0, st>>>(
+        codes, cbase, nb, n_end, f_prev / 512, nblk, H, tw, dst, parity, Y, ybase, f_prev, Y_prev, ybase_prev);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, long long n_end, long long f_prev,
                           long long f_k, const float *rrc, int hmf, DevState *dst, int parity,
                           float *Y, long long ybase, const float *Y_prev, long long ybase_prev,

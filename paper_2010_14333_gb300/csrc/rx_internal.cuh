@@ -129,6 +129,13 @@ cudaError_t launch_kk_fdmf(const float2 *E, long long ebase, long long f_prev, l
                            const double *cg, float2 *Y, long long ybase, const float2 *Y_prev,
                            long long ybase_prev, cudaStream_t st);
 
+// PAM frequency-domain form, 1024-point blocks (hop 512) at the input rate;
+// f_prev and f_k are multiples of 512
+cudaError_t launch_pam_fd1024(const uint16_t *codes, long long cbase, long long nb, long long n_end,
+                              long long f_prev, long long f_k, const float2 *H, const float2 *tw, DevState *dst,
+                              int parity, float *Y, long long ybase, const float *Y_prev, long long ybase_prev,
+                              cudaStream_t st);
+
 cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, long long n_end, long long f_prev,
                           long long f_k, const float *rrc, int hmf, DevState *dst, int parity,
                           float *Y, long long ybase, const float *Y_prev, long long ybase_prev,

@@ -81,9 +81,16 @@ def test_create_rejects_bad_fd_config(kw):
         setattr(c, k, v)
     h = C.c_void_p()
     assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
-    p = rx.rx_default_config(rx.RX_PAM4)   # the frequency-domain form is the KK chain's
-    p.mf_mode = 1
+    p = rx.rx_default_config(rx.RX_PAM4)   # the PAM form runs 1024-point blocks only
+    p.mf_mode, p.fd_n, p.fd_taps = 1, 512, 101
     assert lib.rx_create(rx.RX_PAM4, 2e9, 4e9, 1 << 20, C.byref(p), C.byref(h)) == 1
+    p.fd_n, p.fd_taps = 1024, 515
+    assert lib.rx_create(rx.RX_PAM4, 2e9, 4e9, 1 << 20, C.byref(p), C.byref(h)) == 1
+
+
+def test_fd_default_taps():
+    assert rx.rx_default_config(rx.RX_KK_16QAM).fd_taps == 203
+    assert rx.rx_default_config(rx.RX_PAM4).fd_taps == 503
 
 
 def test_null_handle_calls_are_rejected():
