@@ -591,7 +591,47 @@ def fd_leg(args, g, ring):
         out[key] = {"gsa_s": 2 * len(ring) * NB / (e0.elapsed_time(e1) * 1e-3) / 1e9,
                     "filter_us_per_buffer": ms["mf"] / max(calls, 1) * 1e3}
         del r
+    out["pam4"] = pam_fd(args)
     return out
+
+
+def pam_fd(args):
+    """PAM-4 at 2 GBaud on 2^20-sample buffers: the 503-tap frequency-domain form
+    against the 33-tap time-domain matched filter, with the oracle's BER in the
+    same form on the first two buffers."""
+    import torch
+    import oracle
+    import synth
+    import paper_2010_14333_gb300 as rx
+    nb, nbufs, fmt = 1 << 20, 32, 1
+    g = synth.gen_pam_stream(fmt, nb, nbufs, seed=5)
+    ring = [torch.from_numpy(p).cuda() for p in g["packed"]]
+    o = oracle.Oracle(**oracle.default_cfg(fmt, nb, mf_mode=1))
+    d = rx.Receiver(fmt, nb, mf_mode=1)
+    for b in range(2):
+        o.process(g["packed"][b])
+        d.process(ring[b])
+    res = {"buf_len": nb, "fd_taps": 503, "ber": d.stats()["ber"], "ber_oracle": o.stats()["ber"]}
+    del d
+    for mode in (1, 0):
+        r = rx.Receiver(fmt, nb, mf_mode=mode)
+        for _ in range(2):
+            r.process_batch(ring)
+        torch.cuda.synchronize()
+        rx.rx_profile(r.h, 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(4):
+            r.process_batch(ring)
+        e1.record()
+        torch.cuda.synchronize()
+        ms, calls = rx.rx_profile_read(r.h)
+        rx.rx_profile(r.h, 0)
+        res["frequency_domain" if mode else "time_domain_33_taps"] = {
+            "gsa_s": 4 * nbufs * nb / (e0.elapsed_time(e1) * 1e-3) / 1e9,
+            "filter_us_per_buffer": ms["mf"] / max(calls, 1) * 1e3}
+        del r
+    return res
 
 
 def _gen_member(job):
