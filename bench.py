@@ -71,7 +71,8 @@ class Clocks:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.period_ms = period_ms
         self.samples = []
         self.proc = None
         self.gpu = gpu_index
@@ -80,7 +81,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -199,18 +200,22 @@ def gpu_arm(args, rank, world, local):
     out_ptrs = [b.data_ptr() for b in bits_out]
     sid = stream.cuda_stream
 
+    host_s = [0.0]
+
     def run_steps(rcv, n):
         nbits = 0
         for _ in range(n):
             ins = [ring[(rcv.pos + j) % args.ring].data_ptr() for j in range(args.bufs_per_step)]
+            t = time.perf_counter()
             nbits += sum(rx.rx_process_batch(rcv.h, ins, out_ptrs, sid))
+            host_s[0] += time.perf_counter() - t
             rcv.pos += args.bufs_per_step
         return nbits
 
     # warm-up: at least W steps and at least WARMUP_MIN_S of back-to-back work, so
     # that the timed steps start from the clocks and pipeline state of a busy GPU
     # (the synthetic data generation before this leaves the GPU idle for seconds)
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.smi_ms)
     clocks.start()
     r.pos = 0
     warm_steps, t_w = 0, time.perf_counter()
@@ -226,7 +231,9 @@ def gpu_arm(args, rank, world, local):
     torch.cuda.synchronize()
     clocks.t0 = time.time()
     ev0.record(stream)
+    host_s[0] = 0.0
     run_steps(r, args.steps)
+    host_enqueue_ms = host_s[0] / args.steps * 1e3   # host time spent enqueueing one step
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks.t1 = time.time()
@@ -373,6 +380,8 @@ def gpu_arm(args, rank, world, local):
     fd_line = None
     if rank == 0 and not args.no_fd:
         fd_line = fd_leg(args, g, ring)
+    sweep_line = sweep_leg(args) if rank == 0 and args.sweep else None
+    stab_line = stability_leg(args) if rank == 0 and args.stability > 0 else None
     batched_line = None
     if rank == 0 and not args.no_batched:
         batched_line = batched_leg(args)
@@ -380,13 +389,15 @@ def gpu_arm(args, rank, world, local):
     clk = clocks.summary()
     launches_per_call = 6                 # KK front (three kernels), matched filter, equaliser, demap
     line = {"metric": METRIC, "value": value, "unit": "GSa/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "warmup_run": warm_steps, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "warmup_run": warm_steps, "ms_per_step": ms / args.steps,
+            "host_enqueue_ms_per_step": host_enqueue_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args),
             "e2e": {"value": e2e_value, "unit": "GSa/s", "h2d_bytes_per_step": h2d // e2e_steps,
                     "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
             "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line, "precision": prec_line,
             "fd_filter": fd_line, "batched": batched_line,
+            "q_sweep": sweep_line, "stability": stab_line,
             "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
             "realtime_x": value / 4.0,
             "ber": cpu["ber_gpu_same_buffers"] if cpu else None,
@@ -634,6 +645,117 @@ def pam_fd(args):
     return res
 
 
+SWEEP = {0: (1 << 20, (6.0, 8.0, 10.0, 12.0, 14.0)),      # PAM-2
+         1: (1 << 20, (12.0, 14.0, 16.0, 18.0, 20.0)),    # PAM-4
+         2: (1 << 20, (18.0, 20.0, 22.0, 24.0, 26.0)),    # PAM-8
+         3: (1 << 22, (6.0, 8.0, 10.0, 12.0, 14.0)),      # KK-QPSK
+         4: (1 << 22, (14.0, 16.0, 18.0, 20.0, 22.0))}    # KK-16QAM
+FMT_NAMES = ["PAM-2", "PAM-4", "PAM-8", "KK-QPSK", "KK-16QAM"]
+
+
+def sweep_leg(args):
+    """Synthetic analogue of the paper's Q-factor versus OSNR curves (Fig. 2a, b):
+    every format over five SNR points (in-band Es/N0 of the generator), BER and
+    Q = 20 log10(sqrt(2) erfcinv(2 BER)) of the GPU receiver over a few buffers
+    per point, and the FP64 oracle's BER on the same first buffer at the middle
+    point."""
+    import torch
+    import oracle
+    import synth
+    import paper_2010_14333_gb300 as rx
+    nb_per = 4
+    res = {}
+    for fmt, (nb, snrs) in SWEEP.items():
+        pts = []
+        for i, snr in enumerate(snrs):
+            if fmt >= 3:
+                g = synth.gen_kk_stream(fmt, nb, nb_per, seed=40 + i, snr_db=snr, truth=False,
+                                        workers=min(nb_per, os.cpu_count() or 1))
+            else:
+                g = synth.gen_pam_stream(fmt, nb, nb_per, seed=40 + i, snr_db=snr)
+            r = rx.Receiver(fmt, nb)
+            for p in g["packed"]:
+                r.process(torch.from_numpy(p).cuda())
+            st = r.stats()
+            pt = {"snr_db": snr, "bits": st["bits"], "ber": st["ber"],
+                  "q_db": st["q_db"] if np.isfinite(st["q_db"]) else None,
+                  "slip_windows": st["slip_windows"]}
+            if i == len(snrs) // 2:
+                o = oracle.Oracle(**oracle.default_cfg(fmt, nb))
+                chk = rx.Receiver(fmt, nb)
+                o.process(g["packed"][0])
+                chk.process(torch.from_numpy(g["packed"][0]).cuda())
+                pt["first_buffer_ber_gpu"], pt["first_buffer_ber_oracle"] = chk.stats()["ber"], o.stats()["ber"]
+            pts.append(pt)
+            del r
+        res[FMT_NAMES[fmt]] = {"buf_len": nb, "buffers_per_point": nb_per, "points": pts}
+    return res
+
+
+def stability_leg(args):
+    """Synthetic analogue of the paper's 6-second Q time series (Fig. 2c): one
+    continuous KK-16QAM stream of --stability buffers through the end-to-end host
+    path (pinned host buffers, copies in and out), processed 20 buffers (21 ms of
+    signal) at a time; per window the Q-factor and the device time of the window
+    against its 20.97 ms real-time budget."""
+    import torch
+    import synth
+    import paper_2010_14333_gb300 as rx
+    nbufs, win = args.stability, 20
+    t0 = time.perf_counter()
+    g = synth.gen_kk_stream(FMT, NB, nbufs, seed=77, truth=False, workers=min(16, os.cpu_count() or 1), **GEN)
+    t_gen = time.perf_counter() - t0
+    packed = g["packed"]
+    del g
+    ring = [torch.zeros(len(packed[0]), dtype=torch.uint8).pin_memory() for _ in range(win)]
+    c = rx.rx_default_config(FMT)
+    h = rx.rx_create(FMT, BAUD, FS, NB, c)
+    outs = [torch.zeros(rx.rx_max_bits(h) // 8 + 16, dtype=torch.uint8).pin_memory() for _ in range(win)]
+    sid = torch.cuda.current_stream().cuda_stream
+    series, prev = [], None
+    budget_ms = win * NB / FS * 1e3
+    try:
+        for w0 in range(0, nbufs - win + 1, win):
+            for j in range(win):   # the window's ADC buffers arrive in pinned host memory
+                ring[j].numpy()[:] = packed[w0 + j]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rx.rx_process_host_batch(h, [t.data_ptr() for t in ring], [o.data_ptr() for o in outs], sid)
+            e1.record()
+            torch.cuda.synchronize()
+            st = rx.rx_stats(h, sid)
+            bits = st["bits"] - (prev["bits"] if prev else 0)
+            errs = st["bit_errors"] - (prev["bit_errors"] if prev else 0)
+            ber = errs / bits if bits else None
+            series.append({"window": w0 // win, "bits": bits, "ber": ber,
+                           "q_db": (None if not ber else float(oracle_free_q_db(ber))),
+                           "device_ms": e0.elapsed_time(e1)})
+            prev = st
+    finally:
+        rx.rx_destroy(h)
+    qs = [x["q_db"] for x in series[1:] if x["q_db"] is not None]
+    ms = [x["device_ms"] for x in series[1:]]
+    return {"buffers": nbufs, "window_buffers": win, "window_ms_of_signal": budget_ms, "gen_s": t_gen,
+            "q_db_mean": float(np.mean(qs)) if qs else None, "q_db_min": float(np.min(qs)) if qs else None,
+            "q_db_max": float(np.max(qs)) if qs else None, "device_ms_max": float(np.max(ms)) if ms else None,
+            "deadline_misses": int(sum(m > budget_ms for m in ms)),
+            "note": "the first window holds the training symbols and is excluded from the summary",
+            "series": series}
+
+
+def oracle_free_q_db(ber: float) -> float:
+    """Q = 20 log10(sqrt(2) erfcinv(2 BER)) by bisection on math.erfc."""
+    import math
+    lo, hi = 0.0, 30.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if math.erfc(mid) > 2.0 * ber:
+            lo = mid
+        else:
+            hi = mid
+    return 20.0 * math.log10(math.sqrt(2.0) * 0.5 * (lo + hi))
+
+
 def _gen_member(job):
     """One member stream of the batched workload (runs in a spawned worker)."""
     import synth
@@ -756,6 +878,9 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fd", action="store_true")
+    ap.add_argument("--smi-ms", type=int, default=50, help="clock sampling period during the timed steps")
+    ap.add_argument("--sweep", action="store_true", help="Q-factor versus SNR for every format")
+    ap.add_argument("--stability", type=int, default=0, help="buffers of the Q time series (0: off)")
     ap.add_argument("--batched-streams", type=int, default=64)
     ap.add_argument("--batched-rounds", type=int, default=10)
     ap.add_argument("--latency-reps", type=int, default=300)
