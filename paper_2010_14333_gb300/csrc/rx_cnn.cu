@@ -621,6 +621,12 @@ __global__ void __launch_bounds__(kRxThreads, 2)
     const uint32_t aB1 = smem_u32(sB1), aH1 = smem_u32(sH1), aHX = smem_u32(sHX), aW2 = smem_u32(sW2),
                    aW3 = smem_u32(sW3), aM1 = smem_u32(sM1), aM2 = smem_u32(sM2);
     const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's lane quarter
+    // matrix descriptors at the operand bases; an operand offset of o bytes adds o >> 4
+    // to the start-address field, so the issue loops add compile-time constants
+    const uint64_t dX = umma_sdesc(aHX, 64, 128), dB1 = umma_sdesc(aB1, 512, 128);
+    const uint64_t dH1 = umma_sdesc(aH1, PL1, 128), dW2 = umma_sdesc(aW2, 512, 128), dW3 = umma_sdesc(aW3, 512, 128);
+    const uint64_t dEO = umma_sdesc(aHX, PLE, 128), dM1 = umma_sdesc(aM1, 1024, 128);
+    const uint64_t dHid = umma_sdesc(aHX, 2048, 128), dM2 = umma_sdesc(aM2, 256, 128);
     unsigned phase = 0;
     bool ok = true;
     const int ntiles = (nwin + kWinT - 1) / kWinT;
@@ -673,12 +679,12 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         if (t + (int)gridDim.x < ntiles) prefetch(t + gridDim.x);   // lands while this tile computes
         if (tid == 0) {
             tc_fence_after();
+#pragma unroll
             for (int m = 0; m < kMT1; m++)
-                for (int ks = 0; ks < 2; ks++) {
-                    uint64_t ad = umma_sdesc(aHX + (128 * m + 8 * ks) * 16, 64, 128);
-                    uint64_t bd = umma_sdesc(aB1 + 2 * ks * 512, 512, 128);
-                    umma_f16(tmem + 32 * m, ad, bd, id32, ks > 0);
-                }
+#pragma unroll
+                for (int ks = 0; ks < 2; ks++)
+                    umma_f16(tmem + 32 * m, dX + (((128 * m + 8 * ks) * 16) >> 4), dB1 + ((2 * ks * 512) >> 4), id32,
+                             ks > 0);
             umma_commit(bar);
         }
         if (!(ok = wait_mma())) break;
@@ -690,12 +696,12 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         // layer 2 (reads h1; the input plane is free)
         if (tid == 0) {
             tc_fence_after();
+#pragma unroll
             for (int m = 0; m < kMT2; m++)
-                for (int ks = 0; ks < 18; ks++) {
-                    uint64_t ad = umma_sdesc(aH1 + (128 * m + ks / 2) * 16 + 2 * (ks & 1) * PL1, PL1, 128);
-                    uint64_t bd = umma_sdesc(aW2 + 2 * ks * 512, 512, 128);
-                    umma_f16(tmem + 32 * m, ad, bd, id32, ks > 0);
-                }
+#pragma unroll
+                for (int ks = 0; ks < 18; ks++)
+                    umma_f16(tmem + 32 * m, dH1 + (((128 * m + ks / 2) * 16 + 2 * (ks & 1) * PL1) >> 4),
+                             dW2 + ((2 * ks * 512) >> 4), id32, ks > 0);
             umma_commit(bar);
         }
         if (!(ok = wait_mma())) break;
@@ -708,11 +714,11 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         // layer 3 at the symbol positions: tap d reads set d & 1 from row j + d / 2
         if (tid == 0) {
             tc_fence_after();
+#pragma unroll
             for (int ks = 0; ks < 18; ks++) {
                 const int d = ks >> 1;
-                uint64_t ad = umma_sdesc(aHX + (d & 1) * EO + (d >> 1) * 16 + 2 * (ks & 1) * PLE, PLE, 128);
-                uint64_t bd = umma_sdesc(aW3 + 2 * ks * 512, 512, 128);
-                umma_f16(tmem, ad, bd, id32, ks > 0);
+                umma_f16(tmem, dEO + (((d & 1) * EO + (d >> 1) * 16 + 2 * (ks & 1) * PLE) >> 4),
+                         dW3 + ((2 * ks * 512) >> 4), id32, ks > 0);
             }
             umma_commit(bar);
         }
@@ -726,11 +732,9 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         // MLP 32 -> 64 on the symbols (M = 128, N = 64, K = 32)
         if (tid == 0) {
             tc_fence_after();
-            for (int ks = 0; ks < 2; ks++) {
-                uint64_t ad = umma_sdesc(aH1 + 2 * ks * PL1, PL1, 128);
-                uint64_t bd = umma_sdesc(aM1 + 2 * ks * 1024, 1024, 128);
-                umma_f16(tmem, ad, bd, id64, ks > 0);
-            }
+#pragma unroll
+            for (int ks = 0; ks < 2; ks++)
+                umma_f16(tmem, dH1 + ((2 * ks * PL1) >> 4), dM1 + ((2 * ks * 1024) >> 4), id64, ks > 0);
             umma_commit(bar);
         }
         if (!(ok = wait_mma())) break;
@@ -754,11 +758,9 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         // 64 -> 2 (M = 128, N = 16 with rows 2..15 of B zero, K = 64)
         if (tid == 0) {
             tc_fence_after();
-            for (int ks = 0; ks < 4; ks++) {
-                uint64_t ad = umma_sdesc(aHX + 2 * ks * 2048, 2048, 128);
-                uint64_t bd = umma_sdesc(aM2 + 2 * ks * 256, 256, 128);
-                umma_f16(tmem + kColOut, ad, bd, id16, ks > 0);
-            }
+#pragma unroll
+            for (int ks = 0; ks < 4; ks++)
+                umma_f16(tmem + kColOut, dHid + ((2 * ks * 2048) >> 4), dM2 + ((2 * ks * 256) >> 4), id16, ks > 0);
             umma_commit(bar);
         }
         if (!(ok = wait_mma())) break;
