@@ -29,6 +29,12 @@ import time
 
 import numpy as np
 
+# Each receiver handle pipelines its stages on four streams (plus a copy stream),
+# and a group adds up to eight worker streams.  CUDA maps streams onto a limited
+# set of hardware queues (8 unless raised); two pipeline stages that land on the
+# same queue serialise behind each other.  Raise the limit before CUDA starts.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)

@@ -184,7 +184,10 @@ rx_status rx_process(rx_handle *h, const uint8_t *packed12_in, uint8_t *bits_out
  * as the paper overlaps consecutive buffers in parallel streams chained by
  * events (Sec. 2).  The pipeline starts after the work already on cuda_stream,
  * and cuda_stream waits for its last back end before anything enqueued later.
- * With cfg.debug = 1 the buffers run one at a time on cuda_stream. */
+ * With cfg.debug = 1 the buffers run one at a time on cuda_stream.  The stages
+ * overlap only if their streams reach separate hardware queues: with several
+ * handles or groups in one process, set CUDA_DEVICE_MAX_CONNECTIONS (e.g. 32)
+ * before the process first uses CUDA. */
 rx_status rx_process_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *const *outs, int n,
                            void *cuda_stream, int64_t *nbits_out);
 
