@@ -431,18 +431,21 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
         long long ws = ols_ws(g, j);
         int tlo, thi;
         ols_kept(g, j, tlo, thi);
+        // 32-bit offsets from the block's first stream index: E row base, and the
+        // local index below which the stream index is negative (before the stream)
+        float2 *Eb = E + (ws - g.ebase);
+        const int tneg = ws < 0 ? (int)(-ws) : 0;
 #pragma unroll
         for (int q = 0; q < 16; q++) {
             int tt = n1 + g.N2 * q;
             if (tt < tlo || tt >= thi) continue;
-            long long n = ws + tt;
-            uint32_t code = n < 0 ? c_first : decode_col(raw[16 * half + q], t, pk.order);
+            uint32_t code = tt < tneg ? c_first : decode_col(raw[16 * half + q], t, pk.order);
             float phi = (half ? x[q].y : x[q].x) * invN;
             float sn, cs;
             __sincosf(phi, &sn, &cs);   // |phi| < pi: absolute error <= 2^-21.41
             float A = __ldg(tb.sqt + code);
             float2 e = make_float2(A * cs, A * sn);
-            E[n - g.ebase] = e;
+            Eb[tt] = e;
             sre += e.x;
             sim += e.y;
             si2 += code ? 2 * (int)code : 1;
