@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rx_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liborx.so")
 
-ORX_E, ORX_Y, ORX_Z, ORX_V, ORX_AHAT, ORX_BERR, ORX_WIN, ORX_TAPS, ORX_SCAL, ORX_NEAR, ORX_DRAW = range(1, 12)
+ORX_E, ORX_Y, ORX_Z, ORX_V, ORX_AHAT, ORX_BERR, ORX_WIN, ORX_TAPS, ORX_SCAL, ORX_NEAR, ORX_DRAW, ORX_RS = range(1, 13)
 
 
 class OrxCfg(C.Structure):
@@ -30,6 +30,7 @@ class OrxCfg(C.Structure):
         ("mu", C.c_double), ("mu_train", C.c_double), ("mu_cma", C.c_double),
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
         ("eq_frozen", C.c_int32), ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
+        ("pad_rs", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
     ]
 
 
@@ -71,6 +72,7 @@ def lib():
         L.orx_fd_response.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
         L.orx_fd_block.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
+        L.orx_rs_taps.argtypes = [C.c_double, C.c_void_p]
         L.orx_fd_block_full.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p]
         L.orx_prbs15.argtypes = [C.c_uint32, C.c_int64, C.c_void_p]
@@ -172,6 +174,21 @@ def fd_block_full(x: np.ndarray, H: np.ndarray) -> np.ndarray:
     return yr + 1j * yi
 
 
+def rs_taps(mu: float) -> np.ndarray:
+    """The resampler's 16 interpolator taps (j = -7 .. 8) at fraction mu."""
+    c = np.zeros(16)
+    lib().orx_rs_taps(mu, _ptr(c))
+    return c
+
+
+def rs_params(clock_step: int, clock_phase0: int):
+    """Resampler accumulator (rs_step, rs_phase0) that inverts an ADC clock whose
+    sample n lies at transmitter time (clock_phase0 + n clock_step) / 2^32."""
+    step = ((1 << 64) + clock_step // 2) // clock_step
+    ph = -(((clock_phase0 << 32) + clock_step // 2) // clock_step)
+    return int(step), int(ph)
+
+
 def prbs15(seed: int, nbits: int) -> np.ndarray:
     out = np.zeros(nbits, dtype=np.uint8)
     lib().orx_prbs15(seed, nbits, _ptr(out))
@@ -228,11 +245,12 @@ def cnn_param_slices():
 KK_DEFAULTS = dict(sps=4, pack_order=0, ols_n=65536, ols_v=4096, ds_num=11, ds_den=80,
                    rrc_beta=0.1, mf_span=16, ntaps=31, ntrain=16384, ncma=8192, eq_block=256,
                    win=64, mu=1e-3, mu_train=1e-3, mu_cma=1e-3, bps_b=32, amb_syms=1024,
-                   prbs_seed=1, eq_frozen=0, mf_mode=0, fd_n=1024, fd_taps=203)
+                   prbs_seed=1, eq_frozen=0, mf_mode=0, fd_n=1024, fd_taps=203, pad_rs=0, rs_step=0,
+                   rs_phase0=0)
 PAM_DEFAULTS = dict(sps=2, pack_order=0, ols_n=0, ols_v=0, ds_num=0, ds_den=1, rrc_beta=0.1,
                     mf_span=16, ntaps=15, ntrain=4096, ncma=0, eq_block=256, win=64, mu=1e-3,
                     mu_train=1e-3, mu_cma=0.0, bps_b=1, amb_syms=0, prbs_seed=1, eq_frozen=0, mf_mode=0,
-                    fd_n=1024, fd_taps=503)
+                    fd_n=1024, fd_taps=503, pad_rs=0, rs_step=0, rs_phase0=0)
 
 
 def default_cfg(fmt: int, buf_len: int, **kw) -> dict:
@@ -270,7 +288,7 @@ class Oracle:
     def get(self, what: int):
         start = C.c_int64(0)
         n = lib().orx_get(self._h, what, None, 0, C.byref(start))
-        if what in (ORX_E, ORX_Y, ORX_Z, ORX_V, ORX_TAPS):
+        if what in (ORX_E, ORX_Y, ORX_Z, ORX_V, ORX_TAPS, ORX_RS):
             buf = np.zeros(2 * n, dtype=np.float64)
             lib().orx_get(self._h, what, _ptr(buf), n, C.byref(start))
             return buf[0::2] + 1j * buf[1::2], start.value

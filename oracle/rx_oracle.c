@@ -228,6 +228,24 @@ void orx_fd_block_full(const double *x_re, const double *x_im, int n, const doub
     free(re); free(im);
 }
 
+/* ----------------------------------------------------------- resampler
+ * The paper's ADC is clocked independently of the transmitter; its DSP recovers
+ * the clock phase block by block (Sec. 2).  Here the clock relation is a
+ * configured integer accumulator (reading): nominal sample m of the transmitter's
+ * grid lies at ADC position (rs_phase0 + m rs_step) / 2^32, and the field there is
+ * interpolated from the 16 ADC samples around it with a Hann-windowed sinc,
+ *   c_j(mu) = sinc(j - mu) (1 + cos(pi (j - mu) / 8)) / 2,  j = -7 .. 8,
+ * at the fraction mu rounded down to 10 bits. */
+void orx_rs_taps(double mu, double *c)
+{
+    for (int j = -7; j <= 8; j++) {
+        double x = (double)j - mu;
+        double sn = fabs(x) < 1e-15 ? 1.0 : sin(PI * x) / (PI * x);
+        double w = fabs(x) < 8.0 ? 0.5 * (1.0 + cos(PI * x / 8.0)) : 0.0;
+        c[j + 7] = sn * w;
+    }
+}
+
 /* PRBS-15, Fibonacci LFSR x^15 + x^14 + 1; register loaded with
  * (seed mod 32767) + 1; each step outputs r14 xor r15 and shifts it in. */
 void orx_prbs15(uint32_t seed, int64_t nbits, uint8_t *out)
@@ -267,6 +285,10 @@ struct orx {
     cx *yhist; int64_t yhist_start, yhist_len;
     cx carrier; double gain;
     cx *w;                         /* taps every block of the next call starts from */
+    int rs;                        /* resampler to the transmitter's grid */
+    int64_t r_prev;                /* nominal field samples emitted */
+    cx *rhist; int64_t rhist_start, rhist_len;
+    cx *d_R; int64_t d_R_start, d_R_len;
     int fd;                        /* frequency-domain reduction to 2 samples/symbol */
     double *fd_Hr, *fd_Hi;         /* its filter response, fd_n bins */
     int trained;
@@ -293,6 +315,7 @@ orx *orx_create(const orx_cfg *cfg)
                     cfg->ds_den < 1 || cfg->ols_n < 4 || (cfg->ols_n & (cfg->ols_n - 1)) ||
                     cfg->ols_v < 2 || (cfg->ols_v & 1) || cfg->ols_v >= cfg->ols_n)) ||
         cfg->mf_mode < 0 || cfg->mf_mode > 1 ||
+        (cfg->rs_step != 0 && (f < 3 || cfg->rs_step < (int64_t)4252017623LL || cfg->rs_step > (int64_t)4337916969LL)) ||
         (cfg->mf_mode == 1 && (cfg->sps != (f >= 3 ? 4 : 2) || cfg->fd_n < 16 || (cfg->fd_n & (cfg->fd_n - 1)) ||
                                cfg->fd_taps < 1 || !(cfg->fd_taps & 1) || cfg->fd_taps > cfg->fd_n / 2 + 1))) {
         free(h);
@@ -317,6 +340,7 @@ orx *orx_create(const orx_cfg *cfg)
     h->th = (cfg->ntaps - 1) / 2;
     h->rrc = xcalloc((size_t)(2 * h->hmf + 1), sizeof(double));
     orx_rrc(cfg->rrc_beta, cfg->sps, cfg->mf_span, h->rrc);
+    h->rs = cfg->rs_step != 0;
     h->fd = cfg->mf_mode == 1;
     if (h->fd) {
         double *hf = xcalloc((size_t)cfg->fd_taps, sizeof(double));
@@ -409,6 +433,7 @@ typedef struct {
     const int32_t *cur; int64_t base;   /* current buffer: stream samples [base, base+Nb) */
     cx *E; int64_t E_start, E_len;      /* this call's KK outputs */
     cx *y; int64_t y_start, y_len;      /* this call's matched-filter outputs */
+    cx *R; int64_t R_start, R_len;      /* this call's resampled field (transmitter grid) */
     double mu_pam, sd_pam;
 } ctx;
 
@@ -426,6 +451,14 @@ static cx e_at(const ctx *x, int64_t n)
     if (n < 0) return cx_mk(0.0, 0.0);
     if (n >= x->E_start) return x->E[n - x->E_start];
     return h->ehist[n - h->ehist_start];
+}
+static cx r_at(const ctx *x, int64_t m)   /* the field on the grid the filter reads */
+{
+    const orx *h = x->h;
+    if (!h->rs) return e_at(x, m);
+    if (m < 0) return cx_mk(0.0, 0.0);
+    if (m >= x->R_start) return x->R[m - x->R_start];
+    return h->rhist[m - h->rhist_start];
 }
 static cx y_at(const ctx *x, int64_t m)
 {
@@ -527,10 +560,18 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
     /* emission counts: every step emits what its full support allows */
     int64_t e_k = h->kk ? avail - c->ols_v / 2 : avail;
     if (e_k < 0) e_k = 0;
-    int64_t f_k = (e_k >= h->hmf + 1) ? (e_k - h->hmf - 1) / h->dec + 1 : 0;
+    /* resampler: nominal sample m needs the ADC field up to index i_m + 8, with
+     * i_m = floor((rs_phase0 + m rs_step) / 2^32): r_k = #{m >= 0 : i_m + 8 < e_k} */
+    int64_t r_k = e_k;
+    if (h->rs) {
+        __int128 lim = ((__int128)(e_k - 8) << 32) - (__int128)c->rs_phase0;   /* m rs_step < lim */
+        r_k = lim <= 0 ? 0 : (int64_t)((lim + c->rs_step - 1) / c->rs_step);
+        if (r_k < h->r_prev) r_k = h->r_prev;
+    }
+    int64_t f_k = (r_k >= h->hmf + 1) ? (r_k - h->hmf - 1) / h->dec + 1 : 0;
     if (h->fd) {   /* whole blocks: block b needs the inputs up to hop*b + 3N/4 */
         int64_t N = c->fd_n, hop = N / 2;
-        int64_t bk = (e_k >= 3 * N / 4) ? (e_k - 3 * N / 4) / hop + 1 : 0;
+        int64_t bk = (r_k >= 3 * N / 4) ? (r_k - 3 * N / 4) / hop + 1 : 0;
         f_k = bk * (hop / h->dec);
     }
     int64_t s_k = (f_k >= h->th + 1) ? (f_k - h->th - 1) / 2 + 1 : 0;
@@ -568,6 +609,18 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
         h->carrier = cx_scale(sumE, 1.0 / (double)X.E_len);
         double P = sumI / (double)X.E_len - cx_abs2(h->carrier);
         h->gain = (P > 0.0) ? 1.0 / sqrt((double)c->sps * P) : 1.0;
+    }
+    X.R_start = h->r_prev; X.R_len = h->rs ? r_k - h->r_prev : 0;
+    X.R = xcalloc((size_t)(X.R_len > 0 ? X.R_len : 1), sizeof(cx));
+    for (int64_t m = h->r_prev; m < r_k && h->rs; m++) {
+        __int128 psi = (__int128)c->rs_phase0 + (__int128)m * c->rs_step;
+        int64_t i = (int64_t)(psi >> 32);
+        uint32_t fr = (uint32_t)(psi & 0xFFFFFFFF);
+        double cj[16];
+        orx_rs_taps((double)(fr >> 22) / 1024.0, cj);
+        cx acc = cx_mk(0.0, 0.0);
+        for (int j = -7; j <= 8; j++) acc = cx_add(acc, cx_scale(e_at(&X, i + j), cj[j + 7]));
+        X.R[m - X.R_start] = acc;
     }
     if (!h->kk) {
         /* DC removal and scaling by the buffer's mean and standard deviation */
@@ -609,7 +662,7 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
                 cx xn = cx_mk(0.0, 0.0);
                 if (n >= 0) {
                     int64_t p = ((n % c->ds_den) * c->ds_num) % c->ds_den;
-                    xn = cx_mul(cx_sub(e_at(&X, n), h->carrier), cx_expj(-2.0 * PI * (double)p / (double)c->ds_den));
+                    xn = cx_mul(cx_sub(r_at(&X, n), h->carrier), cx_expj(-2.0 * PI * (double)p / (double)c->ds_den));
                 }
                 xr[t] = xn.re; xi[t] = xn.im;
             }
@@ -628,7 +681,7 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
             if (h->kk) {
                 /* carrier removal, then downshift by ds_num/ds_den cycles/sample */
                 int64_t p = ((n % c->ds_den) * c->ds_num) % c->ds_den;
-                xn = cx_mul(cx_sub(e_at(&X, n), h->carrier),
+                xn = cx_mul(cx_sub(r_at(&X, n), h->carrier),
                             cx_expj(-2.0 * PI * (double)p / (double)c->ds_den));
             } else {
                 xn = cx_mk(((double)code_at(&X, n) - X.mu_pam) / X.sd_pam, 0.0);
@@ -810,6 +863,8 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
     free(h->d_E); free(h->d_y); free(h->d_z); free(h->d_v); free(h->d_ahat);
     free(h->d_draw); free(h->d_berr); free(h->d_near); free(h->d_win);
     h->d_E = X.E; h->d_E_start = X.E_start; h->d_E_len = X.E_len > 0 ? X.E_len : 0;
+    free(h->d_R);
+    h->d_R = X.R; h->d_R_start = X.R_start; h->d_R_len = X.R_len > 0 ? X.R_len : 0;
     h->d_y = X.y; h->d_y_start = X.y_start; h->d_y_len = X.y_len > 0 ? X.y_len : 0;
     h->d_z = Z; h->d_v = Vv; h->d_ahat = ahat; h->d_draw = draw; h->d_berr = berr; h->d_near = nearf;
     h->d_s_start = sym_lo; h->d_s_len = nproc;
@@ -819,9 +874,20 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
     free(msym);
 
     /* ---- carry the stream state to the next buffer ----------------------- */
-    if (h->kk && e_k > 0) {
+    if (h->kk && h->rs && r_k > 0) {
+        /* the filter's history on the transmitter grid */
         int64_t lo = h->fd ? (int64_t)h->dec * f_k - c->fd_n / 4 : (int64_t)h->dec * f_k - h->hmf;
         if (lo < 0) lo = 0;
+        cx *nh = xcalloc((size_t)(r_k - lo + 1), sizeof(cx));
+        for (int64_t m = lo; m < r_k; m++) nh[m - lo] = r_at(&X, m);
+        free(h->rhist); h->rhist = nh; h->rhist_start = lo; h->rhist_len = r_k - lo;
+    }
+    if (h->kk && e_k > 0) {
+        int64_t lo = h->fd ? (int64_t)h->dec * f_k - c->fd_n / 4 : (int64_t)h->dec * f_k - h->hmf;
+        if (h->rs)   /* the resampler's next input: from i at nominal r_k, less 7 */
+            lo = (int64_t)((((__int128)c->rs_phase0 + (__int128)r_k * c->rs_step) >> 32)) - 7;
+        if (lo < 0) lo = 0;
+        if (lo > e_k) lo = e_k;
         cx *nh = xcalloc((size_t)(e_k - lo + 1), sizeof(cx));
         for (int64_t n = lo; n < e_k; n++) nh[n - lo] = e_at(&X, n);
         free(h->ehist); h->ehist = nh; h->ehist_start = lo; h->ehist_len = e_k - lo;
@@ -840,7 +906,7 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
         for (int64_t i = 0; i < keep; i++) nh[i] = code_at(&X, avail - keep + i);
         free(h->chist); h->chist = nh; h->chist_len = keep;
     }
-    h->e_prev = e_k; h->f_prev = f_k; h->q_prev = q_k;
+    h->e_prev = e_k; h->f_prev = f_k; h->q_prev = q_k; h->r_prev = r_k;
     h->calls++;
     h->n_samples += Nb;
     free(cur);
@@ -853,6 +919,7 @@ int64_t orx_get(orx *h, int what, void *dst, int64_t cap, int64_t *start)
     const void *src = NULL;
     switch (what) {
     case ORX_E: n = h->d_E_len; s = h->d_E_start; src = h->d_E; width = sizeof(cx); break;
+    case ORX_RS: n = h->d_R_len; s = h->d_R_start; src = h->d_R; width = sizeof(cx); break;
     case ORX_Y: n = h->d_y_len; s = h->d_y_start; src = h->d_y; width = sizeof(cx); break;
     case ORX_Z: n = h->d_s_len; s = h->d_s_start; src = h->d_z; width = sizeof(cx); break;
     case ORX_V: n = h->d_s_len; s = h->d_s_start; src = h->d_v; width = sizeof(cx); break;
@@ -886,7 +953,7 @@ void orx_destroy(orx *h)
 {
     if (!h) return;
     free(h->rrc); free(h->prbs); free(h->chist); free(h->ehist); free(h->yhist); free(h->w);
-    free(h->fd_Hr); free(h->fd_Hi);
+    free(h->fd_Hr); free(h->fd_Hi); free(h->rhist); free(h->d_R);
     free(h->d_E); free(h->d_y); free(h->d_z); free(h->d_v); free(h->d_ahat);
     free(h->d_draw); free(h->d_berr); free(h->d_near); free(h->d_win);
     free(h);

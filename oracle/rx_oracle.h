@@ -54,6 +54,11 @@ typedef struct {
                             input rate (fd_n-point inverse)                              */
     int32_t fd_n;        /* frequency-domain block length (power of two, >= 16)           */
     int32_t fd_taps;     /* frequency-domain filter taps (odd, <= fd_n/2 + 1)             */
+    int32_t pad_rs;
+    int64_t rs_step;     /* KK resampler to the transmitter's sample grid: 0 off; else the
+                            ADC position of nominal sample m is (rs_phase0 + m rs_step) /
+                            2^32 ADC samples (exact integer accumulator)                 */
+    int64_t rs_phase0;
 } orx_cfg;
 
 typedef struct {
@@ -77,6 +82,7 @@ void    orx_rrc_half(double beta, int sps, int half, double *taps);
 void    orx_fd_response(const double *h, int ntaps, int n, double *H_re, double *H_im);
 void    orx_fd_block(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
                      double *y_re, double *y_im);
+void    orx_rs_taps(double mu, double *c);   /* the 16 interpolator taps at fraction mu */
 void    orx_fd_block_full(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
                           double *y_re, double *y_im);
 void    orx_prbs15(uint32_t seed, int64_t nbits, uint8_t *out);
@@ -109,7 +115,8 @@ enum {
     ORX_TAPS = 8,    /* start taps for the next call, complex                               */
     ORX_SCAL = 9,    /* carrier re, carrier im, gain g, PAM mean, PAM std (5 doubles)       */
     ORX_NEAR = 10,   /* near-threshold flag per processed symbol, int32                      */
-    ORX_DRAW = 11    /* raw decision level-index pair before pi/2 rotation, int32 x2        */
+    ORX_DRAW = 11,   /* raw decision level-index pair before pi/2 rotation, int32 x2        */
+    ORX_RS = 12      /* resampled field on the transmitter's grid (complex)                  */
 };
 
 #ifdef __cplusplus

@@ -135,6 +135,42 @@ def rrc_pulse(beta: float, sps: int, span: int) -> np.ndarray:
     return p / np.sqrt(np.sum(p * p))
 
 
+def rrc_at(beta: float, sps: int, span: int, t: np.ndarray) -> np.ndarray:
+    """The pulse of rrc_pulse(beta, sps, span) at arbitrary sample offsets t (zero
+    beyond +-span/2 symbols), on the same scale as its integer-offset taps."""
+    x = np.asarray(t, dtype=np.float64) / sps
+    v = np.empty_like(x)
+    z = np.abs(x) < 1e-12
+    e = (~z) & (np.abs(np.abs(4.0 * beta * x) - 1.0) < 1e-9) if beta > 0 else np.zeros_like(z)
+    g = ~(z | e)
+    v[z] = 1.0 - beta + 4.0 * beta / np.pi
+    if beta > 0:
+        v[e] = beta / np.sqrt(2.0) * ((1 + 2 / np.pi) * np.sin(np.pi / (4 * beta))
+                                      + (1 - 2 / np.pi) * np.cos(np.pi / (4 * beta)))
+    xg = x[g]
+    v[g] = (np.sin(np.pi * xg * (1 - beta)) + 4 * beta * xg * np.cos(np.pi * xg * (1 + beta))) / \
+        (np.pi * xg * (1 - (4 * beta * xg) ** 2))
+    v[np.abs(x) > span / 2] = 0.0
+    ref = rrc_pulse(beta, sps, span)
+    return v * (ref[len(ref) // 2] / (1.0 - beta + 4.0 * beta / np.pi))
+
+
+def adc_times(n0: int, n1: int, clock_step: int, clock_phase0: int):
+    """Transmitter time of ADC samples n0..n1-1 in nominal samples, from the integer
+    phase accumulator phi_n = phase0 + n * step (2^32 per nominal sample):
+    returns (integer part, fraction) of phi_n / 2^32."""
+    n = np.arange(n0, n1, dtype=object)
+    phi = [clock_phase0 + int(k) * clock_step for k in n]
+    ip = np.array([q >> 32 for q in phi], dtype=np.int64)
+    fr = np.array([(q & 0xFFFFFFFF) / 4294967296.0 for q in phi], dtype=np.float64)
+    return ip, fr
+
+
+def clock_step(ppm: float) -> int:
+    """Accumulator step of an ADC clock whose period is (1 + ppm 1e-6) nominal samples."""
+    return int(round((1.0 + ppm * 1e-6) * 4294967296.0))
+
+
 def pack12(codes: np.ndarray, order: int = 0) -> np.ndarray:
     """Pack 12-bit codes two per three bytes.
 
@@ -272,7 +308,7 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
               beta: float = 0.1, span: int = 16, fd_num: int = 11, fd_den: int = 80,
               noise: bool = True, phase_noise: bool = True, volterra=(0.0, 0.0),
               prbs_seed: int = 1, pack_order: int = 0, symbols=None, phase_steps=(),
-              truth: bool = True):
+              truth: bool = True, clock_step: int = 1 << 32, clock_phase0: int = 0):
     """Buffer b of a Kramers-Kronig single-sideband QAM stream (see gen_kk_stream)."""
     name, bps, kind = FORMATS[fmt]
     assert kind == "qam"
@@ -280,6 +316,10 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
     pulse = rrc_pulse(beta, sps, span)
     half = span // 2 + 2
     ka, kb = (n0 - sps) // sps - half, n1 // sps + half + 1
+    offclock = clock_step != (1 << 32) or clock_phase0 != 0
+    if offclock:   # the ADC samples at transmitter times phi_n / 2^32 (nominal samples)
+        ti, tf = adc_times(n0, n1, clock_step, clock_phase0)
+        ka, kb = int(ti[0]) // sps - half - 2, int(ti[-1]) // sps + half + 3
     if symbols is None:
         a_seg = _tx_symbols(fmt, prbs_seed, ka, kb)
         Es = 1.0   # unit-power constellation
@@ -295,16 +335,27 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
     sig2 = Ps * sps / 10.0 ** (snr_db / 10.0)
     pn_std = np.sqrt(2.0 * np.pi * linewidth / fs)
     # shaped baseband for samples [n0 - sps, n1): symbols re-indexed from ka
-    s = _shape(a_seg, pulse, sps, n0 - sps - ka * sps, n1 - ka * sps)
-    c1, c2 = volterra
-    if c1 != 0.0 or c2 != 0.0:
-        p = np.abs(s) ** 2
-        nl = c1 * s * p
-        nl[sps:] += c2 * s[:-sps] * p[:-sps]
-        s = s + nl
-    s = s[sps:]
-    n = np.arange(n0, n1, dtype=np.int64)
-    up = np.exp(2j * np.pi * np.arange(fd_den) / fd_den)[(n * fd_num) % fd_den]
+    if offclock:
+        assert volterra == (0.0, 0.0), "clock offset with the Volterra channel is not generated"
+        s = np.zeros(buf_len, dtype=np.complex128)
+        kc = ti // sps                   # symbol at or before each sample time
+        for d in range(-(span // 2) - 1, span // 2 + 2):
+            k = kc + d
+            s += a_seg[k - ka] * rrc_at(beta, sps, span, (ti - sps * k) + tf)
+        n = ti                           # integer part of the transmitter time
+        frac_up = np.exp(2j * np.pi * (fd_num / fd_den) * tf)
+    else:
+        s = _shape(a_seg, pulse, sps, n0 - sps - ka * sps, n1 - ka * sps)
+        c1, c2 = volterra
+        if c1 != 0.0 or c2 != 0.0:
+            p = np.abs(s) ** 2
+            nl = c1 * s * p
+            nl[sps:] += c2 * s[:-sps] * p[:-sps]
+            s = s + nl
+        s = s[sps:]
+        n = np.arange(n0, n1, dtype=np.int64)
+        frac_up = 1.0
+    up = np.exp(2j * np.pi * np.arange(fd_den) / fd_den)[(n * fd_num) % fd_den] * frac_up
     if phase_noise and linewidth > 0:
         inc = np.random.default_rng([int(seed), b, 31]).standard_normal(buf_len) * pn_std
         th = theta0 + np.cumsum(inc)
@@ -335,7 +386,7 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
                   fd_den: int = 80, noise: bool = True, phase_noise: bool = True,
                   volterra=(0.0, 0.0), prbs_seed: int = 1, pack_order: int = 0,
                   symbols=None, phase_offset: float = 0.0, phase_steps=(), workers: int = 1,
-                  truth: bool = True):
+                  truth: bool = True, clock_step: int = 1 << 32, clock_phase0: int = 0):
     """Kramers-Kronig single-sideband QAM stream split into ADC buffers.
 
     The signal sits above a real tone at 0 Hz after an up-shift of fd_num/fd_den
@@ -344,6 +395,9 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
     symbols (used for training data that must not follow an LFSR recurrence).
     ``phase_steps`` = [(sample, dtheta), ...] adds instantaneous phase jumps.
     ``workers`` > 1 makes the buffers in a spawn-started process pool.
+    ``clock_step`` / ``clock_phase0``: the ADC takes sample n at transmitter time
+    (clock_phase0 + n clock_step) / 2^32 nominal samples (integer accumulator; see
+    clock_step()); the default is the nominal grid.
     Returns dict with 'packed' (per buffer), 'codes', 'symbols' (the transmitted
     symbols of the stream), 'field' (noiseless complex baseband at sps, before the
     shift: what the receiver should recover; with truth=True) and 'clips'.
@@ -355,7 +409,8 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
               linewidth=linewidth, fs=fs, sps=sps, beta=beta, span=span, fd_num=fd_num,
               fd_den=fd_den, noise=noise, phase_noise=phase_noise, volterra=volterra,
               prbs_seed=prbs_seed, pack_order=pack_order, symbols=symbols,
-              phase_steps=tuple(phase_steps), truth=truth)
+              phase_steps=tuple(phase_steps), truth=truth, clock_step=int(clock_step),
+              clock_phase0=int(clock_phase0))
     th0 = kk_phase_starts(buf_len, nbufs, seed, linewidth, fs, phase_noise, phase_offset)
     jobs = [(kw, b, th0[b]) for b in range(nbufs)]
     if workers > 1 and nbufs > 1:
