@@ -100,7 +100,16 @@ typedef struct {
                             (Sec. 2: FD equaliser on a 1024-point FFT, 512-point IFFT) */
     int32_t fd_n;        /* RX_MF_FD block length: power of two, 16 .. 1024; default 1024  */
     int32_t fd_taps;     /* RX_MF_FD filter taps (root-raised cosine, zero phase, unit
-                            energy): odd, <= fd_n/2 + 1; default 203                       */
+                            energy): odd, <= fd_n/2 + 1; default 203 (KK), 503 (PAM)      */
+    int32_t pad_rs;      /* reserved, 0                                                    */
+    int64_t rs_step;     /* KK resampler to the transmitter's sample grid (the ADC runs on
+                            its own clock; Sec. 2 recovers the clock phase in the DSP):
+                            0 = off (default); else nominal sample m lies at ADC position
+                            (rs_phase0 + m rs_step) / 2^32, an exact integer accumulator,
+                            and the reconstructed field is interpolated there by a 16-tap
+                            Hann-windowed sinc (taps j = -7..8 at the fraction rounded
+                            down to 10 bits) before the filter.  Within 1 % of 2^32.     */
+    int64_t rs_phase0;   /* accumulator value of nominal sample 0 (may be negative)        */
 } rx_config;
 
 /* Reduction to 2 samples/symbol of the KK chain (rx_config.mf_mode). */
@@ -148,7 +157,8 @@ enum {
                             the metrics need debug=1                                         */
     RX_DBG_TAPS = 6,     /* start taps of the next call, float2 per tap                      */
     RX_DBG_SCAL = 7,     /* double[5]: carrier re, carrier im, gain, PAM mean, PAM 1/std     */
-    RX_DBG_CODES = 8     /* uint16 12-bit code per ADC sample of the last buffer             */
+    RX_DBG_CODES = 8,    /* uint16 12-bit code per ADC sample of the last buffer             */
+    RX_DBG_RS = 9        /* KK field resampled to the transmitter's grid, float2 (rs_step)    */
 };
 
 /* Defaults of a format (the workload settings of the synthetic configurations). */

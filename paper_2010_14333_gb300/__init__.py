@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_PKG, "librx.so")
 
 RX_PAM2, RX_PAM4, RX_PAM8, RX_KK_QPSK, RX_KK_16QAM = range(5)
 RX_FIR_ADAPTIVE, RX_FIR_FROZEN_F32, RX_FIR_BF16, RX_FIR_FP16, RX_FIR_FP8 = range(5)
-RX_DBG_FIELD, RX_DBG_MF, RX_DBG_SOFT, RX_DBG_DEC, RX_DBG_WIN, RX_DBG_TAPS, RX_DBG_SCAL, RX_DBG_CODES = range(1, 9)
+RX_DBG_FIELD, RX_DBG_MF, RX_DBG_SOFT, RX_DBG_DEC, RX_DBG_WIN, RX_DBG_TAPS, RX_DBG_SCAL, RX_DBG_CODES, RX_DBG_RS = \
+    range(1, 10)
 BITS_PER_SYMBOL = {0: 1, 1: 2, 2: 3, 3: 2, 4: 4}
 
 
@@ -32,6 +33,7 @@ class RxConfig(C.Structure):
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
         ("debug", C.c_int32), ("fir_prec", C.c_int32), ("kk_front", C.c_int32), ("eq_warps", C.c_int32),
         ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
+        ("pad_rs", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
     ]
 
 
@@ -350,7 +352,7 @@ class Receiver:
 
     _DT = {RX_DBG_FIELD: (np.complex64, 1), RX_DBG_SOFT: (np.complex64, 1), RX_DBG_DEC: (np.uint8, 1),
            RX_DBG_WIN: (np.float32, 4), RX_DBG_TAPS: (np.complex64, 1), RX_DBG_SCAL: (np.float64, 1),
-           RX_DBG_CODES: (np.uint16, 1)}
+           RX_DBG_CODES: (np.uint16, 1), RX_DBG_RS: (np.complex64, 1)}
 
     def debug(self, what: int):
         n, s = rx_debug_copy(self.h, what, None, 0, self.stream())

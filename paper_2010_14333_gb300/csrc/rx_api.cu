@@ -74,6 +74,11 @@ struct rx_handle {
     uint8_t *in_stage[2], *bits_stage;   // device staging of the host-buffer entry points
     float2 *zbuf;                   // payload soft symbols of the tensor-core FIR forms
     float2 *gpart;                  // frozen forms: tap-gradient partials, one row of 32 per window
+    int rs;                         // resampler of the KK field to the transmitter's grid
+    float2 *R[2];                   // resampled field ping-pong [kEHist history | call]
+    int rw;                         // R slot of the last call
+    long long r_prev, rbase_cur, l_r_prev, l_r_k;
+    float *rs_tab;                  // 1024 x 16 interpolator taps
     int fd;                         // frequency-domain reduction to 2 samples/symbol
     float2 *fd_H, *fd_tw;           // its kept-bin response (times 1/N) and N-point twiddles
     long long dec_cap, win_cap, y_cap;
@@ -187,17 +192,25 @@ static void twiddles(int n, float2 *out)   // e^{-2 pi i k / n}
 
 // ------------------------------------------------------------------- schedule
 struct Sched {
-    long long avail, e_k, f_k, s_k, q_k;
+    long long avail, e_k, r_k, f_k, s_k, q_k;
 };
+// nominal samples the resampler can emit from the field [0, e_k): #{m >= 0 :
+// floor((phase0 + m step) / 2^32) + 8 < e_k}, exact in 128-bit integers
+static long long rs_count(const rx_config &c, long long e_k)
+{
+    __int128 lim = ((__int128)(e_k - 8) << 32) - (__int128)c.rs_phase0;
+    return lim <= 0 ? 0 : (long long)((lim + c.rs_step - 1) / c.rs_step);
+}
 static Sched schedule(const rx_handle *h, long long calls, long long q_prev)
 {
     Sched s;
     s.avail = (calls + 1) * h->nb;
     s.e_k = h->kk ? s.avail - h->V / 2 : s.avail;
     if (s.e_k < 0) s.e_k = 0;
-    s.f_k = (s.e_k >= h->hmf + 1) ? (s.e_k - h->hmf - 1) / h->decim + 1 : 0;
+    s.r_k = h->rs ? rs_count(h->cfg, s.e_k) : s.e_k;   // the filter's input on its own grid
+    s.f_k = (s.r_k >= h->hmf + 1) ? (s.r_k - h->hmf - 1) / h->decim + 1 : 0;
     if (h->fd) {   // whole frequency-domain blocks: block b reads up to N/2 b + 3N/4
-        long long N = h->cfg.fd_n, bk = (s.e_k >= 3 * N / 4) ? (s.e_k - 3 * N / 4) / (N / 2) + 1 : 0;
+        long long N = h->cfg.fd_n, bk = (s.r_k >= 3 * N / 4) ? (s.r_k - 3 * N / 4) / (N / 2) + 1 : 0;
         s.f_k = bk * (N / 2) / h->decim;
     }
     s.s_k = (s.f_k >= h->th + 1) ? (s.f_k - h->th - 1) / 2 + 1 : 0;
@@ -270,7 +283,8 @@ void rx_destroy(rx_handle *h)
     if (h->copy) cudaStreamSynchronize(h->copy);
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->partials, h->prbs, h->taps[0], h->taps[1], h->twN,
                     h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
-                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->zbuf, h->gpart, h->fd_H, h->fd_tw};
+                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->zbuf, h->gpart, h->fd_H, h->fd_tw, h->R[0], h->R[1],
+                    h->rs_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kSlots; i++) {
@@ -334,6 +348,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         return RX_EINVAL;
     if (c.kk_front < 0 || c.kk_front > 1 || !(c.eq_warps == 0 || c.eq_warps == 2 || c.eq_warps == 4 || c.eq_warps == 8))
         return RX_EINVAL;
+    if (c.rs_step != 0 && (!kk || c.rs_step < 4252017623LL || c.rs_step > 4337916969LL)) return RX_EINVAL;
     if (c.mf_mode < RX_MF_TIME || c.mf_mode > RX_MF_FD ||
         (c.mf_mode == RX_MF_FD && (c.fd_n < 16 || c.fd_n > kEHist || (c.fd_n & (c.fd_n - 1)) ||
                                    (!kk && c.fd_n != 1024) || c.fd_taps < 1 || !(c.fd_taps & 1) ||
@@ -353,6 +368,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     h->decim = sps / 2;
     h->hmf = sps * c.mf_span / 2;
     h->fd = c.mf_mode == RX_MF_FD;
+    h->rs = c.rs_step != 0;
     h->th = (c.ntaps - 1) / 2;
     h->nb = buf_len;
     h->cfg = c;
@@ -422,6 +438,10 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     }
     if (kk) {
         for (int i = 0; i < kSlots; i++) RX_ALLOC(h->E[i], (kEHist + nb) * sizeof(float2));
+        if (h->rs) {   // a call emits at most nb / 0.99 + 8 nominal samples
+            for (int i = 0; i < 2; i++) RX_ALLOC(h->R[i], (kEHist + nb + nb / 64 + 64) * sizeof(float2));
+            RX_ALLOC(h->rs_tab, 1024 * 16 * sizeof(float));
+        }
         for (int i = 0; i < 2; i++) RX_ALLOC(h->phist[i], (size_t)h->nhist * 3 / 2 + 16);
         RX_ALLOC(h->fftws, (size_t)h->npairs_max * h->N * sizeof(float2));
         int gx = (h->N2 + kCtaK1 - 1) / kCtaK1;
@@ -515,6 +535,20 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         free(Hk);
         free(tw);
     }
+    if (h->rs) {
+        // interpolator taps c_j(q / 1024) = sinc(j - mu) (1 + cos(pi (j - mu) / 8)) / 2, j = -7..8
+        const double pi = 3.14159265358979323846;
+        float *tab = (float *)malloc(sizeof(float) * 1024 * 16);
+        for (int q = 0; q < 1024; q++)
+            for (int j = -7; j <= 8; j++) {
+                double x = (double)j - q / 1024.0;
+                double sn = fabs(x) < 1e-15 ? 1.0 : sin(pi * x) / (pi * x);
+                double w = fabs(x) < 8.0 ? 0.5 * (1.0 + cos(pi * x / 8.0)) : 0.0;
+                tab[q * 16 + j + 7] = (float)(sn * w);
+            }
+        if (e == cudaSuccess) e = cudaMemcpy(h->rs_tab, tab, sizeof(float) * 1024 * 16, cudaMemcpyHostToDevice);
+        free(tab);
+    }
     DevState s0;
     memset(&s0, 0, sizeof s0);
     for (int i = 0; i < kSlots; i++) s0.cg[i][2] = 1.0;
@@ -526,6 +560,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         return RX_ECUDA;
     }
     h->ebase_cur = -kEHist;
+    h->rbase_cur = -kEHist;
     h->ybase_cur = -kYHist;
     {
         int least = 0, greatest = 0;
@@ -669,18 +704,30 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         cudaEventRecord(h->ev_front, sf);
         cudaStreamWaitEvent(sm, h->ev_front, 0);
     }
-    // matched filter
+    // matched filter (after the resampler when the ADC clock is not the transmitter's)
     prof_begin(h, 4, sm);
+    if (e == cudaSuccess && h->kk && h->rs && s.r_k > h->r_prev) {
+        const __int128 psi = (__int128)c.rs_phase0 + (__int128)h->r_prev * c.rs_step;
+        const long long rb = h->r_prev - kEHist;
+        e = launch_kk_resample(h->E[h->ew], h->ebase_cur, h->r_prev, s.r_k, (long long)(psi >> 32),
+                               (unsigned)(psi & 0xFFFFFFFF), c.rs_step, h->rs_tab, h->R[h->rw ^ 1], rb,
+                               h->R[h->rw], h->rbase_cur, sm);
+        h->rw ^= 1;
+        h->rbase_cur = rb;
+    }
     if (e == cudaSuccess && s.f_k > h->f_prev) {
         long long yb = 2 * h->q_prev - kYHist;
         int yw_new = (h->yw + 1) % kSlots;
         if (two) cudaStreamWaitEvent(sm, h->ev_yfree[yw_new], 0);   // the back end is done with this slot
+        // the filter reads the field on the transmitter's grid: resampled, or as reconstructed
+        const float2 *Ef = h->kk && h->rs ? h->R[h->rw] : h->E[h->ew];
+        const long long efbase = h->kk && h->rs ? h->rbase_cur : h->ebase_cur;
         if (h->kk && h->fd)
-            e = launch_kk_fdmf(h->E[h->ew], h->ebase_cur, h->f_prev, s.f_k, c.fd_n, h->fd_H, h->fd_tw, h->ds_tab,
+            e = launch_kk_fdmf(Ef, efbase, h->f_prev, s.f_k, c.fd_n, h->fd_H, h->fd_tw, h->ds_tab,
                                c.ds_num, c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb,
                                (const float2 *)h->Y[h->yw], h->ybase_cur, sm);
         else if (h->kk)
-            e = launch_kk_mf(h->E[h->ew], h->ebase_cur, s.e_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
+            e = launch_kk_mf(Ef, efbase, s.r_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
                              c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw],
                              h->ybase_cur, sm, h->rrc_host);
         else if (h->fd)
@@ -770,6 +817,8 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     }
     h->l_e_prev = h->e_prev;
     h->l_e_k = s.e_k;
+    h->l_r_prev = h->r_prev;
+    h->l_r_k = s.r_k;
     h->l_f_prev = h->f_prev;
     h->l_f_k = s.f_k;
     h->l_sym_lo = sym_lo;
@@ -778,6 +827,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     h->l_nwin = g.nwin;
     h->l_ds = ds;
     h->e_prev = s.e_k;
+    h->r_prev = s.r_k;
     h->f_prev = s.f_k;
     h->q_prev = s.q_k;
     h->calls++;
@@ -906,6 +956,13 @@ rx_status rx_debug_copy(rx_handle *h, int what, void *dst, int64_t cap, int64_t 
         n = h->l_e_k - h->l_e_prev;
         s0 = h->l_e_prev;
         src = h->E[h->ew] + kEHist;
+        el = sizeof(float2);
+        break;
+    case RX_DBG_RS:
+        if (!h->rs) return RX_EINVAL;
+        n = h->l_r_k - h->l_r_prev;
+        s0 = h->l_r_prev;
+        src = h->R[h->rw] + (h->l_r_prev - h->rbase_cur);
         el = sizeof(float2);
         break;
     case RX_DBG_MF:

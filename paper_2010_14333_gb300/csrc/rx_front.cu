@@ -1022,6 +1022,67 @@ cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long l
     return cudaGetLastError();
 }
 
+// ================================================ resampler to the transmitter's grid
+// The ADC runs on its own clock (Sec. 2: the DSP recovers the clock phase).  Nominal
+// sample m of the transmitter's grid lies at ADC position psi_m / 2^32 with the exact
+// integer accumulator psi_m = psi_{m0} + (m - m0) step; its field is the 16-tap
+// Hann-windowed sinc interpolation sum_{j=-7..8} c_j(mu) E[i + j] of the
+// reconstructed field at i = floor(psi / 2^32) and the fraction mu rounded down to
+// 10 bits (a 1024 x 16 table).  The host splits psi_{m0} (m0 = this call's first
+// output) into its integer part i0 and fraction f0, so every offset inside a call
+// fits in 64 bits.  One CTA per kRsOut outputs stages their ADC window in shared
+// memory first.
+constexpr int kRsOut = 256, kRsWin = kRsOut + kRsOut / 64 + 24;
+
+__global__ void __launch_bounds__(kRsOut) k_kk_resample(const float2 *__restrict__ E, long long ebase,
+                                                       long long r_prev, long long r_k, long long i0,
+                                                       unsigned f0, long long step, const float *__restrict__ tab,
+                                                       float2 *__restrict__ R, long long rbase,
+                                                       const float2 *__restrict__ R_prev, long long rbase_prev)
+{
+    __shared__ float2 xs[kRsWin];
+    const long long m0 = r_prev + (long long)blockIdx.x * kRsOut;
+    const long long mlast = min(m0 + kRsOut - 1, r_k - 1);
+    const long long a0 = i0 + (((long long)f0 + (m0 - r_prev) * step) >> 32) - 7;
+    const long long a1 = i0 + (((long long)f0 + (mlast - r_prev) * step) >> 32) + 8;
+    const int len = (int)(a1 - a0 + 1);
+    for (int t = threadIdx.x; t < len && t < kRsWin; t += blockDim.x) {
+        const long long n = a0 + t;
+        xs[t] = n < 0 ? make_float2(0.f, 0.f) : E[n - ebase];
+    }
+    if (blockIdx.x == 0)   // the filter's history on the nominal grid
+        for (long long m = rbase + threadIdx.x; m < r_prev; m += blockDim.x)
+            R[m - rbase] = (m < 0) ? make_float2(0.f, 0.f) : R_prev[m - rbase_prev];
+    __syncthreads();
+    const long long m = m0 + threadIdx.x;
+    if (m > mlast) return;
+    const long long acc = (long long)f0 + (m - r_prev) * step;
+    const int li = (int)(i0 + (acc >> 32) - 7 - a0);   // local index of E[i - 7]
+    const float *c = tab + ((unsigned)(acc & 0xFFFFFFFFLL) >> 22) * 16;
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        const float cj = __ldg(c + j);
+        const float2 v = xs[li + j];
+        re = fmaf(cj, v.x, re);
+        im = fmaf(cj, v.y, im);
+    }
+    R[m - rbase] = make_float2(re, im);
+}
+
+cudaError_t launch_kk_resample(const float2 *E, long long ebase, long long r_prev, long long r_k, long long i0,
+                               unsigned f0, long long step, const float *tab, float2 *R, long long rbase,
+                               const float2 *R_prev, long long rbase_prev, cudaStream_t st)
+{
+    // the window of kRsOut outputs spans at most kRsOut step / 2^32 + 17 ADC samples
+    if (step <= 0 || step > (1LL << 32) + (1LL << 32) / 64) return cudaErrorInvalidValue;
+    const long long n = r_k - r_prev;
+    if (n <= 0) return cudaSuccess;
+    k_kk_resample<<<(unsigned)((n + kRsOut - 1) / kRsOut), kRsOut, 0, st>>>(E, ebase, r_prev, r_k, i0, f0, step, tab,
+                                                                           R, rbase, R_prev, rbase_prev);
+    return cudaGetLastError();
+}
+
 // ============================================ frequency-domain reduction (KK)
 // The paper's form of the filter before the equaliser (Sec. 2, KK chain): a
 // static filter applied in the frequency domain on overlap-save blocks of N =

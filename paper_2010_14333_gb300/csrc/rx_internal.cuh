@@ -122,6 +122,12 @@ cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long l
                          const float2 *Y_prev, long long ybase_prev, cudaStream_t st,
                          const float *rrc_host);
 
+// resampler of the KK field to the transmitter's grid: outputs [r_prev, r_k) at ADC
+// positions (i0 2^32 + f0 + (m - r_prev) step) / 2^32; tab: 1024 x 16 taps
+cudaError_t launch_kk_resample(const float2 *E, long long ebase, long long r_prev, long long r_k, long long i0,
+                               unsigned f0, long long step, const float *tab, float2 *R, long long rbase,
+                               const float2 *R_prev, long long rbase_prev, cudaStream_t st);
+
 // frequency-domain form (static filter on N-point overlap-save blocks, hop N/2,
 // N/2-point bin-truncation inverse); f_prev and f_k are multiples of N/4
 cudaError_t launch_kk_fdmf(const float2 *E, long long ebase, long long f_prev, long long f_k, int N,

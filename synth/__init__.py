@@ -155,14 +155,41 @@ def rrc_at(beta: float, sps: int, span: int, t: np.ndarray) -> np.ndarray:
     return v * (ref[len(ref) // 2] / (1.0 - beta + 4.0 * beta / np.pi))
 
 
+def _shape_at(sym_seg: np.ndarray, k0: int, beta: float, sps: int, span: int, ti: np.ndarray,
+              tf: np.ndarray) -> np.ndarray:
+    """sum_k sym[k] p(t - sps k) at sample times t = ti + tf (integer and fractional
+    parts, nominal samples) for the pulse of rrc_pulse; sym_seg[i] is symbol k0 + i.
+    With u = ((ti mod sps) + tf) / sps and x = u - d (d the symbol offset), the two
+    sines of the pulse follow from sin / cos of u by angle addition, so each sample
+    costs four trigonometric evaluations whatever the span."""
+    kc = ti // sps
+    u = ((ti - sps * kc) + tf) / sps
+    c1, c2 = np.pi * (1 - beta), np.pi * (1 + beta)
+    S1, C1, S2, C2 = np.sin(c1 * u), np.cos(c1 * u), np.sin(c2 * u), np.cos(c2 * u)
+    ref = rrc_pulse(beta, sps, span)
+    scale = ref[len(ref) // 2] / (1.0 - beta + 4.0 * beta / np.pi)
+    out = np.zeros(len(ti), dtype=np.complex128)
+    for d in range(-(span // 2) - 1, span // 2 + 2):
+        x = u - d
+        num = (S1 * np.cos(c1 * d) - C1 * np.sin(c1 * d)) + 4 * beta * x * (C2 * np.cos(c2 * d) + S2 * np.sin(c2 * d))
+        den = np.pi * x * (1 - (4 * beta * x) ** 2)
+        special = (np.abs(x) < 1e-9) | (np.abs(np.abs(4 * beta * x) - 1.0) < 1e-6)
+        v = np.where(special, 0.0, num / np.where(special, 1.0, den)) * scale
+        if special.any():
+            v[special] = rrc_at(beta, sps, span, sps * x[special])
+        v[np.abs(x) > span / 2] = 0.0
+        out += sym_seg[kc + d - k0] * v
+    return out
+
+
 def adc_times(n0: int, n1: int, clock_step: int, clock_phase0: int):
     """Transmitter time of ADC samples n0..n1-1 in nominal samples, from the integer
     phase accumulator phi_n = phase0 + n * step (2^32 per nominal sample):
     returns (integer part, fraction) of phi_n / 2^32."""
-    n = np.arange(n0, n1, dtype=object)
-    phi = [clock_phase0 + int(k) * clock_step for k in n]
-    ip = np.array([q >> 32 for q in phi], dtype=np.int64)
-    fr = np.array([(q & 0xFFFFFFFF) / 4294967296.0 for q in phi], dtype=np.float64)
+    assert 0 <= n0 and n1 < (1 << 30) and abs(clock_phase0) < (1 << 62) and 0 < clock_step < (1 << 33)
+    phi = np.int64(clock_phase0) + np.arange(n0, n1, dtype=np.int64) * np.int64(clock_step)   # < 2^63
+    ip = phi >> 32
+    fr = (phi & 0xFFFFFFFF).astype(np.float64) / 4294967296.0
     return ip, fr
 
 
@@ -337,11 +364,7 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
     # shaped baseband for samples [n0 - sps, n1): symbols re-indexed from ka
     if offclock:
         assert volterra == (0.0, 0.0), "clock offset with the Volterra channel is not generated"
-        s = np.zeros(buf_len, dtype=np.complex128)
-        kc = ti // sps                   # symbol at or before each sample time
-        for d in range(-(span // 2) - 1, span // 2 + 2):
-            k = kc + d
-            s += a_seg[k - ka] * rrc_at(beta, sps, span, (ti - sps * k) + tf)
+        s = _shape_at(a_seg, ka, beta, sps, span, ti, tf)
         n = ti                           # integer part of the transmitter time
         frac_up = np.exp(2j * np.pi * (fd_num / fd_den) * tf)
     else:

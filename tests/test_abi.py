@@ -88,6 +88,18 @@ def test_create_rejects_bad_fd_config(kw):
     assert lib.rx_create(rx.RX_PAM4, 2e9, 4e9, 1 << 20, C.byref(p), C.byref(h)) == 1
 
 
+def test_create_rejects_bad_resampler():
+    lib = rx.load()
+    h = C.c_void_p()
+    for step in (1 << 31, 2 << 32):
+        c = rx.rx_default_config(rx.RX_KK_16QAM)
+        c.rs_step = step
+        assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
+    p = rx.rx_default_config(rx.RX_PAM4)   # the resampler is the KK chain's
+    p.rs_step = 1 << 32
+    assert lib.rx_create(rx.RX_PAM4, 2e9, 4e9, 1 << 20, C.byref(p), C.byref(h)) == 1
+
+
 def test_fd_default_taps():
     assert rx.rx_default_config(rx.RX_KK_16QAM).fd_taps == 203
     assert rx.rx_default_config(rx.RX_PAM4).fd_taps == 503
