@@ -386,6 +386,7 @@ def gpu_arm(args, rank, world, local):
     fd_line = None
     if rank == 0 and not args.no_fd:
         fd_line = fd_leg(args, g, ring)
+    rs_line = resampler_leg(args, ring) if rank == 0 and not args.no_rs else None
     sweep_line = sweep_leg(args) if rank == 0 and args.sweep else None
     stab_line = stability_leg(args) if rank == 0 and args.stability > 0 else None
     batched_line = None
@@ -403,7 +404,7 @@ def gpu_arm(args, rank, world, local):
                     "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
             "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line, "precision": prec_line,
             "fd_filter": fd_line, "batched": batched_line,
-            "q_sweep": sweep_line, "stability": stab_line,
+            "resampler": rs_line, "q_sweep": sweep_line, "stability": stab_line,
             "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
             "realtime_x": value / 4.0,
             "ber": cpu["ber_gpu_same_buffers"] if cpu else None,
@@ -609,6 +610,50 @@ def fd_leg(args, g, ring):
                     "filter_us_per_buffer": ms["mf"] / max(calls, 1) * 1e3}
         del r
     out["pam4"] = pam_fd(args)
+    return out
+
+
+def resampler_leg(args, ring):
+    """The receiver with the resampler to the transmitter's grid (ADC clock off the
+    transmitter's): throughput over the benchmark ring with a -35 ppm accumulator
+    (the resampler's work does not depend on the data), and BER against the FP64
+    oracle on two buffers of a stream generated through a -35 ppm ADC clock with a
+    0.4-sample delay."""
+    import torch
+    import oracle
+    import synth
+    import paper_2010_14333_gb300 as rx
+    st, ph = synth.clock_step(-35.0), int(0.4 * (1 << 32))
+    rs_step, rs_phase0 = oracle.rs_params(st, ph)
+    t0 = time.perf_counter()
+    g = synth.gen_kk_stream(FMT, NB, 2, seed=11, truth=False, clock_step=st, clock_phase0=ph, workers=2, **GEN)
+    t_gen = time.perf_counter() - t0
+    o = oracle.Oracle(**oracle.default_cfg(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0))
+    d = rx.Receiver(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0)
+    plain = rx.Receiver(FMT, NB)
+    for p in g["packed"]:
+        o.process(p)
+        dv = torch.from_numpy(p).cuda()
+        d.process(dv)
+        plain.process(dv)
+    out = {"ppm": -35.0, "delay_samples": 0.4, "ber": d.stats()["ber"], "ber_oracle": o.stats()["ber"],
+           "ber_without_resampler": plain.stats()["ber"], "gen_s": t_gen}
+    del d, plain
+    r = rx.Receiver(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0)
+    for _ in range(2):
+        r.process_batch(ring)
+    torch.cuda.synchronize()
+    rx.rx_profile(r.h, 4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(2):
+        r.process_batch(ring)
+    e1.record()
+    torch.cuda.synchronize()
+    ms, calls = rx.rx_profile_read(r.h)
+    rx.rx_profile(r.h, 0)
+    out["gsa_s"] = 2 * len(ring) * NB / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    out["resampler_and_filter_us_per_buffer"] = ms["mf"] / max(calls, 1) * 1e3
     return out
 
 
@@ -884,6 +929,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fd", action="store_true")
+    ap.add_argument("--no-rs", action="store_true")
     ap.add_argument("--smi-ms", type=int, default=50, help="clock sampling period during the timed steps")
     ap.add_argument("--sweep", action="store_true", help="Q-factor versus SNR for every format")
     ap.add_argument("--stability", type=int, default=0, help="buffers of the Q time series (0: off)")

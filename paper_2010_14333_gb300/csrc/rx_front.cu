@@ -1032,9 +1032,9 @@ cudaError_t launch_kk_mf(const float2 *E, long long ebase, long long e_k, long l
 // output) into its integer part i0 and fraction f0, so every offset inside a call
 // fits in 64 bits.  One CTA per kRsOut outputs stages their ADC window in shared
 // memory first.
-constexpr int kRsOut = 256, kRsWin = kRsOut + kRsOut / 64 + 24;
+constexpr int kRsThreads = 256, kRsPer = 4, kRsOut = kRsThreads * kRsPer, kRsWin = kRsOut + kRsOut / 64 + 24;
 
-__global__ void __launch_bounds__(kRsOut) k_kk_resample(const float2 *__restrict__ E, long long ebase,
+__global__ void __launch_bounds__(kRsThreads) k_kk_resample(const float2 *__restrict__ E, long long ebase,
                                                        long long r_prev, long long r_k, long long i0,
                                                        unsigned f0, long long step, const float *__restrict__ tab,
                                                        float2 *__restrict__ R, long long rbase,
@@ -1042,10 +1042,15 @@ __global__ void __launch_bounds__(kRsOut) k_kk_resample(const float2 *__restrict
 {
     __shared__ float2 xs[kRsWin];
     const long long m0 = r_prev + (long long)blockIdx.x * kRsOut;
-    const long long mlast = min(m0 + kRsOut - 1, r_k - 1);
-    const long long a0 = i0 + (((long long)f0 + (m0 - r_prev) * step) >> 32) - 7;
-    const long long a1 = i0 + (((long long)f0 + (mlast - r_prev) * step) >> 32) + 8;
-    const int len = (int)(a1 - a0 + 1);
+    // the CTA's first output in integer part and fraction; with step = 2^32 + delta
+    // (|delta| < 2^32 / 64) thread t sits at i_b + t + floor((f_b + t delta) / 2^32)
+    const long long accb = (long long)f0 + (m0 - r_prev) * step;
+    const long long i_b = i0 + (accb >> 32);
+    const long long f_b = accb & 0xFFFFFFFFLL;
+    const int delta = (int)(step - (1LL << 32));
+    const int nout = (int)min((long long)kRsOut, r_k - m0);
+    const long long a0 = i_b - 7;
+    const int len = (nout - 1) + (int)((f_b + (long long)(nout - 1) * delta) >> 32) + 16;
     for (int t = threadIdx.x; t < len && t < kRsWin; t += blockDim.x) {
         const long long n = a0 + t;
         xs[t] = n < 0 ? make_float2(0.f, 0.f) : E[n - ebase];
@@ -1054,20 +1059,31 @@ __global__ void __launch_bounds__(kRsOut) k_kk_resample(const float2 *__restrict
         for (long long m = rbase + threadIdx.x; m < r_prev; m += blockDim.x)
             R[m - rbase] = (m < 0) ? make_float2(0.f, 0.f) : R_prev[m - rbase_prev];
     __syncthreads();
-    const long long m = m0 + threadIdx.x;
-    if (m > mlast) return;
-    const long long acc = (long long)f0 + (m - r_prev) * step;
-    const int li = (int)(i0 + (acc >> 32) - 7 - a0);   // local index of E[i - 7]
-    const float *c = tab + ((unsigned)(acc & 0xFFFFFFFFLL) >> 22) * 16;
-    float re = 0.f, im = 0.f;
 #pragma unroll
-    for (int j = 0; j < 16; j++) {
-        const float cj = __ldg(c + j);
-        const float2 v = xs[li + j];
-        re = fmaf(cj, v.x, re);
-        im = fmaf(cj, v.y, im);
+    for (int k = 0; k < kRsPer; k++) {   // outputs t, t + 256, ...: coalesced stores
+        const int t = threadIdx.x + kRsThreads * k;
+        if (t >= nout) return;
+        const long long v = f_b + (long long)t * delta;   // |v| < 2^39
+        const int li = t + (int)(v >> 32);                  // local index of E[i - 7]
+        const float4 *c4 = reinterpret_cast<const float4 *>(tab + ((unsigned)(v & 0xFFFFFFFFLL) >> 22) * 16);
+        float cj[16];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {   // the 64-byte row in four 16-byte loads
+            const float4 w = __ldg(c4 + q);
+            cj[4 * q] = w.x;
+            cj[4 * q + 1] = w.y;
+            cj[4 * q + 2] = w.z;
+            cj[4 * q + 3] = w.w;
+        }
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const float2 x = xs[li + j];
+            re = fmaf(cj[j], x.x, re);
+            im = fmaf(cj[j], x.y, im);
+        }
+        R[m0 + t - rbase] = make_float2(re, im);
     }
-    R[m - rbase] = make_float2(re, im);
 }
 
 cudaError_t launch_kk_resample(const float2 *E, long long ebase, long long r_prev, long long r_k, long long i0,
@@ -1075,10 +1091,10 @@ cudaError_t launch_kk_resample(const float2 *E, long long ebase, long long r_pre
                                const float2 *R_prev, long long rbase_prev, cudaStream_t st)
 {
     // the window of kRsOut outputs spans at most kRsOut step / 2^32 + 17 ADC samples
-    if (step <= 0 || step > (1LL << 32) + (1LL << 32) / 64) return cudaErrorInvalidValue;
+    if (step < (1LL << 32) - (1LL << 32) / 64 || step > (1LL << 32) + (1LL << 32) / 64) return cudaErrorInvalidValue;
     const long long n = r_k - r_prev;
     if (n <= 0) return cudaSuccess;
-    k_kk_resample<<<(unsigned)((n + kRsOut - 1) / kRsOut), kRsOut, 0, st>>>(E, ebase, r_prev, r_k, i0, f0, step, tab,
+    k_kk_resample<<<(unsigned)((n + kRsOut - 1) / kRsOut), kRsThreads, 0, st>>>(E, ebase, r_prev, r_k, i0, f0, step, tab,
                                                                            R, rbase, R_prev, rbase_prev);
     return cudaGetLastError();
 }
