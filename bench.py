@@ -475,7 +475,24 @@ def cnn_leg(args, ring):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    # the same network with FP16 operands
+    rb = rx.Receiver(FMT, nb, cnn_bf16=0)
+    rx.rx_set_cnn(rb.h, tr.h)
+    chk = rx.Receiver(FMT, nb, cnn_bf16=0)
+    rx.rx_set_cnn(chk.h, tr.h)
+    for p in gev["packed"]:
+        chk.process(torch.from_numpy(p).cuda())
+    rb.process_batch(ring[:3])
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    rb.process_batch(ring)
+    rb.process_batch(ring)
+    e3.record()
+    torch.cuda.synchronize()
+    fp16 = {"gsa_s": nrun * nb / (e2.elapsed_time(e3) * 1e-3) / 1e9, "ber": chk.stats()["ber"]}
     return {"gsa_s": nrun * nb / (ms * 1e-3) / 1e9, "ber_cnn": sn["ber"], "ber_lms": sl["ber"],
+            "inference_operands": "bf16", "fp16_operands": fp16,
             "bits": sn["bits"], "train_symbols": int(n_train), "train_steps": steps, "batch_symbols": 64 * 64,
             "train_s": t_train,
             "channel": "KK-16QAM, Volterra (0.05, 0.02), CSPR 6 dB, no laser phase noise; train SNR 16/18/20/22 dB "

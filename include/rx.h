@@ -110,6 +110,9 @@ typedef struct {
                             Hann-windowed sinc (taps j = -7..8 at the fraction rounded
                             down to 10 bits) before the filter.  Within 1 % of 2^32.     */
     int64_t rs_phase0;   /* accumulator value of nominal sample 0 (may be negative)        */
+    int32_t cnn_bf16;    /* receiver CNN (rx_set_cnn) operands: 1 = BF16 (default), 0 =
+                            FP16; FP32 accumulation, bias and GELU in the same packed type */
+    int32_t pad_cnn;     /* reserved, 0                                                    */
 } rx_config;
 
 /* Reduction to 2 samples/symbol of the KK chain (rx_config.mf_mode). */

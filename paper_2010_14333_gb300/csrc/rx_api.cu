@@ -263,6 +263,7 @@ rx_status rx_default_config(rx_format f, rx_config *c)
     c->mf_mode = RX_MF_TIME;
     c->fd_n = 1024;
     c->fd_taps = kk ? 203 : 503;
+    c->cnn_bf16 = 1;
     return RX_OK;
 }
 
@@ -349,6 +350,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     if (c.kk_front < 0 || c.kk_front > 1 || !(c.eq_warps == 0 || c.eq_warps == 2 || c.eq_warps == 4 || c.eq_warps == 8))
         return RX_EINVAL;
     if (c.rs_step != 0 && (!kk || c.rs_step < 4252017623LL || c.rs_step > 4337916969LL)) return RX_EINVAL;
+    if (c.cnn_bf16 < 0 || c.cnn_bf16 > 1) return RX_EINVAL;
     if (c.mf_mode < RX_MF_TIME || c.mf_mode > RX_MF_FD ||
         (c.mf_mode == RX_MF_FD && (c.fd_n < 16 || c.fd_n > kEHist || (c.fd_n & (c.fd_n - 1)) ||
                                    (!kk && c.fd_n != 1024) || c.fd_taps < 1 || !(c.fd_taps & 1) ||
@@ -774,7 +776,8 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
             long long seg_base = 2 * pay_lo - 12 - h->ybase_cur;
             e = launch_cnn_decide(rx_cnn_dev_params(h->cnn), (const float2 *)h->Y[h->yw], seg_base, s.f_k - h->ybase_cur, g.nwin, h->dec[ds],
                                   h->winb[ds], h->winrec[ds], h->prbs_bits, pay_lo, h->ep.scale, h->mq,
-                                  h->dbg_z ? h->dbg_z + (pay_lo - sym_lo) : nullptr, &h->st->err, h->nsm, sb);
+                                  h->dbg_z ? h->dbg_z + (pay_lo - sym_lo) : nullptr, &h->st->err, h->nsm, sb,
+                                  c.cnn_bf16);
         } else {
             const float2 *zin = nullptr;
             if (c.fir_prec >= RX_FIR_BF16) {

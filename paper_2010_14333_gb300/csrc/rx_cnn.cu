@@ -483,12 +483,12 @@ __global__ void k_cnn_tobf(const float *__restrict__ prm, __nv_bfloat16 *__restr
 //   MLP 32 -> 64 (M = 128, N = 64) on the symbols, bias + GELU into FP16
 //      planes, then 64 -> 2 as one more MMA (N = 16, two live columns);
 //   decisions and window records as the FIR receiver.
-// Inference precision: FP16 operands (activations and weights, converted from the
-// FP32 master weights), FP32 accumulation in tensor memory; bias and GELU in
-// packed FP16, GELU by its tanh form 0.5 u (1 + tanh(sqrt(2/pi) (u + 0.044715 u^3)))
-// with the hardware tanh (tanh.approx.f16x2): its distance to the erf form
-// (< 2.2e-4 absolute) and the FP16 arithmetic (2^-11 relative) stay at the
-// resolution the activations are stored with.
+// Inference precision: BF16 operands by default, FP16 as the alternative
+// (activations and weights, converted from the FP32 master weights), FP32
+// accumulation in tensor memory; bias and GELU in the same packed type, GELU by its
+// tanh form 0.5 u (1 + tanh(sqrt(2/pi) (u + 0.044715 u^3))) with the hardware tanh
+// (tanh.approx.bf16x2 / .f16x2): its distance to the erf form (< 2.2e-4 absolute)
+// stays below the resolution the activations are stored with (2^-8 / 2^-11).
 constexpr int kTS = 128;
 constexpr int kP0 = 2 * kTS + 24, kP1 = kP0 - 8, kP2 = kP1 - 8;   // 280 272 264 input / layer-1 / layer-2 positions
 constexpr int kMT1 = (kP1 + 127) / 128, kMT2 = (kP2 + 127) / 128;  // 3, 3 row tiles
@@ -525,6 +525,17 @@ static_assert(2 * (kRE - 4) == kP2, "even / odd h2 rows cover the layer-2 positi
 __device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
 __device__ __forceinline__ __half2 bits_h2(uint32_t u) { return *reinterpret_cast<__half2 *>(&u); }
 
+__device__ __forceinline__ uint32_t b2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t *>(&h); }
+__device__ __forceinline__ __nv_bfloat162 bits_b2(uint32_t u) { return *reinterpret_cast<__nv_bfloat162 *>(&u); }
+
+// two FP32 values as one packed 16-bit pair (round to nearest even): FP16 or BF16
+template <bool BF>
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    if constexpr (BF) return b2_bits(__floats2bfloat162_rn(a, b));
+    else return h2_bits(__floats2half2_rn(a, b));
+}
+
 // bias + GELU of two FP32 accumulators in packed FP16 (tanh form, hardware tanh):
 // u = acc + b; t = tanh(u (c0 + c1 u^2)); 0.5 u (1 + t) = h + h t with h = u / 2
 __device__ __forceinline__ uint32_t gelu_h2(uint32_t a, uint32_t b, uint32_t bias)
@@ -538,7 +549,27 @@ __device__ __forceinline__ uint32_t gelu_h2(uint32_t a, uint32_t b, uint32_t bia
     const __half2 h = __hmul2(u, hf);
     return h2_bits(__hfma2(h, bits_h2(th), h));
 }
+// the same in packed BF16
+__device__ __forceinline__ uint32_t gelu_b2(uint32_t a, uint32_t b, uint32_t bias)
+{
+    const __nv_bfloat162 c0 = __float2bfloat162_rn(0.7978845608028654f),
+                         c1 = __float2bfloat162_rn(0.7978845608028654f * 0.044715f);
+    const __nv_bfloat162 hf = __float2bfloat162_rn(0.5f);
+    const __nv_bfloat162 u = __hadd2(__floats2bfloat162_rn(__uint_as_float(a), __uint_as_float(b)), bits_b2(bias));
+    const __nv_bfloat162 arg = __hmul2(u, __hfma2(__hmul2(u, u), c1, c0));
+    uint32_t th;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(b2_bits(arg)));
+    const __nv_bfloat162 h = __hmul2(u, hf);
+    return b2_bits(__hfma2(h, bits_b2(th), h));
+}
+template <bool BF>
+__device__ __forceinline__ uint32_t gelu2(uint32_t a, uint32_t b, uint32_t bias)
+{
+    if constexpr (BF) return gelu_b2(a, b, bias);
+    else return gelu_h2(a, b, bias);
+}
 
+template <bool BF>
 __global__ void __launch_bounds__(kRxThreads, 2)
     k_cnn_rx_tc(const float *__restrict__ prm, const float2 *__restrict__ y,
                 long long seg_base, long long y_end, int nwin, uint8_t *__restrict__ dec, uint8_t *__restrict__ winb,
@@ -565,7 +596,7 @@ __global__ void __launch_bounds__(kRxThreads, 2)
     auto h8 = [&](const float *src) {   // 8 FP32 weights -> 16 bytes of FP16
         uint32_t w[4];
 #pragma unroll
-        for (int i = 0; i < 4; i++) w[i] = h2_bits(__floats2half2_rn(src[2 * i], src[2 * i + 1]));
+        for (int i = 0; i < 4; i++) w[i] = pack2<BF>(src[2 * i], src[2 * i + 1]);
         return make_uint4(w[0], w[1], w[2], w[3]);
     };
     for (int u = tid; u < 36 * 32; u += kRxThreads) {
@@ -589,15 +620,15 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         for (int i = 0; i < 4; i++) {
             int k0 = 8 * kk + 2 * i;
             float a = k0 < 18 ? prm[OW1 + n * 18 + k0] : 0.f, b = k0 + 1 < 18 ? prm[OW1 + n * 18 + k0 + 1] : 0.f;
-            w[i] = h2_bits(__floats2half2_rn(a, b));
+            w[i] = pack2<BF>(a, b);
         }
         *reinterpret_cast<uint4 *>(sB1 + kk * 512 + n * 16) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     for (int i = tid; i < 3 * 16; i += kRxThreads) {
         const int off = (i < 16 ? OB1 : i < 32 ? OB2 : OB3) + 2 * (i & 15);
-        bh[i] = h2_bits(__floats2half2_rn(prm[off], prm[off + 1]));
+        bh[i] = pack2<BF>(prm[off], prm[off + 1]);
     }
-    for (int i = tid; i < 32; i += kRxThreads) bh[48 + i] = h2_bits(__floats2half2_rn(prm[OC1 + 2 * i], prm[OC1 + 2 * i + 1]));
+    for (int i = tid; i < 32; i += kRxThreads) bh[48 + i] = pack2<BF>(prm[OC1 + 2 * i], prm[OC1 + 2 * i + 1]);
     if (tid < 2) c2[tid] = prm[OC2 + tid];
     for (int i = tid; i < kPrbsWords; i += kRxThreads) s_prbs[i] = prbs_bits[i];
     // the first tile's input, copied asynchronously (zero past the stream end)
@@ -617,7 +648,8 @@ __global__ void __launch_bounds__(kRxThreads, 2)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t id16 = umma_idesc(0, 128, 16), id32 = umma_idesc(0, 128, 32), id64 = umma_idesc(0, 128, 64);
+    constexpr uint32_t kFmt = BF ? 1u : 0u;   // kind::f16 operand format: F16 or BF16
+    const uint32_t id16 = umma_idesc(kFmt, 128, 16), id32 = umma_idesc(kFmt, 128, 32), id64 = umma_idesc(kFmt, 128, 64);
     const uint32_t aB1 = smem_u32(sB1), aH1 = smem_u32(sH1), aHX = smem_u32(sHX), aW2 = smem_u32(sW2),
                    aW3 = smem_u32(sW3), aM1 = smem_u32(sM1), aM2 = smem_u32(sM2);
     const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's lane quarter
@@ -656,8 +688,8 @@ __global__ void __launch_bounds__(kRxThreads, 2)
             const uint32_t *q = r + 8 * m;
             if (row < valid)
                 *reinterpret_cast<uint4 *>(dst_row(row)) =
-                    make_uint4(gelu_h2(q[0], q[1], b.x), gelu_h2(q[2], q[3], b.y), gelu_h2(q[4], q[5], b.z),
-                               gelu_h2(q[6], q[7], b.w));
+                    make_uint4(gelu2<BF>(q[0], q[1], b.x), gelu2<BF>(q[2], q[3], b.y), gelu2<BF>(q[4], q[5], b.z),
+                               gelu2<BF>(q[6], q[7], b.w));
         }
     };
 
@@ -670,7 +702,7 @@ __global__ void __launch_bounds__(kRxThreads, 2)
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 const float2 v = p + i < kP0 ? xs[p + i] : make_float2(0.f, 0.f);
-                w[i] = h2_bits(__floats2half2_rn(v.x, v.y));
+                w[i] = pack2<BF>(v.x, v.y);
             }
             *reinterpret_cast<uint4 *>(sHX + p * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         }
@@ -746,11 +778,11 @@ __global__ void __launch_bounds__(kRxThreads, 2)
             const uint4 b0 = *reinterpret_cast<const uint4 *>(bh + 48 + 8 * cq);
             const uint4 b1 = *reinterpret_cast<const uint4 *>(bh + 48 + 8 * cq + 4);
             *reinterpret_cast<uint4 *>(sHX + (2 * cq) * 2048 + row * 16) =
-                make_uint4(gelu_h2(r[0], r[1], b0.x), gelu_h2(r[2], r[3], b0.y), gelu_h2(r[4], r[5], b0.z),
-                           gelu_h2(r[6], r[7], b0.w));
+                make_uint4(gelu2<BF>(r[0], r[1], b0.x), gelu2<BF>(r[2], r[3], b0.y), gelu2<BF>(r[4], r[5], b0.z),
+                           gelu2<BF>(r[6], r[7], b0.w));
             *reinterpret_cast<uint4 *>(sHX + (2 * cq + 1) * 2048 + row * 16) =
-                make_uint4(gelu_h2(r[8], r[9], b1.x), gelu_h2(r[10], r[11], b1.y), gelu_h2(r[12], r[13], b1.z),
-                           gelu_h2(r[14], r[15], b1.w));
+                make_uint4(gelu2<BF>(r[8], r[9], b1.x), gelu2<BF>(r[10], r[11], b1.y), gelu2<BF>(r[12], r[13], b1.z),
+                           gelu2<BF>(r[14], r[15], b1.w));
         }
         fence_async_smem();
         tc_fence_before();
@@ -830,18 +862,26 @@ __global__ void __launch_bounds__(kRxThreads, 2)
 
 cudaError_t prepare_cnn_rx()
 {
-    return cudaFuncSetAttribute(k_cnn_rx_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, RxSmem::TOTAL);
+    cudaError_t e = cudaFuncSetAttribute(k_cnn_rx_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RxSmem::TOTAL);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cnn_rx_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RxSmem::TOTAL);
+    return e;
 }
 
 cudaError_t launch_cnn_decide(const float *prm, const float2 *y, long long seg_base, long long y_end,
                               int nwin, uint8_t *dec, uint8_t *winb, uint4 *winrec, const uint32_t *prbs_bits,
-                              long long k_first, float scale, int mq, float2 *soft, int *err, int nsm, cudaStream_t st)
+                              long long k_first, float scale, int mq, float2 *soft, int *err, int nsm, cudaStream_t st,
+                              int bf16)
 {
     if (nwin <= 0) return cudaSuccess;
     int ntiles = (nwin + kWinT - 1) / kWinT;
     unsigned grid = (unsigned)(ntiles < 2 * nsm ? ntiles : 2 * nsm);   // two persistent CTAs per SM
-    k_cnn_rx_tc<<<grid, kRxThreads, RxSmem::TOTAL, st>>>(prm, y, seg_base, y_end, nwin,
-                                                        dec, winb, winrec, prbs_bits, k_first, scale, mq, soft, err);
+    if (bf16)
+        k_cnn_rx_tc<true><<<grid, kRxThreads, RxSmem::TOTAL, st>>>(prm, y, seg_base, y_end, nwin, dec, winb, winrec,
+                                                                  prbs_bits, k_first, scale, mq, soft, err);
+    else
+        k_cnn_rx_tc<false><<<grid, kRxThreads, RxSmem::TOTAL, st>>>(prm, y, seg_base, y_end, nwin, dec, winb, winrec,
+                                                                   prbs_bits, k_first, scale, mq, soft, err);
     return cudaGetLastError();
 }
 

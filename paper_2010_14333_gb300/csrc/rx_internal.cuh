@@ -177,7 +177,8 @@ cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, in
 // windows; y[seg_base + 2 j - 12 ..] feeds symbol j, inputs at y_end and beyond read 0
 cudaError_t launch_cnn_decide(const float *prm, const float2 *y, long long seg_base, long long y_end,
                               int nwin, uint8_t *dec, uint8_t *winb, uint4 *winrec, const uint32_t *prbs_bits,
-                              long long k_first, float scale, int mq, float2 *soft, int *err, int nsm, cudaStream_t st);
+                              long long k_first, float scale, int mq, float2 *soft, int *err, int nsm, cudaStream_t st,
+                              int bf16);
 cudaError_t prepare_cnn_rx();
 
 }  // namespace rxk
