@@ -407,6 +407,11 @@ def gpu_arm(args, rank, world, local):
             "resampler": rs_line, "q_sweep": sweep_line, "stability": stab_line,
             "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
             "realtime_x": value / 4.0,
+            # the whole chain against the HBM roofline: 1.625 algorithmic bytes per sample
+            # (1.5 B of packed input, 0.125 B of bits out) at the measured copy bandwidth
+            "chain_hbm": {"gbs": value * 1.625, "peak_gbs": peaks.get("hbm_gbs", 6800.0),
+                          "frac": value * 1.625 / peaks.get("hbm_gbs", 6800.0),
+                          "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
             "ber": cpu["ber_gpu_same_buffers"] if cpu else None,
             "ber_oracle": cpu["ber_oracle"] if cpu else None,
             "ber_note": "BER of the first 2 buffers of the stream, GPU and FP64 oracle on the same input; "
