@@ -371,6 +371,13 @@ void rx_destroy(rx_handle *h);
 /* Static description of a status code. */
 const char *rx_strerror(rx_status s);
 
+/* Self-test of the bounded device waits: one CTA waits for an mbarrier phase that
+ * nothing completes, gives up after a bounded number of polls (as every wait of the
+ * receiver kernels does) and reports it.  Returns RX_ETIMEOUT when the bound worked
+ * (the expected result), RX_OK if the phase somehow completed, RX_ECUDA on a CUDA
+ * error.  Synchronises the stream; the context stays usable. */
+rx_status rx_selftest_wait_timeout(void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

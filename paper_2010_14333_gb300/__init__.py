@@ -52,7 +52,7 @@ class RxError(RuntimeError):
     pass
 
 
-EXPORTED = sorted(["rx_default_config", "rx_create", "rx_process", "rx_process_host", "rx_max_bits",
+EXPORTED = sorted(["rx_selftest_wait_timeout", "rx_default_config", "rx_create", "rx_process", "rx_process_host", "rx_max_bits",
                    "rx_stats", "rx_debug_copy", "rx_set_taps", "rx_destroy", "rx_strerror",
                    "rx_profile", "rx_profile_read", "rx_kk_field_noalloc", "rx_cnn_nparams", "rx_cnn_create",
                    "rx_cnn_set_params", "rx_cnn_get_params", "rx_cnn_forward", "rx_cnn_grad",
@@ -76,6 +76,8 @@ def load(path: str = LIB_PATH):
     L = C.CDLL(path)
     vp, i64, P = C.c_void_p, C.c_int64, C.POINTER
     L.rx_default_config.argtypes = [C.c_int, P(RxConfig)]
+    L.rx_selftest_wait_timeout.argtypes = [vp]
+    L.rx_selftest_wait_timeout.restype = C.c_int
     L.rx_create.argtypes = [C.c_int, C.c_double, C.c_double, i64, P(RxConfig), P(vp)]
     L.rx_process.argtypes = [vp, vp, vp, vp, P(i64)]
     L.rx_process_host.argtypes = [vp, vp, vp, vp, P(i64)]
@@ -121,6 +123,11 @@ def _check(status: int):
 
 
 # ------------------------------------------------------------- C ABI, 1:1
+def rx_selftest_wait_timeout(stream: int = 0) -> int:
+    """Bounded-wait self-test; returns the status code (RX_ETIMEOUT = 5 expected)."""
+    return load().rx_selftest_wait_timeout(stream)
+
+
 def rx_strerror(status: int) -> str:
     return load().rx_strerror(status).decode()
 

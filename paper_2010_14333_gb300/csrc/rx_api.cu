@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include "rx_async.cuh"
 #include "rx_internal.cuh"
 
 using namespace rxk;
@@ -220,7 +221,34 @@ static Sched schedule(const rx_handle *h, long long calls, long long q_prev)
     return s;
 }
 
+// self-test of the bounded waits: a phase that nothing completes
+__global__ void k_selftest_wait(int *status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncwarp();
+    const bool done = mbar_wait<4096>(&bar, 0);
+    if (threadIdx.x == 0) *status = done ? (int)RX_OK : (int)RX_ETIMEOUT;
+}
+
 extern "C" {
+
+rx_status rx_selftest_wait_timeout(void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int *d = nullptr, v = -1;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return RX_ECUDA;
+    cudaError_t e = cudaMemsetAsync(d, 0xFF, sizeof(int), st);
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<1, 32, 0, st>>>(d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return RX_ECUDA;
+    return v == (int)RX_ETIMEOUT ? RX_ETIMEOUT : v == (int)RX_OK ? RX_OK : RX_ECUDA;
+}
 
 const char *rx_strerror(rx_status s)
 {

@@ -45,9 +45,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // bounded wait on phase `parity`; false when the poll limit ran out
+template <int LIMIT = kWaitLimit>
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
 {
-    for (int it = 0; it < kWaitLimit; it++) {
+    for (int it = 0; it < LIMIT; it++) {
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done)

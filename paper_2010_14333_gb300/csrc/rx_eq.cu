@@ -563,6 +563,10 @@ static cudaError_t launch_eq_t(const EqParams &p, const EqGeom &g, int train, co
     if constexpr (QAM) {
         if (p.frozen) {
             if (g.nwin < p.eq_block / kWin) return cudaErrorInvalidValue;
+            // every call counts its last block's windows from zero, whatever an earlier
+            // launch that gave up on a bounded wait left in the ticket
+            cudaError_t e = cudaMemsetAsync(&dst->eq_ticket, 0, sizeof(unsigned), st);
+            if (e != cudaSuccess) return e;
             unsigned grid = (unsigned)((g.nwin + p.warps - 1) / p.warps);
             k_eq_frozen<NT, MQ><<<grid, 32 * p.warps, eq_smem_frozen_per_warp() * p.warps, st>>>(
                 p, g, (const float2 *)Y, zin, taps_in, taps_out, dec, winb, winrec, dbg_win, dbg_z, prbs_bits, dst);
