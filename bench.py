@@ -262,16 +262,24 @@ def gpu_arm(args, rank, world, local):
                 for _ in range(args.bufs_per_step)]
     hout_ptrs = [t.data_ptr() for t in out_host]
     pos = 0
-    e2e_steps = max(1, min(args.steps, 10))
+    e2e_steps = max(1, args.steps)
     h2d = d2h = 0
-    for i in range(args.warmup + e2e_steps):
-        if i == args.warmup:
-            barrier()
+    # warm-up as for the device-resident steps: at least W steps and WARMUP_MIN_S of work
+    e2e_warm, t_w = 0, time.perf_counter()
+    while e2e_warm < args.warmup or time.perf_counter() - t_w < WARMUP_MIN_S:
+        hin = [host_ring[(pos + j) % args.ring].data_ptr() for j in range(args.bufs_per_step)]
+        rx.rx_process_host_batch(h2, hin, hout_ptrs, sid)
+        pos += args.bufs_per_step
+        e2e_warm += 1
+        if e2e_warm % 8 == 0:
             torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            h2d = d2h = 0
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
         hin = [host_ring[(pos + j) % args.ring].data_ptr() for j in range(args.bufs_per_step)]
         ns = rx.rx_process_host_batch(h2, hin, hout_ptrs, sid)
         pos += args.bufs_per_step
@@ -401,7 +409,7 @@ def gpu_arm(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args),
             "e2e": {"value": e2e_value, "unit": "GSa/s", "h2d_bytes_per_step": h2d // e2e_steps,
-                    "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
+                    "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps, "warmup_run": e2e_warm},
             "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line, "precision": prec_line,
             "fd_filter": fd_line, "batched": batched_line,
             "resampler": rs_line, "q_sweep": sweep_line, "stability": stab_line,
