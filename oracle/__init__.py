@@ -17,7 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rx_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liborx.so")
 
-ORX_E, ORX_Y, ORX_Z, ORX_V, ORX_AHAT, ORX_BERR, ORX_WIN, ORX_TAPS, ORX_SCAL, ORX_NEAR, ORX_DRAW, ORX_RS = range(1, 13)
+ORX_E, ORX_Y, ORX_Z, ORX_V, ORX_AHAT, ORX_BERR, ORX_WIN, ORX_TAPS, ORX_SCAL, ORX_NEAR, ORX_DRAW, ORX_RS, ORX_CLK = \
+    range(1, 14)
 
 
 class OrxCfg(C.Structure):
@@ -73,6 +74,10 @@ def lib():
         L.orx_fd_block.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
         L.orx_rs_taps.argtypes = [C.c_double, C.c_void_p]
+        L.orx_fd_clock.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                   C.c_void_p]
+        L.orx_clock_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+        L.orx_clock_fit.restype = C.c_int
         L.orx_fd_block_full.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p]
         L.orx_prbs15.argtypes = [C.c_uint32, C.c_int64, C.c_void_p]
@@ -179,6 +184,28 @@ def rs_taps(mu: float) -> np.ndarray:
     c = np.zeros(16)
     lib().orx_rs_taps(mu, _ptr(c))
     return c
+
+
+def fd_clock(x: np.ndarray, H: np.ndarray, w: int) -> complex:
+    """Band-edge clock correlation of one KK FD block (N inputs)."""
+    xr = np.ascontiguousarray(np.real(x), dtype=np.float64)
+    xi = np.ascontiguousarray(np.imag(x), dtype=np.float64)
+    Hr = np.ascontiguousarray(np.real(H), dtype=np.float64)
+    Hi = np.ascontiguousarray(np.imag(H), dtype=np.float64)
+    cr, ci = C.c_double(), C.c_double()
+    lib().orx_fd_clock(_ptr(xr), _ptr(xi), len(xr), _ptr(Hr), _ptr(Hi), w, C.byref(cr), C.byref(ci))
+    return complex(cr.value, ci.value)
+
+
+def clock_fit(c: np.ndarray, centers: np.ndarray):
+    """(ppm, delay in ADC samples) from block correlations and block centres."""
+    cr = np.ascontiguousarray(np.real(c), dtype=np.float64)
+    ci = np.ascontiguousarray(np.imag(c), dtype=np.float64)
+    ce = np.ascontiguousarray(centers, dtype=np.int64)
+    ppm, dl = C.c_double(), C.c_double()
+    if lib().orx_clock_fit(_ptr(cr), _ptr(ci), _ptr(ce), len(cr), C.byref(ppm), C.byref(dl)) != 0:
+        raise ValueError("too few blocks")
+    return ppm.value, dl.value
 
 
 def rs_params(clock_step: int, clock_phase0: int):
@@ -288,7 +315,7 @@ class Oracle:
     def get(self, what: int):
         start = C.c_int64(0)
         n = lib().orx_get(self._h, what, None, 0, C.byref(start))
-        if what in (ORX_E, ORX_Y, ORX_Z, ORX_V, ORX_TAPS, ORX_RS):
+        if what in (ORX_E, ORX_Y, ORX_Z, ORX_V, ORX_TAPS, ORX_RS, ORX_CLK):
             buf = np.zeros(2 * n, dtype=np.float64)
             lib().orx_get(self._h, what, _ptr(buf), n, C.byref(start))
             return buf[0::2] + 1j * buf[1::2], start.value

@@ -246,6 +246,62 @@ void orx_rs_taps(double mu, double *c)
     }
 }
 
+/* ---------------------------------------------------- FD clock estimate
+ * The paper recovers the clock in the frequency domain block by block and unwraps
+ * the clock phase across blocks and buffers (Sec. 2).  Reading (Godard's band-edge
+ * estimator on the KK form's blocks at 4 samples/symbol): with Y = FFT(x_b) H / N,
+ *   C_b = sum_{|k - N/8| <= w} Y_k conj(Y_{k - N/4}),
+ * the correlation of the spectrum at +1/(2T) with its image one symbol rate lower;
+ * a symbol grid at ADC positions congruent to d (mod 4) gives arg C_b = -pi d / 2.
+ * w is the roll-off half-width ceil(beta N / 8) in bins. */
+void orx_fd_clock(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
+                  int w, double *c_re, double *c_im)
+{
+    double *re = xcalloc((size_t)n, sizeof(double)), *im = xcalloc((size_t)n, sizeof(double));
+    for (int i = 0; i < n; i++) { re[i] = x_re[i]; im[i] = x_im[i]; }
+    orx_fft(re, im, n, 0);
+    double sr = 0.0, si = 0.0;
+    for (int k = n / 8 - w; k <= n / 8 + w; k++) {
+        int kk = ((k % n) + n) % n, km = (((k - n / 4) % n) + n) % n;
+        double ar = (re[kk] * H_re[kk] - im[kk] * H_im[kk]) / n, ai = (re[kk] * H_im[kk] + im[kk] * H_re[kk]) / n;
+        double br = (re[km] * H_re[km] - im[km] * H_im[km]) / n, bi = (re[km] * H_im[km] + im[km] * H_re[km]) / n;
+        sr += ar * br + ai * bi;   /* a conj(b) */
+        si += ai * br - ar * bi;
+    }
+    *c_re = sr; *c_im = si;
+    free(re); free(im);
+}
+
+/* Clock offset and delay from the block correlations: d_b = -(2/pi) arg C_b,
+ * unwrapped across the blocks (period 4 ADC samples, one symbol), then the least-
+ * squares line d_b = -tau0 - eps c_b over the block centres c_b (ADC samples):
+ * ppm = 1e6 eps, delay = tau0 (in (-2, 2], the symbol ambiguity is not resolved). */
+int orx_clock_fit(const double *c_re, const double *c_im, const int64_t *center, int nblk, double *ppm,
+                  double *delay)
+{
+    if (nblk < 2) return -1;
+    double prev = 0.0, off = 0.0, sx = 0, sy = 0, sxx = 0, sxy = 0;
+    double x0 = (double)center[0];
+    for (int b = 0; b < nblk; b++) {
+        double d = -2.0 / PI * atan2(c_im[b], c_re[b]);   /* (-2, 2] */
+        if (b > 0) {
+            while (d + off - prev > 2.0) off -= 4.0;
+            while (d + off - prev < -2.0) off += 4.0;
+        }
+        double y = d + off, x = (double)center[b] - x0;
+        prev = y;
+        sx += x; sy += y; sxx += x * x; sxy += x * y;
+    }
+    double nb = (double)nblk, slope = (nb * sxy - sx * sy) / (nb * sxx - sx * sx);
+    double icpt = (sy - slope * sx) / nb - slope * x0;   /* at stream index 0 */
+    double tau0 = -icpt;
+    while (tau0 > 2.0) tau0 -= 4.0;
+    while (tau0 <= -2.0) tau0 += 4.0;
+    *ppm = -slope * 1e6;
+    *delay = tau0;
+    return 0;
+}
+
 /* PRBS-15, Fibonacci LFSR x^15 + x^14 + 1; register loaded with
  * (seed mod 32767) + 1; each step outputs r14 xor r15 and shifts it in. */
 void orx_prbs15(uint32_t seed, int64_t nbits, uint8_t *out)
@@ -289,6 +345,7 @@ struct orx {
     int64_t r_prev;                /* nominal field samples emitted */
     cx *rhist; int64_t rhist_start, rhist_len;
     cx *d_R; int64_t d_R_start, d_R_len;
+    cx *d_C; int64_t d_C_start, d_C_len;   /* FD clock correlation per emitted block */
     int fd;                        /* frequency-domain reduction to 2 samples/symbol */
     double *fd_Hr, *fd_Hi;         /* its filter response, fd_n bins */
     int trained;
@@ -654,6 +711,10 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
         /* static frequency-domain filter, N-point blocks with hop N/2, bin-truncation
          * downsampling; the block input is the carrier-removed, downshifted field */
         int N = c->fd_n, hop = N / 2;
+        free(h->d_C);
+        h->d_C_start = h->f_prev / (hop / 2);
+        h->d_C_len = f_k / (hop / 2) - h->d_C_start;
+        h->d_C = xcalloc((size_t)(h->d_C_len > 0 ? h->d_C_len : 1), sizeof(cx));
         double *xr = xcalloc((size_t)N, sizeof(double)), *xi = xcalloc((size_t)N, sizeof(double));
         double *yr = xcalloc((size_t)(N / 4), sizeof(double)), *yi = xcalloc((size_t)(N / 4), sizeof(double));
         for (int64_t b = h->f_prev / (hop / 2); b < f_k / (hop / 2); b++) {
@@ -667,6 +728,12 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
                 xr[t] = xn.re; xi[t] = xn.im;
             }
             orx_fd_block(xr, xi, N, h->fd_Hr, h->fd_Hi, yr, yi);
+            {
+                int w = (int)ceil(c->rrc_beta * N / 8.0);
+                double cr, ci;
+                orx_fd_clock(xr, xi, N, h->fd_Hr, h->fd_Hi, w, &cr, &ci);
+                h->d_C[b - h->d_C_start] = cx_mk(cr, ci);
+            }
             for (int m = 0; m < N / 4; m++)
                 X.y[(int64_t)(hop / 2) * b + m - X.y_start] = cx_scale(cx_mk(yr[m], yi[m]), h->gain);
         }
@@ -920,6 +987,7 @@ int64_t orx_get(orx *h, int what, void *dst, int64_t cap, int64_t *start)
     switch (what) {
     case ORX_E: n = h->d_E_len; s = h->d_E_start; src = h->d_E; width = sizeof(cx); break;
     case ORX_RS: n = h->d_R_len; s = h->d_R_start; src = h->d_R; width = sizeof(cx); break;
+    case ORX_CLK: n = h->d_C_len; s = h->d_C_start; src = h->d_C; width = sizeof(cx); break;
     case ORX_Y: n = h->d_y_len; s = h->d_y_start; src = h->d_y; width = sizeof(cx); break;
     case ORX_Z: n = h->d_s_len; s = h->d_s_start; src = h->d_z; width = sizeof(cx); break;
     case ORX_V: n = h->d_s_len; s = h->d_s_start; src = h->d_v; width = sizeof(cx); break;
@@ -953,7 +1021,7 @@ void orx_destroy(orx *h)
 {
     if (!h) return;
     free(h->rrc); free(h->prbs); free(h->chist); free(h->ehist); free(h->yhist); free(h->w);
-    free(h->fd_Hr); free(h->fd_Hi); free(h->rhist); free(h->d_R);
+    free(h->fd_Hr); free(h->fd_Hi); free(h->rhist); free(h->d_R); free(h->d_C);
     free(h->d_E); free(h->d_y); free(h->d_z); free(h->d_v); free(h->d_ahat);
     free(h->d_draw); free(h->d_berr); free(h->d_near); free(h->d_win);
     free(h);

@@ -1,0 +1,65 @@
+"""Pins of the oracle's frequency-domain clock estimate (the paper recovers the
+clock phase in the frequency domain block by block and unwraps it across blocks
+and buffers, Sec. 2): the line fit over exact band-edge phases, whole-sample delays
+on the nominal clock, off-clock streams, and the estimate driving the resampler."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+SMALL = dict(ols_n=8192, ols_v=1024)
+
+
+def test_fit_recovers_exact_phases_across_wraps():
+    """C_b = exp(-i pi d_b / 2) with d_b = -tau0 - eps c_b, through many wraps of the
+    4-sample period: the unwrap and the line give eps and tau0 back."""
+    for ppm, tau0 in ((-35.0, 0.4), (120.0, -1.3), (0.5, 1.9)):
+        centers = 512 * np.arange(3000, 9000) + 256
+        d = -tau0 - ppm * 1e-6 * centers
+        c = 7.0 * np.exp(-0.5j * np.pi * d)
+        p, t = oracle.clock_fit(c, centers)
+        assert abs(p - ppm) < 1e-9 and abs(t - tau0) < 1e-9, (p, t)
+
+
+def _estimate(g, nb, nbufs):
+    o = oracle.Oracle(**oracle.default_cfg(4, nb, mf_mode=1, **SMALL))
+    for b in range(nbufs):
+        o.process(g["packed"][b])
+    c, c0 = o.get(oracle.ORX_CLK)
+    return oracle.clock_fit(c, 512 * (c0 + np.arange(len(c))) + 256)
+
+
+@pytest.mark.parametrize("d", [0, 1, -1, 2])
+def test_whole_sample_delays_on_the_nominal_clock(d):
+    nb = 1 << 18
+    g = synth.gen_kk_stream(4, nb, 2, seed=4, noise=False, phase_noise=False, clock_phase0=d << 32)
+    ppm, delay = _estimate(g, nb, 2)
+    err = (delay - d + 2.0) % 4.0 - 2.0    # the delay is known modulo one symbol (4 samples)
+    assert abs(ppm) < 0.2 and abs(err) < 0.02, (ppm, delay)
+
+
+@pytest.mark.parametrize("ppm,delay", [(-35.0, 0.4), (20.0, -0.7), (80.0, 1.1)])
+def test_off_clock_streams(ppm, delay):
+    nb = 1 << 19
+    g = synth.gen_kk_stream(4, nb, 2, seed=2, clock_step=synth.clock_step(ppm),
+                            clock_phase0=int(round(delay * (1 << 32))))
+    p, t = _estimate(g, nb, 2)
+    assert abs(p - ppm) < 0.5 and abs(t - delay) < 0.05, (p, t)
+
+
+def test_estimate_drives_the_resampler():
+    """Estimate the clock on the first two buffers without the resampler, configure
+    the resampler with the estimate, and decode the noiseless stream error-free."""
+    nb = 1 << 18
+    st, ph = synth.clock_step(-35.0), int(round(0.4 * (1 << 32)))
+    g = synth.gen_kk_stream(4, nb, 4, seed=6, noise=False, phase_noise=False, clock_step=st, clock_phase0=ph)
+    p, t = _estimate(g, nb, 2)
+    rs_step, rs_phase0 = oracle.rs_params(synth.clock_step(p), int(round(t * (1 << 32))))
+    o = oracle.Oracle(**oracle.default_cfg(4, nb, rs_step=rs_step, rs_phase0=rs_phase0, ntrain=4096, ncma=2048,
+                                           **SMALL))
+    for b in range(4):
+        o.process(g["packed"][b])
+    s = o.stats()
+    assert s["bits"] > 200000 and s["bit_errors"] == 0
