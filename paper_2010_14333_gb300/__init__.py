@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(_PKG, "librx.so")
 
 RX_PAM2, RX_PAM4, RX_PAM8, RX_KK_QPSK, RX_KK_16QAM = range(5)
 RX_FIR_ADAPTIVE, RX_FIR_FROZEN_F32, RX_FIR_BF16, RX_FIR_FP16, RX_FIR_FP8 = range(5)
-RX_DBG_FIELD, RX_DBG_MF, RX_DBG_SOFT, RX_DBG_DEC, RX_DBG_WIN, RX_DBG_TAPS, RX_DBG_SCAL, RX_DBG_CODES, RX_DBG_RS = \
-    range(1, 10)
+RX_DBG_FIELD, RX_DBG_MF, RX_DBG_SOFT, RX_DBG_DEC, RX_DBG_WIN, RX_DBG_TAPS, RX_DBG_SCAL, RX_DBG_CODES, RX_DBG_RS, \
+    RX_DBG_CLK = range(1, 11)
 BITS_PER_SYMBOL = {0: 1, 1: 2, 2: 3, 3: 2, 4: 4}
 
 
@@ -52,7 +52,7 @@ class RxError(RuntimeError):
     pass
 
 
-EXPORTED = sorted(["rx_selftest_wait_timeout", "rx_default_config", "rx_create", "rx_process", "rx_process_host", "rx_max_bits",
+EXPORTED = sorted(["rx_selftest_wait_timeout", "rx_clock_estimate", "rx_default_config", "rx_create", "rx_process", "rx_process_host", "rx_max_bits",
                    "rx_stats", "rx_debug_copy", "rx_set_taps", "rx_destroy", "rx_strerror",
                    "rx_profile", "rx_profile_read", "rx_kk_field_noalloc", "rx_cnn_nparams", "rx_cnn_create",
                    "rx_cnn_set_params", "rx_cnn_get_params", "rx_cnn_forward", "rx_cnn_grad",
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.rx_default_config.argtypes = [C.c_int, P(RxConfig)]
     L.rx_selftest_wait_timeout.argtypes = [vp]
     L.rx_selftest_wait_timeout.restype = C.c_int
+    L.rx_clock_estimate.argtypes = [vp, P(C.c_double), P(C.c_double), vp]
     L.rx_create.argtypes = [C.c_int, C.c_double, C.c_double, i64, P(RxConfig), P(vp)]
     L.rx_process.argtypes = [vp, vp, vp, vp, P(i64)]
     L.rx_process_host.argtypes = [vp, vp, vp, vp, P(i64)]
@@ -123,6 +124,13 @@ def _check(status: int):
 
 
 # ------------------------------------------------------------- C ABI, 1:1
+def rx_clock_estimate(h: int, stream: int = 0):
+    """(ppm, delay in ADC samples) of the ADC clock from the last call (KK FD form)."""
+    ppm, dl = C.c_double(), C.c_double()
+    _check(load().rx_clock_estimate(h, C.byref(ppm), C.byref(dl), stream))
+    return ppm.value, dl.value
+
+
 def rx_selftest_wait_timeout(stream: int = 0) -> int:
     """Bounded-wait self-test; returns the status code (RX_ETIMEOUT = 5 expected)."""
     return load().rx_selftest_wait_timeout(stream)
@@ -360,7 +368,7 @@ class Receiver:
 
     _DT = {RX_DBG_FIELD: (np.complex64, 1), RX_DBG_SOFT: (np.complex64, 1), RX_DBG_DEC: (np.uint8, 1),
            RX_DBG_WIN: (np.float32, 4), RX_DBG_TAPS: (np.complex64, 1), RX_DBG_SCAL: (np.float64, 1),
-           RX_DBG_CODES: (np.uint16, 1), RX_DBG_RS: (np.complex64, 1)}
+           RX_DBG_CODES: (np.uint16, 1), RX_DBG_RS: (np.complex64, 1), RX_DBG_CLK: (np.complex64, 1)}
 
     def debug(self, what: int):
         n, s = rx_debug_copy(self.h, what, None, 0, self.stream())

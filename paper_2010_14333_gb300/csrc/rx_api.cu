@@ -82,6 +82,8 @@ struct rx_handle {
     float *rs_tab;                  // 1024 x 16 interpolator taps
     int fd;                         // frequency-domain reduction to 2 samples/symbol
     float2 *fd_H, *fd_tw;           // its kept-bin response (times 1/N) and N-point twiddles
+    float2 *clk;                    // KK FD: band-edge clock correlation of each block of the last call
+    int clk_w;                      // its half-width in bins
     long long dec_cap, win_cap, y_cap;
     int nsm;                        // SMs of the handle's device
     // stage timing: a ring of event sets, one per profiled call
@@ -313,7 +315,7 @@ void rx_destroy(rx_handle *h)
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->partials, h->prbs, h->taps[0], h->taps[1], h->twN,
                     h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
                     h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->zbuf, h->gpart, h->fd_H, h->fd_tw, h->R[0], h->R[1],
-                    h->rs_tab};
+                    h->rs_tab, h->clk};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kSlots; i++) {
@@ -557,6 +559,12 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
             Hk[kp] = make_float2((float)(re / N), (float)(im / N));
         }
         twiddles(N, tw);
+        if (kk) {   // blocks per call: nominal samples (nb / 0.99 + 8 with the resampler) / (N/2) + 2
+            h->clk_w = (int)ceil(c.rrc_beta * N / 8.0);
+            if (h->clk_w >= N / 8) h->clk_w = N / 8 - 1;
+            if (N == 1024 && h->clk_w > 31) h->clk_w = 31;
+            if (e == cudaSuccess) e = cudaMalloc(&h->clk, sizeof(float2) * ((nb + nb / 64 + 64) / (N / 2) + 4));
+        }
         if (e == cudaSuccess) e = cudaMalloc(&h->fd_H, sizeof(float2) * nbins);
         if (e == cudaSuccess) e = cudaMalloc(&h->fd_tw, sizeof(float2) * N);
         if (e == cudaSuccess) e = cudaMemcpy(h->fd_H, Hk, sizeof(float2) * nbins, cudaMemcpyHostToDevice);
@@ -755,7 +763,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         if (h->kk && h->fd)
             e = launch_kk_fdmf(Ef, efbase, h->f_prev, s.f_k, c.fd_n, h->fd_H, h->fd_tw, h->ds_tab,
                                c.ds_num, c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb,
-                               (const float2 *)h->Y[h->yw], h->ybase_cur, sm);
+                               (const float2 *)h->Y[h->yw], h->ybase_cur, sm, h->clk, h->clk_w);
         else if (h->kk)
             e = launch_kk_mf(Ef, efbase, s.r_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
                              c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw],
@@ -974,6 +982,47 @@ rx_status rx_stats(rx_handle *h, rx_stats_t *o, void *stream)
     return RX_OK;
 }
 
+rx_status rx_clock_estimate(rx_handle *h, double *ppm, double *delay, void *stream)
+{
+    if (!h || !ppm || !delay) return RX_EINVAL;
+    if (!h->clk) return RX_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return RX_ECUDA;
+    const long long per = h->cfg.fd_n / 4, b0 = h->l_f_prev / per, n = (h->l_f_k - h->l_f_prev) / per;
+    if (n < 2) return RX_ESTATE;
+    float2 *c = (float2 *)malloc(sizeof(float2) * n);
+    if (!c) return RX_ENOMEM;
+    if (cudaMemcpy(c, h->clk, sizeof(float2) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        free(c);
+        return RX_ECUDA;
+    }
+    // d_b = -(2/pi) arg C_b unwrapped (period 4 samples), least-squares d_b = -tau0 - eps centre_b,
+    // centre_b = (N/2) b + N/4 (the middle of block b's inputs)
+    const double pi = 3.14159265358979323846;
+    const double x0 = (double)((2 * per) * b0 + per);
+    double prev = 0, off = 0, sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (long long i = 0; i < n; i++) {
+        double d = -2.0 / pi * atan2((double)c[i].y, (double)c[i].x);
+        if (i > 0) {
+            while (d + off - prev > 2.0) off -= 4.0;
+            while (d + off - prev < -2.0) off += 4.0;
+        }
+        const double y = d + off, x = (double)(2 * per) * (double)i;
+        prev = y;
+        sx += x;
+        sy += y;
+        sxx += x * x;
+        sxy += x * y;
+    }
+    free(c);
+    const double nb = (double)n, slope = (nb * sxy - sx * sy) / (nb * sxx - sx * sx);
+    double tau0 = -((sy - slope * sx) / nb - slope * x0);
+    while (tau0 > 2.0) tau0 -= 4.0;
+    while (tau0 <= -2.0) tau0 += 4.0;
+    *ppm = -slope * 1e6;
+    *delay = tau0;
+    return RX_OK;
+}
+
 rx_status rx_debug_copy(rx_handle *h, int what, void *dst, int64_t cap, int64_t *count, int64_t *start, void *stream)
 {
     if (!h || !count || !start) return RX_EINVAL;
@@ -994,6 +1043,13 @@ rx_status rx_debug_copy(rx_handle *h, int what, void *dst, int64_t cap, int64_t 
         n = h->l_r_k - h->l_r_prev;
         s0 = h->l_r_prev;
         src = h->R[h->rw] + (h->l_r_prev - h->rbase_cur);
+        el = sizeof(float2);
+        break;
+    case RX_DBG_CLK:
+        if (!h->clk) return RX_EINVAL;
+        n = (h->l_f_k - h->l_f_prev) / (h->cfg.fd_n / 4);
+        s0 = h->l_f_prev / (h->cfg.fd_n / 4);
+        src = h->clk;
         el = sizeof(float2);
         break;
     case RX_DBG_MF:

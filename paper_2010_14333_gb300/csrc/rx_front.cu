@@ -1171,7 +1171,8 @@ __global__ void __launch_bounds__(kFdThreads) k_kk_fdmf(const float2 *__restrict
                                                        const float2 *__restrict__ ds_tab, int ds_num, int ds_den,
                                                        const double *__restrict__ cg, float2 *__restrict__ Y,
                                                        long long ybase, long long f_prev,
-                                                       const float2 *__restrict__ Y_prev, long long ybase_prev)
+                                                       const float2 *__restrict__ Y_prev, long long ybase_prev,
+                                                       float2 *__restrict__ clk, int wbin)
 {
     extern __shared__ float2 fbuf[];   // [2][N]
     float2 *a = fbuf, *b = fbuf + N;
@@ -1199,6 +1200,17 @@ __global__ void __launch_bounds__(kFdThreads) k_kk_fdmf(const float2 *__restrict
     const int half = N >> 1, q = N >> 2;
     for (int kp = threadIdx.x; kp < half; kp += kFdThreads) Z[kp] = cmul(X[kp < q ? kp : kp + half], __ldg(H + kp));
     __syncthreads();
+    if (clk && threadIdx.x < 32) {   // band-edge clock correlation: Y_k conj(Y_{k - N/4}), |k - N/8| <= w
+        float2 acc = make_float2(0.f, 0.f);
+        for (int k = N / 8 - wbin + (int)threadIdx.x; k <= N / 8 + wbin; k += 32) {
+            const float2 a = Z[k], b = Z[k + q];   // kept positions k and (k - N/4) mod N - N/2
+            acc = cadd(acc, cmulc(a, b));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+            acc = make_float2(acc.x + __shfl_xor_sync(0xffffffffu, acc.x, o), acc.y + __shfl_xor_sync(0xffffffffu, acc.y, o));
+        if (threadIdx.x == 0) clk[blockIdx.x] = acc;
+    }
     float2 *z = stockham<true>(Z, X, half, N, tw);
     const long long s0 = (long long)(N / 4) * blk - ybase;   // 2-sps index of the block's first output
     for (int m = threadIdx.x; m < q; m += kFdThreads) Y[s0 + m] = cscale(z[m + N / 8], gn);
@@ -1268,7 +1280,8 @@ __global__ void __launch_bounds__(32 * kFdWarps, 4)
     k_kk_fd1024(const float2 *__restrict__ E, long long ebase, long long b_first, long long nblk,
                 const float2 *__restrict__ H, const float2 *__restrict__ tw, const float2 *__restrict__ ds_tab,
                 int ds_num, int ds_den, const double *__restrict__ cg, float2 *__restrict__ Y, long long ybase,
-                long long f_prev, const float2 *__restrict__ Y_prev, long long ybase_prev)
+                long long f_prev, const float2 *__restrict__ Y_prev, long long ybase_prev,
+                float2 *__restrict__ clk, int wbin)
 {
     __shared__ float2 s_tw[1024];
     __shared__ float2 s_t[kFdWarps][32 * kFdPitch];
@@ -1309,6 +1322,18 @@ __global__ void __launch_bounds__(32 * kFdWarps, 4)
     float2 z[16];
 #pragma unroll
     for (int j = 0; j < 16; j++) z[j] = cmul(x[j < 8 ? j : j + 16], __ldg(H + lane + 32 * j));
+    if (clk) {   // band-edge clock correlation: bins k = lane + 32 k1 (k1 = 3, 4) with k - 256 (k1 + 24 -> j + 8)
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k1 = 3; k1 <= 4; k1++) {
+            const int k = lane + 32 * k1;
+            if (k >= 128 - wbin && k <= 128 + wbin) acc = cadd(acc, cmulc(z[k1], z[k1 + 8]));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+            acc = make_float2(acc.x + __shfl_xor_sync(0xffffffffu, acc.x, o), acc.y + __shfl_xor_sync(0xffffffffu, acc.y, o));
+        if (lane == 0) clk[bi] = acc;
+    }
     dft16<true>(z);
 #pragma unroll
     for (int ma = 1; ma < 16; ma++) z[ma] = cmulc(z[ma], s_tw[2 * lane * ma]);
@@ -1337,19 +1362,21 @@ __global__ void __launch_bounds__(32 * kFdWarps, 4)
 cudaError_t launch_kk_fdmf(const float2 *E, long long ebase, long long f_prev, long long f_k, int N,
                            const float2 *H, const float2 *tw, const float2 *ds_tab, int ds_num, int ds_den,
                            const double *cg, float2 *Y, long long ybase, const float2 *Y_prev,
-                           long long ybase_prev, cudaStream_t st)
+                           long long ybase_prev, cudaStream_t st, float2 *clk, int wbin)
 {
     const int per = N / 4;   // outputs per block
-    if (N < 16 || (N & (N - 1)) || f_prev % per || f_k % per) return cudaErrorInvalidValue;
+    if (N < 16 || (N & (N - 1)) || f_prev % per || f_k % per || wbin < 0 || wbin >= N / 8 || (N == 1024 && wbin > 31))
+        return cudaErrorInvalidValue;
     const long long nblk = (f_k - f_prev) / per;
     if (nblk <= 0) return cudaSuccess;
     if (N == 1024) {
         k_kk_fd1024<<<(unsigned)((nblk + kFdWarps - 1) / kFdWarps), 32 * kFdWarps, 0, st>>>(
-            E, ebase, f_prev / per, nblk, H, tw, ds_tab, ds_num, ds_den, cg, Y, ybase, f_prev, Y_prev, ybase_prev);
+            E, ebase, f_prev / per, nblk, H, tw, ds_tab, ds_num, ds_den, cg, Y, ybase, f_prev, Y_prev, ybase_prev,
+            clk, wbin);
         return cudaGetLastError();
     }
     k_kk_fdmf<<<(unsigned)nblk, kFdThreads, 2 * N * sizeof(float2), st>>>(
-        E, ebase, f_prev / per, N, H, tw, ds_tab, ds_num, ds_den, cg, Y, ybase, f_prev, Y_prev, ybase_prev);
+        E, ebase, f_prev / per, N, H, tw, ds_tab, ds_num, ds_den, cg, Y, ybase, f_prev, Y_prev, ybase_prev, clk, wbin);
     return cudaGetLastError();
 }
 

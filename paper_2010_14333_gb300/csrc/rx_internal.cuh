@@ -129,11 +129,12 @@ cudaError_t launch_kk_resample(const float2 *E, long long ebase, long long r_pre
                                const float2 *R_prev, long long rbase_prev, cudaStream_t st);
 
 // frequency-domain form (static filter on N-point overlap-save blocks, hop N/2,
-// N/2-point bin-truncation inverse); f_prev and f_k are multiples of N/4
+// N/2-point bin-truncation inverse); f_prev and f_k are multiples of N/4; clk (or
+// null) receives each block's band-edge clock correlation over |k - N/8| <= w
 cudaError_t launch_kk_fdmf(const float2 *E, long long ebase, long long f_prev, long long f_k, int N,
                            const float2 *H, const float2 *tw, const float2 *ds_tab, int ds_num, int ds_den,
                            const double *cg, float2 *Y, long long ybase, const float2 *Y_prev,
-                           long long ybase_prev, cudaStream_t st);
+                           long long ybase_prev, cudaStream_t st, float2 *clk, int w);
 
 // PAM frequency-domain form, 1024-point blocks (hop 512) at the input rate;
 // f_prev and f_k are multiples of 512

@@ -1,0 +1,70 @@
+"""Parity of the frequency-domain clock estimate (Sec. 2: the clock recovered in the
+frequency domain block by block) with the FP64 oracle: the band-edge correlation of
+every block within 1e-4 relative, the fitted clock offset and delay equal to the
+oracle's and to the generator's clock, and the estimate driving the GPU resampler."""
+
+import numpy as np
+import pytest
+import torch
+
+from parity_util import Pair, make_stream
+import oracle
+import paper_2010_14333_gb300 as rx
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SMALL_KK = dict(ols_n=4096, ols_v=512, ntrain=4096, ncma=2048, amb_syms=1024)
+
+
+def gen(ppm, delay, nb, nbufs, **kw):
+    return make_stream(4, nb, nbufs, clock_step=synth.clock_step(ppm), clock_phase0=int(round(delay * (1 << 32))),
+                       **kw)
+
+
+@pytest.mark.parametrize("fd_n", [1024, 256])
+def test_block_correlations_match_oracle(fd_n):
+    nb = 1 << 17
+    g = gen(2.0, 0.3, nb, 3)
+    p = Pair(4, nb, mf_mode=1, fd_n=fd_n, fd_taps=fd_n // 4 + 1, **SMALL_KK)
+    for b in range(3):
+        p.feed(g["packed"][b])
+        c, c0 = p.g.debug(rx.RX_DBG_CLK)
+        co, co0 = p.o.get(oracle.ORX_CLK)
+        assert (c0, len(c)) == (co0, len(co)) and len(c) > 0
+        assert np.linalg.norm(c - co) / np.linalg.norm(co) < 1e-4
+    p.compare_stats()
+
+
+@pytest.mark.parametrize("ppm,delay", [(-35.0, 0.4), (20.0, -0.7)])
+def test_estimate_matches_oracle_and_clock(ppm, delay):
+    nb = 1 << 19
+    g = gen(ppm, delay, nb, 2)
+    r = rx.Receiver(4, nb, mf_mode=1, **SMALL_KK)
+    o = oracle.Oracle(**oracle.default_cfg(4, nb, mf_mode=1, **SMALL_KK))
+    for b in range(2):
+        r.process(torch.from_numpy(g["packed"][b]).cuda())
+        o.process(g["packed"][b])
+    gp, gd = rx.rx_clock_estimate(r.h, torch.cuda.current_stream().cuda_stream)
+    c, c0 = o.get(oracle.ORX_CLK)
+    op, od = oracle.clock_fit(c, 512 * (c0 + np.arange(len(c))) + 256)
+    assert abs(gp - op) < 0.01 and abs(gd - od) < 1e-3, (gp, op, gd, od)
+    assert abs(gp - ppm) < 0.5 and abs(gd - delay) < 0.05, (gp, gd)
+
+
+def test_estimate_drives_the_gpu_resampler():
+    nb = 1 << 18
+    g = gen(-35.0, 0.4, nb, 5, seed=6)
+    est = rx.Receiver(4, nb, mf_mode=1, **SMALL_KK)
+    for b in range(2):
+        est.process(torch.from_numpy(g["packed"][b]).cuda())
+    ppm, delay = rx.rx_clock_estimate(est.h, torch.cuda.current_stream().cuda_stream)
+    rs_step, rs_phase0 = oracle.rs_params(synth.clock_step(ppm), int(round(delay * (1 << 32))))
+    r = rx.Receiver(4, nb, rs_step=rs_step, rs_phase0=rs_phase0, **SMALL_KK)
+    plain = rx.Receiver(4, nb, **SMALL_KK)
+    for p in g["packed"]:
+        d = torch.from_numpy(p).cuda()
+        r.process(d)
+        plain.process(d)
+    s, sp = r.stats(), plain.stats()
+    assert s["bits"] > 0 and s["ber"] < 0.02 and sp["ber"] > 0.1, (s["ber"], sp["ber"])
