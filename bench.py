@@ -645,10 +645,11 @@ def fd_leg(args, g, ring):
 
 def resampler_leg(args, ring):
     """The receiver with the resampler to the transmitter's grid (ADC clock off the
-    transmitter's): throughput over the benchmark ring with a -35 ppm accumulator
-    (the resampler's work does not depend on the data), and BER against the FP64
-    oracle on two buffers of a stream generated through a -35 ppm ADC clock with a
-    0.4-sample delay."""
+    transmitter's): on two buffers of a stream generated through a -35 ppm ADC clock
+    with a 0.4-sample delay, the clock estimated from the first buffer in the
+    frequency-domain form, then the BER with the resampler set from the estimate
+    against the FP64 oracle set the same way; throughput over the benchmark ring
+    (the resampler's work does not depend on the data)."""
     import torch
     import oracle
     import synth
@@ -658,6 +659,13 @@ def resampler_leg(args, ring):
     t0 = time.perf_counter()
     g = synth.gen_kk_stream(FMT, NB, 2, seed=11, truth=False, clock_step=st, clock_phase0=ph, workers=2, **GEN)
     t_gen = time.perf_counter() - t0
+    # the clock estimated from the first buffer in the frequency-domain form, then the
+    # resampler configured with the estimate
+    est = rx.Receiver(FMT, NB, mf_mode=1)
+    est.process(torch.from_numpy(g["packed"][0]).cuda())
+    e_ppm, e_delay = rx.rx_clock_estimate(est.h, torch.cuda.current_stream().cuda_stream)
+    del est
+    rs_step, rs_phase0 = oracle.rs_params(synth.clock_step(e_ppm), int(round(e_delay * (1 << 32))))
     o = oracle.Oracle(**oracle.default_cfg(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0))
     d = rx.Receiver(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0)
     plain = rx.Receiver(FMT, NB)
@@ -666,7 +674,8 @@ def resampler_leg(args, ring):
         dv = torch.from_numpy(p).cuda()
         d.process(dv)
         plain.process(dv)
-    out = {"ppm": -35.0, "delay_samples": 0.4, "ber": d.stats()["ber"], "ber_oracle": o.stats()["ber"],
+    out = {"ppm": -35.0, "delay_samples": 0.4, "estimated_ppm": e_ppm, "estimated_delay_samples": e_delay,
+           "ber": d.stats()["ber"], "ber_oracle": o.stats()["ber"],
            "ber_without_resampler": plain.stats()["ber"], "gen_s": t_gen}
     del d, plain
     r = rx.Receiver(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0)
