@@ -638,7 +638,7 @@ cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void 
 }
 
 // ------------------------------------------------------------------ demap / BER
-// kDemapWin windows per CTA, one warp per window at a time.  The pi/2 unwrap
+// kDemapWin windows per CTA, kDemapWin / 8 per warp.  The pi/2 unwrap
 // counter of window w is the carried value plus a prefix sum of integer
 // increments; each CTA sums the increments of all earlier windows itself
 // (16-byte loads of the window phase indices), then scans its own.  The
@@ -668,32 +668,74 @@ __global__ void __launch_bounds__(kDemapThreads)
             uint8_t *__restrict__ bits_out, DevState *dst)
 {
     constexpr int NW = kDemapThreads / 32;
+    constexpr int WPW = kDemapWin / NW;                            // windows per warp
     constexpr int NB = QAM ? BPS / 2 : BPS;
+    constexpr int NBYTES = 8 * BPS;                                // 64 symbols * BPS bits / 8
+    constexpr int NS = (8 % BPS == 0) ? 8 / BPS : 8 / BPS + 2;     // symbols one output byte touches
+    static_assert(kDemapWin == 32 && WPW <= 32, "one scan lane per window of the CTA");
     __shared__ long long s_m[kDemapWin];
     __shared__ int s_red[NW];
     __shared__ int s_r;
-    __shared__ uint8_t s_grp[NW][kWin];
-    __shared__ unsigned long long s_cnt[C_NCNT];
+    __shared__ unsigned s_cnt[C_NCNT];
     int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int w0 = blockIdx.x * kDemapWin;
     int wend = min(w0 + kDemapWin, g.nwin);
     if (tid < C_NCNT) s_cnt[tid] = 0;
+    // Every load that does not depend on the unwrap counter is issued first: the
+    // decisions of this warp's windows (symbols lane and lane + 32 of each), the
+    // record of the warp's window `lane` (lanes < WPW) and the scan lane's phase
+    // indices, so that their latencies overlap with each other and with the prefix.
+    uint32_t dv[WPW];
+#pragma unroll
+    for (int i = 0; i < WPW; i++) {
+        int wi = w0 + wid + NW * i;
+        dv[i] = 0;
+        if (wi < wend) {
+            const uint8_t *d = dec + (long long)wi * kWin;
+            dv[i] = (uint32_t)d[lane] | ((uint32_t)d[lane + 32] << 8);
+        }
+    }
+    const int wr = w0 + wid + NW * lane;
+    uint4 rc = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < WPW && wr < wend) rc = winrec[wr];
     if (QAM) {
         int have = dst->unwrap_have[uw_in];
         int blast = dst->unwrap_b[uw_in];
         long long mstart = have ? dst->unwrap_m[uw_in] : 0;
-        // prefix of increments over windows [0, w0), 16 windows per load
+        const int ws = w0 + tid;   // the window scanned by thread tid < kDemapWin
+        int sb = 0, sbp = 0;
+        if (tid < kDemapWin && ws < wend) {
+            sb = winb[ws];
+            sbp = ws > 0 ? winb[ws - 1] : 0;
+        }
+        // prefix of increments over windows [0, w0): 16 windows per 16-byte load,
+        // four loads in flight per thread
+        const int nch = w0 / 16;
         int part = 0;
-        for (int c = tid; c < w0 / 16; c += kDemapThreads) {
-            uint4 v = *reinterpret_cast<const uint4 *>(winb + 16 * c);
-            uint32_t wd[4] = {v.x, v.y, v.z, v.w};
-            int prev = (c == 0) ? blast : winb[16 * c - 1];
-            bool use_first = (c > 0) || have;
+        for (int cb = tid; cb < nch; cb += 4 * kDemapThreads) {
+            uint4 v[4];
+            int pv[4];
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
-                int b = (wd[i >> 2] >> (8 * (i & 3))) & 0xFF;
-                if (i > 0 || use_first) part += unwrap_inc(prev, b, p.bps_b);
-                prev = b;
+            for (int k = 0; k < 4; k++) {
+                int c = cb + k * kDemapThreads;
+                if (c < nch) {
+                    v[k] = *reinterpret_cast<const uint4 *>(winb + 16 * c);
+                    pv[k] = c ? winb[16 * c - 1] : 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                int c = cb + k * kDemapThreads;
+                if (c >= nch) break;
+                uint32_t wd[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+                int prev = c ? pv[k] : blast;
+                bool use_first = (c > 0) || have;
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    int b = (wd[i >> 2] >> (8 * (i & 3))) & 0xFF;
+                    if (i > 0 || use_first) part += unwrap_inc(prev, b, p.bps_b);
+                    prev = b;
+                }
             }
         }
         part = warp_sum_i(part);
@@ -704,11 +746,7 @@ __global__ void __launch_bounds__(kDemapThreads)
         for (int i = 0; i < NW; i++) pre += s_red[i];
         if (tid < 32) {   // inclusive scan of this CTA's increments
             int inc = 0;
-            if (tid < kDemapWin && w0 + tid < wend) {
-                int w = w0 + tid;
-                int bp = (w == 0) ? blast : winb[w - 1];
-                if (w > 0 || have) inc = unwrap_inc(bp, winb[w], p.bps_b);
-            }
+            if (tid < kDemapWin && ws < wend && (ws > 0 || have)) inc = unwrap_inc(ws ? sbp : blast, sb, p.bps_b);
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 int v = __shfl_up_sync(0xffffffffu, inc, o);
@@ -735,9 +773,9 @@ __global__ void __launch_bounds__(kDemapThreads)
                     int m = acc + v;
                     acc += __shfl_sync(0xffffffffu, v, 31);
                     if (w < nw) {
-                        uint4 rc = winrec[w];
+                        uint4 rw = winrec[w];
 #pragma unroll
-                        for (int r = 0; r < 4; r++) cnt[r] += rec_serr(rc, (m + r) & 3);
+                        for (int r = 0; r < 4; r++) cnt[r] += rec_serr(rw, (m + r) & 3);
                     }
                 }
                 int best = 0;
@@ -759,56 +797,62 @@ __global__ void __launch_bounds__(kDemapThreads)
     __syncthreads();
     const int r = QAM ? s_r : 0;
     const long long amb_end = QAM ? (long long)p.ntrain + p.amb_syms : 0;
-    constexpr int NBYTES = 8 * BPS;   // 64 symbols * BPS bits / 8
-    for (int wi = w0 + wid; wi < wend; wi += NW) {
-        long long k0 = g.pay_lo + (long long)wi * kWin;
-        long long mw = QAM ? s_m[wi - w0] : 0;
-        int qd = (int)((mw + r) & 3);
-        if (dbg_win && lane == 0 && QAM) dbg_win[wi].y = (float)mw;
+    // statistics: lane i < WPW selects from the record of the warp's window i
+    if (lane < WPW && wr < wend) {
+        long long k0 = g.pay_lo + (long long)wr * kWin;
+        int qd = QAM ? (int)((s_m[wr - w0] + r) & 3) : 0;
+        if (!(QAM && k0 < amb_end)) {
+            int best = 0;
+            unsigned be = rec_err(rc, qd);
+#pragma unroll
+            for (int rho = 1; rho < (QAM ? 4 : 1); rho++) {
+                unsigned e = rec_err(rc, (qd + rho) & 3);
+                if (e < be) { be = e; best = rho; }
+            }
+            int qb = (qd + best) & 3;
+            atomicAdd(&s_cnt[C_BITERR], be);
+            atomicAdd(&s_cnt[C_RAWERR], rec_err(rc, qd));
+            atomicAdd(&s_cnt[C_SYMERR], rec_serr(rc, qb));
+            atomicAdd(&s_cnt[C_SLIP], (unsigned)(best != 0));
+            atomicAdd(&s_cnt[C_NEAR], rc.w >> 8);
+            atomicAdd(&s_cnt[C_BITS], (unsigned)(BPS * kWin));
+            atomicAdd(&s_cnt[C_SYMBOLS], (unsigned)kWin);
+        }
+        atomicAdd(&s_cnt[C_WINDOWS], 1u);
+    }
+    // output bits: Gray codes of the rotated decisions, byte b of a window holding
+    // its bits [8b, 8b+8) MSB first, gathered from the owning lanes by shuffle
+    const int sfirst = (8 * lane) / BPS, slast = (8 * lane + 7) / BPS;
+    const int shift = BPS * (slast + 1) - (8 * lane + 8);
+#pragma unroll
+    for (int i = 0; i < WPW; i++) {
+        int wi = w0 + wid + NW * i;
+        if (wi >= wend) break;   // warp-uniform
+        int qd = 0;
+        if (QAM) {
+            long long mw = s_m[wi - w0];
+            qd = (int)((mw + r) & 3);
+            if (dbg_win && lane == 0) dbg_win[wi].y = (float)mw;
+        }
+        uint32_t grp2 = 0;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            int q = lane + 32 * h;
-            uint8_t dv = dec[(k0 - g.pay_lo) + q];
-            int LI = dv & 7, LQ = QAM ? ((dv >> 3) & 7) : 0;
+            int dvb = (dv[i] >> (8 * h)) & 0xFF;
+            int LI = dvb & 7, LQ = QAM ? ((dvb >> 3) & 7) : 0;
             if (QAM) rot_t<MQ>(LI, LQ, qd);
-            s_grp[wid][q] = (uint8_t)(QAM ? ((gray(LI) << NB) | gray(LQ)) : gray(LI));
+            grp2 |= (uint32_t)(QAM ? ((gray(LI) << NB) | gray(LQ)) : gray(LI)) << (8 * h);
         }
-        __syncwarp();
-        // output bytes, MSB first: byte b holds bits [8b, 8b+8) of the window
-        if (lane < NBYTES) {
-            int byte = 0;
+        uint32_t acc = 0;
 #pragma unroll
-            for (int t = 0; t < 8; t++) {
-                int bit = 8 * lane + t, q = bit / BPS, o = bit - q * BPS;
-                byte = (byte << 1) | ((s_grp[wid][q] >> (BPS - 1 - o)) & 1);
-            }
-            bits_out[(long long)wi * NBYTES + lane] = (uint8_t)byte;
+        for (int j = 0; j < NS; j++) {
+            int s = sfirst + j;
+            uint32_t v = __shfl_sync(0xffffffffu, grp2, s & 31);
+            if (s <= slast) acc = (acc << BPS) | (((s & 32) ? v >> 8 : v) & 0xFFu);
         }
-        if (lane == 0) {
-            uint4 rc = winrec[wi];
-            if (!(QAM && k0 < amb_end)) {
-                int best = 0;
-                unsigned be = rec_err(rc, qd);
-#pragma unroll
-                for (int rho = 1; rho < (QAM ? 4 : 1); rho++) {
-                    unsigned e = rec_err(rc, (qd + rho) & 3);
-                    if (e < be) { be = e; best = rho; }
-                }
-                int qb = (qd + best) & 3;
-                atomicAdd(&s_cnt[C_BITERR], (unsigned long long)be);
-                atomicAdd(&s_cnt[C_RAWERR], (unsigned long long)rec_err(rc, qd));
-                atomicAdd(&s_cnt[C_SYMERR], (unsigned long long)rec_serr(rc, qb));
-                atomicAdd(&s_cnt[C_SLIP], (unsigned long long)(best != 0));
-                atomicAdd(&s_cnt[C_NEAR], (unsigned long long)(rc.w >> 8));
-                atomicAdd(&s_cnt[C_BITS], (unsigned long long)(BPS * kWin));
-                atomicAdd(&s_cnt[C_SYMBOLS], (unsigned long long)kWin);
-            }
-            atomicAdd(&s_cnt[C_WINDOWS], 1ull);
-        }
-        __syncwarp();
+        if (lane < NBYTES) bits_out[(long long)wi * NBYTES + lane] = (uint8_t)(acc >> shift);
     }
     __syncthreads();
-    if (tid < C_NCNT && s_cnt[tid]) atomicAdd(&dst->cnt[tid], s_cnt[tid]);
+    if (tid < C_NCNT && s_cnt[tid]) atomicAdd(&dst->cnt[tid], (unsigned long long)s_cnt[tid]);
     // carry the unwrap state to the next call
     if (QAM && wend == g.nwin && w0 < wend && tid == 0) {
         int o = uw_in ^ 1;

@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2
 {
     __shared__ float2 s_tw[512];
     __shared__ __align__(16) uint32_t raw[32][kRawWords];
+    __shared__ __align__(16) float s_ln[kLutCodes];
     int pair = blockIdx.y;
     if (pair == g.npairs) {
         // history of the next call: samples [avail - nhist, avail) = virtual bytes
@@ -251,6 +252,10 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2
         return;
     }
     const TwSmem tw = stage_tw(tb.twN, g.N, s_tw);
+    // the ln table in shared memory: a gather over 32 random codes costs a few bank
+    // conflicts there instead of one L1 wavefront per distinct cache line
+    for (int i = threadIdx.x; i < kLutCodes / 4; i += blockDim.x)
+        reinterpret_cast<float4 *>(s_ln)[i] = __ldg(reinterpret_cast<const float4 *>(tb.lnt) + i);
     const int c0 = blockIdx.x * blockDim.x;
     const int jb = 2 * pair + 1;
     const bool hb = jb < g.J;
@@ -265,11 +270,11 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2
     for (int q = 0; q < 16; q++) {
         long long na = wa + (long long)g.N2 * q;
         uint32_t ca = na < 0 ? c_first : decode_col(raw[q], t, pk.order);
-        float ua = __ldg(tb.lnt + ca), ub = 0.f;
+        float ua = s_ln[ca], ub = 0.f;
         if (hb) {
             long long nb2 = wb + (long long)g.N2 * q;
             uint32_t cb = nb2 < 0 ? c_first : decode_col(raw[16 + q], t, pk.order);
-            ub = __ldg(tb.lnt + cb);
+            ub = s_ln[cb];
         }
         x[q] = make_float2(ua, ub);
     }
@@ -443,7 +448,8 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
             float phi = (half ? x[q].y : x[q].x) * invN;
             float sn, cs;
             __sincosf(phi, &sn, &cs);   // |phi| < pi: absolute error <= 2^-21.41
-            float A = __ldg(tb.sqt + code);
+            // correctly rounded: equal to (float)sqrt(I) of the table for every 12-bit code
+            float A = sqrtf(code ? (float)code : 0.5f);
             float2 e = make_float2(A * cs, A * sn);
             Eb[tt] = e;
             sre += e.x;
@@ -713,7 +719,7 @@ __global__ void __cluster_dims__(kClC, 1, 1) __launch_bounds__(kClThreads, 3)
                 float phi = (half ? x[q].y : x[q].x) * invN;
                 float sn, cs;
                 __sincosf(phi, &sn, &cs);   // |phi| < pi: absolute error <= 2^-21.41
-                float A = __ldg(tb.sqt + code);
+                float A = sqrtf(code ? (float)code : 0.5f);   // = (float)sqrt(I), every code
                 float2 e = make_float2(A * cs, A * sn);
                 E[n - g.ebase] = e;
                 sre += e.x;
