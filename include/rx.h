@@ -192,11 +192,11 @@ rx_status rx_process(rx_handle *h, const uint8_t *packed12_in, uint8_t *bits_out
 
 /* Process n consecutive buffers of the stream (ins[i], outs[i] as in rx_process;
  * nbits_out[i] per buffer).  The results are those of n rx_process calls.  The
- * front end of buffer i+1 (field reconstruction, matched filter) runs
- * concurrently with the back end of buffer i (equaliser, decisions, bits), on
- * two streams the handle owns (the front one at the highest stream priority),
- * as the paper overlaps consecutive buffers in parallel streams chained by
- * events (Sec. 2).  The pipeline starts after the work already on cuda_stream,
+ * stages of consecutive buffers overlap on streams the handle owns, as the paper
+ * overlaps consecutive buffers in parallel streams chained by events (Sec. 2):
+ * the KK field of even and odd buffers on two streams (highest priority), each
+ * ordered after the previous buffer's history copy and field, the matched
+ * filter, the equaliser and the decisions and bits each on a stream of its own.  The pipeline starts after the work already on cuda_stream,
  * and cuda_stream waits for its last back end before anything enqueued later.
  * With cfg.debug = 1 the buffers run one at a time on cuda_stream.  The stages
  * overlap only if their streams reach separate hardware queues: with several

@@ -48,11 +48,11 @@ struct rx_handle {
     int broken;
     // device memory
     uint16_t *codes[2];
-    uint8_t *phist[2];              // KK: packed history, ping-pong
+    uint8_t *phist[3];              // KK: packed history, three slots (see front2)
     int hw;
-    float2 *fftws, *E[kSlots];
+    float2 *fftws[2], *E[kSlots];   // FFT workspace per front-end stream
     void *Y[kSlots];
-    CarrierPartial *partials;
+    CarrierPartial *partials[2];
     uint8_t *dec[kSlots], *winb[kSlots], *prbs;
     uint32_t *prbs_bits;            // the PRBS period bit-packed MSB first, first 256 bits repeated
     uint4 *winrec[kSlots];          // per payload window: errors under the four rotations, near count
@@ -62,9 +62,14 @@ struct rx_handle {
     // (equaliser, demap) of buffer i runs on `back`
     // the front end runs on `front`, created at the highest priority so that its
     // cluster launches are placed ahead of the back end's CTAs
-    cudaStream_t front, mid, back, tail, copy;   // KK: field | matched filter | equaliser | demap
-    cudaEvent_t ev_fork, ev_front, ev_mid, ev_eq, ev_join, ev_yfree[kSlots], ev_efree[kSlots], ev_dfree[kSlots],
-        ev_inready[2], ev_infree[2];
+    // KK: the field of odd calls runs on `front2`, so that the field of call i+1
+    // overlaps the field of call i; its forward pass waits only for the history
+    // copy of call i (ev_hist) and its inverse pass for the field of call i
+    // (ev_front).  Call i+1 writes the history slot that call i-1 read, hence
+    // three slots.
+    cudaStream_t front, front2, mid, back, tail, copy;   // KK: field | matched filter | equaliser | demap
+    cudaEvent_t ev_fork, ev_front, ev_hist, ev_mid, ev_eq, ev_join, ev_yfree[kSlots], ev_efree[kSlots],
+        ev_dfree[kSlots], ev_inready[2], ev_infree[2];
     float2 *taps[2], *twN, *twN2, *ds_tab;
     float *lnt, *sqt;
     float *rrc;
@@ -308,13 +313,14 @@ void rx_destroy(rx_handle *h)
     if (!h) return;
     // work still queued on the pipeline's own streams finishes before the memory goes
     if (h->front) cudaStreamSynchronize(h->front);
+    if (h->front2) cudaStreamSynchronize(h->front2);
     if (h->mid) cudaStreamSynchronize(h->mid);
     if (h->back) cudaStreamSynchronize(h->back);
     if (h->tail) cudaStreamSynchronize(h->tail);
     if (h->copy) cudaStreamSynchronize(h->copy);
-    void *ptrs[] = {h->codes[0], h->codes[1], h->fftws, h->partials, h->prbs, h->taps[0], h->taps[1], h->twN,
+    void *ptrs[] = {h->codes[0], h->codes[1], h->fftws[0], h->fftws[1], h->partials[0], h->partials[1], h->prbs, h->taps[0], h->taps[1], h->twN,
                     h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
-                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->zbuf, h->gpart, h->fd_H, h->fd_tw, h->R[0], h->R[1],
+                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->phist[2], h->zbuf, h->gpart, h->fd_H, h->fd_tw, h->R[0], h->R[1],
                     h->rs_tab, h->clk};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -331,11 +337,12 @@ void rx_destroy(rx_handle *h)
         free(h->prof_ev);
     }
     if (h->front) cudaStreamDestroy(h->front);
+    if (h->front2) cudaStreamDestroy(h->front2);
     if (h->mid) cudaStreamDestroy(h->mid);
     if (h->back) cudaStreamDestroy(h->back);
     if (h->tail) cudaStreamDestroy(h->tail);
     if (h->copy) cudaStreamDestroy(h->copy);
-    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_inready[0],
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_inready[0],
                           &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
     for (cudaEvent_t *ev : evs)
         if (*ev) cudaEventDestroy(*ev);
@@ -474,10 +481,12 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
             for (int i = 0; i < 2; i++) RX_ALLOC(h->R[i], (kEHist + nb + nb / 64 + 64) * sizeof(float2));
             RX_ALLOC(h->rs_tab, 1024 * 16 * sizeof(float));
         }
-        for (int i = 0; i < 2; i++) RX_ALLOC(h->phist[i], (size_t)h->nhist * 3 / 2 + 16);
-        RX_ALLOC(h->fftws, (size_t)h->npairs_max * h->N * sizeof(float2));
+        for (int i = 0; i < 3; i++) RX_ALLOC(h->phist[i], (size_t)h->nhist * 3 / 2 + 16);
         int gx = (h->N2 + kCtaK1 - 1) / kCtaK1;
-        RX_ALLOC(h->partials, (size_t)gx * h->npairs_max * sizeof(CarrierPartial));
+        for (int i = 0; i < 2; i++) {
+            RX_ALLOC(h->fftws[i], (size_t)h->npairs_max * h->N * sizeof(float2));
+            RX_ALLOC(h->partials[i], (size_t)gx * h->npairs_max * sizeof(CarrierPartial));
+        }
         RX_ALLOC(h->twN, kk_tw_entries(h->N) * sizeof(float2));
         RX_ALLOC(h->twN2, kk_tw_entries(h->N2) * sizeof(float2));
         RX_ALLOC(h->lnt, kLutCodes * sizeof(float));
@@ -604,11 +613,12 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         int least = 0, greatest = 0;
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
         bool ok = cudaStreamCreateWithPriority(&h->front, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+                  cudaStreamCreateWithPriority(&h->front2, cudaStreamNonBlocking, greatest) == cudaSuccess &&
                   cudaStreamCreateWithPriority(&h->mid, cudaStreamNonBlocking, greatest) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->tail, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
-        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_inready[0],
+        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_inready[0],
                               &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
         for (cudaEvent_t *ev : evs)
             ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
@@ -672,6 +682,10 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     cudaError_t e = cudaSuccess;
     int par = (int)(h->calls & 1);
     int ds = (int)(h->calls % kSlots);   // decision slot of this call
+    // KK in the pipeline: the field of odd calls on the second front-end stream
+    const bool alt = three && h->front2;
+    if (alt && par) sf = h->front2;
+    const KkSync ksync = {alt ? h->ev_hist : nullptr, alt ? h->ev_hist : nullptr, alt ? h->ev_front : nullptr};
     if (host_in) {
         in = h->in_stage[par];
         if (sc != sf) cudaStreamWaitEvent(sc, h->ev_infree[par], 0);   // the front end two calls back is done
@@ -700,7 +714,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     if (h->kk) {
         kin.hist = h->phist[h->hw];
         kin.in = in;
-        kin.hist_next = h->phist[h->hw ^ 1];
+        kin.hist_next = h->phist[(h->hw + 1) % 3];
         kin.hist_bytes = (long long)h->nhist * 3 / 2;
         kin.in_bytes = h->nb * 3 / 2;
         kin.order = c.pack_order;
@@ -729,14 +743,14 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         g.fused = c.kk_front;
         if (three) cudaStreamWaitEvent(sf, h->ev_efree[ew_new], 0);   // the matched filter is done with this slot
         KkTables tb = {h->lnt, h->sqt, h->twN, h->twN2};
-        e = traced(launch_kk_front(g, kin, h->fftws, tb, h->E[ew_new], h->E[h->ew], h->partials, h->st, sf,
-                                   h->prof_cur ? h : nullptr), "KK front end");
+        e = traced(launch_kk_front(g, kin, h->fftws[par], tb, h->E[ew_new], h->E[h->ew], h->partials[par], h->st, sf,
+                                   h->prof_cur ? h : nullptr, ksync), "KK front end");
         h->ew = ew_new;
         h->ebase_cur = g.ebase;
     } else if (e == cudaSuccess && h->kk) {
-        e = traced(launch_kk_hist(kin, sf), "KK history copy");
+        e = traced(launch_kk_hist(kin, sf, ksync), "KK history copy");
     }
-    if (h->kk) h->hw ^= 1;
+    if (h->kk) h->hw = (h->hw + 1) % 3;
     if (three) {
         if (host_in && sc != sf) cudaEventRecord(h->ev_infree[par], sf);   // the field has read the input
         cudaEventRecord(h->ev_front, sf);
@@ -895,6 +909,7 @@ static rx_status run_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *con
     if (!one) {
         // everything earlier on the caller's stream precedes the pipeline
         if (cudaEventRecord(h->ev_fork, caller) != cudaSuccess || cudaStreamWaitEvent(sf, h->ev_fork, 0) != cudaSuccess ||
+            cudaStreamWaitEvent(h->front2, h->ev_fork, 0) != cudaSuccess ||
             cudaStreamWaitEvent(h->mid, h->ev_fork, 0) != cudaSuccess ||
             cudaStreamWaitEvent(h->tail, h->ev_fork, 0) != cudaSuccess ||
             cudaStreamWaitEvent(sb, h->ev_fork, 0) != cudaSuccess || cudaStreamWaitEvent(sc, h->ev_fork, 0) != cudaSuccess)

@@ -800,8 +800,9 @@ __global__ void k_kk_hist(KkPacked pk)
     }
 }
 
-cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st)
+cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st, const KkSync &sync)
 {
+    if (sync.wait_fwd) cudaStreamWaitEvent(st, sync.wait_fwd, 0);
     KkPacked pk;
     pk.hist = inp.hist;
     pk.in = inp.in;
@@ -811,6 +812,7 @@ cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st)
     pk.order = inp.order;
     pk.first_call = inp.first_call;
     k_kk_hist<<<32, 256, 0, st>>>(pk);
+    if (sync.rec_fwd) cudaEventRecord(sync.rec_fwd, st);
     return cudaGetLastError();
 }
 
@@ -821,7 +823,7 @@ cudaError_t prepare_kk_front()
 
 cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, const KkTables &tb,
                             float2 *E, const float2 *E_prev, CarrierPartial *partials, DevState *dst,
-                            cudaStream_t st, void *prof)
+                            cudaStream_t st, void *prof, const KkSync &sync)
 {
     KkPacked pk;
     pk.hist = inp.hist;
@@ -833,8 +835,11 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     pk.first_call = inp.first_call;
     if (g.N2 == kClN2 && g.fused) {
         // 2^16-point blocks: the fused cluster kernel (profiled as the K1a stage)
+        if (sync.wait_fwd) cudaStreamWaitEvent(st, sync.wait_fwd, 0);
+        if (sync.wait_inv) cudaStreamWaitEvent(st, sync.wait_inv, 0);
         prof_stage(prof, 1, st);
         k_kk_cluster<<<g.npairs * kClC, kClThreads, kClSmem, st>>>(g, pk, tb, E, E_prev, partials, dst);
+        if (sync.rec_fwd) cudaEventRecord(sync.rec_fwd, st);
         prof_stage(prof, -2, st);
         prof_stage(prof, -3, st);
         prof_stage(prof, -4, st);
@@ -842,8 +847,10 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     }
     dim3 grid(g.N2 / kCtaK1, g.npairs);
     dim3 grid_a(g.N2 / kCtaK1, g.npairs + (inp.hist_next ? 1 : 0));
+    if (sync.wait_fwd) cudaStreamWaitEvent(st, sync.wait_fwd, 0);
     prof_stage(prof, 1, st);
     k_kk_fwd<<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
+    if (sync.rec_fwd) cudaEventRecord(sync.rec_fwd, st);
     prof_stage(prof, -2, st);
     int rows = g.npairs * 16;
     if (g.N2 == 4096) {
@@ -855,6 +862,7 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     } else {
         k_kk_rows<1><<<(rows + 255) / 256, 256, 0, st>>>(g, fftws, tb.twN2);
     }
+    if (sync.wait_inv) cudaStreamWaitEvent(st, sync.wait_inv, 0);
     prof_stage(prof, -3, st);
     k_kk_inv<<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, partials, dst);
     prof_stage(prof, -4, st);

@@ -108,11 +108,19 @@ cudaError_t launch_unpack(const uint8_t *in, uint16_t *codes, const uint16_t *co
                           int pack_order, long long *s1, long long *s2, cudaStream_t st);
 
 // copy of the next call's packed history only (calls that emit no field)
-cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st);
+// Cross-stream order of the front end when consecutive calls run on different
+// streams (null events: one stream, nothing to do): the forward pass waits for
+// wait_fwd (the previous call's history copy) and records rec_fwd after its own;
+// the inverse pass waits for wait_inv (the previous call's field, whose tail it
+// carries as history).
+struct KkSync {
+    cudaEvent_t wait_fwd, rec_fwd, wait_inv;
+};
+cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st, const KkSync &sync);
 
 cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, const KkTables &tb,
                             float2 *E, const float2 *E_prev, CarrierPartial *partials, DevState *dst,
-                            cudaStream_t st, void *prof);
+                            cudaStream_t st, void *prof, const KkSync &sync);
 // stage-boundary hook of the profiler (defined with the C ABI; prof may be null)
 void prof_stage(void *prof, int stage, cudaStream_t st);
 
