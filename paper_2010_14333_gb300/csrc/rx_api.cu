@@ -71,7 +71,7 @@ struct rx_handle {
     cudaEvent_t ev_fork, ev_front, ev_hist, ev_mid, ev_eq, ev_join, ev_yfree[kSlots], ev_efree[kSlots],
         ev_dfree[kSlots], ev_inready[2], ev_infree[2];
     float2 *taps[2], *twN, *twN2, *ds_tab;
-    float *lnt, *sqt;
+    float *lnt;
     float *rrc;
     float rrc_host[2 * 64 + 1];     // host copy of the matched-filter taps
     float4 *dbg_win;
@@ -320,7 +320,7 @@ void rx_destroy(rx_handle *h)
     if (h->copy) cudaStreamSynchronize(h->copy);
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws[0], h->fftws[1], h->partials[0], h->partials[1], h->prbs, h->taps[0], h->taps[1], h->twN,
                     h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
-                    h->bits_stage, h->lnt, h->sqt, h->prbs_bits, h->phist[0], h->phist[1], h->phist[2], h->zbuf, h->gpart, h->fd_H, h->fd_tw, h->R[0], h->R[1],
+                    h->bits_stage, h->lnt, h->prbs_bits, h->phist[0], h->phist[1], h->phist[2], h->zbuf, h->gpart, h->fd_H, h->fd_tw, h->R[0], h->R[1],
                     h->rs_tab, h->clk};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -490,7 +490,6 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         RX_ALLOC(h->twN, kk_tw_entries(h->N) * sizeof(float2));
         RX_ALLOC(h->twN2, kk_tw_entries(h->N2) * sizeof(float2));
         RX_ALLOC(h->lnt, kLutCodes * sizeof(float));
-        RX_ALLOC(h->sqt, kLutCodes * sizeof(float));
         RX_ALLOC(h->ds_tab, c.ds_den * sizeof(float2));
     }
     RX_ALLOC(h->prbs, 32767 + 256);
@@ -533,16 +532,14 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     if (kk && e == cudaSuccess) {
         int n1 = kk_tw_entries(h->N), n2 = kk_tw_entries(h->N2);
         float2 *t1 = (float2 *)malloc(sizeof(float2) * n1), *t2 = (float2 *)malloc(sizeof(float2) * n2);
-        float *ln = (float *)malloc(sizeof(float) * kLutCodes), *sq = (float *)malloc(sizeof(float) * kLutCodes);
-        kk_host_tables(h->N, ln, sq, t1, t2);
+        float *ln = (float *)malloc(sizeof(float) * kLutCodes);
+        kk_host_tables(h->N, ln, t1, t2);
         e = cudaMemcpy(h->twN, t1, sizeof(float2) * n1, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(h->twN2, t2, sizeof(float2) * n2, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(h->lnt, ln, sizeof(float) * kLutCodes, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(h->sqt, sq, sizeof(float) * kLutCodes, cudaMemcpyHostToDevice);
         free(t1);
         free(t2);
         free(ln);
-        free(sq);
         float2 *ds = (float2 *)malloc(sizeof(float2) * c.ds_den);
         twiddles(c.ds_den, ds);      // e^{-2 pi i p / den}
         if (e == cudaSuccess) e = cudaMemcpy(h->ds_tab, ds, sizeof(float2) * c.ds_den, cudaMemcpyHostToDevice);
@@ -682,8 +679,10 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     cudaError_t e = cudaSuccess;
     int par = (int)(h->calls & 1);
     int ds = (int)(h->calls % kSlots);   // decision slot of this call
-    // KK in the pipeline: the field of odd calls on the second front-end stream
-    const bool alt = three && h->front2;
+    // KK in the pipeline: the field of odd calls on the second front-end stream.
+    // Not with the CNN receiver: its decision kernel is persistent (one CTA per SM),
+    // and a second field in flight at the higher priority holds SMs it waits for.
+    const bool alt = three && h->front2 && !h->cnn;
     if (alt && par) sf = h->front2;
     const KkSync ksync = {alt ? h->ev_hist : nullptr, alt ? h->ev_hist : nullptr, alt ? h->ev_front : nullptr};
     if (host_in) {
@@ -742,7 +741,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         g.slot = ew_new;
         g.fused = c.kk_front;
         if (three) cudaStreamWaitEvent(sf, h->ev_efree[ew_new], 0);   // the matched filter is done with this slot
-        KkTables tb = {h->lnt, h->sqt, h->twN, h->twN2};
+        KkTables tb = {h->lnt, h->twN, h->twN2};
         e = traced(launch_kk_front(g, kin, h->fftws[par], tb, h->E[ew_new], h->E[h->ew], h->partials[par], h->st, sf,
                                    h->prof_cur ? h : nullptr, ksync), "KK front end");
         h->ew = ew_new;

@@ -154,12 +154,11 @@ static void factored_twiddles(int M, float2 *out)
     }
 }
 
-void kk_host_tables(int N, float *lnt, float *sqt, float2 *twN, float2 *twN2)
+void kk_host_tables(int N, float *lnt, float2 *twN, float2 *twN2)
 {
     for (int c = 0; c < kLutCodes; c++) {
         double I = c ? (double)c : 0.5;
         lnt[c] = (float)(0.5 * log(I / 2048.0));
-        sqt[c] = (float)sqrt(I);
     }
     factored_twiddles(N, twN);
     factored_twiddles(N / 16, twN2);

@@ -64,7 +64,6 @@ struct KkGeom {
 // stored as [lo (2^s) | hi (M / 2^s)].
 struct KkTables {
     const float *lnt;      // 4096: ln(I)/2 - ln(2048)/2, I = code (0.5 for code 0)
-    const float *sqt;      // 4096: sqrt(I)
     const float2 *twN;     // factored W_N
     const float2 *twN2;    // factored W_{N/16}
 };
@@ -72,7 +71,7 @@ constexpr int kLutCodes = 4096;
 // number of float2 entries of the factored table of an M-point transform
 int kk_tw_entries(int M);
 // host: fill the tables of a KK front end with FFT length N
-void kk_host_tables(int N, float *lnt, float *sqt, float2 *twN, float2 *twN2);
+void kk_host_tables(int N, float *lnt, float2 *twN, float2 *twN2);
 
 // packed input of one KK call
 struct KkInput {

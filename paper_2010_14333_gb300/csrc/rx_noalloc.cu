@@ -18,8 +18,8 @@ constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // byte layout of the scratch array: per FFT length (4096, 65536; the 256 slot is unused) a table
-// block [ln table | sqrt table | factored W_N | factored W_{N/16}]
-constexpr size_t kTabBytes = 2 * 4096 * sizeof(float) + 1024 * sizeof(float2);   // >= one block
+// block [ln table | factored W_N | factored W_{N/16}]
+constexpr size_t kTabBytes = 4096 * sizeof(float) + 1024 * sizeof(float2);   // >= one block
 constexpr size_t kTwEntries = 3 * kTabBytes / sizeof(float2);
 constexpr size_t kOffTw = 0;
 constexpr size_t kOffCodes = align_up(kOffTw + kTwEntries * sizeof(float2));
@@ -59,9 +59,9 @@ cudaError_t setup_device(int dev, unsigned char **out)
     const int sizes[3] = {256, 4096, 65536};
     for (int i = 0; i < 3; i++) {
         unsigned char *b = blk + i * kTabBytes;
-        float *ln = (float *)b, *sq = ln + 4096;
-        float2 *t1 = (float2 *)(sq + 4096), *t2 = t1 + kk_tw_entries(sizes[i]);
-        kk_host_tables(sizes[i], ln, sq, t1, t2);
+        float *ln = (float *)b;
+        float2 *t1 = (float2 *)(ln + 4096), *t2 = t1 + kk_tw_entries(sizes[i]);
+        kk_host_tables(sizes[i], ln, t1, t2);
     }
     e = cudaMemcpy((unsigned char *)p + kOffTw, blk, sizeof blk, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
@@ -116,8 +116,7 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     const unsigned char *tabb = base + kOffTw + tab_index(ols_n) * kTabBytes;
     KkTables tb;
     tb.lnt = (const float *)tabb;
-    tb.sqt = tb.lnt + 4096;
-    tb.twN = (const float2 *)(tb.sqt + 4096);
+    tb.twN = (const float2 *)(tb.lnt + 4096);
     tb.twN2 = tb.twN + kk_tw_entries(ols_n);
     uint16_t *codes = (uint16_t *)(base + kOffCodes);
     float2 *fftws = (float2 *)(base + kOffFft);
