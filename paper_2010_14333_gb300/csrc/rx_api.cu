@@ -57,11 +57,10 @@ struct rx_handle {
     uint32_t *prbs_bits;            // the PRBS period bit-packed MSB first, first 256 bits repeated
     uint4 *winrec[kSlots];          // per payload window: errors under the four rotations, near count
     int l_ds;                       // decision slot of the last call
-    // two-stream pipeline of rx_process_batch: the front end (field, matched
-    // filter) of buffer i+1 runs on the caller's stream while the back end
-    // (equaliser, demap) of buffer i runs on `back`
-    // the front end runs on `front`, created at the highest priority so that its
-    // cluster launches are placed ahead of the back end's CTAs
+    // pipeline of rx_process_batch: the front end (field, matched filter) of
+    // buffer i+1 runs while the back end (equaliser, demap) of buffer i runs on
+    // `back` / `tail`; the field runs on `front`, created at the highest priority
+    // so that its launches are placed ahead of the back end's CTAs
     // KK: the field of odd calls runs on `front2`, so that the field of call i+1
     // overlaps the field of call i; its forward pass waits only for the history
     // copy of call i (ev_hist) and its inverse pass for the field of call i
