@@ -194,7 +194,7 @@ rx_status rx_process(rx_handle *h, const uint8_t *packed12_in, uint8_t *bits_out
  * nbits_out[i] per buffer).  The results are those of n rx_process calls.  The
  * stages of consecutive buffers overlap on streams the handle owns, as the paper
  * overlaps consecutive buffers in parallel streams chained by events (Sec. 2):
- * the KK field of even and odd buffers on two streams (highest priority), each
+ * the KK field of even and odd buffers on two streams, each
  * ordered after the previous buffer's history copy and field, the matched
  * filter, the equaliser and the decisions and bits each on a stream of its own.  The pipeline starts after the work already on cuda_stream,
  * and cuda_stream waits for its last back end before anything enqueued later.

@@ -59,8 +59,7 @@ struct rx_handle {
     int l_ds;                       // decision slot of the last call
     // pipeline of rx_process_batch: the front end (field, matched filter) of
     // buffer i+1 runs while the back end (equaliser, demap) of buffer i runs on
-    // `back` / `tail`; the field runs on `front`, created at the highest priority
-    // so that its launches are placed ahead of the back end's CTAs
+    // `back` / `tail`
     // KK: the field of odd calls runs on `front2`, so that the field of call i+1
     // overlaps the field of call i; its forward pass waits only for the history
     // copy of call i (ev_hist) and its inverse pass for the field of call i
@@ -606,11 +605,13 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     h->rbase_cur = -kEHist;
     h->ybase_cur = -kYHist;
     {
-        int least = 0, greatest = 0;
-        cudaDeviceGetStreamPriorityRange(&least, &greatest);
-        bool ok = cudaStreamCreateWithPriority(&h->front, cudaStreamNonBlocking, greatest) == cudaSuccess &&
-                  cudaStreamCreateWithPriority(&h->front2, cudaStreamNonBlocking, greatest) == cudaSuccess &&
-                  cudaStreamCreateWithPriority(&h->mid, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+        // one priority for every stage: measured against the field and matched filter
+        // ahead of the back end, and against the equaliser (the longest chain from
+        // buffer to buffer) ahead of the rest, equal priorities gave the highest
+        // throughput with device and with host buffers
+        bool ok = cudaStreamCreateWithFlags(&h->front, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->front2, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->mid, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->tail, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
@@ -680,7 +681,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     int ds = (int)(h->calls % kSlots);   // decision slot of this call
     // KK in the pipeline: the field of odd calls on the second front-end stream.
     // Not with the CNN receiver: its decision kernel is persistent (one CTA per SM),
-    // and a second field in flight at the higher priority holds SMs it waits for.
+    // and a second field in flight holds SMs it waits for.
     const bool alt = three && h->front2 && !h->cnn;
     if (alt && par) sf = h->front2;
     const KkSync ksync = {alt ? h->ev_hist : nullptr, alt ? h->ev_hist : nullptr, alt ? h->ev_front : nullptr};
