@@ -65,6 +65,27 @@ def workload_config(args):
             "seed": 1}
 
 
+def cpu_model():
+    """The host CPU's model name (or its architecture where the kernel does not say)."""
+    import platform
+    arm = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k = k.strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    return v.strip()
+                if k in ("cpu implementer", "cpu part") and k not in arm:
+                    arm[k] = v.strip()
+    except OSError:
+        pass
+    if arm:   # Arm kernels give the implementer and part numbers only (0x41 / 0xd4f: Neoverse V2)
+        return "%s, implementer %s, part %s" % (platform.machine(), arm.get("cpu implementer", "?"),
+                                                 arm.get("cpu part", "?"))
+    return platform.machine()
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -157,7 +178,8 @@ def reference_arm(args, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": "GSa/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one {nb}-sample buffer of the KK-16QAM stream per step"},
+                             "sample": f"one {nb}-sample buffer of the KK-16QAM stream per step",
+                             "host_cpus": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "GSa/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "ber": s["ber"]}
     print(json.dumps(line), flush=True)
@@ -410,6 +432,7 @@ def gpu_arm(args, rank, world, local):
         sg = chk.stats()
         cpu = {"value": nref * NB / dt / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
                "sample": f"the first {nref} buffers (2^22 samples each) of the same stream, single thread",
+               "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
                "ber_oracle": so["ber"], "ber_gpu_same_buffers": sg["ber"],
                "bit_errors_oracle": so["bit_errors"], "bit_errors_gpu": sg["bit_errors"], "bits": so["bits"]}
 
@@ -1002,7 +1025,7 @@ def main():
     ap.add_argument("--stability", type=int, default=0, help="buffers of the Q time series (0: off)")
     ap.add_argument("--batched-streams", type=int, default=64)
     ap.add_argument("--batched-rounds", type=int, default=10)
-    ap.add_argument("--latency-reps", type=int, default=300)
+    ap.add_argument("--latency-reps", type=int, default=1000)
     ap.add_argument("--eq-warps", type=int, default=0, help="equaliser blocks per CTA (0: library default)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
