@@ -63,6 +63,18 @@ def test_kk16_batch_equals_sequential(splits):
     same(batched(4, nb, g["packed"], splits), ref)
 
 
+@pytest.mark.parametrize("splits", [[7], [2, 1, 4]])
+def test_kk_cluster_front_batch_equals_sequential(splits):
+    """The fused cluster front end in the pipeline: the field of consecutive buffers
+    alternates over two streams, each launch ordered after the previous buffer's
+    history copy and field."""
+    nb = 1 << 19
+    g = make_stream(4, nb, 7, seed=16, workers=4)
+    ref = sequential(4, nb, g["packed"], kk_front=1)
+    assert ref[1]["bits"] > 0
+    same(batched(4, nb, g["packed"], splits, kk_front=1), ref)
+
+
 def test_kk_small_fft_batch_equals_sequential():
     """Many overlap-save blocks per buffer and a ragged buffer length."""
     nb = 65536 * 3 - 160
