@@ -74,9 +74,10 @@ def lib():
         L.orx_fd_block.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
         L.orx_rs_taps.argtypes = [C.c_double, C.c_void_p]
-        L.orx_fd_clock.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
-                                   C.c_void_p]
-        L.orx_clock_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+        L.orx_fd_clock.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                   C.c_void_p, C.c_void_p]
+        L.orx_clock_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                    C.c_void_p]
         L.orx_clock_fit.restype = C.c_int
         L.orx_fd_block_full.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p]
@@ -186,24 +187,25 @@ def rs_taps(mu: float) -> np.ndarray:
     return c
 
 
-def fd_clock(x: np.ndarray, H: np.ndarray, w: int) -> complex:
-    """Band-edge clock correlation of one KK FD block (N inputs)."""
+def fd_clock(x: np.ndarray, H: np.ndarray, w: int, sps: int = 4) -> complex:
+    """Band-edge clock correlation of one FD block (N inputs at sps samples/symbol)."""
     xr = np.ascontiguousarray(np.real(x), dtype=np.float64)
     xi = np.ascontiguousarray(np.imag(x), dtype=np.float64)
     Hr = np.ascontiguousarray(np.real(H), dtype=np.float64)
     Hi = np.ascontiguousarray(np.imag(H), dtype=np.float64)
     cr, ci = C.c_double(), C.c_double()
-    lib().orx_fd_clock(_ptr(xr), _ptr(xi), len(xr), _ptr(Hr), _ptr(Hi), w, C.byref(cr), C.byref(ci))
+    lib().orx_fd_clock(_ptr(xr), _ptr(xi), len(xr), _ptr(Hr), _ptr(Hi), sps, w, C.byref(cr), C.byref(ci))
     return complex(cr.value, ci.value)
 
 
-def clock_fit(c: np.ndarray, centers: np.ndarray):
-    """(ppm, delay in ADC samples) from block correlations and block centres."""
+def clock_fit(c: np.ndarray, centers: np.ndarray, sps: int = 4):
+    """(ppm, delay in ADC samples) from block correlations and block centres
+    (symbol period sps ADC samples: 4 for KK, 2 for PAM)."""
     cr = np.ascontiguousarray(np.real(c), dtype=np.float64)
     ci = np.ascontiguousarray(np.imag(c), dtype=np.float64)
     ce = np.ascontiguousarray(centers, dtype=np.int64)
     ppm, dl = C.c_double(), C.c_double()
-    if lib().orx_clock_fit(_ptr(cr), _ptr(ci), _ptr(ce), len(cr), C.byref(ppm), C.byref(dl)) != 0:
+    if lib().orx_clock_fit(_ptr(cr), _ptr(ci), _ptr(ce), len(cr), sps, C.byref(ppm), C.byref(dl)) != 0:
         raise ValueError("too few blocks")
     return ppm.value, dl.value
 

@@ -248,21 +248,24 @@ void orx_rs_taps(double mu, double *c)
 
 /* ---------------------------------------------------- FD clock estimate
  * The paper recovers the clock in the frequency domain block by block and unwraps
- * the clock phase across blocks and buffers (Sec. 2).  Reading (Godard's band-edge
- * estimator on the KK form's blocks at 4 samples/symbol): with Y = FFT(x_b) H / N,
- *   C_b = sum_{|k - N/8| <= w} Y_k conj(Y_{k - N/4}),
+ * the clock phase across blocks and buffers (Sec. 2), in the PAM chain after its
+ * static FD filter and in the KK chain.  Reading (Godard's band-edge estimator on
+ * the FD form's N-point blocks at sps samples/symbol, 4 for KK, 2 for PAM): with
+ * Y = FFT(x_b) H / N and S = N / sps the bin of the symbol rate,
+ *   C_b = sum_{|k - S/2| <= w} Y_k conj(Y_{k - S}),
  * the correlation of the spectrum at +1/(2T) with its image one symbol rate lower;
- * a symbol grid at ADC positions congruent to d (mod 4) gives arg C_b = -pi d / 2.
- * w is the roll-off half-width ceil(beta N / 8) in bins. */
+ * a symbol grid at ADC positions congruent to d (mod sps) gives
+ * arg C_b = -2 pi d / sps.  w is the roll-off half-width ceil(beta S / 2) in bins. */
 void orx_fd_clock(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
-                  int w, double *c_re, double *c_im)
+                  int sps, int w, double *c_re, double *c_im)
 {
     double *re = xcalloc((size_t)n, sizeof(double)), *im = xcalloc((size_t)n, sizeof(double));
     for (int i = 0; i < n; i++) { re[i] = x_re[i]; im[i] = x_im[i]; }
     orx_fft(re, im, n, 0);
     double sr = 0.0, si = 0.0;
-    for (int k = n / 8 - w; k <= n / 8 + w; k++) {
-        int kk = ((k % n) + n) % n, km = (((k - n / 4) % n) + n) % n;
+    const int S = n / sps;
+    for (int k = S / 2 - w; k <= S / 2 + w; k++) {
+        int kk = ((k % n) + n) % n, km = (((k - S) % n) + n) % n;
         double ar = (re[kk] * H_re[kk] - im[kk] * H_im[kk]) / n, ai = (re[kk] * H_im[kk] + im[kk] * H_re[kk]) / n;
         double br = (re[km] * H_re[km] - im[km] * H_im[km]) / n, bi = (re[km] * H_im[km] + im[km] * H_re[km]) / n;
         sr += ar * br + ai * bi;   /* a conj(b) */
@@ -272,21 +275,23 @@ void orx_fd_clock(const double *x_re, const double *x_im, int n, const double *H
     free(re); free(im);
 }
 
-/* Clock offset and delay from the block correlations: d_b = -(2/pi) arg C_b,
- * unwrapped across the blocks (period 4 ADC samples, one symbol), then the least-
- * squares line d_b = -tau0 - eps c_b over the block centres c_b (ADC samples):
- * ppm = 1e6 eps, delay = tau0 (in (-2, 2], the symbol ambiguity is not resolved). */
-int orx_clock_fit(const double *c_re, const double *c_im, const int64_t *center, int nblk, double *ppm,
-                  double *delay)
+/* Clock offset and delay from the block correlations: d_b = -(sps / 2 pi) arg C_b,
+ * unwrapped across the blocks (period sps ADC samples, one symbol), then the
+ * least-squares line d_b = -tau0 - eps c_b over the block centres c_b (ADC samples):
+ * ppm = 1e6 eps, delay = tau0 (in (-sps/2, sps/2], the symbol ambiguity is not
+ * resolved). */
+int orx_clock_fit(const double *c_re, const double *c_im, const int64_t *center, int nblk, int sps,
+                  double *ppm, double *delay)
 {
-    if (nblk < 2) return -1;
+    if (nblk < 2 || sps < 2) return -1;
+    const double P = (double)sps, H = 0.5 * P;
     double prev = 0.0, off = 0.0, sx = 0, sy = 0, sxx = 0, sxy = 0;
     double x0 = (double)center[0];
     for (int b = 0; b < nblk; b++) {
-        double d = -2.0 / PI * atan2(c_im[b], c_re[b]);   /* (-2, 2] */
+        double d = -P / (2.0 * PI) * atan2(c_im[b], c_re[b]);   /* (-sps/2, sps/2] */
         if (b > 0) {
-            while (d + off - prev > 2.0) off -= 4.0;
-            while (d + off - prev < -2.0) off += 4.0;
+            while (d + off - prev > H) off -= P;
+            while (d + off - prev < -H) off += P;
         }
         double y = d + off, x = (double)center[b] - x0;
         prev = y;
@@ -295,8 +300,8 @@ int orx_clock_fit(const double *c_re, const double *c_im, const int64_t *center,
     double nb = (double)nblk, slope = (nb * sxy - sx * sy) / (nb * sxx - sx * sx);
     double icpt = (sy - slope * sx) / nb - slope * x0;   /* at stream index 0 */
     double tau0 = -icpt;
-    while (tau0 > 2.0) tau0 -= 4.0;
-    while (tau0 <= -2.0) tau0 += 4.0;
+    while (tau0 > H) tau0 -= P;
+    while (tau0 <= -H) tau0 += P;
     *ppm = -slope * 1e6;
     *delay = tau0;
     return 0;
@@ -695,6 +700,10 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
         /* PAM: static frequency-domain filter on N-point blocks with hop N/2 at the
          * input rate; the block input is the normalised code, zero before the stream */
         int N = c->fd_n, hop = N / 2;
+        free(h->d_C);
+        h->d_C_start = h->f_prev / hop;
+        h->d_C_len = f_k / hop - h->d_C_start;
+        h->d_C = xcalloc((size_t)(h->d_C_len > 0 ? h->d_C_len : 1), sizeof(cx));
         double *xr = xcalloc((size_t)N, sizeof(double)), *xi = xcalloc((size_t)N, sizeof(double));
         double *yr = xcalloc((size_t)(N / 2), sizeof(double)), *yi = xcalloc((size_t)(N / 2), sizeof(double));
         for (int64_t b = h->f_prev / hop; b < f_k / hop; b++) {
@@ -704,6 +713,12 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
                 xi[t] = 0.0;
             }
             orx_fd_block_full(xr, xi, N, h->fd_Hr, h->fd_Hi, yr, yi);
+            {
+                int w = (int)ceil(c->rrc_beta * N / 4.0);   /* ceil(beta S / 2), S = N / 2 */
+                double cr, ci;
+                orx_fd_clock(xr, xi, N, h->fd_Hr, h->fd_Hi, 2, w, &cr, &ci);
+                h->d_C[b - h->d_C_start] = cx_mk(cr, ci);
+            }
             for (int m = 0; m < N / 2; m++) X.y[(int64_t)hop * b + m - X.y_start] = cx_mk(yr[m], 0.0);
         }
         free(xr); free(xi); free(yr); free(yi);
@@ -729,9 +744,9 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
             }
             orx_fd_block(xr, xi, N, h->fd_Hr, h->fd_Hi, yr, yi);
             {
-                int w = (int)ceil(c->rrc_beta * N / 8.0);
+                int w = (int)ceil(c->rrc_beta * N / 8.0);   /* ceil(beta S / 2), S = N / 4 */
                 double cr, ci;
-                orx_fd_clock(xr, xi, N, h->fd_Hr, h->fd_Hi, w, &cr, &ci);
+                orx_fd_clock(xr, xi, N, h->fd_Hr, h->fd_Hi, 4, w, &cr, &ci);
                 h->d_C[b - h->d_C_start] = cx_mk(cr, ci);
             }
             for (int m = 0; m < N / 4; m++)

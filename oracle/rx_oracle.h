@@ -84,9 +84,9 @@ void    orx_fd_block(const double *x_re, const double *x_im, int n, const double
                      double *y_re, double *y_im);
 void    orx_rs_taps(double mu, double *c);   /* the 16 interpolator taps at fraction mu */
 void    orx_fd_clock(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
-                     int w, double *c_re, double *c_im);
-int     orx_clock_fit(const double *c_re, const double *c_im, const int64_t *center, int nblk, double *ppm,
-                      double *delay);
+                     int sps, int w, double *c_re, double *c_im);
+int     orx_clock_fit(const double *c_re, const double *c_im, const int64_t *center, int nblk, int sps,
+                      double *ppm, double *delay);
 void    orx_fd_block_full(const double *x_re, const double *x_im, int n, const double *H_re, const double *H_im,
                           double *y_re, double *y_im);
 void    orx_prbs15(uint32_t seed, int64_t nbits, uint8_t *out);
@@ -121,7 +121,7 @@ enum {
     ORX_NEAR = 10,   /* near-threshold flag per processed symbol, int32                      */
     ORX_DRAW = 11,   /* raw decision level-index pair before pi/2 rotation, int32 x2        */
     ORX_RS = 12,     /* resampled field on the transmitter's grid (complex)                  */
-    ORX_CLK = 13     /* KK FD form: band-edge clock correlation C_b per emitted block (complex) */
+    ORX_CLK = 13     /* FD form: band-edge clock correlation C_b per emitted block (complex)   */
 };
 
 #ifdef __cplusplus

@@ -261,11 +261,13 @@ def _quantise(I: np.ndarray):
 def gen_pam_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: float = 18.0,
                    isi=(0.1, 1.0, 0.2), beta: float = 0.1, span: int = 16, sps: int = 2,
                    mod_index: float = 0.5, noise: bool = True, prbs_seed: int = 1,
-                   pack_order: int = 0):
+                   pack_order: int = 0, clock_step: int = 1 << 32, clock_phase0: int = 0):
     """Direct-detection PAM-M stream split into nbufs ADC buffers of buf_len samples.
 
     Returns dict with 'packed' (list of uint8 arrays), 'codes', 'bits',
     'symbols' (transmitted levels), 'intensity' (noiseless I_tx) and 'clips'.
+    ``clock_step`` / ``clock_phase0``: the ADC takes sample n at transmitter time
+    (clock_phase0 + n clock_step) / 2^32 nominal samples, as in gen_kk_stream.
     """
     name, bps, kind = FORMATS[fmt]
     assert kind == "pam"
@@ -279,10 +281,21 @@ def gen_pam_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: fl
     a_isi[:-1] += isi[0] * a[1:]
     a_isi[1:] += isi[2] * a[:-1]
     pulse = rrc_pulse(beta, sps, span)
+    offclock = clock_step != (1 << 32) or clock_phase0 != 0
     packed, codes_all, itx_all, clips = [], [], [], 0
     for b in range(nbufs):
         n0, n1 = b * buf_len, (b + 1) * buf_len
-        s = _shape(a_isi, pulse, sps, n0, n1)
+        if offclock:   # the ADC samples at transmitter times phi_n / 2^32 (nominal samples)
+            ti, tf = adc_times(n0, n1, clock_step, clock_phase0)
+            half = span // 2 + 2
+            ka, kb = int(ti[0]) // sps - half - 2, int(ti[-1]) // sps + half + 3
+            seg = np.zeros(kb - ka)
+            lo, hi = max(ka, 0), min(kb, len(a_isi))
+            if hi > lo:
+                seg[lo - ka:hi - ka] = a_isi[lo:hi]
+            s = _shape_at(seg, ka, beta, sps, span, ti, tf).real
+        else:
+            s = _shape(a_isi, pulse, sps, n0, n1)
         itx = 1.0 + mod_index * s / float(M - 1)
         clips += int(np.count_nonzero(itx < 0))
         itx = np.maximum(itx, 0.0)

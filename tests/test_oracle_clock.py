@@ -63,3 +63,60 @@ def test_estimate_drives_the_resampler():
         o.process(g["packed"][b])
     s = o.stats()
     assert s["bits"] > 200000 and s["bit_errors"] == 0
+
+
+# ---- PAM: the band-edge correlation on the FD form's blocks at 2 samples/symbol
+def test_fit_recovers_exact_phases_across_wraps_pam():
+    """C_b = exp(-2 pi i d_b / 2) with d_b = -tau0 - eps c_b through many wraps of the
+    2-sample period."""
+    for ppm, tau0 in ((-35.0, 0.4), (120.0, -0.7), (0.5, 0.95)):
+        centers = 512 * np.arange(3000, 9000) + 256
+        d = -tau0 - ppm * 1e-6 * centers
+        c = 3.0 * np.exp(-1j * np.pi * d)
+        p, t = oracle.clock_fit(c, centers, sps=2)
+        assert abs(p - ppm) < 1e-9 and abs(t - tau0) < 1e-9, (p, t)
+
+
+def test_pam_generator_whole_sample_offset_is_a_shift():
+    """The off-clock path of the PAM generator at a whole-sample phase is the nominal
+    stream shifted by that many samples."""
+    a = synth.gen_pam_stream(1, 1 << 14, 2, noise=False)
+    b = synth.gen_pam_stream(1, 1 << 14, 2, noise=False, clock_phase0=3 << 32)
+    assert np.max(np.abs(a["intensity"][3:] - b["intensity"][:-3])) < 1e-12
+
+
+def _estimate_pam(g, fmt, nb, nbufs):
+    o = oracle.Oracle(**oracle.default_cfg(fmt, nb, mf_mode=1))
+    for b in range(nbufs):
+        o.process(g["packed"][b])
+    c, c0 = o.get(oracle.ORX_CLK)   # the blocks of the last call
+    assert len(c) == nb // 512, (len(c), c0)
+    return oracle.clock_fit(c, 512 * (c0 + np.arange(len(c))) + 256, sps=2)
+
+
+@pytest.mark.parametrize("fmt,d", [(1, 0), (1, 1), (0, 1), (2, 0)])
+def test_pam_whole_sample_delays_on_the_nominal_clock(fmt, d):
+    nb = 1 << 17
+    g = synth.gen_pam_stream(fmt, nb, 2, seed=4, noise=False, isi=(0.0, 1.0, 0.0), clock_phase0=d << 32)
+    ppm, delay = _estimate_pam(g, fmt, nb, 2)
+    err = (delay - d + 1.0) % 2.0 - 1.0    # the delay is known modulo one symbol (2 samples)
+    assert abs(ppm) < 0.2 and abs(err) < 0.01, (ppm, delay)
+
+
+@pytest.mark.parametrize("ppm,delay", [(-35.0, 0.4), (20.0, -0.3), (80.0, 0.85)])
+def test_pam_off_clock_streams(ppm, delay):
+    nb = 1 << 18
+    g = synth.gen_pam_stream(1, nb, 2, seed=2, isi=(0.0, 1.0, 0.0), clock_step=synth.clock_step(ppm),
+                             clock_phase0=int(round(delay * (1 << 32))))
+    p, t = _estimate_pam(g, 1, nb, 2)
+    err = (t - delay + 1.0) % 2.0 - 1.0
+    assert abs(p - ppm) < 0.5 and abs(err) < 0.05, (p, t)
+
+
+def test_pam_off_clock_with_isi():
+    """With the default asymmetric ISI the symbol-rate line moves by a constant: the
+    clock offset (the slope) stays."""
+    nb = 1 << 18
+    g = synth.gen_pam_stream(1, nb, 2, seed=3, clock_step=synth.clock_step(-35.0), clock_phase0=0)
+    p, _ = _estimate_pam(g, 1, nb, 2)
+    assert abs(p + 35.0) < 0.5, p
