@@ -162,7 +162,7 @@ enum {
     RX_DBG_SCAL = 7,     /* double[5]: carrier re, carrier im, gain, PAM mean, PAM 1/std     */
     RX_DBG_CODES = 8,    /* uint16 12-bit code per ADC sample of the last buffer             */
     RX_DBG_RS = 9,       /* KK field resampled to the transmitter's grid, float2 (rs_step)    */
-    RX_DBG_CLK = 10      /* KK FD form: band-edge clock correlation per emitted block, float2 */
+    RX_DBG_CLK = 10      /* FD form: band-edge clock correlation per emitted block, float2   */
 };
 
 /* Defaults of a format (the workload settings of the synthetic configurations). */
@@ -372,17 +372,20 @@ void rx_destroy(rx_handle *h);
 /* Static description of a status code. */
 const char *rx_strerror(rx_status s);
 
-/* ADC clock estimate from the last call (KK chain, mf_mode = RX_MF_FD; Sec. 2
- * recovers the clock in the frequency domain block by block).  Each frequency-
- * domain block b correlates its filtered spectrum at +1/(2T) with its image one
- * symbol rate lower, C_b = sum_{|k - N/8| <= w} Y_k conj(Y_{k - N/4}) (w the roll-off
- * half-width in bins); a symbol grid at ADC positions d (mod 4) gives arg C_b =
- * -pi d / 2.  The unwrapped d_b over the call's blocks are fitted by the line
- * d_b = -delay - 1e-6 ppm centre_b: *ppm is the ADC clock offset (sample period
- * (1 + 1e-6 ppm) nominal samples), *delay the transmitter time of ADC sample 0 in
- * samples, in (-2, 2] (the whole-symbol ambiguity is not resolved).  With the
- * resampler on, the estimate is the residual against its accumulator.  Synchronises
- * the stream.  RX_EINVAL without the FD form, RX_ESTATE with fewer than 2 blocks. */
+/* ADC clock estimate from the last call (mf_mode = RX_MF_FD, KK or PAM chain; Sec. 2
+ * recovers the clock phase in the frequency domain block by block, in the PAM chain
+ * after its static FD filter).  With P the samples per symbol (4 KK, 2 PAM) and
+ * S = N / P the bin of the symbol rate, each frequency-domain block b correlates its
+ * filtered spectrum at +1/(2T) with its image one symbol rate lower,
+ * C_b = sum_{|k - S/2| <= w} Y_k conj(Y_{k - S}) (w the roll-off half-width
+ * ceil(beta S / 2) in bins, at most 31); a symbol grid at ADC positions d (mod P)
+ * gives arg C_b = -2 pi d / P.  The unwrapped d_b over the call's blocks are fitted
+ * by the line d_b = -delay - 1e-6 ppm centre_b: *ppm is the ADC clock offset (sample
+ * period (1 + 1e-6 ppm) nominal samples), *delay the transmitter time of ADC sample 0
+ * in samples, in (-P/2, P/2] (the whole-symbol ambiguity is not resolved).  With the
+ * KK resampler on, the estimate is the residual against its accumulator.
+ * Synchronises the stream.  RX_EINVAL without the FD form, RX_ESTATE with fewer
+ * than 2 blocks. */
 rx_status rx_clock_estimate(rx_handle *h, double *ppm, double *delay, void *cuda_stream);
 
 /* Self-test of the bounded device waits: one CTA waits for an mbarrier phase that

@@ -125,7 +125,7 @@ def _check(status: int):
 
 # ------------------------------------------------------------- C ABI, 1:1
 def rx_clock_estimate(h: int, stream: int = 0):
-    """(ppm, delay in ADC samples) of the ADC clock from the last call (KK FD form)."""
+    """(ppm, delay in ADC samples) of the ADC clock from the last call (FD form, KK or PAM)."""
     ppm, dl = C.c_double(), C.c_double()
     _check(load().rx_clock_estimate(h, C.byref(ppm), C.byref(dl), stream))
     return ppm.value, dl.value

@@ -563,11 +563,17 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
             Hk[kp] = make_float2((float)(re / N), (float)(im / N));
         }
         twiddles(N, tw);
+        // band-edge clock correlation per block: half-width ceil(beta S / 2) bins around
+        // S / 2, S = N / sps the bin of the symbol rate (the 1024-point kernels cover 31)
         if (kk) {   // blocks per call: nominal samples (nb / 0.99 + 8 with the resampler) / (N/2) + 2
             h->clk_w = (int)ceil(c.rrc_beta * N / 8.0);
             if (h->clk_w >= N / 8) h->clk_w = N / 8 - 1;
             if (N == 1024 && h->clk_w > 31) h->clk_w = 31;
             if (e == cudaSuccess) e = cudaMalloc(&h->clk, sizeof(float2) * ((nb + nb / 64 + 64) / (N / 2) + 4));
+        } else {    // PAM: N = 1024 at 2 samples/symbol, N / 2 outputs per block
+            h->clk_w = (int)ceil(c.rrc_beta * N / 4.0);
+            if (h->clk_w > 31) h->clk_w = 31;
+            if (e == cudaSuccess) e = cudaMalloc(&h->clk, sizeof(float2) * (nb / (N / 2) + 4));
         }
         if (e == cudaSuccess) e = cudaMalloc(&h->fd_H, sizeof(float2) * nbins);
         if (e == cudaSuccess) e = cudaMalloc(&h->fd_tw, sizeof(float2) * N);
@@ -783,7 +789,8 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
                              h->ybase_cur, sm, h->rrc_host);
         else if (h->fd)
             e = launch_pam_fd1024(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->fd_H, h->fd_tw, h->st,
-                                  par, (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf);
+                                  par, (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf,
+                                  h->clk, h->clk_w);
         else
             e = launch_pam_mf(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->rrc, h->hmf, h->st, par,
                               (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf);
@@ -1001,7 +1008,9 @@ rx_status rx_clock_estimate(rx_handle *h, double *ppm, double *delay, void *stre
     if (!h || !ppm || !delay) return RX_EINVAL;
     if (!h->clk) return RX_EINVAL;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return RX_ECUDA;
-    const long long per = h->cfg.fd_n / 4, b0 = h->l_f_prev / per, n = (h->l_f_k - h->l_f_prev) / per;
+    // outputs per block at 2 samples/symbol: N/4 (KK, 4 -> 2 sps) or N/2 (PAM)
+    const long long N = h->cfg.fd_n, per = h->kk ? N / 4 : N / 2;
+    const long long b0 = h->l_f_prev / per, n = (h->l_f_k - h->l_f_prev) / per;
     if (n < 2) return RX_ESTATE;
     float2 *c = (float2 *)malloc(sizeof(float2) * n);
     if (!c) return RX_ENOMEM;
@@ -1009,18 +1018,20 @@ rx_status rx_clock_estimate(rx_handle *h, double *ppm, double *delay, void *stre
         free(c);
         return RX_ECUDA;
     }
-    // d_b = -(2/pi) arg C_b unwrapped (period 4 samples), least-squares d_b = -tau0 - eps centre_b,
-    // centre_b = (N/2) b + N/4 (the middle of block b's inputs)
+    // d_b = -(P / 2 pi) arg C_b unwrapped (period P = samples per symbol: 4 KK, 2 PAM),
+    // least-squares d_b = -tau0 - eps centre_b, centre_b = (N/2) b + N/4 (the middle of
+    // block b's inputs)
     const double pi = 3.14159265358979323846;
-    const double x0 = (double)((2 * per) * b0 + per);
+    const double P = h->kk ? 4.0 : 2.0, Hp = 0.5 * P;
+    const double x0 = (double)((N / 2) * b0 + N / 4);
     double prev = 0, off = 0, sx = 0, sy = 0, sxx = 0, sxy = 0;
     for (long long i = 0; i < n; i++) {
-        double d = -2.0 / pi * atan2((double)c[i].y, (double)c[i].x);
+        double d = -P / (2.0 * pi) * atan2((double)c[i].y, (double)c[i].x);
         if (i > 0) {
-            while (d + off - prev > 2.0) off -= 4.0;
-            while (d + off - prev < -2.0) off += 4.0;
+            while (d + off - prev > Hp) off -= P;
+            while (d + off - prev < -Hp) off += P;
         }
-        const double y = d + off, x = (double)(2 * per) * (double)i;
+        const double y = d + off, x = (double)(N / 2) * (double)i;
         prev = y;
         sx += x;
         sy += y;
@@ -1030,8 +1041,8 @@ rx_status rx_clock_estimate(rx_handle *h, double *ppm, double *delay, void *stre
     free(c);
     const double nb = (double)n, slope = (nb * sxy - sx * sy) / (nb * sxx - sx * sx);
     double tau0 = -((sy - slope * sx) / nb - slope * x0);
-    while (tau0 > 2.0) tau0 -= 4.0;
-    while (tau0 <= -2.0) tau0 += 4.0;
+    while (tau0 > Hp) tau0 -= P;
+    while (tau0 <= -Hp) tau0 += P;
     *ppm = -slope * 1e6;
     *delay = tau0;
     return RX_OK;
@@ -1061,8 +1072,8 @@ rx_status rx_debug_copy(rx_handle *h, int what, void *dst, int64_t cap, int64_t 
         break;
     case RX_DBG_CLK:
         if (!h->clk) return RX_EINVAL;
-        n = (h->l_f_k - h->l_f_prev) / (h->cfg.fd_n / 4);
-        s0 = h->l_f_prev / (h->cfg.fd_n / 4);
+        n = (h->l_f_k - h->l_f_prev) / (h->kk ? h->cfg.fd_n / 4 : h->cfg.fd_n / 2);
+        s0 = h->l_f_prev / (h->kk ? h->cfg.fd_n / 4 : h->cfg.fd_n / 2);
         src = h->clk;
         el = sizeof(float2);
         break;

@@ -1456,7 +1456,7 @@ __global__ void __launch_bounds__(32 * kFdWarps, 4)
     k_pam_fd1024(const uint16_t *__restrict__ codes, long long cbase, long long nb, long long n_end,
                  long long b_first, long long nblk, const float2 *__restrict__ H, const float2 *__restrict__ tw,
                  DevState *dst, int parity, float *__restrict__ Y, long long ybase, long long f_prev,
-                 const float *__restrict__ Y_prev, long long ybase_prev)
+                 const float *__restrict__ Y_prev, long long ybase_prev, float2 *__restrict__ clk, int wbin)
 {
     __shared__ float2 s_tw[1024];
     __shared__ float2 s_t[kFdWarps][32 * kFdPitch];
@@ -1506,6 +1506,19 @@ __global__ void __launch_bounds__(32 * kFdWarps, 4)
     dft32<false>(x);   // x[k1] = X[lane + 32 k1]
 #pragma unroll
     for (int k1 = 0; k1 < 32; k1++) x[k1] = cmul(x[k1], __ldg(H + lane + 32 * k1));
+    if (clk) {   // band-edge clock correlation at 2 samples/symbol: bins k = lane + 32 k1 (k1 = 7, 8)
+                 // around N/4 with k - N/2 (k1 + 16)
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k1 = 7; k1 <= 8; k1++) {
+            const int k = lane + 32 * k1;
+            if (k >= 256 - wbin && k <= 256 + wbin) acc = cadd(acc, cmulc(x[k1], x[k1 + 16]));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+            acc = make_float2(acc.x + __shfl_xor_sync(0xffffffffu, acc.x, o), acc.y + __shfl_xor_sync(0xffffffffu, acc.y, o));
+        if (lane == 0) clk[bi] = acc;
+    }
     dft32<true>(x);    // over k1 -> m_a
 #pragma unroll
     for (int ma = 1; ma < 32; ma++) x[ma] = cmulc(x[ma], s_tw[lane * ma]);
@@ -1523,13 +1536,14 @@ __global__ void __launch_bounds__(32 * kFdWarps, 4)
 cudaError_t launch_pam_fd1024(const uint16_t *codes, long long cbase, long long nb, long long n_end,
                               long long f_prev, long long f_k, const float2 *H, const float2 *tw, DevState *dst,
                               int parity, float *Y, long long ybase, const float *Y_prev, long long ybase_prev,
-                              cudaStream_t st)
+                              cudaStream_t st, float2 *clk, int wbin)
 {
-    if (f_prev % 512 || f_k % 512) return cudaErrorInvalidValue;
+    if (f_prev % 512 || f_k % 512 || wbin < 0 || wbin > 31) return cudaErrorInvalidValue;
     const long long nblk = (f_k - f_prev) / 512;
     if (nblk <= 0) return cudaSuccess;
     k_pam_fd1024<<<(unsigned)((nblk + kFdWarps - 1) / kFdWarps), 32 * kFdWarps, 0, st>>>(
-        codes, cbase, nb, n_end, f_prev / 512, nblk, H, tw, dst, parity, Y, ybase, f_prev, Y_prev, ybase_prev);
+        codes, cbase, nb, n_end, f_prev / 512, nblk, H, tw, dst, parity, Y, ybase, f_prev, Y_prev, ybase_prev, clk,
+        wbin);
     return cudaGetLastError();
 }
 

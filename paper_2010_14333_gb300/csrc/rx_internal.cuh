@@ -148,7 +148,7 @@ cudaError_t launch_kk_fdmf(const float2 *E, long long ebase, long long f_prev, l
 cudaError_t launch_pam_fd1024(const uint16_t *codes, long long cbase, long long nb, long long n_end,
                               long long f_prev, long long f_k, const float2 *H, const float2 *tw, DevState *dst,
                               int parity, float *Y, long long ybase, const float *Y_prev, long long ybase_prev,
-                              cudaStream_t st);
+                              cudaStream_t st, float2 *clk, int wbin);
 
 cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, long long n_end, long long f_prev,
                           long long f_k, const float *rrc, int hmf, DevState *dst, int parity,

@@ -68,3 +68,38 @@ def test_estimate_drives_the_gpu_resampler():
         plain.process(d)
     s, sp = r.stats(), plain.stats()
     assert s["bits"] > 0 and s["ber"] < 0.02 and sp["ber"] > 0.1, (s["ber"], sp["ber"])
+
+
+# ---- PAM: the band-edge correlation in the PAM FD kernel (2 samples/symbol)
+def pam_clock(ppm, delay):
+    return dict(clock_step=synth.clock_step(ppm), clock_phase0=int(round(delay * (1 << 32))))
+
+
+@pytest.mark.parametrize("fmt", [0, 1, 2])
+def test_pam_block_correlations_match_oracle(fmt):
+    nb = 1 << 17
+    g = make_stream(fmt, nb, 3, seed=5, **pam_clock(15.0, 0.3))
+    p = Pair(fmt, nb, mf_mode=1)
+    for b in range(3):
+        p.feed(g["packed"][b], check=False)
+        c, c0 = p.g.debug(rx.RX_DBG_CLK)
+        co, co0 = p.o.get(oracle.ORX_CLK)
+        assert (c0, len(c)) == (co0, len(co)) and len(c) > 0
+        assert np.linalg.norm(c - co) / np.linalg.norm(co) < 1e-4
+
+
+@pytest.mark.parametrize("ppm,delay", [(-35.0, 0.4), (20.0, -0.3)])
+def test_pam_estimate_matches_oracle_and_clock(ppm, delay):
+    nb = 1 << 18
+    g = make_stream(1, nb, 2, seed=7, isi=(0.0, 1.0, 0.0), **pam_clock(ppm, delay))
+    r = rx.Receiver(1, nb, mf_mode=1)
+    o = oracle.Oracle(**oracle.default_cfg(1, nb, mf_mode=1))
+    for b in range(2):
+        r.process(torch.from_numpy(g["packed"][b]).cuda())
+        o.process(g["packed"][b])
+    gp, gd = rx.rx_clock_estimate(r.h, torch.cuda.current_stream().cuda_stream)
+    c, c0 = o.get(oracle.ORX_CLK)
+    op, od = oracle.clock_fit(c, 512 * (c0 + np.arange(len(c))) + 256, sps=2)
+    assert abs(gp - op) < 0.01 and abs(gd - od) < 1e-3, (gp, op, gd, od)
+    err = (gd - delay + 1.0) % 2.0 - 1.0
+    assert abs(gp - ppm) < 0.5 and abs(err) < 0.05, (gp, gd)
