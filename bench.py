@@ -488,7 +488,7 @@ VOLT = dict(volterra=(0.05, 0.02), cspr_db=6.0, linewidth=0.0, phase_noise=False
 
 def cnn_leg(args, ring):
     """Learned equaliser against the adaptive FIR on the Volterra + SSBI channel
-    (CSPR 6 dB, SNR 16..22 dB): train on 2^24 counter-based symbols, judge BER on a
+    (CSPR 6 dB, SNR 16..22 dB): train on 2^24 counter-based symbols, measure the BER on a
     fresh PRBS stream, and time the CNN receiver on the 2^22-sample buffers."""
     import torch
     import synth
@@ -516,7 +516,7 @@ def cnn_leg(args, ring):
     tr.train(steps // 4, lr=2e-4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    # judge: fresh PRBS stream at 19 dB through both receivers
+    # evaluation: fresh PRBS stream at 19 dB through both receivers
     gev = synth.gen_kk_stream(FMT, nb, 4, seed=777, truth=False, snr_db=19.0,
                               workers=min(16, os.cpu_count() or 1), **VOLT)
     lms, net = rx.Receiver(FMT, nb), rx.Receiver(FMT, nb)
@@ -560,7 +560,7 @@ def cnn_leg(args, ring):
             "bits": sn["bits"], "train_symbols": int(n_train), "train_steps": steps, "batch_symbols": 64 * 64,
             "train_s": t_train,
             "channel": "KK-16QAM, Volterra (0.05, 0.02), CSPR 6 dB, no laser phase noise; train SNR 16/18/20/22 dB "
-                       "(counter-based symbols), judge SNR 19 dB (PRBS-15)"}
+                       "(counter-based symbols), test SNR 19 dB (PRBS-15)"}
 
 
 def precision_leg(args, g, ring):

@@ -1,4 +1,4 @@
-"""Training driver of the learned equaliser (argument marshalling only).
+"""Training loop of the learned equaliser (argument marshalling only).
 
 The gradient, the loss and the Adam update run in librx.so's kernels
 (rx_cnn_grad, rx_cnn_adam_step); this module picks training segments and hands

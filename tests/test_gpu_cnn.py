@@ -79,7 +79,7 @@ VOLT = dict(volterra=(0.05, 0.02), cspr_db=6.0, snr_db=19.0, linewidth=0.0, phas
 
 def test_trained_cnn_beats_the_adaptive_fir():
     """Train on counter-based random symbols through the Volterra + SSBI channel
-    (CSPR 6 dB); judge on a fresh PRBS stream: the CNN must reach a lower BER
+    (CSPR 6 dB); evaluate on a fresh PRBS stream: the CNN must reach a lower BER
     than the 31-tap CMA/DD-LMS FIR with blind phase search on the same buffers."""
     nb = 1 << 20
     ntr = 6
