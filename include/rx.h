@@ -170,7 +170,10 @@ rx_status rx_default_config(rx_format format, rx_config *out);
 
 /* Create a receiver for one stream of buffers of buf_len ADC samples taken at
  * fs samples/s of a signal at baud symbols/s.  fs/baud must be 2 (PAM) or 4
- * (KK).  buf_len must be a positive multiple of 32.  cfg may be NULL (defaults).
+ * (KK).  buf_len must be a positive multiple of 32, at most 2^30; for KK a buffer
+ * may span at most about 131000 overlap-save hops (buf_len / (ols_n - ols_v)), which
+ * the defaults (65536 / 4096) allow for every buf_len up to 2^30.  RX_EINVAL
+ * otherwise, before any CUDA call.  cfg may be NULL (defaults).
  * Allocates all device memory up front (cudaMalloc on the current device) and
  * builds the constant tables; no kernel runs.  On success *out owns the handle. */
 rx_status rx_create(rx_format format, double baud, double fs, int64_t buf_len,

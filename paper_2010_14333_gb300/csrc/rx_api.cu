@@ -395,6 +395,13 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
                c.ds_den < 1 || c.ds_num < 0 || c.amb_syms < 0 || c.amb_syms % kWin || c.amb_syms > 4096 ||
                !(c.ols_n == 4096 || c.ols_n == 65536) || c.ols_v < 64 || c.ols_v % 64 || c.ols_v >= c.ols_n))
         return RX_EINVAL;
+    // size limits: per-call symbol and window counts are 32-bit, and the KK forward
+    // pass has one grid row per overlap-save block pair plus the history copy (<= 65535)
+    if (buf_len > (1LL << 30)) return RX_EINVAL;
+    if (kk) {
+        const long long hop = c.ols_n - c.ols_v, jmax = (buf_len + hop - 1) / hop + 1;
+        if ((jmax + 1) / 2 + 1 > 65535) return RX_EINVAL;
+    }
     rx_handle *h = (rx_handle *)calloc(1, sizeof(rx_handle));
     if (!h) return RX_ENOMEM;
     h->fmt = f;

@@ -51,6 +51,7 @@ def test_default_config_and_strerror():
     (rx.RX_KK_16QAM, 2e9, 4e9, 1 << 20),       # KK needs 4 samples/symbol
     (rx.RX_PAM4, 1e9, 4e9, 1 << 20),           # PAM needs 2 samples/symbol
     (7, 1e9, 4e9, 1 << 20),                    # unknown format
+    (rx.RX_PAM4, 2e9, 4e9, (1 << 30) + 32),    # above 2^30 samples
 ])
 def test_create_rejects_bad_arguments(args):
     lib = rx.load()
@@ -86,6 +87,15 @@ def test_create_rejects_bad_fd_config(kw):
     assert lib.rx_create(rx.RX_PAM4, 2e9, 4e9, 1 << 20, C.byref(p), C.byref(h)) == 1
     p.fd_n, p.fd_taps = 1024, 515
     assert lib.rx_create(rx.RX_PAM4, 2e9, 4e9, 1 << 20, C.byref(p), C.byref(h)) == 1
+
+
+def test_create_rejects_too_many_overlap_save_blocks():
+    """A buffer of more overlap-save blocks than the forward pass's grid holds."""
+    lib = rx.load()
+    h = C.c_void_p()
+    c = rx.rx_default_config(rx.RX_KK_16QAM)
+    c.ols_n, c.ols_v = 4096, 4032            # hop of 64 samples: 2^24 / 64 blocks
+    assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 24, C.byref(c), C.byref(h)) == 1
 
 
 def test_create_rejects_bad_resampler():
