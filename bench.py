@@ -567,35 +567,19 @@ def precision_leg(args, g, ring):
     """Precision forms of the equaliser on the KK-16QAM workload (eq_block 1024):
     the adaptive FP32 chain, the frozen-tap form in FP32, and the block-Toeplitz
     FIR on the tensor cores in BF16 / FP16 / FP8-E4M3.  Throughput over the ring;
-    soft-symbol relative RMS error and BER against the FP64 oracle on the first
-    two buffers of the stream; the tensor-core FIR kernel timed alone."""
+    BER on the first two buffers of the stream (their soft-symbol error and BER
+    against the FP64 oracle are asserted by the parity tests); the tensor-core FIR
+    kernel timed alone."""
     import torch
-    import oracle
     import paper_2010_14333_gb300 as rx
     nref = 2
     forms = [("adaptive_f32", rx.RX_FIR_ADAPTIVE), ("frozen_f32", rx.RX_FIR_FROZEN_F32),
              ("bf16", rx.RX_FIR_BF16), ("fp16", rx.RX_FIR_FP16), ("fp8_e4m3", rx.RX_FIR_FP8)]
-    ref = {}
-    for frozen in (0, 1):
-        o = oracle.Oracle(**oracle.default_cfg(FMT, NB, eq_block=1024, eq_frozen=frozen))
-        zs = []
-        for b in range(nref):
-            o.process(g["packed"][b])
-            zs.append(o.get(oracle.ORX_Z))
-        ref[frozen] = (zs, o.stats())
     res = {}
     for name, prec in forms:
-        zs, so = ref[int(prec != rx.RX_FIR_ADAPTIVE)]
-        d = rx.Receiver(FMT, NB, fir_prec=prec, eq_block=1024, debug=1)
-        num = den = 0.0
+        d = rx.Receiver(FMT, NB, fir_prec=prec, eq_block=1024)
         for b in range(nref):
             d.process(ring[b])
-            z, z0 = d.debug(rx.RX_DBG_SOFT)
-            zo, zo0 = zs[b]
-            if len(z):
-                zo = zo[z0 - zo0: z0 - zo0 + len(z)]
-                num += float(np.sum(np.abs(z - zo) ** 2))
-                den += float(np.sum(np.abs(zo) ** 2))
         sd = d.stats()
         del d
         r = rx.Receiver(FMT, NB, fir_prec=prec, eq_block=1024)
@@ -612,9 +596,7 @@ def precision_leg(args, g, ring):
         rx.rx_profile(r.h, 0)
         res[name] = {"gsa_s": 2 * len(ring) * NB / (e0.elapsed_time(e1) * 1e-3) / 1e9,
                      "eq_us_per_buffer": ms["eq"] / max(calls, 1) * 1e3,
-                     "soft_rel_rms_vs_oracle": (num / den) ** 0.5 if den else None,
-                     "ber": sd["ber"], "ber_oracle": so["ber"], "bits": sd["bits"],
-                     "oracle_form": "frozen" if prec != rx.RX_FIR_ADAPTIVE else "adaptive"}
+                     "ber": sd["ber"], "bits": sd["bits"]}
         del r
     # the tensor-core FIR alone: 2^20 symbols (one buffer's payload), 31 taps
     nsym, nt = 1 << 20, 31
@@ -643,7 +625,7 @@ def precision_leg(args, g, ring):
                       "algorithmic_tflops": 8 * nt * nsym / (us * 1e-6) / 1e12,
                       "tensor_tflops_issued": 2 * 128 * 32 * 128 * (nsym // 2048) / (us * 1e-6) / 1e12}
     return {"eq_block": 1024, "forms": res, "fir_kernel": kern,
-            "sample": f"soft symbols and BER on the first {nref} buffers; throughput over the {len(ring)}-buffer ring x 2"}
+            "sample": f"BER on the first {nref} buffers; throughput over the {len(ring)}-buffer ring x 2"}
 
 
 def fd_leg(args, g, ring):
@@ -651,27 +633,18 @@ def fd_leg(args, g, ring):
     203-tap filter in the frequency domain on 1024-point overlap-save blocks (hop
     512, 8192 blocks per buffer) with a 512-point bin-truncation inverse, in place
     of the 65-tap time-domain matched filter.  Receiver throughput over the ring,
-    the filter stage time, and the 2-sps samples and BER against the FP64 oracle
-    in the same form on the first two buffers."""
+    the filter stage time, and the BER in that form on the first two buffers (its
+    2-sps samples and BER against the FP64 oracle are asserted by the parity
+    tests)."""
     import torch
-    import oracle
     import paper_2010_14333_gb300 as rx
     nref = 2
-    o = oracle.Oracle(**oracle.default_cfg(FMT, NB, mf_mode=1))
-    d = rx.Receiver(FMT, NB, mf_mode=1, debug=1)
-    num = den = 0.0
+    d = rx.Receiver(FMT, NB, mf_mode=1)
     for b in range(nref):
-        o.process(g["packed"][b])
         d.process(ring[b])
-        y, y0 = d.debug(rx.RX_DBG_MF)
-        yo, yo0 = o.get(oracle.ORX_Y)
-        if len(y) and (y0, len(y)) == (yo0, len(yo)):
-            num += float(np.sum(np.abs(y - yo) ** 2))
-            den += float(np.sum(np.abs(yo) ** 2))
-    sd, so = d.stats(), o.stats()
+    sd = d.stats()
     del d
-    out = {"fd_n": 1024, "fd_taps": 203, "y_rel_rms_vs_oracle": (num / den) ** 0.5 if den else None,
-           "ber": sd["ber"], "ber_oracle": so["ber"], "bits": sd["bits"]}
+    out = {"fd_n": 1024, "fd_taps": 203, "ber": sd["ber"], "bits": sd["bits"]}
     for mode in (1, 0):
         r = rx.Receiver(FMT, NB, mf_mode=mode)
         for _ in range(2):
@@ -699,14 +672,13 @@ def resampler_leg(args, ring):
     transmitter's): on two buffers of a stream generated through a -35 ppm ADC clock
     with a 0.4-sample delay, the clock estimated from the first buffer in the
     frequency-domain form, then the BER with the resampler set from the estimate
-    against the FP64 oracle set the same way; throughput over the benchmark ring
-    (the resampler's work does not depend on the data)."""
+    (against the FP64 oracle set the same way in the parity tests) and without it;
+    throughput over the benchmark ring (the resampler's work does not depend on the
+    data)."""
     import torch
-    import oracle
     import synth
     import paper_2010_14333_gb300 as rx
     st, ph = synth.clock_step(-35.0), int(0.4 * (1 << 32))
-    rs_step, rs_phase0 = oracle.rs_params(st, ph)
     t0 = time.perf_counter()
     g = synth.gen_kk_stream(FMT, NB, 2, seed=11, truth=False, clock_step=st, clock_phase0=ph, workers=2, **GEN)
     t_gen = time.perf_counter() - t0
@@ -716,18 +688,15 @@ def resampler_leg(args, ring):
     est.process(torch.from_numpy(g["packed"][0]).cuda())
     e_ppm, e_delay = rx.rx_clock_estimate(est.h, torch.cuda.current_stream().cuda_stream)
     del est
-    rs_step, rs_phase0 = oracle.rs_params(synth.clock_step(e_ppm), int(round(e_delay * (1 << 32))))
-    o = oracle.Oracle(**oracle.default_cfg(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0))
+    rs_step, rs_phase0 = rx.resampler_params(e_ppm, e_delay)
     d = rx.Receiver(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0)
     plain = rx.Receiver(FMT, NB)
     for p in g["packed"]:
-        o.process(p)
         dv = torch.from_numpy(p).cuda()
         d.process(dv)
         plain.process(dv)
     out = {"ppm": -35.0, "delay_samples": 0.4, "estimated_ppm": e_ppm, "estimated_delay_samples": e_delay,
-           "ber": d.stats()["ber"], "ber_oracle": o.stats()["ber"],
-           "ber_without_resampler": plain.stats()["ber"], "gen_s": t_gen}
+           "ber": d.stats()["ber"], "ber_without_resampler": plain.stats()["ber"], "gen_s": t_gen}
     del d, plain
     r = rx.Receiver(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0)
     for _ in range(2):
@@ -749,21 +718,18 @@ def resampler_leg(args, ring):
 
 def pam_fd(args):
     """PAM-4 at 2 GBaud on 2^20-sample buffers: the 503-tap frequency-domain form
-    against the 33-tap time-domain matched filter, with the oracle's BER in the
-    same form on the first two buffers."""
+    against the 33-tap time-domain matched filter, with the BER of the
+    frequency-domain form on the first two buffers."""
     import torch
-    import oracle
     import synth
     import paper_2010_14333_gb300 as rx
     nb, nbufs, fmt = 1 << 20, 32, 1
     g = synth.gen_pam_stream(fmt, nb, nbufs, seed=5)
     ring = [torch.from_numpy(p).cuda() for p in g["packed"]]
-    o = oracle.Oracle(**oracle.default_cfg(fmt, nb, mf_mode=1))
     d = rx.Receiver(fmt, nb, mf_mode=1)
     for b in range(2):
-        o.process(g["packed"][b])
         d.process(ring[b])
-    res = {"buf_len": nb, "fd_taps": 503, "ber": d.stats()["ber"], "ber_oracle": o.stats()["ber"]}
+    res = {"buf_len": nb, "fd_taps": 503, "ber": d.stats()["ber"]}
     del d
     for mode in (1, 0):
         r = rx.Receiver(fmt, nb, mf_mode=mode)
@@ -798,10 +764,8 @@ def sweep_leg(args):
     """Synthetic analogue of the paper's Q-factor versus OSNR curves (Fig. 2a, b):
     every format over five SNR points (in-band Es/N0 of the generator), BER and
     Q = 20 log10(sqrt(2) erfcinv(2 BER)) of the GPU receiver over a few buffers
-    per point, and the FP64 oracle's BER on the same first buffer at the middle
-    point."""
+    per point."""
     import torch
-    import oracle
     import synth
     import paper_2010_14333_gb300 as rx
     nb_per = 4
@@ -821,12 +785,6 @@ def sweep_leg(args):
             pt = {"snr_db": snr, "bits": st["bits"], "ber": st["ber"],
                   "q_db": st["q_db"] if np.isfinite(st["q_db"]) else None,
                   "slip_windows": st["slip_windows"]}
-            if i == len(snrs) // 2:
-                o = oracle.Oracle(**oracle.default_cfg(fmt, nb))
-                chk = rx.Receiver(fmt, nb)
-                o.process(g["packed"][0])
-                chk.process(torch.from_numpy(g["packed"][0]).cuda())
-                pt["first_buffer_ber_gpu"], pt["first_buffer_ber_oracle"] = chk.stats()["ber"], o.stats()["ber"]
             pts.append(pt)
             del r
         res[FMT_NAMES[fmt]] = {"buf_len": nb, "buffers_per_point": nb_per, "points": pts}

@@ -124,6 +124,22 @@ def _check(status: int):
 
 
 # ------------------------------------------------------------- C ABI, 1:1
+def resampler_params(ppm: float, delay: float):
+    """rx_config (rs_step, rs_phase0) for an ADC whose sample period is (1 + 1e-6 ppm)
+    nominal samples and whose sample 0 lies at transmitter time `delay` (nominal
+    samples), e.g. the result of rx_clock_estimate.  The resampler reads nominal
+    sample m at ADC position (rs_phase0 + m rs_step) / 2^32; ADC sample n lies at
+    t_n = delay + n (1 + 1e-6 ppm), so position(m) = (m - delay) / (1 + 1e-6 ppm).
+    Both are rounded to the nearest integer in units of 2^-32 samples (host integer
+    arithmetic; the accumulator itself runs on the device)."""
+    period = int(round((1.0 + ppm * 1e-6) * 4294967296.0))   # ADC period in 2^-32 samples
+    offset = int(round(delay * 4294967296.0))                  # delay in 2^-32 samples
+    half = period // 2
+    rs_step = ((1 << 64) + half) // period
+    rs_phase0 = -((offset * (1 << 32) + half) // period)
+    return rs_step, rs_phase0
+
+
 def rx_clock_estimate(h: int, stream: int = 0):
     """(ppm, delay in ADC samples) of the ADC clock from the last call (FD form, KK or PAM)."""
     ppm, dl = C.c_double(), C.c_double()

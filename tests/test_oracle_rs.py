@@ -97,3 +97,12 @@ def test_rejects_bad_accumulators():
             oracle.Oracle(**oracle.default_cfg(4, 1 << 16, **kw))
     with pytest.raises(ValueError):
         oracle.Oracle(**oracle.default_cfg(1, 1 << 16, rs_step=1 << 32))
+
+
+def test_binding_resampler_params_match_the_oracle():
+    """The product's host helper that turns a clock estimate into the accumulator
+    agrees with the oracle's, which the pins above check against exact positions."""
+    import paper_2010_14333_gb300 as rx
+    for ppm, delay in ((-35.0, 0.4), (20.0, -0.7), (80.0, 1.1), (0.0, 0.0), (-0.3, -1.9)):
+        want = oracle.rs_params(synth.clock_step(ppm), int(round(delay * (1 << 32))))
+        assert rx.resampler_params(ppm, delay) == want, (ppm, delay)
