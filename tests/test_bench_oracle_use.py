@@ -1,0 +1,41 @@
+"""The benchmark may run the oracle in two places only: its reference arm and the
+CPU-baseline leg of the GPU arm (the block under `not args.no_cpu_baseline`).
+Every other leg measures the product alone; GPU-oracle equality is the parity
+tests' job."""
+
+import ast
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _parents(tree):
+    par = {}
+    for node in ast.walk(tree):
+        for child in ast.iter_child_nodes(node):
+            par[child] = node
+    return par
+
+
+def test_oracle_only_in_reference_arm_and_cpu_baseline():
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    par = _parents(tree)
+    uses = []
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Import) and any(a.name == "oracle" for a in node.names):
+            uses.append(node)
+        if isinstance(node, ast.ImportFrom) and node.module and node.module.split(".")[0] == "oracle":
+            uses.append(node)
+    assert uses
+    for node in uses:
+        chain, p = [], par.get(node)
+        while p is not None:
+            chain.append(p)
+            p = par.get(p)
+        funcs = [p.name for p in chain if isinstance(p, ast.FunctionDef)]
+        assert funcs, f"module-level oracle import at line {node.lineno}"
+        if funcs[0] == "reference_arm":
+            continue
+        assert funcs[0] == "gpu_arm", f"oracle imported in {funcs[0]} (line {node.lineno})"
+        guards = [ast.unparse(p.test) for p in chain if isinstance(p, ast.If)]
+        assert any("no_cpu_baseline" in g for g in guards), f"oracle outside the CPU-baseline leg (line {node.lineno})"
