@@ -39,3 +39,22 @@ def test_oracle_only_in_reference_arm_and_cpu_baseline():
         assert funcs[0] == "gpu_arm", f"oracle imported in {funcs[0]} (line {node.lineno})"
         guards = [ast.unparse(p.test) for p in chain if isinstance(p, ast.If)]
         assert any("no_cpu_baseline" in g for g in guards), f"oracle outside the CPU-baseline leg (line {node.lineno})"
+
+
+def test_product_package_never_imports_the_oracle():
+    """Nothing in the package (binding, trainer, build) imports, loads or links the
+    oracle: the product path is the CUDA library or an error."""
+    pkg = os.path.join(ROOT, "paper_2010_14333_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if not fn.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                continue
+            path = os.path.join(dirpath, fn)
+            src = open(path, errors="replace").read()
+            if fn.endswith(".py"):
+                for node in ast.walk(ast.parse(src)):
+                    if isinstance(node, ast.Import):
+                        assert not any(a.name.split(".")[0] == "oracle" for a in node.names), path
+                    if isinstance(node, ast.ImportFrom):
+                        assert not (node.module or "").startswith("oracle"), path
+            assert "rx_oracle" not in src and "liborx" not in src, path
