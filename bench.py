@@ -688,7 +688,7 @@ def resampler_leg(args, ring):
     est.process(torch.from_numpy(g["packed"][0]).cuda())
     e_ppm, e_delay = rx.rx_clock_estimate(est.h, torch.cuda.current_stream().cuda_stream)
     del est
-    rs_step, rs_phase0 = rx.resampler_params(e_ppm, e_delay)
+    rs_step, rs_phase0 = rx.rx_resampler_from_clock(e_ppm, e_delay)
     d = rx.Receiver(FMT, NB, rs_step=rs_step, rs_phase0=rs_phase0)
     plain = rx.Receiver(FMT, NB)
     for p in g["packed"]:

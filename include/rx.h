@@ -113,6 +113,12 @@ typedef struct {
     int32_t cnn_bf16;    /* receiver CNN (rx_set_cnn) operands: 1 = BF16 (default), 0 =
                             FP16; FP32 accumulation, bias and GELU in the same packed type */
     int32_t pad_cnn;     /* reserved, 0                                                    */
+    double  deadline_ms; /* per-buffer latency budget for rx_stats (Sec. 2: a buffer
+                            must be processed before the stream that takes it is needed
+                            again; with five streams that is five buffer durations, 5.243
+                            ms for 2^22 samples at 4 GS/s).  0 = five buffer durations
+                            (buf_len / fs each); > 0 = this budget in ms; < 0 = no latency
+                            record (no events are recorded per call)                       */
 } rx_config;
 
 /* Reduction to 2 samples/symbol of the KK chain (rx_config.mf_mode). */
@@ -146,6 +152,18 @@ typedef struct {
     int32_t device_error;      /* 0, or RX_ETIMEOUT if a device-side wait ran out         */
     double  ber;               /* bit_errors / bits                                       */
     double  q_db;              /* 20 log10(sqrt(2) erfcinv(2 BER)), Sec. 3 Q-factor       */
+    /* Per-buffer latency (cfg.deadline_ms >= 0): device time from the start of a
+     * call's first stage (the host->device copy for the host-buffer entry points)
+     * to the end of its last one (its bits in memory), taken with CUDA events on
+     * the streams that run those stages.  Calls inside a group round and flush
+     * calls are not recorded.  Percentiles come from a histogram of 0.5 us bins
+     * up to 32.768 ms (a latency above that counts in the top bin). */
+    int64_t lat_calls;         /* calls whose latency was recorded                       */
+    int64_t deadline_misses;   /* recorded calls whose latency exceeded deadline_ms      */
+    double  deadline_ms;       /* the budget in force (0 when no record is kept)         */
+    double  lat_p50_ms;        /* median latency (centre of its 0.5 us bin)               */
+    double  lat_p99_ms;        /* 99th percentile                                         */
+    double  lat_max_ms;        /* largest recorded latency (exact)                        */
 } rx_stats_t;
 
 /* Debug selectors for rx_debug_copy (each refers to the last rx_process call). */
@@ -224,8 +242,39 @@ rx_status rx_process_host(rx_handle *h, const uint8_t *host_in, uint8_t *host_bi
 rx_status rx_process_host_batch(rx_handle *h, const uint8_t *const *host_ins, uint8_t *const *host_outs, int n,
                                 void *cuda_stream, int64_t *nbits_out);
 
-/* Upper bound of the bits one rx_process call can emit. */
+/* Upper bound of the bits one rx_process or rx_flush call can emit. */
 int64_t rx_max_bits(const rx_handle *h);
+
+/* End of the stream: emit the payload symbols the last buffers still hold back.
+ * Every stage of the chain lags the input (the KK overlap-save margin, the filter
+ * and equaliser supports, whole equaliser blocks), so after the last rx_process
+ * the symbols of the stream's final few thousand samples have not been decided.
+ * rx_flush pads the stream after its last sample with that sample's code
+ * repeated (the mirror of the stream start, where the first sample is
+ * replicated) and runs the chain until every symbol whose centre lies inside the
+ * stream has been decided.  The pad buffers reuse the per-call carrier and gain
+ * (KK) or mean and standard deviation (PAM) of the last real buffer.
+ *   bits_out:  DEVICE pointer with room for rx_max_bits(h)/8 bytes; receives the
+ *              bits of payload symbols [first undecided, last in the stream].
+ *   nbits_out: HOST pointer, the number of bits written (computed on the host).
+ * Windows whose last symbol lies within ceil((mf_span + ntaps) / 2) symbols of
+ * the stream end are decided but not scored in rx_stats (their filter supports
+ * reach into the pad).  Enqueued on cuda_stream, which must be the stream (or
+ * follow the stream) of the last rx_process call.  After rx_flush the handle
+ * accepts no more buffers (RX_ESTATE); a second rx_flush emits nothing. */
+rx_status rx_flush(rx_handle *h, uint8_t *bits_out, void *cuda_stream, int64_t *nbits_out);
+
+/* Resampler accumulator for a measured ADC clock (rx_clock_estimate's result):
+ * ADC sample n lies at transmitter time delay + n (1 + 1e-6 ppm) nominal samples
+ * (Sec. 2: the ADC runs on its own clock and the DSP recovers the clock phase).
+ * The resampler reads nominal sample m at ADC position (rs_phase0 + m rs_step) /
+ * 2^32 = (m - delay) / (1 + 1e-6 ppm).  With the ADC period P = round((1 + 1e-6
+ * ppm) 2^32) and the delay D = round(delay 2^32), both in units of 2^-32 samples
+ * and rounded to nearest (ties to even) from the double product:
+ * rs_step = floor((2^64 + floor(P/2)) / P) and rs_phase0 = -floor((D 2^32 +
+ * floor(P/2)) / P), in exact 128-bit integer arithmetic.  RX_EINVAL unless
+ * |ppm| < 9000 and |delay| < 2^30 (rx_create accepts rs_step within 1 % of 2^32). */
+rx_status rx_resampler_from_clock(double ppm, double delay, int64_t *rs_step, int64_t *rs_phase0);
 
 /* Synchronises cuda_stream, then copies the accumulated counters. */
 rx_status rx_stats(rx_handle *h, rx_stats_t *out, void *cuda_stream);
@@ -309,23 +358,28 @@ rx_status rx_group_destroy(rx_group *g);
  * ln(I)/2 and E = sqrt(I) exp(j phi), for stream samples [0, nsamp - ols_v/2).
  *
  *   packed12_in: DEVICE pointer, nsamp*3/2 bytes, 16-byte aligned.
- *   nsamp:       multiple of 32, at most 524288 (2^19) samples.
+ *   nsamp:       multiple of 32, at most 524288 (2^19) samples, and the overlap-save
+ *                blocks must fit the FFT rows: ceil(J/2) * ols_n <= 2^19 complex
+ *                values with J = ceil((nsamp - ols_v/2) / (ols_n - ols_v)) blocks
+ *                (at ols_n = 65536 and nsamp = 2^19 that allows ols_v up to 4096).
  *   ols_n/ols_v: as in rx_config (4096 or 65536; overlap a multiple of 64, < ols_n).
  *   field_out:   DEVICE pointer, 8-byte aligned, room for 2*(nsamp - ols_v/2)
  *                floats (interleaved real, imaginary).
  *
- * The scratch (twiddle tables, codes, FFT rows, field, reduction partials) is
- * one fixed device array of about 10 MiB in librx.so; every GPU that loads the
- * library holds it until the process exits.  Sizes beyond the limit return
- * RX_EINVAL before anything is enqueued.  The call allocates nothing (no
- * cudaMalloc, cudaFree or allocating library routine); it enqueues its kernels
- * on cuda_stream and returns.  The first call on a device does a one-time
- * set-up with that device current: it looks up the array's device address and
- * uploads the twiddle tables with a synchronous copy, so make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * last call's contents, so calls that overlap on the GPU (on different streams
- * or from different threads) race and corrupt each other's results; issue them
- * in order on one stream.  Returns RX_ECUDA when the set-up or a launch fails. */
+ * The scratch (twiddle and ln tables, a packed-history region, FFT rows, field,
+ * reduction partials) is one fixed device array of about 8.2 MiB in librx.so;
+ * every GPU that loads the library holds it until the process exits.  Sizes
+ * beyond the limits return RX_EINVAL before anything is enqueued.  The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine); it
+ * enqueues its kernels on cuda_stream and returns.  The first call on a device
+ * does a one-time set-up with that device current: it looks up the array's
+ * device address and copies the tables on cuda_stream, then synchronises that
+ * stream, so make that first call before any stream capture.  Host threads that
+ * make their first calls at the same time do the set-up once (it is serialised).
+ * All calls share the one array and it keeps the last call's contents, so calls
+ * that overlap on the GPU (on different streams or from different threads) race
+ * and corrupt each other's results; issue them in order on one stream.  Returns
+ * RX_ECUDA when the set-up or a launch fails. */
 rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsamp, int32_t pack_order,
                               int32_t ols_n, int32_t ols_v, float *field_out, void *cuda_stream);
 

@@ -94,6 +94,8 @@ def lib():
         L.orx_create.restype = C.c_void_p
         L.orx_process.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
         L.orx_process.restype = C.c_int64
+        L.orx_flush.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+        L.orx_flush.restype = C.c_int64
         L.orx_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, P(C.c_int64)]
         L.orx_get.restype = C.c_int64
         L.orx_set_taps.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
@@ -312,6 +314,14 @@ class Oracle:
         cap = self.bps * (c["buf_len"] // c["sps"] + c["eq_block"] + c["ntrain"] + 64)
         out = np.zeros((cap + 7) // 8, dtype=np.uint8)
         nbits = lib().orx_process(self._h, _ptr(packed), _ptr(out), cap)
+        return out[: (nbits + 7) // 8].copy(), int(nbits)
+
+    def flush(self):
+        """End of the stream: (bits, nbits) of the symbols still held back."""
+        c = self.cfg
+        cap = self.bps * (2 * c["buf_len"] + 4 * c["eq_block"] + c["ntrain"] + 2 * c.get("ols_n", 0) + 8192)
+        out = np.zeros((cap + 7) // 8, dtype=np.uint8)
+        nbits = lib().orx_flush(self._h, _ptr(out), cap)
         return out[: (nbits + 7) // 8].copy(), int(nbits)
 
     def get(self, what: int):

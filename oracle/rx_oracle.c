@@ -342,6 +342,9 @@ struct orx {
     int64_t calls, e_prev, f_prev, q_prev;
     int32_t *chist; int64_t chist_len, chist_cap;
     int have_first; int32_t first_code;
+    int flushed;                   /* the stream has ended (orx_flush) */
+    int64_t pad_calls;             /* pad buffers run by orx_flush (not counted as input) */
+    double last_mu, last_sd;       /* PAM: normalisation of the last real buffer */
     cx *ehist; int64_t ehist_start, ehist_len;
     cx *yhist; int64_t yhist_start, yhist_len;
     cx carrier; double gain;
@@ -608,7 +611,12 @@ static void put_bit(uint8_t *out, int64_t t, int bit)
     if (bit) out[t >> 3] |= (uint8_t)(0x80u >> (t & 7));
 }
 
-int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bits_cap)
+/* One buffer through the chain.  `flush` marks a pad buffer of the stream end
+ * (orx_flush): the carrier and gain (KK) or mean and deviation (PAM) stay those
+ * of the last real buffer, and windows reaching symbol score_end are decided but
+ * not scored. */
+static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bits_cap, int flush,
+                              int64_t score_end)
 {
     const orx_cfg *c = &h->c;
     int64_t Nb = c->buf_len;
@@ -668,9 +676,11 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
             sumE = cx_add(sumE, X.E[n - X.E_start]);
             sumI += kk_intensity(code_at(&X, n));
         }
-        h->carrier = cx_scale(sumE, 1.0 / (double)X.E_len);
-        double P = sumI / (double)X.E_len - cx_abs2(h->carrier);
-        h->gain = (P > 0.0) ? 1.0 / sqrt((double)c->sps * P) : 1.0;
+        if (!flush) {
+            h->carrier = cx_scale(sumE, 1.0 / (double)X.E_len);
+            double P = sumI / (double)X.E_len - cx_abs2(h->carrier);
+            h->gain = (P > 0.0) ? 1.0 / sqrt((double)c->sps * P) : 1.0;
+        }
     }
     X.R_start = h->r_prev; X.R_len = h->rs ? r_k - h->r_prev : 0;
     X.R = xcalloc((size_t)(X.R_len > 0 ? X.R_len : 1), sizeof(cx));
@@ -691,6 +701,8 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
         X.mu_pam = s1 / (double)Nb;
         double var = s2 / (double)Nb - X.mu_pam * X.mu_pam;
         X.sd_pam = (var > 0.0) ? sqrt(var) : 1.0;
+        if (flush) { X.mu_pam = h->last_mu; X.sd_pam = h->last_sd; }
+        h->last_mu = X.mu_pam; h->last_sd = X.sd_pam;
     }
 
     /* ---- matched filter (and 4 -> 2 samples/symbol for KK) ------------- */
@@ -898,6 +910,7 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
     for (int64_t wi = 0; wi < nwin; wi++) {
         int64_t k0 = pay_lo + wi * W;
         if (h->kk && k0 < c->ntrain + c->amb_syms) continue;
+        if (k0 + W > score_end) continue;   /* stream end: filter supports reach into the pad */
         int nrot = h->kk ? 4 : 1;
         int64_t errs[4] = {0, 0, 0, 0};
         for (int rho = 0; rho < nrot; rho++) {
@@ -990,9 +1003,73 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
     }
     h->e_prev = e_k; h->f_prev = f_k; h->q_prev = q_k; h->r_prev = r_k;
     h->calls++;
-    h->n_samples += Nb;
+    if (!flush) h->n_samples += Nb;
     free(cur);
     return nbits;
+}
+
+int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bits_cap)
+{
+    if (h->flushed) return -1;
+    return process_buffer(h, packed, bits_out, bits_cap, 0, INT64_MAX);
+}
+
+/* End of the stream.  Every step emits only what its full support allows, so the
+ * symbols of the last few thousand samples are still undecided after the last
+ * buffer.  The stream is continued after its last sample with that sample's
+ * code repeated (the mirror of the stream start, where the first sample is
+ * replicated; reading), buffer by buffer, until every symbol whose centre lies
+ * inside the stream (nominal sample k sps < the stream's nominal length) has been
+ * decided.  Returns the bits of payload symbols [first undecided, last in the
+ * stream]; windows whose last symbol lies within ceil((mf_span + ntaps) / 2)
+ * symbols of the end are not scored. */
+int64_t orx_flush(orx *h, uint8_t *bits_out, int64_t bits_cap)
+{
+    const orx_cfg *c = &h->c;
+    if (bits_out && bits_cap > 0) memset(bits_out, 0, (size_t)((bits_cap + 7) / 8));
+    if (h->flushed) return 0;
+    h->flushed = 1;
+    if (h->calls == 0) return 0;
+    int64_t total = h->calls * c->buf_len, r_end = total;
+    if (h->rs) {
+        __int128 lim = ((__int128)total << 32) - (__int128)c->rs_phase0;
+        r_end = lim <= 0 ? 0 : (int64_t)((lim + c->rs_step - 1) / c->rs_step);
+    }
+    int64_t S = r_end > 0 ? (r_end - 1) / c->sps + 1 : 0;
+    int64_t first = h->q_prev > c->ntrain ? h->q_prev : c->ntrain;
+    if (S <= first) return 0;
+    int32_t last = h->chist[h->chist_len - 1];
+    int64_t nbytes = c->buf_len * 3 / 2;
+    uint8_t *pad = xcalloc((size_t)nbytes, 1);
+    for (int64_t i = 0; i < nbytes; i += 3) {   /* the pair (last, last) in the ADC word order */
+        if (c->pack_order == 0) {
+            pad[i] = (uint8_t)(last & 0xFF);
+            pad[i + 1] = (uint8_t)(((last >> 8) & 0xF) | ((last & 0xF) << 4));
+            pad[i + 2] = (uint8_t)(last >> 4);
+        } else {
+            pad[i] = (uint8_t)(last >> 4);
+            pad[i + 1] = (uint8_t)(((last & 0xF) << 4) | ((last >> 8) & 0xF));
+            pad[i + 2] = (uint8_t)(last & 0xFF);
+        }
+    }
+    int64_t cap = (int64_t)h->bps * (c->buf_len + 8 * c->eq_block + c->ntrain + 65536);
+    uint8_t *tmp = xcalloc((size_t)(cap / 8 + 1), 1);
+    int64_t done = 0, score_end = S - (c->mf_span + c->ntaps + 1) / 2;
+    while (h->q_prev < S) {
+        int64_t q0 = h->q_prev;
+        int trained = h->trained;
+        int64_t nb = process_buffer(h, pad, tmp, cap, 1, score_end);
+        h->pad_calls++;
+        int64_t pay_lo = trained ? q0 : c->ntrain;
+        int64_t hi = h->q_prev < S ? h->q_prev : S;
+        for (int64_t t = 0; nb > 0 && t < (int64_t)h->bps * (hi - pay_lo); t++) {
+            int bit = (tmp[t >> 3] >> (7 - (t & 7))) & 1;
+            if (bits_out && done < bits_cap) put_bit(bits_out, done, bit);
+            done++;
+        }
+    }
+    free(pad); free(tmp);
+    return done;
 }
 
 int64_t orx_get(orx *h, int what, void *dst, int64_t cap, int64_t *start)
@@ -1023,7 +1100,7 @@ int64_t orx_get(orx *h, int what, void *dst, int64_t cap, int64_t *start)
 void orx_stats(orx *h, orx_stats_t *o)
 {
     memset(o, 0, sizeof *o);
-    o->calls = h->calls; o->samples = h->n_samples; o->symbols = h->n_symbols;
+    o->calls = h->calls - h->pad_calls; o->samples = h->n_samples; o->symbols = h->n_symbols;
     o->bits = h->n_bits; o->bit_errors = h->n_bit_err; o->sym_errors = h->n_sym_err;
     o->near_threshold = h->n_near; o->ambiguous_windows = h->n_amb; o->windows = h->n_win;
     o->amb_rot = h->amb_r;

@@ -102,6 +102,9 @@ double  orx_cnn_loss_grad(const double *prm, const double *x, const double *tgt,
 /* streaming receiver */
 orx    *orx_create(const orx_cfg *cfg);
 int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bits_cap);
+/* end of the stream: decide the held-back symbols; returns the bits written, and
+ * orx_process returns -1 afterwards */
+int64_t orx_flush(orx *h, uint8_t *bits_out, int64_t bits_cap);
 int64_t orx_get(orx *h, int what, void *dst, int64_t cap, int64_t *start);
 void    orx_set_taps(orx *h, const double *re, const double *im, int n);
 void    orx_stats(orx *h, orx_stats_t *out);

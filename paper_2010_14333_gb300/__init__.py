@@ -34,7 +34,7 @@ class RxConfig(C.Structure):
         ("debug", C.c_int32), ("fir_prec", C.c_int32), ("kk_front", C.c_int32), ("eq_warps", C.c_int32),
         ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
         ("pad_rs", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
-        ("cnn_bf16", C.c_int32), ("pad_cnn", C.c_int32),
+        ("cnn_bf16", C.c_int32), ("pad_cnn", C.c_int32), ("deadline_ms", C.c_double),
     ]
 
 
@@ -45,6 +45,8 @@ class RxStats(C.Structure):
         ("sym_errors", C.c_int64), ("slip_windows", C.c_int64), ("near_threshold", C.c_int64),
         ("ambiguous_windows", C.c_int64), ("windows", C.c_int64), ("amb_rot", C.c_int32),
         ("device_error", C.c_int32), ("ber", C.c_double), ("q_db", C.c_double),
+        ("lat_calls", C.c_int64), ("deadline_misses", C.c_int64), ("deadline_ms", C.c_double),
+        ("lat_p50_ms", C.c_double), ("lat_p99_ms", C.c_double), ("lat_max_ms", C.c_double),
     ]
 
 
@@ -58,7 +60,7 @@ EXPORTED = sorted(["rx_selftest_wait_timeout", "rx_clock_estimate", "rx_default_
                    "rx_cnn_set_params", "rx_cnn_get_params", "rx_cnn_forward", "rx_cnn_grad",
                    "rx_cnn_adam_step", "rx_cnn_destroy", "rx_set_cnn", "rx_process_batch",
                    "rx_process_host_batch", "rx_fir_block", "rx_group_create", "rx_group_process",
-                   "rx_group_tuning", "rx_group_destroy"])
+                   "rx_group_tuning", "rx_group_destroy", "rx_flush", "rx_resampler_from_clock"])
 RX_GROUP_GRAPH, RX_GROUP_TUNE = 1, 2
 RX_MF_TIME, RX_MF_FD = 0, 1
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
@@ -82,6 +84,8 @@ def load(path: str = LIB_PATH):
     L.rx_create.argtypes = [C.c_int, C.c_double, C.c_double, i64, P(RxConfig), P(vp)]
     L.rx_process.argtypes = [vp, vp, vp, vp, P(i64)]
     L.rx_process_host.argtypes = [vp, vp, vp, vp, P(i64)]
+    L.rx_flush.argtypes = [vp, vp, vp, P(i64)]
+    L.rx_resampler_from_clock.argtypes = [C.c_double, C.c_double, P(i64), P(i64)]
     L.rx_process_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.rx_process_host_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.rx_fir_block.argtypes = [vp, i64, vp, C.c_int, C.c_int, i64, C.c_int, vp, vp, vp]
@@ -124,20 +128,19 @@ def _check(status: int):
 
 
 # ------------------------------------------------------------- C ABI, 1:1
-def resampler_params(ppm: float, delay: float):
-    """rx_config (rs_step, rs_phase0) for an ADC whose sample period is (1 + 1e-6 ppm)
-    nominal samples and whose sample 0 lies at transmitter time `delay` (nominal
-    samples), e.g. the result of rx_clock_estimate.  The resampler reads nominal
-    sample m at ADC position (rs_phase0 + m rs_step) / 2^32; ADC sample n lies at
-    t_n = delay + n (1 + 1e-6 ppm), so position(m) = (m - delay) / (1 + 1e-6 ppm).
-    Both are rounded to the nearest integer in units of 2^-32 samples (host integer
-    arithmetic; the accumulator itself runs on the device)."""
-    period = int(round((1.0 + ppm * 1e-6) * 4294967296.0))   # ADC period in 2^-32 samples
-    offset = int(round(delay * 4294967296.0))                  # delay in 2^-32 samples
-    half = period // 2
-    rs_step = ((1 << 64) + half) // period
-    rs_phase0 = -((offset * (1 << 32) + half) // period)
-    return rs_step, rs_phase0
+def rx_resampler_from_clock(ppm: float, delay: float):
+    """(rs_step, rs_phase0) of the resampler for a measured ADC clock (see include/rx.h)."""
+    st, ph = C.c_int64(), C.c_int64()
+    _check(load().rx_resampler_from_clock(ppm, delay, C.byref(st), C.byref(ph)))
+    return st.value, ph.value
+
+
+
+def rx_flush(h: int, bits_out: int, stream: int = 0) -> int:
+    """Emit the payload the stream still holds back (device pointer); returns the bit count."""
+    n = C.c_int64()
+    _check(load().rx_flush(h, bits_out, stream, C.byref(n)))
+    return n.value
 
 
 def rx_clock_estimate(h: int, stream: int = 0):
@@ -374,6 +377,11 @@ class Receiver:
         n = rx_process_batch(self.h, [p.data_ptr() for p in packed_list], [o.data_ptr() for o in outs],
                              self.stream())
         return [(o[: (k + 7) // 8], k) for o, k in zip(outs, n)]
+
+    def flush(self):
+        """End of the stream: (bits tensor on the device, number of bits) of the held-back payload."""
+        n = rx_flush(self.h, self.bits.data_ptr(), self.stream())
+        return self.bits[: (n + 7) // 8], n
 
     def stats(self) -> dict:
         return rx_stats(self.h, self.stream())

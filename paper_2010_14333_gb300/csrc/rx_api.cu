@@ -98,7 +98,68 @@ struct rx_handle {
     long long prof_head, prof_tail;
     double prof_ms[8];
     long long prof_calls;
+    // per-buffer latency record (events on the streams of a call's first and last stage)
+    double lat_budget;         // ms; 0 = no record
+    cudaEvent_t *lat_ev;       // kLatRing pairs (start, end)
+    long long lat_head, lat_tail;
+    uint32_t *lat_hist;        // kLatBins bins of kLatBin ms
+    long long lat_n, lat_miss;
+    double lat_max;
+    int in_group;              // the call is part of a group round (not recorded)
+    // end of stream (rx_flush)
+    int flushed;               // rx_flush ran: no more buffers
+    int flush_mode;            // the call being enqueued is a pad call of rx_flush
+    int flush_par;             // PAM: parity of the last real call (its mean and deviation)
+    long long flush_score_end; // windows reaching this symbol are not scored
+    long long flush_bits;      // bound of the bits rx_flush emits
+    long long pad_calls;       // pad calls run by rx_flush (not counted as input)
 };
+
+static const int kLatRing = 128;
+static const int kLatBins = 65536;
+static const double kLatBin = 0.0005;   // ms
+
+static void lat_take(rx_handle *h)
+{
+    cudaEvent_t *ev = h->lat_ev + 2 * (h->lat_tail % kLatRing);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess && ms >= 0.f) {
+        long long b = (long long)(ms / kLatBin);
+        if (b >= kLatBins) b = kLatBins - 1;
+        h->lat_hist[b]++;
+        h->lat_n++;
+        if (ms > h->lat_budget) h->lat_miss++;
+        if (ms > h->lat_max) h->lat_max = ms;
+    }
+    cudaGetLastError();
+    h->lat_tail++;
+}
+// collect the recorded calls that have finished (all of them when `block`)
+static void lat_harvest(rx_handle *h, bool block)
+{
+    while (h->lat_tail < h->lat_head) {
+        cudaEvent_t end = h->lat_ev[2 * (h->lat_tail % kLatRing) + 1];
+        if (block) {
+            cudaEventSynchronize(end);
+        } else if (cudaEventQuery(end) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        lat_take(h);
+    }
+}
+// percentile p of the recorded latencies (centre of its bin), 0 without records
+static double lat_pct(const rx_handle *h, double p)
+{
+    if (h->lat_n <= 0) return 0.0;
+    long long want = (long long)ceil(p * (double)h->lat_n), acc = 0;
+    if (want < 1) want = 1;
+    for (int b = 0; b < kLatBins; b++) {
+        acc += h->lat_hist[b];
+        if (acc >= want) return ((double)b + 0.5) * kLatBin;
+    }
+    return h->lat_max;
+}
 
 static const int kProfRing = 1024;
 static const int kStages = 7;        // unpack, kk_fwd, kk_rows, kk_inv, mf, eq, demap
@@ -226,6 +287,32 @@ static Sched schedule(const rx_handle *h, long long calls, long long q_prev)
     return s;
 }
 
+// Pad buffer of rx_flush: the stream's last 12-bit code repeated, packed two per
+// three bytes in the handle's order.  The code is read from the packed history of
+// the last call (KK: its last pair) or from the last unpacked code (PAM).
+__global__ void k_pad_fill(uint8_t *dst, long long nbytes, const uint8_t *hist_end, const uint16_t *code, int order)
+{
+    uint32_t c;
+    if (hist_end) {
+        uint32_t b0 = hist_end[-3], b1 = hist_end[-2], b2 = hist_end[-1];
+        c = order == 0 ? (b1 >> 4) | (b2 << 4) : ((b1 & 0xFu) << 8) | b2;   // second sample of the pair
+    } else {
+        c = *code;
+    }
+    uint8_t pat[3];
+    if (order == 0) {   // s0 = b0 | (b1 & 15) << 8, s1 = b1 >> 4 | b2 << 4
+        pat[0] = (uint8_t)(c & 0xFF);
+        pat[1] = (uint8_t)((c >> 8) | ((c & 0xF) << 4));
+        pat[2] = (uint8_t)(c >> 4);
+    } else {            // s0 = b0 << 4 | b1 >> 4, s1 = (b1 & 15) << 8 | b2
+        pat[0] = (uint8_t)(c >> 4);
+        pat[1] = (uint8_t)(((c & 0xF) << 4) | (c >> 8));
+        pat[2] = (uint8_t)(c & 0xFF);
+    }
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nbytes; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = pat[i % 3];
+}
+
 // self-test of the bounded waits: a phase that nothing completes
 __global__ void k_selftest_wait(int *status)
 {
@@ -303,7 +390,8 @@ rx_status rx_default_config(rx_format f, rx_config *c)
 int64_t rx_max_bits(const rx_handle *h)
 {
     if (!h) return 0;
-    return (long long)h->bps * (h->nb / h->sps + h->cfg.eq_block + h->cfg.ntrain + 64);
+    long long call = (long long)h->bps * (h->nb / h->sps + h->cfg.eq_block + h->cfg.ntrain + 64);
+    return call > h->flush_bits ? call : h->flush_bits;
 }
 
 void rx_destroy(rx_handle *h)
@@ -334,6 +422,12 @@ void rx_destroy(rx_handle *h)
         for (int i = 0; i < kProfRing * kEvPerCall; i++) cudaEventDestroy(h->prof_ev[i]);
         free(h->prof_ev);
     }
+    if (h->lat_ev) {
+        for (int i = 0; i < 2 * kLatRing; i++)
+            if (h->lat_ev[i]) cudaEventDestroy(h->lat_ev[i]);
+        free(h->lat_ev);
+    }
+    free(h->lat_hist);
     if (h->front) cudaStreamDestroy(h->front);
     if (h->front2) cudaStreamDestroy(h->front2);
     if (h->mid) cudaStreamDestroy(h->mid);
@@ -385,7 +479,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     if (c.kk_front < 0 || c.kk_front > 1 || !(c.eq_warps == 0 || c.eq_warps == 2 || c.eq_warps == 4 || c.eq_warps == 8))
         return RX_EINVAL;
     if (c.rs_step != 0 && (!kk || c.rs_step < 4252017623LL || c.rs_step > 4337916969LL)) return RX_EINVAL;
-    if (c.cnn_bf16 < 0 || c.cnn_bf16 > 1) return RX_EINVAL;
+    if (c.cnn_bf16 < 0 || c.cnn_bf16 > 1 || !(c.deadline_ms == c.deadline_ms)) return RX_EINVAL;
     if (c.mf_mode < RX_MF_TIME || c.mf_mode > RX_MF_FD ||
         (c.mf_mode == RX_MF_FD && (c.fd_n < 16 || c.fd_n > kEHist || (c.fd_n & (c.fd_n - 1)) ||
                                    (!kk && c.fd_n != 1024) || c.fd_taps < 1 || !(c.fd_taps & 1) ||
@@ -464,6 +558,23 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         }
     }
 
+    // bound of the payload symbols rx_flush emits: the largest lag of the schedule
+    // (symbols of the stream not yet decided after a call), over enough calls to
+    // pass training and reach the steady state
+    {
+        long long qp = 0, lag = 0;
+        long long span = (long long)c.ntrain * sps + (kk ? c.ols_n : 0) + (long long)c.eq_block * sps + 8192;
+        long long ncalls = 64 + 8 * span / buf_len;
+        if (ncalls > 200000) ncalls = 200000;
+        for (long long k = 0; k < ncalls; k++) {
+            Sched s = schedule(h, k, qp);
+            long long l = (k + 1) * buf_len / sps - s.q_k;
+            if (l > lag) lag = l;
+            qp = s.q_k;
+        }
+        if (h->rs) lag += buf_len / 50 / sps + 16;   // nominal grid within 1 % of the ADC's
+        h->flush_bits = (long long)h->bps * (lag + 64);
+    }
     long long nb = buf_len;
     long long symcap = nb / sps + 2LL * c.eq_block + c.ntrain + 256;
     h->dec_cap = symcap;
@@ -642,6 +753,18 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
             return RX_ECUDA;
         }
     }
+    if (c.deadline_ms >= 0) {
+        h->lat_budget = c.deadline_ms > 0 ? c.deadline_ms : 5.0 * (double)buf_len / fs * 1e3;
+        h->lat_ev = (cudaEvent_t *)calloc(2 * kLatRing, sizeof(cudaEvent_t));
+        h->lat_hist = (uint32_t *)calloc(kLatBins, sizeof(uint32_t));
+        bool ok = h->lat_ev && h->lat_hist;
+        for (int i = 0; i < 2 * kLatRing && ok; i++) ok = cudaEventCreate(&h->lat_ev[i]) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            rx_destroy(h);
+            return RX_ECUDA;
+        }
+    }
     {
         int dev = 0;
         bool ok = cudaGetDevice(&dev) == cudaSuccess &&
@@ -669,10 +792,6 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
                               uint8_t *host_out, cudaStream_t sf, cudaStream_t sb, cudaStream_t sc,
                               int64_t *nbits_out, cudaStream_t smid = nullptr, cudaStream_t stail = nullptr)
 {
-    // the launchers detect failures with cudaGetLastError: clear an error some
-    // earlier, unrelated call left behind (a sticky one makes the launches fail)
-    cudaError_t stale = cudaGetLastError();
-    if (stale != cudaSuccess) traced(stale, "an earlier CUDA call (cleared)");
     const rx_config &c = h->cfg;
     Sched s = schedule(h, h->calls, h->q_prev);
     long long base = h->calls * h->nb;
@@ -681,6 +800,22 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     long long pay_lo = do_train ? c.ntrain : h->q_prev;
     long long npay = (h->trained || do_train) ? s.q_k - pay_lo : 0;
     if (npay > 0 && !bits_out && !host_out) return RX_EINVAL;
+    // latency record of calls that emit payload (not inside group rounds or flushes);
+    // finished records are collected first, without waiting unless the ring is full
+    const bool lat = h->lat_ev && !h->in_group && !h->flush_mode && npay >= c.eq_block;
+    cudaEvent_t *lat_ev = nullptr;
+    if (lat) {
+        lat_harvest(h, false);
+        if (h->lat_head - h->lat_tail >= kLatRing) {
+            cudaEventSynchronize(h->lat_ev[2 * (h->lat_tail % kLatRing) + 1]);
+            lat_take(h);
+        }
+        lat_ev = h->lat_ev + 2 * (h->lat_head % kLatRing);
+    }
+    // the launchers detect failures with cudaGetLastError: clear an error some
+    // earlier, unrelated call left behind (a sticky one makes the launches fail)
+    cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess) traced(stale, "an earlier CUDA call (cleared)");
     const bool two = sf != sb;
     // KK in the pipeline: the matched filter runs on a third stream between the
     // field (front) and the equaliser (back); field slots wait for it to be done
@@ -698,9 +833,11 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     const bool alt = three && h->front2 && !h->cnn;
     if (alt && par) sf = h->front2;
     const KkSync ksync = {alt ? h->ev_hist : nullptr, alt ? h->ev_hist : nullptr, alt ? h->ev_front : nullptr};
+    if (lat_ev && !host_in) cudaEventRecord(lat_ev[0], sf);
     if (host_in) {
         in = h->in_stage[par];
         if (sc != sf) cudaStreamWaitEvent(sc, h->ev_infree[par], 0);   // the front end two calls back is done
+        if (lat_ev) cudaEventRecord(lat_ev[0], sc);
         e = cudaMemcpyAsync(h->in_stage[par], host_in, (size_t)(h->nb * 3 / 2), cudaMemcpyHostToDevice, sc);
         if (sc != sf) {
             cudaEventRecord(h->ev_inready[par], sc);
@@ -716,9 +853,11 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     if (!h->kk || c.debug) {
         prof_begin(h, 0, sf);
         int cw_new = h->cw ^ 1;
+        // a flush pad adds nothing to the PAM sums: its filter uses the last real buffer's
+        const bool sums = !h->kk && !h->flush_mode;
         e = launch_unpack(in, h->codes[cw_new], h->codes[h->cw], h->nb, h->nhist, h->nb, h->calls == 0,
-                          c.pack_order, h->kk ? nullptr : &h->st->pam_s1[par],
-                          h->kk ? nullptr : &h->st->pam_s2[par], sf);
+                          c.pack_order, sums ? &h->st->pam_s1[par] : nullptr,
+                          sums ? &h->st->pam_s2[par] : nullptr, sf);
         h->cw = cw_new;
         prof_end(h, 0, sf);
     }
@@ -785,21 +924,24 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         if (two) cudaStreamWaitEvent(sm, h->ev_yfree[yw_new], 0);   // the back end is done with this slot
         // the filter reads the field on the transmitter's grid: resampled, or as reconstructed
         const float2 *Ef = h->kk && h->rs ? h->R[h->rw] : h->E[h->ew];
+        // carrier and gain of this call (of the last real buffer in a flush)
+        const double *cgp = h->flush_mode ? h->st->cg_flush : &h->st->cg[h->ew][0];
+        const int ppar = h->flush_mode ? h->flush_par : par;
         const long long efbase = h->kk && h->rs ? h->rbase_cur : h->ebase_cur;
         if (h->kk && h->fd)
             e = launch_kk_fdmf(Ef, efbase, h->f_prev, s.f_k, c.fd_n, h->fd_H, h->fd_tw, h->ds_tab,
-                               c.ds_num, c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb,
+                               c.ds_num, c.ds_den, cgp, (float2 *)h->Y[yw_new], yb,
                                (const float2 *)h->Y[h->yw], h->ybase_cur, sm, h->clk, h->clk_w);
         else if (h->kk)
             e = launch_kk_mf(Ef, efbase, s.r_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
-                             c.ds_den, &h->st->cg[h->ew][0], (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw],
+                             c.ds_den, cgp, (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw],
                              h->ybase_cur, sm, h->rrc_host);
         else if (h->fd)
             e = launch_pam_fd1024(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->fd_H, h->fd_tw, h->st,
-                                  par, (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf,
+                                  ppar, (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf,
                                   h->clk, h->clk_w);
         else
-            e = launch_pam_mf(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->rrc, h->hmf, h->st, par,
+            e = launch_pam_mf(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->rrc, h->hmf, h->st, ppar,
                               (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf);
         h->yw = yw_new;
         h->ybase_cur = yb;
@@ -826,6 +968,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     g.nblk = npay > 0 ? (int)(npay / c.eq_block) : 0;
     g.nwin = npay > 0 ? (int)(npay / kWin) : 0;
     g.gpart = h->gpart;
+    g.score_end = h->flush_mode ? h->flush_score_end : 0x7FFFFFFFFFFFFFFFLL;
     if (four) cudaStreamWaitEvent(sb, h->ev_dfree[ds], 0);   // the demap is done with these decision slots
     prof_begin(h, 5, sb);
     if (e == cudaSuccess && do_train) {
@@ -874,6 +1017,10 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
                                 st4);
     }
     if (four) cudaEventRecord(h->ev_dfree[ds], st4);
+    if (lat_ev && e == cudaSuccess) {
+        cudaEventRecord(lat_ev[1], st4);
+        h->lat_head++;
+    }
     if (h->prof_cur) h->prof_head++;
     h->prof_cur = 0;
     if (e != cudaSuccess) {
@@ -904,7 +1051,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
 rx_status rx_process(rx_handle *h, const uint8_t *in, uint8_t *bits_out, void *stream, int64_t *nbits_out)
 {
     if (!h || !in || !nbits_out) return RX_EINVAL;
-    if (h->broken) return RX_ESTATE;
+    if (h->broken || h->flushed) return RX_ESTATE;
     if (((uintptr_t)in) & 15) return RX_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     return enqueue_call(h, in, bits_out, nullptr, nullptr, st, st, st, nbits_out);
@@ -947,7 +1094,7 @@ rx_status rx_process_batch(rx_handle *h, const uint8_t *const *ins, uint8_t *con
                            int64_t *nbits_out)
 {
     if (!h || !ins || !outs || !nbits_out || n <= 0) return RX_EINVAL;
-    if (h->broken) return RX_ESTATE;
+    if (h->broken || h->flushed) return RX_ESTATE;
     for (int i = 0; i < n; i++)
         if (!ins[i] || (((uintptr_t)ins[i]) & 15)) return RX_EINVAL;
     return run_batch(h, ins, outs, false, n, stream, nbits_out);
@@ -957,7 +1104,7 @@ rx_status rx_process_host_batch(rx_handle *h, const uint8_t *const *host_ins, ui
                                 void *stream, int64_t *nbits_out)
 {
     if (!h || !host_ins || !host_outs || !nbits_out || n <= 0) return RX_EINVAL;
-    if (h->broken) return RX_ESTATE;
+    if (h->broken || h->flushed) return RX_ESTATE;
     for (int i = 0; i < n; i++)
         if (!host_ins[i] || !host_outs[i]) return RX_EINVAL;
     return run_batch(h, host_ins, host_outs, true, n, stream, nbits_out);
@@ -967,9 +1114,87 @@ rx_status rx_process_host(rx_handle *h, const uint8_t *host_in, uint8_t *host_bi
                           int64_t *nbits_out)
 {
     if (!h || !host_in || !host_bits_out || !nbits_out) return RX_EINVAL;
-    if (h->broken) return RX_ESTATE;
+    if (h->broken || h->flushed) return RX_ESTATE;
     cudaStream_t st = (cudaStream_t)stream;
     return enqueue_call(h, nullptr, nullptr, host_in, host_bits_out, st, st, st, nbits_out);
+}
+
+rx_status rx_flush(rx_handle *h, uint8_t *bits_out, void *stream, int64_t *nbits_out)
+{
+    if (!h || !nbits_out) return RX_EINVAL;
+    if (h->broken) return RX_ESTATE;
+    *nbits_out = 0;
+    if (h->flushed) return RX_OK;
+    h->flushed = 1;
+    if (h->calls == 0) return RX_OK;
+    const rx_config &c = h->cfg;
+    cudaStream_t st = (cudaStream_t)stream;
+    // symbols whose centre lies inside the stream: nominal samples [0, r_end)
+    const long long total = h->calls * h->nb;
+    long long r_end = total;
+    if (h->rs) {
+        __int128 lim = ((__int128)total << 32) - (__int128)c.rs_phase0;   // m rs_step < lim
+        r_end = lim <= 0 ? 0 : (long long)((lim + c.rs_step - 1) / c.rs_step);
+    }
+    const long long S = r_end > 0 ? (r_end - 1) / h->sps + 1 : 0;
+    const long long first = h->q_prev > c.ntrain ? h->q_prev : (long long)c.ntrain;
+    if (S <= first) return RX_OK;
+    if (!bits_out) return RX_EINVAL;
+    cudaGetLastError();
+    // pad: the last code repeated; the pad calls reuse the last real buffer's carrier
+    // and gain (KK) or mean and deviation (PAM)
+    uint8_t *pad = h->in_stage[0];
+    const long long pbytes = h->nb * 3 / 2;
+    const uint8_t *hend = h->kk ? h->phist[h->hw] + (long long)h->nhist * 3 / 2 : nullptr;
+    const uint16_t *clast = h->kk ? nullptr : h->codes[h->cw] + h->nhist + h->nb - 1;
+    k_pad_fill<<<(unsigned)((pbytes + 255) / 256 < 1024 ? (pbytes + 255) / 256 : 1024), 256, 0, st>>>(
+        pad, pbytes, hend, clast, c.pack_order);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && h->kk)
+        e = cudaMemcpyAsync(h->st->cg_flush, &h->st->cg[h->ew][0], 4 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+        h->broken = 1;
+        return RX_ECUDA;
+    }
+    h->flush_mode = 1;
+    h->flush_par = (int)((h->calls - 1) & 1);
+    h->flush_score_end = S - (c.mf_span + c.ntaps + 1) / 2;
+    long long done = 0;   // bits written to bits_out
+    rx_status r = RX_OK;
+    for (int it = 0; h->q_prev < S && r == RX_OK && it < (1 << 20); it++) {
+        int64_t nb_call = 0;
+        r = enqueue_call(h, pad, h->bits_stage, nullptr, nullptr, st, st, st, &nb_call);
+        if (r != RX_OK) break;
+        h->pad_calls++;
+        long long hi = h->l_q_k < S ? h->l_q_k : S, use = hi - h->l_pay_lo;
+        if (nb_call > 0 && use > 0) {
+            long long bits = (long long)h->bps * use;
+            if (cudaMemcpyAsync(bits_out + done / 8, h->bits_stage, (size_t)((bits + 7) / 8), cudaMemcpyDeviceToDevice,
+                                st) != cudaSuccess) {
+                h->broken = 1;
+                r = RX_ECUDA;
+            }
+            done += bits;
+        }
+    }
+    h->flush_mode = 0;
+    *nbits_out = done;
+    return r;
+}
+
+rx_status rx_resampler_from_clock(double ppm, double delay, int64_t *rs_step, int64_t *rs_phase0)
+{
+    if (!rs_step || !rs_phase0 || !(fabs(ppm) < 9000.0) || !(fabs(delay) < 1073741824.0)) return RX_EINVAL;
+    const __int128 P = (__int128)(long long)nearbyint((1.0 + ppm * 1e-6) * 4294967296.0);   // ADC period, 2^-32
+    const __int128 D = (__int128)(long long)nearbyint(delay * 4294967296.0);              // delay, 2^-32
+    const __int128 half = P / 2;
+    const __int128 num_s = ((__int128)1 << 64) + half;
+    const __int128 num_p = D * ((__int128)1 << 32) + half;
+    __int128 qp = num_p / P;
+    if (num_p % P != 0 && num_p < 0) qp -= 1;   // floor division
+    *rs_step = (int64_t)(num_s / P);
+    *rs_phase0 = (int64_t)(-qp);
+    return RX_OK;
 }
 
 static double q_from_ber(double ber)
@@ -992,8 +1217,8 @@ rx_status rx_stats(rx_handle *h, rx_stats_t *o, void *stream)
     DevState s;
     if (cudaMemcpy(&s, h->st, sizeof s, cudaMemcpyDeviceToHost) != cudaSuccess) return RX_ECUDA;
     memset(o, 0, sizeof *o);
-    o->calls = h->calls;
-    o->samples = h->calls * h->nb;
+    o->calls = h->calls - h->pad_calls;
+    o->samples = o->calls * h->nb;
     o->symbols = (int64_t)s.cnt[C_SYMBOLS];
     o->bits = (int64_t)s.cnt[C_BITS];
     o->bit_errors = (int64_t)s.cnt[C_BITERR];
@@ -1007,6 +1232,15 @@ rx_status rx_stats(rx_handle *h, rx_stats_t *o, void *stream)
     o->device_error = s.err;
     o->ber = o->bits ? (double)o->bit_errors / (double)o->bits : 0.0;
     o->q_db = q_from_ber(o->ber);
+    if (h->lat_ev) {
+        lat_harvest(h, true);
+        o->lat_calls = h->lat_n;
+        o->deadline_misses = h->lat_miss;
+        o->deadline_ms = h->lat_budget;
+        o->lat_p50_ms = lat_pct(h, 0.50);
+        o->lat_p99_ms = lat_pct(h, 0.99);
+        o->lat_max_ms = h->lat_max;
+    }
     return RX_OK;
 }
 
@@ -1334,7 +1568,7 @@ rx_status rx_group_create(rx_handle *const *members, int n, int flags, rx_group 
     if (!members || !out || n < 1 || (flags & ~(RX_GROUP_GRAPH | RX_GROUP_TUNE))) return RX_EINVAL;
     *out = nullptr;
     for (int i = 0; i < n; i++) {
-        if (!members[i] || members[i]->broken) return RX_EINVAL;
+        if (!members[i] || members[i]->broken || members[i]->flushed) return RX_EINVAL;
         for (int j = 0; j < i; j++)
             if (members[j] == members[i]) return RX_EINVAL;
     }
@@ -1398,7 +1632,7 @@ rx_status rx_group_process(rx_group *g, const uint8_t *const *ins, uint8_t *cons
     const bool graph = (g->flags & RX_GROUP_GRAPH) != 0;
     if (graph && !caller) return RX_EINVAL;   // the legacy default stream cannot be captured
     for (int i = 0; i < g->n; i++) {
-        if (g->m[i]->broken) return RX_ESTATE;
+        if (g->m[i]->broken || g->m[i]->flushed) return RX_ESTATE;
         if (!ins[i] || (((uintptr_t)ins[i]) & 15)) return RX_EINVAL;
     }
     if (graph && cudaStreamBeginCapture(caller, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return RX_ECUDA;
@@ -1410,8 +1644,10 @@ rx_status rx_group_process(rx_group *g, const uint8_t *const *ins, uint8_t *cons
         rx_handle *h = g->m[i];
         cudaStream_t ws = g->ws[k % g->nw];
         int prof = h->prof_on;
-        h->prof_on = 0;   // no stage events inside a group round
+        h->prof_on = 0;   // no stage or latency events inside a group round
+        h->in_group = 1;
         r = enqueue_call(h, ins[i], outs[i], nullptr, nullptr, ws, ws, ws, &nbits_out[i]);
+        h->in_group = 0;
         h->prof_on = prof;
     }
     for (int w = 0; w < g->nw && r == RX_OK; w++)

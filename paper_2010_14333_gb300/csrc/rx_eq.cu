@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(kDemapThreads)
     if (lane < WPW && wr < wend) {
         long long k0 = g.pay_lo + (long long)wr * kWin;
         int qd = QAM ? (int)((s_m[wr - w0] + r) & 3) : 0;
-        if (!(QAM && k0 < amb_end)) {
+        if (!(QAM && k0 < amb_end) && k0 + kWin <= g.score_end) {
             int best = 0;
             unsigned be = rec_err(rc, qd);
 #pragma unroll

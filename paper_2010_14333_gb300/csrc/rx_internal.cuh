@@ -28,6 +28,7 @@ enum { C_SYMBOLS, C_BITS, C_BITERR, C_RAWERR, C_SYMERR, C_SLIP, C_NEAR, C_AMBIG,
 struct DevState {
     unsigned long long cnt[C_NCNT];
     double cg[kSlots][4];                  // KK per slot: carrier re, carrier im, gain
+    double cg_flush[4];                    // KK: carrier and gain of the last real buffer (flush)
     double pam_mu, pam_inv_sd;             // PAM: this call's normalisation (debug view)
     long long pam_s1[2], pam_s2[2];        // PAM: integer sums of codes / codes^2, by call parity
     int unwrap_have[2], unwrap_b[2];       // pi/2 unwrap carry, by parity
@@ -91,6 +92,7 @@ struct EqGeom {
     int nblk;                  // payload blocks in this call
     int nwin;                  // payload windows in this call
     float2 *gpart;             // frozen form: per-window tap-gradient partials of the last block
+    long long score_end;       // windows reaching symbol score_end or beyond are not scored
 };
 
 struct EqParams {

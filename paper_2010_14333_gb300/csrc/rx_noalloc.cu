@@ -5,6 +5,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "rx_internal.cuh"
@@ -17,14 +20,20 @@ constexpr long long kNaMaxSamples = 1LL << 19;          // largest buffer one ca
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-// byte layout of the scratch array: per FFT length (4096, 65536; the 256 slot is unused) a table
-// block [ln table | factored W_N | factored W_{N/16}]
+// byte layout of the scratch array:
+//   tables   per FFT length (4096, 65536) a block [ln table | factored W_N | factored W_{N/16}]
+//   hist     the packed history the front end is handed; on a stream's first buffer it
+//            is never read for values (samples before the stream are the first sample
+//            replicated), so it only has to be a valid region of ols_n * 3 / 2 bytes
+//   fft      the two-block complex FFT rows, at most 2^19 complex values
+//   E        the field [kEHist history | buffer]
+//   part     per-CTA carrier partials, state: the front end's reduction state
+constexpr int kNaSizes = 2;
 constexpr size_t kTabBytes = 4096 * sizeof(float) + 1024 * sizeof(float2);   // >= one block
-constexpr size_t kTwEntries = 3 * kTabBytes / sizeof(float2);
 constexpr size_t kOffTw = 0;
-constexpr size_t kOffCodes = align_up(kOffTw + kTwEntries * sizeof(float2));
-constexpr size_t kCodesBytes = (size_t)(65536 + kNaMaxSamples) * sizeof(uint16_t);
-constexpr size_t kOffFft = align_up(kOffCodes + kCodesBytes);
+constexpr size_t kOffHist = align_up(kOffTw + kNaSizes * kTabBytes);
+constexpr size_t kHistBytes = (size_t)65536 * 3 / 2;
+constexpr size_t kOffFft = align_up(kOffHist + kHistBytes);
 constexpr size_t kFftBytes = 4u << 20;                   // two-block complex FFT rows
 constexpr size_t kOffE = align_up(kOffFft + kFftBytes);
 constexpr size_t kEBytes = (size_t)(kEHist + kNaMaxSamples) * sizeof(float2);
@@ -37,36 +46,47 @@ constexpr size_t kScratchBytes = align_up(kOffState + sizeof(DevState));
 // Every call uses it, so calls that overlap on the GPU race with each other.
 static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
 
-// index of the table block of an FFT length
-int tab_index(int n) { return n == 256 ? 0 : (n == 4096 ? 1 : 2); }
+// index of the table block of an FFT length (4096 or 65536)
+int tab_index(int n) { return n == 4096 ? 0 : 1; }
 
-// per-device set-up: device address of the scratch array and the uploaded tables
+// per-device set-up: device address of the scratch array and the uploaded tables.
+// The first call on a device does it under a lock, so host threads that make their
+// first calls at the same time do it once; later calls only read the published flag.
 constexpr int kMaxDevices = 64;
 unsigned char *g_dev_ptr[kMaxDevices];
-bool g_ready[kMaxDevices];
+std::atomic<bool> g_ready[kMaxDevices];
+std::mutex g_setup_mu;
 
-cudaError_t setup_device(int dev, unsigned char **out)
+cudaError_t setup_device(int dev, cudaStream_t st, unsigned char **out)
 {
-    if (g_ready[dev]) {
+    if (g_ready[dev].load(std::memory_order_acquire)) {
+        *out = g_dev_ptr[dev];
+        return cudaSuccess;
+    }
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (g_ready[dev].load(std::memory_order_acquire)) {
         *out = g_dev_ptr[dev];
         return cudaSuccess;
     }
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
     if (e != cudaSuccess) return e;
-    // lookup and twiddle tables of the three FFT lengths, once per device
-    static unsigned char blk[3 * kTabBytes];
-    const int sizes[3] = {256, 4096, 65536};
-    for (int i = 0; i < 3; i++) {
+    // lookup and twiddle tables of the two FFT lengths, once per device: copied on the
+    // caller's stream, which is then synchronised, so the tables are in place before
+    // this call's kernels and before any later call on any stream
+    static unsigned char blk[kNaSizes * kTabBytes];
+    const int sizes[kNaSizes] = {4096, 65536};
+    for (int i = 0; i < kNaSizes; i++) {
         unsigned char *b = blk + i * kTabBytes;
         float *ln = (float *)b;
         float2 *t1 = (float2 *)(ln + 4096), *t2 = t1 + kk_tw_entries(sizes[i]);
         kk_host_tables(sizes[i], ln, t1, t2);
     }
-    e = cudaMemcpy((unsigned char *)p + kOffTw, blk, sizeof blk, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync((unsigned char *)p + kOffTw, blk, sizeof blk, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
     g_dev_ptr[dev] = (unsigned char *)p;
-    g_ready[dev] = true;
+    g_ready[dev].store(true, std::memory_order_release);
     *out = (unsigned char *)p;
     return cudaSuccess;
 }
@@ -99,7 +119,7 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     g.e_prev = 0;
     g.e_k = e_k;
     g.avail = nsamp;
-    g.cbase = -(long long)ols_n;        // codes: [ols_n samples before the stream | buffer]
+    g.cbase = -(long long)ols_n;        // stream index of the packed history's first sample
     g.ebase = -kEHist;                  // field: [kEHist history | buffer]
     g.ebase_prev = -kEHist;
     g.sps = 4;
@@ -110,15 +130,15 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RX_ECUDA;
-    unsigned char *base = nullptr;
-    if (setup_device(dev, &base) != cudaSuccess) return RX_ECUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    unsigned char *base = nullptr;
+    if (setup_device(dev, st, &base) != cudaSuccess) return RX_ECUDA;
     const unsigned char *tabb = base + kOffTw + tab_index(ols_n) * kTabBytes;
     KkTables tb;
     tb.lnt = (const float *)tabb;
     tb.twN = (const float2 *)(tb.lnt + 4096);
     tb.twN2 = tb.twN + kk_tw_entries(ols_n);
-    uint16_t *codes = (uint16_t *)(base + kOffCodes);
+    const uint8_t *hist = base + kOffHist;
     float2 *fftws = (float2 *)(base + kOffFft);
     float2 *E = (float2 *)(base + kOffE);
     CarrierPartial *part = (CarrierPartial *)(base + kOffPart);
@@ -126,7 +146,7 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     // the last-CTA ticket of the carrier reduction must start at zero
     if (cudaMemsetAsync(ds, 0, sizeof(DevState), st) != cudaSuccess) return RX_ECUDA;
     KkInput kin;
-    kin.hist = (const uint8_t *)codes;      // never read for values: the first call fills the pre-stream
+    kin.hist = hist;                        // never read for values: the first call fills the pre-stream
     kin.in = packed12_in;
     kin.hist_next = nullptr;
     kin.hist_bytes = (long long)ols_n * 3 / 2;

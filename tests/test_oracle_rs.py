@@ -100,9 +100,14 @@ def test_rejects_bad_accumulators():
 
 
 def test_binding_resampler_params_match_the_oracle():
-    """The product's host helper that turns a clock estimate into the accumulator
-    agrees with the oracle's, which the pins above check against exact positions."""
+    """librx's rx_resampler_from_clock (C ABI; host integer arithmetic, no GPU)
+    turns a clock estimate into the accumulator exactly as the oracle does, which
+    the pins above check against exact positions; out-of-range clocks are refused."""
     import paper_2010_14333_gb300 as rx
-    for ppm, delay in ((-35.0, 0.4), (20.0, -0.7), (80.0, 1.1), (0.0, 0.0), (-0.3, -1.9)):
+    for ppm, delay in ((-35.0, 0.4), (20.0, -0.7), (80.0, 1.1), (0.0, 0.0), (-0.3, -1.9),
+                       (1234.5, -100.25), (-8999.0, 1e6), (7.25, 3.5)):
         want = oracle.rs_params(synth.clock_step(ppm), int(round(delay * (1 << 32))))
-        assert rx.resampler_params(ppm, delay) == want, (ppm, delay)
+        assert rx.rx_resampler_from_clock(ppm, delay) == want, (ppm, delay)
+    for ppm, delay in ((9000.0, 0.0), (-1e5, 0.0), (0.0, 2.0 ** 31), (float("nan"), 0.0)):
+        with pytest.raises(rx.RxError):
+            rx.rx_resampler_from_clock(ppm, delay)

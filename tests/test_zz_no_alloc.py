@@ -51,3 +51,5 @@ def test_noalloc_rejects_oversize_and_bad_arguments():
     assert lib.rx_kk_field_noalloc(buf.data_ptr(), (1 << 19) + 32, 0, 65536, 4096, out.data_ptr(), None) == 1
     assert lib.rx_kk_field_noalloc(buf.data_ptr(), 1000, 0, 4096, 512, out.data_ptr(), None) == 1
     assert lib.rx_kk_field_noalloc(buf.data_ptr(), 4096, 0, 8192, 512, out.data_ptr(), None) == 1
+    # legal sizes whose overlap-save blocks need more FFT rows than the array holds
+    assert lib.rx_kk_field_noalloc(buf.data_ptr(), 1 << 19, 0, 65536, 61440, out.data_ptr(), None) == 1
