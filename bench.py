@@ -52,7 +52,7 @@ OLS = 65536 / (65536 - 4096)
 FLOPS_PER_SAMPLE = {"kk_fwd": 13.0 * OLS, "kk_rows": 60.0 * OLS, "kk_inv": 13.0 * OLS, "mf": 130.0,
                     "eq": 252.0, "kk_front": 86.0 * OLS}
 BYTES_PER_SAMPLE = {"unpack": 1.5 + 2.0}   # packed read + 16-bit code write
-SMS, LANES = 152, 128
+LANES = 128                 # FP32 lanes per SM (the SM count is queried from the device)
 
 
 def workload_config(args):
@@ -157,8 +157,8 @@ def reference_arm(args, rank):
     import oracle
     import synth
     total = args.steps + args.warmup
-    nb = 1 << 22
-    while nb > 1 << 15 and total * nb / 0.6e6 > 150.0:   # keep the whole run within minutes
+    nb = NB   # the workload's own 2^22-sample buffer (about 3 s of oracle time each)
+    while nb > 1 << 15 and total * nb / 1.2e6 > 240.0:   # only a very long run shrinks it
         nb //= 2
     g = synth.gen_kk_stream(FMT, nb, total, seed=1, truth=False,
                             workers=min(16, os.cpu_count() or 1), **GEN)
@@ -183,6 +183,34 @@ def reference_arm(args, rank):
             "e2e": {"value": value, "unit": "GSa/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "ber": s["ber"]}
     print(json.dumps(line), flush=True)
+
+
+def _oracle_worker(bufs):
+    """One independent oracle stream in a spawned process: (samples, seconds)."""
+    import oracle
+    o = oracle.Oracle(**oracle.default_cfg(FMT, len(bufs[0]) * 2 // 3))
+    t = time.perf_counter()
+    for b in bufs:
+        o.process(b)
+    return len(bufs) * len(bufs[0]) * 2 // 3, time.perf_counter() - t
+
+
+def cpu_all_cores(packed, per_core: int = 2):
+    """The oracle on every host core: one independent stream of `per_core`
+    consecutive ring buffers per core, in spawned processes (the oracle itself stays
+    single-threaded).  GSa/s = all samples over the wall time of the slowest core."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    jobs = [[packed[(per_core * i + j) % len(packed)] for j in range(per_core)] for i in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, [[jobs[0][0][:3 * 8192]]] * cores)   # import and load in every worker first
+        t = time.perf_counter()
+        res = pool.map(_oracle_worker, jobs, chunksize=1)
+        wall = time.perf_counter() - t
+    return {"cores": cores, "value": sum(n for n, _ in res) / wall / 1e9,
+            "sample": f"{cores} independent streams of {per_core} buffers of 2^22 samples, one per core, "
+                      "spawned processes, wall time of the slowest"}
 
 
 def replica_throughput(ms_local, units_per_rank, dist=None, device="cpu"):
@@ -373,7 +401,8 @@ def gpu_arm(args, rank, world, local):
     dom = "eq" if per_call.get("eq", 0.0) > 0 else max(per_call, key=per_call.get)
     peaks = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SMS * LANES * 2 * sm_max * 1e6 / 1e12        # FP32 TFLOP/s at the maximum SM clock
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * LANES * 2 * sm_max * 1e6 / 1e12        # FP32 TFLOP/s at the maximum SM clock
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     stages = {}
     tot_alone = sum(per_alone.values())
@@ -388,10 +417,21 @@ def gpu_arm(args, rank, world, local):
             d["gbs"] = BYTES_PER_SAMPLE[s] * NB / (ta * 1e-3) / 1e9
             d["frac_hbm"] = d["gbs"] / hbm_peak
         stages[s] = d
-    traffic = None
+    traffic, traffic_src = None, None
     tr_path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if os.path.exists(tr_path):
-        traffic = json.load(open(tr_path)).get(dom)
+        # ncu DRAM bytes of one launch, valid only while the kernel's source is the one
+        # the capture was taken from (its sha256 is stored beside the figure)
+        ent = json.load(open(tr_path)).get(dom)
+        if isinstance(ent, dict):
+            import hashlib
+            src = os.path.join(ROOT, "paper_2010_14333_gb300", "csrc", ent.get("source", ""))
+            cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.isfile(src) else None
+            if cur and cur == ent.get("source_sha16"):
+                traffic = ent.get("bytes_per_launch")
+                traffic_src = {k: ent.get(k) for k in ("capture", "source", "source_sha16", "profile")}
+            else:
+                traffic_src = {"stale": "kernel source changed since the capture", "capture": ent.get("capture")}
     timing = ("launches timed alone: CUDA events on the launching stream around each of %d launches, "
               "one buffer in flight (in the pipelined timed region the stages on five streams share the SMs, "
               "which stretches each launch: see pipelined)" % alone_calls)
@@ -402,15 +442,16 @@ def gpu_arm(args, rank, world, local):
         ach = stages[dom]["tflops"]
         live = FLOPS_PER_SAMPLE[dom] * NB / (t_live * 1e-3) / 1e12 if t_live > 0 else None
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": ach / alu_peak, "traffic": traffic, "timing": timing,
+                "frac": ach / alu_peak, "traffic": traffic, "traffic_source": traffic_src, "timing": timing,
                 "pipelined": {"achieved": live, "frac": live / alu_peak if live else None,
                               "ms_per_launch": t_live},
-                "peak_source": "FP32: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured)" % sm_max}
+                "peak_source": "FP32: %d SMs (queried) x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured)" % (
+                    sms, sm_max)}
     else:
         ach = stages[dom]["gbs"]
         live = BYTES_PER_SAMPLE[dom] * NB / (t_live * 1e-3) / 1e9 if t_live > 0 else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": traffic, "timing": timing,
+                "frac": ach / hbm_peak, "traffic": traffic, "traffic_source": traffic_src, "timing": timing,
                 "pipelined": {"achieved": live, "frac": live / hbm_peak if live else None,
                               "ms_per_launch": t_live},
                 "peak_source": "hbm_gbs of measured"}
@@ -430,8 +471,10 @@ def gpu_arm(args, rank, world, local):
         for b in range(nref):
             chk.process(ring[b])
         sg = chk.stats()
+        allc = cpu_all_cores(g["packed"])
         cpu = {"value": nref * NB / dt / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
                "sample": f"the first {nref} buffers (2^22 samples each) of the same stream, single thread",
+               "cores_all": allc["cores"], "value_all_cores": allc["value"], "sample_all_cores": allc["sample"],
                "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
                "ber_oracle": so["ber"], "ber_gpu_same_buffers": sg["ber"],
                "bit_errors_oracle": so["bit_errors"], "bit_errors_gpu": sg["bit_errors"], "bits": so["bits"]}
