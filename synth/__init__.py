@@ -348,7 +348,8 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
               beta: float = 0.1, span: int = 16, fd_num: int = 11, fd_den: int = 80,
               noise: bool = True, phase_noise: bool = True, volterra=(0.0, 0.0),
               prbs_seed: int = 1, pack_order: int = 0, symbols=None, phase_steps=(),
-              truth: bool = True, clock_step: int = 1 << 32, clock_phase0: int = 0):
+              truth: bool = True, clock_step: int = 1 << 32, clock_phase0: int = 0,
+              isi=None, sym_snr_db=None):
     """Buffer b of a Kramers-Kronig single-sideband QAM stream (see gen_kk_stream)."""
     name, bps, kind = FORMATS[fmt]
     assert kind == "qam"
@@ -370,6 +371,15 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
         if hi > lo:
             a_seg[lo - ka:hi - ka] = sy[lo:hi]
         Es = float(np.mean(np.abs(sy) ** 2))
+    if isi is not None:
+        # symbol-spaced ISI: a'_k = isi[0] a_{k+1} + isi[1] a_k + isi[2] a_{k-1}
+        ext = np.concatenate(([0j], a_seg, [0j]))
+        if symbols is None:
+            ext[0] = _tx_symbols(fmt, prbs_seed, ka - 1, ka)[0]
+            ext[-1] = _tx_symbols(fmt, prbs_seed, kb, kb + 1)[0]
+        a_seg = isi[0] * ext[2:] + isi[1] * ext[1:-1] + isi[2] * ext[:-2]
+    if sym_snr_db is not None:
+        a_seg = a_seg + _symbol_noise(seed, ka, kb, Es / 10.0 ** (sym_snr_db / 10.0))
     Ps = Es / sps                      # per-sample power of the shaped signal
     A = np.sqrt(10.0 ** (cspr_db / 10.0) * Ps)
     sig2 = Ps * sps / 10.0 ** (snr_db / 10.0)
@@ -411,6 +421,22 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
     return out
 
 
+def _symbol_noise(seed: int, ka: int, kb: int, var: float) -> np.ndarray:
+    """Complex Gaussian noise of variance var for symbols [ka, kb) (zero for k < 0),
+    drawn in blocks of 4096 symbols keyed by the block index, so a symbol gets the
+    same value in every buffer whose span holds it."""
+    out = np.zeros(kb - ka, dtype=np.complex128)
+    for blk in range(max(ka, 0) // 4096, max(kb - 1, 0) // 4096 + 1):
+        lo, hi = blk * 4096, blk * 4096 + 4096
+        a, b = max(lo, ka, 0), min(hi, kb)
+        if b <= a:
+            continue
+        r = np.random.default_rng([int(seed), blk, 41]).standard_normal((4096, 2))
+        v = (r[:, 0] + 1j * r[:, 1]) * np.sqrt(var / 2.0)
+        out[a - ka:b - ka] = v[a - lo:b - lo]
+    return out
+
+
 def _kk_worker(args):
     kw, b, th0 = args
     return kk_buffer(b=b, theta0=th0, **kw)
@@ -422,7 +448,8 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
                   fd_den: int = 80, noise: bool = True, phase_noise: bool = True,
                   volterra=(0.0, 0.0), prbs_seed: int = 1, pack_order: int = 0,
                   symbols=None, phase_offset: float = 0.0, phase_steps=(), workers: int = 1,
-                  truth: bool = True, clock_step: int = 1 << 32, clock_phase0: int = 0):
+                  truth: bool = True, clock_step: int = 1 << 32, clock_phase0: int = 0,
+                  isi=None, sym_snr_db=None):
     """Kramers-Kronig single-sideband QAM stream split into ADC buffers.
 
     The signal sits above a real tone at 0 Hz after an up-shift of fd_num/fd_den
@@ -434,6 +461,11 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
     ``clock_step`` / ``clock_phase0``: the ADC takes sample n at transmitter time
     (clock_phase0 + n clock_step) / 2^32 nominal samples (integer accumulator; see
     clock_step()); the default is the nominal grid.
+    ``isi`` = (pre, main, post): symbol-spaced ISI on the symbols before shaping, as
+    in gen_pam_stream.  ``sym_snr_db``: complex AWGN of that Es/N0 added to the
+    symbols before shaping, i.e. noise confined to the signal band (after the unit-
+    energy matched filter the symbol samples carry exactly that noise); usually
+    with noise=False.
     Returns dict with 'packed' (per buffer), 'codes', 'symbols' (the transmitted
     symbols of the stream), 'field' (noiseless complex baseband at sps, before the
     shift: what the receiver should recover; with truth=True) and 'clips'.
@@ -446,7 +478,8 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
               fd_den=fd_den, noise=noise, phase_noise=phase_noise, volterra=volterra,
               prbs_seed=prbs_seed, pack_order=pack_order, symbols=symbols,
               phase_steps=tuple(phase_steps), truth=truth, clock_step=int(clock_step),
-              clock_phase0=int(clock_phase0))
+              clock_phase0=int(clock_phase0), isi=None if isi is None else tuple(isi),
+              sym_snr_db=sym_snr_db)
     th0 = kk_phase_starts(buf_len, nbufs, seed, linewidth, fs, phase_noise, phase_offset)
     jobs = [(kw, b, th0[b]) for b in range(nbufs)]
     if workers > 1 and nbufs > 1:

@@ -34,11 +34,34 @@ def test_oracle_only_in_reference_arm_and_cpu_baseline():
             p = par.get(p)
         funcs = [p.name for p in chain if isinstance(p, ast.FunctionDef)]
         assert funcs, f"module-level oracle import at line {node.lineno}"
-        if funcs[0] == "reference_arm":
+        if funcs[0] in ("reference_arm", "_oracle_worker"):
             continue
         assert funcs[0] == "gpu_arm", f"oracle imported in {funcs[0]} (line {node.lineno})"
         guards = [ast.unparse(p.test) for p in chain if isinstance(p, ast.If)]
         assert any("no_cpu_baseline" in g for g in guards), f"oracle outside the CPU-baseline leg (line {node.lineno})"
+    # the all-cores baseline runs the oracle in spawned workers (a module-level function,
+    # so that it can be pickled): it is reached only from the CPU-baseline leg
+    calls = {"_oracle_worker": [], "cpu_all_cores": []}
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Name) and node.id in calls and not isinstance(par.get(node), ast.FunctionDef):
+            calls[node.id].append(node)
+    for node in calls["_oracle_worker"]:
+        chain, p = [], par.get(node)
+        while p is not None:
+            chain.append(p)
+            p = par.get(p)
+        funcs = [p.name for p in chain if isinstance(p, ast.FunctionDef)]
+        assert funcs and funcs[0] == "cpu_all_cores", f"oracle worker used in {funcs} (line {node.lineno})"
+    assert calls["cpu_all_cores"]
+    for node in calls["cpu_all_cores"]:
+        chain, p = [], par.get(node)
+        while p is not None:
+            chain.append(p)
+            p = par.get(p)
+        funcs = [p.name for p in chain if isinstance(p, ast.FunctionDef)]
+        guards = [ast.unparse(p.test) for p in chain if isinstance(p, ast.If)]
+        assert funcs and funcs[0] == "gpu_arm" and any("no_cpu_baseline" in g for g in guards), \
+            f"all-cores oracle baseline outside the CPU-baseline leg (line {node.lineno})"
 
 
 def test_product_package_never_imports_the_oracle():

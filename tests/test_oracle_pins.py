@@ -364,3 +364,67 @@ def test_bps_metric_brute_force(mq, scale):
         ref = np.sum(np.min(np.abs(v[:, None] - pts[None, :]) ** 2, axis=1))
         assert abs(got[b] - ref) <= 1e-12 * ref
     assert abs((np.argmin(got) / B * np.pi / 2 - np.pi / 4) - 0.37) <= np.pi / 64
+
+
+@pytest.mark.parametrize("fmt,snr_db", [(4, 14.0), (4, 16.0), (3, 8.0), (3, 10.0)])
+def test_awgn_kk_qam_ber_matches_textbook(fmt, snr_db):
+    """KK-16QAM / KK-QPSK with AWGN confined to the signal band (added to the
+    symbols before shaping, Es/N0 = snr), no phase noise, CSPR 20 dB (the field
+    is minimum phase everywhere, so KK reconstructs it), ideal frozen taps that
+    undo the chain's power normalisation and a phase search on {-pi/4, 0}: the BER
+    lies in the 99 % binomial interval of the exact Gray-QAM BER (two independent
+    Gray PAM-sqrt(M) dimensions, half level spacing / sigma = d).  The chain's own
+    deterministic distortion (filter truncation, KK residual) is measured on the
+    same stream without noise and added as an independent Gaussian term; it must be
+    small (> 30 dB below the symbols)."""
+    N = 1 << 21
+    snr = 10 ** (snr_db / 10)
+    scale2 = 10.0 if fmt == 4 else 2.0        # unnormalised level units: z * sqrt(10) or sqrt(2)
+    cfg = oracle.default_cfg(fmt, N, mu=0.0, mu_cma=0.0, ntrain=4096, ncma=2048, bps_b=2)
+
+    def run(noisy):
+        g = synth.gen_kk_stream(fmt, N, 1, seed=11, noise=False, phase_noise=False, cspr_db=20.0,
+                                sym_snr_db=snr_db if noisy else None, truth=False)
+        o = oracle.Oracle(**cfg)
+        taps = np.zeros(cfg["ntaps"], complex)
+        # the chain divides by sqrt(sps * signal power), which includes the symbol noise
+        taps[cfg["ntaps"] // 2] = math.sqrt(1 + 1 / snr) if noisy else 1.0
+        o.set_taps(taps)
+        o.process(g["packed"][0])
+        return o, g
+
+    o0, g0 = run(False)
+    v, s0 = o0.get(oracle.ORX_V)
+    a = g0["symbols"][s0:s0 + len(v)] * math.sqrt(scale2)
+    floor = float(np.mean(np.abs(v[5000:-100] - a[5000:-100]) ** 2) / 2)   # per dimension
+    assert o0.stats()["bit_errors"] == 0 and floor < 1e-3 * scale2 / 2
+    o, _ = run(True)
+    s = o.stats()
+    M = 4 if fmt == 4 else 2
+    p = _pam_gray_ber(M, 1.0 / math.sqrt(scale2 / (2 * snr) + floor))
+    n = s["bits"]
+    tol = 2.576 * math.sqrt(n * p * (1 - p))
+    assert abs(s["bit_errors"] - n * p) <= tol, (s["bit_errors"], n * p, tol)
+
+
+@pytest.mark.parametrize("fmt", [3, 4])
+@pytest.mark.parametrize("isi,closed", [((0.1, 1.0, 0.2), False), ((0.3 + 0.2j, 1.0, -0.45 + 0.25j), True)])
+def test_kk_isi_channel_equalised_to_zero_errors(fmt, isi, closed):
+    """Noiseless KK stream through a symbol-spaced ISI channel (mild and real; strong
+    and complex, which closes the eye of both formats): CMA then DD-LMS from
+    identity taps converge, and every payload bit is right.  On the strong channel
+    the same stream with the taps frozen at identity has errors, so the equaliser is
+    what removes the ISI."""
+    N = 1 << 20
+    g = synth.gen_kk_stream(fmt, N, 2, seed=3, noise=False, phase_noise=False, cspr_db=14.0, isi=isi,
+                            truth=False)
+    o = oracle.Oracle(**oracle.default_cfg(fmt, N))
+    for b in range(2):
+        o.process(g["packed"][b])
+    s = o.stats()
+    assert s["bits"] > 900_000 and s["bit_errors"] == 0 and s["raw_bit_errors"] == 0
+    if closed:
+        of = oracle.Oracle(**oracle.default_cfg(fmt, N, mu=0.0, mu_cma=0.0))
+        for b in range(2):
+            of.process(g["packed"][b])
+        assert of.stats()["bit_errors"] > 10000
