@@ -248,7 +248,7 @@ def gpu_arm(args, rank, world, local):
                             workers=min(16, os.cpu_count() or 1), **GEN)
     t_gen = time.perf_counter() - t_gen
     ring = [torch.from_numpy(p).cuda() for p in g["packed"]]
-    r = rx.Receiver(FMT, NB, eq_warps=args.eq_warps)
+    r = rx.Receiver(FMT, NB, eq_warps=args.eq_warps, deadline_ms=args.deadline_ms)
     stream = torch.cuda.current_stream()
 
     # one step = one pipelined call over bufs_per_step consecutive buffers of the ring
@@ -308,6 +308,7 @@ def gpu_arm(args, rank, world, local):
     host_ring = [torch.from_numpy(p).pin_memory() for p in g["packed"]]
     c2 = rx.rx_default_config(FMT)
     c2.eq_warps = args.eq_warps
+    c2.deadline_ms = args.deadline_ms
     h2 = rx.rx_create(FMT, BAUD, FS, NB, c2)
     out_host = [torch.zeros(rx.rx_max_bits(h2) // 8 + 16, dtype=torch.uint8).pin_memory()
                 for _ in range(args.bufs_per_step)]
@@ -1028,6 +1029,9 @@ def main():
     ap.add_argument("--batched-rounds", type=int, default=10)
     ap.add_argument("--latency-reps", type=int, default=1000)
     ap.add_argument("--eq-warps", type=int, default=0, help="equaliser blocks per CTA (0: library default)")
+    ap.add_argument("--deadline-ms", type=float, default=0.0,
+                    help="per-buffer latency budget of the timed receivers (0: the library default, five buffer "
+                         "durations; < 0: no latency record)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

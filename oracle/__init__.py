@@ -274,7 +274,7 @@ def cnn_param_slices():
 
 # ------------------------------------------------------------------ receiver
 KK_DEFAULTS = dict(sps=4, pack_order=0, ols_n=65536, ols_v=4096, ds_num=11, ds_den=80,
-                   rrc_beta=0.1, mf_span=16, ntaps=31, ntrain=16384, ncma=8192, eq_block=256,
+                   rrc_beta=0.1, mf_span=16, ntaps=31, ntrain=16384, ncma=8192, eq_block=128,
                    win=64, mu=1e-3, mu_train=1e-3, mu_cma=1e-3, bps_b=32, amb_syms=1024,
                    prbs_seed=1, eq_frozen=0, mf_mode=0, fd_n=1024, fd_taps=203, pad_rs=0, rs_step=0,
                    rs_phase0=0)

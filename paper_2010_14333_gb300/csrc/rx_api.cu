@@ -371,7 +371,9 @@ rx_status rx_default_config(rx_format f, rx_config *c)
     c->ntaps = kk ? 31 : 15;
     c->ntrain = kk ? 16384 : 4096;
     c->ncma = kk ? 8192 : 0;
-    c->eq_block = 256;
+    // the paper's 8192 data blocks of a 2^22-sample buffer: 128 symbols at 4 samples/symbol
+    // (KK), 256 at 2 samples/symbol (PAM)
+    c->eq_block = kk ? 128 : 256;
     c->win = 64;
     c->mu = 1e-3;
     c->mu_train = 1e-3;

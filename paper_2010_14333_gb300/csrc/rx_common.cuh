@@ -80,6 +80,42 @@ __device__ __forceinline__ void dft16(float2 (&x)[16])
         for (int k0 = 0; k0 < 4; k0++) x[k1 + 4 * k0] = t[4 * k1 + k0];
 }
 
+// ------------------------------------------------------------ packed FP32 pairs
+// Two FP32 values in one 64-bit register, operated on by the sm_100-family paired
+// FP32 instructions (fma.rn.f32x2 and friends): each half is an IEEE round-to-
+// nearest operation, identical to the scalar one, at one instruction per pair.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2_pack(float a, float b)
+{
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(f2x v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c)
+{
+    f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b)
+{
+    f2x d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b)
+{
+    f2x d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // padded shared-memory index: one spare element per 16 avoids bank conflicts
 // in the stride-16 radix-16 pass
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }

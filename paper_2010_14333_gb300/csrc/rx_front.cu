@@ -921,7 +921,10 @@ __global__ void __launch_bounds__(kMfOut) k_kk_mf(const float2 *__restrict__ E, 
 // with ge[u] = h[HMF - 2u], go[u] = h[HMF - 2u - 1].  Each thread computes 8
 // consecutive outputs from a sliding window of 8 pairs held in registers (one
 // 16-byte shared load per tap); the pair layout keeps one spare slot per 8 pairs,
-// which makes the stride-8-pair loads of a warp free of bank conflicts.
+// which makes the stride-8-pair loads of a warp free of bank conflicts.  The real
+// and imaginary parts of an output accumulate as one packed FP32 pair (one
+// fma.rn.f32x2 per tap and output, the same roundings as two scalar FMAs in the
+// same order); the taps sit in shared memory as (ge, ge, go, go).
 template <int HMF>
 struct MfTaps {
     float ge[HMF + 1];
@@ -941,10 +944,15 @@ __global__ void __launch_bounds__(kMfThreads) k_kk_mf_t(const float2 *__restrict
 {
     constexpr int NPAIR = kMfTileOut + HMF + kMfR;
     extern __shared__ float4 pr[];     // padded pair tile
+    __shared__ float4 s_tp[HMF + 1];   // (ge, ge, go, go) per tap index u (go[HMF] = 0)
     long long m0 = f_prev + (long long)blockIdx.x * kMfTileOut;
     long long n0 = 2 * m0 - HMF;
     const float2 c = make_float2((float)cg[0], (float)cg[1]);
     const float gn = (float)cg[2];
+    for (int u = threadIdx.x; u <= HMF; u += kMfThreads) {
+        const float ho = u < HMF ? taps.go[u] : 0.f;
+        s_tp[u] = make_float4(taps.ge[u], taps.ge[u], ho, ho);
+    }
     // integer phase index of the downshift, advanced incrementally
     int idx = (int)((((n0 % ds_den) + ds_den) % ds_den + 2LL * threadIdx.x) % ds_den);
     idx = (int)(((long long)idx * ds_num) % ds_den);
@@ -965,33 +973,32 @@ __global__ void __launch_bounds__(kMfThreads) k_kk_mf_t(const float2 *__restrict
             Y[m - ybase] = (m < 0) ? make_float2(0.f, 0.f) : Y_prev[m - ybase_prev];
     }
     __syncthreads();
+    const ulonglong2 *prp = reinterpret_cast<const ulonglong2 *>(pr);
+    const ulonglong2 *tpp = reinterpret_cast<const ulonglong2 *>(s_tp);
     const int j0 = kMfR * threadIdx.x;
-    float4 win[kMfR];
+    ulonglong2 win[kMfR];
 #pragma unroll
-    for (int r = 0; r < kMfR; r++) win[r] = pr[pad8(j0 + r)];
-    float ar[kMfR], ai[kMfR];
+    for (int r = 0; r < kMfR; r++) win[r] = prp[pad8(j0 + r)];
+    f2x acc[kMfR];
 #pragma unroll
-    for (int r = 0; r < kMfR; r++) ar[r] = ai[r] = 0.f;
+    for (int r = 0; r < kMfR; r++) acc[r] = 0ull;   // (+0, +0)
 #pragma unroll
     for (int u = 0; u <= HMF; u++) {
-        const float he = taps.ge[u];
+        const ulonglong2 T = tpp[u];
 #pragma unroll
-        for (int r = 0; r < kMfR; r++) {
-            ar[r] = fmaf(he, win[r].x, ar[r]);
-            ai[r] = fmaf(he, win[r].y, ai[r]);
-        }
+        for (int r = 0; r < kMfR; r++) acc[r] = f2_fma(T.x, win[r].x, acc[r]);
         if (u < HMF) {
-            const float ho = taps.go[u];
 #pragma unroll
-            for (int r = 0; r < kMfR; r++) {
-                ar[r] = fmaf(ho, win[r].z, ar[r]);
-                ai[r] = fmaf(ho, win[r].w, ai[r]);
-            }
+            for (int r = 0; r < kMfR; r++) acc[r] = f2_fma(T.y, win[r].y, acc[r]);
 #pragma unroll
             for (int r = 0; r < kMfR - 1; r++) win[r] = win[r + 1];
-            win[kMfR - 1] = pr[pad8(j0 + u + kMfR)];
+            win[kMfR - 1] = prp[pad8(j0 + u + kMfR)];
         }
     }
+    const f2x g2 = f2_pack(gn, gn);
+    float2 out[kMfR];
+#pragma unroll
+    for (int r = 0; r < kMfR; r++) out[r] = f2_unpack(f2_mul(g2, acc[r]));
     long long mb = m0 + j0;
     if (mb + kMfR <= f_k) {
         float4 *o = reinterpret_cast<float4 *>(Y + (mb - ybase));
@@ -999,15 +1006,15 @@ __global__ void __launch_bounds__(kMfThreads) k_kk_mf_t(const float2 *__restrict
         if (al) {
 #pragma unroll
             for (int r = 0; r < kMfR; r += 2)
-                o[r / 2] = make_float4(gn * ar[r], gn * ai[r], gn * ar[r + 1], gn * ai[r + 1]);
+                o[r / 2] = make_float4(out[r].x, out[r].y, out[r + 1].x, out[r + 1].y);
         } else {
 #pragma unroll
-            for (int r = 0; r < kMfR; r++) Y[mb + r - ybase] = make_float2(gn * ar[r], gn * ai[r]);
+            for (int r = 0; r < kMfR; r++) Y[mb + r - ybase] = out[r];
         }
     } else {
 #pragma unroll
         for (int r = 0; r < kMfR; r++)
-            if (mb + r < f_k) Y[mb + r - ybase] = make_float2(gn * ar[r], gn * ai[r]);
+            if (mb + r < f_k) Y[mb + r - ybase] = out[r];
     }
 }
 
