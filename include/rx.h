@@ -101,7 +101,11 @@ typedef struct {
     int32_t fd_n;        /* RX_MF_FD block length: power of two, 16 .. 1024; default 1024  */
     int32_t fd_taps;     /* RX_MF_FD filter taps (root-raised cosine, zero phase, unit
                             energy): odd, <= fd_n/2 + 1; default 203 (KK), 503 (PAM)      */
-    int32_t pad_rs;      /* reserved, 0                                                    */
+    int32_t clk_track;   /* 1: track the ADC clock across calls (needs RX_MF_FD): every
+                            call's frequency-domain blocks feed one running estimate (the
+                            band-edge delays unwrapped across buffers, a least-squares line
+                            over all blocks since the last re-timing; rx_clock_track), which
+                            rx_clock_retime can feed back into the resampler.  0 = off     */
     int64_t rs_step;     /* KK resampler to the transmitter's sample grid (the ADC runs on
                             its own clock; Sec. 2 recovers the clock phase in the DSP):
                             0 = off (default); else nominal sample m lies at ADC position
@@ -444,6 +448,33 @@ const char *rx_strerror(rx_status s);
  * Synchronises the stream.  RX_EINVAL without the FD form, RX_ESTATE with fewer
  * than 2 blocks. */
 rx_status rx_clock_estimate(rx_handle *h, double *ppm, double *delay, void *cuda_stream);
+
+/* Running ADC clock estimate (rx_config.clk_track = 1): the band-edge delays of every
+ * call's frequency-domain blocks (as in rx_clock_estimate), unwrapped across buffers
+ * (the first block of a call against the last of the previous one; Sec. 2 unwraps the
+ * clock phase with the previous buffer's stream), fitted by one least-squares line
+ * over all blocks since the stream start or the last re-timing.  *ppm, *delay as in
+ * rx_clock_estimate (with the resampler on: the residual against its accumulator);
+ * *nblocks the blocks fitted.  Synchronises the stream.  RX_EINVAL without
+ * clk_track, RX_ESTATE with fewer than 2 blocks. */
+rx_status rx_clock_track(rx_handle *h, double *ppm, double *delay, int64_t *nblocks, void *cuda_stream);
+
+/* Closed clock loop, run between calls (KK chain with the resampler and clk_track):
+ * the running fit y(c) = y0 + s c of the unwrapped block delays (the symbol grid sits
+ * at resampled positions congruent to y mod 4) re-times the resampler from the next
+ * nominal sample r on: the step becomes round(step (1 + s)) and the accumulator at r
+ * moves by round(w step), w = y(r) wrapped into (-2, 2] (whole symbols are not
+ * observable and are left alone); halves round away from zero.  The tracker then
+ * restarts.  *step_out / *nudge_out (nullable) receive the applied values.
+ * Synchronises the stream.  RX_EINVAL without the resampler or clk_track, RX_ESTATE
+ * with fewer than 2 blocks, RX_EBOUNDS when the step would leave 1 % of 2^32. */
+rx_status rx_clock_retime(rx_handle *h, int64_t *step_out, int64_t *nudge_out, void *cuda_stream);
+
+/* Re-time the resampler by hand from the next nominal sample on: its accumulator
+ * moves by nudge (units of 2^-32 ADC samples, |nudge| < 2^36) and then advances by
+ * step per nominal sample (within 1 % of 2^32).  The clock tracker restarts.
+ * Synchronises the stream.  RX_EINVAL without the resampler or out of range. */
+rx_status rx_set_resampler(rx_handle *h, int64_t step, int64_t nudge, void *cuda_stream);
 
 /* Self-test of the bounded device waits: one CTA waits for an mbarrier phase that
  * nothing completes, gives up after a bounded number of polls (as every wait of the

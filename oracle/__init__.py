@@ -31,7 +31,7 @@ class OrxCfg(C.Structure):
         ("mu", C.c_double), ("mu_train", C.c_double), ("mu_cma", C.c_double),
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
         ("eq_frozen", C.c_int32), ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
-        ("pad_rs", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
+        ("clk_track", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
     ]
 
 
@@ -96,6 +96,12 @@ def lib():
         L.orx_process.restype = C.c_int64
         L.orx_flush.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
         L.orx_flush.restype = C.c_int64
+        L.orx_clock_track.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orx_clock_track.restype = C.c_int64
+        L.orx_set_rs.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
+        L.orx_set_rs.restype = C.c_int
+        L.orx_clock_retime.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orx_clock_retime.restype = C.c_int
         L.orx_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, P(C.c_int64)]
         L.orx_get.restype = C.c_int64
         L.orx_set_taps.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
@@ -276,12 +282,12 @@ def cnn_param_slices():
 KK_DEFAULTS = dict(sps=4, pack_order=0, ols_n=65536, ols_v=4096, ds_num=11, ds_den=80,
                    rrc_beta=0.1, mf_span=16, ntaps=31, ntrain=16384, ncma=8192, eq_block=128,
                    win=64, mu=1e-3, mu_train=1e-3, mu_cma=1e-3, bps_b=32, amb_syms=1024,
-                   prbs_seed=1, eq_frozen=0, mf_mode=0, fd_n=1024, fd_taps=203, pad_rs=0, rs_step=0,
+                   prbs_seed=1, eq_frozen=0, mf_mode=0, fd_n=1024, fd_taps=203, clk_track=0, rs_step=0,
                    rs_phase0=0)
 PAM_DEFAULTS = dict(sps=2, pack_order=0, ols_n=0, ols_v=0, ds_num=0, ds_den=1, rrc_beta=0.1,
                     mf_span=16, ntaps=15, ntrain=4096, ncma=0, eq_block=256, win=64, mu=1e-3,
                     mu_train=1e-3, mu_cma=0.0, bps_b=1, amb_syms=0, prbs_seed=1, eq_frozen=0, mf_mode=0,
-                    fd_n=1024, fd_taps=503, pad_rs=0, rs_step=0, rs_phase0=0)
+                    fd_n=1024, fd_taps=503, clk_track=0, rs_step=0, rs_phase0=0)
 
 
 def default_cfg(fmt: int, buf_len: int, **kw) -> dict:
@@ -323,6 +329,23 @@ class Oracle:
         out = np.zeros((cap + 7) // 8, dtype=np.uint8)
         nbits = lib().orx_flush(self._h, _ptr(out), cap)
         return out[: (nbits + 7) // 8].copy(), int(nbits)
+
+    def clock_track(self):
+        """(ppm, delay, blocks) of the clock tracker's running fit (clk_track=1), or None."""
+        ppm, dl = C.c_double(), C.c_double()
+        n = lib().orx_clock_track(self._h, C.byref(ppm), C.byref(dl))
+        return None if n < 0 else (ppm.value, dl.value, int(n))
+
+    def set_rs(self, step: int, nudge: int = 0):
+        if lib().orx_set_rs(self._h, int(step), int(nudge)) != 0:
+            raise ValueError("resampler step rejected")
+
+    def clock_retime(self):
+        """Closed loop: re-time the resampler from the tracker; returns (step, nudge)."""
+        st, nu = C.c_int64(), C.c_int64()
+        if lib().orx_clock_retime(self._h, C.byref(st), C.byref(nu)) != 0:
+            raise ValueError("no retime (no resampler or too few blocks)")
+        return int(st.value), int(nu.value)
 
     def get(self, what: int):
         start = C.c_int64(0)

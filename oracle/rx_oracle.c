@@ -343,6 +343,15 @@ struct orx {
     int32_t *chist; int64_t chist_len, chist_cap;
     int have_first; int32_t first_code;
     int flushed;                   /* the stream has ended (orx_flush) */
+    /* resampler accumulator, piecewise: nominal sample m >= rs_r0 lies at ADC position
+     * (rs_psi0 + (m - rs_r0) rs_step) / 2^32; a step change keeps the position of the
+     * next nominal sample (orx_set_rs_step) */
+    int64_t rs_r0, rs_step;
+    __int128 rs_psi0;
+    /* clock tracker across calls (clk_track, frequency-domain form): unwrap carry and
+     * least-squares sums of the unwrapped block delays since the last reset */
+    int ck_have; double ck_y, ck_off, ck_x0;
+    int64_t ck_n; double ck_sx, ck_sy, ck_sxx, ck_sxy;
     int64_t pad_calls;             /* pad buffers run by orx_flush (not counted as input) */
     double last_mu, last_sd;       /* PAM: normalisation of the last real buffer */
     cx *ehist; int64_t ehist_start, ehist_len;
@@ -379,7 +388,7 @@ orx *orx_create(const orx_cfg *cfg)
         (f >= 3 && (cfg->ncma < 0 || cfg->ncma > cfg->ntrain || cfg->ncma % cfg->win || cfg->bps_b < 1 ||
                     cfg->ds_den < 1 || cfg->ols_n < 4 || (cfg->ols_n & (cfg->ols_n - 1)) ||
                     cfg->ols_v < 2 || (cfg->ols_v & 1) || cfg->ols_v >= cfg->ols_n)) ||
-        cfg->mf_mode < 0 || cfg->mf_mode > 1 ||
+        cfg->mf_mode < 0 || cfg->mf_mode > 1 || cfg->clk_track < 0 || cfg->clk_track > 1 || (cfg->clk_track && cfg->mf_mode != 1) ||
         (cfg->rs_step != 0 && (f < 3 || cfg->rs_step < (int64_t)4252017623LL || cfg->rs_step > (int64_t)4337916969LL)) ||
         (cfg->mf_mode == 1 && (cfg->sps != (f >= 3 ? 4 : 2) || cfg->fd_n < 16 || (cfg->fd_n & (cfg->fd_n - 1)) ||
                                cfg->fd_taps < 1 || !(cfg->fd_taps & 1) || cfg->fd_taps > cfg->fd_n / 2 + 1))) {
@@ -406,6 +415,9 @@ orx *orx_create(const orx_cfg *cfg)
     h->rrc = xcalloc((size_t)(2 * h->hmf + 1), sizeof(double));
     orx_rrc(cfg->rrc_beta, cfg->sps, cfg->mf_span, h->rrc);
     h->rs = cfg->rs_step != 0;
+    h->rs_r0 = 0;
+    h->rs_step = cfg->rs_step;
+    h->rs_psi0 = (__int128)cfg->rs_phase0;
     h->fd = cfg->mf_mode == 1;
     if (h->fd) {
         double *hf = xcalloc((size_t)cfg->fd_taps, sizeof(double));
@@ -611,6 +623,38 @@ static void put_bit(uint8_t *out, int64_t t, int bit)
     if (bit) out[t >> 3] |= (uint8_t)(0x80u >> (t & 7));
 }
 
+/* resampler accumulator at nominal sample m (>= rs_r0), in units of 2^-32 ADC samples */
+static __int128 rs_psi(const orx *h, int64_t m) { return h->rs_psi0 + (__int128)(m - h->rs_r0) * h->rs_step; }
+/* #{m >= 0 : accumulator(m) < lim}, for lim at or beyond the accumulator at rs_r0 */
+static int64_t rs_below(const orx *h, __int128 lim)
+{
+    __int128 d = lim - h->rs_psi0;
+    if (d <= 0) return h->rs_r0;
+    return h->rs_r0 + (int64_t)((d + h->rs_step - 1) / h->rs_step);
+}
+
+/* Clock tracker (frequency-domain form): the block delays d_b = -(P / 2 pi) arg C_b of
+ * every call, unwrapped against the last block of the previous call (period P = sps
+ * samples, as within a call), feed least-squares sums over the blocks since the last
+ * reset; x is the block centre (N/2) b + N/4 relative to the first block's. */
+static void clock_track(orx *h, const cx *C, int64_t b0, int64_t nblk, int N, int sps)
+{
+    const double P = (double)sps, H = 0.5 * P;
+    for (int64_t i = 0; i < nblk; i++) {
+        double d = -P / (2.0 * PI) * atan2(C[i].im, C[i].re);
+        double off = h->ck_have ? h->ck_off : 0.0;
+        if (h->ck_have) {
+            if (d + off - h->ck_y > H) off -= P;
+            else if (d + off - h->ck_y < -H) off += P;
+        }
+        double y = d + off, c = (double)(N / 2) * (double)(b0 + i) + (double)(N / 4);
+        if (h->ck_n == 0) h->ck_x0 = c;
+        double x = c - h->ck_x0;
+        h->ck_sx += x; h->ck_sy += y; h->ck_sxx += x * x; h->ck_sxy += x * y; h->ck_n++;
+        h->ck_y = y; h->ck_off = off; h->ck_have = 1;
+    }
+}
+
 /* One buffer through the chain.  `flush` marks a pad buffer of the stream end
  * (orx_flush): the carrier and gain (KK) or mean and deviation (PAM) stay those
  * of the last real buffer, and windows reaching symbol score_end are decided but
@@ -634,8 +678,7 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
      * i_m = floor((rs_phase0 + m rs_step) / 2^32): r_k = #{m >= 0 : i_m + 8 < e_k} */
     int64_t r_k = e_k;
     if (h->rs) {
-        __int128 lim = ((__int128)(e_k - 8) << 32) - (__int128)c->rs_phase0;   /* m rs_step < lim */
-        r_k = lim <= 0 ? 0 : (int64_t)((lim + c->rs_step - 1) / c->rs_step);
+        r_k = rs_below(h, (__int128)(e_k - 8) << 32);
         if (r_k < h->r_prev) r_k = h->r_prev;
     }
     int64_t f_k = (r_k >= h->hmf + 1) ? (r_k - h->hmf - 1) / h->dec + 1 : 0;
@@ -685,7 +728,7 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
     X.R_start = h->r_prev; X.R_len = h->rs ? r_k - h->r_prev : 0;
     X.R = xcalloc((size_t)(X.R_len > 0 ? X.R_len : 1), sizeof(cx));
     for (int64_t m = h->r_prev; m < r_k && h->rs; m++) {
-        __int128 psi = (__int128)c->rs_phase0 + (__int128)m * c->rs_step;
+        __int128 psi = rs_psi(h, m);
         int64_t i = (int64_t)(psi >> 32);
         uint32_t fr = (uint32_t)(psi & 0xFFFFFFFF);
         double cj[16];
@@ -734,6 +777,7 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
             for (int m = 0; m < N / 2; m++) X.y[(int64_t)hop * b + m - X.y_start] = cx_mk(yr[m], 0.0);
         }
         free(xr); free(xi); free(yr); free(yi);
+        if (c->clk_track) clock_track(h, h->d_C, h->d_C_start, h->d_C_len, N, 2);
     } else if (h->fd) {
         /* static frequency-domain filter, N-point blocks with hop N/2, bin-truncation
          * downsampling; the block input is the carrier-removed, downshifted field */
@@ -765,6 +809,7 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
                 X.y[(int64_t)(hop / 2) * b + m - X.y_start] = cx_scale(cx_mk(yr[m], yi[m]), h->gain);
         }
         free(xr); free(xi); free(yr); free(yi);
+        if (c->clk_track) clock_track(h, h->d_C, h->d_C_start, h->d_C_len, N, 4);
     }
     for (int64_t m = h->fd ? f_k : h->f_prev; m < f_k; m++) {
         cx acc = cx_mk(0.0, 0.0);
@@ -979,8 +1024,9 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
     }
     if (h->kk && e_k > 0) {
         int64_t lo = h->fd ? (int64_t)h->dec * f_k - c->fd_n / 4 : (int64_t)h->dec * f_k - h->hmf;
-        if (h->rs)   /* the resampler's next input: from i at nominal r_k, less 7 */
-            lo = (int64_t)((((__int128)c->rs_phase0 + (__int128)r_k * c->rs_step) >> 32)) - 7;
+        if (h->rs)   /* the resampler's next input: from i at nominal r_k, less 7, and less 4
+                      * more for a re-timing between calls (its nudge is within half a symbol) */
+            lo = (int64_t)(rs_psi(h, r_k) >> 32) - 11;
         if (lo < 0) lo = 0;
         if (lo > e_k) lo = e_k;
         cx *nh = xcalloc((size_t)(e_k - lo + 1), sizeof(cx));
@@ -1031,10 +1077,7 @@ int64_t orx_flush(orx *h, uint8_t *bits_out, int64_t bits_cap)
     h->flushed = 1;
     if (h->calls == 0) return 0;
     int64_t total = h->calls * c->buf_len, r_end = total;
-    if (h->rs) {
-        __int128 lim = ((__int128)total << 32) - (__int128)c->rs_phase0;
-        r_end = lim <= 0 ? 0 : (int64_t)((lim + c->rs_step - 1) / c->rs_step);
-    }
+    if (h->rs) r_end = rs_below(h, (__int128)total << 32);
     int64_t S = r_end > 0 ? (r_end - 1) / c->sps + 1 : 0;
     int64_t first = h->q_prev > c->ntrain ? h->q_prev : c->ntrain;
     if (S <= first) return 0;
@@ -1070,6 +1113,62 @@ int64_t orx_flush(orx *h, uint8_t *bits_out, int64_t bits_cap)
     }
     free(pad); free(tmp);
     return done;
+}
+
+/* The tracker's line fit over the blocks since the last reset (the convention of
+ * orx_clock_fit: d_b = -tau0 - eps c_b, c_b the block centre): ppm = 1e6 eps and the
+ * delay at stream index 0, in (-sps/2, sps/2].  Returns the block count, -1 below 2. */
+int64_t orx_clock_track(const orx *h, double *ppm, double *delay)
+{
+    if (h->ck_n < 2) return -1;
+    const double P = (double)h->c.sps, H = 0.5 * P, nb = (double)h->ck_n;
+    double slope = (nb * h->ck_sxy - h->ck_sx * h->ck_sy) / (nb * h->ck_sxx - h->ck_sx * h->ck_sx);
+    double tau0 = -((h->ck_sy - slope * h->ck_sx) / nb - slope * h->ck_x0);
+    while (tau0 > H) tau0 -= P;
+    while (tau0 <= -H) tau0 += P;
+    *ppm = -slope * 1e6;
+    *delay = tau0;
+    return h->ck_n;
+}
+
+/* New resampler accumulator from the next nominal sample r on: its ADC position moves
+ * by `nudge` (2^-32 ADC samples) and later samples advance by `step`.  The tracker
+ * restarts (sums and unwrap carry): later estimates are residuals against it. */
+int orx_set_rs(orx *h, int64_t step, int64_t nudge)
+{
+    if (!h->rs || step < (int64_t)4252017623LL || step > (int64_t)4337916969LL) return -1;
+    h->rs_psi0 = rs_psi(h, h->r_prev) + (__int128)nudge;
+    h->rs_r0 = h->r_prev;
+    h->rs_step = step;
+    h->ck_n = 0; h->ck_sx = h->ck_sy = h->ck_sxx = h->ck_sxy = 0.0;
+    h->ck_have = 0;
+    return 0;
+}
+
+/* Closed loop (a second-order timing loop run between calls): the tracker's line
+ * y(c) = y0 + s (c - x0) of the unwrapped block delays (the symbol grid sits at
+ * resampled sample positions congruent to y mod P) re-times the accumulator from the
+ * next nominal sample r: the grid drifts by s samples per sample, so the step scales
+ * to round(step (1 + s)), and the grid is off by y(r) now, so the position moves by
+ * round(w step) with w = y(r) wrapped into (-P/2, P/2] (whole symbols are not
+ * observable and are left alone).  Halves round away from zero.  Returns 0, or -1 (no
+ * resampler, fewer than 2 blocks, or a step outside 1 % of 2^32); *step_out and
+ * *nudge_out receive the applied values. */
+int orx_clock_retime(orx *h, int64_t *step_out, int64_t *nudge_out)
+{
+    if (!h->rs || h->ck_n < 2) return -1;
+    const double P = (double)h->c.sps, H = 0.5 * P, nb = (double)h->ck_n;
+    double s = (nb * h->ck_sxy - h->ck_sx * h->ck_sy) / (nb * h->ck_sxx - h->ck_sx * h->ck_sx);
+    double y0 = (h->ck_sy - s * h->ck_sx) / nb;
+    double w = y0 + s * ((double)h->r_prev - h->ck_x0);
+    w -= P * floor(w / P);          /* [0, P) */
+    if (w > H) w -= P;              /* (-P/2, P/2] */
+    int64_t step = (int64_t)llround((double)h->rs_step * (1.0 + s));
+    int64_t nudge = (int64_t)llround(w * (double)h->rs_step);
+    if (orx_set_rs(h, step, nudge) != 0) return -1;
+    if (step_out) *step_out = step;
+    if (nudge_out) *nudge_out = nudge;
+    return 0;
 }
 
 int64_t orx_get(orx *h, int what, void *dst, int64_t cap, int64_t *start)

@@ -54,7 +54,7 @@ typedef struct {
                             input rate (fd_n-point inverse)                              */
     int32_t fd_n;        /* frequency-domain block length (power of two, >= 16)           */
     int32_t fd_taps;     /* frequency-domain filter taps (odd, <= fd_n/2 + 1)             */
-    int32_t pad_rs;
+    int32_t clk_track;   /* clock tracker across calls (frequency-domain form only): 1 on       */
     int64_t rs_step;     /* KK resampler to the transmitter's sample grid: 0 off; else the
                             ADC position of nominal sample m is (rs_phase0 + m rs_step) /
                             2^32 ADC samples (exact integer accumulator)                 */
@@ -105,6 +105,14 @@ int64_t orx_process(orx *h, const uint8_t *packed, uint8_t *bits_out, int64_t bi
 /* end of the stream: decide the held-back symbols; returns the bits written, and
  * orx_process returns -1 afterwards */
 int64_t orx_flush(orx *h, uint8_t *bits_out, int64_t bits_cap);
+/* clock tracker across calls (cfg.clk_track = 1, mf_mode = 1): the running line fit;
+ * returns the block count or -1 */
+int64_t orx_clock_track(const orx *h, double *ppm, double *delay);
+/* resampler from the next nominal sample on: position moved by nudge (2^-32 samples),
+ * then step per nominal sample; 0 or -1 */
+int     orx_set_rs(orx *h, int64_t step, int64_t nudge);
+/* closed loop: re-time the resampler (step and position) from the tracker; 0 or -1 */
+int     orx_clock_retime(orx *h, int64_t *step_out, int64_t *nudge_out);
 int64_t orx_get(orx *h, int what, void *dst, int64_t cap, int64_t *start);
 void    orx_set_taps(orx *h, const double *re, const double *im, int n);
 void    orx_stats(orx *h, orx_stats_t *out);

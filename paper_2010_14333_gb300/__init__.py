@@ -33,7 +33,7 @@ class RxConfig(C.Structure):
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
         ("debug", C.c_int32), ("fir_prec", C.c_int32), ("kk_front", C.c_int32), ("eq_warps", C.c_int32),
         ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
-        ("pad_rs", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
+        ("clk_track", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
         ("cnn_bf16", C.c_int32), ("pad_cnn", C.c_int32), ("deadline_ms", C.c_double),
     ]
 
@@ -60,7 +60,8 @@ EXPORTED = sorted(["rx_selftest_wait_timeout", "rx_clock_estimate", "rx_default_
                    "rx_cnn_set_params", "rx_cnn_get_params", "rx_cnn_forward", "rx_cnn_grad",
                    "rx_cnn_adam_step", "rx_cnn_destroy", "rx_set_cnn", "rx_process_batch",
                    "rx_process_host_batch", "rx_fir_block", "rx_group_create", "rx_group_process",
-                   "rx_group_tuning", "rx_group_destroy", "rx_flush", "rx_resampler_from_clock"])
+                   "rx_group_tuning", "rx_group_destroy", "rx_flush", "rx_resampler_from_clock",
+                   "rx_clock_track", "rx_clock_retime", "rx_set_resampler"])
 RX_GROUP_GRAPH, RX_GROUP_TUNE = 1, 2
 RX_MF_TIME, RX_MF_FD = 0, 1
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
@@ -81,6 +82,9 @@ def load(path: str = LIB_PATH):
     L.rx_selftest_wait_timeout.argtypes = [vp]
     L.rx_selftest_wait_timeout.restype = C.c_int
     L.rx_clock_estimate.argtypes = [vp, P(C.c_double), P(C.c_double), vp]
+    L.rx_clock_track.argtypes = [vp, P(C.c_double), P(C.c_double), P(i64), vp]
+    L.rx_clock_retime.argtypes = [vp, P(i64), P(i64), vp]
+    L.rx_set_resampler.argtypes = [vp, i64, i64, vp]
     L.rx_create.argtypes = [C.c_int, C.c_double, C.c_double, i64, P(RxConfig), P(vp)]
     L.rx_process.argtypes = [vp, vp, vp, vp, P(i64)]
     L.rx_process_host.argtypes = [vp, vp, vp, vp, P(i64)]
@@ -148,6 +152,24 @@ def rx_clock_estimate(h: int, stream: int = 0):
     ppm, dl = C.c_double(), C.c_double()
     _check(load().rx_clock_estimate(h, C.byref(ppm), C.byref(dl), stream))
     return ppm.value, dl.value
+
+
+def rx_clock_track(h: int, stream: int = 0):
+    """(ppm, delay, blocks) of the running clock estimate across calls (clk_track=1)."""
+    ppm, dl, n = C.c_double(), C.c_double(), C.c_int64()
+    _check(load().rx_clock_track(h, C.byref(ppm), C.byref(dl), C.byref(n), stream))
+    return ppm.value, dl.value, n.value
+
+
+def rx_clock_retime(h: int, stream: int = 0):
+    """Closed clock loop between calls; returns the applied (step, nudge)."""
+    st, nu = C.c_int64(), C.c_int64()
+    _check(load().rx_clock_retime(h, C.byref(st), C.byref(nu), stream))
+    return st.value, nu.value
+
+
+def rx_set_resampler(h: int, step: int, nudge: int = 0, stream: int = 0):
+    _check(load().rx_set_resampler(h, step, nudge, stream))
 
 
 def rx_selftest_wait_timeout(stream: int = 0) -> int:

@@ -113,6 +113,10 @@ struct rx_handle {
     long long flush_score_end; // windows reaching this symbol are not scored
     long long flush_bits;      // bound of the bits rx_flush emits
     long long pad_calls;       // pad calls run by rx_flush (not counted as input)
+    // resampler accumulator, piecewise: nominal sample m >= rs_r0 lies at ADC position
+    // (rs_psi0 + (m - rs_r0) cfg.rs_step) / 2^32 (a re-timing starts a new piece)
+    long long rs_r0;
+    __int128 rs_psi0;
 };
 
 static const int kLatRing = 128;
@@ -261,12 +265,24 @@ static void twiddles(int n, float2 *out)   // e^{-2 pi i k / n}
 struct Sched {
     long long avail, e_k, r_k, f_k, s_k, q_k;
 };
-// nominal samples the resampler can emit from the field [0, e_k): #{m >= 0 :
-// floor((phase0 + m step) / 2^32) + 8 < e_k}, exact in 128-bit integers
-static long long rs_count(const rx_config &c, long long e_k)
+// accumulator of nominal sample m (>= rs_r0) and the count of nominal samples whose
+// accumulator lies below lim (lim at or beyond the accumulator at rs_r0), exact in
+// 128-bit integers
+static __int128 rs_psi(const rx_handle *h, long long m)
 {
-    __int128 lim = ((__int128)(e_k - 8) << 32) - (__int128)c.rs_phase0;
-    return lim <= 0 ? 0 : (long long)((lim + c.rs_step - 1) / c.rs_step);
+    return h->rs_psi0 + (__int128)(m - h->rs_r0) * h->cfg.rs_step;
+}
+static long long rs_below(const rx_handle *h, __int128 lim)
+{
+    __int128 d = lim - h->rs_psi0;
+    if (d <= 0) return h->rs_r0;
+    return h->rs_r0 + (long long)((d + h->cfg.rs_step - 1) / h->cfg.rs_step);
+}
+// nominal samples the resampler can emit from the field [0, e_k): #{m >= 0 :
+// floor(psi_m / 2^32) + 8 < e_k}
+static long long rs_count(const rx_handle *h, long long e_k)
+{
+    return rs_below(h, (__int128)(e_k - 8) << 32);
 }
 static Sched schedule(const rx_handle *h, long long calls, long long q_prev)
 {
@@ -274,7 +290,8 @@ static Sched schedule(const rx_handle *h, long long calls, long long q_prev)
     s.avail = (calls + 1) * h->nb;
     s.e_k = h->kk ? s.avail - h->V / 2 : s.avail;
     if (s.e_k < 0) s.e_k = 0;
-    s.r_k = h->rs ? rs_count(h->cfg, s.e_k) : s.e_k;   // the filter's input on its own grid
+    s.r_k = h->rs ? rs_count(h, s.e_k) : s.e_k;   // the filter's input on its own grid
+    if (h->rs && s.r_k < h->r_prev) s.r_k = h->r_prev;
     s.f_k = (s.r_k >= h->hmf + 1) ? (s.r_k - h->hmf - 1) / h->decim + 1 : 0;
     if (h->fd) {   // whole frequency-domain blocks: block b reads up to N/2 b + 3N/4
         long long N = h->cfg.fd_n, bk = (s.r_k >= 3 * N / 4) ? (s.r_k - 3 * N / 4) / (N / 2) + 1 : 0;
@@ -311,6 +328,84 @@ __global__ void k_pad_fill(uint8_t *dst, long long nbytes, const uint8_t *hist_e
     }
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nbytes; i += (long long)gridDim.x * blockDim.x)
         dst[i] = pat[i % 3];
+}
+
+// Clock tracker across calls (one CTA): the band-edge delay d_b = -(P / 2 pi) arg C_b of
+// each of this call's nblk blocks (global block index b0 + i, centre (N/2) b + N/4),
+// unwrapped block to block (one period P added or taken away when consecutive delays
+// differ by more than P/2; the first block against the previous call's last), and the
+// least-squares sums over the unwrapped delays, x relative to the first block since
+// the last reset.  Thread t takes a contiguous run of blocks; the period counts are
+// scanned across threads and the sums reduced in a fixed order.
+constexpr int kCkThreads = 256;
+__device__ __forceinline__ double ck_delay(float2 c, double P)
+{
+    return -P / (2.0 * 3.14159265358979323846) * atan2((double)c.y, (double)c.x);
+}
+__global__ void __launch_bounds__(kCkThreads) k_clock_track(const float2 *__restrict__ clk, int nblk, long long b0,
+                                                           int N, int P, DevState *dst)
+{
+    __shared__ int s_k[kCkThreads];
+    __shared__ double s_r[4][kCkThreads];
+    ClockTrack *ck = &dst->ck;
+    const double Pd = (double)P, H = 0.5 * Pd;
+    const int t = threadIdx.x, per = (nblk + kCkThreads - 1) / kCkThreads;
+    const int lo = min(t * per, nblk), hi = min(lo + per, nblk);
+    const int have = ck->have;
+    const double dcarry = ck->y - ck->off;   // the previous call's last raw delay
+    // period steps: k_i = -1 when d_i - d_{i-1} > P/2, +1 below -P/2
+    int ksum = 0;
+    double dprev = lo > 0 ? ck_delay(clk[lo - 1], Pd) : dcarry;
+    for (int i = lo; i < hi; i++) {
+        const double d = ck_delay(clk[i], Pd);
+        if (i > 0 || have) ksum += (d - dprev > H) ? -1 : (d - dprev < -H) ? 1 : 0;
+        dprev = d;
+    }
+    s_k[t] = ksum;
+    __syncthreads();
+    int pre = 0;
+    for (int j = 0; j < t; j++) pre += s_k[j];
+    const double x0 = ck->n > 0 ? ck->x0 : (double)(N / 2) * (double)b0 + (double)(N / 4);
+    const double off0 = have ? ck->off : 0.0;
+    double sx = 0, sy = 0, sxx = 0, sxy = 0, ylast = 0, offlast = 0;
+    int kk = pre;
+    dprev = lo > 0 ? ck_delay(clk[lo - 1], Pd) : dcarry;
+    for (int i = lo; i < hi; i++) {
+        const double d = ck_delay(clk[i], Pd);
+        if (i > 0 || have) kk += (d - dprev > H) ? -1 : (d - dprev < -H) ? 1 : 0;
+        dprev = d;
+        const double off = off0 + Pd * (double)kk, y = d + off;
+        const double x = (double)(N / 2) * (double)(b0 + i) + (double)(N / 4) - x0;
+        sx += x;
+        sy += y;
+        sxx += x * x;
+        sxy += x * y;
+        ylast = y;
+        offlast = off;
+    }
+    s_r[0][t] = sx;
+    s_r[1][t] = sy;
+    s_r[2][t] = sxx;
+    s_r[3][t] = sxy;
+    __syncthreads();
+    for (int w = kCkThreads / 2; w > 0; w >>= 1) {
+        if (t < w)
+            for (int q = 0; q < 4; q++) s_r[q][t] += s_r[q][t + w];
+        __syncthreads();
+    }
+    if (t == 0) {
+        ck->x0 = x0;
+        ck->sx += s_r[0][0];
+        ck->sy += s_r[1][0];
+        ck->sxx += s_r[2][0];
+        ck->sxy += s_r[3][0];
+        ck->n += nblk;
+    }
+    if (nblk > 0 && hi == nblk && lo < hi) {   // the thread holding the last block
+        ck->y = ylast;
+        ck->off = offlast;
+        ck->have = 1;
+    }
 }
 
 // self-test of the bounded waits: a phase that nothing completes
@@ -482,6 +577,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         return RX_EINVAL;
     if (c.rs_step != 0 && (!kk || c.rs_step < 4252017623LL || c.rs_step > 4337916969LL)) return RX_EINVAL;
     if (c.cnn_bf16 < 0 || c.cnn_bf16 > 1 || !(c.deadline_ms == c.deadline_ms)) return RX_EINVAL;
+    if (c.clk_track < 0 || c.clk_track > 1 || (c.clk_track && c.mf_mode != RX_MF_FD)) return RX_EINVAL;
     if (c.mf_mode < RX_MF_TIME || c.mf_mode > RX_MF_FD ||
         (c.mf_mode == RX_MF_FD && (c.fd_n < 16 || c.fd_n > kEHist || (c.fd_n & (c.fd_n - 1)) ||
                                    (!kk && c.fd_n != 1024) || c.fd_taps < 1 || !(c.fd_taps & 1) ||
@@ -727,6 +823,8 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         rx_destroy(h);
         return RX_ECUDA;
     }
+    h->rs_r0 = 0;
+    h->rs_psi0 = (__int128)c.rs_phase0;
     h->ebase_cur = -kEHist;
     h->rbase_cur = -kEHist;
     h->ybase_cur = -kYHist;
@@ -912,7 +1010,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     // matched filter (after the resampler when the ADC clock is not the transmitter's)
     prof_begin(h, 4, sm);
     if (e == cudaSuccess && h->kk && h->rs && s.r_k > h->r_prev) {
-        const __int128 psi = (__int128)c.rs_phase0 + (__int128)h->r_prev * c.rs_step;
+        const __int128 psi = rs_psi(h, h->r_prev);
         const long long rb = h->r_prev - kEHist;
         e = launch_kk_resample(h->E[h->ew], h->ebase_cur, h->r_prev, s.r_k, (long long)(psi >> 32),
                                (unsigned)(psi & 0xFFFFFFFF), c.rs_step, h->rs_tab, h->R[h->rw ^ 1], rb,
@@ -945,6 +1043,16 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         else
             e = launch_pam_mf(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->rrc, h->hmf, h->st, ppar,
                               (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf);
+        if (e == cudaSuccess && h->fd && c.clk_track) {
+            // blocks of this call: outputs at 2 samples/symbol per block N/4 (KK) or N/2 (PAM)
+            const long long per = h->kk ? c.fd_n / 4 : c.fd_n / 2;
+            const long long nblk = (s.f_k - h->f_prev) / per;
+            if (nblk > 0) {
+                k_clock_track<<<1, kCkThreads, 0, h->kk ? sm : sf>>>(h->clk, (int)nblk, h->f_prev / per, c.fd_n,
+                                                                    h->sps, h->st);
+                e = cudaGetLastError();
+            }
+        }
         h->yw = yw_new;
         h->ybase_cur = yb;
     }
@@ -1134,10 +1242,7 @@ rx_status rx_flush(rx_handle *h, uint8_t *bits_out, void *stream, int64_t *nbits
     // symbols whose centre lies inside the stream: nominal samples [0, r_end)
     const long long total = h->calls * h->nb;
     long long r_end = total;
-    if (h->rs) {
-        __int128 lim = ((__int128)total << 32) - (__int128)c.rs_phase0;   // m rs_step < lim
-        r_end = lim <= 0 ? 0 : (long long)((lim + c.rs_step - 1) / c.rs_step);
-    }
+    if (h->rs) r_end = rs_below(h, (__int128)total << 32);
     const long long S = r_end > 0 ? (r_end - 1) / h->sps + 1 : 0;
     const long long first = h->q_prev > c.ntrain ? h->q_prev : (long long)c.ntrain;
     if (S <= first) return RX_OK;
@@ -1288,6 +1393,78 @@ rx_status rx_clock_estimate(rx_handle *h, double *ppm, double *delay, void *stre
     while (tau0 <= -Hp) tau0 += P;
     *ppm = -slope * 1e6;
     *delay = tau0;
+    return RX_OK;
+}
+
+// the tracker state after everything enqueued on the stream
+static rx_status read_track(rx_handle *h, void *stream, ClockTrack *ck)
+{
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return RX_ECUDA;
+    if (cudaMemcpy(ck, &h->st->ck, sizeof *ck, cudaMemcpyDeviceToHost) != cudaSuccess) return RX_ECUDA;
+    return RX_OK;
+}
+
+rx_status rx_clock_track(rx_handle *h, double *ppm, double *delay, int64_t *nblocks, void *stream)
+{
+    if (!h || !ppm || !delay || !h->cfg.clk_track) return RX_EINVAL;
+    ClockTrack ck;
+    rx_status r = read_track(h, stream, &ck);
+    if (r != RX_OK) return r;
+    if (nblocks) *nblocks = ck.n;
+    if (ck.n < 2) return RX_ESTATE;
+    // the line d = -delay - 1e-6 ppm c over the block centres c, delay at stream index 0
+    const double P = (double)h->sps, Hp = 0.5 * P, n = (double)ck.n;
+    const double slope = (n * ck.sxy - ck.sx * ck.sy) / (n * ck.sxx - ck.sx * ck.sx);
+    double tau0 = -((ck.sy - slope * ck.sx) / n - slope * ck.x0);
+    while (tau0 > Hp) tau0 -= P;
+    while (tau0 <= -Hp) tau0 += P;
+    *ppm = -slope * 1e6;
+    *delay = tau0;
+    return RX_OK;
+}
+
+// new piece of the resampler accumulator from the next nominal sample on, and a
+// restart of the clock tracker
+static rx_status apply_resampler(rx_handle *h, long long step, long long nudge, cudaStream_t st)
+{
+    if (step < 4252017623LL || step > 4337916969LL) return RX_EBOUNDS;
+    h->rs_psi0 = rs_psi(h, h->r_prev) + (__int128)nudge;
+    h->rs_r0 = h->r_prev;
+    h->cfg.rs_step = step;
+    if (cudaMemsetAsync(&h->st->ck, 0, sizeof(ClockTrack), st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RX_ECUDA;
+    return RX_OK;
+}
+
+rx_status rx_set_resampler(rx_handle *h, int64_t step, int64_t nudge, void *stream)
+{
+    if (!h || !h->rs || nudge <= -(1LL << 36) || nudge >= (1LL << 36)) return RX_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return RX_ECUDA;
+    rx_status r = apply_resampler(h, step, nudge, (cudaStream_t)stream);
+    return r == RX_EBOUNDS ? RX_EINVAL : r;
+}
+
+rx_status rx_clock_retime(rx_handle *h, int64_t *step_out, int64_t *nudge_out, void *stream)
+{
+    if (!h || !h->rs || !h->cfg.clk_track) return RX_EINVAL;
+    ClockTrack ck;
+    rx_status r = read_track(h, stream, &ck);
+    if (r != RX_OK) return r;
+    if (ck.n < 2) return RX_ESTATE;
+    // line y = y0 + s x of the unwrapped delays (x relative to the first block's centre)
+    const double P = (double)h->sps, Hp = 0.5 * P, n = (double)ck.n;
+    const double s = (n * ck.sxy - ck.sx * ck.sy) / (n * ck.sxx - ck.sx * ck.sx);
+    const double y0 = (ck.sy - s * ck.sx) / n;
+    double w = y0 + s * ((double)h->r_prev - ck.x0);
+    w -= P * floor(w / P);
+    if (w > Hp) w -= P;
+    const long long step = llround((double)h->cfg.rs_step * (1.0 + s));
+    const long long nudge = llround(w * (double)h->cfg.rs_step);
+    r = apply_resampler(h, step, nudge, (cudaStream_t)stream);
+    if (r != RX_OK) return r;
+    if (step_out) *step_out = step;
+    if (nudge_out) *nudge_out = nudge;
     return RX_OK;
 }
 

@@ -24,8 +24,17 @@ constexpr int kPrbsWords = 1040;   // PRBS-15 period + 256 bits, bit-packed MSB 
 // counters in DevState::cnt
 enum { C_SYMBOLS, C_BITS, C_BITERR, C_RAWERR, C_SYMERR, C_SLIP, C_NEAR, C_AMBIG, C_WINDOWS, C_NCNT };
 
+// clock tracker across calls: unwrap carry (last unwrapped delay and its offset)
+// and least-squares sums of the unwrapped block delays since the last reset
+struct ClockTrack {
+    int have, pad;
+    long long n;
+    double y, off, x0, sx, sy, sxx, sxy;
+};
+
 // device-resident state of one stream
 struct DevState {
+    ClockTrack ck;
     unsigned long long cnt[C_NCNT];
     double cg[kSlots][4];                  // KK per slot: carrier re, carrier im, gain
     double cg_flush[4];                    // KK: carrier and gain of the last real buffer (flush)

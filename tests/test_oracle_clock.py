@@ -120,3 +120,80 @@ def test_pam_off_clock_with_isi():
     g = synth.gen_pam_stream(1, nb, 2, seed=3, clock_step=synth.clock_step(-35.0), clock_phase0=0)
     p, _ = _estimate_pam(g, 1, nb, 2)
     assert abs(p + 35.0) < 0.5, p
+
+
+# ------------------------------------------------------------ tracking across calls
+TRK = dict(ols_n=4096, ols_v=512, ntrain=4096, ncma=2048, amb_syms=1024, mf_mode=1, clk_track=1)
+
+
+def _ramp_stream(nb, ppms, seed=9, **gen):
+    """Buffer b sampled by an ADC clock of ppms[b], the accumulator continuous at the
+    buffer edges (a staircase approximation of a drifting clock)."""
+    steps = [synth.clock_step(p) for p in ppms]
+    bufs, ph = [], 0
+    for b in range(len(ppms)):
+        if b > 0:
+            ph += b * nb * (steps[b - 1] - steps[b])
+        bufs.append(synth.kk_buffer(4, nb, b, 0.0, seed=seed, truth=False, clock_step=steps[b],
+                                    clock_phase0=ph, **gen)["packed"])
+    return bufs, steps
+
+
+def test_tracker_equals_one_fit_over_all_calls():
+    """The running estimate after several calls equals the line fit of the same
+    blocks concatenated (orx_clock_fit, which unwraps block to block): the unwrap
+    carries from the last block of a call to the first of the next."""
+    nb = 1 << 17
+    g = synth.gen_kk_stream(4, nb, 4, seed=4, clock_step=synth.clock_step(-35.0), clock_phase0=int(0.3 * 2 ** 32),
+                            truth=False, noise=False, phase_noise=False)
+    o = oracle.Oracle(**oracle.default_cfg(4, nb, **TRK))
+    cs, cents = [], []
+    for p in g["packed"]:
+        o.process(p)
+        c, b0 = o.get(oracle.ORX_CLK)
+        cs.append(c)
+        cents.append(512 * (b0 + np.arange(len(c))) + 256)
+    ppm, dl, n = o.clock_track()
+    ppm_f, dl_f = oracle.clock_fit(np.concatenate(cs), np.concatenate(cents), 4)
+    assert n == sum(len(c) for c in cs) > 500
+    assert abs(ppm - ppm_f) < 1e-9 and abs(dl - dl_f) < 1e-9
+    assert abs(ppm + 35.0) < 0.1 and abs(dl - 0.3) < 0.02
+
+
+def test_retime_with_unchanged_accumulator_changes_nothing():
+    """A re-timing to the same step with no nudge continues the accumulator exactly:
+    every later output equals that of the stream left alone."""
+    nb = 1 << 16
+    step = synth.clock_step(20.0)
+    g = synth.gen_kk_stream(4, nb, 3, seed=6, clock_step=step, truth=False)
+    st, ph = oracle.rs_params(step, 0)
+    outs = []
+    for retime in (False, True):
+        o = oracle.Oracle(**oracle.default_cfg(4, nb, rs_step=st, rs_phase0=ph, **TRK))
+        bits = []
+        for b, p in enumerate(g["packed"]):
+            bits.append(o.process(p)[0])
+            if retime:
+                o.set_rs(st, 0)
+        outs.append((np.concatenate(bits), o.get(oracle.ORX_RS)[0]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_closed_loop_follows_a_drifting_clock():
+    """A noiseless KK-16QAM stream whose ADC clock drifts by 1 ppm per 2^18-sample
+    buffer (-35 to -22 ppm): with the resampler fixed at the starting clock the
+    timing runs off by whole symbols and the decisions fall apart; re-timed after
+    every buffer from the tracker (frequency and phase) every payload bit is right."""
+    nb, nbufs = 1 << 18, 14
+    bufs, steps = _ramp_stream(nb, [-35.0 + b for b in range(nbufs)], noise=False, phase_noise=False)
+    st, ph = oracle.rs_params(steps[0], 0)
+    res = {}
+    for loop in (False, True):
+        o = oracle.Oracle(**oracle.default_cfg(4, nb, rs_step=st, rs_phase0=ph, **TRK))
+        for p in bufs:
+            o.process(p)
+            if loop:
+                o.clock_retime()
+        res[loop] = o.stats()
+    assert res[True]["bits"] > 3_000_000 and res[True]["bit_errors"] == 0
+    assert res[False]["bit_errors"] > 0.1 * res[False]["bits"]
