@@ -103,3 +103,92 @@ def test_pam_estimate_matches_oracle_and_clock(ppm, delay):
     assert abs(gp - op) < 0.01 and abs(gd - od) < 1e-3, (gp, op, gd, od)
     err = (gd - delay + 1.0) % 2.0 - 1.0
     assert abs(gp - ppm) < 0.5 and abs(err) < 0.05, (gp, gd)
+
+
+# ------------------------------------------------------------ tracking across calls
+def _ramp(nb, ppms, seed=9, **kw):
+    steps = [synth.clock_step(p) for p in ppms]
+    bufs, ph = [], 0
+    for b in range(len(ppms)):
+        if b > 0:
+            ph += b * nb * (steps[b - 1] - steps[b])
+        bufs.append(synth.kk_buffer(4, nb, b, 0.0, seed=seed, truth=False, clock_step=steps[b], clock_phase0=ph,
+                                    **kw)["packed"])
+    return bufs, steps
+
+
+def test_running_estimate_matches_oracle_tracker():
+    """KK with the resampler and PAM-4: after every call the GPU's running estimate
+    (blocks unwrapped across calls, one line fit) equals the oracle tracker's within
+    0.01 ppm and 1e-3 samples, over the same number of blocks."""
+    sid = torch.cuda.current_stream().cuda_stream
+    nb = 1 << 17
+    step = synth.clock_step(-35.0)
+    st, ph = oracle.rs_params(synth.clock_step(-30.0), 0)   # a resampler 5 ppm off the clock
+    g = gen(-35.0, 0.4, nb, 4)
+    p = Pair(4, nb, mf_mode=1, clk_track=1, rs_step=st, rs_phase0=ph, **SMALL_KK)
+    for b in range(4):
+        p.feed(g["packed"][b])
+        gp, gd, gn = rx.rx_clock_track(p.g.h, sid)
+        op, od, on = p.o.clock_track()
+        assert gn == on and abs(gp - op) < 0.01 and abs(gd - od) < 1e-3, (b, gp, op, gd, od)
+    assert abs(gp + 5.0) < 0.2   # the residual of a -35 ppm clock against a -30 ppm resampler
+    gpam = make_stream(1, 1 << 18, 3, clock_step=synth.clock_step(20.0))
+    p = Pair(1, 1 << 18, mf_mode=1, clk_track=1)
+    for b in range(3):
+        p.feed(gpam["packed"][b])
+        gp, gd, gn = rx.rx_clock_track(p.g.h, sid)
+        op, od, on = p.o.clock_track()
+        assert gn == on and abs(gp - op) < 0.01 and abs(gd - od) < 1e-3, (b, gp, op, gd, od)
+
+
+def test_retime_parity_with_oracle():
+    """The GPU closes the loop between calls (rx_clock_retime); the oracle is re-timed
+    with the same integers, and every later call stays at parity (fields, filter
+    output, decisions, counts)."""
+    sid = torch.cuda.current_stream().cuda_stream
+    nb = 1 << 17
+    bufs, steps = _ramp(nb, [-35.0 + 2.0 * b for b in range(6)])
+    st, ph = oracle.rs_params(steps[0], 0)
+    p = Pair(4, nb, mf_mode=1, clk_track=1, rs_step=st, rs_phase0=ph, **SMALL_KK)
+    applied = []
+    for b, buf in enumerate(bufs):
+        p.feed(buf)
+        step, nudge = rx.rx_clock_retime(p.g.h, sid)
+        p.o.set_rs(step, nudge)
+        applied.append((step, nudge))
+    p.compare_stats()
+    assert len({a for a, _ in applied}) > 3   # the step followed the drift
+
+
+def test_closed_loop_follows_a_drifting_clock_on_gpu():
+    """As the oracle pin: 1 ppm per 2^18-sample buffer of drift, re-timed after every
+    buffer by the GPU's own loop: every payload bit right; open loop falls apart."""
+    sid = torch.cuda.current_stream().cuda_stream
+    nb, nbufs = 1 << 18, 14
+    bufs, steps = _ramp(nb, [-35.0 + b for b in range(nbufs)], noise=False, phase_noise=False)
+    st, ph = oracle.rs_params(steps[0], 0)
+    res = {}
+    for loop in (False, True):
+        r = rx.Receiver(4, nb, mf_mode=1, clk_track=1, rs_step=st, rs_phase0=ph, **SMALL_KK)
+        for buf in bufs:
+            r.process(torch.from_numpy(buf).cuda())
+            if loop:
+                rx.rx_clock_retime(r.h, sid)
+        res[loop] = r.stats()
+    assert res[True]["bits"] > 3_000_000 and res[True]["bit_errors"] == 0
+    assert res[False]["bit_errors"] > 0.1 * res[False]["bits"]
+
+
+def test_tracker_argument_errors():
+    nb = 1 << 16
+    r = rx.Receiver(4, nb, **SMALL_KK)
+    with pytest.raises(rx.RxError):
+        rx.rx_clock_track(r.h)
+    with pytest.raises(rx.RxError):
+        rx.rx_clock_retime(r.h)
+    with pytest.raises(rx.RxError):
+        rx.Receiver(4, nb, clk_track=1, **SMALL_KK)   # needs the frequency-domain form
+    r = rx.Receiver(1, nb, mf_mode=1, clk_track=1)
+    with pytest.raises(rx.RxError):
+        rx.rx_clock_retime(r.h)                        # the PAM chain has no resampler
