@@ -277,30 +277,72 @@ __global__ void __launch_bounds__(kCnnThreads)
 
 // shared-memory layout of the backward kernel (bytes)
 struct BwdSmem {
+    static constexpr int LDV = CH + 8;                           // padded rows of the MLP tiles (bf16)
+    static constexpr int LDT = 152;                              // positions of duT (>= 144 + 8)
+    static constexpr int LDH = 160;                              // positions of the transposed layer input
+    static constexpr int NDU = 160;                              // rows of the padded du (8 zero rows first)
     static constexpr int X = 0;                                  // float [L0][2]
-    static constexpr int HIN = X + L0 * 2 * 4;                   // bf16 layer input [L1][32]
-    static constexpr int WB = HIN + L1 * CC * 2;                 // bf16 weights [32][288]
-    static constexpr int DU = WB + CC * KW * 2;                  // float [L1][32]
-    static constexpr int DH = DU + L1 * CC * 4;                  // float [L1][32]
-    static constexpr int DV = DH + L1 * CC * 4;                  // float [S][64]
-    static constexpr int TOTAL = DV + CS * CH * 4;
+    static constexpr int DV = 1280;                              // float [S][64]
+    static constexpr int DVB = DV + CS * CH * 4;                 // bf16 [S][LDV]   dv, rows j
+    static constexpr int DVT = DVB + CS * LDV * 2;               // bf16 [64][LDV]  dv transposed, rows m
+    static constexpr int H3T = DVT + CH * LDV * 2;               // bf16 [32][LDV]  h3 at the symbols, rows c
+    static constexpr int M1T = H3T + CC * LDV * 2;               // bf16 [32][LDV]  M1 transposed, rows c
+    static constexpr int DH = M1T + CC * LDV * 2;                // float [L1][32]  gradient of the layer output
+    static constexpr int DUP = DH + L1 * CC * 4;                 // bf16 [NDU][32]  du from row 8 on
+    static constexpr int DUT = DUP + NDU * CC * 2;               // bf16 [32][LDT]  du transposed
+    static constexpr int HT0 = DUT + CC * LDT * 2;               // bf16 [32][LDH]  layer input transposed
+    static constexpr int HT1 = HT0 + CC * LDH * 2;               // bf16 [32][LDH]  the same from position 1 on
+    static constexpr int RED = HT1 + CC * LDH * 2;               // float [8][32]   bias partials
+    static constexpr int TOTAL = RED + 8 * CC * 4;
 };
+static_assert(BwdSmem::TOTAL <= 113 * 1024, "two backward CTAs per SM");
+static_assert(L1 + 8 <= BwdSmem::LDT && L1 + 16 <= BwdSmem::NDU && L0 <= BwdSmem::LDH,
+              "padded tiles cover the largest layer");
 
-// Backward pass of one segment per CTA: per-segment partial gradient gpart[s][NPRM].
+// one m16n8k16 BF16 product: D += A * B with A row-major (row stride lda elements,
+// even) and B given by its transpose Bt, row-major (row stride ldb, even)
+__device__ __forceinline__ void mma_tile(float (&d)[4], const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt,
+                                         int ldb, int g, int tq)
+{
+    uint32_t a[4];
+    a[0] = *reinterpret_cast<const uint32_t *>(A + lda * g + 2 * tq);
+    a[1] = *reinterpret_cast<const uint32_t *>(A + lda * (g + 8) + 2 * tq);
+    a[2] = *reinterpret_cast<const uint32_t *>(A + lda * g + 2 * tq + 8);
+    a[3] = *reinterpret_cast<const uint32_t *>(A + lda * (g + 8) + 2 * tq + 8);
+    mma_bf16(d, a, *reinterpret_cast<const uint32_t *>(Bt + ldb * g + 2 * tq),
+             *reinterpret_cast<const uint32_t *>(Bt + ldb * g + 2 * tq + 8));
+}
+
+// Backward pass of one segment per CTA (256 threads): per-segment partial gradient
+// gpart[s][NPRM].  The contractions run on the tensor cores with BF16 operands and
+// FP32 accumulation (mma.sync m16n8k16): the MLP's dM1 and the gradient at the
+// layer-3 output; per convolution layer 3 and 2 the weight gradient (K = the
+// positions) and the input gradient (the forward's convolution over the zero-padded
+// du with the tap-flipped, transposed weights wdT).  Elementwise steps (GELU
+// derivatives, dM2, biases) and the 2-channel layer 1 stay in FP32.
 __global__ void __launch_bounds__(256)
-    k_cnn_bwd(const float *__restrict__ prm, const __nv_bfloat16 *__restrict__ prm_bf, const float2 *__restrict__ y,
+    k_cnn_bwd(const float *__restrict__ prm, const __nv_bfloat16 *__restrict__ wdT, const float2 *__restrict__ y,
               const long long *__restrict__ seg_start, const float *__restrict__ tgt, CnnSave sv, float norm,
               float *__restrict__ gpart)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     float *xs = reinterpret_cast<float *>(sm + BwdSmem::X);
-    __nv_bfloat16 *hin = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::HIN);
-    __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::WB);
-    float *du = reinterpret_cast<float *>(sm + BwdSmem::DU);
-    float *dh = reinterpret_cast<float *>(sm + BwdSmem::DH);
     float *dv = reinterpret_cast<float *>(sm + BwdSmem::DV);
-    const int tid = threadIdx.x, nth = blockDim.x;
+    __nv_bfloat16 *dvb = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::DVB);
+    __nv_bfloat16 *dvt = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::DVT);
+    __nv_bfloat16 *h3t = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::H3T);
+    __nv_bfloat16 *m1t = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::M1T);
+    float *dh = reinterpret_cast<float *>(sm + BwdSmem::DH);
+    __nv_bfloat16 *dup = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::DUP);
+    __nv_bfloat16 *dut = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::DUT);
+    __nv_bfloat16 *ht0 = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::HT0);
+    __nv_bfloat16 *ht1 = reinterpret_cast<__nv_bfloat16 *>(sm + BwdSmem::HT1);
+    float *red = reinterpret_cast<float *>(sm + BwdSmem::RED);
+    constexpr int LDV = BwdSmem::LDV, LDT = BwdSmem::LDT, LDH = BwdSmem::LDH, NDU = BwdSmem::NDU;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, tq = lane & 3;
     const int s = blockIdx.x;
+    const __nv_bfloat16 bz = __float2bfloat16(0.f);
     float *G = gpart + (size_t)s * NPRM;
     const long long st = seg_start[s];
     for (int i = tid; i < L0; i += nth) {
@@ -309,7 +351,7 @@ __global__ void __launch_bounds__(256)
         xs[2 * i + 1] = v.y;
     }
     const __nv_bfloat16 *h3 = sv.h3 + (size_t)s * L3 * CC;
-    // ---- MLP head
+    // ---- MLP head: dv = (dout . M2) gelu'(v) in FP32, bf16 copies for the products
     for (int i = tid; i < CS * CH; i += nth) {
         int j = i / CH, m = i - CH * j;
         float o0 = sv.out[((size_t)s * CS + j) * 2], o1 = sv.out[((size_t)s * CS + j) * 2 + 1];
@@ -317,90 +359,143 @@ __global__ void __launch_bounds__(256)
         float d1 = 2.f * (o1 - tgt[((size_t)s * CS + j) * 2 + 1]) * norm;
         float vv = sv.v[((size_t)s * CS + j) * CH + m];
         float dz = d0 * prm[OM2 + m] + d1 * prm[OM2 + CH + m];
-        dv[i] = dz * gelu_df(vv);
+        float d = dz * gelu_df(vv);
+        dv[i] = d;
+        dvb[j * LDV + m] = __float2bfloat16(d);
+        dvt[m * LDV + j] = __float2bfloat16(d);
     }
+    for (int i = tid; i < CC * CS; i += nth) {   // h3 at the symbol positions, transposed
+        int c = i / CS, j = i - CS * c;
+        h3t[c * LDV + j] = h3[(2 * j) * CC + c];
+    }
+    for (int i = tid; i < CC * CH; i += nth) {   // M1 transposed, bf16
+        int c = i / CH, m = i - CH * c;
+        m1t[c * LDV + m] = __float2bfloat16(prm[OM1 + m * CC + c]);
+    }
+    for (int i = tid; i < L3 * CC; i += nth)     // odd positions of h3 feed nothing
+        if ((i >> 5) & 1) dh[i] = 0.f;
     __syncthreads();
-    // dM2, dc2 (z recomputed from v), dM1, dc1
-    for (int i = tid; i < 2 * CH + 2; i += nth) {
+    // dM2, dc2 (z recomputed from v) and dc1 in FP32
+    for (int i = tid; i < 2 * CH + 2 + CH; i += nth) {
         float a = 0.f;
-        for (int j = 0; j < CS; j++) {
-            float o = sv.out[((size_t)s * CS + j) * 2 + (i < 2 * CH ? i / CH : i - 2 * CH)];
-            float d = 2.f * (o - tgt[((size_t)s * CS + j) * 2 + (i < 2 * CH ? i / CH : i - 2 * CH)]) * norm;
-            a += (i < 2 * CH) ? d * gelu_f(sv.v[((size_t)s * CS + j) * CH + (i % CH)]) : d;
-        }
-        G[OM2 + i] = a;   // OC2 follows OM2 contiguously
-    }
-    for (int i = tid; i < CH * CC + CH; i += nth) {
-        float a = 0.f;
-        if (i < CH * CC) {
-            int m = i / CC, c = i - CC * m;
-            for (int j = 0; j < CS; j++) a += dv[j * CH + m] * __bfloat162float(h3[(2 * j) * CC + c]);
-            G[OM1 + i] = a;
+        if (i < 2 * CH + 2) {
+            const int oc = i < 2 * CH ? i / CH : i - 2 * CH;
+            for (int j = 0; j < CS; j++) {
+                float o = sv.out[((size_t)s * CS + j) * 2 + oc];
+                float d = 2.f * (o - tgt[((size_t)s * CS + j) * 2 + oc]) * norm;
+                a += (i < 2 * CH) ? d * gelu_f(sv.v[((size_t)s * CS + j) * CH + (i % CH)]) : d;
+            }
+            G[OM2 + i] = a;   // OC2 follows OM2 contiguously
         } else {
-            int m = i - CH * CC;
+            const int m = i - (2 * CH + 2);
             for (int j = 0; j < CS; j++) a += dv[j * CH + m];
             G[OC1 + m] = a;
         }
     }
-    // dh3 at the symbol positions (zero elsewhere)
-    for (int i = tid; i < L3 * CC; i += nth) {
-        int p = i >> 5, c = i & 31;
-        float a = 0.f;
-        if (!(p & 1)) {
-            int j = p >> 1;
-            for (int m = 0; m < CH; m++) a += prm[OM1 + m * CC + c] * dv[j * CH + m];
+    // tiles 0..15: dM1[m][c] = sum_j dv[j][m] h3[2j][c]   (M = 64 m, N = 32 c, K = 64 j)
+    // tiles 16..31: dh3[2j][c] = sum_m M1[m][c] dv[j][m]   (M = 64 j, N = 32 c, K = 64 m)
+    for (int tile = warp; tile < 32; tile += 8) {
+        const bool second = tile >= 16;
+        const int mt = (tile & 15) >> 2, nt = tile & 3;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const __nv_bfloat16 *A = (second ? dvb : dvt) + LDV * 16 * mt;
+        const __nv_bfloat16 *Bt = (second ? m1t : h3t) + LDV * 8 * nt;
+#pragma unroll
+        for (int k0 = 0; k0 < 64; k0 += 16) mma_tile(acc, A + k0, LDV, Bt + k0, LDV, g, tq);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int r = 16 * mt + g + 8 * (i >> 1), c = 8 * nt + 2 * tq + (i & 1);
+            if (second) dh[(2 * r) * CC + c] = acc[i];
+            else G[OM1 + r * CC + c] = acc[i];
         }
-        dh[i] = a;
     }
     __syncthreads();
-    // ---- conv layers 3, 2, 1
+    // ---- convolution layers 3 and 2 on the tensor cores, layer 1 in FP32
     for (int l = 3; l >= 1; l--) {
         const int Lout = (l == 3) ? L3 : (l == 2) ? L2 : L1;
         const int Lin = Lout + 8;
-        const int Cin = (l == 1) ? 2 : CC;
         const float *U = (l == 3) ? sv.u3 + (size_t)s * L3 * CC : (l == 2) ? sv.u2 + (size_t)s * L2 * CC
                                                                           : sv.u1 + (size_t)s * L1 * CC;
         const int OW = (l == 3) ? OW3 : (l == 2) ? OW2 : OW1, OB = (l == 3) ? OB3 : (l == 2) ? OB2 : OB1;
-        // layer input (bf16) and weights
-        if (l > 1) {
-            const __nv_bfloat16 *src = (l == 3) ? sv.h2 + (size_t)s * L2 * CC : sv.h1 + (size_t)s * L1 * CC;
-            for (int i = tid; i < Lin * CC / 8; i += nth)
-                reinterpret_cast<uint4 *>(hin)[i] = reinterpret_cast<const uint4 *>(src)[i];
-            for (int i = tid; i < CC * KW / 8; i += nth)
-                reinterpret_cast<uint4 *>(wb)[i] = reinterpret_cast<const uint4 *>(prm_bf + OW)[i];
-        }
-        for (int i = tid; i < Lout * CC; i += nth) du[i] = dh[i] * gelu_df(U[i]);
-        __syncthreads();
-        // dW[o][t][c] = sum_p du[p][o] in[p + t][c];  db[o] = sum_p du[p][o]
-        const int nw = CC * CK * Cin;
-        for (int i = tid; i < nw + CC; i += nth) {
-            float a = 0.f;
-            if (i < nw) {
-                int o = i / (CK * Cin), r = i - o * CK * Cin, t = r / Cin, c = r - t * Cin;
-                if (l > 1)
-                    for (int p = 0; p < Lout; p++) a = fmaf(du[p * CC + o], __bfloat162float(hin[(p + t) * CC + c]), a);
-                else
-                    for (int p = 0; p < Lout; p++) a = fmaf(du[p * CC + o], xs[(p + t) * 2 + c], a);
-                G[OW + i] = a;
-            } else {
-                int o = i - nw;
-                for (int p = 0; p < Lout; p++) a += du[p * CC + o];
-                G[OB + o] = a;
+        // du = dh gelu'(u) for positions p < Lout (zero beyond): bias partials in FP32,
+        // bf16 copies padded (dup: row p + 8) and transposed (dut); layer 1 in place
+        float bsum = 0.f;
+        for (int i = tid; i < LDT * CC; i += nth) {   // thread tid always holds channel tid & 31
+            const int p = i >> 5, o = i & 31;
+            const float d = p < Lout ? dh[p * CC + o] * gelu_df(U[p * CC + o]) : 0.f;
+            bsum += d;
+            if (l > 1) {
+                dut[o * LDT + p] = __float2bfloat16(d);
+                if (p + 8 < NDU) dup[(p + 8) * CC + o] = __float2bfloat16(d);
+            } else if (p < Lout) {
+                dh[p * CC + o] = d;
             }
         }
-        // gradient of the layer input: dh_in[q][c] = sum_t sum_o W[o][t][c] du[q - t][o]
+        red[warp * CC + lane] = bsum;
         if (l > 1) {
-            __syncthreads();
-            for (int i = tid; i < Lin * CC; i += nth) {
-                int q = i >> 5, c = i & 31;
-                float a = 0.f;
-                for (int t = 0; t < CK; t++) {
-                    int p = q - t;
-                    if (p < 0 || p >= Lout) continue;
-#pragma unroll 8
-                    for (int o = 0; o < CC; o++) a = fmaf(__bfloat162float(wb[o * KW + t * CC + c]), du[p * CC + o], a);
+            for (int i = tid; i < 8 * CC; i += nth) dup[i] = bz;
+            // layer input (h2 for layer 3, h1 for layer 2) transposed, zero beyond Lin
+            const __nv_bfloat16 *src = (l == 3) ? sv.h2 + (size_t)s * L2 * CC : sv.h1 + (size_t)s * L1 * CC;
+            for (int i = tid; i < CC * LDH; i += nth) {
+                const int c = i / LDH, q = i - LDH * c;
+                ht0[i] = q < Lin ? src[q * CC + c] : bz;
+                ht1[i] = q + 1 < Lin ? src[(q + 1) * CC + c] : bz;
+            }
+        }
+        __syncthreads();
+        if (tid < CC) {
+            float a = 0.f;
+            for (int w = 0; w < 8; w++) a += red[w * CC + tid];
+            G[OB + tid] = a;
+        }
+        if (l > 1) {
+            // weight gradient dW[o][t][c] = sum_p du[p][o] h_in[p + t][c]: M = 32 (o),
+            // N = 288 (t, c), K = 144 (p; du is zero from Lout on)
+            for (int tile = warp; tile < 2 * 36; tile += 8) {
+                const int mt = tile / 36, nt = tile - 36 * mt, t = nt >> 2, c0 = 8 * (nt & 3);
+                // 32-bit loads need an even start: odd taps read the copy shifted by one
+                const __nv_bfloat16 *Bt = ((t & 1) ? ht1 + (t - 1) : ht0 + t) + LDH * c0;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 3
+                for (int k0 = 0; k0 < 144; k0 += 16) mma_tile(acc, dut + LDT * 16 * mt + k0, LDT, Bt + k0, LDH, g, tq);
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int o = 16 * mt + g + 8 * (i >> 1), n = 8 * nt + 2 * tq + (i & 1);
+                    G[OW + o * KW + n] = acc[i];
                 }
-                dh[i] = a;
+            }
+            // input gradient dh_in[q][c] = sum_t sum_o W[o][t][c] du[q - t][o]: row q of the
+            // A operand is the padded du from row q on (tap t' = 8 - t at row q + t'); dh
+            // (this layer's output gradient) was consumed above, so it takes dh_in
+            const __nv_bfloat16 *Wt = wdT + (size_t)(l == 3 ? 1 : 0) * CC * KW;
+            for (int tile = warp; tile < 9 * 4; tile += 8) {
+                const int mt = tile >> 2, nt = tile & 3;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+                for (int k0 = 0; k0 < KW; k0 += 16) {
+                    uint32_t a[4];
+                    const __nv_bfloat16 *ar = dup + CC * (16 * mt + g) + k0 + 2 * tq;
+                    a[0] = *reinterpret_cast<const uint32_t *>(ar);
+                    a[1] = *reinterpret_cast<const uint32_t *>(ar + CC * 8);
+                    a[2] = *reinterpret_cast<const uint32_t *>(ar + 8);
+                    a[3] = *reinterpret_cast<const uint32_t *>(ar + CC * 8 + 8);
+                    const __nv_bfloat16 *br = Wt + KW * (8 * nt + g) + k0 + 2 * tq;
+                    mma_bf16(acc, a, __ldg(reinterpret_cast<const unsigned int *>(br)),
+                             __ldg(reinterpret_cast<const unsigned int *>(br + 8)));
+                }
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int q = 16 * mt + g + 8 * (i >> 1), c = 8 * nt + 2 * tq + (i & 1);
+                    if (q < Lin) dh[q * CC + c] = acc[i];
+                }
+            }
+        } else {
+            // layer 1 (2 input channels) in FP32: dW1[o][t][c] = sum_p du1[p][o] x[p + t][c]
+            for (int i = tid; i < CC * CK * 2; i += nth) {
+                int o = i / (CK * 2), r = i - o * CK * 2, t = r / 2, c = r - 2 * t;
+                float a = 0.f;
+                for (int p = 0; p < Lout; p++) a = fmaf(dh[p * CC + o], xs[(p + t) * 2 + c], a);
+                G[OW + i] = a;
             }
         }
         __syncthreads();
@@ -436,9 +531,20 @@ __global__ void k_cnn_loss(const float *__restrict__ out, const float *__restric
     if (threadIdx.x == 0) *loss = red[0] * norm;
 }
 
-// Adam on the FP32 master weights; refreshes the BF16 copy
-__global__ void k_cnn_adam(float *__restrict__ prm, __nv_bfloat16 *__restrict__ prm_bf, float *__restrict__ m,
-                           float *__restrict__ v, const float *__restrict__ grad, float lr, float b1t, float b2t)
+// BF16 copy of a weight of layer 2 or 3 in the layout the backward input gradient
+// reads: wdT[layer - 2][c][(8 - t) 32 + o] = W[o][t][c]
+__device__ __forceinline__ void put_wdt(__nv_bfloat16 *wdT, int i, float w)
+{
+    const int lay = (i >= OW2 && i < OW2 + CC * KW) ? 0 : (i >= OW3 && i < OW3 + CC * KW) ? 1 : -1;
+    if (lay < 0) return;
+    const int rel = i - (lay ? OW3 : OW2), o = rel / KW, t = (rel % KW) / CC, c = rel % CC;
+    wdT[(size_t)lay * CC * KW + c * KW + (CK - 1 - t) * CC + o] = __float2bfloat16(w);
+}
+
+// Adam on the FP32 master weights; refreshes the BF16 copies
+__global__ void k_cnn_adam(float *__restrict__ prm, __nv_bfloat16 *__restrict__ prm_bf, __nv_bfloat16 *__restrict__ wdT,
+                           float *__restrict__ m, float *__restrict__ v, const float *__restrict__ grad, float lr,
+                           float b1t, float b2t)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NPRM) return;
@@ -451,12 +557,17 @@ __global__ void k_cnn_adam(float *__restrict__ prm, __nv_bfloat16 *__restrict__ 
     float w = prm[i] - lr * mh / (sqrtf(vh) + eps);
     prm[i] = w;
     prm_bf[i] = __float2bfloat16(w);
+    put_wdt(wdT, i, w);
 }
 
-__global__ void k_cnn_tobf(const float *__restrict__ prm, __nv_bfloat16 *__restrict__ prm_bf)
+__global__ void k_cnn_tobf(const float *__restrict__ prm, __nv_bfloat16 *__restrict__ prm_bf,
+                           __nv_bfloat16 *__restrict__ wdT)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < NPRM) prm_bf[i] = __float2bfloat16(prm[i]);
+    if (i < NPRM) {
+        prm_bf[i] = __float2bfloat16(prm[i]);
+        put_wdt(wdT, i, prm[i]);
+    }
 }
 
 // ====================================================================
@@ -893,6 +1004,7 @@ struct rx_cnn {
     int max_seg;
     float *prm, *grad, *m, *v, *gpart, *loss;
     __nv_bfloat16 *prm_bf;
+    __nv_bfloat16 *wdT;   // layer 2 and 3 weights for the backward input gradient
     CnnSave sv;
     long long step;
 };
@@ -904,7 +1016,7 @@ int rx_cnn_nparams(void) { return NPRM; }
 void rx_cnn_destroy(rx_cnn *c)
 {
     if (!c) return;
-    void *p[] = {c->prm, c->grad, c->m, c->v, c->gpart, c->loss, c->prm_bf, c->sv.u1, c->sv.u2, c->sv.u3,
+    void *p[] = {c->prm, c->grad, c->m, c->v, c->gpart, c->loss, c->prm_bf, c->wdT, c->sv.u1, c->sv.u2, c->sv.u3,
                  c->sv.h1, c->sv.h2, c->sv.h3, c->sv.v, c->sv.out};
     for (void *q : p)
         if (q) cudaFree(q);
@@ -929,6 +1041,7 @@ rx_status rx_cnn_create(int max_seg, rx_cnn **out)
               {(void **)&c->gpart, S * NPRM * 4},
               {(void **)&c->loss, 16},
               {(void **)&c->prm_bf, NPRM * 2 + 64},
+              {(void **)&c->wdT, 2 * CC * KW * 2},
               {(void **)&c->sv.u1, S * L1 * CC * 4},
               {(void **)&c->sv.u2, S * L2 * CC * 4},
               {(void **)&c->sv.u3, S * L3 * CC * 4},
@@ -957,7 +1070,7 @@ rx_status rx_cnn_set_params(rx_cnn *c, const float *host, int n)
     cudaMemset(c->m, 0, NPRM * 4);
     cudaMemset(c->v, 0, NPRM * 4);
     c->step = 0;
-    k_cnn_tobf<<<(NPRM + 255) / 256, 256>>>(c->prm, c->prm_bf);
+    k_cnn_tobf<<<(NPRM + 255) / 256, 256>>>(c->prm, c->prm_bf, c->wdT);
     if (cudaDeviceSynchronize() != cudaSuccess) return RX_ECUDA;
     return RX_OK;
 }
@@ -989,7 +1102,7 @@ rx_status rx_cnn_grad(rx_cnn *c, const float *y, const int64_t *seg_start, const
     k_cnn_fwd<<<nseg, kCnnThreads, FwdSmem::TOTAL, st>>>(c->prm, c->prm_bf, (const float2 *)y,
                                                          (const long long *)seg_start, 0, 0, nullptr, c->sv, nullptr,
                                                          nullptr, nullptr, nullptr, 0, 1.f, 4);
-    k_cnn_bwd<<<nseg, 256, BwdSmem::TOTAL, st>>>(c->prm, c->prm_bf, (const float2 *)y, (const long long *)seg_start,
+    k_cnn_bwd<<<nseg, 256, BwdSmem::TOTAL, st>>>(c->prm, c->wdT, (const float2 *)y, (const long long *)seg_start,
                                                  tgt, c->sv, norm, c->gpart);
     k_cnn_reduce<<<(NPRM + 255) / 256, 256, 0, st>>>(c->gpart, nseg, c->grad);
     k_cnn_loss<<<1, 256, 0, st>>>(c->sv.out, tgt, (long long)nseg * CS * 2, norm, c->loss);
@@ -1003,8 +1116,8 @@ rx_status rx_cnn_adam_step(rx_cnn *c, float lr, void *stream)
     if (!c || !(lr > 0)) return RX_EINVAL;
     c->step++;
     float b1t = powf(0.9f, (float)c->step), b2t = powf(0.999f, (float)c->step);
-    k_cnn_adam<<<(NPRM + 255) / 256, 256, 0, (cudaStream_t)stream>>>(c->prm, c->prm_bf, c->m, c->v, c->grad, lr, b1t,
-                                                                     b2t);
+    k_cnn_adam<<<(NPRM + 255) / 256, 256, 0, (cudaStream_t)stream>>>(c->prm, c->prm_bf, c->wdT, c->m, c->v, c->grad,
+                                                                     lr, b1t, b2t);
     return cudaGetLastError() == cudaSuccess ? RX_OK : RX_ECUDA;
 }
 
