@@ -389,7 +389,8 @@ orx *orx_create(const orx_cfg *cfg)
                     cfg->ds_den < 1 || cfg->ols_n < 4 || (cfg->ols_n & (cfg->ols_n - 1)) ||
                     cfg->ols_v < 2 || (cfg->ols_v & 1) || cfg->ols_v >= cfg->ols_n)) ||
         cfg->mf_mode < 0 || cfg->mf_mode > 1 || cfg->clk_track < 0 || cfg->clk_track > 1 || (cfg->clk_track && cfg->mf_mode != 1) ||
-        (cfg->rs_step != 0 && (f < 3 || cfg->rs_step < (int64_t)4252017623LL || cfg->rs_step > (int64_t)4337916969LL)) ||
+        (cfg->rs_step != 0 && ((f < 3 && cfg->mf_mode == 1) || cfg->rs_step < (int64_t)4252017623LL ||
+                               cfg->rs_step > (int64_t)4337916969LL)) ||
         (cfg->mf_mode == 1 && (cfg->sps != (f >= 3 ? 4 : 2) || cfg->fd_n < 16 || (cfg->fd_n & (cfg->fd_n - 1)) ||
                                cfg->fd_taps < 1 || !(cfg->fd_taps & 1) || cfg->fd_taps > cfg->fd_n / 2 + 1))) {
         free(h);
@@ -430,6 +431,7 @@ orx *orx_create(const orx_cfg *cfg)
     h->prbs = xcalloc(32767, 1);
     orx_prbs15(cfg->prbs_seed, 32767, h->prbs);
     h->chist_cap = h->kk ? cfg->ols_n : 2 * h->hmf;
+    if (!h->kk && cfg->rs_step != 0 && h->chist_cap < 64) h->chist_cap = 64;   /* the resampler's reach */
     if (!h->kk && cfg->mf_mode == 1 && h->chist_cap < cfg->fd_n) h->chist_cap = cfg->fd_n;
     h->chist = xcalloc((size_t)h->chist_cap, sizeof(int32_t));
     h->w = xcalloc((size_t)cfg->ntaps, sizeof(cx));
@@ -725,18 +727,6 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
             h->gain = (P > 0.0) ? 1.0 / sqrt((double)c->sps * P) : 1.0;
         }
     }
-    X.R_start = h->r_prev; X.R_len = h->rs ? r_k - h->r_prev : 0;
-    X.R = xcalloc((size_t)(X.R_len > 0 ? X.R_len : 1), sizeof(cx));
-    for (int64_t m = h->r_prev; m < r_k && h->rs; m++) {
-        __int128 psi = rs_psi(h, m);
-        int64_t i = (int64_t)(psi >> 32);
-        uint32_t fr = (uint32_t)(psi & 0xFFFFFFFF);
-        double cj[16];
-        orx_rs_taps((double)(fr >> 22) / 1024.0, cj);
-        cx acc = cx_mk(0.0, 0.0);
-        for (int j = -7; j <= 8; j++) acc = cx_add(acc, cx_scale(e_at(&X, i + j), cj[j + 7]));
-        X.R[m - X.R_start] = acc;
-    }
     if (!h->kk) {
         /* DC removal and scaling by the buffer's mean and standard deviation */
         double s1 = 0.0, s2 = 0.0;
@@ -746,6 +736,26 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
         X.sd_pam = (var > 0.0) ? sqrt(var) : 1.0;
         if (flush) { X.mu_pam = h->last_mu; X.sd_pam = h->last_sd; }
         h->last_mu = X.mu_pam; h->last_sd = X.sd_pam;
+    }
+    X.R_start = h->r_prev; X.R_len = h->rs ? r_k - h->r_prev : 0;
+    X.R = xcalloc((size_t)(X.R_len > 0 ? X.R_len : 1), sizeof(cx));
+    /* resampler to the transmitter's grid: KK interpolates the reconstructed field,
+     * PAM the normalised code (zero before the stream), both computed in the call
+     * that emits the nominal sample */
+    for (int64_t m = h->r_prev; m < r_k && h->rs; m++) {
+        __int128 psi = rs_psi(h, m);
+        int64_t i = (int64_t)(psi >> 32);
+        uint32_t fr = (uint32_t)(psi & 0xFFFFFFFF);
+        double cj[16];
+        orx_rs_taps((double)(fr >> 22) / 1024.0, cj);
+        cx acc = cx_mk(0.0, 0.0);
+        for (int j = -7; j <= 8; j++) {
+            int64_t n = i + j;
+            cx v = h->kk ? e_at(&X, n)
+                         : cx_mk(n < 0 ? 0.0 : ((double)code_at(&X, n) - X.mu_pam) / X.sd_pam, 0.0);
+            acc = cx_add(acc, cx_scale(v, cj[j + 7]));
+        }
+        X.R[m - X.R_start] = acc;
     }
 
     /* ---- matched filter (and 4 -> 2 samples/symbol for KK) ------------- */
@@ -822,6 +832,8 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
                 int64_t p = ((n % c->ds_den) * c->ds_num) % c->ds_den;
                 xn = cx_mul(cx_sub(r_at(&X, n), h->carrier),
                             cx_expj(-2.0 * PI * (double)p / (double)c->ds_den));
+            } else if (h->rs) {
+                xn = r_at(&X, n);
             } else {
                 xn = cx_mk(((double)code_at(&X, n) - X.mu_pam) / X.sd_pam, 0.0);
             }
@@ -1014,7 +1026,7 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
     free(msym);
 
     /* ---- carry the stream state to the next buffer ----------------------- */
-    if (h->kk && h->rs && r_k > 0) {
+    if (h->rs && r_k > 0) {
         /* the filter's history on the transmitter grid */
         int64_t lo = h->fd ? (int64_t)h->dec * f_k - c->fd_n / 4 : (int64_t)h->dec * f_k - h->hmf;
         if (lo < 0) lo = 0;

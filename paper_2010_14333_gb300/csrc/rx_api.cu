@@ -575,7 +575,8 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         return RX_EINVAL;
     if (c.kk_front < 0 || c.kk_front > 1 || !(c.eq_warps == 0 || c.eq_warps == 2 || c.eq_warps == 4 || c.eq_warps == 8))
         return RX_EINVAL;
-    if (c.rs_step != 0 && (!kk || c.rs_step < 4252017623LL || c.rs_step > 4337916969LL)) return RX_EINVAL;
+    if (c.rs_step != 0 && ((!kk && c.mf_mode == RX_MF_FD) || c.rs_step < 4252017623LL || c.rs_step > 4337916969LL))
+        return RX_EINVAL;
     if (c.cnn_bf16 < 0 || c.cnn_bf16 > 1 || !(c.deadline_ms == c.deadline_ms)) return RX_EINVAL;
     if (c.clk_track < 0 || c.clk_track > 1 || (c.clk_track && c.mf_mode != RX_MF_FD)) return RX_EINVAL;
     if (c.mf_mode < RX_MF_TIME || c.mf_mode > RX_MF_FD ||
@@ -691,10 +692,6 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     }
     if (kk) {
         for (int i = 0; i < kSlots; i++) RX_ALLOC(h->E[i], (kEHist + nb) * sizeof(float2));
-        if (h->rs) {   // a call emits at most nb / 0.99 + 8 nominal samples
-            for (int i = 0; i < 2; i++) RX_ALLOC(h->R[i], (kEHist + nb + nb / 64 + 64) * sizeof(float2));
-            RX_ALLOC(h->rs_tab, 1024 * 16 * sizeof(float));
-        }
         for (int i = 0; i < 3; i++) RX_ALLOC(h->phist[i], (size_t)h->nhist * 3 / 2 + 16);
         int gx = (h->N2 + kCtaK1 - 1) / kCtaK1;
         for (int i = 0; i < 2; i++) {
@@ -705,6 +702,11 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         RX_ALLOC(h->twN2, kk_tw_entries(h->N2) * sizeof(float2));
         RX_ALLOC(h->lnt, kLutCodes * sizeof(float));
         RX_ALLOC(h->ds_tab, c.ds_den * sizeof(float2));
+    }
+    if (h->rs) {   // a call emits at most nb / 0.99 + 8 nominal samples
+        for (int i = 0; i < 2; i++) RX_ALLOC(h->R[i], (kEHist + nb + nb / 64 + 64) * sizeof(float2));
+        RX_ALLOC(h->rs_tab, 1024 * 16 * sizeof(float));
+        if (!kk) RX_ALLOC(h->E[0], (h->nhist + nb) * sizeof(float2));   // PAM: the normalised codes
     }
     RX_ALLOC(h->prbs, 32767 + 256);
     RX_ALLOC(h->prbs_bits, kPrbsWords * sizeof(uint32_t));
@@ -1009,12 +1011,16 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     }
     // matched filter (after the resampler when the ADC clock is not the transmitter's)
     prof_begin(h, 4, sm);
-    if (e == cudaSuccess && h->kk && h->rs && s.r_k > h->r_prev) {
+    if (e == cudaSuccess && h->rs && s.r_k > h->r_prev) {
         const __int128 psi = rs_psi(h, h->r_prev);
         const long long rb = h->r_prev - kEHist;
-        e = launch_kk_resample(h->E[h->ew], h->ebase_cur, h->r_prev, s.r_k, (long long)(psi >> 32),
-                               (unsigned)(psi & 0xFFFFFFFF), c.rs_step, h->rs_tab, h->R[h->rw ^ 1], rb,
-                               h->R[h->rw], h->rbase_cur, sm);
+        const int ppar_rs = h->flush_mode ? h->flush_par : par;
+        // the resampler reads the reconstructed field (KK) or the call's normalised codes (PAM)
+        if (!h->kk) e = launch_pam_norm(h->codes[h->cw], cbase, h->nb, s.avail, h->st, ppar_rs, h->E[0], sm);
+        if (e == cudaSuccess)
+            e = launch_kk_resample(h->kk ? h->E[h->ew] : h->E[0], h->kk ? h->ebase_cur : cbase, h->r_prev, s.r_k,
+                                   (long long)(psi >> 32), (unsigned)(psi & 0xFFFFFFFF), c.rs_step, h->rs_tab,
+                                   h->R[h->rw ^ 1], rb, h->R[h->rw], h->rbase_cur, sm);
         h->rw ^= 1;
         h->rbase_cur = rb;
     }
@@ -1036,6 +1042,9 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
             e = launch_kk_mf(Ef, efbase, s.r_k, h->f_prev, s.f_k, h->rrc, h->hmf, h->ds_tab, c.ds_num,
                              c.ds_den, cgp, (float2 *)h->Y[yw_new], yb, (const float2 *)h->Y[h->yw],
                              h->ybase_cur, sm, h->rrc_host);
+        else if (h->rs)
+            e = launch_pam_mf_r(h->R[h->rw], h->rbase_cur, h->f_prev, s.f_k, h->rrc, h->hmf, (float *)h->Y[yw_new], yb,
+                                (const float *)h->Y[h->yw], h->ybase_cur, sf);
         else if (h->fd)
             e = launch_pam_fd1024(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->fd_H, h->fd_tw, h->st,
                                   ppar, (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf,

@@ -1449,6 +1449,78 @@ __global__ void __launch_bounds__(kMfOut) k_pam_mf(const uint16_t *__restrict__ 
     Y[m - ybase] = a;
 }
 
+// ========================================== PAM resampler path (ADC off the transmitter's clock)
+// The normalised code x[n] = (code - mu) / sd of the call (complex, imaginary part 0)
+// for stream samples [cbase, n_end), the input of the resampler (which treats
+// samples before the stream as zero); the call's mean and deviation come from the
+// exact integer sums, and the sums of the next call start from zero.
+__global__ void k_pam_norm(const uint16_t *__restrict__ codes, long long cbase, long long nb, long long n_end,
+                           DevState *dst, int parity, float2 *__restrict__ X)
+{
+    __shared__ float s_mu, s_inv;
+    if (threadIdx.x == 0) {
+        double mu = (double)dst->pam_s1[parity] / (double)nb;
+        double var = (double)dst->pam_s2[parity] / (double)nb - mu * mu;
+        double inv = (var > 0.0) ? 1.0 / sqrt(var) : 1.0;
+        s_mu = (float)mu;
+        s_inv = (float)inv;
+    }
+    __syncthreads();
+    const long long n = cbase + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < n_end) X[n - cbase] = make_float2(((float)codes[n - cbase] - s_mu) * s_inv, 0.f);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        dst->pam_mu = (double)s_mu;
+        dst->pam_inv_sd = (double)s_inv;
+        dst->pam_s1[parity ^ 1] = 0;   // the sums of the next call start from zero
+        dst->pam_s2[parity ^ 1] = 0;
+    }
+}
+
+// the PAM matched filter (2 samples/symbol, no decimation) on the resampled series
+// (real parts of R, stream index m at R[m - rbase]; zero before the stream)
+__global__ void __launch_bounds__(kMfOut) k_pam_mf_r(const float2 *__restrict__ R, long long rbase, long long f_prev,
+                                                    long long f_k, const float *__restrict__ rrc, int hmf,
+                                                    float *__restrict__ Y, long long ybase,
+                                                    const float *__restrict__ Y_prev, long long ybase_prev)
+{
+    extern __shared__ float xf[];
+    long long m0 = f_prev + (long long)blockIdx.x * kMfOut;
+    int L = kMfOut + 2 * hmf;
+    long long n0 = m0 - hmf;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        long long n = n0 + i;
+        xf[i] = n < 0 ? 0.f : R[n - rbase].x;
+    }
+    if (blockIdx.x == 0)
+        for (long long m = ybase + threadIdx.x; m < f_prev; m += blockDim.x)
+            Y[m - ybase] = (m < 0) ? 0.f : Y_prev[m - ybase_prev];
+    __syncthreads();
+    long long m = m0 + threadIdx.x;
+    if (m >= f_k) return;
+    const float *xc = xf + threadIdx.x + hmf;
+    float a = 0.f;
+    for (int i = -hmf; i <= hmf; i++) a = fmaf(__ldg(rrc + i + hmf), xc[-i], a);
+    Y[m - ybase] = a;
+}
+
+cudaError_t launch_pam_norm(const uint16_t *codes, long long cbase, long long nb, long long n_end, DevState *dst,
+                            int parity, float2 *X, cudaStream_t st)
+{
+    const long long n = n_end - cbase;
+    k_pam_norm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(codes, cbase, nb, n_end, dst, parity, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pam_mf_r(const float2 *R, long long rbase, long long f_prev, long long f_k, const float *rrc, int hmf,
+                            float *Y, long long ybase, const float *Y_prev, long long ybase_prev, cudaStream_t st)
+{
+    long long n = f_k - f_prev;
+    unsigned grid = (unsigned)((n + kMfOut - 1) / kMfOut);
+    size_t smem = (size_t)(kMfOut + 2 * hmf) * sizeof(float);
+    k_pam_mf_r<<<grid, kMfOut, smem, st>>>(R, rbase, f_prev, f_k, rrc, hmf, Y, ybase, Y_prev, ybase_prev);
+    return cudaGetLastError();
+}
+
 // ===================================================== PAM frequency-domain filter
 // The paper's PAM form (Sec. 2): a static filter applied on 1024-point
 // overlap-save blocks (hop 512) at the input rate.  One warp per block: the

@@ -161,6 +161,13 @@ cudaError_t launch_pam_fd1024(const uint16_t *codes, long long cbase, long long 
                               int parity, float *Y, long long ybase, const float *Y_prev, long long ybase_prev,
                               cudaStream_t st, float2 *clk, int wbin);
 
+// PAM with the resampler: the call's normalised codes for [cbase, n_end) as a complex
+// series (imaginary 0), then the matched filter on the resampled series
+cudaError_t launch_pam_norm(const uint16_t *codes, long long cbase, long long nb, long long n_end, DevState *dst,
+                            int parity, float2 *X, cudaStream_t st);
+cudaError_t launch_pam_mf_r(const float2 *R, long long rbase, long long f_prev, long long f_k, const float *rrc, int hmf,
+                            float *Y, long long ybase, const float *Y_prev, long long ybase_prev, cudaStream_t st);
+
 cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, long long n_end, long long f_prev,
                           long long f_k, const float *rrc, int hmf, DevState *dst, int parity,
                           float *Y, long long ybase, const float *Y_prev, long long ybase_prev,

@@ -105,8 +105,9 @@ def test_create_rejects_bad_resampler():
         c = rx.rx_default_config(rx.RX_KK_16QAM)
         c.rs_step = step
         assert lib.rx_create(rx.RX_KK_16QAM, 1e9, 4e9, 1 << 22, C.byref(c), C.byref(h)) == 1
-    p = rx.rx_default_config(rx.RX_PAM4)   # the resampler is the KK chain's
+    p = rx.rx_default_config(rx.RX_PAM4)   # the PAM resampler feeds the time-domain filter only
     p.rs_step = 1 << 32
+    p.mf_mode = rx.RX_MF_FD
     assert lib.rx_create(rx.RX_PAM4, 2e9, 4e9, 1 << 20, C.byref(p), C.byref(h)) == 1
 
 
