@@ -491,6 +491,7 @@ def gpu_arm(args, rank, world, local):
         fd_line = fd_leg(args, g, ring)
     rs_line = resampler_leg(args, ring) if rank == 0 and not args.no_rs else None
     sweep_line = sweep_leg(args) if rank == 0 and not args.no_sweep else None
+    diff_line = diff_leg(args) if rank == 0 and not args.no_sweep else None
     stab_line = stability_leg(args) if rank == 0 and args.stability > 0 else None
     batched_line = None
     if rank == 0 and not args.no_batched:
@@ -507,7 +508,7 @@ def gpu_arm(args, rank, world, local):
                     "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps, "warmup_run": e2e_warm},
             "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line, "precision": prec_line,
             "fd_filter": fd_line, "batched": batched_line,
-            "resampler": rs_line, "q_sweep": sweep_line, "stability": stab_line,
+            "resampler": rs_line, "q_sweep": sweep_line, "stability": stab_line, "diff_coding": diff_line,
             "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
             "realtime_x": value / 4.0,
             # the whole chain against the HBM roofline: 1.625 algorithmic bytes per sample
@@ -901,6 +902,30 @@ def stability_leg(args):
             "note": "the first window holds the training symbols and is excluded from the summary",
             "series": [{"w": x["window"], "q": None if x["q_db"] is None else round(x["q_db"], 3),
                         "ms": round(x["device_ms"], 3)} for x in series]}
+
+
+def diff_leg(args):
+    """Plain Gray mapping against differential quadrant coding on the workload's
+    KK-16QAM stream (20 dB, 100 kHz laser phase noise: the blind phase search slips
+    by pi/2 now and then): the BER-tester view (each window scored under its best
+    rotation) and the raw BER of the delivered bits, for 8 buffers of 2^22 samples."""
+    import torch
+    import synth
+    import paper_2010_14333_gb300 as rx
+    nb, nbufs, out = NB, 8, {}
+    for diff in (0, 1):
+        g = synth.gen_kk_stream(FMT, nb, nbufs, seed=31, truth=False, diff=bool(diff),
+                                workers=min(8, os.cpu_count() or 1), **GEN)
+        r = rx.Receiver(FMT, nb, diff_code=diff)
+        for p in g["packed"]:
+            r.process(torch.from_numpy(p).cuda())
+        st = r.stats()
+        out["differential" if diff else "gray"] = {
+            "bits": st["bits"], "ber_tester_view": st["ber"],
+            "raw_ber_delivered": st["raw_bit_errors"] / st["bits"] if st["bits"] else None,
+            "slip_windows": st["slip_windows"]}
+        del r
+    return out
 
 
 def oracle_free_q_db(ber: float) -> float:

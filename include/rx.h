@@ -116,7 +116,13 @@ typedef struct {
     int64_t rs_phase0;   /* accumulator value of nominal sample 0 (may be negative)        */
     int32_t cnn_bf16;    /* receiver CNN (rx_set_cnn) operands: 1 = BF16 (default), 0 =
                             FP16; FP32 accumulation, bias and GELU in the same packed type */
-    int32_t pad_cnn;     /* reserved, 0                                                    */
+    int32_t diff_code;   /* KK: 1 = differentially quadrant-coded symbols (the transmitter
+                            steps the quadrant by the Gray-decoded first two bits of a
+                            symbol and picks a rotation-invariant point in it with the
+                            rest): the output bits are decoded from quadrant differences, so
+                            a pi/2 cycle slip costs one symbol instead of the rest of the
+                            stream, and the BER counts the decoded bits against the PRBS
+                            (bit_errors = raw_bit_errors).  0 = plain Gray mapping       */
     double  deadline_ms; /* per-buffer latency budget for rx_stats (Sec. 2: a buffer
                             must be processed before the stream that takes it is needed
                             again; with five streams that is five buffer durations, 5.243

@@ -343,6 +343,7 @@ struct orx {
     int32_t *chist; int64_t chist_len, chist_cap;
     int have_first; int32_t first_code;
     int flushed;                   /* the stream has ended (orx_flush) */
+    int dq_have, dq_prev;          /* differential coding: quadrant of the last decided symbol */
     /* resampler accumulator, piecewise: nominal sample m >= rs_r0 lies at ADC position
      * (rs_psi0 + (m - rs_r0) rs_step) / 2^32; a step change keeps the position of the
      * next nominal sample (orx_set_rs_step) */
@@ -389,6 +390,7 @@ orx *orx_create(const orx_cfg *cfg)
                     cfg->ds_den < 1 || cfg->ols_n < 4 || (cfg->ols_n & (cfg->ols_n - 1)) ||
                     cfg->ols_v < 2 || (cfg->ols_v & 1) || cfg->ols_v >= cfg->ols_n)) ||
         cfg->mf_mode < 0 || cfg->mf_mode > 1 || cfg->clk_track < 0 || cfg->clk_track > 1 || (cfg->clk_track && cfg->mf_mode != 1) ||
+        cfg->diff_code < 0 || cfg->diff_code > 1 || (cfg->diff_code && f < 3) ||
         (cfg->rs_step != 0 && ((f < 3 && cfg->mf_mode == 1) || cfg->rs_step < (int64_t)4252017623LL ||
                                cfg->rs_step > (int64_t)4337916969LL)) ||
         (cfg->mf_mode == 1 && (cfg->sps != (f >= 3 ? 4 : 2) || cfg->fd_n < 16 || (cfg->fd_n & (cfg->fd_n - 1)) ||
@@ -475,6 +477,20 @@ static double dist_dim(double t, int mq)
 }
 static int gray_of(int L) { return L ^ (L >> 1); }
 static int gray_inv(int g) { int L = g; for (int s = g >> 1; s; s >>= 1) L ^= s; return L; }
+/* Differential quadrant coding (KK option, reading): the quadrant of a decided QAM
+ * point (0: I > 0, Q > 0, then counterclockwise) and the point turned back into the
+ * first quadrant, whose coordinates (1 + 2 b2, 1 + 2 b3) give the last two bits (16QAM) */
+static int quad_of(int LI, int LQ, int mq, int *b2, int *b3)
+{
+    int I = 2 * LI - (mq - 1), Q = 2 * LQ - (mq - 1), q, x, y;
+    if (I > 0 && Q > 0) { q = 0; x = I; y = Q; }
+    else if (I < 0 && Q > 0) { q = 1; x = Q; y = -I; }
+    else if (I < 0 && Q < 0) { q = 2; x = -I; y = -Q; }
+    else { q = 3; x = -Q; y = I; }
+    *b2 = (x - 1) / 2;
+    *b3 = (y - 1) / 2;
+    return q;
+}
 
 /* transmitted level indices of symbol k from the PRBS (MSB first) */
 static void tx_symbol(const orx *h, int64_t k, int *LI, int *LQ)
@@ -941,6 +957,7 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
     }
     int64_t nbits = (int64_t)h->bps * npay;
     if (bits_out && bits_cap > 0) memset(bits_out, 0, (size_t)((bits_cap + 7) / 8));
+    int32_t *dword = xcalloc((size_t)(nproc + 1), sizeof(int32_t));   /* differentially decoded words */
     int nb = h->kk ? h->bps / 2 : h->bps;
     for (int64_t i = 0; i < npay; i++) {
         int64_t o = off + i;
@@ -952,6 +969,18 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
         ahat[2 * o] = LI; ahat[2 * o + 1] = LQ;
         int gi = gray_of(LI), gq = gray_of(LQ);
         int64_t t0 = (int64_t)h->bps * i;
+        if (h->kk && c->diff_code) {
+            /* differential decoding: the quadrant step from the previous symbol (Gray),
+             * then the point's bits in its quadrant; the word replaces (gi, gq) */
+            int b2, b3, q = quad_of(LI, LQ, h->mq, &b2, &b3);
+            int d = ((q - (h->dq_have ? h->dq_prev : q)) % 4 + 4) % 4, gd = d ^ (d >> 1);
+            int w = (h->mq == 4) ? (gd << 2) | (b2 << 1) | b3 : gd;
+            dword[o] = w;
+            h->dq_prev = q; h->dq_have = 1;
+            if (bits_out && t0 + h->bps <= bits_cap)
+                for (int t = 0; t < h->bps; t++) put_bit(bits_out, t0 + t, (w >> (h->bps - 1 - t)) & 1);
+            continue;
+        }
         if (bits_out && t0 + h->bps <= bits_cap) {
             for (int t = 0; t < nb; t++) put_bit(bits_out, t0 + t, (gi >> (nb - 1 - t)) & 1);
             if (h->kk) for (int t = 0; t < nb; t++) put_bit(bits_out, t0 + nb + t, (gq >> (nb - 1 - t)) & 1);
@@ -968,6 +997,24 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
         int64_t k0 = pay_lo + wi * W;
         if (h->kk && k0 < c->ntrain + c->amb_syms) continue;
         if (k0 + W > score_end) continue;   /* stream end: filter supports reach into the pad */
+        if (h->kk && c->diff_code) {
+            /* the decoded data bits against the PRBS: rotation-free, so one count serves
+             * both the BER-tester view and the delivered output */
+            for (int q = 0; q < W; q++) {
+                int64_t o = off + wi * W + q, k = k0 + q;
+                int ne = 0;
+                for (int t = 0; t < h->bps; t++)
+                    ne += ((dword[o] >> (h->bps - 1 - t)) & 1) != h->prbs[((int64_t)h->bps * k + t) % 32767];
+                berr[o] = ne;
+                h->n_bit_err += ne;
+                h->n_raw_err += ne;
+                h->n_sym_err += ne > 0;
+                h->n_near += nearf[o];
+            }
+            h->n_bits += (int64_t)h->bps * W;
+            h->n_symbols += W;
+            continue;
+        }
         int nrot = h->kk ? 4 : 1;
         int64_t errs[4] = {0, 0, 0, 0};
         for (int rho = 0; rho < nrot; rho++) {
@@ -1020,6 +1067,7 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
     h->d_y = X.y; h->d_y_start = X.y_start; h->d_y_len = X.y_len > 0 ? X.y_len : 0;
     h->d_z = Z; h->d_v = Vv; h->d_ahat = ahat; h->d_draw = draw; h->d_berr = berr; h->d_near = nearf;
     h->d_s_start = sym_lo; h->d_s_len = nproc;
+    free(dword);
     h->d_win = dwin; h->d_win_len = nwin;
     h->scal[0] = h->carrier.re; h->scal[1] = h->carrier.im; h->scal[2] = h->gain;
     h->scal[3] = X.mu_pam; h->scal[4] = X.sd_pam;

@@ -59,6 +59,10 @@ typedef struct {
                             ADC position of nominal sample m is (rs_phase0 + m rs_step) /
                             2^32 ADC samples (exact integer accumulator)                 */
     int64_t rs_phase0;
+    int32_t diff_code;   /* KK: 1 = differentially quadrant-coded symbols: the first two bits
+                            of a symbol (Gray) step the quadrant, the rest pick a rotation-
+                            invariant point in it; decoded bits are quadrant differences  */
+    int32_t pad_dc;
 } orx_cfg;
 
 typedef struct {

@@ -34,7 +34,7 @@ class RxConfig(C.Structure):
         ("debug", C.c_int32), ("fir_prec", C.c_int32), ("kk_front", C.c_int32), ("eq_warps", C.c_int32),
         ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
         ("clk_track", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
-        ("cnn_bf16", C.c_int32), ("pad_cnn", C.c_int32), ("deadline_ms", C.c_double),
+        ("cnn_bf16", C.c_int32), ("diff_code", C.c_int32), ("deadline_ms", C.c_double),
     ]
 
 

@@ -578,6 +578,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     if (c.rs_step != 0 && ((!kk && c.mf_mode == RX_MF_FD) || c.rs_step < 4252017623LL || c.rs_step > 4337916969LL))
         return RX_EINVAL;
     if (c.cnn_bf16 < 0 || c.cnn_bf16 > 1 || !(c.deadline_ms == c.deadline_ms)) return RX_EINVAL;
+    if (c.diff_code < 0 || c.diff_code > 1 || (c.diff_code && !kk)) return RX_EINVAL;
     if (c.clk_track < 0 || c.clk_track > 1 || (c.clk_track && c.mf_mode != RX_MF_FD)) return RX_EINVAL;
     if (c.mf_mode < RX_MF_TIME || c.mf_mode > RX_MF_FD ||
         (c.mf_mode == RX_MF_FD && (c.fd_n < 16 || c.fd_n > kEHist || (c.fd_n & (c.fd_n - 1)) ||
@@ -636,6 +637,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     p.mu_train = (float)c.mu_train;
     p.mu_cma = (float)c.mu_cma;
     p.frozen = c.fir_prec != RX_FIR_ADAPTIVE;
+    p.diff = c.diff_code;
     if (c.eq_warps) {
         p.warps = c.eq_warps;
         if (eq_smem_bytes(p, p.warps) > kMaxSmemCta) { free(h); return RX_EINVAL; }
@@ -1127,7 +1129,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         prof_begin(h, 6, st4);
         int resolve = h->kk && !h->amb_done;
         e = launch_demap(h->ep, g, resolve, h->uw, h->dec[ds], h->winb[ds], h->winrec[ds], h->dbg_win, bits_out,
-                         h->st, st4);
+                         h->prbs_bits, h->st, st4);
         if (h->kk) h->uw ^= 1;
         h->amb_done = 1;
         prof_end(h, 6, st4);

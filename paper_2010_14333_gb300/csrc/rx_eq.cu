@@ -661,11 +661,27 @@ __device__ __forceinline__ unsigned rec_err(const uint4 &r, int q)
 }
 __device__ __forceinline__ unsigned rec_serr(const uint4 &r, int q) { return (r.z >> (8 * q)) & 0xFFu; }
 
+// differential coding: quadrant of a (rotated) decided point (0: I > 0, Q > 0, then
+// counterclockwise) and the bits of the point turned back into the first quadrant,
+// (1 + 2 b2, 1 + 2 b3) -> lb = b2 b3 (16QAM; QPSK has none)
+template <int MQ>
+__device__ __forceinline__ int quad_t(int LI, int LQ, int &lb)
+{
+    const int I = 2 * LI - (MQ - 1), Q = 2 * LQ - (MQ - 1);
+    int q, x, y;
+    if (I > 0 && Q > 0) { q = 0; x = I; y = Q; }
+    else if (I < 0 && Q > 0) { q = 1; x = Q; y = -I; }
+    else if (I < 0 && Q < 0) { q = 2; x = -I; y = -Q; }
+    else { q = 3; x = -Q; y = I; }
+    lb = (MQ == 4) ? ((((x - 1) >> 1) << 1) | ((y - 1) >> 1)) : 0;
+    return q;
+}
+
 template <bool QAM, int BPS, int MQ>
 __global__ void __launch_bounds__(kDemapThreads)
     k_demap(EqParams p, EqGeom g, int resolve_amb, int uw_in, const uint8_t *__restrict__ dec,
             const uint8_t *__restrict__ winb, const uint4 *__restrict__ winrec, float4 *__restrict__ dbg_win,
-            uint8_t *__restrict__ bits_out, DevState *dst)
+            uint8_t *__restrict__ bits_out, const uint32_t *__restrict__ prbs_bits, DevState *dst)
 {
     constexpr int NW = kDemapThreads / 32;
     constexpr int WPW = kDemapWin / NW;                            // windows per warp
@@ -674,6 +690,7 @@ __global__ void __launch_bounds__(kDemapThreads)
     constexpr int NS = (8 % BPS == 0) ? 8 / BPS : 8 / BPS + 2;     // symbols one output byte touches
     static_assert(kDemapWin == 32 && WPW <= 32, "one scan lane per window of the CTA");
     __shared__ long long s_m[kDemapWin];
+    __shared__ long long s_mbase;   // unwrap count of the window before the CTA's first
     __shared__ int s_red[NW];
     __shared__ int s_r;
     __shared__ unsigned s_cnt[C_NCNT];
@@ -753,6 +770,7 @@ __global__ void __launch_bounds__(kDemapThreads)
                 if (lane >= o) inc += v;
             }
             if (tid < kDemapWin) s_m[tid] = mstart + pre + inc;
+            if (tid == 0) s_mbase = mstart + pre;
         }
         if (resolve_amb) {
             // stream-start pi/2 ambiguity from the first amb_syms payload symbols:
@@ -801,7 +819,9 @@ __global__ void __launch_bounds__(kDemapThreads)
     if (lane < WPW && wr < wend) {
         long long k0 = g.pay_lo + (long long)wr * kWin;
         int qd = QAM ? (int)((s_m[wr - w0] + r) & 3) : 0;
-        if (!(QAM && k0 < amb_end) && k0 + kWin <= g.score_end) {
+        if (QAM && p.diff) {   // differential coding: errors are counted on the decoded bits below
+            if (!(k0 < amb_end) && k0 + kWin <= g.score_end) atomicAdd(&s_cnt[C_NEAR], rc.w >> 8);
+        } else if (!(QAM && k0 < amb_end) && k0 + kWin <= g.score_end) {
             int best = 0;
             unsigned be = rec_err(rc, qd);
 #pragma unroll
@@ -821,7 +841,11 @@ __global__ void __launch_bounds__(kDemapThreads)
         atomicAdd(&s_cnt[C_WINDOWS], 1u);
     }
     // output bits: Gray codes of the rotated decisions, byte b of a window holding
-    // its bits [8b, 8b+8) MSB first, gathered from the owning lanes by shuffle
+    // its bits [8b, 8b+8) MSB first, gathered from the owning lanes by shuffle.
+    // Differential coding: the word of a symbol is the Gray code of its quadrant step
+    // from the previous symbol, then (16QAM) its point's bits in the quadrant; the
+    // previous symbol of a window's first one is the last of the window before it
+    // (or the last of the previous call), and the decoded bits are scored here.
     const int sfirst = (8 * lane) / BPS, slast = (8 * lane + 7) / BPS;
     const int shift = BPS * (slast + 1) - (8 * lane + 8);
 #pragma unroll
@@ -835,12 +859,64 @@ __global__ void __launch_bounds__(kDemapThreads)
             if (dbg_win && lane == 0) dbg_win[wi].y = (float)mw;
         }
         uint32_t grp2 = 0;
+        if (QAM && p.diff) {
+            int qu[2], lb[2];
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            int dvb = (dv[i] >> (8 * h)) & 0xFF;
-            int LI = dvb & 7, LQ = QAM ? ((dvb >> 3) & 7) : 0;
-            if (QAM) rot_t<MQ>(LI, LQ, qd);
-            grp2 |= (uint32_t)(QAM ? ((gray(LI) << NB) | gray(LQ)) : gray(LI)) << (8 * h);
+            for (int h = 0; h < 2; h++) {
+                int dvb = (dv[i] >> (8 * h)) & 0xFF;
+                int LI = dvb & 7, LQ = (dvb >> 3) & 7;
+                rot_t<MQ>(LI, LQ, qd);
+                qu[h] = quad_t<MQ>(LI, LQ, lb[h]);
+            }
+            // quadrant of the symbol before this window's first
+            int qprev0 = -1;
+            if (lane == 0) {
+                if (wi > 0) {
+                    const long long mp = (wi - 1 >= w0) ? s_m[wi - 1 - w0] : s_mbase;
+                    const int db = dec[(long long)(wi - 1) * kWin + kWin - 1];
+                    int LI = db & 7, LQ = (db >> 3) & 7, lbx;
+                    rot_t<MQ>(LI, LQ, (int)((mp + r) & 3));
+                    qprev0 = quad_t<MQ>(LI, LQ, lbx);
+                } else if (dst->diff_have[uw_in]) {
+                    qprev0 = dst->diff_q[uw_in];
+                }
+            }
+            const int up0 = __shfl_up_sync(0xffffffffu, qu[0], 1), up1 = __shfl_up_sync(0xffffffffu, qu[1], 1);
+            const int last0 = __shfl_sync(0xffffffffu, qu[0], 31);
+            int qp[2] = {lane ? up0 : (qprev0 < 0 ? qu[0] : qprev0), lane ? up1 : last0};
+            const long long k0 = g.pay_lo + (long long)wi * kWin;
+            const int pwin = (int)(((long long)BPS * k0) % 32767);
+            unsigned ne = 0, se = 0;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int d = (qu[h] - qp[h]) & 3, gd = d ^ (d >> 1);
+                const int w = (MQ == 4) ? ((gd << 2) | lb[h]) : gd;
+                grp2 |= (uint32_t)w << (8 * h);
+                const unsigned e = __popc((unsigned)(w ^ ref_bits<BPS>(prbs_bits, pwin + BPS * (lane + 32 * h))));
+                ne += e;
+                se += e > 0;
+            }
+            ne = warp_sum_i(ne);
+            se = warp_sum_i(se);
+            if (lane == 0 && !(k0 < amb_end) && k0 + kWin <= g.score_end) {
+                atomicAdd(&s_cnt[C_BITERR], ne);
+                atomicAdd(&s_cnt[C_RAWERR], ne);
+                atomicAdd(&s_cnt[C_SYMERR], se);
+                atomicAdd(&s_cnt[C_BITS], (unsigned)(BPS * kWin));
+                atomicAdd(&s_cnt[C_SYMBOLS], (unsigned)kWin);
+            }
+            if (wi == g.nwin - 1 && lane == 31) {   // the next call's previous symbol
+                dst->diff_q[uw_in ^ 1] = qu[1];
+                dst->diff_have[uw_in ^ 1] = 1;
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                int dvb = (dv[i] >> (8 * h)) & 0xFF;
+                int LI = dvb & 7, LQ = QAM ? ((dvb >> 3) & 7) : 0;
+                if (QAM) rot_t<MQ>(LI, LQ, qd);
+                grp2 |= (uint32_t)(QAM ? ((gray(LI) << NB) | gray(LQ)) : gray(LI)) << (8 * h);
+            }
         }
         uint32_t acc = 0;
 #pragma unroll
@@ -864,12 +940,12 @@ __global__ void __launch_bounds__(kDemapThreads)
 
 cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in, const uint8_t *dec,
                          const uint8_t *winb, const uint4 *winrec, float4 *dbg_win, uint8_t *bits_out,
-                         DevState *dst, cudaStream_t st)
+                         const uint32_t *prbs_bits, DevState *dst, cudaStream_t st)
 {
     unsigned grid = (unsigned)((g.nwin + kDemapWin - 1) / kDemapWin);
 #define RX_DEMAP(Q, B, M)                                                                                   \
     k_demap<Q, B, M><<<grid, kDemapThreads, 0, st>>>(p, g, resolve_amb, uw_in, dec, winb, winrec, dbg_win,  \
-                                                     bits_out, dst)
+                                                     bits_out, prbs_bits, dst)
     if (p.kk && p.mq == 4) RX_DEMAP(true, 4, 4);
     else if (p.kk) RX_DEMAP(true, 2, 2);
     else if (p.mq == 2) RX_DEMAP(false, 1, 2);

@@ -41,6 +41,7 @@ struct DevState {
     double pam_mu, pam_inv_sd;             // PAM: this call's normalisation (debug view)
     long long pam_s1[2], pam_s2[2];        // PAM: integer sums of codes / codes^2, by call parity
     int unwrap_have[2], unwrap_b[2];       // pi/2 unwrap carry, by parity
+    int diff_have[2], diff_q[2];           // differential coding: quadrant of the last symbol, by parity
     long long unwrap_m[2];
     int amb_r;                             // stream-start rotation, -1 before
     int first_code;                        // 12-bit code of the stream's first sample
@@ -108,6 +109,7 @@ struct EqParams {
     int kk, mq, bps, ntaps, th, win, eq_block, ntrain, ncma, bps_b, amb_syms;
     float scale, r2, mu, mu_train, mu_cma;
     int frozen;   // payload blocks filter with the call's start taps (block-Toeplitz form)
+    int diff;     // differentially quadrant-coded QAM: decode and score quadrant differences
     int warps;    // equaliser blocks (warps) per CTA
 };
 
@@ -196,7 +198,7 @@ cudaError_t prepare_kk_front();
 
 cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in,
                          const uint8_t *dec, const uint8_t *winb, const uint4 *winrec, float4 *dbg_win,
-                         uint8_t *bits_out, DevState *dst, cudaStream_t st);
+                         uint8_t *bits_out, const uint32_t *prbs_bits, DevState *dst, cudaStream_t st);
 
 // CNN decisions for nseg consecutive payload windows (receiver mode)
 // CNN receiver on the tensor cores: soft symbols and decisions of nwin 64-symbol

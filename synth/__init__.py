@@ -314,8 +314,27 @@ def gen_pam_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: fl
                 buf_len=buf_len)
 
 
-def _tx_symbols(fmt: int, prbs_seed: int, k0: int, k1: int, period_cache={}) -> np.ndarray:
-    """Transmitted symbols k in [k0, k1) of the PRBS-15 stream (k < 0 gives 0)."""
+def diff_qam_symbols(fmt: int, bits: np.ndarray, q0: int = 0):
+    """Differentially quadrant-coded QAM (the optional coding of the KK chain): per
+    symbol the first two bits, Gray-decoded, step the quadrant, Q_k = (Q_{k-1} + D_k)
+    mod 4 (Q_{-1} = q0); 16QAM's last two bits pick the point of the first quadrant,
+    (1 + 2 b2) + j (1 + 2 b3), which is then turned by Q_k quarter turns (so a pi/2
+    rotation of the whole constellation changes the quadrants only).  Unit power.
+    Returns (symbols, quadrant of the last symbol)."""
+    name, bps, kind = FORMATS[fmt]
+    b = bits.reshape(-1, bps).astype(np.int64)
+    D = gray_index(b[:, :2].reshape(-1), 2)
+    Q = (q0 + np.cumsum(D)) % 4
+    base = (1 + 2 * b[:, 2] + 1j * (1 + 2 * b[:, 3])) if bps == 4 else np.full(len(b), 1 + 1j)
+    sym = base * (1j ** Q) / (np.sqrt(10.0) if bps == 4 else np.sqrt(2.0))
+    return sym, int(Q[-1]) if len(Q) else q0
+
+
+def _tx_symbols(fmt: int, prbs_seed: int, k0: int, k1: int, period_cache={}, diff: bool = False) -> np.ndarray:
+    """Transmitted symbols k in [k0, k1) of the PRBS-15 stream (k < 0 gives 0); with
+    diff, the differentially quadrant-coded QAM symbols (diff_qam_symbols from
+    stream symbol 0; the quadrant is a prefix sum, periodic up to a constant step per
+    PRBS period of 32767 symbols)."""
     name, bps, kind = FORMATS[fmt]
     key = (prbs_seed,)
     if key not in period_cache:
@@ -325,7 +344,21 @@ def _tx_symbols(fmt: int, prbs_seed: int, k0: int, k1: int, period_cache={}) -> 
     out = np.zeros(k1 - k0, dtype=np.float64 if kind == "pam" else np.complex128)
     if len(ks):
         idx = (ks[:, None] * bps + np.arange(bps)[None, :]) % 32767
-        out[max(k0, 0) - k0:] = tx_levels(fmt, per[idx].reshape(-1))
+        if not diff:
+            out[max(k0, 0) - k0:] = tx_levels(fmt, per[idx].reshape(-1))
+        else:
+            dkey = ("diff", prbs_seed, fmt)
+            if dkey not in period_cache:   # quadrant prefix over one period, and its total step
+                pidx = (np.arange(32767, dtype=np.int64)[:, None] * bps + np.arange(bps)[None, :]) % 32767
+                pb = per[pidx].reshape(-1, bps)
+                D = gray_index(pb[:, :2].reshape(-1), 2)
+                P = np.cumsum(D) % 4
+                period_cache[dkey] = (P, int(P[-1]))
+            P, C = period_cache[dkey]
+            Q = ((ks // 32767) * C + P[ks % 32767]) % 4
+            b = per[idx].reshape(-1, bps).astype(np.int64)
+            base = (1 + 2 * b[:, 2] + 1j * (1 + 2 * b[:, 3])) if bps == 4 else np.full(len(b), 1 + 1j)
+            out[max(k0, 0) - k0:] = base * (1j ** Q) / (np.sqrt(10.0) if bps == 4 else np.sqrt(2.0))
     return out
 
 
@@ -349,7 +382,7 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
               noise: bool = True, phase_noise: bool = True, volterra=(0.0, 0.0),
               prbs_seed: int = 1, pack_order: int = 0, symbols=None, phase_steps=(),
               truth: bool = True, clock_step: int = 1 << 32, clock_phase0: int = 0,
-              isi=None, sym_snr_db=None):
+              isi=None, sym_snr_db=None, diff: bool = False):
     """Buffer b of a Kramers-Kronig single-sideband QAM stream (see gen_kk_stream)."""
     name, bps, kind = FORMATS[fmt]
     assert kind == "qam"
@@ -362,7 +395,7 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
         ti, tf = adc_times(n0, n1, clock_step, clock_phase0)
         ka, kb = int(ti[0]) // sps - half - 2, int(ti[-1]) // sps + half + 3
     if symbols is None:
-        a_seg = _tx_symbols(fmt, prbs_seed, ka, kb)
+        a_seg = _tx_symbols(fmt, prbs_seed, ka, kb, diff=diff)
         Es = 1.0   # unit-power constellation
     else:
         sy = np.asarray(symbols, dtype=np.complex128)
@@ -375,8 +408,8 @@ def kk_buffer(fmt: int, buf_len: int, b: int, theta0: float, seed: int = 1, snr_
         # symbol-spaced ISI: a'_k = isi[0] a_{k+1} + isi[1] a_k + isi[2] a_{k-1}
         ext = np.concatenate(([0j], a_seg, [0j]))
         if symbols is None:
-            ext[0] = _tx_symbols(fmt, prbs_seed, ka - 1, ka)[0]
-            ext[-1] = _tx_symbols(fmt, prbs_seed, kb, kb + 1)[0]
+            ext[0] = _tx_symbols(fmt, prbs_seed, ka - 1, ka, diff=diff)[0]
+            ext[-1] = _tx_symbols(fmt, prbs_seed, kb, kb + 1, diff=diff)[0]
         a_seg = isi[0] * ext[2:] + isi[1] * ext[1:-1] + isi[2] * ext[:-2]
     if sym_snr_db is not None:
         a_seg = a_seg + _symbol_noise(seed, ka, kb, Es / 10.0 ** (sym_snr_db / 10.0))
@@ -449,7 +482,7 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
                   volterra=(0.0, 0.0), prbs_seed: int = 1, pack_order: int = 0,
                   symbols=None, phase_offset: float = 0.0, phase_steps=(), workers: int = 1,
                   truth: bool = True, clock_step: int = 1 << 32, clock_phase0: int = 0,
-                  isi=None, sym_snr_db=None):
+                  isi=None, sym_snr_db=None, diff: bool = False):
     """Kramers-Kronig single-sideband QAM stream split into ADC buffers.
 
     The signal sits above a real tone at 0 Hz after an up-shift of fd_num/fd_den
@@ -465,7 +498,8 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
     in gen_pam_stream.  ``sym_snr_db``: complex AWGN of that Es/N0 added to the
     symbols before shaping, i.e. noise confined to the signal band (after the unit-
     energy matched filter the symbol samples carry exactly that noise); usually
-    with noise=False.
+    with noise=False.  ``diff``: differentially quadrant-coded symbols of the PRBS bits
+    (diff_qam_symbols); the receiver needs rx_config.diff_code = 1.
     Returns dict with 'packed' (per buffer), 'codes', 'symbols' (the transmitted
     symbols of the stream), 'field' (noiseless complex baseband at sps, before the
     shift: what the receiver should recover; with truth=True) and 'clips'.
@@ -479,7 +513,7 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
               prbs_seed=prbs_seed, pack_order=pack_order, symbols=symbols,
               phase_steps=tuple(phase_steps), truth=truth, clock_step=int(clock_step),
               clock_phase0=int(clock_phase0), isi=None if isi is None else tuple(isi),
-              sym_snr_db=sym_snr_db)
+              sym_snr_db=sym_snr_db, diff=bool(diff))
     th0 = kk_phase_starts(buf_len, nbufs, seed, linewidth, fs, phase_noise, phase_offset)
     jobs = [(kw, b, th0[b]) for b in range(nbufs)]
     if workers > 1 and nbufs > 1:
@@ -490,7 +524,7 @@ def gen_kk_stream(fmt: int, buf_len: int, nbufs: int, seed: int = 1, snr_db: flo
     else:
         parts = [_kk_worker(j) for j in jobs]
     if symbols is None:
-        a = _tx_symbols(fmt, prbs_seed, 0, nsym)
+        a = _tx_symbols(fmt, prbs_seed, 0, nsym, diff=diff)
         bits = prbs15_bits(prbs_seed, nsym * bps)
     else:
         a, bits = np.asarray(symbols, dtype=np.complex128), None

@@ -93,3 +93,27 @@ def test_host_buffers_match_device_path():
         assert rx.rx_stats(h)["bit_errors"] == a.stats()["bit_errors"]
     finally:
         rx.rx_destroy(h)
+
+
+@pytest.mark.parametrize("fmt", [3, 4])
+def test_differential_coding_parity(fmt):
+    """Differentially quadrant-coded KK streams (noise and laser phase noise): GPU at
+    parity with the oracle, bits and counts; the decoded output's raw BER equals the
+    BER-tester view."""
+    p, s, so = run(fmt, 1 << 17, 3, gen=dict(diff=True), diff_code=1, **SMALL_KK)
+    assert s["bits"] > 0 and s["raw_bit_errors"] == s["bit_errors"] and s["slip_windows"] == 0
+
+
+def test_differential_coding_survives_a_slip_on_gpu():
+    import synth
+    nb = 1 << 20
+    res = {}
+    for diff in (0, 1):
+        g = synth.gen_kk_stream(4, nb, 2, seed=3, noise=False, phase_noise=False, diff=bool(diff), truth=False,
+                                phase_steps=((3 << 18, np.pi / 2),))
+        r = rx.Receiver(4, nb, diff_code=diff)
+        for pk in g["packed"]:
+            r.process(torch.from_numpy(pk).cuda())
+        res[diff] = r.stats()
+    assert res[0]["raw_bit_errors"] > 0.2 * res[0]["bits"]
+    assert res[1]["raw_bit_errors"] <= 8
