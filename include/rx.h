@@ -128,7 +128,7 @@ typedef struct {
                             again; with five streams that is five buffer durations, 5.243
                             ms for 2^22 samples at 4 GS/s).  0 = five buffer durations
                             (buf_len / fs each); > 0 = this budget in ms; < 0 = no latency
-                            record (no events are recorded per call)                       */
+                            record (the kernels then take no timestamps)                   */
 } rx_config;
 
 /* Reduction to 2 samples/symbol of the KK chain (rx_config.mf_mode). */
@@ -163,11 +163,14 @@ typedef struct {
     double  ber;               /* bit_errors / bits                                       */
     double  q_db;              /* 20 log10(sqrt(2) erfcinv(2 BER)), Sec. 3 Q-factor       */
     /* Per-buffer latency (cfg.deadline_ms >= 0): device time from the start of a
-     * call's first stage (the host->device copy for the host-buffer entry points)
-     * to the end of its last one (its bits in memory), taken with CUDA events on
-     * the streams that run those stages.  Calls inside a group round and flush
-     * calls are not recorded.  Percentiles come from a histogram of 0.5 us bins
-     * up to 32.768 ms (a latency above that counts in the top bin). */
+     * call's first kernel to the end of its demap (its bits in device memory),
+     * read from the GPU's global timer by those kernels themselves, so that a
+     * recorded call costs no API call.  The host<->device copies of the
+     * host-buffer entry points are not included.  Calls inside a group round,
+     * flush calls and calls that emit less than one equaliser block are not
+     * recorded.  Percentiles come from a histogram of 0.5 us bins up to
+     * 32.768 ms (a latency above that counts in the top bin; a percentile is
+     * its bin's centre, capped at the exact maximum). */
     int64_t lat_calls;         /* calls whose latency was recorded                       */
     int64_t deadline_misses;   /* recorded calls whose latency exceeded deadline_ms      */
     double  deadline_ms;       /* the budget in force (0 when no record is kept)         */

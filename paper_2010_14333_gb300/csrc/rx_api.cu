@@ -66,7 +66,7 @@ struct rx_handle {
     // (ev_front).  Call i+1 writes the history slot that call i-1 read, hence
     // three slots.
     cudaStream_t front, front2, mid, back, tail, copy;   // KK: field | matched filter | equaliser | demap
-    cudaEvent_t ev_fork, ev_front, ev_hist, ev_mid, ev_eq, ev_join, ev_yfree[kSlots], ev_efree[kSlots],
+    cudaEvent_t ev_fork, ev_front, ev_hist, ev_join, ev_yfree[kSlots], ev_efree[kSlots],
         ev_dfree[kSlots], ev_inready[2], ev_infree[2];
     float2 *taps[2], *twN, *twN2, *ds_tab;
     float *lnt;
@@ -98,13 +98,12 @@ struct rx_handle {
     long long prof_head, prof_tail;
     double prof_ms[8];
     long long prof_calls;
-    // per-buffer latency record (events on the streams of a call's first and last stage)
+    // per-buffer latency record, kept on the device clock by the call's first kernel
+    // and its demap (no API call per buffer)
     double lat_budget;         // ms; 0 = no record
-    cudaEvent_t *lat_ev;       // kLatRing pairs (start, end)
-    long long lat_head, lat_tail;
-    uint32_t *lat_hist;        // kLatBins bins of kLatBin ms
-    long long lat_n, lat_miss;
-    double lat_max;
+    LatRecord *lat_dev;        // device record, or null
+    long long lat_head;        // recorded calls enqueued (slot = lat_head % kLatSlots)
+    uint32_t *lat_hist;        // host copy of the histogram for rx_stats
     int in_group;              // the call is part of a group round (not recorded)
     // end of stream (rx_flush)
     int flushed;               // rx_flush ran: no more buffers
@@ -119,50 +118,19 @@ struct rx_handle {
     __int128 rs_psi0;
 };
 
-static const int kLatRing = 128;
-static const int kLatBins = 65536;
-static const double kLatBin = 0.0005;   // ms
+static const double kLatBinMs = (double)kLatBinNs * 1e-6;
 
-static void lat_take(rx_handle *h)
+// percentile p of n recorded latencies (centre of its bin), 0 without records
+static double lat_pct(const uint32_t *hist, long long n, double max_ms, double p)
 {
-    cudaEvent_t *ev = h->lat_ev + 2 * (h->lat_tail % kLatRing);
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess && ms >= 0.f) {
-        long long b = (long long)(ms / kLatBin);
-        if (b >= kLatBins) b = kLatBins - 1;
-        h->lat_hist[b]++;
-        h->lat_n++;
-        if (ms > h->lat_budget) h->lat_miss++;
-        if (ms > h->lat_max) h->lat_max = ms;
-    }
-    cudaGetLastError();
-    h->lat_tail++;
-}
-// collect the recorded calls that have finished (all of them when `block`)
-static void lat_harvest(rx_handle *h, bool block)
-{
-    while (h->lat_tail < h->lat_head) {
-        cudaEvent_t end = h->lat_ev[2 * (h->lat_tail % kLatRing) + 1];
-        if (block) {
-            cudaEventSynchronize(end);
-        } else if (cudaEventQuery(end) != cudaSuccess) {
-            cudaGetLastError();
-            break;
-        }
-        lat_take(h);
-    }
-}
-// percentile p of the recorded latencies (centre of its bin), 0 without records
-static double lat_pct(const rx_handle *h, double p)
-{
-    if (h->lat_n <= 0) return 0.0;
-    long long want = (long long)ceil(p * (double)h->lat_n), acc = 0;
+    if (n <= 0) return 0.0;
+    long long want = (long long)ceil(p * (double)n), acc = 0;
     if (want < 1) want = 1;
     for (int b = 0; b < kLatBins; b++) {
-        acc += h->lat_hist[b];
-        if (acc >= want) return ((double)b + 0.5) * kLatBin;
+        acc += hist[b];
+        if (acc >= want) return fmin(((double)b + 0.5) * kLatBinMs, max_ms);
     }
-    return h->lat_max;
+    return max_ms;
 }
 
 static const int kProfRing = 1024;
@@ -504,7 +472,7 @@ void rx_destroy(rx_handle *h)
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws[0], h->fftws[1], h->partials[0], h->partials[1], h->prbs, h->taps[0], h->taps[1], h->twN,
                     h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
                     h->bits_stage, h->lnt, h->prbs_bits, h->phist[0], h->phist[1], h->phist[2], h->zbuf, h->gpart, h->fd_H, h->fd_tw, h->R[0], h->R[1],
-                    h->rs_tab, h->clk};
+                    h->rs_tab, h->clk, h->lat_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kSlots; i++) {
@@ -519,11 +487,6 @@ void rx_destroy(rx_handle *h)
         for (int i = 0; i < kProfRing * kEvPerCall; i++) cudaEventDestroy(h->prof_ev[i]);
         free(h->prof_ev);
     }
-    if (h->lat_ev) {
-        for (int i = 0; i < 2 * kLatRing; i++)
-            if (h->lat_ev[i]) cudaEventDestroy(h->lat_ev[i]);
-        free(h->lat_ev);
-    }
     free(h->lat_hist);
     if (h->front) cudaStreamDestroy(h->front);
     if (h->front2) cudaStreamDestroy(h->front2);
@@ -531,7 +494,7 @@ void rx_destroy(rx_handle *h)
     if (h->back) cudaStreamDestroy(h->back);
     if (h->tail) cudaStreamDestroy(h->tail);
     if (h->copy) cudaStreamDestroy(h->copy);
-    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_inready[0],
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_join, &h->ev_inready[0],
                           &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
     for (cudaEvent_t *ev : evs)
         if (*ev) cudaEventDestroy(*ev);
@@ -843,7 +806,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
                   cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->tail, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
-        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_mid, &h->ev_eq, &h->ev_join, &h->ev_inready[0],
+        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_join, &h->ev_inready[0],
                               &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
         for (cudaEvent_t *ev : evs)
             ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
@@ -859,10 +822,12 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     }
     if (c.deadline_ms >= 0) {
         h->lat_budget = c.deadline_ms > 0 ? c.deadline_ms : 5.0 * (double)buf_len / fs * 1e3;
-        h->lat_ev = (cudaEvent_t *)calloc(2 * kLatRing, sizeof(cudaEvent_t));
         h->lat_hist = (uint32_t *)calloc(kLatBins, sizeof(uint32_t));
-        bool ok = h->lat_ev && h->lat_hist;
-        for (int i = 0; i < 2 * kLatRing && ok; i++) ok = cudaEventCreate(&h->lat_ev[i]) == cudaSuccess;
+        const unsigned long long budget_ns = (unsigned long long)llround(h->lat_budget * 1e6);
+        bool ok = h->lat_hist && cudaMalloc(&h->lat_dev, sizeof(LatRecord)) == cudaSuccess &&
+                  cudaMemset(h->lat_dev, 0, sizeof(LatRecord)) == cudaSuccess &&
+                  cudaMemcpy(&h->lat_dev->budget_ns, &budget_ns, sizeof budget_ns, cudaMemcpyHostToDevice) ==
+                      cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             rx_destroy(h);
@@ -904,18 +869,11 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     long long pay_lo = do_train ? c.ntrain : h->q_prev;
     long long npay = (h->trained || do_train) ? s.q_k - pay_lo : 0;
     if (npay > 0 && !bits_out && !host_out) return RX_EINVAL;
-    // latency record of calls that emit payload (not inside group rounds or flushes);
-    // finished records are collected first, without waiting unless the ring is full
-    const bool lat = h->lat_ev && !h->in_group && !h->flush_mode && npay >= c.eq_block;
-    cudaEvent_t *lat_ev = nullptr;
-    if (lat) {
-        lat_harvest(h, false);
-        if (h->lat_head - h->lat_tail >= kLatRing) {
-            cudaEventSynchronize(h->lat_ev[2 * (h->lat_tail % kLatRing) + 1]);
-            lat_take(h);
-        }
-        lat_ev = h->lat_ev + 2 * (h->lat_head % kLatRing);
-    }
+    // latency record of calls that emit payload (not inside group rounds or flushes):
+    // the call's first kernel stamps its slot, its demap closes it
+    const bool lat = h->lat_dev && !h->in_group && !h->flush_mode && npay >= c.eq_block;
+    const int lat_slot = (int)(h->lat_head % kLatSlots);
+    LatSlot *lat_first = lat ? &h->lat_dev->slot[lat_slot] : nullptr;
     // the launchers detect failures with cudaGetLastError: clear an error some
     // earlier, unrelated call left behind (a sticky one makes the launches fail)
     cudaError_t stale = cudaGetLastError();
@@ -937,11 +895,9 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     const bool alt = three && h->front2 && !h->cnn;
     if (alt && par) sf = h->front2;
     const KkSync ksync = {alt ? h->ev_hist : nullptr, alt ? h->ev_hist : nullptr, alt ? h->ev_front : nullptr};
-    if (lat_ev && !host_in) cudaEventRecord(lat_ev[0], sf);
     if (host_in) {
         in = h->in_stage[par];
         if (sc != sf) cudaStreamWaitEvent(sc, h->ev_infree[par], 0);   // the front end two calls back is done
-        if (lat_ev) cudaEventRecord(lat_ev[0], sc);
         e = cudaMemcpyAsync(h->in_stage[par], host_in, (size_t)(h->nb * 3 / 2), cudaMemcpyHostToDevice, sc);
         if (sc != sf) {
             cudaEventRecord(h->ev_inready[par], sc);
@@ -961,7 +917,8 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         const bool sums = !h->kk && !h->flush_mode;
         e = launch_unpack(in, h->codes[cw_new], h->codes[h->cw], h->nb, h->nhist, h->nb, h->calls == 0,
                           c.pack_order, sums ? &h->st->pam_s1[par] : nullptr,
-                          sums ? &h->st->pam_s2[par] : nullptr, sf);
+                          sums ? &h->st->pam_s2[par] : nullptr, sf, lat_first);
+        lat_first = nullptr;   // stamped: the KK front end (debug view) comes after
         h->cw = cw_new;
         prof_end(h, 0, sf);
     }
@@ -974,6 +931,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         kin.in_bytes = h->nb * 3 / 2;
         kin.order = c.pack_order;
         kin.first_call = h->calls == 0;
+        kin.lat = lat_first;
     }
     long long cbase = base - h->nhist;
 
@@ -1069,9 +1027,9 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     }
     prof_end(h, 4, sm);
     if (three) {
+        // the field slot's release is also the equaliser's start signal
         cudaEventRecord(h->ev_efree[h->ew], sm);
-        cudaEventRecord(h->ev_mid, sm);
-        cudaStreamWaitEvent(sb, h->ev_mid, 0);
+        cudaStreamWaitEvent(sb, h->ev_efree[h->ew], 0);
     } else {
         if (host_in && sc != sf) cudaEventRecord(h->ev_infree[par], sf);
         if (two) {
@@ -1090,6 +1048,8 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     g.nwin = npay > 0 ? (int)(npay / kWin) : 0;
     g.gpart = h->gpart;
     g.score_end = h->flush_mode ? h->flush_score_end : 0x7FFFFFFFFFFFFFFFLL;
+    g.lat = lat ? h->lat_dev : nullptr;
+    g.lat_slot = lat_slot;
     if (four) cudaStreamWaitEvent(sb, h->ev_dfree[ds], 0);   // the demap is done with these decision slots
     prof_begin(h, 5, sb);
     if (e == cudaSuccess && do_train) {
@@ -1120,11 +1080,9 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         }
     }
     prof_end(h, 5, sb);
+    // the filter slot's release is also the demap's start signal
     if (two) cudaEventRecord(h->ev_yfree[h->yw], sb);
-    if (four) {
-        cudaEventRecord(h->ev_eq, sb);
-        cudaStreamWaitEvent(st4, h->ev_eq, 0);
-    }
+    if (four) cudaStreamWaitEvent(st4, h->ev_yfree[h->yw], 0);
     if (e == cudaSuccess && g.nblk > 0) {
         prof_begin(h, 6, st4);
         int resolve = h->kk && !h->amb_done;
@@ -1138,10 +1096,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
                                 st4);
     }
     if (four) cudaEventRecord(h->ev_dfree[ds], st4);
-    if (lat_ev && e == cudaSuccess) {
-        cudaEventRecord(lat_ev[1], st4);
-        h->lat_head++;
-    }
+    if (lat && e == cudaSuccess) h->lat_head++;
     if (h->prof_cur) h->prof_head++;
     h->prof_cur = 0;
     if (e != cudaSuccess) {
@@ -1350,14 +1305,19 @@ rx_status rx_stats(rx_handle *h, rx_stats_t *o, void *stream)
     o->device_error = s.err;
     o->ber = o->bits ? (double)o->bit_errors / (double)o->bits : 0.0;
     o->q_db = q_from_ber(o->ber);
-    if (h->lat_ev) {
-        lat_harvest(h, true);
-        o->lat_calls = h->lat_n;
-        o->deadline_misses = h->lat_miss;
+    if (h->lat_dev) {
+        unsigned long long cnt[3];   // n, miss, max_ns
+        if (cudaMemcpy(cnt, &h->lat_dev->n, sizeof cnt, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(h->lat_hist, h->lat_dev->hist, sizeof(uint32_t) * kLatBins, cudaMemcpyDeviceToHost) !=
+                cudaSuccess)
+            return RX_ECUDA;
+        const double max_ms = (double)cnt[2] * 1e-6;
+        o->lat_calls = (int64_t)cnt[0];
+        o->deadline_misses = (int64_t)cnt[1];
         o->deadline_ms = h->lat_budget;
-        o->lat_p50_ms = lat_pct(h, 0.50);
-        o->lat_p99_ms = lat_pct(h, 0.99);
-        o->lat_max_ms = h->lat_max;
+        o->lat_p50_ms = lat_pct(h->lat_hist, (long long)cnt[0], max_ms, 0.50);
+        o->lat_p99_ms = lat_pct(h->lat_hist, (long long)cnt[0], max_ms, 0.99);
+        o->lat_max_ms = max_ms;
     }
     return RX_OK;
 }

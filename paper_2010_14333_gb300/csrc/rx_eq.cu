@@ -936,6 +936,7 @@ __global__ void __launch_bounds__(kDemapThreads)
         dst->unwrap_b[o] = winb[g.nwin - 1];
         dst->unwrap_m[o] = s_m[g.nwin - 1 - w0];
     }
+    if (g.lat && tid == 0) lat_end(g.lat, g.lat_slot);
 }
 
 cudaError_t launch_demap(const EqParams &p, const EqGeom &g, int resolve_amb, int uw_in, const uint8_t *dec,

@@ -39,9 +39,10 @@ __device__ __forceinline__ void decode_pair(uint32_t b0, uint32_t b1, uint32_t b
 __global__ void k_unpack(const uint8_t *__restrict__ in, uint16_t *__restrict__ codes,
                          const uint16_t *__restrict__ codes_prev, long long nb, int nhist,
                          long long prev_off, int first_call, int order, long long *s1,
-                         long long *s2)
+                         long long *s2, LatSlot *lat)
 {
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (lat && g == 0) lat_start(lat);
     long long ngroups = nb / 8;
     long long lsum = 0, lsq = 0;
     if (g < ngroups) {
@@ -100,13 +101,13 @@ __global__ void k_unpack(const uint8_t *__restrict__ in, uint16_t *__restrict__ 
 
 cudaError_t launch_unpack(const uint8_t *in, uint16_t *codes, const uint16_t *codes_prev,
                           long long nb, int nhist, long long prev_off, int first_call,
-                          int pack_order, long long *s1, long long *s2, cudaStream_t st)
+                          int pack_order, long long *s1, long long *s2, cudaStream_t st, LatSlot *lat)
 {
     long long items = nb / 8 + nhist;
     int tpb = 256;
     unsigned grid = (unsigned)((items + tpb - 1) / tpb);
     k_unpack<<<grid, tpb, 0, st>>>(in, codes, codes_prev, nb, nhist, prev_off, first_call,
-                                   pack_order, s1, s2);
+                                   pack_order, s1, s2, lat);
     return cudaGetLastError();
 }
 
@@ -196,6 +197,7 @@ struct KkPacked {
     long long hist_bytes;  // nhist * 3 / 2
     long long in_bytes;    // buf_len * 3 / 2
     int order, first_call;
+    LatSlot *lat;          // latency slot to stamp (first kernel of the call), or null
 };
 constexpr int kRawWords = 100;   // 384 bytes of a row + spare word, 16-byte multiple
 
@@ -239,6 +241,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2
     __shared__ __align__(16) uint32_t raw[32][kRawWords];
     __shared__ __align__(16) float s_ln[kLutCodes];
     int pair = blockIdx.y;
+    if (pk.lat && blockIdx.x == 0 && pair == 0 && threadIdx.x == 0) lat_start(pk.lat);
     if (pair == g.npairs) {
         // history of the next call: samples [avail - nhist, avail) = virtual bytes
         // [in_bytes, in_bytes + hist_bytes)
@@ -572,6 +575,7 @@ __global__ void __cluster_dims__(kClC, 1, 1) __launch_bounds__(kClThreads, 3)
     const int c = (int)cl.block_rank();
     const int pair = blockIdx.x / kClC;
     const int t = threadIdx.x;
+    if (pk.lat && blockIdx.x == 0 && t == 0) lat_start(pk.lat);
     const bool hb = 2 * pair + 1 < g.J;
     const uint32_t c_first = first_code(pk, dst);
     if (pk.first_call && blockIdx.x == 0 && t == 0) dst->first_code = (int)c_first;
@@ -791,6 +795,7 @@ __global__ void __cluster_dims__(kClC, 1, 1) __launch_bounds__(kClThreads, 3)
 
 __global__ void k_kk_hist(KkPacked pk)
 {
+    if (pk.lat && blockIdx.x == 0 && threadIdx.x == 0) lat_start(pk.lat);
     long long nch = pk.hist_bytes / 16;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += (long long)gridDim.x * blockDim.x) {
         long long vb = pk.in_bytes + 16 * c;
@@ -810,6 +815,7 @@ cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st, const KkSync &sy
     pk.in_bytes = inp.in_bytes;
     pk.order = inp.order;
     pk.first_call = inp.first_call;
+    pk.lat = inp.lat;
     k_kk_hist<<<32, 256, 0, st>>>(pk);
     if (sync.rec_fwd) cudaEventRecord(sync.rec_fwd, st);
     return cudaGetLastError();
@@ -832,6 +838,7 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     pk.in_bytes = inp.in_bytes;
     pk.order = inp.order;
     pk.first_call = inp.first_call;
+    pk.lat = inp.lat;
     if (g.N2 == kClN2 && g.fused) {
         // 2^16-point blocks: the fused cluster kernel (profiled as the K1a stage)
         if (sync.wait_fwd) cudaStreamWaitEvent(st, sync.wait_fwd, 0);

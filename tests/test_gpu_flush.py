@@ -121,3 +121,23 @@ def test_latency_default_budget_and_off():
     assert abs(s["deadline_ms"] - 5 * (1 << 17) / 4e9 * 1e3) < 1e-12
     s = _lat_run(1 << 17, 4, deadline_ms=-1.0)
     assert s["lat_calls"] == 0 and s["deadline_ms"] == 0.0
+
+
+def test_latency_record_outlives_its_slot_ring():
+    """More recorded calls than the record's 64 device slots, in one pipelined batch:
+    every call is closed once, and no latency exceeds the batch's wall time."""
+    import time
+    g = make_stream(4, 1 << 17, 4)
+    r = rx.Receiver(4, 1 << 17, **SMALL_KK, deadline_ms=10000.0)
+    bufs = [torch.from_numpy(g["packed"][b]).cuda() for b in range(4)]
+    r.process_batch(bufs)
+    s0 = r.stats()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    r.process_batch([bufs[i % 4] for i in range(150)])
+    r.stats()
+    wall_ms = (time.perf_counter() - t) * 1e3
+    s = r.stats()
+    assert s["lat_calls"] - s0["lat_calls"] == 150
+    assert s["deadline_misses"] == 0 and s["device_error"] == 0
+    assert 0 < s["lat_p50_ms"] <= s["lat_p99_ms"] <= s["lat_max_ms"] < wall_ms
