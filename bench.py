@@ -639,8 +639,18 @@ def precision_leg(args, g, ring):
         torch.cuda.synchronize()
         ms, calls = rx.rx_profile_read(r.h)
         rx.rx_profile(r.h, 0)
+        # the equaliser stage alone: one buffer in flight, a synchronize after each
+        sid = torch.cuda.current_stream().cuda_stream
+        obuf = torch.empty(NB, dtype=torch.uint8, device="cuda")
+        rx.rx_profile(r.h, 1)
+        for i in range(10):
+            rx.rx_process(r.h, ring[i % len(ring)].data_ptr(), obuf.data_ptr(), sid)
+            torch.cuda.synchronize()
+        ams, acalls = rx.rx_profile_read(r.h)
+        rx.rx_profile(r.h, 0)
         res[name] = {"gsa_s": 2 * len(ring) * NB / (e0.elapsed_time(e1) * 1e-3) / 1e9,
                      "eq_us_per_buffer": ms["eq"] / max(calls, 1) * 1e3,
+                     "eq_alone_us_per_buffer": ams["eq"] / max(acalls, 1) * 1e3,
                      "ber": sd["ber"], "bits": sd["bits"]}
         del r
     # the tensor-core FIR alone: 2^20 symbols (one buffer's payload), 31 taps

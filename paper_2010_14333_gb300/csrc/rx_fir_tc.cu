@@ -335,13 +335,166 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+
+// ---------------------------------------------------------------------------
+// 16-bit forms (BF16, FP16): each input sample is converted once.  Block row q of
+// a tile holds the 32 complex samples that start at stream sample
+// 2 (k_lo + 16 (r0 + q)) - 16, i.e. 64 K elements in 8 core-matrix columns whose
+// rows lie 16 bytes apart across 8-row groups (SBO = 128).  Output row r (symbols
+// k = k_lo + 16 (r0 + r) + j, j < 16) needs samples 2k - TH .. 2k + TH with TH <= 15,
+// all inside block rows r and r + 1: the tile is X[r] B0 + X[r + 1] B1, two sets
+// of four K = 16 MMAs over the same planes, the second with its descriptors
+// shifted by one row (16 bytes).  Persistent CTAs, two per SM: the next tile's
+// samples are loaded into registers while this tile's MMAs and stores run (a
+// launch of one CTA per tile spent its first 4 us bringing 512 CTAs up).
+constexpr int kT2Rows = kTileRows + 8;            // block rows a plane holds (129 used)
+constexpr int kT2Plane = kT2Rows * 16 + 16;       // plane pitch: + 16 bytes skews the planes by 4 banks
+constexpr int kT2Planes = 2 * kRowSyms * 2 / 8;   // 64 K elements of a block row, 8 per core row
+constexpr int kT2BPlane = kN * 16;                // one K core-matrix column of B (32 rows)
+constexpr int kT2OffB = kT2Planes * kT2Plane;
+constexpr int kT2OffW = kT2OffB + 2 * kT2Planes * kT2BPlane;   // the taps (32 complex)
+constexpr int kT2OffBar = kT2OffW + 32 * 8;
+constexpr int kT2Smem = kT2OffBar + 16;
+constexpr int kT2Threads = 256;
+constexpr int kT2Samples = (kTileRows + 1) * 2 * kRowSyms;   // complex samples a tile converts
+constexpr int kT2Iter = (kT2Samples + kT2Threads - 1) / kT2Threads;
+static_assert(kT2Plane % 16 == 0 && kT2OffB % 16 == 0 && kT2OffBar % 8 == 0, "16-byte aligned operands");
+static_assert((kT2Plane / 4) % 32 == 4, "planes four banks apart: a warp's 32 samples store conflict-free");
+
+template <int PREC>
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    if (PREC == RX_FIR_BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kT2Threads, 2)
+    k_fir_tc2(const float2 *__restrict__ Y, long long ybase, long long k_lo, int nrows,
+              const float2 *__restrict__ taps, int ntaps, float2 *__restrict__ z, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sA = sm, *sB = sm + kT2OffB;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kT2OffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    float2 *s_w = reinterpret_cast<float2 *>(sm + kT2OffW);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quarter = warp & 3, half = warp >> 2;
+    const int th = (ntaps - 1) / 2;
+    const int ntiles = (nrows + kTileRows - 1) / kTileRows;
+    // a tile's samples into registers: sample j of tile t is stream sample
+    // 2 (k_lo + 16 r0) - 16 + j; zero outside the samples its symbols use, so that
+    // nothing outside the caller's range is read
+    float2 v[kT2Iter];
+    auto load_tile = [&](int t) {
+        const int r0 = t * kTileRows, rows = min(kTileRows, nrows - r0);
+        const long long n0 = 2 * (k_lo + (long long)r0 * kRowSyms) - 16;
+        const int jlo = 16 - th, jhi = 2 * (rows * kRowSyms - 1) + th + 16;
+        const float2 *Yb = Y + (n0 - ybase);
+#pragma unroll
+        for (int i = 0; i < kT2Iter; i++) {
+            const int j = tid + i * kT2Threads;
+            v[i] = (j >= jlo && j <= jhi && j < kT2Samples) ? __ldg(Yb + j) : make_float2(0.f, 0.f);
+        }
+    };
+    int t = blockIdx.x;
+    if (tid < 32) s_w[tid] = tid < ntaps ? __ldg(taps + tid) : make_float2(0.f, 0.f);
+    if (t < ntiles) load_tile(t);
+    if (tid == 0) mbar_init(bar, 1);
+    if (warp == 0) tmem_alloc(tslot, kTmemCols);
+    __syncthreads();   // the taps in shared memory
+    // B: rows n = 2 j + c (c: re / im output of symbol j), K index k = 64 h + 2 s + d
+    // (block row r + h, sample s, d: re / im); sample 32 h + s of the pair is stream
+    // sample 2 k_row - 16 + 32 h + s, so tap i = 2 j + TH + 16 - (32 h + s)
+    for (int u = tid; u < kN * 2 * kT2Planes; u += kT2Threads) {
+        const int n = u % kN, pl = u / kN;
+        const int j = n >> 1, c = n & 1;
+        float vb[16];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int k = 8 * pl + q, hb = k >> 6, sp = (k & 63) >> 1, d = k & 1;
+            const int i = 2 * j + th + 16 - (32 * hb + sp);
+            float val = 0.f;
+            if (i >= 0 && i < ntaps) {
+                const float2 w = s_w[i];
+                // conj(w) y: re = a yr + b yi, im = a yi - b yr
+                val = c == 0 ? (d == 0 ? w.x : w.y) : (d == 0 ? -w.y : w.x);
+            }
+            vb[q] = val;
+        }
+        *reinterpret_cast<uint4 *>(sB + pl * kT2BPlane + n * 16) = pack16<PREC>(vb, 1.f);
+    }
+    const uint32_t idesc = umma_idesc(Fmt<PREC>::code, kTileRows, kN);
+    bool ok = true;
+    for (int it = 0; t < ntiles; t += gridDim.x, it++) {
+        const int r0 = t * kTileRows, rows = min(kTileRows, nrows - r0);
+        // A: sample j of the tile -> block row j / 32, K elements 2 (j % 32) and + 1
+#pragma unroll
+        for (int i = 0; i < kT2Iter; i++) {
+            const int j = tid + i * kT2Threads;
+            if (j < kT2Samples) {
+                const int q = j >> 5, s = j & 31;
+                *reinterpret_cast<uint32_t *>(sA + (s >> 2) * kT2Plane + q * 16 + (s & 3) * 4) =
+                    pack2<PREC>(v[i].x, v[i].y);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const uint32_t tmem = *tslot;
+        // the next tile's loads are in flight while this tile's MMAs and stores run
+        if (t + (int)gridDim.x < ntiles) load_tile(t + gridDim.x);
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+            for (int q = 0; q < kT2Planes; q++) {
+                const uint32_t shift = q < kT2Planes / 2 ? 0u : 16u;   // block row r, then r + 1
+                const uint64_t ad = umma_sdesc(a0 + shift + (q % (kT2Planes / 2)) * 2 * kT2Plane, kT2Plane, 128);
+                const uint64_t bd = umma_sdesc(b0 + q * 2 * kT2BPlane, kT2BPlane, 128);
+                umma_f16(tmem, ad, bd, idesc, q > 0);
+            }
+            umma_commit(bar);
+        }
+        bool done = mbar_wait(bar, (unsigned)(it & 1));
+        if (!done) {
+            atomicExch(err, (int)RX_ETIMEOUT);
+            mbar_wait(bar, (unsigned)(it & 1));
+        }
+        ok = __syncthreads_and(done) != 0;
+        tc_fence_after();
+        if (!ok) break;
+        // warp (quarter, half): accumulator lanes (rows) 32 quarter .. + 31, columns
+        // 16 half .. + 15 = symbols 8 half .. + 7 of the row, stored as four 16-byte pieces
+        uint32_t acc[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16 * half, acc);
+        const int r = 32 * quarter + lane;
+        if (r < rows) {
+            float4 *zr = reinterpret_cast<float4 *>(z + ((long long)(r0 + r) * kRowSyms + 8 * half));
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                zr[q] = make_float4(__uint_as_float(acc[4 * q]), __uint_as_float(acc[4 * q + 1]),
+                                    __uint_as_float(acc[4 * q + 2]), __uint_as_float(acc[4 * q + 3]));
+        }
+        tc_fence_before();
+        __syncthreads();   // A and the accumulator are free again
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(*tslot, kTmemCols);
+}
+
 }  // namespace
 
 cudaError_t prepare_fir_tc(int prec)
 {
     switch (prec) {
-    case RX_FIR_BF16: return cudaFuncSetAttribute(k_fir_tc<RX_FIR_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    case RX_FIR_FP16: return cudaFuncSetAttribute(k_fir_tc<RX_FIR_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    case RX_FIR_BF16:
+    case RX_FIR_FP16: return cudaSuccess;   // the 16-bit kernel's shared memory is under the default limit
     case RX_FIR_FP8: return cudaFuncSetAttribute(k_fir_tc<RX_FIR_FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     default: return cudaErrorInvalidValue;
     }
@@ -358,14 +511,18 @@ cudaError_t launch_fir_tc(int prec, const float2 *Y, long long ybase, long long 
     int nrows = (int)(nsym / kRowSyms);
     int rps = scale_block / kRowSyms;
     int ntiles = (nrows + kTileRows - 1) / kTileRows;
+    if (prec == RX_FIR_BF16 || prec == RX_FIR_FP16) {
+        const unsigned g2 = (unsigned)min(ntiles, 2 * nsm);   // two persistent CTAs per SM
+        if (prec == RX_FIR_BF16)
+            k_fir_tc2<RX_FIR_BF16><<<g2, kT2Threads, kT2Smem, st>>>(Y, ybase, k_lo, nrows, taps, ntaps, z, err);
+        else
+            k_fir_tc2<RX_FIR_FP16><<<g2, kT2Threads, kT2Smem, st>>>(Y, ybase, k_lo, nrows, taps, ntaps, z, err);
+        return cudaGetLastError();
+    }
     unsigned grid = (unsigned)min(ntiles, 2 * nsm);   // two persistent CTAs per SM
 #define RX_FIR_LAUNCH(P) k_fir_tc<P><<<grid, kThreads, kSmem, st>>>(Y, ybase, k_lo, nrows, taps, ntaps, rps, z, err)
-    switch (prec) {
-    case RX_FIR_BF16: RX_FIR_LAUNCH(RX_FIR_BF16); break;
-    case RX_FIR_FP16: RX_FIR_LAUNCH(RX_FIR_FP16); break;
-    case RX_FIR_FP8: RX_FIR_LAUNCH(RX_FIR_FP8); break;
-    default: return cudaErrorInvalidValue;
-    }
+    if (prec != RX_FIR_FP8) return cudaErrorInvalidValue;
+    RX_FIR_LAUNCH(RX_FIR_FP8);
 #undef RX_FIR_LAUNCH
     return cudaGetLastError();
 }
