@@ -286,6 +286,8 @@ def gpu_arm(args, rank, world, local):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.start()
     clocks.t0 = time.time()
     ev0.record(stream)
     host_s[0] = 0.0
@@ -294,6 +296,8 @@ def gpu_arm(args, rank, world, local):
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks.t1 = time.time()
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     barrier()
     ms = ev0.elapsed_time(ev1)
     stage_ms, calls = rx.rx_profile_read(r.h)
@@ -1081,6 +1085,9 @@ def main():
     ap.add_argument("--batched-streams", type=int, default=64)
     ap.add_argument("--batched-rounds", type=int, default=10)
     ap.add_argument("--latency-reps", type=int, default=1000)
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop, for a range profile of the "
+                         "pipelined chain (DRAM bytes of all its kernels as they overlap)")
     ap.add_argument("--eq-warps", type=int, default=0, help="equaliser blocks per CTA (0: library default)")
     ap.add_argument("--deadline-ms", type=float, default=0.0,
                     help="per-buffer latency budget of the timed receivers (0: the library default, five buffer "
