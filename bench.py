@@ -778,7 +778,8 @@ def resampler_leg(args, ring):
 def pam_fd(args):
     """PAM-4 at 2 GBaud on 2^20-sample buffers: the 503-tap frequency-domain form
     against the 33-tap time-domain matched filter, with the BER of the
-    frequency-domain form on the first two buffers."""
+    frequency-domain form on the first two buffers, and the form's static taps
+    fitted by least squares against its RRC taps."""
     import torch
     import synth
     import paper_2010_14333_gb300 as rx
@@ -790,6 +791,33 @@ def pam_fd(args):
         d.process(ring[b])
     res = {"buf_len": nb, "fd_taps": 503, "ber": d.stats()["ber"]}
     del d
+    # static taps from a least-squares fit on the first buffer (the calibration the
+    # paper's lab taps came from): normalised codes against the transmitted levels at
+    # the symbol centres; then the filter output's error at the symbol centres of the
+    # held-out third buffer (best gain for the RRC taps, none for the fitted ones) and
+    # the BER of the three buffers, against the RRC taps
+    codes = g["codes"][:nb].astype(np.float64)
+    x = (codes - codes.mean()) / codes.std()
+    k0, na = 126, 100000
+    t0 = time.perf_counter()
+    h = rx.rx_fd_ls_taps(x, 2 * k0, 2, g["symbols"][k0:k0 + na], 503)
+    res["ls_fit_s"] = time.perf_counter() - t0
+    for name, taps in (("rrc_taps", None), ("least_squares_taps", h)):
+        d = rx.Receiver(fmt, nb, mf_mode=1, debug=1)
+        if taps is not None:
+            d.set_fd_taps(taps)
+        for b in range(3):
+            d.process(ring[b])
+        y, y0 = d.debug(rx.RX_DBG_MF)
+        y = np.asarray(y, np.float64)
+        m = np.arange(y0 + (y0 & 1), y0 + len(y), 2)
+        m = m[(m >= 2 * nb) & (m < 3 * nb - 600)]
+        ys, a = y[m - y0], g["symbols"][m // 2]
+        gain = float(ys @ a / (ys @ ys)) if taps is None else 1.0
+        st = d.stats()
+        res[name] = {"filter_rel_mse": float(np.mean((a - gain * ys) ** 2) / np.mean(a ** 2)),
+                     "ber": st["ber"], "bit_errors": st["bit_errors"], "bits": st["bits"]}
+        del d
     for mode in (1, 0):
         r = rx.Receiver(fmt, nb, mf_mode=mode)
         for _ in range(2):

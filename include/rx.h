@@ -289,6 +289,38 @@ rx_status rx_flush(rx_handle *h, uint8_t *bits_out, void *cuda_stream, int64_t *
  * |ppm| < 9000 and |delay| < 2^30 (rx_create accepts rs_step within 1 % of 2^32). */
 rx_status rx_resampler_from_clock(double ppm, double delay, int64_t *rs_step, int64_t *rs_phase0);
 
+/* Taps of the static frequency-domain filter (mf_mode = RX_MF_FD), in place of
+ * the root-raised-cosine taps it starts with (Sec. 2: both chains filter with a
+ * static frequency-domain equaliser whose taps come from the link; the paper does
+ * not publish them).  re / im: HOST arrays of n taps h_i, i = -(n-1)/2 .. (n-1)/2
+ * in that order (index 0 holds h_{-(n-1)/2}); im may be NULL (real taps) and must
+ * be NULL or all zero for PAM, whose filter output is taken as real.  n odd,
+ * 1 <= n <= fd_n / 2 + 1.  The filter's response at the kept bins is recomputed
+ * on the host and copied after the device has finished all work (synchronous);
+ * calls made afterwards use it.  RX_EINVAL for other arguments or a handle
+ * without the frequency-domain form. */
+rx_status rx_set_fd_taps(rx_handle *h, const double *re, const double *im, int n);
+
+/* Least-squares fit of static filter taps to a training capture (the calibration
+ * that gives rx_set_fd_taps its taps):
+ *   minimise  sum_{k=0}^{na-1} | a_k - sum_{i=-L}^{L} h_i x[first + step k - i] |^2
+ *             + ridge (trace(R) / n) sum_i |h_i|^2
+ * over n = ntaps = 2L + 1 taps, R the normal matrix X^H X of the data matrix
+ * X[k][i] = x[first + step k - i].  x: HOST, nx samples at the filter's input rate
+ * (x_im NULL for real data); a: HOST, na targets (a_im NULL for real targets);
+ * step: input samples per target (PAM 2, KK 4 for one target per symbol).  The
+ * normal equations are formed in FP64 (the first `step` rows of R directly, the
+ * rest by the shift recurrence R[i+step][j+step] = R[i][j] + the term of the
+ * target before the first minus that of the last) and solved by Cholesky
+ * factorisation.  Output h_re / h_im (n values, ordered as rx_set_fd_taps takes
+ * them); h_im may be NULL only for real data and targets (then the taps are
+ * real).  RX_EINVAL unless ntaps is odd in [1, 2049], step >= 1, na >= ntaps,
+ * first >= L and first + step (na - 1) + L < nx, or when R + ridge is not
+ * positive definite.  Host only; no device is used. */
+rx_status rx_fd_ls_taps(const double *x_re, const double *x_im, int64_t nx, int64_t first, int step,
+                        const double *a_re, const double *a_im, int64_t na, int ntaps, double ridge,
+                        double *h_re, double *h_im);
+
 /* Synchronises cuda_stream, then copies the accumulated counters. */
 rx_status rx_stats(rx_handle *h, rx_stats_t *out, void *cuda_stream);
 

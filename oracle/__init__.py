@@ -106,6 +106,8 @@ def lib():
         L.orx_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, P(C.c_int64)]
         L.orx_get.restype = C.c_int64
         L.orx_set_taps.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.orx_set_fd_taps.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.orx_set_fd_taps.restype = C.c_int
         L.orx_stats.argtypes = [C.c_void_p, P(OrxStats)]
         L.orx_destroy.argtypes = [C.c_void_p]
         _lib = L
@@ -379,6 +381,14 @@ class Oracle:
         re = np.ascontiguousarray(taps.real)
         im = np.ascontiguousarray(taps.imag)
         lib().orx_set_taps(self._h, _ptr(re), _ptr(im), len(taps))
+
+    def set_fd_taps(self, taps: np.ndarray):
+        """Zero-phase taps of the static frequency-domain filter, h_{-L} first."""
+        taps = np.asarray(taps)
+        re = np.ascontiguousarray(taps.real, dtype=np.float64)
+        im = np.ascontiguousarray(taps.imag, dtype=np.float64) if np.iscomplexobj(taps) else None
+        if lib().orx_set_fd_taps(self._h, _ptr(re), None if im is None else _ptr(im), len(taps)) != 0:
+            raise ValueError("static FD taps refused")
 
     def stats(self) -> dict:
         s = OrxStats()

@@ -448,6 +448,32 @@ void orx_set_taps(orx *h, const double *re, const double *im, int n)
     for (int i = 0; i < n && i < h->c.ntaps; i++) h->w[i] = cx_mk(re[i], im ? im[i] : 0.0);
 }
 
+/* Static frequency-domain filter with given zero-phase taps h_i = re + j im at
+ * index i + L, i = -L .. L (Sec. 2: the static FD equalisers' taps come from the
+ * link): its N-bin response H_k = sum_i h_i e^{-2 pi i k i / N} replaces the RRC
+ * response.  PAM takes the filter output as real, so its taps must be real.
+ * Returns 0, or -1 (no FD form, n even or above N/2 + 1, complex PAM taps). */
+int orx_set_fd_taps(orx *h, const double *re, const double *im, int n)
+{
+    if (!h->fd || n < 1 || !(n & 1) || n > h->c.fd_n / 2 + 1) return -1;
+    if (!h->kk && im)
+        for (int i = 0; i < n; i++)
+            if (im[i] != 0.0) return -1;
+    int N = h->c.fd_n, half = (n - 1) / 2;
+    for (int k = 0; k < N; k++) {
+        double hr = 0.0, hi = 0.0;
+        for (int i = -half; i <= half; i++) {
+            double a = -2.0 * PI * (double)(((int64_t)k * i) % N) / (double)N;
+            cx t = cx_mul(cx_mk(re[i + half], im ? im[i + half] : 0.0), cx_expj(a));
+            hr += t.re;
+            hi += t.im;
+        }
+        h->fd_Hr[k] = hr;
+        h->fd_Hi[k] = hi;
+    }
+    return 0;
+}
+
 /* --------------------------------------------------------------- decisions */
 /* level index (0 = lowest) of t on odd-integer levels -(mq-1)..(mq-1);
  * thresholds at the even integers between them, ties to the upper level */

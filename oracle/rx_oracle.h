@@ -119,6 +119,8 @@ int     orx_set_rs(orx *h, int64_t step, int64_t nudge);
 int     orx_clock_retime(orx *h, int64_t *step_out, int64_t *nudge_out);
 int64_t orx_get(orx *h, int what, void *dst, int64_t cap, int64_t *start);
 void    orx_set_taps(orx *h, const double *re, const double *im, int n);
+/* static FD filter taps (zero-phase, index i + (n-1)/2): 0 or -1 */
+int     orx_set_fd_taps(orx *h, const double *re, const double *im, int n);
 void    orx_stats(orx *h, orx_stats_t *out);
 void    orx_destroy(orx *h);
 

@@ -61,6 +61,7 @@ EXPORTED = sorted(["rx_selftest_wait_timeout", "rx_clock_estimate", "rx_default_
                    "rx_cnn_adam_step", "rx_cnn_destroy", "rx_set_cnn", "rx_process_batch",
                    "rx_process_host_batch", "rx_fir_block", "rx_group_create", "rx_group_process",
                    "rx_group_tuning", "rx_group_destroy", "rx_flush", "rx_resampler_from_clock",
+                   "rx_set_fd_taps", "rx_fd_ls_taps",
                    "rx_clock_track", "rx_clock_retime", "rx_set_resampler"])
 RX_GROUP_GRAPH, RX_GROUP_TUNE = 1, 2
 RX_MF_TIME, RX_MF_FD = 0, 1
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH):
     L.rx_process_host.argtypes = [vp, vp, vp, vp, P(i64)]
     L.rx_flush.argtypes = [vp, vp, vp, P(i64)]
     L.rx_resampler_from_clock.argtypes = [C.c_double, C.c_double, P(i64), P(i64)]
+    L.rx_set_fd_taps.argtypes = [vp, vp, vp, C.c_int]
+    L.rx_fd_ls_taps.argtypes = [vp, vp, i64, i64, C.c_int, vp, vp, i64, C.c_int, C.c_double, vp, vp]
     L.rx_process_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.rx_process_host_batch.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.rx_fir_block.argtypes = [vp, i64, vp, C.c_int, C.c_int, i64, C.c_int, vp, vp, vp]
@@ -138,6 +141,31 @@ def rx_resampler_from_clock(ppm: float, delay: float):
     _check(load().rx_resampler_from_clock(ppm, delay, C.byref(st), C.byref(ph)))
     return st.value, ph.value
 
+
+
+def rx_set_fd_taps(h: int, taps):
+    """Zero-phase taps of the static frequency-domain filter, h_{-L} first (real or complex)."""
+    taps = np.asarray(taps)
+    re = np.ascontiguousarray(taps.real, dtype=np.float64)
+    im = np.ascontiguousarray(taps.imag, dtype=np.float64) if np.iscomplexobj(taps) else None
+    _check(load().rx_set_fd_taps(h, re.ctypes.data, None if im is None else im.ctypes.data, len(re)))
+
+
+def rx_fd_ls_taps(x, first: int, step: int, a, ntaps: int, ridge: float = 0.0):
+    """Least-squares static filter taps (see include/rx.h); real in and real targets
+    give real taps, otherwise complex."""
+    x, a = np.asarray(x), np.asarray(a)
+    cplx = np.iscomplexobj(x) or np.iscomplexobj(a)
+    xr = np.ascontiguousarray(x.real, dtype=np.float64)
+    xi = np.ascontiguousarray(x.imag, dtype=np.float64) if np.iscomplexobj(x) else None
+    ar = np.ascontiguousarray(a.real, dtype=np.float64)
+    ai = np.ascontiguousarray(a.imag, dtype=np.float64) if np.iscomplexobj(a) else None
+    hr = np.zeros(ntaps, np.float64)
+    hi = np.zeros(ntaps, np.float64) if cplx else None
+    _check(load().rx_fd_ls_taps(xr.ctypes.data, None if xi is None else xi.ctypes.data, len(xr), int(first),
+                                int(step), ar.ctypes.data, None if ai is None else ai.ctypes.data, len(ar),
+                                int(ntaps), float(ridge), hr.ctypes.data, None if hi is None else hi.ctypes.data))
+    return hr + 1j * hi if cplx else hr
 
 
 def rx_flush(h: int, bits_out: int, stream: int = 0) -> int:
@@ -411,6 +439,9 @@ class Receiver:
     def set_taps(self, taps):
         taps = np.asarray(taps, dtype=np.complex128)
         rx_set_taps(self.h, taps.real, taps.imag)
+
+    def set_fd_taps(self, taps):
+        rx_set_fd_taps(self.h, taps)
 
     _DT = {RX_DBG_FIELD: (np.complex64, 1), RX_DBG_SOFT: (np.complex64, 1), RX_DBG_DEC: (np.uint8, 1),
            RX_DBG_WIN: (np.float32, 4), RX_DBG_TAPS: (np.complex64, 1), RX_DBG_SCAL: (np.float64, 1),

@@ -4,6 +4,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <cmath>
+#include <complex>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -515,6 +518,26 @@ void rx_destroy(rx_handle *h)
         }                                                                               \
     } while (0)
 
+// Response of the zero-phase taps h_i = re[i + L] + j im[i + L], i = -L .. L, at the
+// bins the frequency-domain kernels multiply, times 1/N: KK the N/2 kept bins in
+// downsampled order (k' < N/4 -> k = k', else k = k' + N/2), PAM all N bins.
+static void fd_response(const double *re, const double *im, int ntaps, int N, bool kk, float2 *Hk)
+{
+    const double pi = 3.14159265358979323846;
+    const int half = (ntaps - 1) / 2, nbins = kk ? N / 2 : N;
+    for (int kp = 0; kp < nbins; kp++) {
+        const int k = (!kk || kp < N / 4) ? kp : kp + N / 2;
+        double hr = 0, hi = 0;
+        for (int i = -half; i <= half; i++) {
+            const double a = -2.0 * pi * (double)(((long long)k * i) % N) / N;
+            const double tr = re[i + half], ti = im ? im[i + half] : 0.0;
+            hr += tr * cos(a) - ti * sin(a);
+            hi += tr * sin(a) + ti * cos(a);
+        }
+        Hk[kp] = make_float2((float)(hr / N), (float)(hi / N));
+    }
+}
+
 rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const rx_config *cfg_in,
                     rx_handle **out)
 {
@@ -727,24 +750,13 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
         free(ds);
     }
     if (h->fd) {
-        // frequency-domain filter: response of the zero-phase taps at the kept bins
-        // (k' < N/4 -> k = k', else k = k' + N/2), times 1/N; N-point twiddles
-        const double pi = 3.14159265358979323846;
-        // (KK: the N/2 kept bins in downsampled order; PAM: all N bins)
+        // frequency-domain filter: response of the zero-phase RRC taps at the kept
+        // bins, times 1/N; N-point twiddles
         const int N = c.fd_n, half = (c.fd_taps - 1) / 2, nbins = kk ? N / 2 : N;
         double *hf = (double *)malloc(sizeof(double) * c.fd_taps);
         float2 *Hk = (float2 *)malloc(sizeof(float2) * nbins), *tw = (float2 *)malloc(sizeof(float2) * N);
         rrc_half(c.rrc_beta, sps, half, hf);
-        for (int kp = 0; kp < nbins; kp++) {
-            int k = (!kk || kp < N / 4) ? kp : kp + N / 2;
-            double re = 0, im = 0;
-            for (int i = -half; i <= half; i++) {
-                double a = -2.0 * pi * (double)(((long long)k * i) % N) / N;
-                re += hf[i + half] * cos(a);
-                im += hf[i + half] * sin(a);
-            }
-            Hk[kp] = make_float2((float)(re / N), (float)(im / N));
-        }
+        fd_response(hf, nullptr, c.fd_taps, N, kk, Hk);
         twiddles(N, tw);
         // band-edge clock correlation per block: half-width ceil(beta S / 2) bins around
         // S / 2, S = N / sps the bin of the symbol rate (the 1024-point kernels cover 31)
@@ -1267,6 +1279,101 @@ rx_status rx_resampler_from_clock(double ppm, double delay, int64_t *rs_step, in
     if (num_p % P != 0 && num_p < 0) qp -= 1;   // floor division
     *rs_step = (int64_t)(num_s / P);
     *rs_phase0 = (int64_t)(-qp);
+    return RX_OK;
+}
+
+rx_status rx_set_fd_taps(rx_handle *h, const double *re, const double *im, int n)
+{
+    if (!h || !re || !h->fd || !h->fd_H || n < 1 || !(n & 1) || n > h->cfg.fd_n / 2 + 1) return RX_EINVAL;
+    if (!h->kk && im)
+        for (int i = 0; i < n; i++)
+            if (im[i] != 0.0) return RX_EINVAL;   // the PAM filter output is taken as real
+    for (int i = 0; i < n; i++)
+        if (!std::isfinite(re[i]) || (im && !std::isfinite(im[i]))) return RX_EINVAL;
+    const int N = h->cfg.fd_n, nbins = h->kk ? N / 2 : N;
+    float2 *Hk = (float2 *)malloc(sizeof(float2) * nbins);
+    if (!Hk) return RX_ENOMEM;
+    fd_response(re, h->kk ? im : nullptr, n, N, h->kk, Hk);
+    // calls in flight read the response: replace it only after they are done
+    rx_status r = RX_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(h->fd_H, Hk, sizeof(float2) * nbins, cudaMemcpyHostToDevice) != cudaSuccess)
+        r = RX_ECUDA;
+    free(Hk);
+    if (r == RX_OK) h->cfg.fd_taps = n;
+    return r;
+}
+
+rx_status rx_fd_ls_taps(const double *x_re, const double *x_im, int64_t nx, int64_t first, int step,
+                        const double *a_re, const double *a_im, int64_t na, int ntaps, double ridge,
+                        double *h_re, double *h_im)
+{
+    const bool cplx = x_im || a_im;
+    if (!x_re || !a_re || !h_re || (cplx && !h_im) || ntaps < 1 || ntaps > 2049 || !(ntaps & 1) || step < 1 ||
+        na < ntaps || !(ridge >= 0.0) || !std::isfinite(ridge))
+        return RX_EINVAL;
+    const int n = ntaps, L = (ntaps - 1) / 2;
+    if (first < L || first + (int64_t)step * (na - 1) + L >= nx) return RX_EINVAL;
+    typedef std::complex<double> cd;
+    auto X = [&](int64_t k, int c) {   // data matrix entry: x[first + step k - (c - L)]
+        const int64_t idx = first + (int64_t)step * k - c + L;
+        return cd(x_re[idx], x_im ? x_im[idx] : 0.0);
+    };
+    std::vector<cd> R((size_t)n * n), p(n);
+    // rows c1 < step directly; the others by the shift recurrence (X[k][c + step] = X[k-1][c])
+    const int s0 = step < n ? step : n;
+    for (int c1 = 0; c1 < s0; c1++)
+        for (int c2 = 0; c2 < n; c2++) {
+            cd acc = 0.0;
+            for (int64_t k = 0; k < na; k++) acc += std::conj(X(k, c1)) * X(k, c2);
+            R[(size_t)c1 * n + c2] = acc;
+        }
+    for (int c1 = s0; c1 < n; c1++)
+        for (int c2 = 0; c2 < n; c2++) {
+            if (c2 < s0) {
+                R[(size_t)c1 * n + c2] = std::conj(R[(size_t)c2 * n + c1]);
+            } else {
+                const int a1 = c1 - step, a2 = c2 - step;
+                R[(size_t)c1 * n + c2] = R[(size_t)a1 * n + a2] + std::conj(X(-1, a1)) * X(-1, a2) -
+                                         std::conj(X(na - 1, a1)) * X(na - 1, a2);
+            }
+        }
+    for (int c = 0; c < n; c++) {
+        cd acc = 0.0;
+        for (int64_t k = 0; k < na; k++) acc += std::conj(X(k, c)) * cd(a_re[k], a_im ? a_im[k] : 0.0);
+        p[c] = acc;
+    }
+    double tr = 0.0;
+    for (int c = 0; c < n; c++) tr += R[(size_t)c * n + c].real();
+    for (int c = 0; c < n; c++) R[(size_t)c * n + c] += ridge * tr / n;
+    // Cholesky R = G G^H (lower G in place), then G y = p and G^H h = y
+    for (int j = 0; j < n; j++) {
+        double d = R[(size_t)j * n + j].real();
+        for (int q = 0; q < j; q++) d -= std::norm(R[(size_t)j * n + q]);
+        if (!(d > 0.0)) return RX_EINVAL;
+        const double gjj = std::sqrt(d);
+        R[(size_t)j * n + j] = gjj;
+        for (int i = j + 1; i < n; i++) {
+            cd v = R[(size_t)i * n + j];
+            for (int q = 0; q < j; q++) v -= R[(size_t)i * n + q] * std::conj(R[(size_t)j * n + q]);
+            R[(size_t)i * n + j] = v / gjj;
+        }
+    }
+    std::vector<cd> y(n);
+    for (int i = 0; i < n; i++) {
+        cd v = p[i];
+        for (int q = 0; q < i; q++) v -= R[(size_t)i * n + q] * y[q];
+        y[i] = v / R[(size_t)i * n + i].real();
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        cd v = y[i];
+        for (int q = i + 1; q < n; q++) v -= std::conj(R[(size_t)q * n + i]) * p[q];
+        p[i] = v / R[(size_t)i * n + i].real();   // p now holds h
+    }
+    for (int c = 0; c < n; c++) {
+        h_re[c] = p[c].real();
+        if (h_im) h_im[c] = cplx ? p[c].imag() : 0.0;
+    }
     return RX_OK;
 }
 

@@ -87,3 +87,44 @@ def test_fd_pam_batch_equals_sequential():
     for (bits, n), ref in zip(b.process_batch(dev), seq):
         assert np.array_equal(bits[: (n + 7) // 8].cpu().numpy(), ref)
     assert a.stats()["bit_errors"] == b.stats()["bit_errors"]
+
+
+def _pair_with_taps(fmt, nb, nbufs, taps, gen, **cfg):
+    g = make_stream(fmt, nb, nbufs, **gen)
+    p = Pair(fmt, nb, mf_mode=1, **cfg)
+    t = taps(g) if callable(taps) else taps
+    p.o.set_fd_taps(t)
+    p.g.set_fd_taps(t)
+    for b in range(nbufs):
+        p.feed(g["packed"][b])
+    return p.compare_stats()
+
+
+def test_fd_pam_least_squares_taps():
+    """PAM-4 through the ISI channel (0.1, 1, 0.2) with the 503 static taps fitted
+    by least squares on the first buffer (numpy, oracle side), set on both receivers."""
+    from test_fd_ls import pam_ls_taps
+    nb = 1 << 17
+    s, so = _pair_with_taps(1, nb, 3, lambda g: pam_ls_taps(g, nb), dict(seed=5, snr_db=14.0))
+    assert s["bits"] > 0 and so["ber"] < 5e-3
+
+
+def test_fd_kk_complex_taps():
+    """KK-16QAM with complex, asymmetric static taps (207): the RRC taps plus an echo
+    of 0.1 of them two input samples later, turned by e^{0.3j}."""
+    import oracle
+    rrc = oracle.rrc_half(0.1, 4, 101)
+    taps = (np.concatenate([np.zeros(2), rrc, np.zeros(2)]) +
+            0.1 * np.concatenate([np.zeros(4), rrc])) * np.exp(0.3j)
+    s, so = _pair_with_taps(4, 1 << 17, 3, taps, {}, **SMALL_KK)
+    assert s["bits"] > 0 and so["ber"] < 0.05
+
+
+def test_fd_taps_rejected():
+    r = rx.Receiver(1, 1 << 16, mf_mode=1)
+    for bad in (np.ones(4), np.ones(5) * (1 + 0.5j), np.ones(515), np.array([1.0, np.nan, 1.0])):
+        with pytest.raises(rx.RxError):
+            r.set_fd_taps(bad)
+    t = rx.Receiver(1, 1 << 16)   # time-domain form
+    with pytest.raises(rx.RxError):
+        t.set_fd_taps(np.ones(5))
