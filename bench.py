@@ -561,9 +561,12 @@ def cnn_leg(args, ring):
     tr = cnn.CnnTrainer(batch=64, seed=7)
     tr.set_data(y_all, s_all, k_lo=64)
     steps = int(os.environ.get("RX_CNN_STEPS", "6000"))
+    torch.cuda.synchronize()
+    t_tr = time.perf_counter()
     tr.train(steps - steps // 4, lr=1e-3)
     tr.train(steps // 4, lr=2e-4)
     torch.cuda.synchronize()
+    t_steps = time.perf_counter() - t_tr
     t_train = time.perf_counter() - t0
     # evaluation: fresh PRBS stream at 19 dB through both receivers
     gev = synth.gen_kk_stream(FMT, nb, 4, seed=777, truth=False, snr_db=19.0,
@@ -607,7 +610,8 @@ def cnn_leg(args, ring):
     return {"gsa_s": nrun * nb / (ms * 1e-3) / 1e9, "ber_cnn": sn["ber"], "ber_lms": sl["ber"],
             "inference_operands": "bf16", "fp16_operands": fp16,
             "bits": sn["bits"], "train_symbols": int(n_train), "train_steps": steps, "batch_symbols": 64 * 64,
-            "train_s": t_train,
+            "train_s": t_train, "train_steps_per_s": steps / t_steps,
+            "train_symbols_per_s": steps * 64 * 64 / t_steps,
             "channel": "KK-16QAM, Volterra (0.05, 0.02), CSPR 6 dB, no laser phase noise; train SNR 16/18/20/22 dB "
                        "(counter-based symbols), test SNR 19 dB (PRBS-15)"}
 

@@ -87,15 +87,15 @@ __device__ __forceinline__ bool near_t(float t)
     for (int j = 0; j < MQ - 1; j++) n |= fabsf(t - (float)(2 * j - (MQ - 2))) < 1e-4f;
     return n;
 }
-// squared distance to the nearest odd-integer level: fold |t| about the level
-// mid-points (4 levels: (||t| - 2| - 1)^2; 2 levels: (|t| - 1)^2)
+// squared distance to the nearest level of the odd-integer grid scaled by r: fold |t|
+// about the level mid-points (4 levels: (||t| - 2r| - r)^2; 2 levels: (|t| - r)^2)
 template <int MQ>
-__device__ __forceinline__ float dist_t(float t, float acc)
+__device__ __forceinline__ float dist_s(float t, float r, float acc)
 {
     float a = fabsf(t);
 #pragma unroll
-    for (int h = MQ >> 1; h > 1; h >>= 1) a = fabsf(a - (float)h);
-    a -= 1.f;
+    for (int h = MQ >> 1; h > 1; h >>= 1) a = fabsf(a - (float)h * r);
+    a -= r;
     return fmaf(a, a, acc);
 }
 
@@ -154,19 +154,24 @@ __device__ __forceinline__ WinOut qam_window(const EqParams &p, const float2 *ys
     R.second = 0.f;
     float cs = 1.f, sn = 0.f;   // cos / sin of the chosen phase
     if (mode == 2) {
-        // blind phase search: lane b tests theta_b = (b/B)(pi/2) - pi/4 (tph = cos, sin)
+        // blind phase search: lane b tests theta_b = (b/B)(pi/2) - pi/4 (tph = cos, sin).
+        // The rotated, scaled symbol s z e^{-j theta} divided by s cos(theta) is
+        // (zr + zi tan, zi - zr tan): one FMA per dimension.  Its distance to the
+        // nearest level is that of the original with the level grid scaled by
+        // 1 / (s cos), times (s cos)^2, a factor common to the whole window.
         const float tcs = tph.x, tsn = tph.y;
-        const float sc = p.scale * tcs, ss = p.scale * tsn;
+        const float tn = tsn / tcs, sc = p.scale * tcs, r = 1.f / sc;
         float M = 0.f;
         const float4 *z4 = reinterpret_cast<const float4 *>(zs);
 #pragma unroll 8
         for (int q2 = 0; q2 < kWin / 2; q2++) {
             float4 Z = z4[q2];
-            M = dist_t<MQ>(fmaf(Z.x, sc, Z.y * ss), M);
-            M = dist_t<MQ>(fmaf(Z.y, sc, -Z.x * ss), M);
-            M = dist_t<MQ>(fmaf(Z.z, sc, Z.w * ss), M);
-            M = dist_t<MQ>(fmaf(Z.w, sc, -Z.z * ss), M);
+            M = dist_s<MQ>(fmaf(Z.y, tn, Z.x), r, M);
+            M = dist_s<MQ>(fmaf(-Z.x, tn, Z.y), r, M);
+            M = dist_s<MQ>(fmaf(Z.w, tn, Z.z), r, M);
+            M = dist_s<MQ>(fmaf(-Z.z, tn, Z.w), r, M);
         }
+        M *= sc * sc;
         if (lane >= p.bps_b) M = __int_as_float(0x7f800000);
         float m1 = M, m2 = __int_as_float(0x7f800000);
         int b1 = lane;

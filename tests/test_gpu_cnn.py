@@ -178,3 +178,35 @@ def test_cnn_receiver_pass_through_closed_form(bf16, tol):
         assert np.max(np.abs(got - ref)) < tol * max(1.0, np.max(np.abs(ref)))
     finally:
         rx.rx_cnn_destroy(c)
+
+
+@pytest.mark.parametrize("bf16,tol", [(0, 1.5e-2), (1, 3e-2)])
+def test_cnn_receiver_soft_matches_oracle_forward(bf16, tol):
+    """The receiver's tensor-core inference against the FP64 oracle's forward pass
+    (orx_cnn_loss_grad's outputs) on the same 2-sps samples, random weights: FP16
+    or BF16 activations between layers, FP32 accumulation."""
+    nb = 1 << 19
+    g = synth.gen_kk_stream(4, nb, 2, seed=25, truth=False, **VOLT)
+    p = cnn.init_params(13).astype(np.float32)
+    p += np.random.default_rng(14).standard_normal(len(p)).astype(np.float32) * 0.02
+    c = rx.rx_cnn_create(64)
+    try:
+        rx.rx_cnn_set_params(c, p)
+        r = rx.Receiver(4, nb, debug=1, cnn_bf16=bf16)
+        rx.rx_set_cnn(r.h, c)
+        for b in range(2):
+            r.process(torch.from_numpy(g["packed"][b]).cuda())
+        soft, s0 = r.debug(rx.RX_DBG_SOFT)
+        y, y0 = r.debug(rx.RX_DBG_MF)
+        ks = [k for k in range(s0 + 64 * 20, s0 + len(soft) - 64 * 20, 64 * 41)][:24]
+        seg = [2 * k - 12 - y0 for k in ks]
+        assert min(seg) >= 0 and max(seg) + L0 <= len(y)
+        yv = y.astype(np.complex128)
+        x = np.stack([np.stack([yv[s:s + L0].real, yv[s:s + L0].imag], axis=1) for s in seg])
+        _, _, out = oracle.cnn_loss_grad(p.astype(np.float64), x, np.zeros((len(seg), S, 2)), grad=False)
+        ref = out[..., 0] + 1j * out[..., 1]
+        got = np.stack([soft[k - s0: k - s0 + S] for k in ks])
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert rel < tol, rel
+    finally:
+        rx.rx_cnn_destroy(c)
