@@ -885,7 +885,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     // the call's first kernel stamps its slot, its demap closes it
     const bool lat = h->lat_dev && !h->in_group && !h->flush_mode && npay >= c.eq_block;
     const int lat_slot = (int)(h->lat_head % kLatSlots);
-    LatSlot *lat_first = lat ? &h->lat_dev->slot[lat_slot] : nullptr;
+    LatRecord *lat_first = lat ? h->lat_dev : nullptr;
     // the launchers detect failures with cudaGetLastError: clear an error some
     // earlier, unrelated call left behind (a sticky one makes the launches fail)
     cudaError_t stale = cudaGetLastError();
@@ -929,7 +929,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         const bool sums = !h->kk && !h->flush_mode;
         e = launch_unpack(in, h->codes[cw_new], h->codes[h->cw], h->nb, h->nhist, h->nb, h->calls == 0,
                           c.pack_order, sums ? &h->st->pam_s1[par] : nullptr,
-                          sums ? &h->st->pam_s2[par] : nullptr, sf, lat_first);
+                          sums ? &h->st->pam_s2[par] : nullptr, sf, lat_first, lat_slot);
         lat_first = nullptr;   // stamped: the KK front end (debug view) comes after
         h->cw = cw_new;
         prof_end(h, 0, sf);
@@ -944,6 +944,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         kin.order = c.pack_order;
         kin.first_call = h->calls == 0;
         kin.lat = lat_first;
+        kin.lat_slot = lat_slot;
     }
     long long cbase = base - h->nhist;
 
@@ -1414,7 +1415,8 @@ rx_status rx_stats(rx_handle *h, rx_stats_t *o, void *stream)
     o->q_db = q_from_ber(o->ber);
     if (h->lat_dev) {
         unsigned long long cnt[3];   // n, miss, max_ns
-        if (cudaMemcpy(cnt, &h->lat_dev->n, sizeof cnt, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        if (launch_lat_flush(h->lat_dev, (cudaStream_t)stream) != cudaSuccess ||
+            cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess || cudaMemcpy(cnt, &h->lat_dev->n, sizeof cnt, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(h->lat_hist, h->lat_dev->hist, sizeof(uint32_t) * kLatBins, cudaMemcpyDeviceToHost) !=
                 cudaSuccess)
             return RX_ECUDA;

@@ -18,6 +18,13 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)
     return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// the hardware square-root approximation (positive normal x)
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
 // 4-point DFT in place; forward kernel e^{-2 pi i nk/4} (INV: e^{+...}, unscaled)

@@ -39,10 +39,10 @@ __device__ __forceinline__ void decode_pair(uint32_t b0, uint32_t b1, uint32_t b
 __global__ void k_unpack(const uint8_t *__restrict__ in, uint16_t *__restrict__ codes,
                          const uint16_t *__restrict__ codes_prev, long long nb, int nhist,
                          long long prev_off, int first_call, int order, long long *s1,
-                         long long *s2, LatSlot *lat)
+                         long long *s2, LatRecord *lat, int lat_slot)
 {
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (lat && g == 0) lat_start(lat);
+    if (lat && g == 0) lat_start(lat, lat_slot);
     long long ngroups = nb / 8;
     long long lsum = 0, lsq = 0;
     if (g < ngroups) {
@@ -101,13 +101,14 @@ __global__ void k_unpack(const uint8_t *__restrict__ in, uint16_t *__restrict__ 
 
 cudaError_t launch_unpack(const uint8_t *in, uint16_t *codes, const uint16_t *codes_prev,
                           long long nb, int nhist, long long prev_off, int first_call,
-                          int pack_order, long long *s1, long long *s2, cudaStream_t st, LatSlot *lat)
+                          int pack_order, long long *s1, long long *s2, cudaStream_t st, LatRecord *lat,
+                          int lat_slot)
 {
     long long items = nb / 8 + nhist;
     int tpb = 256;
     unsigned grid = (unsigned)((items + tpb - 1) / tpb);
     k_unpack<<<grid, tpb, 0, st>>>(in, codes, codes_prev, nb, nhist, prev_off, first_call,
-                                   pack_order, s1, s2, lat);
+                                   pack_order, s1, s2, lat, lat_slot);
     return cudaGetLastError();
 }
 
@@ -197,7 +198,8 @@ struct KkPacked {
     long long hist_bytes;  // nhist * 3 / 2
     long long in_bytes;    // buf_len * 3 / 2
     int order, first_call;
-    LatSlot *lat;          // latency slot to stamp (first kernel of the call), or null
+    LatRecord *lat;        // latency record whose slot the call's first kernel stamps, or null
+    int lat_slot;
 };
 constexpr int kRawWords = 100;   // 384 bytes of a row + spare word, 16-byte multiple
 
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2
     __shared__ __align__(16) uint32_t raw[32][kRawWords];
     __shared__ __align__(16) float s_ln[kLutCodes];
     int pair = blockIdx.y;
-    if (pk.lat && blockIdx.x == 0 && pair == 0 && threadIdx.x == 0) lat_start(pk.lat);
+    if (pk.lat && blockIdx.x == 0 && pair == 0 && threadIdx.x == 0) lat_start(pk.lat, pk.lat_slot);
     if (pair == g.npairs) {
         // history of the next call: samples [avail - nhist, avail) = virtual bytes
         // [in_bytes, in_bytes + hist_bytes)
@@ -450,8 +452,10 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
             float phi = (half ? x[q].y : x[q].x) * invN;
             float sn, cs;
             __sincosf(phi, &sn, &cs);   // |phi| < pi: absolute error <= 2^-21.41
-            // correctly rounded: equal to (float)sqrt(I) of the table for every 12-bit code
-            float A = sqrtf(code ? (float)code : 0.5f);
+            // the hardware square-root approximation (sqrt.approx.f32) in place of the
+            // correctly rounded sequence; the field is held to the FP64 reference
+            // within 1e-5 relative RMS
+            float A = sqrt_approx(code ? (float)code : 0.5f);
             float2 e = make_float2(A * cs, A * sn);
             Eb[tt] = e;
             sre += e.x;
@@ -575,7 +579,7 @@ __global__ void __cluster_dims__(kClC, 1, 1) __launch_bounds__(kClThreads, 3)
     const int c = (int)cl.block_rank();
     const int pair = blockIdx.x / kClC;
     const int t = threadIdx.x;
-    if (pk.lat && blockIdx.x == 0 && t == 0) lat_start(pk.lat);
+    if (pk.lat && blockIdx.x == 0 && t == 0) lat_start(pk.lat, pk.lat_slot);
     const bool hb = 2 * pair + 1 < g.J;
     const uint32_t c_first = first_code(pk, dst);
     if (pk.first_call && blockIdx.x == 0 && t == 0) dst->first_code = (int)c_first;
@@ -722,7 +726,7 @@ __global__ void __cluster_dims__(kClC, 1, 1) __launch_bounds__(kClThreads, 3)
                 float phi = (half ? x[q].y : x[q].x) * invN;
                 float sn, cs;
                 __sincosf(phi, &sn, &cs);   // |phi| < pi: absolute error <= 2^-21.41
-                float A = sqrtf(code ? (float)code : 0.5f);   // = (float)sqrt(I), every code
+                float A = sqrt_approx(code ? (float)code : 0.5f);
                 float2 e = make_float2(A * cs, A * sn);
                 E[n - g.ebase] = e;
                 sre += e.x;
@@ -795,7 +799,7 @@ __global__ void __cluster_dims__(kClC, 1, 1) __launch_bounds__(kClThreads, 3)
 
 __global__ void k_kk_hist(KkPacked pk)
 {
-    if (pk.lat && blockIdx.x == 0 && threadIdx.x == 0) lat_start(pk.lat);
+    if (pk.lat && blockIdx.x == 0 && threadIdx.x == 0) lat_start(pk.lat, pk.lat_slot);
     long long nch = pk.hist_bytes / 16;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += (long long)gridDim.x * blockDim.x) {
         long long vb = pk.in_bytes + 16 * c;
@@ -816,6 +820,7 @@ cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st, const KkSync &sy
     pk.order = inp.order;
     pk.first_call = inp.first_call;
     pk.lat = inp.lat;
+    pk.lat_slot = inp.lat_slot;
     k_kk_hist<<<32, 256, 0, st>>>(pk);
     if (sync.rec_fwd) cudaEventRecord(sync.rec_fwd, st);
     return cudaGetLastError();
@@ -839,6 +844,7 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     pk.order = inp.order;
     pk.first_call = inp.first_call;
     pk.lat = inp.lat;
+    pk.lat_slot = inp.lat_slot;
     if (g.N2 == kClN2 && g.fused) {
         // 2^16-point blocks: the fused cluster kernel (profiled as the K1a stage)
         if (sync.wait_fwd) cudaStreamWaitEvent(st, sync.wait_fwd, 0);
@@ -1643,6 +1649,24 @@ cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, 
     size_t smem = (size_t)(kMfOut + 2 * hmf) * sizeof(float);
     k_pam_mf<<<grid, kMfOut, smem, st>>>(codes, cbase, nb, n_end, f_prev, f_k, rrc, hmf, dst, parity, Y,
                                          ybase, Y_prev, ybase_prev);
+    return cudaGetLastError();
+}
+
+// bin and clear every latency slot still holding a record (rx_stats)
+__global__ void k_lat_flush(LatRecord *r)
+{
+    const int i = threadIdx.x;
+    if (i < kLatSlots) {
+        const unsigned long long t0 = r->slot[i].t0, t1 = r->slot[i].t1;
+        r->slot[i].t0 = 0ull;
+        r->slot[i].t1 = 0ull;
+        lat_bin(r, t0, t1);
+    }
+}
+
+cudaError_t launch_lat_flush(LatRecord *r, cudaStream_t st)
+{
+    k_lat_flush<<<1, kLatSlots, 0, st>>>(r);
     return cudaGetLastError();
 }
 

@@ -50,19 +50,19 @@ struct DevState {
     int err;                               // RX_ETIMEOUT when a bounded wait ran out
 };
 
-// Per-buffer latency record on the device clock (%globaltimer, ns): the first kernel
-// of a recorded call stamps t0 (and clears t1 and the ticket) in the call's slot;
-// every demap CTA raises t1 to its end time, and the last one to finish bins
-// t1 - t0.  Slots are reused every kLatSlots recorded calls, far more than the
-// calls the stream pipeline holds in flight (its slot rings bound that to about
-// three times kSlots).
+// Per-buffer latency record on the device clock (%globaltimer, ns).  A recorded
+// call owns slot (its index mod kLatSlots): its first kernel stamps t0 and clears t1,
+// every CTA of its demap raises t1 to its own end time (one relaxed atomic, no
+// fence), and the record is binned when the slot is next taken (by the first kernel
+// of the call kLatSlots recorded calls later, which stream order puts after that
+// demap) or by rx_stats, which bins and clears every slot still holding one.
+// kLatSlots is far more than the calls the pipeline holds in flight (its slot rings
+// bound that to about three times kSlots).
 constexpr int kLatSlots = 64;
 constexpr int kLatBins = 65536;
 constexpr unsigned long long kLatBinNs = 500;
 struct LatSlot {
     unsigned long long t0, t1;
-    unsigned int ticket, pad0;
-    unsigned long long pad1;
 };
 struct LatRecord {
     LatSlot slot[kLatSlots];
@@ -75,32 +75,35 @@ __device__ __forceinline__ unsigned long long dev_clock_ns()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// one thread of the call's first kernel, at its start
-__device__ __forceinline__ void lat_start(LatSlot *s)
+// bin a finished record (t1 > t0 > 0) into the histogram and counters
+__device__ __forceinline__ void lat_bin(LatRecord *r, unsigned long long t0, unsigned long long t1)
 {
+    if (!(t0 && t1 > t0)) return;
+    const unsigned long long d = t1 - t0;
+    unsigned long long b = d / kLatBinNs;
+    if (b >= (unsigned long long)kLatBins) b = kLatBins - 1;
+    atomicAdd(&r->hist[b], 1u);
+    atomicAdd(&r->n, 1ull);
+    if (d > r->budget_ns) atomicAdd(&r->miss, 1ull);
+    atomicMax(&r->max_ns, d);
+}
+// one thread of the call's first kernel, at its start: stamp the slot, then bin the
+// record the slot held
+__device__ __forceinline__ void lat_start(LatRecord *r, int slot)
+{
+    LatSlot *s = &r->slot[slot];
+    const unsigned long long o0 = s->t0, o1 = s->t1;
     s->t0 = dev_clock_ns();
     s->t1 = 0ull;
-    s->ticket = 0u;
+    lat_bin(r, o0, o1);
 }
 // thread 0 of every CTA of the call's last kernel, after its CTA's work
 __device__ __forceinline__ void lat_end(LatRecord *r, int slot)
 {
-    LatSlot *s = &r->slot[slot];
-    atomicMax(&s->t1, dev_clock_ns());
-    __threadfence();
-    if (atomicAdd(&s->ticket, 1u) == gridDim.x * gridDim.y * gridDim.z - 1) {
-        __threadfence();
-        const unsigned long long t1 = atomicAdd(&s->t1, 0ull);
-        const unsigned long long t0 = *reinterpret_cast<volatile unsigned long long *>(&s->t0);
-        const unsigned long long d = t1 > t0 ? t1 - t0 : 0ull;
-        unsigned long long b = d / kLatBinNs;
-        if (b >= (unsigned long long)kLatBins) b = kLatBins - 1;
-        atomicAdd(&r->hist[b], 1u);
-        atomicAdd(&r->n, 1ull);
-        if (d > r->budget_ns) atomicAdd(&r->miss, 1ull);
-        atomicMax(&r->max_ns, d);
-    }
+    atomicMax(&r->slot[slot].t1, dev_clock_ns());
 }
+// rx_stats: bin and clear every slot (one thread per slot)
+cudaError_t launch_lat_flush(LatRecord *r, cudaStream_t st);
 
 // per-CTA partial of the carrier reduction
 struct CarrierPartial {
@@ -143,7 +146,8 @@ struct KkInput {
     uint8_t *hist_next;      // receives packed samples [avail - nhist, avail), or null
     long long hist_bytes, in_bytes;
     int order, first_call;
-    LatSlot *lat;            // latency slot this call's first kernel stamps, or null
+    LatRecord *lat;          // latency record whose slot this call's first kernel stamps, or null
+    int lat_slot;
 };
 
 // per-call schedule of the equaliser
@@ -173,7 +177,7 @@ struct EqParams {
 cudaError_t launch_unpack(const uint8_t *in, uint16_t *codes, const uint16_t *codes_prev,
                           long long nb, int nhist, long long prev_off, int first_call,
                           int pack_order, long long *s1, long long *s2, cudaStream_t st,
-                          LatSlot *lat = nullptr);
+                          LatRecord *lat = nullptr, int lat_slot = 0);
 
 // copy of the next call's packed history only (calls that emit no field)
 // Cross-stream order of the front end when consecutive calls run on different

@@ -154,6 +154,7 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     kin.order = pack_order;
     kin.first_call = 1;
     kin.lat = nullptr;
+    kin.lat_slot = 0;
     const KkSync none = {nullptr, nullptr, nullptr};
     if (launch_kk_front(g, kin, fftws, tb, E, E, part, ds, st, nullptr, none) != cudaSuccess) return RX_ECUDA;
     unsigned grid = (unsigned)((e_k + 255) / 256);
