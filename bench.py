@@ -943,8 +943,9 @@ def stability_leg(args):
             "per_buffer_latency": {"calls": st["lat_calls"], "budget_ms": st["deadline_ms"],
                                    "deadline_misses": st["deadline_misses"], "p50_ms": st["lat_p50_ms"],
                                    "p99_ms": st["lat_p99_ms"], "max_ms": st["lat_max_ms"],
-                                   "note": "device time from a buffer's host-to-device copy to its bits in host "
-                                           "memory, 20 buffers enqueued at a time"},
+                                   "note": "the receiver's own record: device time from the start of a buffer's "
+                                           "first kernel to the end of its demap (GPU global timer), 20 buffers "
+                                           "enqueued at a time"},
             "note": "the first window holds the training symbols and is excluded from the summary",
             "series": [{"w": x["window"], "q": None if x["q_db"] is None else round(x["q_db"], 3),
                         "ms": round(x["device_ms"], 3)} for x in series]}
