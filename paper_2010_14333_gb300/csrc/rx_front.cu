@@ -970,24 +970,13 @@ __global__ void __launch_bounds__(kMfThreads) k_kk_mf_t(const float2 *__restrict
     int idx = (int)((((n0 % ds_den) + ds_den) % ds_den + 2LL * threadIdx.x) % ds_den);
     idx = (int)(((long long)idx * ds_num) % ds_den);
     const int step = (int)((2LL * kMfThreads * ds_num) % ds_den), odd = ds_num % ds_den;
-    // a pair of samples is one 16-byte load when the pairs start on 16 bytes
-    const bool vec = ((n0 - ebase) & 1) == 0;
     for (int pp = threadIdx.x; pp < NPAIR; pp += kMfThreads) {
         long long n = n0 + 2 * pp;
-        const bool ia = n >= 0 && n < e_k, ib = n + 1 >= 0 && n + 1 < e_k;
-        float2 ea = make_float2(0.f, 0.f), eb = ea;
-        if (vec && ia && ib) {
-            const float4 v = *reinterpret_cast<const float4 *>(E + (n - ebase));
-            ea = make_float2(v.x, v.y);
-            eb = make_float2(v.z, v.w);
-        } else {
-            if (ia) ea = E[n - ebase];
-            if (ib) eb = E[n + 1 - ebase];
-        }
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (n >= 0 && n < e_k) a = cmul(csub(E[n - ebase], c), __ldg(ds_tab + idx));
         int idx1 = idx + odd;
         idx1 = idx1 >= ds_den ? idx1 - ds_den : idx1;
-        const float2 a = ia ? cmul(csub(ea, c), __ldg(ds_tab + idx)) : make_float2(0.f, 0.f);
-        const float2 b = ib ? cmul(csub(eb, c), __ldg(ds_tab + idx1)) : make_float2(0.f, 0.f);
+        if (n + 1 >= 0 && n + 1 < e_k) b = cmul(csub(E[n + 1 - ebase], c), __ldg(ds_tab + idx1));
         pr[pad8(pp)] = make_float4(a.x, a.y, b.x, b.y);
         idx += step;
         idx = idx >= ds_den ? idx - ds_den : idx;
