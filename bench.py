@@ -452,6 +452,14 @@ def gpu_arm(args, rank, world, local):
                               "ms_per_launch": t_live},
                 "peak_source": "FP32: %d SMs (queried) x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured)" % (
                     sms, sm_max)}
+        # cross-check of the derived peak: the library's FMA-rate self-test on this GPU now
+        try:
+            fma = rx.rx_selftest_fma_rate(1 << 16, sid)
+            roof["fma_rate_measured"] = {"tflops": fma, "frac": ach / fma if fma > 0 else None,
+                                         "kernel": "rx_selftest_fma_rate: 8 independent FMA chains per thread, "
+                                                   "every SM filled, CUDA events"}
+        except rx.RxError:
+            roof["fma_rate_measured"] = None
     else:
         ach = stages[dom]["gbs"]
         live = BYTES_PER_SAMPLE[dom] * NB / (t_live * 1e-3) / 1e9 if t_live > 0 else None

@@ -524,6 +524,15 @@ rx_status rx_set_resampler(rx_handle *h, int64_t step, int64_t nudge, void *cuda
  * error.  Synchronises the stream; the context stays usable. */
 rx_status rx_selftest_wait_timeout(void *cuda_stream);
 
+/* FP32 arithmetic rate of this GPU, measured: every SM runs resident CTAs whose threads
+ * each advance 8 independent FMA chains for `iters` steps (16 iters flop per thread),
+ * timed with CUDA events on the stream (after one untimed launch).  *tflops receives
+ * flop / time in TFLOP/s, the denominator of the ALU rooflines measured on the part as
+ * it runs (clock and power as they are); the values the chains end with go to a
+ * device word so that no FMA is removed.  iters in [1, 2^24].  Synchronises the
+ * stream.  Not part of the receiver: the paper has no counterpart. */
+rx_status rx_selftest_fma_rate(int iters, double *tflops, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

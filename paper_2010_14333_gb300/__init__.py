@@ -54,7 +54,7 @@ class RxError(RuntimeError):
     pass
 
 
-EXPORTED = sorted(["rx_selftest_wait_timeout", "rx_clock_estimate", "rx_default_config", "rx_create", "rx_process", "rx_process_host", "rx_max_bits",
+EXPORTED = sorted(["rx_selftest_wait_timeout", "rx_selftest_fma_rate", "rx_clock_estimate", "rx_default_config", "rx_create", "rx_process", "rx_process_host", "rx_max_bits",
                    "rx_stats", "rx_debug_copy", "rx_set_taps", "rx_destroy", "rx_strerror",
                    "rx_profile", "rx_profile_read", "rx_kk_field_noalloc", "rx_cnn_nparams", "rx_cnn_create",
                    "rx_cnn_set_params", "rx_cnn_get_params", "rx_cnn_forward", "rx_cnn_grad",
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
     L.rx_default_config.argtypes = [C.c_int, P(RxConfig)]
     L.rx_selftest_wait_timeout.argtypes = [vp]
     L.rx_selftest_wait_timeout.restype = C.c_int
+    L.rx_selftest_fma_rate.argtypes = [C.c_int, P(C.c_double), vp]
     L.rx_clock_estimate.argtypes = [vp, P(C.c_double), P(C.c_double), vp]
     L.rx_clock_track.argtypes = [vp, P(C.c_double), P(C.c_double), P(i64), vp]
     L.rx_clock_retime.argtypes = [vp, P(i64), P(i64), vp]
@@ -198,6 +199,13 @@ def rx_clock_retime(h: int, stream: int = 0):
 
 def rx_set_resampler(h: int, step: int, nudge: int = 0, stream: int = 0):
     _check(load().rx_set_resampler(h, step, nudge, stream))
+
+
+def rx_selftest_fma_rate(iters: int = 1 << 16, stream: int = 0) -> float:
+    """Measured FP32 FMA rate of this GPU in TFLOP/s (see include/rx.h)."""
+    t = C.c_double()
+    _check(load().rx_selftest_fma_rate(int(iters), C.byref(t), stream))
+    return t.value
 
 
 def rx_selftest_wait_timeout(stream: int = 0) -> int:

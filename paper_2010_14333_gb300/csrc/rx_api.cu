@@ -408,6 +408,54 @@ rx_status rx_selftest_wait_timeout(void *stream)
     return v == (int)RX_ETIMEOUT ? RX_ETIMEOUT : v == (int)RX_OK ? RX_OK : RX_ECUDA;
 }
 
+// 8 independent FMA chains per thread; the sum of the chains goes to *sink
+__global__ void __launch_bounds__(256) k_fma_rate(int iters, float a, float b, float *sink)
+{
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) x[j] = (float)(threadIdx.x + j) * 1e-3f;
+    for (int i = 0; i < iters; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) x[j] = fmaf(x[j], a, b);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; j++) s += x[j];
+    if (s == 1234.5f) *sink = s;   // practically never; keeps the chains live
+}
+
+rx_status rx_selftest_fma_rate(int iters, double *tflops, void *stream)
+{
+    if (!tflops || iters < 1 || iters > (1 << 24)) return RX_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0, per = 0;
+    float *sink = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    rx_status r = RX_ECUDA;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fma_rate, 256, 0) == cudaSuccess && per > 0 &&
+        cudaMalloc(&sink, sizeof(float)) == cudaSuccess && cudaEventCreate(&a) == cudaSuccess &&
+        cudaEventCreate(&b) == cudaSuccess) {
+        const unsigned grid = (unsigned)(nsm * per);
+        // a close to 1, b small: the chains stay finite for any iters
+        k_fma_rate<<<grid, 256, 0, st>>>(iters, 0.999999f, 1e-6f, sink);
+        cudaEventRecord(a, st);
+        k_fma_rate<<<grid, 256, 0, st>>>(iters, 0.999999f, 1e-6f, sink);
+        cudaEventRecord(b, st);
+        float ms = 0.f;
+        if (cudaGetLastError() == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms > 0.f) {
+            *tflops = 16.0 * iters * (double)grid * 256.0 / (ms * 1e-3) / 1e12;
+            r = RX_OK;
+        }
+    }
+    cudaGetLastError();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (sink) cudaFree(sink);
+    return r;
+}
+
 const char *rx_strerror(rx_status s)
 {
     switch (s) {

@@ -184,3 +184,16 @@ def test_bounded_wait_reports_timeout_and_context_stays_usable():
         r.process(torch.from_numpy(p).cuda())
     s = r.stats()
     assert s["device_error"] == 0 and s["bits"] > 0
+
+
+def test_fma_rate_selftest():
+    """The FMA-rate self-test reports a rate between a tenth of and a little above the
+    peak derived from the SM count and the maximum SM clock, and rejects bad sizes."""
+    props = torch.cuda.get_device_properties(0)
+    derived = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    sid = torch.cuda.current_stream().cuda_stream
+    t = rx.rx_selftest_fma_rate(1 << 14, sid)
+    assert 0.1 * derived < t < 1.1 * derived, (t, derived)
+    for bad in (0, (1 << 24) + 1):
+        with pytest.raises(rx.RxError):
+            rx.rx_selftest_fma_rate(bad, sid)
