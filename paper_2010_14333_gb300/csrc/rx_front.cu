@@ -1639,12 +1639,90 @@ cudaError_t launch_pam_fd1024(const uint16_t *codes, long long cbase, long long 
     return cudaGetLastError();
 }
 
+// Register-tiled PAM matched filter for a compile-time half length HMF: each thread
+// computes kPmR consecutive outputs from a sliding window held in registers (one
+// shared-memory load per tap), the taps read from shared memory as broadcasts.  Per
+// output the products are accumulated in the same order as k_pam_mf (tap index
+// ascending), so the outputs are the same bit for bit.
+constexpr int kPmThreads = 128, kPmR = 8, kPmTile = kPmThreads * kPmR;
+
+template <int HMF>
+__global__ void __launch_bounds__(kPmThreads) k_pam_mf_t(const uint16_t *__restrict__ codes, long long cbase,
+                                                        long long nb, long long n_end, long long f_prev, long long f_k,
+                                                        const float *__restrict__ rrc, DevState *dst, int parity,
+                                                        float *__restrict__ Y, long long ybase,
+                                                        const float *__restrict__ Y_prev, long long ybase_prev)
+{
+    __shared__ float xf[kPmTile + 2 * HMF];
+    __shared__ float s_h[2 * HMF + 1];
+    __shared__ float s_mu, s_inv;
+    if (threadIdx.x == 0) {
+        double mu = (double)dst->pam_s1[parity] / (double)nb;
+        double var = (double)dst->pam_s2[parity] / (double)nb - mu * mu;
+        double inv = (var > 0.0) ? 1.0 / sqrt(var) : 1.0;
+        s_mu = (float)mu;
+        s_inv = (float)inv;
+        if (blockIdx.x == 0) {
+            dst->pam_mu = mu;
+            dst->pam_inv_sd = inv;
+        }
+    }
+    for (int i = threadIdx.x; i <= 2 * HMF; i += kPmThreads) s_h[i] = __ldg(rrc + i);
+    __syncthreads();
+    const long long m0 = f_prev + (long long)blockIdx.x * kPmTile;
+    const long long n0 = m0 - HMF;
+    const float mu = s_mu, inv = s_inv;
+    for (int i = threadIdx.x; i < kPmTile + 2 * HMF; i += kPmThreads) {
+        const long long n = n0 + i;
+        xf[i] = (n >= 0 && n < n_end) ? ((float)codes[n - cbase] - mu) * inv : 0.f;
+    }
+    if (blockIdx.x == 0) {
+        for (long long m = ybase + threadIdx.x; m < f_prev; m += blockDim.x)
+            Y[m - ybase] = (m < 0) ? 0.f : Y_prev[m - ybase_prev];
+        if (threadIdx.x == 0) {   // the sums of the next call start from zero
+            dst->pam_s1[parity ^ 1] = 0;
+            dst->pam_s2[parity ^ 1] = 0;
+        }
+    }
+    __syncthreads();
+    // output j = j0 + r: y = sum_{i=-HMF}^{HMF} h[i + HMF] xf[j + HMF - i]; with u = HMF - i
+    // running from 2 HMF down to 0 the window xf[j0 + u + r] slides down by one per tap
+    const int j0 = kPmR * threadIdx.x;
+    float win[kPmR], acc[kPmR];
+#pragma unroll
+    for (int r = 0; r < kPmR; r++) {
+        win[r] = xf[j0 + 2 * HMF + r];
+        acc[r] = 0.f;
+    }
+#pragma unroll
+    for (int u = 2 * HMF; u >= 0; u--) {
+        const float hu = s_h[2 * HMF - u];
+#pragma unroll
+        for (int r = 0; r < kPmR; r++) acc[r] = fmaf(hu, win[r], acc[r]);
+        if (u > 0) {
+#pragma unroll
+            for (int r = kPmR - 1; r > 0; r--) win[r] = win[r - 1];
+            win[0] = xf[j0 + u - 1];
+        }
+    }
+    const long long mb = m0 + j0;
+#pragma unroll
+    for (int r = 0; r < kPmR; r++)
+        if (mb + r < f_k) Y[mb + r - ybase] = acc[r];
+}
+
 cudaError_t launch_pam_mf(const uint16_t *codes, long long cbase, long long nb, long long n_end, long long f_prev,
                           long long f_k, const float *rrc, int hmf, DevState *dst, int parity,
                           float *Y, long long ybase, const float *Y_prev, long long ybase_prev,
                           cudaStream_t st)
 {
     long long n = f_k - f_prev;
+    if (hmf == 16) {   // the default span (16 symbols at 2 samples/symbol)
+        unsigned grid = (unsigned)((n + kPmTile - 1) / kPmTile);
+        k_pam_mf_t<16><<<grid, kPmThreads, 0, st>>>(codes, cbase, nb, n_end, f_prev, f_k, rrc, dst, parity, Y, ybase,
+                                                    Y_prev, ybase_prev);
+        return cudaGetLastError();
+    }
     unsigned grid = (unsigned)((n + kMfOut - 1) / kMfOut);
     size_t smem = (size_t)(kMfOut + 2 * hmf) * sizeof(float);
     k_pam_mf<<<grid, kMfOut, smem, st>>>(codes, cbase, nb, n_end, f_prev, f_k, rrc, hmf, dst, parity, Y,
