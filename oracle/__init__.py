@@ -32,7 +32,7 @@ class OrxCfg(C.Structure):
         ("bps_b", C.c_int32), ("amb_syms", C.c_int32), ("prbs_seed", C.c_uint32),
         ("eq_frozen", C.c_int32), ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
         ("clk_track", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
-        ("diff_code", C.c_int32), ("pad_dc", C.c_int32),
+        ("diff_code", C.c_int32), ("eq_mode", C.c_int32),
     ]
 
 
@@ -286,12 +286,12 @@ KK_DEFAULTS = dict(sps=4, pack_order=0, ols_n=65536, ols_v=4096, ds_num=11, ds_d
                    rrc_beta=0.1, mf_span=16, ntaps=31, ntrain=16384, ncma=8192, eq_block=128,
                    win=64, mu=1e-3, mu_train=1e-3, mu_cma=1e-3, bps_b=32, amb_syms=1024,
                    prbs_seed=1, eq_frozen=0, mf_mode=0, fd_n=1024, fd_taps=203, clk_track=0, rs_step=0,
-                   rs_phase0=0, diff_code=0, pad_dc=0)
+                   rs_phase0=0, diff_code=0, eq_mode=0)
 PAM_DEFAULTS = dict(sps=2, pack_order=0, ols_n=0, ols_v=0, ds_num=0, ds_den=1, rrc_beta=0.1,
                     mf_span=16, ntaps=15, ntrain=4096, ncma=0, eq_block=256, win=64, mu=1e-3,
                     mu_train=1e-3, mu_cma=0.0, bps_b=1, amb_syms=0, prbs_seed=1, eq_frozen=0, mf_mode=0,
                     fd_n=1024, fd_taps=503, clk_track=0, rs_step=0, rs_phase0=0,
-                    diff_code=0, pad_dc=0)
+                    diff_code=0, eq_mode=0)
 
 
 def default_cfg(fmt: int, buf_len: int, **kw) -> dict:

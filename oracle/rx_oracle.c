@@ -383,7 +383,9 @@ orx *orx_create(const orx_cfg *cfg)
     orx *h = xcalloc(1, sizeof(orx));
     h->c = *cfg;
     int f = cfg->format;
-    if (f < 0 || f > 4 || cfg->ntaps < 1 || !(cfg->ntaps & 1) || cfg->win < 1 || cfg->win > 4096 ||
+    if (f < 0 || f > 4 || cfg->ntaps < 1 || (!(cfg->ntaps & 1) && cfg->eq_mode != 1) || cfg->win < 1 || cfg->win > 4096 ||
+        cfg->eq_mode < 0 || cfg->eq_mode > 1 ||
+        (cfg->eq_mode == 1 && (f < 3 || cfg->eq_frozen || cfg->ntaps < 2 || cfg->ntaps > 31)) ||
         cfg->eq_block < cfg->win || cfg->eq_block % cfg->win || cfg->ntrain < 0 || cfg->ntrain % cfg->win ||
         cfg->buf_len < 2 || (cfg->buf_len & 1) || cfg->sps < 2 || (cfg->sps & 1) || cfg->mf_span < 0 ||
         (f >= 3 && (cfg->ncma < 0 || cfg->ncma > cfg->ntrain || cfg->ncma % cfg->win || cfg->bps_b < 1 ||
@@ -587,6 +589,47 @@ static cx y_at(const ctx *x, int64_t m)
     if (m < 0) return cx_mk(0.0, 0.0);
     if (m >= x->y_start) return x->y[m - x->y_start];
     return h->yhist[m - h->yhist_start];
+}
+
+/* ------------------------------------------------ symbol-by-symbol DD-LMS (KK)
+ * The paper's KK equaliser (Sec. 2, KK chain): a short decision-directed LMS
+ * whose complex taps are updated after every symbol, so that they follow the
+ * clock phase (a fractional delay at 2 samples/symbol) and the symbol phase (a
+ * common rotation) together, with no separate phase search.  For symbols
+ * k0 .. k0+n-1, with th = (ntaps-1)/2:
+ *   z_k = sum_{j=0}^{ntaps-1} conj(w_j) y[2k + th - j]
+ *   decision per dimension on s z_k
+ *   error: CMA e = z (R2 - |z|^2) for k < cma_until (mu_cma), else
+ *          decision-directed e = d/s - z (mu)
+ *   then at once w_j += mu y[2k + th - j] conj(e). */
+static void dd_symbols(ctx *x, cx *w, int64_t k0, int64_t n, int64_t cma_until, double mu_cma, double mu,
+                       cx *z, cx *v, int32_t *draw, int32_t *nearf)
+{
+    orx *h = x->h;
+    int nt = h->c.ntaps, th = h->th;
+    for (int64_t q = 0; q < n; q++) {
+        int64_t k = k0 + q;
+        cx acc = cx_mk(0.0, 0.0);
+        for (int j = 0; j < nt; j++) acc = cx_add(acc, cx_mul(cx_conj(w[j]), y_at(x, 2 * k + th - j)));
+        z[q] = acc;
+        cx t = cx_scale(acc, h->scale);
+        v[q] = t;
+        int LI = decide_dim(t.re, h->mq), LQ = decide_dim(t.im, h->mq);
+        draw[2 * q] = LI; draw[2 * q + 1] = LQ;
+        nearf[q] = near_dim(t.re, h->mq) || near_dim(t.im, h->mq);
+        cx e;
+        double m;
+        if (k < cma_until) {
+            e = cx_scale(acc, h->r2 - cx_abs2(acc));
+            m = mu_cma;
+        } else {
+            cx d = cx_mk(level_value(LI, h->mq), level_value(LQ, h->mq));
+            e = cx_sub(cx_scale(d, 1.0 / h->scale), acc);
+            m = mu;
+        }
+        for (int j = 0; j < nt; j++)
+            w[j] = cx_add(w[j], cx_scale(cx_mul(y_at(x, 2 * k + th - j), cx_conj(e)), m));
+    }
 }
 
 /* ----------------------------------------------------------- equaliser window
@@ -896,10 +939,14 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
     if (nproc > 0 && !h->trained) {
         /* training at stream start, sequential over windows: KK CMA for the first
          * ncma symbols then decision-directed; PAM data-aided LMS */
-        for (int64_t k0 = 0; k0 < c->ntrain; k0 += W) {
-            int mode = h->kk ? (k0 < c->ncma ? 0 : 2) : 1;
-            double mu = h->kk ? (mode == 0 ? c->mu_cma : c->mu) : c->mu_train;
-            eq_window(&X, h->w, k0, mode, mu, Z + k0, Vv + k0, draw + 2 * k0, nearf + k0, NULL);
+        if (c->eq_mode == 1) {
+            dd_symbols(&X, h->w, 0, c->ntrain, c->ncma, c->mu_cma, c->mu, Z, Vv, draw, nearf);
+        } else {
+            for (int64_t k0 = 0; k0 < c->ntrain; k0 += W) {
+                int mode = h->kk ? (k0 < c->ncma ? 0 : 2) : 1;
+                double mu = h->kk ? (mode == 0 ? c->mu_cma : c->mu) : c->mu_train;
+                eq_window(&X, h->w, k0, mode, mu, Z + k0, Vv + k0, draw + 2 * k0, nearf + k0, NULL);
+            }
         }
         h->trained = 1;
         pay_lo = c->ntrain;
@@ -923,6 +970,13 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
         for (int64_t b0 = pay_lo; b0 < q_k; b0 += c->eq_block) {
             memcpy(wb, h->w, sizeof(cx) * (size_t)c->ntaps);
             int last = b0 + c->eq_block >= q_k;
+            if (c->eq_mode == 1) {
+                /* symbol-by-symbol DD-LMS: no phase search, window index 0 throughout */
+                int64_t o = b0 - sym_lo;
+                dd_symbols(&X, wb, b0, c->eq_block, -1, 0.0, c->mu, Z + o, Vv + o, draw + 2 * o, nearf + o);
+                memcpy(wlast, wb, sizeof(cx) * (size_t)c->ntaps);
+                continue;
+            }
             for (int64_t k0 = b0; k0 < b0 + c->eq_block; k0 += W) {
                 int64_t o = k0 - sym_lo;
                 winres R = eq_window(&X, wb, k0, 2, c->mu, Z + o, Vv + o, draw + 2 * o, nearf + o,

@@ -62,7 +62,10 @@ typedef struct {
     int32_t diff_code;   /* KK: 1 = differentially quadrant-coded symbols: the first two bits
                             of a symbol (Gray) step the quadrant, the rest pick a rotation-
                             invariant point in it; decoded bits are quadrant differences  */
-    int32_t pad_dc;
+    int32_t eq_mode;     /* KK equaliser: 0 the block-window CMA / DD-LMS of ntaps taps with the
+                            blind phase search; 1 the paper's short decision-directed LMS,
+                            updated symbol by symbol, whose complex taps track the clock and
+                            the symbol phase together (no phase search; ntaps 2..31, any parity) */
 } orx_cfg;
 
 typedef struct {
