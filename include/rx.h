@@ -129,7 +129,20 @@ typedef struct {
                             ms for 2^22 samples at 4 GS/s).  0 = five buffer durations
                             (buf_len / fs each); > 0 = this budget in ms; < 0 = no latency
                             record (the kernels then take no timestamps)                   */
+    int32_t eq_mode;     /* KK equaliser (rx_eq_mode): RX_EQ_WINDOW (default) = the adaptive
+                            FIR of ntaps taps updated once per 64-symbol window, with the
+                            32-phase blind phase search; RX_EQ_DD_SYMBOL = the paper's short
+                            decision-directed LMS (Sec. 2, KK chain: 4 taps recover the clock
+                            and symbol phase), updated after every symbol, no phase search
+                            (ntaps 2..8, any parity; CMA for the first ncma training symbols).
+                            Its blocks restart from the call's start taps, so it suits links
+                            whose carrier phase holds still over a call (the self-coherent KK
+                            link); relative laser phase noise needs the phase search          */
+    int32_t pad_eq;
 } rx_config;
+
+/* Equaliser forms of the KK chain (rx_config.eq_mode). */
+typedef enum { RX_EQ_WINDOW = 0, RX_EQ_DD_SYMBOL = 1 } rx_eq_mode;
 
 /* Reduction to 2 samples/symbol of the KK chain (rx_config.mf_mode). */
 typedef enum { RX_MF_TIME = 0, RX_MF_FD = 1 } rx_mf_mode;

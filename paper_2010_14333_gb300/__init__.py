@@ -34,7 +34,7 @@ class RxConfig(C.Structure):
         ("debug", C.c_int32), ("fir_prec", C.c_int32), ("kk_front", C.c_int32), ("eq_warps", C.c_int32),
         ("mf_mode", C.c_int32), ("fd_n", C.c_int32), ("fd_taps", C.c_int32),
         ("clk_track", C.c_int32), ("rs_step", C.c_int64), ("rs_phase0", C.c_int64),
-        ("cnn_bf16", C.c_int32), ("diff_code", C.c_int32), ("deadline_ms", C.c_double),
+        ("cnn_bf16", C.c_int32), ("diff_code", C.c_int32), ("deadline_ms", C.c_double), ("eq_mode", C.c_int32), ("pad_eq", C.c_int32),
     ]
 
 
@@ -65,6 +65,7 @@ EXPORTED = sorted(["rx_selftest_wait_timeout", "rx_selftest_fma_rate", "rx_clock
                    "rx_clock_track", "rx_clock_retime", "rx_set_resampler"])
 RX_GROUP_GRAPH, RX_GROUP_TUNE = 1, 2
 RX_MF_TIME, RX_MF_FD = 0, 1
+RX_EQ_WINDOW, RX_EQ_DD_SYMBOL = 0, 1
 STAGES = ["unpack", "kk_fwd", "kk_rows", "kk_inv", "mf", "eq", "demap"]
 
 _lib = None

@@ -599,7 +599,11 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     double ratio = fs / baud;
     int sps = (int)floor(ratio + 0.5);
     if (fabs(ratio - sps) > 1e-9 * ratio || sps != (kk ? 4 : 2)) return RX_EINVAL;
-    if (c.pack_order < 0 || c.pack_order > 1 || c.ntaps < 1 || c.ntaps > kMaxTaps || !(c.ntaps & 1) ||
+    if (c.eq_mode < RX_EQ_WINDOW || c.eq_mode > RX_EQ_DD_SYMBOL ||
+        (c.eq_mode == RX_EQ_DD_SYMBOL && (!kk || c.ntaps < 2 || c.ntaps > 8 || c.fir_prec != RX_FIR_ADAPTIVE)))
+        return RX_EINVAL;
+    if (c.pack_order < 0 || c.pack_order > 1 || c.ntaps < 1 || c.ntaps > kMaxTaps ||
+        (!(c.ntaps & 1) && c.eq_mode != RX_EQ_DD_SYMBOL) ||
         c.win != kWin || c.eq_block < kWin || c.eq_block % kWin || c.ntrain < 0 || c.ntrain % kWin ||
         c.mf_span < 0 || c.mf_span % 2 || sps * c.mf_span / 2 > kEHist / 2 || !(c.rrc_beta >= 0) ||
         c.rrc_beta > 1 || c.eq_block > kMaxEqBlock)
@@ -658,6 +662,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     p.mq = h->mq;
     p.bps = h->bps;
     p.ntaps = c.ntaps;
+    p.dd = c.eq_mode == RX_EQ_DD_SYMBOL;
     p.th = h->th;
     p.win = c.win;
     p.eq_block = c.eq_block;

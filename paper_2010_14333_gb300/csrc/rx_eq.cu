@@ -600,6 +600,136 @@ static cudaError_t prepare_eq_t(const EqParams &p)
     return cudaFuncSetAttribute(k_eq<QAM, NT, MQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
+// ----------------------------------- symbol-by-symbol DD-LMS (KK, eq_mode 1)
+// The paper's short KK equaliser (Sec. 2, KK chain): a decision-directed LMS
+// whose complex taps are updated after every symbol, so that they follow the
+// clock phase and the symbol phase together; no phase search.  One thread runs
+// one block's recursion (the training: one thread over the training symbols,
+// CMA for the first ncma):
+//   z_k = sum_j conj(w_j) y[2k + TH - j],  decision on s z_k,
+//   e = z (R2 - |z|^2) (CMA) or d / s - z (decision directed),
+//   w_j += mu y[2k + TH - j] conj(e).
+// The inputs of the next symbol are those of this one moved by two samples.
+template <int NT, int MQ>
+__global__ void __launch_bounds__(128)
+    k_eq_dd(EqParams p, EqGeom g, int train, const float2 *__restrict__ Y, float2 *taps_in, float2 *taps_out,
+            uint8_t *__restrict__ dec, float2 *__restrict__ dbg_z)
+{
+    constexpr int TH = (NT - 1) / 2;
+    const long long blk = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (train ? blk > 0 : blk >= g.nblk) return;
+    float2 w[NT];
+#pragma unroll
+    for (int j = 0; j < NT; j++) w[j] = taps_in[j];
+    const long long k0 = train ? 0 : g.pay_lo + blk * p.eq_block;
+    const long long n = train ? p.ntrain : p.eq_block;
+    const long long cma_until = train ? p.ncma : -1;
+    const float s = p.scale, inv_s = 1.0f / p.scale;
+    float2 yv[NT];   // yv[j] = y[2k + TH - j]
+#pragma unroll
+    for (int j = 0; j < NT; j++) yv[j] = Y[2 * k0 + TH - j - g.ybase];
+    for (long long q = 0; q < n; q++) {
+        const long long k = k0 + q;
+        float zr = 0.f, zi = 0.f;
+#pragma unroll
+        for (int j = 0; j < NT; j++) {   // conj(w) y
+            zr = fmaf(w[j].x, yv[j].x, fmaf(w[j].y, yv[j].y, zr));
+            zi = fmaf(w[j].x, yv[j].y, fmaf(-w[j].y, yv[j].x, zi));
+        }
+        const float vr = s * zr, vi = s * zi;
+        const int LI = decide_t<MQ>(vr), LQ = decide_t<MQ>(vi);
+        const bool nr = near_t<MQ>(vr) || near_t<MQ>(vi);
+        if (!train) dec[k - g.pay_lo] = (uint8_t)(LI | (LQ << 3) | (nr ? 64 : 0));
+        if (dbg_z) dbg_z[k - g.sym_lo] = make_float2(zr, zi);
+        float er, ei, mu;
+        if (k < cma_until) {
+            const float f = p.r2 - (zr * zr + zi * zi);
+            er = zr * f;
+            ei = zi * f;
+            mu = p.mu_cma;
+        } else {
+            er = (float)(2 * LI - (MQ - 1)) * inv_s - zr;
+            ei = (float)(2 * LQ - (MQ - 1)) * inv_s - zi;
+            mu = p.mu;
+        }
+#pragma unroll
+        for (int j = 0; j < NT; j++) {   // w += mu y conj(e)
+            w[j].x = fmaf(mu, fmaf(yv[j].x, er, yv[j].y * ei), w[j].x);
+            w[j].y = fmaf(mu, fmaf(yv[j].y, er, -yv[j].x * ei), w[j].y);
+        }
+        if (q + 1 < n) {
+#pragma unroll
+            for (int j = NT - 1; j >= 2; j--) yv[j] = yv[j - 2];
+            yv[1] = Y[2 * k + TH + 1 - g.ybase];
+            yv[0] = Y[2 * k + TH + 2 - g.ybase];
+        }
+    }
+    if (train) {
+#pragma unroll
+        for (int j = 0; j < NT; j++) taps_in[j] = w[j];
+    } else if (blk == g.nblk - 1) {
+#pragma unroll
+        for (int j = 0; j < NT; j++) taps_out[j] = w[j];
+    }
+}
+
+// window records of the symbol-by-symbol form: one warp per 64-symbol window, from
+// the decisions: bit errors under the four absolute pi/2 rotations (as the window
+// equaliser scores them), near-threshold count, phase index 0
+template <int MQ>
+__global__ void __launch_bounds__(128)
+    k_dd_score(EqParams p, EqGeom g, const uint8_t *__restrict__ dec, uint8_t *__restrict__ winb,
+               uint4 *__restrict__ winrec, float4 *__restrict__ dbg_win, const uint32_t *__restrict__ prbs_bits)
+{
+    constexpr int NB = MQ == 2 ? 1 : 2, BPS = 2 * NB;
+    const int lane = threadIdx.x & 31;
+    const long long wi = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wi >= g.nwin) return;
+    const long long k0 = g.pay_lo + wi * kWin;
+    const int pwin = (int)(((long long)BPS * k0) % 32767);
+    unsigned eA = 0, eB = 0, se = 0, nn = 0;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int q = lane + 32 * h;
+        const int d = dec[wi * kWin + q];
+        const int LI = d & 7, LQ = (d >> 3) & 7;
+        const int ref = ref_bits<BPS>(prbs_bits, pwin + BPS * q);
+        constexpr int cm = MQ == 2 ? 1 : 2;
+        const int gI = gray(LI), gQ = gray(LQ);
+        const int X = ((gI << NB) | gQ) ^ ref, Xs = ((gQ << NB) | gI) ^ ref;
+        const unsigned n0 = __popc(X), n1 = __popc(Xs ^ cm), n2 = __popc(X ^ ((cm << NB) | cm)),
+                       n3 = __popc(Xs ^ (cm << NB));
+        eA += n0 + (n1 << 16);
+        eB += n2 + (n3 << 16);
+        se += (unsigned)(n0 > 0) | ((unsigned)(n1 > 0) << 8) | ((unsigned)(n2 > 0) << 16) | ((unsigned)(n3 > 0) << 24);
+        nn += (d & 64) != 0;
+    }
+    eA = warp_sum_i(eA);
+    eB = warp_sum_i(eB);
+    se = warp_sum_i(se);
+    nn = warp_sum_i(nn);
+    if (lane == 0) {
+        winb[wi] = 0;
+        winrec[wi] = make_uint4(eA, eB, se, nn << 8);
+        if (dbg_win) dbg_win[wi] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <int NT, int MQ>
+static cudaError_t launch_eq_dd(const EqParams &p, const EqGeom &g, int train, const float2 *Y, float2 *taps_in,
+                                float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec, float4 *dbg_win,
+                                float2 *dbg_z, const uint32_t *prbs_bits, cudaStream_t st)
+{
+    if (train) {
+        k_eq_dd<NT, MQ><<<1, 32, 0, st>>>(p, g, 1, Y, taps_in, taps_out, dec, dbg_z);
+        return cudaGetLastError();
+    }
+    k_eq_dd<NT, MQ><<<(unsigned)((g.nblk + 127) / 128), 128, 0, st>>>(p, g, 0, Y, taps_in, taps_out, dec, dbg_z);
+    if (g.nwin > 0)
+        k_dd_score<MQ><<<(unsigned)((g.nwin + 3) / 4), 128, 0, st>>>(p, g, dec, winb, winrec, dbg_win, prbs_bits);
+    return cudaGetLastError();
+}
+
 // tap counts with a compiled kernel (odd, half-length odd)
 #define RX_EQ_TAPS(X) X(3) X(7) X(11) X(15) X(19) X(23) X(27) X(31)
 
@@ -607,6 +737,7 @@ size_t eq_smem_bytes(const EqParams &p, int warps) { return eq_smem_per_warp(p.k
 
 cudaError_t prepare_eq(const EqParams &p)
 {
+    if (p.dd) return cudaSuccess;   // the symbol-by-symbol kernels take no dynamic shared memory
 #define RX_PREP(NTV)                                                                                           \
     if (p.ntaps == NTV) {                                                                                      \
         if (p.kk && p.mq == 2) return prepare_eq_t<true, NTV, 2>(p);                                            \
@@ -624,6 +755,19 @@ cudaError_t launch_eq(const EqParams &p, const EqGeom &g, int train, const void 
                       float2 *taps_in, float2 *taps_out, uint8_t *dec, uint8_t *winb, uint4 *winrec, float4 *dbg_win,
                       float2 *dbg_z, const uint8_t *prbs, const uint32_t *prbs_bits, DevState *dst, cudaStream_t st)
 {
+    if (p.dd) {
+        const float2 *Yc = (const float2 *)Y;
+#define RX_DD(NTV)                                                                                             \
+        if (p.ntaps == NTV && p.mq == 4)                                                                       \
+            return launch_eq_dd<NTV, 4>(p, g, train, Yc, taps_in, taps_out, dec, winb, winrec, dbg_win, dbg_z,  \
+                                        prbs_bits, st);                                                        \
+        if (p.ntaps == NTV && p.mq == 2)                                                                       \
+            return launch_eq_dd<NTV, 2>(p, g, train, Yc, taps_in, taps_out, dec, winb, winrec, dbg_win, dbg_z,  \
+                                        prbs_bits, st);
+        RX_DD(2) RX_DD(3) RX_DD(4) RX_DD(5) RX_DD(6) RX_DD(7) RX_DD(8)
+#undef RX_DD
+        return cudaErrorInvalidValue;
+    }
 #define RX_CASE(NTV)                                                                                           \
     if (p.ntaps == NTV) {                                                                                      \
         if (p.kk && p.mq == 2) return launch_eq_t<true, NTV, 2>(p, g, train, Y, zin, taps_in, taps_out, dec, winb,  \

@@ -170,6 +170,7 @@ struct EqParams {
     int frozen;   // payload blocks filter with the call's start taps (block-Toeplitz form)
     int diff;     // differentially quadrant-coded QAM: decode and score quadrant differences
     int warps;    // equaliser blocks (warps) per CTA
+    int dd;       // KK: the short decision-directed LMS updated symbol by symbol, no phase search
 };
 
 // ------------------------------------------------------------------ launchers

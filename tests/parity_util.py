@@ -112,7 +112,9 @@ class Pair:
         amb = np.zeros(nwin, bool)
         wb_bad = np.zeros(nwin, bool)
         if fmt >= 3:
-            amb = (win[:, 3] - win[:, 2]) <= 1e-6 * win[:, 2]
+            # the symbol-by-symbol form runs no phase search: no metrics, no ambiguity
+            if getattr(g.cfg, "eq_mode", 0) != rx.RX_EQ_DD_SYMBOL:
+                amb = (win[:, 3] - win[:, 2]) <= 1e-6 * win[:, 2]
             wb_bad = gwin[:, 0].astype(np.int64) != win[:, 0].astype(np.int64)
         # bit streams compared symbol by symbol
         bps = rx.BITS_PER_SYMBOL[fmt]
