@@ -504,6 +504,7 @@ def gpu_arm(args, rank, world, local):
     rs_line = resampler_leg(args, ring) if rank == 0 and not args.no_rs else None
     sweep_line = sweep_leg(args) if rank == 0 and not args.no_sweep else None
     diff_line = diff_leg(args) if rank == 0 and not args.no_sweep else None
+    dd_line = dd_leg(args) if rank == 0 and not args.no_dd else None
     stab_line = stability_leg(args) if rank == 0 and args.stability > 0 else None
     batched_line = None
     if rank == 0 and not args.no_batched:
@@ -520,7 +521,7 @@ def gpu_arm(args, rank, world, local):
                     "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps, "warmup_run": e2e_warm},
             "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line, "precision": prec_line,
             "fd_filter": fd_line, "batched": batched_line,
-            "resampler": rs_line, "q_sweep": sweep_line, "stability": stab_line, "diff_coding": diff_line,
+            "resampler": rs_line, "q_sweep": sweep_line, "stability": stab_line, "diff_coding": diff_line, "dd_symbol_equaliser": dd_line,
             "clocks": clk, "gpu_launches": launches_per_call * args.bufs_per_step * args.steps,
             "realtime_x": value / 4.0,
             # the whole chain against the HBM roofline: 1.625 algorithmic bytes per sample
@@ -983,6 +984,54 @@ def diff_leg(args):
     return out
 
 
+def dd_leg(args):
+    """The paper's short KK equaliser (4-tap decision-directed LMS updated after every
+    symbol, no phase search; eq_mode = RX_EQ_DD_SYMBOL) against the workload's 31-tap
+    window equaliser with the 32-phase search, on a KK-16QAM stream at 20 dB without
+    relative laser phase noise (the paper's self-coherent link; with 100 kHz of it the
+    short form loses the phase between blocks): BER over 16 consecutive 2^22-sample
+    buffers generated on the GPU, receiver throughput over them, and the equaliser
+    stage timed alone."""
+    import torch
+    import paper_2010_14333_gb300 as rx
+    from synth.gpu import KKStreamGPU
+    t0 = time.perf_counter()
+    gen = KKStreamGPU(FMT, NB, seed=41, snr_db=20.0, linewidth=0.0)
+    ring = [gen.next().clone() for _ in range(16)]
+    torch.cuda.synchronize()
+    out = {"buffers": len(ring), "gen_s": time.perf_counter() - t0,
+           "stream": "KK-16QAM 20 dB, CSPR 10 dB, no relative laser phase noise (synth.gpu, seed 41)"}
+    sid = torch.cuda.current_stream().cuda_stream
+    for name, cfg in (("window_31_taps_phase_search", {}),
+                      ("dd_symbol_4_taps", dict(eq_mode=rx.RX_EQ_DD_SYMBOL, ntaps=4))):
+        r = rx.Receiver(FMT, NB, **cfg)
+        r.process_batch(ring)
+        st = r.stats()
+        del r
+        r = rx.Receiver(FMT, NB, **cfg)
+        r.process_batch(ring)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            r.process_batch(ring)
+        e1.record()
+        torch.cuda.synchronize()
+        gsa = 2 * len(ring) * NB / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        obuf = torch.empty(NB, dtype=torch.uint8, device="cuda")
+        rx.rx_profile(r.h, 1)
+        for i in range(8):
+            rx.rx_process(r.h, ring[i].data_ptr(), obuf.data_ptr(), sid)
+            torch.cuda.synchronize()
+        ms, calls = rx.rx_profile_read(r.h)
+        rx.rx_profile(r.h, 0)
+        out[name] = {"ber": st["ber"], "bits": st["bits"], "bit_errors": st["bit_errors"],
+                     "slip_windows": st["slip_windows"], "gsa_s": gsa,
+                     "eq_alone_us_per_buffer": ms["eq"] / max(calls, 1) * 1e3}
+        del r
+    return out
+
+
 def oracle_free_q_db(ber: float) -> float:
     """Q = 20 log10(sqrt(2) erfcinv(2 BER)) by bisection on math.erfc."""
     import math
@@ -1121,6 +1170,7 @@ def main():
     ap.add_argument("--no-rs", action="store_true")
     ap.add_argument("--smi-ms", type=int, default=50, help="clock sampling period during the timed steps")
     ap.add_argument("--no-sweep", action="store_true", help="skip the Q-factor versus SNR sweep of every format")
+    ap.add_argument("--no-dd", action="store_true", help="skip the leg of the paper's short symbol-by-symbol equaliser")
     ap.add_argument("--stability", type=int, default=5720,
                     help="buffers of the Q time series (5720 = the paper's 6 s at 4 GS/s; 0: off)")
     ap.add_argument("--batched-streams", type=int, default=64)

@@ -610,6 +610,8 @@ static cudaError_t prepare_eq_t(const EqParams &p)
 //   e = z (R2 - |z|^2) (CMA) or d / s - z (decision directed),
 //   w_j += mu y[2k + TH - j] conj(e).
 // The inputs of the next symbol are those of this one moved by two samples.
+constexpr int kDdU = 8;   // symbols per batch of loaded samples
+
 template <int NT, int MQ>
 __global__ void __launch_bounds__(128)
     k_eq_dd(EqParams p, EqGeom g, int train, const float2 *__restrict__ Y, float2 *taps_in, float2 *taps_out,
@@ -628,40 +630,55 @@ __global__ void __launch_bounds__(128)
     float2 yv[NT];   // yv[j] = y[2k + TH - j]
 #pragma unroll
     for (int j = 0; j < NT; j++) yv[j] = Y[2 * k0 + TH - j - g.ybase];
-    for (long long q = 0; q < n; q++) {
-        const long long k = k0 + q;
-        float zr = 0.f, zi = 0.f;
+    // the samples that enter the window, kDdU symbols at a time: batch b brings
+    // y[2 kb + TH + 1 + i], i < 2 kDdU (kb its first symbol), loaded while the batch
+    // before it is computed (n is a multiple of kDdU; the last batch reads two samples
+    // past the last symbol's window, inside the workspace, and never uses them)
+    float2 nx[2 * kDdU];
 #pragma unroll
-        for (int j = 0; j < NT; j++) {   // conj(w) y
-            zr = fmaf(w[j].x, yv[j].x, fmaf(w[j].y, yv[j].y, zr));
-            zi = fmaf(w[j].x, yv[j].y, fmaf(-w[j].y, yv[j].x, zi));
-        }
-        const float vr = s * zr, vi = s * zi;
-        const int LI = decide_t<MQ>(vr), LQ = decide_t<MQ>(vi);
-        const bool nr = near_t<MQ>(vr) || near_t<MQ>(vi);
-        if (!train) dec[k - g.pay_lo] = (uint8_t)(LI | (LQ << 3) | (nr ? 64 : 0));
-        if (dbg_z) dbg_z[k - g.sym_lo] = make_float2(zr, zi);
-        float er, ei, mu;
-        if (k < cma_until) {
-            const float f = p.r2 - (zr * zr + zi * zi);
-            er = zr * f;
-            ei = zi * f;
-            mu = p.mu_cma;
-        } else {
-            er = (float)(2 * LI - (MQ - 1)) * inv_s - zr;
-            ei = (float)(2 * LQ - (MQ - 1)) * inv_s - zi;
-            mu = p.mu;
+    for (int i = 0; i < 2 * kDdU; i++) nx[i] = Y[2 * k0 + TH + 1 + i - g.ybase];
+    for (long long q0 = 0; q0 < n; q0 += kDdU) {
+        float2 cb[2 * kDdU];
+#pragma unroll
+        for (int i = 0; i < 2 * kDdU; i++) cb[i] = nx[i];
+        if (q0 + kDdU < n) {
+#pragma unroll
+            for (int i = 0; i < 2 * kDdU; i++) nx[i] = Y[2 * (k0 + q0 + kDdU) + TH + 1 + i - g.ybase];
         }
 #pragma unroll
-        for (int j = 0; j < NT; j++) {   // w += mu y conj(e)
-            w[j].x = fmaf(mu, fmaf(yv[j].x, er, yv[j].y * ei), w[j].x);
-            w[j].y = fmaf(mu, fmaf(yv[j].y, er, -yv[j].x * ei), w[j].y);
-        }
-        if (q + 1 < n) {
+        for (int u = 0; u < kDdU; u++) {
+            const long long k = k0 + q0 + u;
+            float zr = 0.f, zi = 0.f;
+#pragma unroll
+            for (int j = 0; j < NT; j++) {   // conj(w) y
+                zr = fmaf(w[j].x, yv[j].x, fmaf(w[j].y, yv[j].y, zr));
+                zi = fmaf(w[j].x, yv[j].y, fmaf(-w[j].y, yv[j].x, zi));
+            }
+            const float vr = s * zr, vi = s * zi;
+            const int LI = decide_t<MQ>(vr), LQ = decide_t<MQ>(vi);
+            const bool nr = near_t<MQ>(vr) || near_t<MQ>(vi);
+            if (!train) dec[k - g.pay_lo] = (uint8_t)(LI | (LQ << 3) | (nr ? 64 : 0));
+            if (dbg_z) dbg_z[k - g.sym_lo] = make_float2(zr, zi);
+            float er, ei, mu;
+            if (k < cma_until) {
+                const float f = p.r2 - (zr * zr + zi * zi);
+                er = zr * f;
+                ei = zi * f;
+                mu = p.mu_cma;
+            } else {
+                er = (float)(2 * LI - (MQ - 1)) * inv_s - zr;
+                ei = (float)(2 * LQ - (MQ - 1)) * inv_s - zi;
+                mu = p.mu;
+            }
+#pragma unroll
+            for (int j = 0; j < NT; j++) {   // w += mu y conj(e)
+                w[j].x = fmaf(mu, fmaf(yv[j].x, er, yv[j].y * ei), w[j].x);
+                w[j].y = fmaf(mu, fmaf(yv[j].y, er, -yv[j].x * ei), w[j].y);
+            }
 #pragma unroll
             for (int j = NT - 1; j >= 2; j--) yv[j] = yv[j - 2];
-            yv[1] = Y[2 * k + TH + 1 - g.ybase];
-            yv[0] = Y[2 * k + TH + 2 - g.ybase];
+            yv[1] = cb[2 * u];
+            yv[0] = cb[2 * u + 1];
         }
     }
     if (train) {
