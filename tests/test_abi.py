@@ -168,3 +168,20 @@ def test_group_rejects_bad_arguments():
     f, w = C.c_int32(), C.c_int32()
     assert lib.rx_group_tuning(None, 0, C.byref(f), C.byref(w)) == 1
     assert lib.rx_group_destroy(None) == 1
+
+
+@pytest.mark.parametrize("fmt,kw", [(rx.RX_KK_16QAM, dict(eq_mode=2)), (rx.RX_KK_16QAM, dict(eq_mode=-1)),
+                                    (rx.RX_KK_16QAM, dict(eq_mode=1, ntaps=9)),
+                                    (rx.RX_KK_16QAM, dict(eq_mode=1, ntaps=1)),
+                                    (rx.RX_KK_16QAM, dict(eq_mode=1, ntaps=4, fir_prec=2, eq_block=1024)),
+                                    (rx.RX_KK_16QAM, dict(eq_mode=0, ntaps=4)),
+                                    (rx.RX_PAM4, dict(eq_mode=1, ntaps=4))])
+def test_create_rejects_bad_equaliser_form(fmt, kw):
+    """The symbol-by-symbol form: KK only, 2..8 taps, adaptive; even tap counts in it only."""
+    lib = rx.load()
+    c = rx.rx_default_config(fmt)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    h = C.c_void_p()
+    baud, nb = (1e9, 1 << 22) if fmt >= 3 else (2e9, 1 << 20)
+    assert lib.rx_create(fmt, baud, 4e9, nb, C.byref(c), C.byref(h)) == 1
