@@ -70,7 +70,7 @@ struct rx_handle {
     // three slots.
     cudaStream_t front, front2, mid, back, tail, copy;   // KK: field | matched filter | equaliser | demap
     cudaEvent_t ev_fork, ev_front, ev_hist, ev_join, ev_yfree[kSlots], ev_efree[kSlots],
-        ev_dfree[kSlots], ev_inready[2], ev_infree[2];
+        ev_dfree[kSlots], ev_inready[2], ev_infree[2], ev_cfree[2];
     float2 *taps[2], *twN, *twN2, *ds_tab;
     float *lnt;
     float *rrc;
@@ -111,7 +111,7 @@ struct rx_handle {
     // end of stream (rx_flush)
     int flushed;               // rx_flush ran: no more buffers
     int flush_mode;            // the call being enqueued is a pad call of rx_flush
-    int flush_par;             // PAM: parity of the last real call (its mean and deviation)
+    int flush_par;             // PAM: sums slot (call index mod 3) of the last real call (its mean and deviation)
     long long flush_score_end; // windows reaching this symbol are not scored
     long long flush_bits;      // bound of the bits rx_flush emits
     long long pad_calls;       // pad calls run by rx_flush (not counted as input)
@@ -546,7 +546,7 @@ void rx_destroy(rx_handle *h)
     if (h->tail) cudaStreamDestroy(h->tail);
     if (h->copy) cudaStreamDestroy(h->copy);
     cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_join, &h->ev_inready[0],
-                          &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
+                          &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1], &h->ev_cfree[0], &h->ev_cfree[1]};
     for (cudaEvent_t *ev : evs)
         if (*ev) cudaEventDestroy(*ev);
     free(h->prof_used);
@@ -872,7 +872,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
                   cudaStreamCreateWithFlags(&h->tail, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
         cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_join, &h->ev_inready[0],
-                              &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1]};
+                              &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1], &h->ev_cfree[0], &h->ev_cfree[1]};
         for (cudaEvent_t *ev : evs)
             ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
         for (int i = 0; i < kSlots; i++)
@@ -944,20 +944,21 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     cudaError_t stale = cudaGetLastError();
     if (stale != cudaSuccess) traced(stale, "an earlier CUDA call (cleared)");
     const bool two = sf != sb;
-    // KK in the pipeline: the matched filter runs on a third stream between the
-    // field (front) and the equaliser (back); field slots wait for it to be done
-    const bool three = two && h->kk && smid;
+    // in the pipeline the filter runs on a third stream between the front end (KK field,
+    // PAM unpack) and the equaliser (back); field and codes slots wait for it to be done
+    const bool three = two && smid;
     cudaStream_t sm = three ? smid : sf;
     // the demap (and the copy of the bits) on a fourth stream, after its equaliser
     const bool four = two && stail;
     cudaStream_t st4 = four ? stail : sb;
     cudaError_t e = cudaSuccess;
     int par = (int)(h->calls & 1);
+    const int spar = (int)(h->calls % 3);   // PAM sums slot: the filter of call i clears call i+2's
     int ds = (int)(h->calls % kSlots);   // decision slot of this call
     // KK in the pipeline: the field of odd calls on the second front-end stream.
     // Not with the CNN receiver: its decision kernel is persistent (one CTA per SM),
     // and a second field in flight holds SMs it waits for.
-    const bool alt = three && h->front2 && !h->cnn;
+    const bool alt = three && h->kk && h->front2 && !h->cnn;
     if (alt && par) sf = h->front2;
     const KkSync ksync = {alt ? h->ev_hist : nullptr, alt ? h->ev_hist : nullptr, alt ? h->ev_front : nullptr};
     if (host_in) {
@@ -978,11 +979,14 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     if (!h->kk || c.debug) {
         prof_begin(h, 0, sf);
         int cw_new = h->cw ^ 1;
+        // PAM in the pipeline: the filter two calls back (on its own stream) is done with
+        // this codes slot, and has cleared this call's sums
+        if (three && !h->kk) cudaStreamWaitEvent(sf, h->ev_cfree[cw_new], 0);
         // a flush pad adds nothing to the PAM sums: its filter uses the last real buffer's
         const bool sums = !h->kk && !h->flush_mode;
         e = launch_unpack(in, h->codes[cw_new], h->codes[h->cw], h->nb, h->nhist, h->nb, h->calls == 0,
-                          c.pack_order, sums ? &h->st->pam_s1[par] : nullptr,
-                          sums ? &h->st->pam_s2[par] : nullptr, sf, lat_first, lat_slot);
+                          c.pack_order, sums ? &h->st->pam_s1[spar] : nullptr,
+                          sums ? &h->st->pam_s2[spar] : nullptr, sf, lat_first, lat_slot);
         lat_first = nullptr;   // stamped: the KK front end (debug view) comes after
         h->cw = cw_new;
         prof_end(h, 0, sf);
@@ -1040,7 +1044,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     if (e == cudaSuccess && h->rs && s.r_k > h->r_prev) {
         const __int128 psi = rs_psi(h, h->r_prev);
         const long long rb = h->r_prev - kEHist;
-        const int ppar_rs = h->flush_mode ? h->flush_par : par;
+        const int ppar_rs = h->flush_mode ? h->flush_par : spar;
         // the resampler reads the reconstructed field (KK) or the call's normalised codes (PAM)
         if (!h->kk) e = launch_pam_norm(h->codes[h->cw], cbase, h->nb, s.avail, h->st, ppar_rs, h->E[0], sm);
         if (e == cudaSuccess)
@@ -1058,7 +1062,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         const float2 *Ef = h->kk && h->rs ? h->R[h->rw] : h->E[h->ew];
         // carrier and gain of this call (of the last real buffer in a flush)
         const double *cgp = h->flush_mode ? h->st->cg_flush : &h->st->cg[h->ew][0];
-        const int ppar = h->flush_mode ? h->flush_par : par;
+        const int ppar = h->flush_mode ? h->flush_par : spar;
         const long long efbase = h->kk && h->rs ? h->rbase_cur : h->ebase_cur;
         if (h->kk && h->fd)
             e = launch_kk_fdmf(Ef, efbase, h->f_prev, s.f_k, c.fd_n, h->fd_H, h->fd_tw, h->ds_tab,
@@ -1070,20 +1074,20 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
                              h->ybase_cur, sm, h->rrc_host);
         else if (h->rs)
             e = launch_pam_mf_r(h->R[h->rw], h->rbase_cur, h->f_prev, s.f_k, h->rrc, h->hmf, (float *)h->Y[yw_new], yb,
-                                (const float *)h->Y[h->yw], h->ybase_cur, sf);
+                                (const float *)h->Y[h->yw], h->ybase_cur, sm);
         else if (h->fd)
             e = launch_pam_fd1024(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->fd_H, h->fd_tw, h->st,
-                                  ppar, (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf,
+                                  ppar, (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sm,
                                   h->clk, h->clk_w);
         else
             e = launch_pam_mf(h->codes[h->cw], cbase, h->nb, s.avail, h->f_prev, s.f_k, h->rrc, h->hmf, h->st, ppar,
-                              (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sf);
+                              (float *)h->Y[yw_new], yb, (const float *)h->Y[h->yw], h->ybase_cur, sm);
         if (e == cudaSuccess && h->fd && c.clk_track) {
             // blocks of this call: outputs at 2 samples/symbol per block N/4 (KK) or N/2 (PAM)
             const long long per = h->kk ? c.fd_n / 4 : c.fd_n / 2;
             const long long nblk = (s.f_k - h->f_prev) / per;
             if (nblk > 0) {
-                k_clock_track<<<1, kCkThreads, 0, h->kk ? sm : sf>>>(h->clk, (int)nblk, h->f_prev / per, c.fd_n,
+                k_clock_track<<<1, kCkThreads, 0, sm>>>(h->clk, (int)nblk, h->f_prev / per, c.fd_n,
                                                                     h->sps, h->st);
                 e = cudaGetLastError();
             }
@@ -1093,9 +1097,10 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     }
     prof_end(h, 4, sm);
     if (three) {
-        // the field slot's release is also the equaliser's start signal
-        cudaEventRecord(h->ev_efree[h->ew], sm);
-        cudaStreamWaitEvent(sb, h->ev_efree[h->ew], 0);
+        // the field (KK) or codes (PAM) slot's release is also the equaliser's start signal
+        cudaEvent_t rel = h->kk ? h->ev_efree[h->ew] : h->ev_cfree[h->cw];
+        cudaEventRecord(rel, sm);
+        cudaStreamWaitEvent(sb, rel, 0);
     } else {
         if (host_in && sc != sf) cudaEventRecord(h->ev_infree[par], sf);
         if (two) {
@@ -1296,7 +1301,7 @@ rx_status rx_flush(rx_handle *h, uint8_t *bits_out, void *stream, int64_t *nbits
         return RX_ECUDA;
     }
     h->flush_mode = 1;
-    h->flush_par = (int)((h->calls - 1) & 1);
+    h->flush_par = (int)((h->calls - 1) % 3);
     h->flush_score_end = S - (c.mf_span + c.ntaps + 1) / 2;
     long long done = 0;   // bits written to bits_out
     rx_status r = RX_OK;

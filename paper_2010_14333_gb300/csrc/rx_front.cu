@@ -1448,9 +1448,9 @@ __global__ void __launch_bounds__(kMfOut) k_pam_mf(const uint16_t *__restrict__ 
     if (blockIdx.x == 0) {
         for (long long m = ybase + threadIdx.x; m < f_prev; m += blockDim.x)
             Y[m - ybase] = (m < 0) ? 0.f : Y_prev[m - ybase_prev];
-        if (threadIdx.x == 0) {   // the sums of the next call start from zero
-            dst->pam_s1[parity ^ 1] = 0;
-            dst->pam_s2[parity ^ 1] = 0;
+        if (threadIdx.x == 0) {   // the sums of the call after next start from zero
+            dst->pam_s1[(parity + 2) % 3] = 0;
+            dst->pam_s2[(parity + 2) % 3] = 0;
         }
     }
     __syncthreads();
@@ -1484,8 +1484,8 @@ __global__ void k_pam_norm(const uint16_t *__restrict__ codes, long long cbase, 
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         dst->pam_mu = (double)s_mu;
         dst->pam_inv_sd = (double)s_inv;
-        dst->pam_s1[parity ^ 1] = 0;   // the sums of the next call start from zero
-        dst->pam_s2[parity ^ 1] = 0;
+        dst->pam_s1[(parity + 2) % 3] = 0;   // the sums of the call after next start from zero
+        dst->pam_s2[(parity + 2) % 3] = 0;
     }
 }
 
@@ -1571,8 +1571,8 @@ __global__ void __launch_bounds__(32 * kFdWarps, 4)
             double var = (double)dst->pam_s2[parity] / (double)nb - mu * mu;
             dst->pam_mu = mu;
             dst->pam_inv_sd = (var > 0.0) ? 1.0 / sqrt(var) : 1.0;
-            dst->pam_s1[parity ^ 1] = 0;
-            dst->pam_s2[parity ^ 1] = 0;
+            dst->pam_s1[(parity + 2) % 3] = 0;
+            dst->pam_s2[(parity + 2) % 3] = 0;
         }
     }
     const long long bi = (long long)blockIdx.x * kFdWarps + w;
@@ -1679,9 +1679,9 @@ __global__ void __launch_bounds__(kPmThreads) k_pam_mf_t(const uint16_t *__restr
     if (blockIdx.x == 0) {
         for (long long m = ybase + threadIdx.x; m < f_prev; m += blockDim.x)
             Y[m - ybase] = (m < 0) ? 0.f : Y_prev[m - ybase_prev];
-        if (threadIdx.x == 0) {   // the sums of the next call start from zero
-            dst->pam_s1[parity ^ 1] = 0;
-            dst->pam_s2[parity ^ 1] = 0;
+        if (threadIdx.x == 0) {   // the sums of the call after next start from zero
+            dst->pam_s1[(parity + 2) % 3] = 0;
+            dst->pam_s2[(parity + 2) % 3] = 0;
         }
     }
     __syncthreads();

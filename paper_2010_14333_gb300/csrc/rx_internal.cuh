@@ -39,7 +39,7 @@ struct DevState {
     double cg[kSlots][4];                  // KK per slot: carrier re, carrier im, gain
     double cg_flush[4];                    // KK: carrier and gain of the last real buffer (flush)
     double pam_mu, pam_inv_sd;             // PAM: this call's normalisation (debug view)
-    long long pam_s1[2], pam_s2[2];        // PAM: integer sums of codes / codes^2, by call parity
+    long long pam_s1[3], pam_s2[3];        // PAM: integer sums of codes / codes^2, by call index mod 3
     int unwrap_have[2], unwrap_b[2];       // pi/2 unwrap carry, by parity
     int diff_have[2], diff_q[2];           // differential coding: quadrant of the last symbol, by parity
     long long unwrap_m[2];
