@@ -970,6 +970,9 @@ __global__ void __launch_bounds__(kMfThreads) k_kk_mf_t(const float2 *__restrict
     int idx = (int)((((n0 % ds_den) + ds_den) % ds_den + 2LL * threadIdx.x) % ds_den);
     idx = (int)(((long long)idx * ds_num) % ds_den);
     const int step = (int)((2LL * kMfThreads * ds_num) % ds_den), odd = ds_num % ds_den;
+    // unrolled (a compile-time trip count): every iteration's loads can issue before
+    // the first one is used
+#pragma unroll
     for (int pp = threadIdx.x; pp < NPAIR; pp += kMfThreads) {
         long long n = n0 + 2 * pp;
         float2 a = make_float2(0.f, 0.f), b = a;
