@@ -203,10 +203,14 @@ struct KkPacked {
 };
 constexpr int kRawWords = 100;   // 384 bytes of a row + spare word, 16-byte multiple
 
+// (CTAs of kCtaK1 threads; the loop is unrolled so that every load issues before the
+// first one is used)
 __device__ __forceinline__ void stage_rows(const KkGeom &g, const KkPacked &pk, int pair, int c0,
                                            uint32_t (*raw)[kRawWords], bool hb)
 {
-    for (int i = threadIdx.x; i < 32 * 24; i += blockDim.x) {
+    static_assert((32 * 24) % kCtaK1 == 0, "whole iterations");
+#pragma unroll
+    for (int i = threadIdx.x; i < 32 * 24; i += kCtaK1) {
         int row = i / 24, ch = i - 24 * (i / 24), blk = row >> 4, q = row & 15;
         if (blk && !hb) continue;
         long long n = ols_ws(g, 2 * pair + blk) + c0 + (long long)g.N2 * q;
