@@ -23,6 +23,7 @@
 #include "rx_oracle.h"
 
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -568,11 +569,19 @@ static int32_t code_at(const ctx *x, int64_t n)
     int64_t i = n - (x->base - h->chist_len);
     return (i >= 0) ? h->chist[i] : 0;   /* never reached for valid configs */
 }
+/* a read before the history a call keeps is a bug of this program: stop loudly */
+static void history_miss(const char *what, int64_t idx, int64_t start)
+{
+    fprintf(stderr, "rx_oracle: %s index %lld precedes the kept history (from %lld)\n", what, (long long)idx,
+            (long long)start);
+    abort();
+}
 static cx e_at(const ctx *x, int64_t n)
 {
     const orx *h = x->h;
     if (n < 0) return cx_mk(0.0, 0.0);
     if (n >= x->E_start) return x->E[n - x->E_start];
+    if (n < h->ehist_start) history_miss("field", n, h->ehist_start);
     return h->ehist[n - h->ehist_start];
 }
 static cx r_at(const ctx *x, int64_t m)   /* the field on the grid the filter reads */
@@ -581,6 +590,7 @@ static cx r_at(const ctx *x, int64_t m)   /* the field on the grid the filter re
     if (!h->rs) return e_at(x, m);
     if (m < 0) return cx_mk(0.0, 0.0);
     if (m >= x->R_start) return x->R[m - x->R_start];
+    if (m < h->rhist_start) history_miss("resampled field", m, h->rhist_start);
     return h->rhist[m - h->rhist_start];
 }
 static cx y_at(const ctx *x, int64_t m)
@@ -588,6 +598,7 @@ static cx y_at(const ctx *x, int64_t m)
     const orx *h = x->h;
     if (m < 0) return cx_mk(0.0, 0.0);
     if (m >= x->y_start) return x->y[m - x->y_start];
+    if (m < h->yhist_start) history_miss("2-sps sample", m, h->yhist_start);
     return h->yhist[m - h->yhist_start];
 }
 
@@ -1174,7 +1185,11 @@ static int64_t process_buffer(orx *h, const uint8_t *packed, uint8_t *bits_out, 
         free(h->ehist); h->ehist = nh; h->ehist_start = lo; h->ehist_len = e_k - lo;
     }
     {
-        int64_t lo = 2 * (h->trained ? q_k : 0) - h->th;
+        /* the 2-sps history the next call's first symbols read: the filter of
+         * symbol k reaches back to y[2k + th - (ntaps - 1)], ntaps - 1 - th samples
+         * before 2k (th for the symmetric window filter; one more for an even tap
+         * count of the symbol-by-symbol form) */
+        int64_t lo = 2 * (h->trained ? q_k : 0) - (c->ntaps - 1 - h->th);
         if (lo < 0) lo = 0;
         if (lo > f_k) lo = f_k;
         cx *nh = xcalloc((size_t)(f_k - lo + 1), sizeof(cx));

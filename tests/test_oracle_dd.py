@@ -60,6 +60,36 @@ def test_dd_filter_definition(taps):
         assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("nt", [2, 3, 4, 6, 8])
+def test_dd_filter_definition_across_calls(nt):
+    """The same definition for every symbol of a stream, the first symbols of each
+    call included: they reach back into the previous call's 2-sps samples (ntaps - 1 -
+    th of them, one more than th for an even tap count).  The calls' views of the
+    samples are consecutive, so their concatenation is the whole 2-sps stream."""
+    g = stream(nbufs=3, noise=False)
+    o = oracle.Oracle(**oracle.default_cfg(4, NB, eq_mode=1, ntaps=nt, mu=0.0, mu_cma=0.0, **SMALL))
+    w = np.exp(1j * np.arange(nt)) * np.linspace(0.2, 1.0, nt)   # every tap non-zero
+    o.set_taps(w)
+    ys, zs = [], []
+    for p in g["packed"]:
+        o.process(p)
+        ys.append(o.get(oracle.ORX_Y))
+        zs.append(o.get(oracle.ORX_Z))
+    for (y_a, a0), (y_b, b0) in zip(ys, ys[1:]):
+        assert b0 == a0 + len(y_a)
+    assert ys[0][1] == 0
+    Y = np.concatenate([y for y, _ in ys])
+    th = (nt - 1) // 2
+    checked = 0
+    for z, z0 in zs[1:]:   # calls after the first: their first symbols read the previous call's samples
+        k = np.arange(z0, z0 + len(z))
+        k = k[2 * k + th < len(Y)]
+        ref = sum(np.conj(w[j]) * np.where(2 * k + th - j >= 0, Y[np.maximum(2 * k + th - j, 0)], 0) for j in range(nt))
+        assert np.max(np.abs(z[: len(k)] - ref)) < 1e-12 * np.max(np.abs(ref)), nt
+        checked += len(k)
+    assert checked > 60000
+
+
 @pytest.mark.parametrize("fmt,delay", [(4, 0.0), (4, 0.35), (3, 0.0), (3, 0.35)])
 def test_dd_noiseless_zero_errors(fmt, delay):
     g = stream(fmt, noise=False, clock_phase0=int(delay * (1 << 32)))
