@@ -425,7 +425,7 @@ rx_status rx_group_destroy(rx_group *g);
  *                floats (interleaved real, imaginary).
  *
  * The scratch (twiddle and ln tables, a packed-history region, FFT rows, field,
- * reduction partials) is one fixed device array of about 8.2 MiB in librx.so;
+ * carrier sums) is one fixed device array of about 8.1 MiB in librx.so;
  * every GPU that loads the library holds it until the process exits.  Sizes
  * beyond the limits return RX_EINVAL before anything is enqueued.  The call
  * allocates nothing (no cudaMalloc, cudaFree or allocating library routine); it

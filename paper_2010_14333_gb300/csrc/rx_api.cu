@@ -55,7 +55,6 @@ struct rx_handle {
     int hw;
     float2 *fftws[2], *E[kSlots];   // FFT workspace per front-end stream
     void *Y[kSlots];
-    CarrierPartial *partials[2];
     uint8_t *dec[kSlots], *winb[kSlots], *prbs;
     uint32_t *prbs_bits;            // the PRBS period bit-packed MSB first, first 256 bits repeated
     uint4 *winrec[kSlots];          // per payload window: errors under the four rotations, near count
@@ -520,7 +519,7 @@ void rx_destroy(rx_handle *h)
     if (h->back) cudaStreamSynchronize(h->back);
     if (h->tail) cudaStreamSynchronize(h->tail);
     if (h->copy) cudaStreamSynchronize(h->copy);
-    void *ptrs[] = {h->codes[0], h->codes[1], h->fftws[0], h->fftws[1], h->partials[0], h->partials[1], h->prbs, h->taps[0], h->taps[1], h->twN,
+    void *ptrs[] = {h->codes[0], h->codes[1], h->fftws[0], h->fftws[1], h->prbs, h->taps[0], h->taps[1], h->twN,
                     h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
                     h->bits_stage, h->lnt, h->prbs_bits, h->phist[0], h->phist[1], h->phist[2], h->zbuf, h->gpart, h->fd_H, h->fd_tw, h->R[0], h->R[1],
                     h->rs_tab, h->clk, h->lat_dev};
@@ -734,11 +733,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     if (kk) {
         for (int i = 0; i < kSlots; i++) RX_ALLOC(h->E[i], (kEHist + nb) * sizeof(float2));
         for (int i = 0; i < 3; i++) RX_ALLOC(h->phist[i], (size_t)h->nhist * 3 / 2 + 16);
-        int gx = (h->N2 + kCtaK1 - 1) / kCtaK1;
-        for (int i = 0; i < 2; i++) {
-            RX_ALLOC(h->fftws[i], (size_t)h->npairs_max * h->N * sizeof(float2));
-            RX_ALLOC(h->partials[i], (size_t)gx * h->npairs_max * sizeof(CarrierPartial));
-        }
+        for (int i = 0; i < 2; i++) RX_ALLOC(h->fftws[i], (size_t)h->npairs_max * h->N * sizeof(float2));
         RX_ALLOC(h->twN, kk_tw_entries(h->N) * sizeof(float2));
         RX_ALLOC(h->twN2, kk_tw_entries(h->N2) * sizeof(float2));
         RX_ALLOC(h->lnt, kLutCodes * sizeof(float));
@@ -1026,7 +1021,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         g.fused = c.kk_front;
         if (three) cudaStreamWaitEvent(sf, h->ev_efree[ew_new], 0);   // the matched filter is done with this slot
         KkTables tb = {h->lnt, h->twN, h->twN2};
-        e = traced(launch_kk_front(g, kin, h->fftws[par], tb, h->E[ew_new], h->E[h->ew], h->partials[par], h->st, sf,
+        e = traced(launch_kk_front(g, kin, h->fftws[par], tb, h->E[ew_new], h->E[h->ew], h->st, sf,
                                    h->prof_cur ? h : nullptr, ksync), "KK front end");
         h->ew = ew_new;
         h->ebase_cur = g.ebase;

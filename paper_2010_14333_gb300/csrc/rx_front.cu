@@ -220,14 +220,33 @@ __device__ __forceinline__ void stage_rows(const KkGeom &g, const KkPacked &pk, 
     }
 }
 
-// 12-bit code of column t of a staged row (two samples per three bytes)
-__device__ __forceinline__ uint32_t decode_col(const uint32_t *rw, int t, int order)
+// 12-bit code of column t of a staged row.  The row is a stream of 12-bit fields,
+// two per three bytes.  In pack order 0 sample t fills bits [12 t, 12 t + 12) of the
+// little-endian stream: one funnel shift of the two words that hold them and a mask.
+// In pack order 1 the code's high nibble comes first: the two bytes that hold it are
+// swapped, then a shift takes the high 12 bits (even t) or the low 12 bits (odd t).
+// The word index and the shifts depend on t only, so a thread computes them once.
+struct ColPos {
+    int w;         // first of the two words
+    unsigned fs;   // funnel shift
+    unsigned ps;   // pack order 1: shift after the byte swap
+};
+template <int ORD>
+__device__ __forceinline__ ColPos col_pos(int t)
 {
-    int b = (3 * t) >> 1;
-    uint32_t v = __funnelshift_r(rw[b >> 2], rw[(b >> 2) + 1], 8 * (b & 3));
-    uint32_t lo = v & 0xFFu, hi = (v >> 8) & 0xFFu;
-    if (order == 0) return (t & 1) ? ((lo >> 4) | (hi << 4)) : (lo | ((hi & 0xFu) << 8));
-    return (t & 1) ? (((lo & 0xFu) << 8) | hi) : ((lo << 4) | (hi >> 4));
+    const int b = (3 * t) >> 1;   // first byte of the sample
+    ColPos c;
+    c.w = b >> 2;
+    c.fs = 8 * (b & 3) + (ORD == 0 ? 4 * (t & 1) : 0);
+    c.ps = ORD == 0 ? 0u : 4u * (1 - (t & 1));
+    return c;
+}
+template <int ORD>
+__device__ __forceinline__ uint32_t col_code(const uint32_t *rw, const ColPos &c)
+{
+    uint32_t v = __funnelshift_r(rw[c.w], rw[c.w + 1], c.fs);
+    if (ORD == 1) v = __byte_perm(v, 0u, 0x4401) >> c.ps;   // (byte 0 << 8) | byte 1
+    return v & 0xFFFu;
 }
 
 __device__ __forceinline__ uint32_t first_code(const KkPacked &pk, const DevState *dst)
@@ -240,6 +259,8 @@ __device__ __forceinline__ uint32_t first_code(const KkPacked &pk, const DevStat
 
 // K1a: unpack, u = ln(I)/2 by table, radix-16 pass over the stride-N2 index of two
 // packed blocks, twiddle.  CTAs with blockIdx.y == npairs copy the next history.
+// ORD: the pack order of the 12-bit input.
+template <int ORD>
 __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2 *__restrict__ fftws,
                                                   const KkTables tb, DevState *dst)
 {
@@ -273,15 +294,17 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2
     __syncthreads();
     const int t = threadIdx.x, n1 = c0 + t;
     const long long wa = ols_ws(g, 2 * pair) + c0 + t, wb = hb ? ols_ws(g, jb) + c0 + t : 0;
+    // rows q below qa (qb) hold stream indices before the stream: the first code
+    const int qa = wa < 0 ? (int)min((-wa + g.N2 - 1) / g.N2, 16LL) : 0;
+    const int qb = wb < 0 ? (int)min((-wb + g.N2 - 1) / g.N2, 16LL) : 0;
+    const ColPos cp = col_pos<ORD>(t);
     float2 x[16];
 #pragma unroll
     for (int q = 0; q < 16; q++) {
-        long long na = wa + (long long)g.N2 * q;
-        uint32_t ca = na < 0 ? c_first : decode_col(raw[q], t, pk.order);
+        uint32_t ca = q < qa ? c_first : col_code<ORD>(raw[q], cp);
         float ua = s_ln[ca], ub = 0.f;
         if (hb) {
-            long long nb2 = wb + (long long)g.N2 * q;
-            uint32_t cb = nb2 < 0 ? c_first : decode_col(raw[16 + q], t, pk.order);
+            uint32_t cb = q < qb ? c_first : col_code<ORD>(raw[16 + q], cp);
             ub = s_ln[cb];
         }
         x[q] = make_float2(ua, ub);
@@ -401,14 +424,64 @@ __global__ void __launch_bounds__(256, 3) k_kk_rows(KkGeom g, float2 *__restrict
         for (int r = 0; r < 16; r++) d[t + r * TPR] = x[r];
 }
 
+// Carrier and intensity sums of a call, from which its carrier and gain follow.
+// Each warp's FP32 sums of E become exact integers in units of 2^-24 (a warp's sum
+// is below 2^17 in magnitude and a call holds at most 2^30 samples of |E| <= 64, so
+// every total fits a signed 64-bit integer).  One 64-bit atomic per CTA and quantity
+// adds them to the slot's totals.  Integer addition does not depend on order, so the
+// totals, and the carrier, are the same whatever order the CTAs run in.  The CTA that
+// takes the last ticket forms, in FP64, the carrier c = sum E / n, the mean intensity
+// sum 2I / 2n and the gain 1 / sqrt(sps (mean I - |c|^2)), then clears the totals and
+// the ticket for the slot's next call.
+constexpr double kCarrierUnit = 16777216.0;   // 2^24
+__device__ __forceinline__ void carrier_sums(const KkGeom &g, DevState *dst, float sre, float sim, int si2,
+                                             int ncta)
+{
+    __shared__ long long s_q[3][32];
+    sre = warp_sum_f(sre);
+    sim = warp_sum_f(sim);
+    si2 = warp_sum_i(si2);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_q[0][wid] = __double2ll_rn((double)sre * kCarrierUnit);
+        s_q[1][wid] = __double2ll_rn((double)sim * kCarrierUnit);
+        s_q[2][wid] = si2;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    long long a = 0, b = 0, c = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+        a += s_q[0][i];
+        b += s_q[1][i];
+        c += s_q[2][i];
+    }
+    unsigned long long *S = dst->csum[g.slot];
+    atomicAdd(S + 0, (unsigned long long)a);
+    atomicAdd(S + 1, (unsigned long long)b);
+    atomicAdd(S + 2, (unsigned long long)c);
+    __threadfence();
+    if (atomicAdd(&dst->ticket[g.slot], 1u) != (unsigned)(ncta - 1)) return;
+    __threadfence();
+    const long long ta = (long long)atomicExch(S + 0, 0ull), tb = (long long)atomicExch(S + 1, 0ull),
+                    tc = (long long)atomicExch(S + 2, 0ull);
+    const double cnt = (double)(g.e_k - g.e_prev);
+    const double cr = (double)ta / kCarrierUnit / cnt, ci = (double)tb / kCarrierUnit / cnt;
+    const double ibar = (double)tc / (2.0 * cnt);
+    const double P = ibar - (cr * cr + ci * ci);
+    dst->cg[g.slot][0] = cr;
+    dst->cg[g.slot][1] = ci;
+    dst->cg[g.slot][2] = (P > 0.0) ? 1.0 / sqrt((double)g.sps * P) : 1.0;
+    dst->ticket[g.slot] = 0u;
+}
+
 // K1c: inverse radix-16 pass, then for every kept output
 // E = sqrt(I) * exp(j phi) (Fig. 1d), written at its stream position, and the
-// per-call carrier / intensity sums (deterministic: fixed-order trees, last-CTA
-// finalisation in FP64).  The codes for sqrt(I) come from the same staged rows.
+// per-call carrier / intensity sums (exact integer totals, carrier_sums).  The
+// codes for sqrt(I) come from the same staged rows.  ORD: the pack order.
+template <int ORD>
 __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const float2 *__restrict__ fftws,
                                                   const KkTables tb, float2 *__restrict__ E,
-                                                  const float2 *__restrict__ E_prev,
-                                                  CarrierPartial *__restrict__ partials, DevState *dst)
+                                                  const float2 *__restrict__ E_prev, DevState *dst)
 {
     __shared__ float2 s_tw[512];
     __shared__ __align__(16) uint32_t raw[32][kRawWords];
@@ -428,6 +501,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
         }
     }
     const int t = threadIdx.x, n1 = c0 + t;
+    const ColPos cp = col_pos<ORD>(t);
     float2 x[16];
     const float2 *in = fftws + (size_t)pair * g.N + n1;
 #pragma unroll
@@ -452,7 +526,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
         for (int q = 0; q < 16; q++) {
             int tt = n1 + g.N2 * q;
             if (tt < tlo || tt >= thi) continue;
-            uint32_t code = tt < tneg ? c_first : decode_col(raw[16 * half + q], t, pk.order);
+            uint32_t code = tt < tneg ? c_first : col_code<ORD>(raw[16 * half + q], cp);
             float phi = (half ? x[q].y : x[q].x) * invN;
             float sn, cs;
             __sincosf(phi, &sn, &cs);   // |phi| < pi: absolute error <= 2^-21.41
@@ -467,65 +541,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
             si2 += code ? 2 * (int)code : 1;
         }
     }
-    // CTA partial (fixed-order tree)
-    __shared__ float rre[kCtaK1 / 32], rim[kCtaK1 / 32];
-    __shared__ int ri[kCtaK1 / 32];
-    __shared__ bool last;
-    sre = warp_sum_f(sre);
-    sim = warp_sum_f(sim);
-    si2 = warp_sum_i(si2);
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) { rre[wid] = sre; rim[wid] = sim; ri[wid] = si2; }
-    __syncthreads();
-    int cta = blockIdx.y * gridDim.x + blockIdx.x;
-    int ncta = gridDim.x * gridDim.y;
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0;
-        long long c = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) { a += rre[i]; b += rim[i]; c += ri[i]; }
-        partials[cta].re = a;
-        partials[cta].im = b;
-        partials[cta].i2 = c;
-        __threadfence();
-        unsigned tk = atomicAdd(&dst->ticket[g.slot], 1u);
-        last = (tk == (unsigned)(ncta - 1));
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // last CTA: strided per-thread sums then a fixed-order tree in FP64
-    __shared__ double dre[kCtaK1], dim[kCtaK1];
-    __shared__ long long dii[kCtaK1];
-    double a = 0, b = 0;
-    long long c = 0;
-    for (int i = threadIdx.x; i < ncta; i += blockDim.x) {
-        volatile CarrierPartial *pp = partials + i;
-        a += pp->re;
-        b += pp->im;
-        c += pp->i2;
-    }
-    dre[threadIdx.x] = a;
-    dim[threadIdx.x] = b;
-    dii[threadIdx.x] = c;
-    __syncthreads();
-    for (int sft = blockDim.x / 2; sft > 0; sft >>= 1) {
-        if ((int)threadIdx.x < sft) {
-            dre[threadIdx.x] += dre[threadIdx.x + sft];
-            dim[threadIdx.x] += dim[threadIdx.x + sft];
-            dii[threadIdx.x] += dii[threadIdx.x + sft];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        double cnt = (double)(g.e_k - g.e_prev);
-        double cr = dre[0] / cnt, ci = dim[0] / cnt;
-        double ibar = (double)dii[0] / (2.0 * cnt);
-        double P = ibar - (cr * cr + ci * ci);
-        dst->cg[g.slot][0] = cr;
-        dst->cg[g.slot][1] = ci;
-        dst->cg[g.slot][2] = (P > 0.0) ? 1.0 / sqrt((double)g.sps * P) : 1.0;
-        dst->ticket[g.slot] = 0u;
-    }
+    carrier_sums(g, dst, sre, sim, si2, gridDim.x * gridDim.y);
 }
 
 // ====================================================== KK front end, fused
@@ -572,7 +588,7 @@ __device__ __forceinline__ uint32_t warp_codes(const KkPacked &pk, long long t0,
 
 __global__ void __cluster_dims__(kClC, 1, 1) __launch_bounds__(kClThreads, 3)
     k_kk_cluster(KkGeom g, KkPacked pk, const KkTables tb, float2 *__restrict__ E,
-                 const float2 *__restrict__ E_prev, CarrierPartial *__restrict__ partials, DevState *dst)
+                 const float2 *__restrict__ E_prev, DevState *dst)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -741,64 +757,7 @@ __global__ void __cluster_dims__(kClC, 1, 1) __launch_bounds__(kClThreads, 3)
     }
     cl.sync();   // no CTA leaves while its rows may still be read
 
-    // CTA partial (fixed-order tree), then the last CTA of the grid reduces in FP64
-    __shared__ float rre[kClThreads / 32], rim[kClThreads / 32];
-    __shared__ int ri[kClThreads / 32];
-    __shared__ bool last;
-    sre = warp_sum_f(sre);
-    sim = warp_sum_f(sim);
-    si2 = warp_sum_i(si2);
-    int lane = t & 31, wid = t >> 5;
-    if (lane == 0) { rre[wid] = sre; rim[wid] = sim; ri[wid] = si2; }
-    __syncthreads();
-    const int ncta = gridDim.x;
-    if (t == 0) {
-        double a = 0, b = 0;
-        long long cc = 0;
-        for (int i = 0; i < kClThreads / 32; i++) { a += rre[i]; b += rim[i]; cc += ri[i]; }
-        partials[blockIdx.x].re = a;
-        partials[blockIdx.x].im = b;
-        partials[blockIdx.x].i2 = cc;
-        __threadfence();
-        unsigned tk = atomicAdd(&dst->ticket[g.slot], 1u);
-        last = (tk == (unsigned)(ncta - 1));
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // FP64 scratch in the row area: no CTA of the cluster reads it after the last barrier
-    double *dre = reinterpret_cast<double *>(rows), *dim = dre + kClThreads;
-    long long *dii = reinterpret_cast<long long *>(dim + kClThreads);
-    double a = 0, b = 0;
-    long long cc = 0;
-    for (int i = t; i < ncta; i += blockDim.x) {
-        volatile CarrierPartial *pp = partials + i;
-        a += pp->re;
-        b += pp->im;
-        cc += pp->i2;
-    }
-    dre[t] = a;
-    dim[t] = b;
-    dii[t] = cc;
-    __syncthreads();
-    for (int sft = blockDim.x / 2; sft > 0; sft >>= 1) {
-        if (t < sft) {
-            dre[t] += dre[t + sft];
-            dim[t] += dim[t + sft];
-            dii[t] += dii[t + sft];
-        }
-        __syncthreads();
-    }
-    if (t == 0) {
-        double cnt = (double)(g.e_k - g.e_prev);
-        double cr = dre[0] / cnt, ci = dim[0] / cnt;
-        double ibar = (double)dii[0] / (2.0 * cnt);
-        double P = ibar - (cr * cr + ci * ci);
-        dst->cg[g.slot][0] = cr;
-        dst->cg[g.slot][1] = ci;
-        dst->cg[g.slot][2] = (P > 0.0) ? 1.0 / sqrt((double)g.sps * P) : 1.0;
-        dst->ticket[g.slot] = 0u;
-    }
+    carrier_sums(g, dst, sre, sim, si2, gridDim.x);
 }
 
 __global__ void k_kk_hist(KkPacked pk)
@@ -836,8 +795,8 @@ cudaError_t prepare_kk_front()
 }
 
 cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, const KkTables &tb,
-                            float2 *E, const float2 *E_prev, CarrierPartial *partials, DevState *dst,
-                            cudaStream_t st, void *prof, const KkSync &sync)
+                            float2 *E, const float2 *E_prev, DevState *dst, cudaStream_t st, void *prof,
+                            const KkSync &sync)
 {
     KkPacked pk;
     pk.hist = inp.hist;
@@ -854,7 +813,7 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
         if (sync.wait_fwd) cudaStreamWaitEvent(st, sync.wait_fwd, 0);
         if (sync.wait_inv) cudaStreamWaitEvent(st, sync.wait_inv, 0);
         prof_stage(prof, 1, st);
-        k_kk_cluster<<<g.npairs * kClC, kClThreads, kClSmem, st>>>(g, pk, tb, E, E_prev, partials, dst);
+        k_kk_cluster<<<g.npairs * kClC, kClThreads, kClSmem, st>>>(g, pk, tb, E, E_prev, dst);
         if (sync.rec_fwd) cudaEventRecord(sync.rec_fwd, st);
         prof_stage(prof, -2, st);
         prof_stage(prof, -3, st);
@@ -865,7 +824,8 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     dim3 grid_a(g.N2 / kCtaK1, g.npairs + (inp.hist_next ? 1 : 0));
     if (sync.wait_fwd) cudaStreamWaitEvent(st, sync.wait_fwd, 0);
     prof_stage(prof, 1, st);
-    k_kk_fwd<<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
+    if (pk.order) k_kk_fwd<1><<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
+    else k_kk_fwd<0><<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
     if (sync.rec_fwd) cudaEventRecord(sync.rec_fwd, st);
     prof_stage(prof, -2, st);
     int rows = g.npairs * 16;
@@ -880,7 +840,8 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     }
     if (sync.wait_inv) cudaStreamWaitEvent(st, sync.wait_inv, 0);
     prof_stage(prof, -3, st);
-    k_kk_inv<<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, partials, dst);
+    if (pk.order) k_kk_inv<1><<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, dst);
+    else k_kk_inv<0><<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, dst);
     prof_stage(prof, -4, st);
     return cudaGetLastError();
 }

@@ -45,6 +45,7 @@ struct DevState {
     long long unwrap_m[2];
     int amb_r;                             // stream-start rotation, -1 before
     int first_code;                        // 12-bit code of the stream's first sample
+    unsigned long long csum[kSlots][3];    // KK per slot: carrier sums (re, im in 2^-24) and sum of 2I
     unsigned int ticket[kSlots];           // last-CTA ticket of the carrier reduction, per slot
     unsigned int eq_ticket;                // last-warp ticket of the frozen form's tap step
     int err;                               // RX_ETIMEOUT when a bounded wait ran out
@@ -104,13 +105,6 @@ __device__ __forceinline__ void lat_end(LatRecord *r, int slot)
 }
 // rx_stats: bin and clear every slot (one thread per slot)
 cudaError_t launch_lat_flush(LatRecord *r, cudaStream_t st);
-
-// per-CTA partial of the carrier reduction
-struct CarrierPartial {
-    double re, im;
-    long long i2;   // sum over kept outputs of 2*I (I = code, 0.5 for code 0), exact
-    long long pad;
-};
 
 // per-call geometry of the KK overlap-save blocks
 struct KkGeom {
@@ -192,8 +186,8 @@ struct KkSync {
 cudaError_t launch_kk_hist(const KkInput &inp, cudaStream_t st, const KkSync &sync);
 
 cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, const KkTables &tb,
-                            float2 *E, const float2 *E_prev, CarrierPartial *partials, DevState *dst,
-                            cudaStream_t st, void *prof, const KkSync &sync);
+                            float2 *E, const float2 *E_prev, DevState *dst, cudaStream_t st, void *prof,
+                            const KkSync &sync);
 // stage-boundary hook of the profiler (defined with the C ABI; prof may be null)
 void prof_stage(void *prof, int stage, cudaStream_t st);
 

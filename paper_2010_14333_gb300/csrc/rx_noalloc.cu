@@ -27,7 +27,7 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 //            replicated), so it only has to be a valid region of ols_n * 3 / 2 bytes
 //   fft      the two-block complex FFT rows, at most 2^19 complex values
 //   E        the field [kEHist history | buffer]
-//   part     per-CTA carrier partials, state: the front end's reduction state
+//   state    the front end's reduction state (carrier sums and their ticket)
 constexpr int kNaSizes = 2;
 constexpr size_t kTabBytes = 4096 * sizeof(float) + 1024 * sizeof(float2);   // >= one block
 constexpr size_t kOffTw = 0;
@@ -37,9 +37,7 @@ constexpr size_t kOffFft = align_up(kOffHist + kHistBytes);
 constexpr size_t kFftBytes = 4u << 20;                   // two-block complex FFT rows
 constexpr size_t kOffE = align_up(kOffFft + kFftBytes);
 constexpr size_t kEBytes = (size_t)(kEHist + kNaMaxSamples) * sizeof(float2);
-constexpr size_t kOffPart = align_up(kOffE + kEBytes);
-constexpr size_t kPartBytes = 64u << 10;                 // per-CTA carrier partials
-constexpr size_t kOffState = align_up(kOffPart + kPartBytes);
+constexpr size_t kOffState = align_up(kOffE + kEBytes);
 constexpr size_t kScratchBytes = align_up(kOffState + sizeof(DevState));
 
 // One scratch region per GPU that loads the library (held until the process exits).
@@ -125,8 +123,7 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     g.sps = 4;
     g.slot = 0;
     size_t need_fft = (size_t)g.npairs * ols_n * sizeof(float2);
-    size_t need_part = (size_t)((g.N2 + kCtaK1 - 1) / kCtaK1) * g.npairs * sizeof(CarrierPartial);
-    if (need_fft > kFftBytes || need_part > kPartBytes) return RX_EINVAL;
+    if (need_fft > kFftBytes) return RX_EINVAL;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RX_ECUDA;
@@ -141,9 +138,8 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     const uint8_t *hist = base + kOffHist;
     float2 *fftws = (float2 *)(base + kOffFft);
     float2 *E = (float2 *)(base + kOffE);
-    CarrierPartial *part = (CarrierPartial *)(base + kOffPart);
     DevState *ds = (DevState *)(base + kOffState);
-    // the last-CTA ticket of the carrier reduction must start at zero
+    // the carrier sums and the last-CTA ticket of their reduction must start at zero
     if (cudaMemsetAsync(ds, 0, sizeof(DevState), st) != cudaSuccess) return RX_ECUDA;
     KkInput kin;
     kin.hist = hist;                        // never read for values: the first call fills the pre-stream
@@ -156,7 +152,7 @@ extern "C" rx_status rx_kk_field_noalloc(const uint8_t *packed12_in, int64_t nsa
     kin.lat = nullptr;
     kin.lat_slot = 0;
     const KkSync none = {nullptr, nullptr, nullptr};
-    if (launch_kk_front(g, kin, fftws, tb, E, E, part, ds, st, nullptr, none) != cudaSuccess) return RX_ECUDA;
+    if (launch_kk_front(g, kin, fftws, tb, E, E, ds, st, nullptr, none) != cudaSuccess) return RX_ECUDA;
     unsigned grid = (unsigned)((e_k + 255) / 256);
     k_na_copy_field<<<grid, 256, 0, st>>>(E + kEHist, reinterpret_cast<float2 *>(field_out), e_k);
     if (cudaGetLastError() != cudaSuccess) return RX_ECUDA;
