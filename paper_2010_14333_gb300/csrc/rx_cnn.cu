@@ -573,9 +573,13 @@ __global__ void k_cnn_tobf(const float *__restrict__ prm, __nv_bfloat16 *__restr
 // ====================================================================
 // Receiver inference on the fifth-generation tensor cores (tcgen05).
 //
-// Tiles of kTS = 128 symbols (two 64-symbol windows) per iteration of a
-// persistent CTA (two per SM, 512 threads each: four warps per tensor-memory lane
-// quarter, each taking a quarter of the accumulator columns).  Activations live
+// Tiles of kTS = 128 symbols (two 64-symbol windows).  One persistent CTA per SM
+// runs kRxGroups independent groups of 8 warps, each with its own tile loop,
+// activation planes, mbarrier, 128 tensor-memory columns and named barrier, and all
+// reading the weights staged once per CTA: while one group waits on its MMAs or its
+// tensor-memory loads, the others issue, so kRxGroups tiles are in flight per SM.  In
+// a group two warps share each tensor-memory lane quarter, each taking half of the
+// accumulator columns.  Activations live
 // in shared memory as "planes" of 8 channels, each position one 16-byte row: with
 // this layout the im2col operand of a 32-channel, 9-tap convolution at K-step ks
 // (tap ks/2, channel groups 2 (ks % 2) and +1) is the plane pair read from
@@ -607,31 +611,56 @@ constexpr int kRX = 128 * kMT1 + 12;         // rows of the layer-1 input plane 
 constexpr int kR1 = 128 * kMT2 + 8;          // rows of the h1 planes (rows >= kP1 stay zero); h3 reuses rows < 128
 constexpr int kRE = kP2 / 2 + 4;             // rows of each even / odd h2 plane (136; rows < 132 written)
 constexpr int kWinT = kTS / 64;              // windows per tile
-constexpr int kRxThreads = 512;
-constexpr uint32_t kRxTmem = 128;
+constexpr int kRxGroups = 4;                 // tile groups per CTA (tiles in flight per SM)
+constexpr int kRxGroupThreads = 256;         // 8 warps: two per tensor-memory lane quarter
+constexpr int kRxThreads = kRxGroups * kRxGroupThreads;
+constexpr uint32_t kRxTmemGroup = 128;       // accumulator columns of one group
+constexpr uint32_t kRxTmem = 512;            // the CTA's allocation (a power of two)
 constexpr uint32_t kColOut = 96;             // accumulator columns of the 64 -> 2 projection
+static_assert(kRxGroups * kRxTmemGroup <= kRxTmem && kRxTmem <= 512, "tensor memory of one SM");
+// Shared memory: the weights (read by every group), then one block per group.
 struct RxSmem {
     static constexpr int W2 = 0;                          // fp16 planes [36][32 rows][16 B]
     static constexpr int W3 = W2 + 36 * 512;
     static constexpr int M1 = W3 + 36 * 512;              // fp16 planes [4][64 rows][16 B]
     static constexpr int M2 = M1 + 4 * 1024;              // fp16 planes [8][16 rows][16 B] (rows 0, 1 live)
     static constexpr int B1 = M2 + 8 * 256;               // fp16 planes [4][32 rows][16 B]
-    static constexpr int H1 = B1 + 4 * 512;               // fp16 planes [4][kR1][16 B] (h1, then h3)
+    static constexpr int BH = B1 + 4 * 512;               // half2 biases: layers 1..3 [3][16], MLP [32]
+    static constexpr int C2 = BH + 80 * 4;                // float [2]: output bias
+    static constexpr int GRP = (C2 + 16 + 1023) & ~1023;  // first group block
+    // one group's block, offsets from its start
+    static constexpr int H1 = 0;                          // fp16 planes [4][kR1][16 B] (h1, then h3)
     static constexpr int HX = H1 + 4 * kR1 * 16;          // the layer-1 input plane [kRX][16 B], then the
                                                           // even/odd h2 planes [2][4][kRE][16 B], then the
-                                                          // hidden planes [8][128][16 B]
+                                                          // hidden planes [8][128][16 B], then the outputs
+                                                          // float [kTS][2]
     static constexpr int HXB = 2 * 4 * kRE * 16;
-    static constexpr int BH = HX + HXB;                   // half2 biases: layers 1..3 [3][16], MLP [32]
-    static constexpr int C2 = BH + 80 * 4;                // float [2]: output bias
-    static constexpr int OS = C2 + 16;                    // float [kTS][2]
-    static constexpr int XS = OS + kTS * 8;               // float2 [kP0]: the next tile's input (async copy)
-    static constexpr int PRB = XS + kP0 * 8;              // uint32 [kPrbsWords]: the PRBS reference bits
-    static constexpr int BAR = PRB + kPrbsWords * 4;      // mbarrier, TMEM slot
-    static constexpr int TOTAL = BAR + 64;
+    static constexpr int XS = HX + HXB;                   // float2 [kP0]: the next tile's input (async copy)
+    static constexpr int BAR = XS + kP0 * 8;              // mbarrier
+    static constexpr int GROUP = (BAR + 16 + 127) & ~127;
+    static constexpr int SLOT = GRP + kRxGroups * GROUP;  // tensor-memory base address
+    static constexpr int TOTAL = SLOT + 16;
 };
 static_assert(kRX * 16 <= RxSmem::HXB && 8 * 128 * 16 <= RxSmem::HXB, "aliases of the HX region fit");
-static_assert(RxSmem::TOTAL <= 113 * 1024, "two receiver CNN CTAs per SM");
+static_assert(RxSmem::TOTAL <= 227 * 1024, "one receiver CNN CTA per SM");
 static_assert(2 * (kRE - 4) == kP2, "even / odd h2 rows cover the layer-2 positions");
+
+// barrier of one group's 256 threads (named barrier id, 1 + group); the second form
+// also returns whether pred held in every thread of the group
+__device__ __forceinline__ void group_sync(int id)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kRxGroupThreads) : "memory");
+}
+__device__ __forceinline__ bool group_and(int id, bool pred)
+{
+    uint32_t r;
+    asm volatile("{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred o, %2, %3, q;\n"
+                 " selp.u32 %0, 1, 0, o;\n}"
+                 : "=r"(r)
+                 : "r"((uint32_t)pred), "r"(id), "n"(kRxGroupThreads)
+                 : "memory");
+    return r != 0;
+}
 
 __device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
 __device__ __forceinline__ __half2 bits_h2(uint32_t u) { return *reinterpret_cast<__half2 *>(&u); }
@@ -681,7 +710,7 @@ __device__ __forceinline__ uint32_t gelu2(uint32_t a, uint32_t b, uint32_t bias)
 }
 
 template <bool BF>
-__global__ void __launch_bounds__(kRxThreads, 2)
+__global__ void __launch_bounds__(kRxThreads, 1)
     k_cnn_rx_tc(const float *__restrict__ prm, const float2 *__restrict__ y,
                 long long seg_base, long long y_end, int nwin, uint8_t *__restrict__ dec, uint8_t *__restrict__ winb,
                 uint4 *__restrict__ winrec, const uint32_t *__restrict__ prbs_bits, long long k_first, float scale,
@@ -689,18 +718,21 @@ __global__ void __launch_bounds__(kRxThreads, 2)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sW2 = sm + RxSmem::W2, *sW3 = sm + RxSmem::W3, *sM1 = sm + RxSmem::M1, *sM2 = sm + RxSmem::M2;
-    unsigned char *sB1 = sm + RxSmem::B1, *sH1 = sm + RxSmem::H1, *sHX = sm + RxSmem::HX;
+    unsigned char *sB1 = sm + RxSmem::B1;
     uint32_t *bh = reinterpret_cast<uint32_t *>(sm + RxSmem::BH);   // half2 bias pairs
     float *c2 = reinterpret_cast<float *>(sm + RxSmem::C2);
-    float *os = reinterpret_cast<float *>(sm + RxSmem::OS);
-    float2 *xs = reinterpret_cast<float2 *>(sm + RxSmem::XS);
-    uint32_t *s_prbs = reinterpret_cast<uint32_t *>(sm + RxSmem::PRB);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + RxSmem::BAR);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quarter = warp & 3, cq = warp >> 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + RxSmem::SLOT);
+    const int tid = threadIdx.x, grp = tid / kRxGroupThreads, gtid = tid % kRxGroupThreads;
+    const int lane = tid & 31, warp = tid >> 5, gwarp = gtid >> 5, quarter = gwarp & 3, ch = gwarp >> 2;
+    const int gbar = 1 + grp;   // the group's named barrier
+    unsigned char *gb = sm + RxSmem::GRP + grp * RxSmem::GROUP;
+    unsigned char *sH1 = gb + RxSmem::H1, *sHX = gb + RxSmem::HX;
+    float *os = reinterpret_cast<float *>(sHX);   // the outputs, after the hidden planes are consumed
+    float2 *xs = reinterpret_cast<float2 *>(gb + RxSmem::XS);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(gb + RxSmem::BAR);
     constexpr int PL1 = kR1 * 16, PLE = kRE * 16, EO = 4 * PLE;
 
-    if (tid == 0) mbar_init(bar, 1);
+    if (gtid == 0) mbar_init(bar, 1);
     __syncwarp();
     if (warp == 0) tmem_alloc(tslot, kRxTmem);
     // weights: B operands as K-major planes (chunk (row n, K column kk) at kk * rows * 16 + n * 16)
@@ -741,24 +773,25 @@ __global__ void __launch_bounds__(kRxThreads, 2)
     }
     for (int i = tid; i < 32; i += kRxThreads) bh[48 + i] = pack2<BF>(prm[OC1 + 2 * i], prm[OC1 + 2 * i + 1]);
     if (tid < 2) c2[tid] = prm[OC2 + tid];
-    for (int i = tid; i < kPrbsWords; i += kRxThreads) s_prbs[i] = prbs_bits[i];
-    // the first tile's input, copied asynchronously (zero past the stream end)
+    const int ntiles = (nwin + kWinT - 1) / kWinT;
+    const int t0 = (int)blockIdx.x * kRxGroups + grp, tstep = (int)gridDim.x * kRxGroups;
+    // a tile's input, copied asynchronously into the group's buffer (zero past the stream end)
     auto prefetch = [&](int t) {
-        if (tid < kP0) {
-            const long long g = seg_base + 2LL * kTS * t + tid;
-            cp_async8(xs + tid, g < y_end ? y + g : y, g < y_end);
+        for (int i = gtid; i < kP0; i += kRxGroupThreads) {
+            const long long g = seg_base + 2LL * kTS * t + i;
+            cp_async8(xs + i, g < y_end ? y + g : y, g < y_end);
         }
         cp_async_commit();
     };
-    if ((int)blockIdx.x < (nwin + kWinT - 1) / kWinT) prefetch(blockIdx.x);
+    if (t0 < ntiles) prefetch(t0);
     // rows past the computed positions are read by the last row tiles: zero once
-    for (int i = tid; i < 4 * kR1; i += kRxThreads)
+    for (int i = gtid; i < 4 * kR1; i += kRxGroupThreads)
         *reinterpret_cast<uint4 *>(sH1 + (i / kR1) * PL1 + (i % kR1) * 16) = make_uint4(0, 0, 0, 0);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot;
+    const uint32_t tmem = *tslot + (uint32_t)grp * kRxTmemGroup;   // the group's columns
     constexpr uint32_t kFmt = BF ? 1u : 0u;   // kind::f16 operand format: F16 or BF16
     const uint32_t id16 = umma_idesc(kFmt, 128, 16), id32 = umma_idesc(kFmt, 128, 32), id64 = umma_idesc(kFmt, 128, 64);
     const uint32_t aB1 = smem_u32(sB1), aH1 = smem_u32(sH1), aHX = smem_u32(sHX), aW2 = smem_u32(sW2),
@@ -772,7 +805,6 @@ __global__ void __launch_bounds__(kRxThreads, 2)
     const uint64_t dHid = umma_sdesc(aHX, 2048, 128), dM2 = umma_sdesc(aM2, 256, 128);
     unsigned phase = 0;
     bool ok = true;
-    const int ntiles = (nwin + kWinT - 1) / kWinT;
 
     auto wait_mma = [&]() -> bool {
         bool done = mbar_wait(bar, phase);
@@ -781,34 +813,40 @@ __global__ void __launch_bounds__(kRxThreads, 2)
             mbar_wait(bar, phase);
         }
         phase ^= 1u;
-        return __syncthreads_and(done) != 0;
+        return group_and(gbar, done);
     };
-    // conv epilogue of MT row tiles: rows of this warp's lane quarter, channel group
-    // cq (8 channels); every tile's accumulator load in flight before one wait;
-    // row -> address of its 16-byte FP16 row in the destination
+    // conv epilogue of MT row tiles: rows of this warp's lane quarter, channel groups
+    // 2 ch and 2 ch + 1 (8 channels each) one after the other, each with every row
+    // tile's accumulator load in flight before one wait; row -> address of its
+    // 16-byte FP16 row of channel group cq in the destination
     auto conv_epi = [&](auto mt, int valid, const uint32_t *bias, auto dst_row) {
         constexpr int MT = decltype(mt)::value;
-        uint32_t r[8 * MT];
 #pragma unroll
-        for (int m = 0; m < MT; m++) tmem_ld8_nw(tq + 32 * m + 8 * cq, *reinterpret_cast<uint32_t(*)[8]>(r + 8 * m));
-        tmem_wait_ld(r);
-        const uint4 b = *reinterpret_cast<const uint4 *>(bias + 4 * cq);
+        for (int c = 0; c < 2; c++) {
+            const int cq = 2 * ch + c;
+            uint32_t r[8 * MT];
 #pragma unroll
-        for (int m = 0; m < MT; m++) {
-            const int row = 128 * m + 32 * quarter + lane;
-            const uint32_t *q = r + 8 * m;
-            if (row < valid)
-                *reinterpret_cast<uint4 *>(dst_row(row)) =
-                    make_uint4(gelu2<BF>(q[0], q[1], b.x), gelu2<BF>(q[2], q[3], b.y), gelu2<BF>(q[4], q[5], b.z),
-                               gelu2<BF>(q[6], q[7], b.w));
+            for (int m = 0; m < MT; m++)
+                tmem_ld8_nw(tq + 32 * m + 8 * cq, *reinterpret_cast<uint32_t(*)[8]>(r + 8 * m));
+            tmem_wait_ld(r);
+            const uint4 b = *reinterpret_cast<const uint4 *>(bias + 4 * cq);
+#pragma unroll
+            for (int m = 0; m < MT; m++) {
+                const int row = 128 * m + 32 * quarter + lane;
+                const uint32_t *q = r + 8 * m;
+                if (row < valid)
+                    *reinterpret_cast<uint4 *>(dst_row(row, cq)) =
+                        make_uint4(gelu2<BF>(q[0], q[1], b.x), gelu2<BF>(q[2], q[3], b.y),
+                                   gelu2<BF>(q[4], q[5], b.z), gelu2<BF>(q[6], q[7], b.w));
+            }
         }
     };
 
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int t = t0; t < ntiles && ok; t += tstep) {
         // layer-1 input plane: row p = positions p .. p+3 (8 reals) in FP16, zero past kP0
         cp_async_wait_all();
-        __syncthreads();   // the tile's input is in xs
-        for (int p = tid; p < kRX; p += kRxThreads) {
+        group_sync(gbar);   // the tile's input is in xs
+        for (int p = gtid; p < kRX; p += kRxGroupThreads) {
             uint32_t w[4];
 #pragma unroll
             for (int i = 0; i < 4; i++) {
@@ -818,9 +856,9 @@ __global__ void __launch_bounds__(kRxThreads, 2)
             *reinterpret_cast<uint4 *>(sHX + p * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         fence_async_smem();
-        __syncthreads();
-        if (t + (int)gridDim.x < ntiles) prefetch(t + gridDim.x);   // lands while this tile computes
-        if (tid == 0) {
+        group_sync(gbar);
+        if (t + tstep < ntiles) prefetch(t + tstep);   // lands while this tile computes
+        if (gtid == 0) {
             tc_fence_after();
 #pragma unroll
             for (int m = 0; m < kMT1; m++)
@@ -832,12 +870,13 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         }
         if (!(ok = wait_mma())) break;
         tc_fence_after();
-        conv_epi(std::integral_constant<int, kMT1>(), kP1, bh, [&](int row) { return sH1 + cq * PL1 + row * 16; });
+        conv_epi(std::integral_constant<int, kMT1>(), kP1, bh,
+                 [&](int row, int cq) { return sH1 + cq * PL1 + row * 16; });
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        group_sync(gbar);
         // layer 2 (reads h1; the input plane is free)
-        if (tid == 0) {
+        if (gtid == 0) {
             tc_fence_after();
 #pragma unroll
             for (int m = 0; m < kMT2; m++)
@@ -850,12 +889,12 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         if (!(ok = wait_mma())) break;
         tc_fence_after();
         conv_epi(std::integral_constant<int, kMT2>(), kP2, bh + 16,
-                 [&](int row) { return sHX + (row & 1) * EO + cq * PLE + (row >> 1) * 16; });
+                 [&](int row, int cq) { return sHX + (row & 1) * EO + cq * PLE + (row >> 1) * 16; });
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        group_sync(gbar);
         // layer 3 at the symbol positions: tap d reads set d & 1 from row j + d / 2
-        if (tid == 0) {
+        if (gtid == 0) {
             tc_fence_after();
 #pragma unroll
             for (int ks = 0; ks < 18; ks++) {
@@ -868,12 +907,12 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         if (!(ok = wait_mma())) break;
         tc_fence_after();
         conv_epi(std::integral_constant<int, 1>(), kTS, bh + 32,
-                 [&](int row) { return sH1 + cq * PL1 + row * 16; });   // h3, row = symbol
+                 [&](int row, int cq) { return sH1 + cq * PL1 + row * 16; });   // h3, row = symbol
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        group_sync(gbar);
         // MLP 32 -> 64 on the symbols (M = 128, N = 64, K = 32)
-        if (tid == 0) {
+        if (gtid == 0) {
             tc_fence_after();
 #pragma unroll
             for (int ks = 0; ks < 2; ks++)
@@ -882,24 +921,27 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         }
         if (!(ok = wait_mma())) break;
         tc_fence_after();
-        {   // hidden units 16 cq .. + 15 of symbol row -> planes 2 cq, 2 cq + 1 (the h2 planes are free)
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            // hidden units 16 hq .. + 15 of symbol row -> planes 2 hq, 2 hq + 1 (the h2 planes are free)
+            const int hq = 2 * ch + c;
             uint32_t r[16];
-            tmem_ld16(tq + 16 * cq, r);
+            tmem_ld16(tq + 16 * hq, r);
             const int row = 32 * quarter + lane;
-            const uint4 b0 = *reinterpret_cast<const uint4 *>(bh + 48 + 8 * cq);
-            const uint4 b1 = *reinterpret_cast<const uint4 *>(bh + 48 + 8 * cq + 4);
-            *reinterpret_cast<uint4 *>(sHX + (2 * cq) * 2048 + row * 16) =
+            const uint4 b0 = *reinterpret_cast<const uint4 *>(bh + 48 + 8 * hq);
+            const uint4 b1 = *reinterpret_cast<const uint4 *>(bh + 48 + 8 * hq + 4);
+            *reinterpret_cast<uint4 *>(sHX + (2 * hq) * 2048 + row * 16) =
                 make_uint4(gelu2<BF>(r[0], r[1], b0.x), gelu2<BF>(r[2], r[3], b0.y), gelu2<BF>(r[4], r[5], b0.z),
                            gelu2<BF>(r[6], r[7], b0.w));
-            *reinterpret_cast<uint4 *>(sHX + (2 * cq + 1) * 2048 + row * 16) =
+            *reinterpret_cast<uint4 *>(sHX + (2 * hq + 1) * 2048 + row * 16) =
                 make_uint4(gelu2<BF>(r[8], r[9], b1.x), gelu2<BF>(r[10], r[11], b1.y), gelu2<BF>(r[12], r[13], b1.z),
                            gelu2<BF>(r[14], r[15], b1.w));
         }
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        group_sync(gbar);
         // 64 -> 2 (M = 128, N = 16 with rows 2..15 of B zero, K = 64)
-        if (tid == 0) {
+        if (gtid == 0) {
             tc_fence_after();
 #pragma unroll
             for (int ks = 0; ks < 4; ks++)
@@ -908,7 +950,8 @@ __global__ void __launch_bounds__(kRxThreads, 2)
         }
         if (!(ok = wait_mma())) break;
         tc_fence_after();
-        if (cq == 0) {
+        // the projection has read the hidden planes: the outputs take their place
+        if (ch == 0) {
             uint32_t r[8];
             tmem_ld8(tq + kColOut, r);
             const int j = 32 * quarter + lane;
@@ -919,11 +962,11 @@ __global__ void __launch_bounds__(kRxThreads, 2)
             if (soft && ks < 64LL * nwin) soft[ks] = make_float2(o0, o1);
         }
         tc_fence_before();
-        __syncthreads();
-        // decisions and window records: warp w < kWinT takes window kWinT t + w
-        if (warp < kWinT && kWinT * t + warp < nwin) {
-            const int s = kWinT * t + warp;
-            const float *osw = os + 2 * 64 * warp;
+        group_sync(gbar);
+        // decisions and window records: warp w < kWinT of the group takes window kWinT t + w
+        if (gwarp < kWinT && kWinT * t + gwarp < nwin) {
+            const int s = kWinT * t + gwarp;
+            const float *osw = os + 2 * 64 * gwarp;
             const int NB = mq == 2 ? 1 : 2, BPS = 2 * NB;
             long long k0 = k_first + (long long)s * CS;
             int pwin = (int)(((long long)BPS * k0) % 32767);
@@ -941,7 +984,7 @@ __global__ void __launch_bounds__(kRxThreads, 2)
                 }
                 dec[(size_t)s * CS + q] = (uint8_t)(LI | (LQ << 3) | (nr ? 64 : 0));
                 int pos = pwin + BPS * q;
-                uint32_t w0 = s_prbs[pos >> 5], w1w = s_prbs[(pos >> 5) + 1];
+                uint32_t w0 = __ldg(prbs_bits + (pos >> 5)), w1w = __ldg(prbs_bits + (pos >> 5) + 1);
                 int ref = (int)(__funnelshift_l(w1w, w0, pos & 31) >> (32 - BPS));
                 for (int rq = 0; rq < 4; rq++) {
                     int a = LI, bq = LQ;
@@ -963,12 +1006,12 @@ __global__ void __launch_bounds__(kRxThreads, 2)
                 winrec[s] = make_uint4(eA, eB, se, nn << 8);
             }
         }
-        __syncthreads();
+        group_sync(gbar);   // the outputs are read before the next tile's input plane
     }
     cp_async_wait_all();   // a prefetch may still be in flight after an early exit
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kRxTmem);
+    if (warp == 0) tmem_dealloc(*tslot, kRxTmem);
 }
 
 cudaError_t prepare_cnn_rx()
@@ -985,8 +1028,8 @@ cudaError_t launch_cnn_decide(const float *prm, const float2 *y, long long seg_b
                               int bf16)
 {
     if (nwin <= 0) return cudaSuccess;
-    int ntiles = (nwin + kWinT - 1) / kWinT;
-    unsigned grid = (unsigned)(ntiles < 2 * nsm ? ntiles : 2 * nsm);   // two persistent CTAs per SM
+    int ntiles = (nwin + kWinT - 1) / kWinT, nctas = (ntiles + kRxGroups - 1) / kRxGroups;
+    unsigned grid = (unsigned)(nctas < nsm ? nctas : nsm);   // one persistent CTA per SM
     if (bf16)
         k_cnn_rx_tc<true><<<grid, kRxThreads, RxSmem::TOTAL, st>>>(prm, y, seg_base, y_end, nwin, dec, winb, winrec,
                                                                   prbs_bits, k_first, scale, mq, soft, err);
