@@ -676,31 +676,31 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
     else return h2_bits(__floats2half2_rn(a, b));
 }
 
-// bias + GELU of two FP32 accumulators in packed FP16 (tanh form, hardware tanh):
-// u = acc + b; t = tanh(u (c0 + c1 u^2)); 0.5 u (1 + t) = h + h t with h = u / 2
+// bias + GELU of two FP32 accumulators in packed FP16 (tanh form, hardware tanh),
+// returned doubled: u = acc + b; t = tanh(u (c0 + c1 u^2)); 2 GELU(u) = u (1 + t) =
+// u + u t.  The layers that read these activations take their weights halved, so the
+// products they accumulate are those of GELU(u) and the true weights: a factor of two
+// commutes with rounding, so the result is that of the undoubled form (BF16; FP16
+// where no value is subnormal) at one operation less per pair.
 __device__ __forceinline__ uint32_t gelu_h2(uint32_t a, uint32_t b, uint32_t bias)
 {
     const __half2 c0 = __float2half2_rn(0.7978845608028654f), c1 = __float2half2_rn(0.7978845608028654f * 0.044715f);
-    const __half2 hf = __float2half2_rn(0.5f);
     const __half2 u = __hadd2(__floats2half2_rn(__uint_as_float(a), __uint_as_float(b)), bits_h2(bias));
     const __half2 arg = __hmul2(u, __hfma2(__hmul2(u, u), c1, c0));
     uint32_t th;
     asm("tanh.approx.f16x2 %0, %1;" : "=r"(th) : "r"(h2_bits(arg)));
-    const __half2 h = __hmul2(u, hf);
-    return h2_bits(__hfma2(h, bits_h2(th), h));
+    return h2_bits(__hfma2(u, bits_h2(th), u));
 }
 // the same in packed BF16
 __device__ __forceinline__ uint32_t gelu_b2(uint32_t a, uint32_t b, uint32_t bias)
 {
     const __nv_bfloat162 c0 = __float2bfloat162_rn(0.7978845608028654f),
                          c1 = __float2bfloat162_rn(0.7978845608028654f * 0.044715f);
-    const __nv_bfloat162 hf = __float2bfloat162_rn(0.5f);
     const __nv_bfloat162 u = __hadd2(__floats2bfloat162_rn(__uint_as_float(a), __uint_as_float(b)), bits_b2(bias));
     const __nv_bfloat162 arg = __hmul2(u, __hfma2(__hmul2(u, u), c1, c0));
     uint32_t th;
     asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(b2_bits(arg)));
-    const __nv_bfloat162 h = __hmul2(u, hf);
-    return b2_bits(__hfma2(h, bits_b2(th), h));
+    return b2_bits(__hfma2(u, bits_b2(th), u));
 }
 template <bool BF>
 __device__ __forceinline__ uint32_t gelu2(uint32_t a, uint32_t b, uint32_t bias)
@@ -736,10 +736,12 @@ __global__ void __launch_bounds__(kRxThreads, 1)
     __syncwarp();
     if (warp == 0) tmem_alloc(tslot, kRxTmem);
     // weights: B operands as K-major planes (chunk (row n, K column kk) at kk * rows * 16 + n * 16)
-    auto h8 = [&](const float *src) {   // 8 FP32 weights -> 16 bytes of FP16
+    // 8 FP32 weights of a layer that reads GELU outputs -> 16 bytes of FP16 / BF16,
+    // halved (the epilogues store 2 GELU(u))
+    auto h8 = [&](const float *src) {
         uint32_t w[4];
 #pragma unroll
-        for (int i = 0; i < 4; i++) w[i] = pack2<BF>(src[2 * i], src[2 * i + 1]);
+        for (int i = 0; i < 4; i++) w[i] = pack2<BF>(0.5f * src[2 * i], 0.5f * src[2 * i + 1]);
         return make_uint4(w[0], w[1], w[2], w[3]);
     };
     for (int u = tid; u < 36 * 32; u += kRxThreads) {

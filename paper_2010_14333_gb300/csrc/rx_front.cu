@@ -172,6 +172,26 @@ struct TwSmem {
     int s, mask;
     __device__ __forceinline__ float2 operator()(int a) const { return cmul(hi[a >> s], lo[a & mask]); }
 };
+// x[r] times W^(a r), r = 1..15 (conjugated twiddles when CONJ), W the table's root.
+// Four twiddles come from the table (exponents a, 4a, 8a, 12a); the others are the
+// powers w^2 = w w, w^3 = w^2 w of the first and the products W^(4qa) w^b, a few
+// roundings more than a table value each.  The caller keeps 15 a below the table's
+// length.
+template <bool CONJ>
+__device__ __forceinline__ void twiddle16(float2 (&x)[16], const TwSmem &tw, int a)
+{
+    const float2 w1 = tw(a), w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+    const float2 wb[4] = {make_float2(1.f, 0.f), w1, w2, w3};
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float2 wq = q ? tw(4 * q * a) : make_float2(1.f, 0.f);
+#pragma unroll
+        for (int b = (q ? 0 : 1); b < 4; b++) {
+            const float2 w = q ? (b ? cmul(wq, wb[b]) : wq) : wb[b];
+            x[4 * q + b] = CONJ ? cmulc(x[4 * q + b], w) : cmul(x[4 * q + b], w);
+        }
+    }
+}
 __device__ __forceinline__ TwSmem stage_tw(const float2 *__restrict__ gtab, int M, float2 *sm)
 {
     int m = 31 - __clz(M);
@@ -310,9 +330,10 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2
         x[q] = make_float2(ua, ub);
     }
     dft16<false>(x);
+    twiddle16<false>(x, tw, n1);
     float2 *out = fftws + (size_t)pair * g.N + n1;
 #pragma unroll
-    for (int k2 = 0; k2 < 16; k2++) out[(size_t)k2 * g.N2] = k2 ? cmul(x[k2], tw(n1 * k2)) : x[0];
+    for (int k2 = 0; k2 < 16; k2++) out[(size_t)k2 * g.N2] = x[k2];
 }
 
 // digit reversal of a P-digit base-16 index
@@ -358,8 +379,7 @@ __global__ void __launch_bounds__(256, 3) k_kk_rows(KkGeom g, float2 *__restrict
 #pragma unroll
     for (int r = 0; r < 16; r++) x[r] = active ? d[t + r * TPR] : make_float2(0.f, 0.f);
     dft16<false>(x);
-#pragma unroll
-    for (int r = 1; r < 16; r++) x[r] = cmul(x[r], tw2(t * r));
+    twiddle16<false>(x, tw2, t);
     if (P == 1) {
 #pragma unroll
         for (int r = 0; r < 16; r++) x[r] = hilbert_mul(x[r], k2 + 16 * drev16<P>(r), g.N);
@@ -382,8 +402,7 @@ __global__ void __launch_bounds__(256, 3) k_kk_rows(KkGeom g, float2 *__restrict
         for (int r = 0; r < 16; r++) x[r] = s[pad16(o + j + r * sub)];
         dft16<false>(x);
         if (p < P - 1) {
-#pragma unroll
-            for (int r = 1; r < 16; r++) x[r] = cmul(x[r], tw2(j * r * (N2 / M)));
+            twiddle16<false>(x, tw2, j * (N2 / M));
 #pragma unroll
             for (int r = 0; r < 16; r++) s[pad16(o + j + r * sub)] = x[r];
             __syncthreads();
@@ -403,10 +422,8 @@ __global__ void __launch_bounds__(256, 3) k_kk_rows(KkGeom g, float2 *__restrict
         const int M = N2 >> (4 * p), sub = M / 16;
         int o = (t / sub) * M, j = t % sub;
 #pragma unroll
-        for (int r = 0; r < 16; r++) {
-            x[r] = s[pad16(o + j + r * sub)];
-            if (r) x[r] = cmulc(x[r], tw2(j * r * (N2 / M)));
-        }
+        for (int r = 0; r < 16; r++) x[r] = s[pad16(o + j + r * sub)];
+        twiddle16<true>(x, tw2, j * (N2 / M));
         dft16<true>(x);
 #pragma unroll
         for (int r = 0; r < 16; r++) s[pad16(o + j + r * sub)] = x[r];
@@ -414,10 +431,8 @@ __global__ void __launch_bounds__(256, 3) k_kk_rows(KkGeom g, float2 *__restrict
     }
     // inverse pass 0 to global memory
 #pragma unroll
-    for (int r = 0; r < 16; r++) {
-        x[r] = s[pad16(t + r * TPR)];
-        if (r) x[r] = cmulc(x[r], tw2(t * r));
-    }
+    for (int r = 0; r < 16; r++) x[r] = s[pad16(t + r * TPR)];
+    twiddle16<true>(x, tw2, t);
     dft16<true>(x);
     if (active)
 #pragma unroll
@@ -507,8 +522,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
 #pragma unroll
     for (int k2 = 0; k2 < 16; k2++) x[k2] = in[(size_t)k2 * g.N2];
     __syncthreads();   // staged twiddles and rows
-#pragma unroll
-    for (int k2 = 1; k2 < 16; k2++) x[k2] = cmulc(x[k2], tw(n1 * k2));
+    twiddle16<true>(x, tw, n1);
     dft16<true>(x);
     const float invN = 1.0f / (float)g.N;
 #pragma unroll
