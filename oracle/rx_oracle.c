@@ -561,26 +561,37 @@ typedef struct {
     double mu_pam, sd_pam;
 } ctx;
 
-static int32_t code_at(const ctx *x, int64_t n)
-{
-    const orx *h = x->h;
-    if (n < 0) return h->have_first ? h->first_code : x->cur[0];   /* pre-stream: first sample replicated */
-    if (n >= x->base) return x->cur[n - x->base];
-    int64_t i = n - (x->base - h->chist_len);
-    return (i >= 0) ? h->chist[i] : 0;   /* never reached for valid configs */
-}
-/* a read before the history a call keeps is a bug of this program: stop loudly */
+/* a read before the history a call keeps, or past what the call has computed, is a
+ * bug of this program: stop loudly */
 static void history_miss(const char *what, int64_t idx, int64_t start)
 {
     fprintf(stderr, "rx_oracle: %s index %lld precedes the kept history (from %lld)\n", what, (long long)idx,
             (long long)start);
     abort();
 }
+static void past_end(const char *what, int64_t idx, int64_t end)
+{
+    fprintf(stderr, "rx_oracle: %s index %lld is past the computed values (to %lld)\n", what, (long long)idx,
+            (long long)end);
+    abort();
+}
+static int32_t code_at(const ctx *x, int64_t n)
+{
+    const orx *h = x->h;
+    if (n < 0) return h->have_first ? h->first_code : x->cur[0];   /* pre-stream: first sample replicated */
+    if (n >= x->base) return x->cur[n - x->base];
+    int64_t i = n - (x->base - h->chist_len);
+    if (i < 0) history_miss("12-bit code", n, x->base - h->chist_len);
+    return h->chist[i];
+}
 static cx e_at(const ctx *x, int64_t n)
 {
     const orx *h = x->h;
     if (n < 0) return cx_mk(0.0, 0.0);
-    if (n >= x->E_start) return x->E[n - x->E_start];
+    if (n >= x->E_start) {
+        if (n >= x->E_start + x->E_len) past_end("field", n, x->E_start + x->E_len);
+        return x->E[n - x->E_start];
+    }
     if (n < h->ehist_start) history_miss("field", n, h->ehist_start);
     return h->ehist[n - h->ehist_start];
 }
@@ -589,7 +600,10 @@ static cx r_at(const ctx *x, int64_t m)   /* the field on the grid the filter re
     const orx *h = x->h;
     if (!h->rs) return e_at(x, m);
     if (m < 0) return cx_mk(0.0, 0.0);
-    if (m >= x->R_start) return x->R[m - x->R_start];
+    if (m >= x->R_start) {
+        if (m >= x->R_start + x->R_len) past_end("resampled field", m, x->R_start + x->R_len);
+        return x->R[m - x->R_start];
+    }
     if (m < h->rhist_start) history_miss("resampled field", m, h->rhist_start);
     return h->rhist[m - h->rhist_start];
 }
@@ -597,7 +611,10 @@ static cx y_at(const ctx *x, int64_t m)
 {
     const orx *h = x->h;
     if (m < 0) return cx_mk(0.0, 0.0);
-    if (m >= x->y_start) return x->y[m - x->y_start];
+    if (m >= x->y_start) {
+        if (m >= x->y_start + x->y_len) past_end("2-sps sample", m, x->y_start + x->y_len);
+        return x->y[m - x->y_start];
+    }
     if (m < h->yhist_start) history_miss("2-sps sample", m, h->yhist_start);
     return h->yhist[m - h->yhist_start];
 }
