@@ -1168,7 +1168,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fd", action="store_true")
     ap.add_argument("--no-rs", action="store_true")
-    ap.add_argument("--smi-ms", type=int, default=50, help="clock sampling period during the timed steps")
+    ap.add_argument("--smi-ms", type=int, default=10, help="clock sampling period (ms) during the timed steps")
     ap.add_argument("--no-sweep", action="store_true", help="skip the Q-factor versus SNR sweep of every format")
     ap.add_argument("--no-dd", action="store_true", help="skip the leg of the paper's short symbol-by-symbol equaliser")
     ap.add_argument("--stability", type=int, default=5720,
