@@ -281,7 +281,7 @@ __global__ void k_pad_fill(uint8_t *dst, long long nbytes, const uint8_t *hist_e
 {
     uint32_t c;
     if (hist_end) {
-        uint32_t b0 = hist_end[-3], b1 = hist_end[-2], b2 = hist_end[-1];
+        uint32_t b1 = hist_end[-2], b2 = hist_end[-1];   // the pair's last two bytes
         c = order == 0 ? (b1 >> 4) | (b2 << 4) : ((b1 & 0xFu) << 8) | b2;   // second sample of the pair
     } else {
         c = *code;

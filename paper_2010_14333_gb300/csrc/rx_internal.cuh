@@ -19,7 +19,7 @@ constexpr int kEqWarpsMax = 8;    // most warps (equaliser blocks) per K3 CTA
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before flagging RX_ETIMEOUT
 constexpr int kSlots = 3;
 constexpr int kMaxEqBlock = 4096;  // largest eq_block (symbols)
-constexpr int kPrbsWords = 1040;   // PRBS-15 period + 256 bits, bit-packed MSB first         // per-call buffer ring (field, MF output, decisions, carrier/gain)
+constexpr int kPrbsWords = 1040;   // PRBS-15 period + 256 bits, bit-packed MSB first
 
 // counters in DevState::cnt
 enum { C_SYMBOLS, C_BITS, C_BITERR, C_RAWERR, C_SYMERR, C_SLIP, C_NEAR, C_AMBIG, C_WINDOWS, C_NCNT };
