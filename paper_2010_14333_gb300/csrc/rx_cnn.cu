@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(kRxThreads, 1)
                 uint4 *__restrict__ winrec, const uint32_t *__restrict__ prbs_bits, long long k_first, float scale,
                 int mq, float2 *__restrict__ soft, int *err)
 {
-    extern __shared__ __align__(1024) unsigned char sm[];
+    extern __shared__ __align__(16) unsigned char sm[];   // no-swizzle operands: 16-byte rows
     unsigned char *sW2 = sm + RxSmem::W2, *sW3 = sm + RxSmem::W3, *sM1 = sm + RxSmem::M1, *sM2 = sm + RxSmem::M2;
     unsigned char *sB1 = sm + RxSmem::B1;
     uint32_t *bh = reinterpret_cast<uint32_t *>(sm + RxSmem::BH);   // half2 bias pairs
