@@ -389,22 +389,28 @@ __global__ void __launch_bounds__(256, 3) k_kk_rows(KkGeom g, float2 *__restrict
             for (int r = 0; r < 16; r++) d[r] = x[r];
         return;
     }
+    // a pass's 16 elements base + r stride sit at pad16(base) + r (stride + stride / 16)
+    // when stride is a multiple of 16, or base is one and stride is 1: one pointer per
+    // pass and compile-time offsets
+    float2 *const s0 = s + pad16(t);
+    constexpr int STR0 = TPR + TPR / 16;
 #pragma unroll
-    for (int r = 0; r < 16; r++) s[pad16(t + r * TPR)] = x[r];
+    for (int r = 0; r < 16; r++) s0[r * STR0] = x[r];
     __syncthreads();
     // remaining forward passes; the last one is fused with the multiplier and the
     // first inverse pass
 #pragma unroll
     for (int p = 1; p < P; p++) {
-        const int M = N2 >> (4 * p), sub = M / 16;
+        const int M = N2 >> (4 * p), sub = M / 16, str = sub + sub / 16;
         int o = (t / sub) * M, j = t % sub;
+        float2 *const sb = s + pad16(o + j);
 #pragma unroll
-        for (int r = 0; r < 16; r++) x[r] = s[pad16(o + j + r * sub)];
+        for (int r = 0; r < 16; r++) x[r] = sb[r * str];
         dft16<false>(x);
         if (p < P - 1) {
             twiddle16<false>(x, tw2, j * (N2 / M));
 #pragma unroll
-            for (int r = 0; r < 16; r++) s[pad16(o + j + r * sub)] = x[r];
+            for (int r = 0; r < 16; r++) sb[r * str] = x[r];
             __syncthreads();
         } else {
             // M = 16: positions o + r hold X[k2 + 16 * drev(o + r)]
@@ -412,26 +418,27 @@ __global__ void __launch_bounds__(256, 3) k_kk_rows(KkGeom g, float2 *__restrict
             for (int r = 0; r < 16; r++) x[r] = hilbert_mul(x[r], k2 + 16 * drev16<P>(o + r), g.N);
             dft16<true>(x);
 #pragma unroll
-            for (int r = 0; r < 16; r++) s[pad16(o + r)] = x[r];
+            for (int r = 0; r < 16; r++) sb[r] = x[r];   // sub = 1, j = 0
             __syncthreads();
         }
     }
     // inverse passes P-2 .. 1
 #pragma unroll
     for (int p = P - 2; p >= 1; p--) {
-        const int M = N2 >> (4 * p), sub = M / 16;
+        const int M = N2 >> (4 * p), sub = M / 16, str = sub + sub / 16;
         int o = (t / sub) * M, j = t % sub;
+        float2 *const sb = s + pad16(o + j);
 #pragma unroll
-        for (int r = 0; r < 16; r++) x[r] = s[pad16(o + j + r * sub)];
+        for (int r = 0; r < 16; r++) x[r] = sb[r * str];
         twiddle16<true>(x, tw2, j * (N2 / M));
         dft16<true>(x);
 #pragma unroll
-        for (int r = 0; r < 16; r++) s[pad16(o + j + r * sub)] = x[r];
+        for (int r = 0; r < 16; r++) sb[r * str] = x[r];
         __syncthreads();
     }
     // inverse pass 0 to global memory
 #pragma unroll
-    for (int r = 0; r < 16; r++) x[r] = s[pad16(t + r * TPR)];
+    for (int r = 0; r < 16; r++) x[r] = s0[r * STR0];
     twiddle16<true>(x, tw2, t);
     dft16<true>(x);
     if (active)
