@@ -225,6 +225,7 @@ constexpr int kRawWords = 100;   // 384 bytes of a row + spare word, 16-byte mul
 
 // (CTAs of kCtaK1 threads; the loop is unrolled so that every load issues before the
 // first one is used)
+template <int N2T>
 __device__ __forceinline__ void stage_rows(const KkGeom &g, const KkPacked &pk, int pair, int c0,
                                            uint32_t (*raw)[kRawWords], bool hb)
 {
@@ -233,7 +234,7 @@ __device__ __forceinline__ void stage_rows(const KkGeom &g, const KkPacked &pk, 
     for (int i = threadIdx.x; i < 32 * 24; i += kCtaK1) {
         int row = i / 24, ch = i - 24 * (i / 24), blk = row >> 4, q = row & 15;
         if (blk && !hb) continue;
-        long long n = ols_ws(g, 2 * pair + blk) + c0 + (long long)g.N2 * q;
+        long long n = ols_ws(g, 2 * pair + blk) + c0 + (long long)N2T * q;
         long long vb = (n - g.cbase) * 3 / 2 + 16 * ch;   // >= 0 for every window of the call
         const uint8_t *src = vb < pk.hist_bytes ? pk.hist + vb : pk.in + (vb - pk.hist_bytes);
         *reinterpret_cast<uint4 *>(&raw[row][4 * ch]) = __ldg(reinterpret_cast<const uint4 *>(src));
@@ -279,8 +280,9 @@ __device__ __forceinline__ uint32_t first_code(const KkPacked &pk, const DevStat
 
 // K1a: unpack, u = ln(I)/2 by table, radix-16 pass over the stride-N2 index of two
 // packed blocks, twiddle.  CTAs with blockIdx.y == npairs copy the next history.
-// ORD: the pack order of the 12-bit input.
-template <int ORD>
+// ORD: the pack order of the 12-bit input; N2T: the row length N / 16 (256 or 4096), so
+// that the stride-N2 accesses take compile-time offsets.
+template <int ORD, int N2T>
 __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2 *__restrict__ fftws,
                                                   const KkTables tb, DevState *dst)
 {
@@ -308,15 +310,15 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2
     const int c0 = blockIdx.x * blockDim.x;
     const int jb = 2 * pair + 1;
     const bool hb = jb < g.J;
-    stage_rows(g, pk, pair, c0, raw, hb);
+    stage_rows<N2T>(g, pk, pair, c0, raw, hb);
     const uint32_t c_first = first_code(pk, dst);
     if (pk.first_call && blockIdx.x == 0 && pair == 0 && threadIdx.x == 0) dst->first_code = (int)c_first;
     __syncthreads();
     const int t = threadIdx.x, n1 = c0 + t;
     const long long wa = ols_ws(g, 2 * pair) + c0 + t, wb = hb ? ols_ws(g, jb) + c0 + t : 0;
     // rows q below qa (qb) hold stream indices before the stream: the first code
-    const int qa = wa < 0 ? (int)min((-wa + g.N2 - 1) / g.N2, 16LL) : 0;
-    const int qb = wb < 0 ? (int)min((-wb + g.N2 - 1) / g.N2, 16LL) : 0;
+    const int qa = wa < 0 ? (int)min((-wa + N2T - 1) / N2T, 16LL) : 0;
+    const int qb = wb < 0 ? (int)min((-wb + N2T - 1) / N2T, 16LL) : 0;
     const ColPos cp = col_pos<ORD>(t);
     float2 x[16];
 #pragma unroll
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_fwd(KkGeom g, KkPacked pk, float2
     twiddle16<false>(x, tw, n1);
     float2 *out = fftws + (size_t)pair * g.N + n1;
 #pragma unroll
-    for (int k2 = 0; k2 < 16; k2++) out[(size_t)k2 * g.N2] = x[k2];
+    for (int k2 = 0; k2 < 16; k2++) out[k2 * N2T] = x[k2];
 }
 
 // digit reversal of a P-digit base-16 index
@@ -499,8 +501,9 @@ __device__ __forceinline__ void carrier_sums(const KkGeom &g, DevState *dst, flo
 // K1c: inverse radix-16 pass, then for every kept output
 // E = sqrt(I) * exp(j phi) (Fig. 1d), written at its stream position, and the
 // per-call carrier / intensity sums (exact integer totals, carrier_sums).  The
-// codes for sqrt(I) come from the same staged rows.  ORD: the pack order.
-template <int ORD>
+// codes for sqrt(I) come from the same staged rows.  ORD: the pack order; N2T: the
+// row length N / 16.
+template <int ORD, int N2T>
 __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const float2 *__restrict__ fftws,
                                                   const KkTables tb, float2 *__restrict__ E,
                                                   const float2 *__restrict__ E_prev, DevState *dst)
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
     int pair = blockIdx.y;
     const int c0 = blockIdx.x * blockDim.x;
     const bool hb = 2 * pair + 1 < g.J;
-    stage_rows(g, pk, pair, c0, raw, hb);
+    stage_rows<N2T>(g, pk, pair, c0, raw, hb);
     const uint32_t c_first = first_code(pk, dst);
     float sre = 0.f, sim = 0.f;
     int si2 = 0;
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
     float2 x[16];
     const float2 *in = fftws + (size_t)pair * g.N + n1;
 #pragma unroll
-    for (int k2 = 0; k2 < 16; k2++) x[k2] = in[(size_t)k2 * g.N2];
+    for (int k2 = 0; k2 < 16; k2++) x[k2] = in[k2 * N2T];
     __syncthreads();   // staged twiddles and rows
     twiddle16<true>(x, tw, n1);
     dft16<true>(x);
@@ -545,7 +548,7 @@ __global__ void __launch_bounds__(kCtaK1) k_kk_inv(KkGeom g, KkPacked pk, const 
         const int tneg = ws < 0 ? (int)(-ws) : 0;
 #pragma unroll
         for (int q = 0; q < 16; q++) {
-            int tt = n1 + g.N2 * q;
+            int tt = n1 + N2T * q;
             if (tt < tlo || tt >= thi) continue;
             uint32_t code = tt < tneg ? c_first : col_code<ORD>(raw[16 * half + q], cp);
             float phi = (half ? x[q].y : x[q].x) * invN;
@@ -845,8 +848,15 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     dim3 grid_a(g.N2 / kCtaK1, g.npairs + (inp.hist_next ? 1 : 0));
     if (sync.wait_fwd) cudaStreamWaitEvent(st, sync.wait_fwd, 0);
     prof_stage(prof, 1, st);
-    if (pk.order) k_kk_fwd<1><<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
-    else k_kk_fwd<0><<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
+    if (g.N2 != 4096 && g.N2 != 256) return cudaErrorInvalidValue;   // N is 65536 or 4096
+    const bool long_rows = g.N2 == 4096;
+    if (pk.order) {
+        if (long_rows) k_kk_fwd<1, 4096><<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
+        else k_kk_fwd<1, 256><<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
+    } else {
+        if (long_rows) k_kk_fwd<0, 4096><<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
+        else k_kk_fwd<0, 256><<<grid_a, kCtaK1, 0, st>>>(g, pk, fftws, tb, dst);
+    }
     if (sync.rec_fwd) cudaEventRecord(sync.rec_fwd, st);
     prof_stage(prof, -2, st);
     int rows = g.npairs * 16;
@@ -861,8 +871,13 @@ cudaError_t launch_kk_front(const KkGeom &g, const KkInput &inp, float2 *fftws, 
     }
     if (sync.wait_inv) cudaStreamWaitEvent(st, sync.wait_inv, 0);
     prof_stage(prof, -3, st);
-    if (pk.order) k_kk_inv<1><<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, dst);
-    else k_kk_inv<0><<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, dst);
+    if (pk.order) {
+        if (long_rows) k_kk_inv<1, 4096><<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, dst);
+        else k_kk_inv<1, 256><<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, dst);
+    } else {
+        if (long_rows) k_kk_inv<0, 4096><<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, dst);
+        else k_kk_inv<0, 256><<<grid, kCtaK1, 0, st>>>(g, pk, fftws, tb, E, E_prev, dst);
+    }
     prof_stage(prof, -4, st);
     return cudaGetLastError();
 }
