@@ -348,6 +348,25 @@ def gpu_arm(args, rank, world, local):
     e2e_ms, e2e_value = replica_throughput(e2e_ms, e2e_steps * args.bufs_per_step * NB, dist, "cuda")
     e2e_value /= 1e9
     rx.rx_destroy(h2)
+    # one step's host-to-device copies alone (pinned ring to the device, one copy per
+    # buffer as the receiver issues them, best of three): the copy rate of this machine,
+    # which bounds the end-to-end number
+    nbytes = NB * 3 // 2
+    h2d_gbs = None
+    dst = torch.empty(nbytes * args.bufs_per_step, dtype=torch.uint8, device="cuda")
+    best = None
+    for _ in range(3):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for j in range(args.bufs_per_step):
+            dst[j * nbytes:(j + 1) * nbytes].copy_(host_ring[j % args.ring], non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        t = c0.elapsed_time(c1)
+        best = t if best is None else min(best, t)
+    if best and best > 0:
+        h2d_gbs = nbytes * args.bufs_per_step / (best * 1e-3) / 1e9
+    del dst
 
     # ---- per-buffer latency, one buffer in flight at a time (the paper's budget:
     # five streams of 2^22 samples within 5 * 2^22 / 4 GS/s = 5.243 ms; one buffer
@@ -518,7 +537,8 @@ def gpu_arm(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args),
             "e2e": {"value": e2e_value, "unit": "GSa/s", "h2d_bytes_per_step": h2d // e2e_steps,
-                    "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps, "warmup_run": e2e_warm},
+                    "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps, "warmup_run": e2e_warm,
+                    "h2d_gbs_copies_alone": h2d_gbs},
             "roofline": roof, "stages": stages, "latency": latency, "cpu_baseline": cpu, "cnn": cnn_line, "precision": prec_line,
             "fd_filter": fd_line, "batched": batched_line,
             "resampler": rs_line, "q_sweep": sweep_line, "stability": stab_line, "diff_coding": diff_line, "dd_symbol_equaliser": dd_line,
