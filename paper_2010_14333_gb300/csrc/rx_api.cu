@@ -69,7 +69,7 @@ struct rx_handle {
     // three slots.
     cudaStream_t front, front2, mid, back, tail, copy;   // KK: field | matched filter | equaliser | demap
     cudaEvent_t ev_fork, ev_front, ev_hist, ev_join, ev_yfree[kSlots], ev_efree[kSlots],
-        ev_dfree[kSlots], ev_inready[2], ev_infree[2], ev_cfree[2];
+        ev_dfree[kSlots], ev_inready[kInSlots], ev_infree[kInSlots], ev_cfree[2];
     float2 *taps[2], *twN, *twN2, *ds_tab;
     float *lnt;
     float *rrc;
@@ -77,7 +77,7 @@ struct rx_handle {
     float4 *dbg_win;
     float2 *dbg_z;
     DevState *st;
-    uint8_t *in_stage[2], *bits_stage;   // device staging of the host-buffer entry points
+    uint8_t *in_stage[kInSlots], *bits_stage;   // device staging of the host-buffer entry points
     float2 *zbuf;                   // payload soft symbols of the tensor-core FIR forms
     float2 *gpart;                  // frozen forms: tap-gradient partials, one row of 32 per window
     int rs;                         // resampler of the KK field to the transmitter's grid
@@ -520,7 +520,7 @@ void rx_destroy(rx_handle *h)
     if (h->tail) cudaStreamSynchronize(h->tail);
     if (h->copy) cudaStreamSynchronize(h->copy);
     void *ptrs[] = {h->codes[0], h->codes[1], h->fftws[0], h->fftws[1], h->prbs, h->taps[0], h->taps[1], h->twN,
-                    h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st, h->in_stage[0], h->in_stage[1],
+                    h->twN2, h->ds_tab, h->rrc, h->dbg_win, h->dbg_z, h->st,
                     h->bits_stage, h->lnt, h->prbs_bits, h->phist[0], h->phist[1], h->phist[2], h->zbuf, h->gpart, h->fd_H, h->fd_tw, h->R[0], h->R[1],
                     h->rs_tab, h->clk, h->lat_dev};
     for (void *p : ptrs)
@@ -544,10 +544,14 @@ void rx_destroy(rx_handle *h)
     if (h->back) cudaStreamDestroy(h->back);
     if (h->tail) cudaStreamDestroy(h->tail);
     if (h->copy) cudaStreamDestroy(h->copy);
-    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_join, &h->ev_inready[0],
-                          &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1], &h->ev_cfree[0], &h->ev_cfree[1]};
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_join, &h->ev_cfree[0], &h->ev_cfree[1]};
     for (cudaEvent_t *ev : evs)
         if (*ev) cudaEventDestroy(*ev);
+    for (int i = 0; i < kInSlots; i++) {
+        if (h->ev_inready[i]) cudaEventDestroy(h->ev_inready[i]);
+        if (h->ev_infree[i]) cudaEventDestroy(h->ev_infree[i]);
+        if (h->in_stage[i]) cudaFree(h->in_stage[i]);
+    }
     free(h->prof_used);
     free(h);
 }
@@ -748,7 +752,7 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
     RX_ALLOC(h->prbs_bits, kPrbsWords * sizeof(uint32_t));
     RX_ALLOC(h->rrc, (2 * h->hmf + 1) * sizeof(float));
     RX_ALLOC(h->st, sizeof(DevState));
-    for (int i = 0; i < 2; i++) RX_ALLOC(h->in_stage[i], nb * 3 / 2 + 16);
+    for (int i = 0; i < kInSlots; i++) RX_ALLOC(h->in_stage[i], nb * 3 / 2 + 16);
     RX_ALLOC(h->bits_stage, rx_max_bits(h) / 8 + 16);
     if (c.fir_prec >= RX_FIR_BF16) RX_ALLOC(h->zbuf, symcap * sizeof(float2));
     if (c.fir_prec >= RX_FIR_FROZEN_F32) RX_ALLOC(h->gpart, (size_t)(kMaxEqBlock / kWin) * 32 * sizeof(float2));
@@ -866,10 +870,12 @@ rx_status rx_create(rx_format f, double baud, double fs, int64_t buf_len, const 
                   cudaStreamCreateWithFlags(&h->back, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->tail, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess;
-        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_join, &h->ev_inready[0],
-                              &h->ev_inready[1], &h->ev_infree[0], &h->ev_infree[1], &h->ev_cfree[0], &h->ev_cfree[1]};
+        cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_front, &h->ev_hist, &h->ev_join, &h->ev_cfree[0], &h->ev_cfree[1]};
         for (cudaEvent_t *ev : evs)
             ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < kInSlots; i++)
+            ok = ok && cudaEventCreateWithFlags(&h->ev_inready[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->ev_infree[i], cudaEventDisableTiming) == cudaSuccess;
         for (int i = 0; i < kSlots; i++)
             ok = ok && cudaEventCreateWithFlags(&h->ev_yfree[i], cudaEventDisableTiming) == cudaSuccess &&
                  cudaEventCreateWithFlags(&h->ev_efree[i], cudaEventDisableTiming) == cudaSuccess &&
@@ -948,6 +954,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     cudaStream_t st4 = four ? stail : sb;
     cudaError_t e = cudaSuccess;
     int par = (int)(h->calls & 1);
+    const int isl = (int)(h->calls % kInSlots);   // input staging slot of a host-buffer call
     const int spar = (int)(h->calls % 3);   // PAM sums slot: the filter of call i clears call i+2's
     int ds = (int)(h->calls % kSlots);   // decision slot of this call
     // KK in the pipeline: the field of odd calls on the second front-end stream.
@@ -957,12 +964,12 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     if (alt && par) sf = h->front2;
     const KkSync ksync = {alt ? h->ev_hist : nullptr, alt ? h->ev_hist : nullptr, alt ? h->ev_front : nullptr};
     if (host_in) {
-        in = h->in_stage[par];
-        if (sc != sf) cudaStreamWaitEvent(sc, h->ev_infree[par], 0);   // the front end two calls back is done
-        e = cudaMemcpyAsync(h->in_stage[par], host_in, (size_t)(h->nb * 3 / 2), cudaMemcpyHostToDevice, sc);
+        in = h->in_stage[isl];
+        if (sc != sf) cudaStreamWaitEvent(sc, h->ev_infree[isl], 0);   // the front end kInSlots calls back is done
+        e = cudaMemcpyAsync(h->in_stage[isl], host_in, (size_t)(h->nb * 3 / 2), cudaMemcpyHostToDevice, sc);
         if (sc != sf) {
-            cudaEventRecord(h->ev_inready[par], sc);
-            cudaStreamWaitEvent(sf, h->ev_inready[par], 0);
+            cudaEventRecord(h->ev_inready[isl], sc);
+            cudaStreamWaitEvent(sf, h->ev_inready[isl], 0);
         }
     }
     if (host_out) bits_out = h->bits_stage;
@@ -1030,7 +1037,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
     }
     if (h->kk) h->hw = (h->hw + 1) % 3;
     if (three) {
-        if (host_in && sc != sf) cudaEventRecord(h->ev_infree[par], sf);   // the field has read the input
+        if (host_in && sc != sf) cudaEventRecord(h->ev_infree[isl], sf);   // the field has read the input
         cudaEventRecord(h->ev_front, sf);
         cudaStreamWaitEvent(sm, h->ev_front, 0);
     }
@@ -1097,7 +1104,7 @@ static rx_status enqueue_call(rx_handle *h, const uint8_t *in, uint8_t *bits_out
         cudaEventRecord(rel, sm);
         cudaStreamWaitEvent(sb, rel, 0);
     } else {
-        if (host_in && sc != sf) cudaEventRecord(h->ev_infree[par], sf);
+        if (host_in && sc != sf) cudaEventRecord(h->ev_infree[isl], sf);
         if (two) {
             cudaEventRecord(h->ev_front, sf);
             cudaStreamWaitEvent(sb, h->ev_front, 0);

@@ -18,6 +18,7 @@ constexpr int kCtaK1 = 256;       // threads per K1a / K1c CTA
 constexpr int kEqWarpsMax = 8;    // most warps (equaliser blocks) per K3 CTA
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before flagging RX_ETIMEOUT
 constexpr int kSlots = 3;
+constexpr int kInSlots = 4;     // device staging slots of host input buffers (copies run up to 3 calls ahead)
 constexpr int kMaxEqBlock = 4096;  // largest eq_block (symbols)
 constexpr int kPrbsWords = 1040;   // PRBS-15 period + 256 bits, bit-packed MSB first
 
