@@ -261,10 +261,11 @@ rx_status rx_process_host(rx_handle *h, const uint8_t *host_in, uint8_t *host_bi
 
 /* rx_process_batch with HOST buffers (page-locked for the copies to overlap):
  * host_ins[i] holds buffer i as packed 12-bit bytes, host_outs[i] receives its
- * bits (capacity rx_max_bits / 8 + 1 bytes).  The copy of buffer i+1 to the
- * device runs on a stream the handle owns, concurrently with the front end of
- * buffer i; each buffer's bits are copied back after its demap.  The outputs are
- * valid once cuda_stream has reached the end of the call. */
+ * bits (capacity rx_max_bits / 8 + 1 bytes).  The copies to the device run on a
+ * stream the handle owns, into four device staging slots, so the copy of buffer
+ * i+1 (up to i+3) overlaps the front end of buffer i; each buffer's bits are
+ * copied back after its demap.  The outputs are valid once cuda_stream has
+ * reached the end of the call. */
 rx_status rx_process_host_batch(rx_handle *h, const uint8_t *const *host_ins, uint8_t *const *host_outs, int n,
                                 void *cuda_stream, int64_t *nbits_out);
 
