@@ -81,3 +81,26 @@ def test_product_package_never_imports_the_oracle():
                     if isinstance(node, ast.ImportFrom):
                         assert not (node.module or "").startswith("oracle"), path
             assert "rx_oracle" not in src and "liborx" not in src, path
+
+
+def test_reference_arm_prints_its_line():
+    """The reference arm (the FP64 oracle on the host cores) runs one step of the
+    workload's buffers and prints one JSON line with the fields the launch contract
+    asks of it: impl, the GPU arm's metric and unit, its own cpu_baseline and a zero-copy
+    e2e block whose value is the line's."""
+    import json
+    import subprocess
+    import sys
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GSa/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GSa/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert 0 < d["ber"] < 0.02
